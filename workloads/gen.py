@@ -1,0 +1,218 @@
+"""Seeded input generators.
+
+Random numbers: SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), evaluated in counter form: the
+k-th draw of stream `seed` is mix(seed + (k+1)*GOLDEN) mod 2^64.  Doubles take
+the top 53 bits: u = (z >> 11) * 2^-53 in [0, 1).
+
+Grids follow one convention everywhere in this repository: a level with n
+interior points per side is stored as an (n+2) x (n+2) row-major array indexed
+[j, i] (i = x, fastest), interior i, j in 1..n, and a ghost ring at 0 and n+1
+that carries the Dirichlet value zero.
+
+Stencils are stored as five planes [O, W, S, SW, NW] of shape (n+2, n+2): the
+matrix entries a(p, p) and a(p, p-x), a(p, p-y), a(p, p-x-y), a(p, p-x+y).  The
+other four couplings follow from the symmetry of A: E(p) = W(p+x),
+N(p) = S(p+y), NE(p) = SW(p+x+y), SE(p) = NW(p+x-y).  Couplings that would
+reach a ghost point are not entries of A (Dirichlet rows drop them) and are
+stored as zero, as is the whole ghost ring of every plane.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+M1 = np.uint64(0xBF58476D1CE4E5B9)
+M2 = np.uint64(0x94D049BB133111EB)
+
+PLANES = ("O", "W", "S", "SW", "NW")
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Draws offset .. offset+count-1 of the SplitMix64 stream `seed` (uint64)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * M1
+        z = (z ^ (z >> np.uint64(27))) * M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """count doubles in [0, 1) from stream `seed`."""
+    z = splitmix64(seed, count)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform_pm1(seed: int, count: int) -> np.ndarray:
+    """count doubles in [-1, 1) from stream `seed`."""
+    return 2.0 * uniform01(seed, count) - 1.0
+
+
+def normal(seed: int, count: int) -> np.ndarray:
+    """count standard normals (Box-Muller on pairs of uniforms of stream `seed`)."""
+    m = (count + 1) // 2
+    u = uniform01(seed, 2 * m)
+    u1 = 1.0 - u[0::2]                 # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+    return z[:count]
+
+
+def is_level_size(n: int) -> bool:
+    """n = 2^m - 1 with m >= 2 (3, 7, 15, ...)."""
+    return n >= 3 and ((n + 1) & n) == 0
+
+
+def grid_zeros(n: int) -> np.ndarray:
+    return np.zeros((n + 2, n + 2), dtype=np.float64)
+
+
+def rhs_uniform(n: int, seed: int) -> np.ndarray:
+    """Right-hand side: interior i.i.d. uniform[-1, 1), ghost ring zero."""
+    f = grid_zeros(n)
+    f[1:n + 1, 1:n + 1] = uniform_pm1(seed, n * n).reshape(n, n)
+    return f
+
+
+def zero_ghost_couplings(planes: np.ndarray) -> np.ndarray:
+    """Zero the ghost ring of all planes and the couplings of interior points to
+    ghost points (in place; returns planes)."""
+    O, W, S, SW, NW = planes
+    n = planes.shape[1] - 2
+    for a in planes:
+        a[0, :] = 0.0
+        a[n + 1, :] = 0.0
+        a[:, 0] = 0.0
+        a[:, n + 1] = 0.0
+    W[:, 1] = 0.0          # (1, j) -> (0, j)
+    S[1, :] = 0.0          # (i, 1) -> (i, 0)
+    SW[:, 1] = 0.0
+    SW[1, :] = 0.0
+    NW[:, 1] = 0.0
+    NW[n, :] = 0.0         # (i, n) -> (i-1, n+1)
+    return planes
+
+
+def poisson5(n: int) -> np.ndarray:
+    """5-point finite-difference Laplacian (unscaled): O = 4, W = S = -1."""
+    planes = np.zeros((5, n + 2, n + 2), dtype=np.float64)
+    planes[0, 1:n + 1, 1:n + 1] = 4.0
+    planes[1, 1:n + 1, 1:n + 1] = -1.0
+    planes[2, 1:n + 1, 1:n + 1] = -1.0
+    return zero_ghost_couplings(planes)
+
+
+def fe9_from_cells(k: np.ndarray) -> np.ndarray:
+    """9-point bilinear (Q1) finite-element stiffness stencil of -div(k grad u)
+    on a uniform grid, with k constant on each cell.
+
+    k has shape (n+1, n+1), k[cj, ci] on the cell whose lower-left node is
+    (ci, cj).  The Q1 element matrix of a square cell, scaled by k, has 2k/3 on
+    its diagonal, -k/6 between nodes sharing a cell edge and -k/3 between
+    opposite corners.  Summing the cells around each node gives
+      O(i,j)  = (2/3) (k[j-1,i-1] + k[j-1,i] + k[j,i-1] + k[j,i])
+      W(i,j)  = -(k[j-1,i-1] + k[j,i-1]) / 6
+      S(i,j)  = -(k[j-1,i-1] + k[j-1,i]) / 6
+      SW(i,j) = -k[j-1,i-1] / 3
+      NW(i,j) = -k[j,i-1] / 3
+    """
+    n = k.shape[0] - 1
+    assert k.shape == (n + 1, n + 1)
+    planes = np.zeros((5, n + 2, n + 2), dtype=np.float64)
+    kll = k[0:n, 0:n]          # cell (i-1, j-1) for interior node (i, j)
+    klr = k[0:n, 1:n + 1]      # cell (i,   j-1)
+    kul = k[1:n + 1, 0:n]      # cell (i-1, j)
+    kur = k[1:n + 1, 1:n + 1]  # cell (i,   j)
+    I = (slice(1, n + 1), slice(1, n + 1))
+    planes[0][I] = (2.0 / 3.0) * (kll + klr + kul + kur)
+    planes[1][I] = -(kll + kul) / 6.0
+    planes[2][I] = -(kll + klr) / 6.0
+    planes[3][I] = -kll / 3.0
+    planes[4][I] = -kul / 3.0
+    return zero_ghost_couplings(planes)
+
+
+def binary_blocks(n: int, block: int, lo: float, hi: float, seed: int, p: float = 0.5) -> np.ndarray:
+    """Cell field on (n+1)^2 cells, constant on block x block tiles, each tile
+    `hi` with probability p (uniform draw < p) else `lo`."""
+    cells = n + 1
+    nb = (cells + block - 1) // block
+    u = uniform01(seed, nb * nb).reshape(nb, nb)
+    tile = np.where(u < p, hi, lo)
+    return np.repeat(np.repeat(tile, block, axis=0), block, axis=1)[:cells, :cells].copy()
+
+
+def gaussian_field(cells: int, std: float, corr_len: float, seed: int) -> np.ndarray:
+    """Periodic Gaussian random field on cells x cells with covariance close to
+    std^2 exp(-r^2 / (2 corr_len^2)): white noise smoothed by a Gaussian filter
+    of width corr_len/sqrt(2), then shifted and scaled to sample mean 0 and
+    sample standard deviation std."""
+    from scipy.ndimage import gaussian_filter
+    w = normal(seed, cells * cells).reshape(cells, cells)
+    g = gaussian_filter(w, sigma=corr_len / np.sqrt(2.0), mode="wrap", truncate=4.0)
+    g = g - g.mean()
+    return g * (std / g.std())
+
+
+def lognormal_cells(n: int, std: float, corr_len: float, seed: int) -> np.ndarray:
+    """k = exp(g) on (n+1)^2 cells, g a Gaussian random field (see gaussian_field)."""
+    return np.exp(gaussian_field(n + 1, std, corr_len, seed))
+
+
+def layered_cells(n: int, values_by_column: np.ndarray) -> np.ndarray:
+    """k depending on the cell column ci only (k[cj, ci] = values_by_column[ci])."""
+    v = np.asarray(values_by_column, dtype=np.float64)
+    assert v.shape == (n + 1,)
+    return np.tile(v, (n + 1, 1))
+
+
+# ----------------------------------------------------------------------------
+# The named workloads.  Each returns (kind, planes, rhs) with float64 arrays.
+# ----------------------------------------------------------------------------
+
+def poisson_problem(n: int = 127, seed: int = 1):
+    """2D Poisson, 5-point stencil, Dirichlet zero boundary, RHS uniform[-1,1)."""
+    return 5, poisson5(n), rhs_uniform(n, seed)
+
+
+def binary_contrast_problem(n: int = 2047, block: int = 16, lo: float = 1.0, hi: float = 1e4,
+                            seed_k: int = 2, seed_f: int = 3, p: float = 0.5):
+    """-div(k grad u) with k in {lo, hi} on block x block tiles (Bernoulli p),
+    9-point Q1 stencil, RHS uniform[-1,1)."""
+    k = binary_blocks(n, block, lo, hi, seed_k, p)
+    return 9, fe9_from_cells(k), rhs_uniform(n, seed_f)
+
+
+def lognormal_problem(n: int = 8191, std: float = 2.0, corr_len: float = 32.0,
+                      seed_k: int = 4, seed_f: int = 7):
+    """-div(k grad u) with k = exp(g), g a Gaussian field; 9-point Q1 stencil."""
+    k = lognormal_cells(n, std, corr_len, seed_k)
+    return 9, fe9_from_cells(k), rhs_uniform(n, seed_f)
+
+
+def batched_sizes(count: int = 256, seed: int = 5, choices=(63, 127, 255, 511, 1023)):
+    """Interior sides drawn uniformly from `choices`."""
+    u = uniform01(seed, count)
+    idx = np.minimum((u * len(choices)).astype(np.int64), len(choices) - 1)
+    return [int(choices[i]) for i in idx]
+
+
+def batched_problems(count: int = 256, seed: int = 5, std: float = 1.0, corr_len: float = 32.0,
+                     choices=(63, 127, 255, 511, 1023)):
+    """Independent 9-point log-normal problems of uneven sizes; problem b uses
+    coefficient seed 10000 + 2b and RHS seed 10001 + 2b."""
+    out = []
+    for b, n in enumerate(batched_sizes(count, seed, choices)):
+        k = lognormal_cells(n, std, corr_len, 10000 + 2 * b)
+        out.append((9, fe9_from_cells(k), rhs_uniform(n, 10001 + 2 * b)))
+    return out
+
+
+def high_contrast_problem(n: int = 4095, block: int = 8, lo: float = 1.0, hi: float = 1e6,
+                          seed: int = 6):
+    """Binary blocks k in {1, 1e6} on 8 x 8 cell tiles (the learned-interpolation
+    family); RHS seed = seed + 100000."""
+    return binary_contrast_problem(n, block, lo, hi, seed_k=seed, seed_f=seed + 100000)
