@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""BoxMG V(2,1) throughput on one GB300 (or N replicas), one JSON line.
+
+Workload (default): 2D -div(k grad u) on a 2047 x 2047 interior grid, 9-point
+Q1 finite-element stencil, k in {1, 1e4} on 16 x 16 cell blocks (Bernoulli 0.5,
+seed 2), RHS uniform[-1, 1) (seed 3), four-colour Gauss-Seidel V(2,1), ten
+levels down to 3 x 3, synthetic seeded inputs.
+
+A step is one iteration of the solve loop: one V(2,1) cycle (FP64) followed by
+the residual norm and the device-side convergence test.  `value` is the FP64
+path's unknowns per second per V(2,1) (grid unknowns x steps / device time),
+over all ranks.  The FP32- and BF16-stencil refinement variants and the time to
+a 1e-10 relative residual of every variant are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+`--impl reference` times the CPU oracle (numpy, FP64) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as w  # noqa: E402
+
+METRIC = "unknowns/s per V(2,1) & time to 1e-10 residual: FP64 vs mixed/learned, 1 GB300"
+UNIT = "unknowns/s"
+
+WORKLOADS = {
+    "fe2047-binary1e4": dict(
+        text="2047x2047 interior, 9-point Q1 FE of -div(k grad u), k in {1,1e4} on 16x16 blocks "
+             "(Bernoulli 0.5, seed 2), RHS U[-1,1) seed 3, four-colour GS V(2,1), 10 levels",
+        make=lambda: w.binary_contrast_problem(2047, 16, 1.0, 1e4, seed_k=2, seed_f=3)),
+    "poisson127": dict(
+        text="127x127 interior, 5-point Poisson, RHS U[-1,1) seed 1, red-black GS V(2,1), 6 levels",
+        make=lambda: w.poisson_problem(127, 1)),
+    "lognormal8191": dict(
+        text="8191x8191 interior, 9-point Q1 FE, k = exp(g), g Gaussian field std 2, correlation 32 cells, "
+             "seed 4; RHS U[-1,1) seed 7; 12 levels",
+        make=lambda: w.lognormal_problem(8191, 2.0, 32.0, seed_k=4, seed_f=7)),
+}
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by
+# (workload, variant, kernel); None until captured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ----------------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        return False
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sms, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "samples": len(sms), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------------
+
+ALG_FLOPS_PER_POINT = {5: 9, 9: 17}        # one GS update: (k-1) mul + (k-1) sub + 1 mul
+SWEEP_BYTES = {("fp64", 9): 64, ("fp64", 5): 48, ("fp32", 9): 32, ("fp32", 5): 24, ("bf16", 9): 24, ("bf16", 5): 20}
+
+
+def run_ours(args, rank, local_rank, world):
+    import torch
+    import paper_2502_05279_gb300 as bmg
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    spec = WORKLOADS[args.workload]
+    kind, planes, f = spec["make"]()
+    n = planes.shape[-1] - 2
+    N = n * n
+    coef = torch.from_numpy(planes if kind == 9 else planes[:3].copy()).cuda()
+    rhs = torch.from_numpy(f).cuda()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    variants = {}
+    clock_s = None
+    timed_launches = 0
+    fp64_rate = bmg.measure_fp64_rate() * 1e9        # DP instructions per second, measured here
+    for prec in ("fp64", "fp32", "bf16"):
+        barrier()
+        t0 = time.perf_counter()
+        h = bmg.Hierarchy(kind, coef, precision=prec)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        x = torch.zeros_like(rhs)
+        h.time_cycles(rhs, x, max(args.warmup, 3))
+        barrier()
+        before = h.launch_count
+        if prec == "fp64":
+            with ClockSampler(local_rank) as cs:
+                ms = h.time_cycles(rhs, x, args.steps)
+            clock_s = cs.summary()
+            timed_launches = h.launch_count - before
+        else:
+            ms = h.time_cycles(rhs, x, args.steps)
+        barrier()
+        ms = max_over_ranks(ms)
+        # time to tolerance from a zero guess (host-timed: includes the host polls)
+        x.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        _, iters, relres, ok = h.solve(rhs, x, tol=1e-10, maxit=500)
+        torch.cuda.synchronize()
+        tts_ms = max_over_ranks((time.perf_counter() - t0) * 1e3)
+        prof = h.profile(rhs, torch.zeros_like(rhs), 3)
+        variants[prec] = dict(ms=ms, setup_ms=setup_ms, tts_ms=tts_ms, iters=iters, relres=relres, ok=ok,
+                              prof=prof, h=h)
+
+    # end to end through the public API with host buffers (FP64 path)
+    h = variants["fp64"]["h"]
+    rhs_host = torch.from_numpy(f).pin_memory()
+    x_host = torch.empty_like(rhs_host).pin_memory()
+    rhs_dev = torch.empty_like(rhs)
+    x_dev = torch.empty_like(rhs)
+    e2e_steps = 2
+    e2e_cycles = 0
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rhs_dev.copy_(rhs_host, non_blocking=True)
+        x_dev.zero_()
+        _, it, _, _ = h.solve(rhs_dev, x_dev, tol=1e-10, maxit=500)
+        x_host.copy_(x_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_cycles += it
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    def dominant(prof, fp32):
+        rows = [r for r in prof if r["kernel"] == "relax" and r["level"] == 0 and r["fp32"] == fp32]
+        return rows[0] if rows else max(prof, key=lambda r: r["ms"])
+
+    def roofline_fp64():
+        r = dominant(variants["fp64"]["prof"], False)
+        per_launch_s = r["ms"] / r["launches"] * 1e-3
+        flops = ALG_FLOPS_PER_POINT[kind] * N / 4.0             # one colour = a quarter of the grid
+        achieved = flops / per_launch_s / 1e12
+        peak = fp64_rate / 1e12
+        share = r["ms"] / sum(q["ms"] for q in variants["fp64"]["prof"])
+        byt = SWEEP_BYTES[("fp64", kind)] * N / 4.0
+        return {"bound": "alu", "kernel": "k_gs_colour<double> level 0", "achieved": round(achieved, 4),
+                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": "FP64 instruction rate measured in this run (bmg_measure_fp64_rate)",
+                "traffic": NCU_TRAFFIC.get((args.workload, "fp64", "relax")),
+                "alg_bytes_per_launch": byt, "hbm_gbs_equiv": round(byt / per_launch_s / 1e9, 1),
+                "time_share": round(share, 3), "avg_launch_us": round(per_launch_s * 1e6, 2)}
+
+    def roofline_32(prec):
+        r = dominant(variants[prec]["prof"], True)
+        per_launch_s = r["ms"] / r["launches"] * 1e-3
+        byt = SWEEP_BYTES[(prec, kind)] * N / 4.0
+        achieved = byt / per_launch_s / 1e9
+        peak = measured_peak("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "kernel": f"k_gs_colour<float,{'bf16' if prec == 'bf16' else 'float'}> level 0",
+                "achieved": round(achieved, 1), "peak": peak[0], "unit": "GB/s", "frac": round(achieved / peak[0], 4),
+                "peak_source": peak[1], "traffic": NCU_TRAFFIC.get((args.workload, prec, "relax")),
+                "avg_launch_us": round(per_launch_s * 1e6, 2)}
+
+    v64 = variants["fp64"]
+    value = world * N * args.steps / (v64["ms"] * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": v64["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generators, no datasets)",
+        "config": {"workload": args.workload, "description": spec["text"], "unknowns": N,
+                   "levels": v64["h"].num_levels, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "working set > L2 (FP64 level-0 stencil + vectors = %.0f MB)" % (N * 64 / 1e6)},
+        "roofline": roofline_fp64(),
+        "e2e": {"value": world * N * e2e_cycles / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(f.nbytes),
+                "note": "bmg_solve to 1e-10 from a zero guess per step, rhs H2D from pinned memory, x D2H"},
+        "gpu_launches": int(timed_launches),
+        "clocks": clock_s,
+        "time_to_tol": {p: {"solve_ms": round(v["tts_ms"], 3), "setup_ms": round(v["setup_ms"], 1),
+                            "cycles": v["iters"], "relres": v["relres"], "converged": v["ok"]}
+                        for p, v in variants.items()},
+        "variants": {p: {"value": world * N * args.steps / (v["ms"] * 1e-3), "ms_per_step": v["ms"] / args.steps,
+                         "roofline": roofline_32(p)}
+                     for p, v in variants.items() if p != "fp64"},
+    }
+    out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu else None
+    print(json.dumps(out))
+    for v in variants.values():
+        v["h"].close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key]), "MEASURED_PEAKS.json (measured)"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+# ----------------------------------------------------------------------------------
+# the CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------------
+
+def oracle_cycles(kind, planes, f, cycles):
+    """Oracle setup, then `cycles` V(2,1) cycles each followed by the residual
+    norm; returns (setup_s, per-cycle seconds)."""
+    from oracle import boxmg as bx
+    t0 = time.perf_counter()
+    levels = bx.setup(kind, planes)
+    setup_s = time.perf_counter() - t0
+    x = np.zeros_like(f)
+    times = []
+    for _ in range(cycles):
+        t0 = time.perf_counter()
+        bx.vcycle(levels, 0, x, f)
+        bx.norm(bx.residual(levels[0].planes, x, f))
+        times.append(time.perf_counter() - t0)
+    return setup_s, times
+
+
+def cpu_baseline(args, kind, planes, f):
+    n = planes.shape[-1] - 2
+    cycles = 3 if n >= 2047 else 20
+    setup_s, times = oracle_cycles(kind, planes, f, cycles)
+    per = statistics.median(times)
+    return {"value": n * n / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (numpy FP64, one thread) setup ({setup_s:.1f} s) + {cycles} V(2,1) cycles with "
+                      f"residual norm on the full {args.workload} problem; median cycle {per * 1e3:.0f} ms"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    spec = WORKLOADS[args.workload]
+    kind, planes, f = spec["make"]()
+    n = planes.shape[-1] - 2
+    steps = min(args.steps, 5 if n >= 2047 else 50)
+    setup_s, times = oracle_cycles(kind, planes, f, steps + min(args.warmup, 1))
+    times = times[min(args.warmup, 1):]
+    tot = sum(times)
+    value = n * n * len(times) / tot
+    sample = (f"{len(times)} timed V(2,1) cycles (+ {min(args.warmup, 1)} warm-up) of the oracle on the full "
+              f"{args.workload} problem (steps capped from {args.steps} to keep the CPU run to minutes); "
+              f"setup {setup_s:.1f} s")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times), "warmup": args.warmup,
+           "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded generators, no datasets)", "impl": "reference",
+           "config": {"workload": args.workload, "description": spec["text"], "unknowns": n * n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="fe2047-binary1e4", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, local_rank, world = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, local_rank, world)
+
+
+if __name__ == "__main__":
+    main()

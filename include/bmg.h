@@ -1,0 +1,212 @@
+/*
+ * bmg.h -- C ABI of a GB300 (sm_103a) black-box multigrid (BoxMG) solver for
+ * 2D 5- and 9-point variable-coefficient stencils with zero Dirichlet
+ * boundaries (Nytko, Reisner, Moulton, Olson, West, "Teaching an old dog new
+ * tricks", arXiv 2502.05279: the problem A x = b of Sec. 2 and the V-cycle of
+ * Fig. 1; the method itself is Dendy's black-box multigrid, which Sec. 2 cites).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * Grid.  A level with n = 2^m - 1 interior points per side (n >= 3) is stored
+ * as an (n+2) x (n+2) row-major array of doubles indexed [j][i] (i = x is the
+ * fastest index), interior i, j in 1..n; the ghost ring i, j in {0, n+1}
+ * carries the Dirichlet value 0.  Coarse point (ic, jc) lies on fine point
+ * (2ic, 2jc); n_c = (n - 1) / 2.
+ *
+ * Stencil.  Five planes O, W, S, SW, NW, each (n+2)^2, back to back: the
+ * matrix entries a(p,p), a(p,p-x), a(p,p-y), a(p,p-x-y), a(p,p-x+y).  A is
+ * symmetric, so E(p) = W(p+x), N(p) = S(p+y), NE(p) = SW(p+x+y),
+ * SE(p) = NW(p+x-y).  A 5-point stencil (kind 5) passes three planes O, W, S.
+ * Couplings from an interior point to a ghost point are not entries of A; the
+ * library ignores (zeroes) them and the ghost ring of every plane.
+ *
+ * Interpolation weights.  Eight planes of (n_c+2)^2 doubles in the order
+ * LSW, LSE, LNW, LNE, LL, LR, LB, LA (the labels of Fig. 2), indexed by the
+ * coarse cell (ic, jc) whose north-east corner is coarse point (ic, jc):
+ *   fine (2ic-1, 2jc-1): LSW, LSE, LNW, LNE = weights toward coarse
+ *                        (ic-1,jc-1), (ic,jc-1), (ic-1,jc), (ic,jc);
+ *   fine (2ic-1, 2jc):   LL, LR = toward (ic-1,jc), (ic,jc);
+ *   fine (2ic, 2jc-1):   LB, LA = toward (ic,jc-1), (ic,jc).
+ *
+ * Arithmetic.  The FP64 path rounds every multiply, add and subtract
+ * separately (no fused multiply-add) and sums each row of A in the order
+ * O, W, E, S, N, SW, NE, NW, SE, so its iterates are reproducible bit for bit.
+ *
+ * Pointers.  "device" = memory the calling process allocated on the current
+ * CUDA device; "host" = ordinary host memory.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream); all device work is enqueued on it and a call
+ * returns once its results are ready, unless stated otherwise.  No call takes
+ * ownership of a caller pointer.
+ *
+ * Errors.  Every int-returning call returns BMG_OK (0) or a negative code;
+ * bmg_strerror() names it and bmg_last_error() gives the detail of the most
+ * recent failure on the calling thread.  No exception crosses the ABI.  A
+ * hierarchy is not thread-safe.
+ */
+#ifndef BMG_H
+#define BMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BMG_OK = 0,
+  BMG_EINVAL = -1,      /* bad size, kind, option or pointer */
+  BMG_ENOMEM = -2,      /* device allocation failed */
+  BMG_ECUDA = -3,       /* a CUDA runtime call failed (detail in bmg_last_error) */
+  BMG_ESINGULAR = -4,   /* non-positive pivot in the coarsest Cholesky, a non-positive
+                           diagonal, or a zero / non-finite interpolation denominator */
+  BMG_ENAN = -5,        /* the residual norm became NaN or Inf */
+  BMG_ENOTCONV = -6,    /* maxit cycles ran without reaching tol; x holds the last iterate */
+  BMG_ETIMEOUT = -7     /* a bounded device-side wait gave up */
+};
+
+enum { BMG_FP64 = 0, BMG_FP32_IR = 1, BMG_BF16_IR = 2 };
+enum { BMG_INTERP_DENDY = 0, BMG_INTERP_LEARNED = 1 };
+
+typedef struct bmg_hierarchy bmg_hierarchy;   /* opaque, library-owned */
+
+typedef struct {
+  int kind;             /* 5 or 9 */
+  const double* coef;   /* device; kind 9: 5 planes O,W,S,SW,NW; kind 5: 3 planes O,W,S;
+                           each (n+2)^2 doubles (see Stencil above) */
+} bmg_stencil;
+
+typedef struct {
+  int precision;        /* BMG_FP64 (default), BMG_FP32_IR or BMG_BF16_IR */
+  int interp;           /* BMG_INTERP_DENDY (default) */
+  int coarsest;         /* coarsest level size, 2^m - 1 >= 3 (0 = 3) */
+  int nu1, nu2;         /* pre- and post-smoothing sweeps (0,0 = 2,1) */
+  int inner_cycles;     /* FP32 V-cycles per refinement step (0 = 1) */
+  int bf16_levels;      /* levels with BF16 stencils under BMG_BF16_IR (0 = 2) */
+  int use_graph;        /* 1 = replay one captured CUDA graph per cycle (default), 0 = plain launches */
+  void* stream;         /* cudaStream_t for setup and every later call on the hierarchy */
+} bmg_opts;
+
+/* ---- whole solver ------------------------------------------------------ */
+
+/* Build the hierarchy (Sec. 2: "construction of coarse programs through local
+ * stencil operations"): Dendy interpolation and the Galerkin operator
+ * A_c = P^T A P level by level down to `coarsest`, then the Cholesky factor of
+ * the coarsest operator (Fig. 1 "Cholesky").  The stencil is copied; the caller
+ * may free it on return.  nx == ny == n = 2^m - 1 >= 3.  opts may be NULL.
+ * Returns BMG_EINVAL (sizes, kind, options), BMG_ENOMEM, BMG_ECUDA or
+ * BMG_ESINGULAR; *out is NULL on failure. */
+int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* opts, bmg_hierarchy** out);
+
+/* Solve A x = rhs by V(nu1,nu2) cycles (Fig. 1) until ||r_k||/||r_0|| <= tol
+ * (r_0 = rhs - A x_in, Euclidean norm over the interior) or `maxit` cycles.
+ * rhs: device, (n+2)^2, read only.  x: device, (n+2)^2, in: initial guess,
+ * out: solution (its ghost ring is not written).  iters, relres: host, may be
+ * NULL.  Under BMG_FP32_IR / BMG_BF16_IR one "cycle" is one FP64 refinement
+ * step around `inner_cycles` FP32 V-cycles.  Returns BMG_OK, BMG_ENOTCONV,
+ * BMG_ENAN, BMG_EINVAL or BMG_ECUDA. */
+int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int maxit,
+              int* iters, double* relres);
+
+/* Residual norms [||r_0||, ||r_1||, ...] of the last solve, copied to the host
+ * array out (capacity cap).  Returns the number of entries available (which may
+ * exceed cap) or a negative code. */
+int bmg_history(const bmg_hierarchy* h, double* out, int cap);
+
+/* Measurement: enqueue `cycles` solve iterations (one V-cycle, or one
+ * refinement step, plus the residual norm each) with no convergence test,
+ * bracketed by CUDA events recorded on the hierarchy's own stream, and return
+ * their elapsed device time in *ms.  The iterations replay the same CUDA graph
+ * bmg_solve uses (when use_graph is set).  x: in/out iterate (device).  Waits
+ * for completion. */
+int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, double* ms);
+
+/* Per-level, per-kernel device time of `cycles` iterations launched one step
+ * at a time without the graph, each step bracketed by CUDA events on the
+ * hierarchy's stream (the Fig. 10 breakdown).  Fills up to `cap` rows of the
+ * host array `rows` and returns the number of rows. */
+enum { BMG_K_RELAX = 0, BMG_K_RESID_RESTRICT = 1, BMG_K_INTERP = 2, BMG_K_COARSE = 3, BMG_K_NORM = 4,
+       BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7 };
+typedef struct {
+  int level;            /* 0 = finest */
+  int kernel;           /* BMG_K_* */
+  int fp32;             /* 1 = a kernel of the FP32 inner cycle */
+  int launches;         /* kernel launches summed into this row */
+  double ms;            /* total device time */
+} bmg_prof_row;
+int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_prof_row* rows, int cap);
+
+/* Number of levels, and the size n of level l (0 = finest). */
+int bmg_num_levels(const bmg_hierarchy* h);
+int bmg_level_size(const bmg_hierarchy* h, int level);
+
+/* Copy level `level`'s stencil (5 planes O,W,S,SW,NW, FP64, ghost couplings
+ * zero) or its interpolation weights (8 planes, FP64; not for the coarsest
+ * level) into device memory `out` of the matching size. */
+int bmg_get_stencil(const bmg_hierarchy* h, int level, double* out);
+int bmg_get_interp(const bmg_hierarchy* h, int level, double* out);
+
+/* Kernel launches issued on the hierarchy's stream since setup (a counter kept
+ * by the host side of the library). */
+long long bmg_launch_count(const bmg_hierarchy* h);
+
+/* Release everything the hierarchy owns.  NULL is a no-op. */
+void bmg_free(bmg_hierarchy* h);
+
+const char* bmg_strerror(int code);
+const char* bmg_last_error(void);
+
+/* ---- single steps, for testing and composition -------------------------
+ * Stateless: every pointer is caller-owned device memory in the layouts above;
+ * `kind` is 5 or 9 and `coef` holds 5 planes either way (kind 5 ignores SW, NW).
+ * The caller zeroes ghost couplings (bmg_setup does it for the hierarchy). */
+
+/* Dendy operator-dependent interpolation weights of one level (setup of
+ * Fig. 1's "Interpolate" and of the Fig. 2 restriction).  coef: 5 planes
+ * (n+2)^2; ci: out, 8 planes (n_c+2)^2 (entries outside the defined ranges
+ * are set to 0). */
+int bmg_dendy_interp(int n, const double* coef, double* ci, void* stream);
+
+/* Galerkin coarse operator A_c = P^T A P as a coarse 9-point stencil.
+ * coef: 5 planes (n+2)^2; ci: 8 planes (n_c+2)^2; coarse: out, 5 planes
+ * (n_c+2)^2 with zero ghost ring and ghost couplings. */
+int bmg_rap(int n, const double* coef, const double* ci, double* coarse, void* stream);
+
+/* `sweeps` Gauss-Seidel sweeps in place on x (Fig. 1 "Gauss Seidel"):
+ * red-black for kind 5, four colours (i,j parities (odd,odd), (even,odd),
+ * (odd,even), (even,even)) for kind 9; x_p = (f_p - sum_{q!=p} a_pq x_q) * (1/a_pp). */
+int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, int sweeps, void* stream);
+
+/* f_c = P^T (f - A x) with the Fig. 2 restriction (Fig. 1 "Residual",
+ * "Restrict"); fc: out, (n_c+2)^2, interior written, ghost ring zeroed. */
+int bmg_resid_restrict(int n, int kind, const double* coef, const double* ci, const double* x,
+                       const double* f, double* fc, void* stream);
+
+/* x += P e_c (Fig. 1 "Interpolate"); ec: (n_c+2)^2 with zero ghost ring. */
+int bmg_interp_correct(int n, const double* ci, const double* ec, double* x, void* stream);
+
+/* r = f - A x over the interior (ghost ring of r zeroed) and, if norm != NULL,
+ * its Euclidean norm to host *norm. */
+int bmg_residual(int n, int kind, const double* coef, const double* x, const double* f,
+                 double* r, double* norm, void* stream);
+
+/* Lower-triangular Cholesky factor L (row-major m x m, m = n^2, lexicographic
+ * unknowns j outer, i inner) of a level's operator (Fig. 1 "Cholesky");
+ * BMG_ESINGULAR on a non-positive pivot.  n <= 15. */
+int bmg_coarse_factor(int n, const double* coef, double* L, void* stream);
+
+/* x = (L L^T)^{-1} f on one level, FP64 forward and back substitution. */
+int bmg_coarse_solve(int n, const double* L, const double* f, double* x, void* stream);
+
+/* One FP32 inner V(nu1,nu2) cycle of a BMG_FP32_IR / BMG_BF16_IR hierarchy on a
+ * caller-supplied FP32 right-hand side: e = V32(r32) from a zero guess.
+ * r32, e32: device floats, (n+2)^2 (ghost ring of e32 not written). */
+int bmg_inner_cycle(bmg_hierarchy* h, const float* r32, float* e32);
+
+/* Measured FP64 instruction throughput of this GPU (giga-instructions per
+ * second, dependent multiply-add chains on every SM), for roofline reports. */
+int bmg_measure_fp64_rate(double* ginstr_per_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMG_H */

@@ -1,0 +1,11 @@
+"""GB300-native black-box multigrid (BoxMG) for 2D 5-/9-point stencils.
+
+The solver lives in the CUDA library libbmg.so (C ABI declared in
+include/bmg.h); this package only marshals torch tensors into that ABI.
+There is no CPU fallback: importing the binding fails when the library is
+missing or cannot load.
+"""
+from ._lib import (  # noqa: F401
+    BMG_BF16_IR, BMG_FP32_IR, BMG_FP64, BmgError, Hierarchy, coarse_factor, coarse_solve, dendy_interp,
+    interp_correct, lib, library_path, measure_fp64_rate, rap, relax, resid_restrict, residual,
+)

@@ -1,0 +1,256 @@
+"""ctypes binding of libbmg.so.  Argument marshalling only: every step of the
+solver runs in the library's CUDA kernels.
+
+Tensors passed in must be contiguous CUDA tensors of the documented dtype and
+shape; work is enqueued on torch's current CUDA stream, with which the library
+orders itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libbmg.so")
+
+BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ESINGULAR, BMG_ENAN, BMG_ENOTCONV, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+BMG_FP64, BMG_FP32_IR, BMG_BF16_IR = 0, 1, 2
+_PREC = {"fp64": BMG_FP64, "fp32": BMG_FP32_IR, "bf16": BMG_BF16_IR}
+
+
+class BmgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+if not os.path.exists(library_path):
+    raise ImportError(f"{library_path} is missing: build it with paper_2502_05279_gb300.build.build() "
+                      "(there is no CPU fallback)")
+lib = ctypes.CDLL(library_path)
+
+
+class Stencil(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("coef", ctypes.c_void_p)]
+
+
+class ProfRow(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("kernel", ctypes.c_int), ("fp32", ctypes.c_int),
+                ("launches", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
+                "ir_update", "ir_residual")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("coarsest", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_sig = {
+    "bmg_setup": (I, [ctypes.POINTER(Stencil), I, I, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
+    "bmg_solve": (I, [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+    "bmg_history": (I, [P, ctypes.POINTER(D), I]),
+    "bmg_num_levels": (I, [P]),
+    "bmg_level_size": (I, [P, I]),
+    "bmg_get_stencil": (I, [P, I, P]),
+    "bmg_get_interp": (I, [P, I, P]),
+    "bmg_launch_count": (L, [P]),
+    "bmg_free": (None, [P]),
+    "bmg_strerror": (ctypes.c_char_p, [I]),
+    "bmg_last_error": (ctypes.c_char_p, []),
+    "bmg_dendy_interp": (I, [I, P, P, P]),
+    "bmg_rap": (I, [I, P, P, P, P]),
+    "bmg_relax": (I, [I, I, P, P, P, I, P]),
+    "bmg_resid_restrict": (I, [I, I, P, P, P, P, P, P]),
+    "bmg_interp_correct": (I, [I, P, P, P, P]),
+    "bmg_residual": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
+    "bmg_coarse_factor": (I, [I, P, P, P]),
+    "bmg_coarse_solve": (I, [I, P, P, P, P]),
+    "bmg_inner_cycle": (I, [P, P, P]),
+    "bmg_measure_fp64_rate": (I, [ctypes.POINTER(D), P]),
+    "bmg_time_cycles": (I, [P, P, P, I, ctypes.POINTER(D)]),
+    "bmg_profile": (I, [P, P, P, I, P, I]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def _check(rc: int, allow=()):
+    if rc != BMG_OK and rc not in allow:
+        raise BmgError(rc, f"{lib.bmg_strerror(rc).decode()}: {lib.bmg_last_error().decode()}")
+    return rc
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor, dtype=torch.float64, name="tensor"):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _n_of(t: torch.Tensor) -> int:
+    return t.shape[-1] - 2
+
+
+class Hierarchy:
+    """A BoxMG hierarchy built on the GPU (bmg_setup) and its solver (bmg_solve)."""
+
+    def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
+                 nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
+                 use_graph: bool = True):
+        n = _n_of(coef)
+        self.n, self.kind, self.precision = n, kind, precision
+        st = Stencil(kind, _ptr(coef, name="coef"))
+        o = Opts(_PREC[precision], 0, coarsest, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), _stream())
+        h = ctypes.c_void_p()
+        _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, rhs: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-10, maxit: int = 100):
+        """Returns (x, iterations, relative residual, converged)."""
+        if x is None:
+            x = torch.zeros_like(rhs)
+        it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = _check(lib.bmg_solve(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), tol, maxit,
+                                  ctypes.byref(it), ctypes.byref(rr)), allow=(BMG_ENOTCONV,))
+        return x, it.value, rr.value, rc == BMG_OK
+
+    def time_cycles(self, rhs: torch.Tensor, x: torch.Tensor, cycles: int) -> float:
+        """Device milliseconds of `cycles` solve iterations (no convergence test)."""
+        ms = ctypes.c_double(0.0)
+        _check(lib.bmg_time_cycles(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), cycles, ctypes.byref(ms)))
+        return ms.value
+
+    def profile(self, rhs: torch.Tensor, x: torch.Tensor, cycles: int):
+        """Per (level, kernel, fp32) device time of `cycles` iterations: a list of
+        dicts with keys level, kernel, fp32, launches, ms."""
+        rows = (ProfRow * 256)()
+        cnt = _check_size(lib.bmg_profile(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), cycles, rows, 256))
+        return [dict(level=r.level, kernel=KERNEL_NAMES[r.kernel], fp32=bool(r.fp32), launches=r.launches, ms=r.ms)
+                for r in rows[:cnt]]
+
+    def history(self):
+        cnt = lib.bmg_history(self._h, None, 0)
+        buf = (ctypes.c_double * max(cnt, 1))()
+        lib.bmg_history(self._h, buf, cnt)
+        return list(buf[:cnt])
+
+    @property
+    def num_levels(self) -> int:
+        return lib.bmg_num_levels(self._h)
+
+    def level_size(self, level: int) -> int:
+        return _check_size(lib.bmg_level_size(self._h, level))
+
+    def stencil(self, level: int) -> torch.Tensor:
+        m = self.level_size(level) + 2
+        out = torch.empty((5, m, m), dtype=torch.float64, device="cuda")
+        _check(lib.bmg_get_stencil(self._h, level, _ptr(out)))
+        return out
+
+    def interp(self, level: int) -> torch.Tensor:
+        m = self.level_size(level + 1) + 2
+        out = torch.empty((8, m, m), dtype=torch.float64, device="cuda")
+        _check(lib.bmg_get_interp(self._h, level, _ptr(out)))
+        return out
+
+    def inner_cycle(self, r32: torch.Tensor) -> torch.Tensor:
+        e = torch.empty_like(r32)
+        _check(lib.bmg_inner_cycle(self._h, _ptr(r32, torch.float32, "r32"), _ptr(e, torch.float32, "e32")))
+        return e
+
+    @property
+    def launch_count(self) -> int:
+        return lib.bmg_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bmg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_size(v: int) -> int:
+    if v < 0:
+        _check(v)
+    return v
+
+
+def dendy_interp(coef: torch.Tensor) -> torch.Tensor:
+    n = _n_of(coef)
+    nc = (n - 1) // 2
+    ci = torch.empty((8, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
+    _check(lib.bmg_dendy_interp(n, _ptr(coef), _ptr(ci), _stream()))
+    return ci
+
+
+def rap(coef: torch.Tensor, ci: torch.Tensor) -> torch.Tensor:
+    n = _n_of(coef)
+    nc = (n - 1) // 2
+    out = torch.empty((5, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
+    _check(lib.bmg_rap(n, _ptr(coef), _ptr(ci), _ptr(out), _stream()))
+    return out
+
+
+def relax(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
+    _check(lib.bmg_relax(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), sweeps, _stream()))
+    return x
+
+
+def resid_restrict(kind: int, coef, ci, x, f) -> torch.Tensor:
+    n = _n_of(coef)
+    nc = (n - 1) // 2
+    fc = torch.empty((nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
+    _check(lib.bmg_resid_restrict(n, kind, _ptr(coef), _ptr(ci), _ptr(x), _ptr(f), _ptr(fc), _stream()))
+    return fc
+
+
+def interp_correct(ci, ec, x) -> torch.Tensor:
+    _check(lib.bmg_interp_correct(_n_of(x), _ptr(ci), _ptr(ec), _ptr(x), _stream()))
+    return x
+
+
+def residual(kind: int, coef, x, f, want_r: bool = True):
+    """Returns (r or None, ||r||)."""
+    n = _n_of(coef)
+    r = torch.empty_like(f) if want_r else None
+    nrm = ctypes.c_double(0.0)
+    _check(lib.bmg_residual(n, kind, _ptr(coef), _ptr(x), _ptr(f), _ptr(r) if want_r else None,
+                            ctypes.byref(nrm), _stream()))
+    return r, nrm.value
+
+
+def coarse_factor(coef: torch.Tensor) -> torch.Tensor:
+    n = _n_of(coef)
+    L = torch.empty((n * n, n * n), dtype=torch.float64, device=coef.device)
+    _check(lib.bmg_coarse_factor(n, _ptr(coef), _ptr(L), _stream()))
+    return L
+
+
+def coarse_solve(L: torch.Tensor, f: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    _check(lib.bmg_coarse_solve(_n_of(f), _ptr(L), _ptr(f), _ptr(x), _stream()))
+    return x
+
+
+def measure_fp64_rate() -> float:
+    v = ctypes.c_double(0.0)
+    _check(lib.bmg_measure_fp64_rate(ctypes.byref(v), _stream()))
+    return v.value

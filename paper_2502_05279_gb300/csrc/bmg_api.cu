@@ -1,0 +1,729 @@
+// C ABI of the BoxMG solver: the hierarchy object, its level schedule (the
+// V-cycle of Fig. 1 enqueued level by level), CUDA-graph replay of one cycle,
+// device-side convergence control, and the stateless single-step entry points.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bmg {
+
+static thread_local char g_err[512] = "";
+static thread_local long long* g_counter = nullptr;
+static long long g_free_launches = 0;
+
+void count_launch() {
+  if (g_counter)
+    ++*g_counter;
+  else
+    ++g_free_launches;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return BMG_OK;
+  if (e == cudaErrorMemoryAllocation) return set_error(BMG_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(BMG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void zero_ring(int n, double* r, cudaStream_t s);   // k_cycle.cu
+
+}  // namespace bmg
+
+using namespace bmg;
+
+#define CK(call)                                     \
+  do {                                               \
+    int _rc = cuda_check((call), #call);             \
+    if (_rc != BMG_OK) return _rc;                   \
+  } while (0)
+
+namespace {
+
+struct Level {
+  int n = 0, kind = 9;
+  double* st = nullptr;   // O, W, S, SW, NW, D
+  double* ci = nullptr;   // 8 interpolation planes toward level + 1
+  double* x = nullptr;    // levels >= 1
+  double* f = nullptr;
+  bool bf16 = false;      // FP32 cycle reads BF16 off-diagonals on this level
+  float* st32 = nullptr;  // O, W, S, SW, NW, D in FP32
+  __nv_bfloat16* off16 = nullptr;
+  float* od32 = nullptr;  // O32, D32 of a BF16 level
+  float* ci32 = nullptr;
+  float* x32 = nullptr;
+  float* f32 = nullptr;
+};
+
+StencilView<double, double> view64(const Level& L) {
+  size_t ps = plane_size(L.n);
+  return {L.st, L.st + ps, L.st + 2 * ps, L.st + 3 * ps, L.st + 4 * ps, L.st + 5 * ps, L.n, L.n + 2};
+}
+StencilView<float, float> view32(const Level& L) {
+  size_t ps = plane_size(L.n);
+  return {L.st32, L.st32 + ps, L.st32 + 2 * ps, L.st32 + 3 * ps, L.st32 + 4 * ps, L.st32 + 5 * ps, L.n, L.n + 2};
+}
+StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
+  size_t ps = plane_size(L.n);
+  return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2};
+}
+
+}  // namespace
+
+struct bmg_hierarchy {
+  int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3;
+  std::vector<Level> lv;
+  cudaStream_t user = nullptr;   // caller stream (ordering only)
+  cudaStream_t ws = nullptr;     // internal non-blocking work stream
+  cudaEvent_t ev = nullptr;
+  double* Lfac = nullptr;        // coarsest Cholesky factor (m x m)
+  double* work = nullptr;        // m x m factor workspace, then m doubles for substitutions
+  int m = 0;
+  double* partials = nullptr;
+  int* err = nullptr;            // device error word of setup kernels
+  Ctl* ctl = nullptr;            // device control block (hist sized for maxit_cap + 1)
+  Ctl* ctl_host = nullptr;       // pinned mirror of the header
+  int maxit_cap = 0;
+  float* r32_user_dummy = nullptr;
+  // graph of one cycle, keyed by the caller buffers it was captured with
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_rhs = nullptr;
+  double* g_x = nullptr;
+  long long g_kernels = 0;
+  long long launches = 0;
+  struct Mark {
+    int level, kernel, fp32;
+    long long launches;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark>* prof = nullptr;   // non-null while bmg_profile records
+  int last_hist = 0;
+  std::vector<double> hist;
+};
+
+namespace {
+
+struct CounterScope {
+  long long* prev;
+  explicit CounterScope(long long* c) : prev(g_counter) { g_counter = c; }
+  ~CounterScope() { g_counter = prev; }
+};
+
+// Run one step's launches, bracketed by CUDA events when profiling.
+template <class F>
+void step(bmg_hierarchy* h, int level, int kernel, int fp32, F&& f) {
+  if (!h->prof) {
+    f();
+    return;
+  }
+  bmg_hierarchy::Mark m{level, kernel, fp32, 0, nullptr, nullptr};
+  cudaEventCreate(&m.a);
+  cudaEventCreate(&m.b);
+  cudaEventRecord(m.a, h->ws);
+  long long before = h->launches;
+  f();
+  m.launches = h->launches - before;
+  cudaEventRecord(m.b, h->ws);
+  h->prof->push_back(m);
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return BMG_OK;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return BMG_OK;
+}
+
+void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* done) {
+  Level& L = h->lv[l];
+  cudaStream_t s = h->ws;
+  if (l == h->nlev - 1) {
+    step(h, l, BMG_K_COARSE, 0, [&] { launch_coarse_solve<double>(L.n, h->Lfac, f, x, h->work, done, s); });
+    return;
+  }
+  auto v = view64(L);
+  Level& C = h->lv[l + 1];
+  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu1, done, s); });
+  step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, x, f, C.f, C.x, done, s); });
+  vcycle64(h, l + 1, C.x, C.f, done);
+  step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s); });
+  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu2, done, s); });
+}
+
+template <typename S>
+void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, const int* done) {
+  Level& L = h->lv[l];
+  step(h, l, BMG_K_RELAX, 1, [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws); });
+}
+
+template <typename S>
+void restrict32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, const int* done) {
+  Level& L = h->lv[l];
+  Level& C = h->lv[l + 1];
+  step(h, l, BMG_K_RESID_RESTRICT, 1,
+       [&] { launch_resid_restrict(v, L.kind, (const float*)L.ci32, (const float*)L.x32, (const float*)L.f32,
+                                   C.f32, C.x32, done, h->ws); });
+}
+
+void vcycle32(bmg_hierarchy* h, int l, const int* done) {
+  Level& L = h->lv[l];
+  cudaStream_t s = h->ws;
+  if (l == h->nlev - 1) {
+    step(h, l, BMG_K_COARSE, 1,
+         [&] { launch_coarse_solve<float>(L.n, h->Lfac, (const float*)L.f32, L.x32, h->work, done, s); });
+    return;
+  }
+  Level& C = h->lv[l + 1];
+  if (L.bf16) {
+    relax32(h, viewbf(L), l, h->nu1, done);
+    restrict32(h, viewbf(L), l, done);
+  } else {
+    relax32(h, view32(L), l, h->nu1, done);
+    restrict32(h, view32(L), l, done);
+  }
+  vcycle32(h, l + 1, done);
+  step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_correct<float>(L.n, L.ci32, C.x32, L.x32, done, s); });
+  if (L.bf16)
+    relax32(h, viewbf(L), l, h->nu2, done);
+  else
+    relax32(h, view32(L), l, h->nu2, done);
+}
+
+// One iteration of the solve loop: a V-cycle (or a refinement step) followed by
+// the residual norm and the convergence test, all on the device.
+void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
+  const int* done = &h->ctl->done;
+  Level& L0 = h->lv[0];
+  int np = 0;
+  if (h->precision == BMG_FP64) {
+    vcycle64(h, 0, x, rhs, done);
+    step(h, 0, BMG_K_NORM, 0, [&] {
+      np = launch_residual(view64(L0), L0.kind, (const double*)x, rhs, (double*)nullptr, h->partials, done, h->ws);
+    });
+  } else {
+    for (int c = 0; c < h->inner; ++c) vcycle32(h, 0, done);
+    step(h, 0, BMG_K_IR_UPDATE, 0, [&] { launch_ir_update(L0.n, x, L0.x32, h->ctl, h->ws); });
+    step(h, 0, BMG_K_IR_RESIDUAL, 0, [&] {
+      np = launch_ir_residual(view64(L0), L0.kind, x, rhs, L0.f32, L0.x32, h->partials, h->ctl, h->ws);
+    });
+  }
+  step(h, 0, BMG_K_FINALIZE, 0, [&] { launch_norm_finalize(h->partials, np, h->ctl, 1, nullptr, h->ws); });
+}
+
+int enqueue_initial(bmg_hierarchy* h, const double* rhs, double* x) {
+  Level& L0 = h->lv[0];
+  if (h->precision == BMG_FP64) {
+    int np = launch_residual(view64(L0), L0.kind, x, rhs, (double*)nullptr, h->partials, (const int*)nullptr, h->ws);
+    launch_norm_finalize(h->partials, np, h->ctl, 0, nullptr, h->ws);
+  } else {
+    int np = launch_ir_residual(view64(L0), L0.kind, x, rhs, L0.f32, L0.x32, h->partials, h->ctl, h->ws);
+    launch_norm_finalize(h->partials, np, h->ctl, 0, nullptr, h->ws);
+  }
+  return BMG_OK;
+}
+
+int capture_graph(bmg_hierarchy* h, const double* rhs, double* x) {
+  if (h->gexec && h->g_rhs == rhs && h->g_x == x) return BMG_OK;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->ws, cudaStreamCaptureModeThreadLocal));
+  long long before = h->launches;
+  enqueue_iteration(h, rhs, x);
+  h->g_kernels = h->launches - before;
+  h->launches = before;
+  CK(cudaStreamEndCapture(h->ws, &g));
+  cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  h->g_rhs = rhs;
+  h->g_x = x;
+  return BMG_OK;
+}
+
+int order_after_user(bmg_hierarchy* h) {
+  CK(cudaEventRecord(h->ev, h->user));
+  CK(cudaStreamWaitEvent(h->ws, h->ev, 0));
+  return BMG_OK;
+}
+
+int ensure_ctl(bmg_hierarchy* h, int maxit) {
+  if (maxit <= h->maxit_cap && h->ctl) return BMG_OK;
+  if (h->ctl) cudaFree(h->ctl);
+  h->ctl = nullptr;
+  int cap = maxit < 64 ? 64 : maxit;
+  CK(cudaMalloc((void**)&h->ctl, sizeof(Ctl) + sizeof(double) * (size_t)(cap + 1)));
+  h->maxit_cap = cap;
+  if (h->gexec) {   // the graph holds the old control block address
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return BMG_OK;
+}
+
+void free_level(Level& L) {
+  cudaFree(L.st);
+  cudaFree(L.ci);
+  cudaFree(L.x);
+  cudaFree(L.f);
+  cudaFree(L.st32);
+  cudaFree(L.off16);
+  cudaFree(L.od32);
+  cudaFree(L.ci32);
+  cudaFree(L.x32);
+  cudaFree(L.f32);
+  L = Level{};
+}
+
+bool is_level_size(int n) { return n >= 3 && ((n + 1) & n) == 0; }
+
+int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o) {
+  cudaStream_t s = h->ws;
+  // level sizes
+  std::vector<int> sizes{n};
+  while (sizes.back() > h->coarsest) sizes.push_back((sizes.back() - 1) / 2);
+  h->nlev = (int)sizes.size();
+  h->lv.resize(h->nlev);
+  int rc;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->lv[l];
+    L.n = sizes[l];
+    L.kind = l == 0 ? A->kind : 9;
+    size_t ps = plane_size(L.n);
+    if ((rc = dalloc(&L.st, 6 * ps))) return rc;
+    if (l + 1 < h->nlev)
+      if ((rc = dalloc(&L.ci, 8 * plane_size(sizes[l + 1])))) return rc;
+    if (l > 0) {
+      if ((rc = dalloc(&L.x, ps))) return rc;
+      if ((rc = dalloc(&L.f, ps))) return rc;
+      CK(cudaMemsetAsync(L.x, 0, ps * sizeof(double), s));
+      CK(cudaMemsetAsync(L.f, 0, ps * sizeof(double), s));
+    }
+  }
+  h->m = h->coarsest * h->coarsest;
+  if ((rc = dalloc(&h->Lfac, (size_t)h->m * h->m))) return rc;
+  if ((rc = dalloc(&h->work, (size_t)h->m * h->m + h->m))) return rc;
+  if ((rc = dalloc(&h->partials, (size_t)norm_partials_max()))) return rc;
+  if ((rc = dalloc(&h->err, 1))) return rc;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+
+  launch_prepare(n, A->kind, A->coef, h->lv[0].st, h->err, s);
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    Level& L = h->lv[l];
+    Level& C = h->lv[l + 1];
+    launch_dendy(L.n, L.st, L.ci, h->err, s);
+    launch_rap(L.n, L.st, L.ci, C.st, s);
+    launch_dinv(C.n, C.st, h->err, s);
+  }
+  Level& Lc = h->lv[h->nlev - 1];
+  launch_factor(Lc.n, Lc.st, h->Lfac, h->work, h->err, s);
+  CK(cudaGetLastError());
+
+  if (h->precision != BMG_FP64) {
+    int nbf = h->precision == BMG_BF16_IR ? (o && o->bf16_levels > 0 ? o->bf16_levels : 2) : 0;
+    for (int l = 0; l < h->nlev; ++l) {
+      Level& L = h->lv[l];
+      size_t ps = plane_size(L.n);
+      L.bf16 = l < nbf && l + 1 < h->nlev;
+      if (L.bf16) {
+        if ((rc = dalloc(&L.off16, 4 * ps))) return rc;
+        if ((rc = dalloc(&L.od32, 2 * ps))) return rc;
+        launch_lower_bf16(L.n, L.st, L.off16, L.od32, s);
+      } else {
+        if ((rc = dalloc(&L.st32, 6 * ps))) return rc;
+      }
+      if (l + 1 < h->nlev && (rc = dalloc(&L.ci32, 8 * plane_size(h->lv[l + 1].n)))) return rc;
+      launch_lower32(L.n, L.bf16 ? nullptr : L.st, L.bf16 ? nullptr : L.st32, L.ci, L.ci32, s);
+      if ((rc = dalloc(&L.x32, ps))) return rc;
+      if ((rc = dalloc(&L.f32, ps))) return rc;
+      CK(cudaMemsetAsync(L.x32, 0, ps * sizeof(float), s));
+      CK(cudaMemsetAsync(L.f32, 0, ps * sizeof(float), s));
+    }
+  }
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (herr) return set_error(BMG_ESINGULAR, "setup: non-positive %s",
+                             herr == 1 ? "diagonal" : herr == 2 ? "interpolation denominator" : "Cholesky pivot");
+  return BMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bmg_strerror(int code) {
+  switch (code) {
+    case BMG_OK: return "ok";
+    case BMG_EINVAL: return "invalid argument";
+    case BMG_ENOMEM: return "out of device memory";
+    case BMG_ECUDA: return "CUDA error";
+    case BMG_ESINGULAR: return "singular or indefinite operator";
+    case BMG_ENAN: return "residual is NaN or Inf";
+    case BMG_ENOTCONV: return "not converged within maxit";
+    case BMG_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* bmg_last_error(void) { return g_err; }
+
+int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hierarchy** out) {
+  if (!out) return set_error(BMG_EINVAL, "bmg_setup: out is NULL");
+  *out = nullptr;
+  if (!A || !A->coef) return set_error(BMG_EINVAL, "bmg_setup: stencil is NULL");
+  if (A->kind != 5 && A->kind != 9) return set_error(BMG_EINVAL, "bmg_setup: kind %d is not 5 or 9", A->kind);
+  if (nx != ny) return set_error(BMG_EINVAL, "bmg_setup: nx %d != ny %d", nx, ny);
+  if (!is_level_size(nx)) return set_error(BMG_EINVAL, "bmg_setup: n = %d is not 2^m - 1 >= 3", nx);
+  bmg_hierarchy* h = new bmg_hierarchy();
+  h->n = nx;
+  if (o) {
+    h->precision = o->precision;
+    h->coarsest = o->coarsest ? o->coarsest : 3;
+    if (o->nu1 || o->nu2) {
+      h->nu1 = o->nu1;
+      h->nu2 = o->nu2;
+    }
+    h->inner = o->inner_cycles > 0 ? o->inner_cycles : 1;
+    h->use_graph = o->use_graph;
+    h->user = (cudaStream_t)o->stream;
+  }
+  if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
+      h->nu1 < 0 || h->nu2 < 0 || (o && o->interp != BMG_INTERP_DENDY)) {
+    delete h;
+    return set_error(BMG_EINVAL, "bmg_setup: bad options");
+  }
+  if (h->coarsest > nx) h->coarsest = nx;
+  CounterScope cs(&h->launches);
+  int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
+  if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
+  if (!rc) rc = order_after_user(h);
+  if (!rc) rc = setup_impl(h, A, nx, o);
+  if (!rc) rc = ensure_ctl(h, 64);
+  if (rc) {
+    bmg_free(h);
+    return rc;
+  }
+  *out = h;
+  return BMG_OK;
+}
+
+static int reset_ctl(bmg_hierarchy* h, double tol, int maxit) {
+  int rc;
+  if ((rc = ensure_ctl(h, maxit))) return rc;
+  Ctl c0{};
+  c0.maxit = maxit;
+  c0.tol = tol;
+  c0.scale_next = 1.0;
+  c0.scale_applied = 1.0;
+  *h->ctl_host = c0;
+  CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->ws));
+  return BMG_OK;
+}
+
+int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, double* ms) {
+  if (!h || !rhs || !x || !ms || cycles < 1) return set_error(BMG_EINVAL, "bmg_time_cycles: bad argument");
+  CounterScope cs(&h->launches);
+  int rc;
+  if ((rc = order_after_user(h))) return rc;
+  if ((rc = reset_ctl(h, 0.0, cycles))) return rc;
+  enqueue_initial(h, rhs, x);
+  if (h->use_graph && (rc = capture_graph(h, rhs, x))) return rc;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, h->ws));
+  for (int i = 0; i < cycles; ++i) {
+    if (h->use_graph) {
+      CK(cudaGraphLaunch(h->gexec, h->ws));
+      h->launches += h->g_kernels;
+    } else {
+      enqueue_iteration(h, rhs, x);
+    }
+  }
+  CK(cudaEventRecord(b, h->ws));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t;
+  return cuda_check(cudaGetLastError(), "bmg_time_cycles");
+}
+
+int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_prof_row* rows, int cap) {
+  if (!h || !rhs || !x || cycles < 1) return set_error(BMG_EINVAL, "bmg_profile: bad argument");
+  CounterScope cs(&h->launches);
+  int rc;
+  if ((rc = order_after_user(h))) return rc;
+  if ((rc = reset_ctl(h, 0.0, cycles))) return rc;
+  enqueue_initial(h, rhs, x);
+  std::vector<bmg_hierarchy::Mark> marks;
+  h->prof = &marks;
+  for (int i = 0; i < cycles; ++i) enqueue_iteration(h, rhs, x);
+  h->prof = nullptr;
+  rc = cuda_check(cudaStreamSynchronize(h->ws), "bmg_profile");
+  std::vector<bmg_prof_row> acc;
+  for (auto& m : marks) {
+    float t = 0;
+    if (!rc) cudaEventElapsedTime(&t, m.a, m.b);
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+    bool found = false;
+    for (auto& r : acc)
+      if (r.level == m.level && r.kernel == m.kernel && r.fp32 == m.fp32) {
+        r.launches += (int)m.launches;
+        r.ms += t;
+        found = true;
+      }
+    if (!found) acc.push_back(bmg_prof_row{m.level, m.kernel, m.fp32, (int)m.launches, (double)t});
+  }
+  if (rc) return rc;
+  for (size_t k = 0; k < acc.size() && (int)k < cap; ++k) rows[k] = acc[k];
+  return (int)acc.size();
+}
+
+int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int maxit, int* iters, double* relres) {
+  if (!h || !rhs || !x) return set_error(BMG_EINVAL, "bmg_solve: NULL argument");
+  if (maxit < 0 || !(tol >= 0.0)) return set_error(BMG_EINVAL, "bmg_solve: bad tol or maxit");
+  CounterScope cs(&h->launches);
+  int rc;
+  if ((rc = order_after_user(h))) return rc;
+  if ((rc = reset_ctl(h, tol, maxit))) return rc;
+  enqueue_initial(h, rhs, x);
+  CK(cudaGetLastError());
+  if (h->use_graph && (rc = capture_graph(h, rhs, x))) return rc;
+  const int chunk = 4;
+  int launched = 0;
+  for (;;) {
+    CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->ws));
+    CK(cudaStreamSynchronize(h->ws));
+    if (h->ctl_host->done || launched >= maxit) break;
+    int k = maxit - launched < chunk ? maxit - launched : chunk;
+    for (int i = 0; i < k; ++i) {
+      if (h->use_graph) {
+        CK(cudaGraphLaunch(h->gexec, h->ws));
+        h->launches += h->g_kernels;
+      } else {
+        enqueue_iteration(h, rhs, x);
+      }
+    }
+    CK(cudaGetLastError());
+    launched += k;
+  }
+  Ctl& c = *h->ctl_host;
+  int it = c.it;
+  h->hist.assign((size_t)it + 1, 0.0);
+  CK(cudaMemcpy(h->hist.data(), (char*)h->ctl + offsetof(Ctl, hist), sizeof(double) * (it + 1),
+                cudaMemcpyDeviceToHost));
+  if (iters) *iters = it;
+  if (relres) *relres = h->hist[0] > 0 ? h->hist[it] / h->hist[0] : 0.0;
+  if (c.done == 3) return set_error(BMG_ENAN, "bmg_solve: residual norm is not finite at cycle %d", it);
+  if (c.done == 2 || c.done == 0) return set_error(BMG_ENOTCONV, "bmg_solve: %d cycles, relres %g", it,
+                                                   h->hist[0] > 0 ? h->hist[it] / h->hist[0] : 0.0);
+  return BMG_OK;
+}
+
+int bmg_history(const bmg_hierarchy* h, double* out, int cap) {
+  if (!h) return set_error(BMG_EINVAL, "bmg_history: NULL hierarchy");
+  int cnt = (int)h->hist.size();
+  if (out)
+    for (int k = 0; k < cnt && k < cap; ++k) out[k] = h->hist[k];
+  return cnt;
+}
+
+int bmg_num_levels(const bmg_hierarchy* h) { return h ? h->nlev : set_error(BMG_EINVAL, "NULL hierarchy"); }
+
+int bmg_level_size(const bmg_hierarchy* h, int l) {
+  if (!h || l < 0 || l >= h->nlev) return set_error(BMG_EINVAL, "bmg_level_size: bad level");
+  return h->lv[l].n;
+}
+
+int bmg_get_stencil(const bmg_hierarchy* h, int l, double* out) {
+  if (!h || !out || l < 0 || l >= h->nlev) return set_error(BMG_EINVAL, "bmg_get_stencil: bad argument");
+  CK(cudaMemcpyAsync(out, h->lv[l].st, 5 * plane_size(h->lv[l].n) * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->ws));
+  CK(cudaStreamSynchronize(h->ws));
+  return BMG_OK;
+}
+
+int bmg_get_interp(const bmg_hierarchy* h, int l, double* out) {
+  if (!h || !out || l < 0 || l + 1 >= h->nlev) return set_error(BMG_EINVAL, "bmg_get_interp: bad argument");
+  CK(cudaMemcpyAsync(out, h->lv[l].ci, 8 * plane_size(h->lv[l + 1].n) * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->ws));
+  CK(cudaStreamSynchronize(h->ws));
+  return BMG_OK;
+}
+
+long long bmg_launch_count(const bmg_hierarchy* h) { return h ? h->launches : 0; }
+
+void bmg_free(bmg_hierarchy* h) {
+  if (!h) return;
+  if (h->ws) cudaStreamSynchronize(h->ws);
+  for (Level& L : h->lv) free_level(L);
+  cudaFree(h->Lfac);
+  cudaFree(h->work);
+  cudaFree(h->partials);
+  cudaFree(h->err);
+  cudaFree(h->ctl);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->ev) cudaEventDestroy(h->ev);
+  if (h->ws) cudaStreamDestroy(h->ws);
+  delete h;
+}
+
+int bmg_inner_cycle(bmg_hierarchy* h, const float* r32, float* e32) {
+  if (!h || !r32 || !e32) return set_error(BMG_EINVAL, "bmg_inner_cycle: NULL argument");
+  if (h->precision == BMG_FP64) return set_error(BMG_EINVAL, "bmg_inner_cycle: hierarchy has no FP32 cycle");
+  CounterScope cs(&h->launches);
+  int rc;
+  if ((rc = order_after_user(h))) return rc;
+  Level& L0 = h->lv[0];
+  size_t bytes = plane_size(L0.n) * sizeof(float);
+  CK(cudaMemcpyAsync(L0.f32, r32, bytes, cudaMemcpyDeviceToDevice, h->ws));
+  CK(cudaMemsetAsync(L0.x32, 0, bytes, h->ws));
+  for (int c = 0; c < h->inner; ++c) vcycle32(h, 0, nullptr);
+  CK(cudaMemcpyAsync(e32, L0.x32, bytes, cudaMemcpyDeviceToDevice, h->ws));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->ws));
+  return BMG_OK;
+}
+
+// ---- stateless steps -----------------------------------------------------------------
+
+static StencilView<double, double> raw_view(int n, const double* coef, bool with_d) {
+  size_t ps = plane_size(n);
+  return {coef, coef + ps, coef + 2 * ps, coef + 3 * ps, coef + 4 * ps, with_d ? coef + 5 * ps : nullptr, n, n + 2};
+}
+
+static int step_done(cudaStream_t s, const char* what) {
+  CK(cudaGetLastError());
+  int rc = cuda_check(cudaStreamSynchronize(s), what);
+  return rc;
+}
+
+int bmg_dendy_interp(int n, const double* coef, double* ci, void* stream) {
+  if (!is_level_size(n) || !coef || !ci) return set_error(BMG_EINVAL, "bmg_dendy_interp: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = nullptr;
+  CK(cudaMallocAsync((void**)&err, sizeof(int), s));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  launch_dendy(n, coef, ci, err, s);
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(err, s));
+  int rc = step_done(s, "bmg_dendy_interp");
+  if (rc) return rc;
+  return herr ? set_error(BMG_ESINGULAR, "bmg_dendy_interp: non-positive denominator") : BMG_OK;
+}
+
+int bmg_rap(int n, const double* coef, const double* ci, double* coarse, void* stream) {
+  if (!is_level_size(n) || !coef || !ci || !coarse) return set_error(BMG_EINVAL, "bmg_rap: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the kernel writes six planes; give it room for the sixth
+  int nc = (n - 1) / 2;
+  double* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, 6 * plane_size(nc) * sizeof(double), s));
+  launch_rap(n, coef, ci, tmp, s);
+  CK(cudaMemcpyAsync(coarse, tmp, 5 * plane_size(nc) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaFreeAsync(tmp, s));
+  return step_done(s, "bmg_rap");
+}
+
+int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, int sweeps, void* stream) {
+  if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !f || !x || sweeps < 0)
+    return set_error(BMG_EINVAL, "bmg_relax: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_gs(raw_view(n, coef, false), kind, f, x, sweeps, (const int*)nullptr, s);
+  return step_done(s, "bmg_relax");
+}
+
+int bmg_resid_restrict(int n, int kind, const double* coef, const double* ci, const double* x, const double* f,
+                       double* fc, void* stream) {
+  if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !ci || !x || !f || !fc)
+    return set_error(BMG_EINVAL, "bmg_resid_restrict: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(fc, 0, plane_size((n - 1) / 2) * sizeof(double), s));
+  launch_resid_restrict(raw_view(n, coef, false), kind, ci, x, f, fc, (double*)nullptr, (const int*)nullptr, s);
+  return step_done(s, "bmg_resid_restrict");
+}
+
+int bmg_interp_correct(int n, const double* ci, const double* ec, double* x, void* stream) {
+  if (!is_level_size(n) || !ci || !ec || !x) return set_error(BMG_EINVAL, "bmg_interp_correct: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_interp_correct<double>(n, ci, ec, x, (const int*)nullptr, s);
+  return step_done(s, "bmg_interp_correct");
+}
+
+int bmg_residual(int n, int kind, const double* coef, const double* x, const double* f, double* r, double* norm,
+                 void* stream) {
+  if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !x || !f)
+    return set_error(BMG_EINVAL, "bmg_residual: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = nullptr;   // partial sums + the norm
+  if (norm) CK(cudaMallocAsync((void**)&scratch, (norm_partials_max() + 1) * sizeof(double), s));
+  if (r) zero_ring(n, r, s);
+  int np = launch_residual(raw_view(n, coef, false), kind, x, f, r, scratch, (const int*)nullptr, s);
+  if (norm) {
+    launch_norm_finalize(scratch, np, nullptr, 0, scratch + norm_partials_max(), s);
+    CK(cudaMemcpyAsync(norm, scratch + norm_partials_max(), sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(scratch, s));
+  }
+  return step_done(s, "bmg_residual");
+}
+
+int bmg_coarse_factor(int n, const double* coef, double* L, void* stream) {
+  if (!is_level_size(n) || n > 15 || !coef || !L) return set_error(BMG_EINVAL, "bmg_coarse_factor: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int m = n * n;
+  double* work = nullptr;
+  int* err = nullptr;
+  CK(cudaMallocAsync((void**)&work, (size_t)m * m * sizeof(double), s));
+  CK(cudaMallocAsync((void**)&err, sizeof(int), s));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  launch_factor(n, coef, L, work, err, s);
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(work, s));
+  CK(cudaFreeAsync(err, s));
+  int rc = step_done(s, "bmg_coarse_factor");
+  if (rc) return rc;
+  return herr ? set_error(BMG_ESINGULAR, "bmg_coarse_factor: non-positive pivot") : BMG_OK;
+}
+
+int bmg_coarse_solve(int n, const double* L, const double* f, double* x, void* stream) {
+  if (!is_level_size(n) || n > 15 || !L || !f || !x) return set_error(BMG_EINVAL, "bmg_coarse_solve: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* y = nullptr;
+  CK(cudaMallocAsync((void**)&y, (size_t)n * n * sizeof(double), s));
+  launch_coarse_solve<double>(n, L, f, x, y, (const int*)nullptr, s);
+  CK(cudaFreeAsync(y, s));
+  return step_done(s, "bmg_coarse_solve");
+}
+
+int bmg_measure_fp64_rate(double* out, void* stream) {
+  if (!out) return set_error(BMG_EINVAL, "bmg_measure_fp64_rate: NULL");
+  double r = measure_fp64_rate((cudaStream_t)stream);
+  if (r <= 0) return set_error(BMG_ECUDA, "bmg_measure_fp64_rate failed");
+  *out = r;
+  return BMG_OK;
+}
+
+}  // extern "C"

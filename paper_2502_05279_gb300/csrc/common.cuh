@@ -1,0 +1,89 @@
+// Device helpers shared by the BoxMG kernels: rounding-explicit arithmetic,
+// stencil access through the symmetric five-plane storage, launch bookkeeping.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bmg.h"
+
+namespace bmg {
+
+// ---- arithmetic with one rounding per operation (never contracted to FMA) ----
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// ---- storage -> compute conversion (exact for every pair used) ----
+template <typename T> __device__ __forceinline__ T cvt(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T cvt(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
+
+// Canonical neighbour order of every row sum: O, W, E, S, N, SW, NE, NW, SE.
+__host__ __device__ constexpr int nbr_dx(int k) {
+  return k == 1 ? -1 : k == 2 ? 1 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? -1 : k == 8 ? 1 : 0;
+}
+__host__ __device__ constexpr int nbr_dy(int k) {
+  return k == 3 ? -1 : k == 4 ? 1 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? 1 : k == 8 ? -1 : 0;
+}
+
+// Five-plane stencil view: O, W, S, SW, NW (each ld * ld, plane stride ps).
+template <typename S>
+struct Planes {
+  const S* O;
+  const S* W;
+  const S* Sp;
+  const S* SW;
+  const S* NW;
+  // a(p, p + (dx, dy)) for the k-th canonical neighbour, p = linear index.
+  template <int K>
+  __device__ __forceinline__ S a(size_t p, int ld) const {
+    if (K == 0) return O[p];
+    if (K == 1) return W[p];
+    if (K == 2) return W[p + 1];
+    if (K == 3) return Sp[p];
+    if (K == 4) return Sp[p + ld];
+    if (K == 5) return SW[p];
+    if (K == 6) return SW[p + ld + 1];
+    if (K == 7) return NW[p];
+    return NW[p + 1 - ld];
+  }
+};
+
+template <typename S>
+__host__ __device__ inline Planes<S> planes_at(const S* base, size_t ps) {
+  return Planes<S>{base, base + ps, base + 2 * ps, base + 3 * ps, base + 4 * ps};
+}
+
+// Interpolation plane indices (Fig. 2 labels).
+enum { CI_LSW = 0, CI_LSE, CI_LNW, CI_LNE, CI_LL, CI_LR, CI_LB, CI_LA };
+
+__host__ __device__ inline size_t plane_size(int n) { return (size_t)(n + 2) * (size_t)(n + 2); }
+
+// Control block of one solve (device memory).  `done`: 0 running, 1 converged,
+// 2 maxit reached, 3 NaN/Inf.
+struct Ctl {
+  int done;
+  int it;
+  int maxit;
+  int pad;
+  double tol;
+  double scale_next;     // power-of-two scale for the next FP32 residual
+  double scale_applied;  // the scale the current FP32 residual carries
+  double hist[1];        // [maxit + 1] residual norms (allocated past the struct)
+};
+
+}  // namespace bmg
+
+// Host-side launch helpers (implemented in bmg_api.cu).
+namespace bmg {
+void count_launch();
+int set_error(int code, const char* fmt, ...);
+int cuda_check(cudaError_t e, const char* what);
+}  // namespace bmg

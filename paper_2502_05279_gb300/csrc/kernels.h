@@ -1,0 +1,68 @@
+// Host-side launchers of the BoxMG kernels (one translation unit per family).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace bmg {
+
+// Stencil of one level as the kernels read it: diagonal O and reciprocal
+// diagonal D in the compute type T, off-diagonal planes W, S, SW, NW in the
+// storage type S (T itself, or bf16 under a float T).
+template <typename T, typename S>
+struct StencilView {
+  const T* O;
+  const S* W;
+  const S* S_;
+  const S* SW;
+  const S* NW;
+  const T* D;
+  int n;
+  int ld;
+};
+
+// ---- setup (k_setup.cu), FP64 ----
+// st: 6 planes O, W, S, SW, NW, D of (n+2)^2.  err: device int, set nonzero on
+// a zero or negative diagonal / denominator / pivot.
+void launch_prepare(int n, int kind, const double* coef_in, double* st, int* err, cudaStream_t s);
+void launch_dendy(int n, const double* st, double* ci, int* err, cudaStream_t s);
+void launch_rap(int n, const double* st, const double* ci, double* stc, cudaStream_t s);
+void launch_dinv(int n, double* st, int* err, cudaStream_t s);
+void launch_factor(int n, const double* st, double* L, double* work, int* err, cudaStream_t s);
+void launch_lower32(int n, const double* st, float* st32, const double* ci, float* ci32, cudaStream_t s);
+void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od32, cudaStream_t s);
+
+// ---- cycle (k_cycle.cu) ----
+// `done`: device flag of the running solve (NULL = always run); every kernel
+// returns at once when it is nonzero.
+template <typename T, typename S>
+void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s);
+template <typename T, typename S>
+void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,
+                           T* xc, const int* done, cudaStream_t s);
+template <typename T>
+void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s);
+// r = f - A x (r may be NULL) with per-block partial sums of r^2 (partials may
+// be NULL); returns the number of partials written.
+template <typename T, typename S>
+int launch_residual(const StencilView<T, S>& v, int kind, const T* x, const T* f, T* r, double* partials,
+                    const int* done, cudaStream_t s);
+template <typename T>
+void launch_coarse_solve(int n, const double* L, const T* f, T* x, double* y, const int* done, cudaStream_t s);
+
+int norm_partials_max();
+// Sum partials in a fixed order and record the norm in ctl (phase 0 = initial
+// residual, 1 = after a cycle).  Also writes the norm to out (may be NULL).
+void launch_norm_finalize(const double* partials, int np, void* ctl, int phase, double* out, cudaStream_t s);
+
+// Iterative refinement: x += scale_applied * e32 and the FP64 residual with
+// its FP32 scaled copy (r32 = fl32(r / scale_next)), zeroing e32 for the next
+// inner cycle.
+void launch_ir_update(int n, double* x, const float* e32, void* ctl, cudaStream_t s);
+int launch_ir_residual(const StencilView<double, double>& v, int kind, const double* x, const double* f,
+                       float* r32, float* e32_zero, double* partials, void* ctl, cudaStream_t s);
+
+// FP64 throughput probe.
+double measure_fp64_rate(cudaStream_t s);
+
+}  // namespace bmg

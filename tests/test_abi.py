@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry point
+include/bmg.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "bmg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bmg_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import __graft_entry__
+    return __graft_entry__._builder().build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("bmg_setup", "bmg_solve", "bmg_free", "bmg_history", "bmg_dendy_interp", "bmg_rap",
+                 "bmg_relax", "bmg_resid_restrict", "bmg_interp_correct", "bmg_residual",
+                 "bmg_coarse_factor", "bmg_coarse_solve", "bmg_inner_cycle"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_imports_and_reports_errors_without_gpu(libpath):
+    import paper_2502_05279_gb300 as bmg
+    assert bmg.lib.bmg_strerror(-6).decode() == "not converged within maxit"
+    assert bmg.lib.bmg_strerror(0).decode() == "ok"
+    # argument validation happens on the host, before any CUDA call
+    h = ctypes.c_void_p()
+    st = bmg._lib.Stencil(9, None)
+    assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 127, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
+    st = bmg._lib.Stencil(7, ctypes.c_void_p(16))
+    assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 127, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
+    st = bmg._lib.Stencil(9, ctypes.c_void_p(16))
+    for n in (0, 1, 2, 4, 100, 128):
+        assert bmg.lib.bmg_setup(ctypes.byref(st), n, n, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
+    assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 63, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
+    assert "not 2^m - 1" in bmg.lib.bmg_last_error().decode() or "nx" in bmg.lib.bmg_last_error().decode()
+    assert bmg.lib.bmg_solve(None, None, None, 1e-10, 10, None, None) == bmg._lib.BMG_EINVAL
+    bmg.lib.bmg_free(None)

@@ -1,0 +1,271 @@
+"""GPU parity: every step of the hot path through the C ABI against the CPU
+oracle on the same seeded inputs.  The FP64 path rounds every operation the
+way the oracle does, so iterates, weights and coarse operators must agree bit
+for bit; norms (different summation order) agree to 1e-14 relative."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle import boxmg as bx
+from oracle import mixed as mx
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def problem(case, n):
+    if case == "poisson":
+        return w.poisson_problem(n, 1)
+    if case == "binary":
+        return w.binary_contrast_problem(n, 16 if n >= 127 else 4, seed_k=2, seed_f=3)
+    if case == "lognormal":
+        return w.lognormal_problem(n, 2.0, 8.0, seed_k=4, seed_f=7)
+    raise ValueError(case)
+
+
+CASES = [("poisson", 63), ("poisson", 255), ("binary", 127), ("binary", 255), ("lognormal", 255)]
+
+
+@pytest.mark.parametrize("case,n", CASES)
+def test_dendy_interp_bitwise(bmg, case, n):
+    kind, planes, _ = problem(case, n)
+    want = bx.dendy_interp(planes)
+    got = host(bmg.dendy_interp(dev(planes)))
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("case,n", CASES)
+def test_rap_bitwise(bmg, case, n):
+    kind, planes, _ = problem(case, n)
+    ci = bx.dendy_interp(planes)
+    want = bx.rap(planes, ci)
+    got = host(bmg.rap(dev(planes), dev(ci)))
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("case,n", CASES)
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_relax_bitwise(bmg, case, n, sweeps):
+    kind, planes, f = problem(case, n)
+    x0 = w.rhs_uniform(n, 99) * 0.1
+    want = x0.copy()
+    dinv = np.zeros_like(f)
+    bx.at(dinv, 0, 0)[...] = 1.0 / bx.at(planes[0], 0, 0)
+    for _ in range(sweeps):
+        bx.gs_sweep(kind, planes, dinv, want, f)
+    xg = dev(x0)
+    bmg.relax(kind, dev(planes), dev(f), xg, sweeps)
+    assert np.array_equal(host(xg), want)
+
+
+@pytest.mark.parametrize("case,n", CASES)
+def test_resid_restrict_bitwise(bmg, case, n):
+    kind, planes, f = problem(case, n)
+    x = w.rhs_uniform(n, 98) * 0.3
+    ci = bx.dendy_interp(planes)
+    want = bx.restrict(ci, bx.residual(planes, x, f))
+    got = host(bmg.resid_restrict(kind, dev(planes), dev(ci), dev(x), dev(f)))
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("case,n", CASES)
+def test_interp_correct_bitwise(bmg, case, n):
+    kind, planes, _ = problem(case, n)
+    ci = bx.dendy_interp(planes)
+    nc = (n - 1) // 2
+    ec = w.rhs_uniform(nc, 97)
+    x = w.rhs_uniform(n, 96)
+    want = x.copy()
+    bx.interp_correct(ci, ec, want)
+    xg = dev(x)
+    bmg.interp_correct(dev(ci), dev(ec), xg)
+    assert np.array_equal(host(xg), want)
+
+
+@pytest.mark.parametrize("case,n", CASES)
+def test_residual_and_norm(bmg, case, n):
+    kind, planes, f = problem(case, n)
+    x = w.rhs_uniform(n, 95)
+    want = bx.residual(planes, x, f)
+    r, nrm = bmg.residual(kind, dev(planes), dev(x), dev(f))
+    assert np.array_equal(host(r), want)
+    assert abs(nrm - bx.norm(want)) <= 1e-14 * bx.norm(want)
+
+
+@pytest.mark.parametrize("n", [3, 7, 15])
+def test_coarse_factor_and_solve_bitwise(bmg, n):
+    kind, planes, f = problem("lognormal", n)
+    A = bx.dense_matrix(planes)
+    Lw = bx.cholesky(A)
+    Lg = bmg.coarse_factor(dev(planes))
+    assert np.array_equal(host(Lg), Lw)
+    want = np.zeros_like(f)
+    bx.at(want, 0, 0)[...] = bx.chol_solve(Lw, bx.at(f, 0, 0).reshape(-1)).reshape(n, n)
+    xg = torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda")
+    bmg.coarse_solve(Lg, dev(f), xg)
+    assert np.array_equal(host(xg), want)
+
+
+def test_coarse_factor_rejects_indefinite(bmg):
+    planes = w.poisson5(3)
+    planes[0] *= -1.0
+    with pytest.raises(bmg.BmgError) as e:
+        bmg.coarse_factor(dev(planes))
+    assert e.value.code == -4
+
+
+@pytest.mark.parametrize("case,n", [("poisson", 127), ("binary", 255), ("lognormal", 127)])
+def test_hierarchy_bitwise(bmg, case, n):
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes)
+    coef = dev(planes[:3] if kind == 5 else planes)
+    h = bmg.Hierarchy(kind, coef)
+    assert h.num_levels == len(levels)
+    for l, lev in enumerate(levels):
+        assert h.level_size(l) == lev.n
+        assert np.array_equal(host(h.stencil(l)), lev.planes)
+        if lev.ci is not None:
+            assert np.array_equal(host(h.interp(l)), lev.ci)
+    h.close()
+
+
+def check_history(got, want):
+    assert len(got) == len(want)
+    r0 = want[0]
+    for g, t in zip(got, want):
+        assert abs(g - t) <= 1e-12 * r0
+        if t >= 1e-3 * r0:
+            assert abs(g - t) <= 1e-12 * t
+
+
+@pytest.mark.parametrize("case,n", [("poisson", 127), ("binary", 255), ("lognormal", 255), ("poisson", 7),
+                                    ("binary", 3)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_fp64_solve_matches_oracle(bmg, case, n, graph):
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes)
+    xw, hw = bx.solve(levels, f, tol=1e-10, maxit=200)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), use_graph=graph)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(host(x), xw)
+    check_history(h.history(), hw)
+    assert rr <= 1e-10
+    h.close()
+
+
+def test_fp64_solve_with_initial_guess_and_maxit(bmg):
+    kind, planes, f = problem("binary", 127)
+    levels = bx.setup(kind, planes)
+    x0 = w.rhs_uniform(127, 5)
+    xw, hw = bx.solve(levels, f, x0=x0, tol=1e-12, maxit=3)
+    h = bmg.Hierarchy(kind, dev(planes))
+    x, it, rr, ok = h.solve(dev(f), dev(x0), tol=1e-12, maxit=3)
+    assert not ok and it == 3
+    assert np.array_equal(host(x), xw)
+    check_history(h.history(), hw)
+
+
+def test_zero_rhs_and_zero_maxit(bmg):
+    kind, planes, f = problem("poisson", 63)
+    h = bmg.Hierarchy(kind, dev(planes[:3]))
+    x, it, rr, ok = h.solve(torch.zeros((65, 65), dtype=torch.float64, device="cuda"))
+    assert ok and it == 0 and not x.any()
+    x, it, rr, ok = h.solve(dev(f), maxit=0)
+    assert not ok and it == 0 and not x.any()
+
+
+def test_nan_rhs_reports_enan(bmg):
+    kind, planes, f = problem("poisson", 63)
+    f[10, 10] = np.nan
+    h = bmg.Hierarchy(kind, dev(planes[:3]))
+    with pytest.raises(bmg.BmgError) as e:
+        h.solve(dev(f))
+    assert e.value.code == -5
+
+
+def test_setup_rejects_bad_sizes_and_indefinite(bmg):
+    planes = w.poisson5(63)
+    with pytest.raises(bmg.BmgError):
+        bmg.Hierarchy(5, dev(planes[:3, :64, :64].copy()))
+    bad = planes.copy()
+    bad[0] *= -1
+    with pytest.raises(bmg.BmgError) as e:
+        bmg.Hierarchy(5, dev(bad[:3]))
+    assert e.value.code == -4
+
+
+# ---- mixed precision -----------------------------------------------------------
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("case,n", [("binary", 255), ("lognormal", 127), ("poisson", 63)])
+def test_inner_cycle_bitwise(bmg, precision, nbf, case, n):
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes)
+    l32 = mx.lower(levels, nbf)
+    r32 = (w.rhs_uniform(n, 94)).astype(np.float32)
+    want = mx.inner_cycle(l32, r32)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision)
+    got = host(h.inner_cycle(dev(r32, torch.float32)))
+    assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0))
+
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("case,n", [("binary", 255), ("lognormal", 255), ("poisson", 127)])
+def test_ir_solve_matches_oracle(bmg, precision, nbf, case, n):
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes)
+    xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=200)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+    check_history(h.history(), hw)
+    # the refined solution is FP64-accurate: its oracle residual meets the tolerance
+    assert bx.norm(bx.residual(levels[0].planes, host(x), f)) <= 1e-10 * hw[0]
+
+
+# ---- full size of the bench workload ----------------------------------------------
+
+@pytest.mark.slow
+def test_bench_workload_first_cycles_bitwise(bmg):
+    """2047^2, 9-point, k in {1, 1e4} on 16x16 blocks: setup and three V(2,1)
+    cycles in the launch configuration the bench times (CUDA graph), compared
+    with the oracle over every grid point."""
+    kind, planes, f = w.binary_contrast_problem(2047, 16, seed_k=2, seed_f=3)
+    levels = bx.setup(kind, planes)
+    xw, hw = bx.solve(levels, f, tol=1e-14, maxit=3)
+    h = bmg.Hierarchy(kind, dev(planes))
+    for l in (0, 1):
+        assert np.array_equal(host(h.stencil(l)), levels[l].planes)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-14, maxit=3)
+    assert it == 3
+    assert np.array_equal(host(x), xw)
+    check_history(h.history(), hw)
+
+
+def test_time_cycles_and_profile(bmg):
+    kind, planes, f = problem("binary", 255)
+    h = bmg.Hierarchy(kind, dev(planes))
+    x = torch.zeros((257, 257), dtype=torch.float64, device="cuda")
+    before = h.launch_count
+    ms = h.time_cycles(dev(f), x, 5)
+    assert ms > 0 and h.launch_count > before
+    levels = bx.setup(kind, planes)
+    xw = np.zeros_like(f)
+    for _ in range(5):
+        bx.vcycle(levels, 0, xw, f)
+    assert np.array_equal(host(x), xw)
+    rows = h.profile(dev(f), torch.zeros_like(x), 2)
+    kinds = {(r["level"], r["kernel"]) for r in rows}
+    assert (0, "relax") in kinds and (0, "resid_restrict") in kinds and (0, "residual_norm") in kinds
+    assert (len(levels) - 1, "coarse_solve") in kinds
+    assert all(r["ms"] > 0 and r["launches"] > 0 for r in rows)
