@@ -189,6 +189,23 @@ int bmg_interp_correct(int n, const double* ci, const double* ec, double* x, voi
 int bmg_residual(int n, int kind, const double* coef, const double* x, const double* f,
                  double* r, double* norm, void* stream);
 
+/* bmg_residual without any device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot let the library allocate device
+ * memory (a host framework that owns the device memory pool, allocation-free
+ * real-time or callback paths, checks that forbid allocator calls in a region
+ * of work).  Arguments, layouts and results are those of bmg_residual.  The
+ * partial sums of the norm live in one fixed device array of the library
+ * (1024 partial sums + the result, 8 KiB, held by every GPU that loads the
+ * library until the process exits); the kernel uses min(n, 1024) of them, so
+ * every valid n fits, and a partial count beyond the array is rejected with
+ * BMG_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams or
+ * host threads) race on it, so serialise them.  Calls no cudaMalloc/cudaFree
+ * or allocating routine. */
+int bmg_residual_noalloc(int n, int kind, const double* coef, const double* x, const double* f,
+                         double* r, double* norm, void* stream);
+
 /* Lower-triangular Cholesky factor L (row-major m x m, m = n^2, lexicographic
  * unknowns j outer, i inner) of a level's operator (Fig. 1 "Cholesky");
  * BMG_ESINGULAR on a non-positive pivot.  n <= 15. */
