@@ -66,6 +66,7 @@ enum {
 
 enum { BMG_FP64 = 0, BMG_FP32_IR = 1, BMG_BF16_IR = 2 };
 enum { BMG_INTERP_DENDY = 0, BMG_INTERP_LEARNED = 1 };
+enum { BMG_KRYLOV_NONE = 0, BMG_KRYLOV_FCG = 1 };
 
 typedef struct bmg_hierarchy bmg_hierarchy;   /* opaque, library-owned */
 
@@ -83,6 +84,8 @@ typedef struct {
   int inner_cycles;     /* FP32 V-cycles per refinement step (0 = 1) */
   int bf16_levels;      /* levels with BF16 stencils under BMG_BF16_IR (0 = 2) */
   int use_graph;        /* 1 = replay one captured CUDA graph per cycle (default), 0 = plain launches */
+  int krylov;           /* BMG_KRYLOV_NONE (default): stationary V-cycle iteration;
+                           BMG_KRYLOV_FCG: flexible CG with one cycle as preconditioner */
   void* stream;         /* cudaStream_t for setup and every later call on the hierarchy */
 } bmg_opts;
 
@@ -99,6 +102,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* opts, bmg_hi
 
 /* Solve A x = rhs by V(nu1,nu2) cycles (Fig. 1) until ||r_k||/||r_0|| <= tol
  * (r_0 = rhs - A x_in, Euclidean norm over the interior) or `maxit` cycles.
+ * With krylov = BMG_KRYLOV_FCG each iteration is one step of flexible CG
+ * (one-term recurrence) preconditioned by one cycle from a zero guess, and the
+ * test uses the recursively updated residual.  Norms and inner products sum in
+ * one fixed order (rows b, b+G, ... per block b < G = min(n,1024), columns
+ * t, t+256, ... per thread t < 256, then halving trees), so histories repeat
+ * bit for bit.
  * rhs: device, (n+2)^2, read only.  x: device, (n+2)^2, in: initial guess,
  * out: solution (its ghost ring is not written).  iters, relres: host, may be
  * NULL.  Under BMG_FP32_IR / BMG_BF16_IR one "cycle" is one FP64 refinement
@@ -125,7 +134,7 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
  * hierarchy's stream (the Fig. 10 breakdown).  Fills up to `cap` rows of the
  * host array `rows` and returns the number of rows. */
 enum { BMG_K_RELAX = 0, BMG_K_RESID_RESTRICT = 1, BMG_K_INTERP = 2, BMG_K_COARSE = 3, BMG_K_NORM = 4,
-       BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7 };
+       BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7, BMG_K_FCG = 8 };
 typedef struct {
   int level;            /* 0 = finest */
   int kernel;           /* BMG_K_* */

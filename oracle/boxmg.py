@@ -137,10 +137,57 @@ def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray) -> np.ndarray:
     return r
 
 
+REDUCE_BLOCKS = 1024
+REDUCE_THREADS = 256
+
+
+def ordered_sum(v: np.ndarray) -> float:
+    """Sum of an (n, n) array of interior values in one fixed order, FP64, one
+    rounding per addition:
+      1. for b < G = min(n, 1024) and t < 256, a running sum over the rows
+         j = b, b+G, ... (outer) and the columns i = t, t+256, ... (inner);
+      2. per b, a halving tree over t: s[t] += s[t + h] for h = 128, 64, ..., 1;
+      3. over the G block sums: running sums over b = t, t+256, ... per t < 256,
+         then the same halving tree.
+    Any order gives the sum to within n^2 rounding errors; this one is stated so
+    that every implementation of it gets the same bits."""
+    v = np.asarray(v, dtype=np.float64)
+    n_rows, n_cols = v.shape
+    G = min(n_rows, REDUCE_BLOCKS)
+    T = REDUCE_THREADS
+    acc = np.zeros((G, T))
+    for k in range(0, (n_rows + G - 1) // G):
+        rows = v[k * G:(k + 1) * G]                       # row k*G + b for block b
+        for m in range(0, (n_cols + T - 1) // T):
+            blk = rows[:, m * T:(m + 1) * T]
+            acc[:blk.shape[0], :blk.shape[1]] = acc[:blk.shape[0], :blk.shape[1]] + blk
+    acc = _halving_tree(acc)
+    parts = np.zeros(((G + T - 1) // T) * T)
+    parts[:G] = acc
+    fin = np.zeros((1, T))
+    for m in range(0, len(parts) // T):
+        fin[0] = fin[0] + parts[m * T:(m + 1) * T]
+    return float(_halving_tree(fin)[0])
+
+
+def _halving_tree(a: np.ndarray) -> np.ndarray:
+    a = a.copy()
+    h = a.shape[1] // 2
+    while h >= 1:
+        a[:, :h] = a[:, :h] + a[:, h:2 * h]
+        h //= 2
+    return a[:, 0]
+
+
 def norm(r: np.ndarray) -> float:
-    """Euclidean norm over the interior, accumulated in FP64."""
+    """Euclidean norm over the interior: sqrt of the ordered sum of squares."""
     v = at(r, 0, 0).astype(np.float64)
-    return float(np.sqrt(np.sum(v * v)))
+    return math.sqrt(ordered_sum(v * v))
+
+
+def dot(a: np.ndarray, b: np.ndarray) -> float:
+    """Interior inner product in the same order as norm()."""
+    return ordered_sum(at(a, 0, 0).astype(np.float64) * at(b, 0, 0).astype(np.float64))
 
 
 # ---------------------------------------------------------------------------
@@ -486,5 +533,46 @@ def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
     while it < maxit and hist[-1] / hist[0] > tol:
         vcycle(levels, 0, x, f, nu1, nu2)
         hist.append(norm(residual(lev.planes, x, f)))
+        it += 1
+    return x, hist
+
+
+def solve_fcg(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
+    """Flexible conjugate gradients (one-term recurrence, Notay's FCG(1)) with
+    one V(nu1, nu2) cycle from a zero guess as the preconditioner.  Per step:
+      z = V(r); p = z if first else z + beta p with beta = -(z.q)/(p.q) of the
+      previous step; q = A p; alpha = (p.r)/(p.q); x += alpha p; r -= alpha q.
+    The test uses the recursively updated residual.  Returns (x, history)."""
+    return _fcg(levels[0].planes, lambda r: _precondition64(levels, r, nu1, nu2), f, x0, tol, maxit)
+
+
+def _precondition64(levels, r, nu1, nu2):
+    z = np.zeros_like(r)
+    vcycle(levels, 0, z, r, nu1, nu2)
+    return z
+
+
+def _fcg(planes, precond, f, x0, tol, maxit):
+    x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
+    r = residual(planes, x, f)
+    hist = [norm(r)]
+    if hist[0] == 0.0:
+        return x, hist
+    p = q = None
+    pq = 0.0
+    it = 0
+    while it < maxit and hist[-1] / hist[0] > tol:
+        z = precond(r)
+        if p is None:
+            p = z
+        else:
+            beta = -(dot(z, q) / pq)
+            p = z + beta * p
+        q = apply(planes, p)
+        pq = dot(p, q)
+        alpha = dot(p, r) / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        hist.append(norm(r))
         it += 1
     return x, hist

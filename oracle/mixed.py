@@ -102,3 +102,14 @@ def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2
         hist.append(bx.norm(r))
         it += 1
     return x, hist
+
+
+def solve_fcg_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2, nu2=1):
+    """Flexible CG in FP64 whose preconditioner is the FP32 cycle:
+    z = s fl64(V32(fl32(r / s))) with s = 2^e the power of two of ||r||
+    (any power of two gives the same z bit for bit)."""
+    def precond(r):
+        s = scale_of(bx.norm(r))
+        r32 = (r * (1.0 / s)).astype(F32)
+        return s * inner_cycle(levels32, r32, cycles, nu1, nu2).astype(np.float64)
+    return bx._fcg(levels[0].planes, precond, f, x0, tol, maxit)

@@ -42,13 +42,15 @@ class ProfRow(ctypes.Structure):
 
 
 KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
-                "ir_update", "ir_residual")
+                "ir_update", "ir_residual", "fcg")
+_KRYLOV = {"none": 0, "fcg": 1}
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -110,11 +112,12 @@ class Hierarchy:
 
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
-                 use_graph: bool = True):
+                 use_graph: bool = True, krylov: str = "none"):
         n = _n_of(coef)
         self.n, self.kind, self.precision = n, kind, precision
         st = Stencil(kind, _ptr(coef, name="coef"))
-        o = Opts(_PREC[precision], 0, coarsest, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), _stream())
+        o = Opts(_PREC[precision], 0, coarsest, nu1, nu2, inner_cycles, bf16_levels, int(use_graph),
+                 _KRYLOV[krylov], _stream())
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -82,7 +82,8 @@ StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
 }  // namespace
 
 struct bmg_hierarchy {
-  int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3;
+  int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3, krylov = 0;
+  double* kr = nullptr;   // flexible CG vectors r, z, p, q (FP64, (n+2)^2 each)
   std::vector<Level> lv;
   cudaStream_t user = nullptr;   // caller stream (ordering only)
   cudaStream_t ws = nullptr;     // internal non-blocking work stream
@@ -207,7 +208,21 @@ void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
   const int* done = &h->ctl->done;
   Level& L0 = h->lv[0];
   int np = 0;
-  if (h->precision == BMG_FP64) {
+  if (h->krylov == BMG_KRYLOV_FCG) {
+    size_t ps = plane_size(L0.n);
+    double *r = h->kr, *z = h->kr + ps, *pv = h->kr + 2 * ps, *q = h->kr + 3 * ps;
+    bool mixed = h->precision != BMG_FP64;
+    if (mixed)
+      for (int c = 0; c < h->inner; ++c) vcycle32(h, 0, done);
+    else
+      vcycle64(h, 0, z, r, done);
+    step(h, 0, BMG_K_FCG, 0, [&] {
+      launch_fcg_step(view64(L0), L0.kind, x, r, mixed ? nullptr : z, mixed ? L0.x32 : nullptr, pv, q,
+                      mixed ? L0.f32 : nullptr, mixed ? L0.x32 : nullptr, mixed ? nullptr : z, h->partials, h->ctl,
+                      h->ws, nullptr, nullptr);
+    });
+    np = L0.n < norm_partials_max() ? L0.n : norm_partials_max();
+  } else if (h->precision == BMG_FP64) {
     vcycle64(h, 0, x, rhs, done);
     step(h, 0, BMG_K_NORM, 0, [&] {
       np = launch_residual(view64(L0), L0.kind, (const double*)x, rhs, (double*)nullptr, h->partials, done, h->ws);
@@ -224,7 +239,13 @@ void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
 
 int enqueue_initial(bmg_hierarchy* h, const double* rhs, double* x) {
   Level& L0 = h->lv[0];
-  if (h->precision == BMG_FP64) {
+  if (h->krylov == BMG_KRYLOV_FCG) {
+    size_t ps = plane_size(L0.n);
+    bool mixed = h->precision != BMG_FP64;
+    int np = launch_fcg_init(view64(L0), L0.kind, x, rhs, h->kr, mixed ? nullptr : h->kr + ps,
+                             mixed ? L0.f32 : nullptr, mixed ? L0.x32 : nullptr, h->partials, h->ctl, h->ws);
+    launch_norm_finalize(h->partials, np, h->ctl, 0, nullptr, h->ws);
+  } else if (h->precision == BMG_FP64) {
     int np = launch_residual(view64(L0), L0.kind, x, rhs, (double*)nullptr, h->partials, (const int*)nullptr, h->ws);
     launch_norm_finalize(h->partials, np, h->ctl, 0, nullptr, h->ws);
   } else {
@@ -317,7 +338,12 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
   h->m = h->coarsest * h->coarsest;
   if ((rc = dalloc(&h->Lfac, (size_t)h->m * h->m))) return rc;
   if ((rc = dalloc(&h->work, (size_t)h->m * h->m + h->m))) return rc;
-  if ((rc = dalloc(&h->partials, (size_t)norm_partials_max()))) return rc;
+  if ((rc = dalloc(&h->partials, 2 * (size_t)norm_partials_max()))) return rc;
+  if (h->krylov == BMG_KRYLOV_FCG) {
+    size_t ps = plane_size(n);
+    if ((rc = dalloc(&h->kr, 4 * ps))) return rc;
+    CK(cudaMemsetAsync(h->kr, 0, 4 * ps * sizeof(double), s));
+  }
   if ((rc = dalloc(&h->err, 1))) return rc;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
 
@@ -401,10 +427,11 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     }
     h->inner = o->inner_cycles > 0 ? o->inner_cycles : 1;
     h->use_graph = o->use_graph;
+    h->krylov = o->krylov;
     h->user = (cudaStream_t)o->stream;
   }
   if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
-      h->nu1 < 0 || h->nu2 < 0 || (o && o->interp != BMG_INTERP_DENDY)) {
+      h->nu1 < 0 || h->nu2 < 0 || (o && o->interp != BMG_INTERP_DENDY) || h->krylov < 0 || h->krylov > 1) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad options");
   }
@@ -580,6 +607,7 @@ void bmg_free(bmg_hierarchy* h) {
   cudaFree(h->Lfac);
   cudaFree(h->work);
   cudaFree(h->partials);
+  cudaFree(h->kr);
   cudaFree(h->err);
   cudaFree(h->ctl);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);

@@ -76,6 +76,10 @@ struct Ctl {
   double tol;
   double scale_next;     // power-of-two scale for the next FP32 residual
   double scale_applied;  // the scale the current FP32 residual carries
+  // flexible CG scalars
+  double zq, pq, pr, pq_prev;
+  int first;             // 1 until the first direction is formed
+  int pad2;
   double hist[1];        // [maxit + 1] residual norms (allocated past the struct)
 };
 

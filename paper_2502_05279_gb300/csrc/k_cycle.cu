@@ -413,3 +413,219 @@ template void launch_coarse_solve<float>(int, const double*, const float*, float
                                          cudaStream_t);
 
 }  // namespace bmg
+
+// ==== flexible conjugate gradients ======================================================
+// Notay's FCG(1) with the V-cycle as preconditioner, FP64 outer loop:
+//   z = M r; p = z (first step) or z + beta p with beta = -(z.q)/(p.q)_previous;
+//   q = A p; alpha = (p.r)/(p.q); x += alpha p; r -= alpha q.
+// Every inner product uses the reduction order of k_residual / k_norm_finalize.
+namespace bmg {
+namespace {
+
+__device__ __forceinline__ double zval(const double* z, const float* z32, double s, size_t p) {
+  return z32 ? rmul(s, (double)z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
+}
+
+// p.q over the grid with the canonical order; f(p) gives the product term.
+template <class F>
+__device__ __forceinline__ void ordered_partial(int n, int ld, double* partials, F term) {
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) acc = __dadd_rn(acc, term((size_t)j * ld + i));
+  double tot = block_sum<double>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __restrict__ z,
+                                                         const float* __restrict__ z32, const double* __restrict__ q,
+                                                         double* __restrict__ partials, const Ctl* ctl) {
+  if (ctl->done) return;
+  const double s = ctl->scale_applied;
+  ordered_partial(n, n + 2, partials, [&](size_t p) { return rmul(zval(z, z32, s, p), q[p]); });
+}
+
+__device__ __forceinline__ double reduce_partials(const double* partials, int np) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < np; k += NORM_THREADS) acc = __dadd_rn(acc, partials[k]);
+  return block_sum<double>(acc);
+}
+
+// slot 0: zq; slot 1: pq and pr (second partial array right after the first)
+__global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __restrict__ partials, int np, Ctl* ctl,
+                                                             int which) {
+  if (ctl->done) return;
+  if (which == 0) {
+    double v = reduce_partials(partials, np);
+    if (threadIdx.x == 0) ctl->zq = v;
+  } else {
+    double a = reduce_partials(partials, np);
+    __syncthreads();
+    double b = reduce_partials(partials + NORM_BLOCKS_MAX, np);
+    if (threadIdx.x == 0) {
+      ctl->pq = a;
+      ctl->pr = b;
+    }
+  }
+}
+
+__global__ void k_fcg_direction(int n, const double* __restrict__ z, const float* __restrict__ z32,
+                                double* __restrict__ pv, const Ctl* ctl) {
+  if (ctl->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > n || j > n) return;
+  size_t p = (size_t)j * (n + 2) + i;
+  double zp = zval(z, z32, ctl->scale_applied, p);
+  if (ctl->first) {
+    pv[p] = zp;
+  } else {
+    double beta = -rdiv(ctl->zq, ctl->pq_prev);
+    pv[p] = radd(zp, rmul(beta, pv[p]));
+  }
+}
+
+// q = A p (row sum a_O p + a_W p_W + ... in canonical order), partial p.q and p.r
+__global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double, double> v, int nine,
+                                                             const double* __restrict__ pv, const double* __restrict__ r,
+                                                             double* __restrict__ q, double* __restrict__ partials,
+                                                             const Ctl* ctl) {
+  if (ctl->done) return;
+  const int n = v.n, ld = v.ld;
+  double apq = 0.0, apr = 0.0;
+  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
+      size_t p = (size_t)j * ld + i;
+      double acc = rmul(v.O[p], pv[p]);
+      acc = radd(acc, rmul(v.W[p], pv[p - 1]));
+      acc = radd(acc, rmul(v.W[p + 1], pv[p + 1]));
+      acc = radd(acc, rmul(v.S_[p], pv[p - ld]));
+      acc = radd(acc, rmul(v.S_[p + ld], pv[p + ld]));
+      if (nine) {
+        acc = radd(acc, rmul(v.SW[p], pv[p - ld - 1]));
+        acc = radd(acc, rmul(v.SW[p + ld + 1], pv[p + ld + 1]));
+        acc = radd(acc, rmul(v.NW[p], pv[p + ld - 1]));
+        acc = radd(acc, rmul(v.NW[p + 1 - ld], pv[p + 1 - ld]));
+      }
+      q[p] = acc;
+      apq = __dadd_rn(apq, rmul(pv[p], acc));
+      apr = __dadd_rn(apr, rmul(pv[p], r[p]));
+    }
+  double t1 = block_sum<double>(apq);
+  __syncthreads();
+  double t2 = block_sum<double>(apr);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = t1;
+    partials[NORM_BLOCKS_MAX + blockIdx.x] = t2;
+  }
+}
+
+// x += alpha p, r -= alpha q, partial r.r; zero the preconditioner output and,
+// in mixed precision, write r32 = fl32(r / scale_next).
+__global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __restrict__ x, double* __restrict__ r,
+                                                             const double* __restrict__ pv,
+                                                             const double* __restrict__ q, float* __restrict__ r32,
+                                                             float* __restrict__ z32, double* __restrict__ z,
+                                                             double* __restrict__ partials, Ctl* ctl) {
+  if (ctl->done) return;
+  const int ld = n + 2;
+  const double alpha = rdiv(ctl->pr, ctl->pq);
+  const double s = ctl->scale_next;
+  const double inv = 1.0 / s;
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
+      size_t p = (size_t)j * ld + i;
+      x[p] = radd(x[p], rmul(alpha, pv[p]));
+      double rr = rsub(r[p], rmul(alpha, q[p]));
+      r[p] = rr;
+      if (r32) {
+        r32[p] = __double2float_rn(rmul(rr, inv));
+        z32[p] = 0.0f;
+      } else {
+        z[p] = 0.0;
+      }
+      acc = __dadd_rn(acc, rmul(rr, rr));
+    }
+  double tot = block_sum<double>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = tot;
+    if (blockIdx.x == 0) {
+      ctl->scale_applied = s;
+      ctl->pq_prev = ctl->pq;
+      ctl->first = 0;
+    }
+  }
+}
+
+// r = f - A x, stored; r32 / zero z as in k_fcg_update; partial r.r.
+__global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, double> v, int nine,
+                                                           const double* __restrict__ x, const double* __restrict__ f,
+                                                           double* __restrict__ r, double* __restrict__ z,
+                                                           float* __restrict__ r32, float* __restrict__ z32,
+                                                           double* __restrict__ partials, Ctl* ctl) {
+  const int n = v.n, ld = v.ld;
+  const double s = ctl->scale_next;
+  const double inv = 1.0 / s;
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
+      size_t p = (size_t)j * ld + i;
+      double rr = nine ? row_residual<double, double, true, true>(v, x, p, f[p])
+                       : row_residual<double, double, false, true>(v, x, p, f[p]);
+      r[p] = rr;
+      if (r32) {
+        r32[p] = __double2float_rn(rmul(rr, inv));
+        z32[p] = 0.0f;
+      } else {
+        z[p] = 0.0;
+      }
+      acc = __dadd_rn(acc, rmul(rr, rr));
+    }
+  double tot = block_sum<double>(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = tot;
+    if (blockIdx.x == 0) {
+      ctl->scale_applied = s;
+      ctl->first = 1;
+    }
+  }
+}
+
+}  // namespace
+
+int launch_fcg_init(const StencilView<double, double>& v, int kind, const double* x, const double* f, double* r,
+                    double* z, float* r32, float* z32, double* partials, void* ctl, cudaStream_t s) {
+  int g = norm_blocks(v.n);
+  k_fcg_init<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
+  count_launch();
+  return g;
+}
+
+// One FCG step after the preconditioner: z.q, beta and p, q = A p with p.q and
+// p.r, then the x / r update with r.r partials (finalised by the caller).
+// `mark(arg, k)` (may be NULL) brackets the sub-steps for profiling.
+void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
+                     const float* z32, double* pv, double* q, float* r32, float* z32_zero, double* z_zero,
+                     double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg) {
+  const int n = v.n;
+  int g = norm_blocks(n);
+  Ctl* c = (Ctl*)ctl;
+  if (mark) mark(mark_arg, 0);
+  k_fcg_zq<<<g, NORM_THREADS, 0, s>>>(n, z, z32, q, partials, c);
+  count_launch();
+  k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 0);
+  count_launch();
+  k_fcg_direction<<<grid2(n, n), dim3(BX, BY), 0, s>>>(n, z, z32, pv, c);
+  count_launch();
+  if (mark) mark(mark_arg, 1);
+  k_fcg_matvec<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, pv, r, q, partials, c);
+  count_launch();
+  k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 1);
+  count_launch();
+  if (mark) mark(mark_arg, 2);
+  k_fcg_update<<<g, NORM_THREADS, 0, s>>>(n, x, r, pv, q, r32, z32_zero, z_zero, partials, c);
+  count_launch();
+  if (mark) mark(mark_arg, 3);
+}
+
+}  // namespace bmg

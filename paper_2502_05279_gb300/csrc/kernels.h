@@ -62,6 +62,14 @@ void launch_ir_update(int n, double* x, const float* e32, void* ctl, cudaStream_
 int launch_ir_residual(const StencilView<double, double>& v, int kind, const double* x, const double* f,
                        float* r32, float* e32_zero, double* partials, void* ctl, cudaStream_t s);
 
+// Flexible CG (FP64 outer loop).  z is the preconditioned residual: an FP64
+// vector, or (z32 != NULL) scale_applied * z32.
+int launch_fcg_init(const StencilView<double, double>& v, int kind, const double* x, const double* f, double* r,
+                    double* z, float* r32, float* z32, double* partials, void* ctl, cudaStream_t s);
+void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
+                     const float* z32, double* p, double* q, float* r32, float* z32_zero, double* z_zero,
+                     double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg);
+
 // FP64 throughput probe.
 double measure_fp64_rate(cudaStream_t s);
 

@@ -459,3 +459,52 @@ def test_ir_scale_is_power_of_two():
     for rho in (1.0, 0.75, 3e-11, 123456.0):
         s = mx.scale_of(rho)
         assert math.frexp(s)[0] == 0.5 and 0.5 <= rho / s < 1.0
+
+
+# --------------------------------------------------------------------------
+# Reductions and flexible CG
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 7, 255, 1023, 1500])
+def test_ordered_sum_is_the_sum(n):
+    v = w.normal(900 + n, n * n).reshape(n, n)
+    exact = math.fsum(v.reshape(-1))
+    assert abs(bx.ordered_sum(v) - exact) <= 4 * n * n * 2.3e-16 * np.abs(v).sum()
+    ints = np.round(v * 1000)                      # integer-valued: every order is exact
+    assert bx.ordered_sum(ints) == math.fsum(ints.reshape(-1))
+
+
+def test_fcg_single_level_is_one_direct_step():
+    levels = bx.setup(9, w.fe9_from_cells(w.lognormal_cells(3, 2.0, 2.0, 5)))
+    f = w.rhs_uniform(3, 6)
+    x, hist = bx.solve_fcg(levels, f, tol=1e-14)
+    assert len(hist) == 2 and hist[1] <= 1e-14 * hist[0]
+
+
+@pytest.mark.parametrize("n", [7, 15])
+def test_fcg_matches_dense_direct_solve(n):
+    k = w.binary_blocks(n, 2, 1.0, 1e4, 70 + n)
+    levels = bx.setup(9, w.fe9_from_cells(k))
+    f = w.rhs_uniform(n, 71 + n)
+    x, hist = bx.solve_fcg(levels, f, tol=1e-13, maxit=100)
+    u = np.linalg.solve(q1_assembled_matrix(k), interior(f).reshape(-1))
+    assert np.abs(interior(x).reshape(-1) - u).max() <= 1e-9 * np.abs(u).max()
+
+
+def test_fcg_beats_stagnating_vcycle_on_high_contrast():
+    kind, planes, f = w.binary_contrast_problem(255, 8, 1.0, 1e6, seed_k=6, seed_f=7)
+    levels = bx.setup(kind, planes)
+    _, hv = bx.solve(levels, f, tol=1e-8, maxit=40)
+    x, hf = bx.solve_fcg(levels, f, tol=1e-8, maxit=200)
+    assert hv[-1] / hv[0] > 1e-8            # the stationary cycle has not got there in 40
+    assert hf[-1] <= 1e-8 * hf[0] and len(hf) - 1 < 150
+    true = bx.norm(bx.residual(levels[0].planes, x, f))
+    assert true <= 1e-6 * hf[0]             # recursive and true residual agree to the FP64 floor
+
+
+def test_fcg_ir_reaches_fp64_accuracy():
+    kind, planes, f = w.binary_contrast_problem(127, 8, seed_k=2, seed_f=3)
+    levels = bx.setup(kind, planes)
+    x, hist = mx.solve_fcg_ir(levels, mx.lower(levels, 2), f, tol=1e-10, maxit=200)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert bx.norm(bx.residual(levels[0].planes, x, f)) <= 1e-9 * hist[0]
