@@ -148,6 +148,18 @@ def run_ours(args, rank, local_rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.only:
+        # one hierarchy, warm-up and timed cycles only: the small run profiled by ncu
+        h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov)
+        x = torch.zeros_like(rhs)
+        h.time_cycles(rhs, x, args.warmup)
+        ms = h.time_cycles(rhs, x, args.steps)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "krylov": args.krylov, "workload": args.workload,
+                              "ms_per_step": ms / args.steps, "launches": h.launch_count}))
+        h.close()
+        return
+
     variants = {}
     clock_s = None
     timed_launches = 0
@@ -346,6 +358,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--maxit-vcycle", type=int, default=200, help="cap of the stationary-cycle solve")
+    ap.add_argument("--only", choices=("fp64", "fp32", "bf16"), default=None,
+                    help="time one hierarchy's cycles only (short run for profilers)")
+    ap.add_argument("--krylov", choices=("none", "fcg"), default="none", help="solve mode for --only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

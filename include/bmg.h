@@ -164,6 +164,43 @@ void bmg_free(bmg_hierarchy* h);
 const char* bmg_strerror(int code);
 const char* bmg_last_error(void);
 
+/* ---- batched solver ---------------------------------------------------------
+ * Many independent problems solved together: every stage of the cycle (a
+ * level counted from the coarsest, so all problems in it share one size) is
+ * one kernel launch over all problems, and one iteration of the whole batch is
+ * one CUDA graph.  Each problem keeps its own hierarchy, convergence test and
+ * history, and its arithmetic is that of a solo solve, so its iterates and
+ * history equal those of bmg_solve on that problem bit for bit.  Stationary
+ * cycles only (krylov must be BMG_KRYLOV_NONE); all problems share `kind`. */
+typedef struct bmg_batch bmg_batch;   /* opaque, library-owned */
+
+/* nprob problems; A[p] and n[p] as in bmg_setup (n[p] = 2^m - 1 >= coarsest).
+ * opts (may be NULL) apply to every problem.  With opts->use_graph the row
+ * tile of the Gauss-Seidel kernels of every stage with n >= 127 is chosen by
+ * timing the candidates on scratch copies of that stage (autotuner). */
+int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* opts, bmg_batch** out);
+
+/* rhs[p], x[p]: host arrays of nprob device pointers, layouts as in bmg_solve.
+ * iters, relres: host arrays of nprob entries (may be NULL).  Problems stop
+ * individually at ||r_k||/||r_0|| <= tol.  Returns BMG_OK when all converged,
+ * else BMG_ENOTCONV / BMG_ENAN (per-problem detail in iters, relres). */
+int bmg_solve_batched(bmg_batch* b, const double* const* rhs, double* const* x, double tol, int maxit,
+                      int* iters, double* relres);
+
+/* History of problem p in the last batched solve (as bmg_history). */
+int bmg_batched_history(const bmg_batch* b, int p, double* out, int cap);
+
+/* `cycles` batch iterations with no convergence test, timed with CUDA events
+ * on the batch's stream (as bmg_time_cycles). */
+int bmg_time_cycles_batched(bmg_batch* b, const double* const* rhs, double* const* x, int cycles, double* ms);
+
+/* Kernel launches issued for the batch since setup; the row-kernel cluster
+ * size the autotuner chose for stage `stage` (0 = coarsest), or 0. */
+long long bmg_batched_launch_count(const bmg_batch* b);
+int bmg_batched_tuned_cluster(const bmg_batch* b, int stage);
+
+void bmg_free_batched(bmg_batch* b);   /* NULL is a no-op */
+
 /* ---- single steps, for testing and composition -------------------------
  * Stateless: every pointer is caller-owned device memory in the layouts above;
  * `kind` is 5 or 9 and `coef` holds 5 planes either way (kind 5 ignores SW, NW).

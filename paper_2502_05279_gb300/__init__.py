@@ -6,6 +6,6 @@ There is no CPU fallback: importing the binding fails when the library is
 missing or cannot load.
 """
 from ._lib import (  # noqa: F401
-    BMG_BF16_IR, BMG_FP32_IR, BMG_FP64, BmgError, Hierarchy, coarse_factor, coarse_solve, dendy_interp,
+    BMG_BF16_IR, BMG_FP32_IR, BMG_FP64, Batch, BmgError, Hierarchy, coarse_factor, coarse_solve, dendy_interp,
     interp_correct, lib, library_path, measure_fp64_rate, rap, relax, resid_restrict, residual,
 )

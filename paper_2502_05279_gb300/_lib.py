@@ -77,6 +77,14 @@ _sig = {
     "bmg_inner_cycle": (I, [P, P, P]),
     "bmg_measure_fp64_rate": (I, [ctypes.POINTER(D), P]),
     "bmg_time_cycles": (I, [P, P, P, I, ctypes.POINTER(D)]),
+    "bmg_setup_batched": (I, [I, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
+    "bmg_solve_batched": (I, [P, P, P, D, I, P, P]),
+    "bmg_batched_history": (I, [P, I, ctypes.POINTER(D), I]),
+    "bmg_time_cycles_batched": (I, [P, P, P, I, ctypes.POINTER(D)]),
+    "bmg_batched_launch_count": (L, [P]),
+    "bmg_batched_tuned_cluster": (I, [P, I]),
+    "bmg_free_batched": (None, [P]),
+    "bmg_residual_noalloc": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
     "bmg_profile": (I, [P, P, P, I, P, I]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -182,6 +190,68 @@ class Hierarchy:
     def close(self):
         if getattr(self, "_h", None):
             lib.bmg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent problems solved together (bmg_setup_batched): one
+    launch per cycle stage over all problems, one CUDA graph per iteration."""
+
+    def __init__(self, kind: int, coefs, precision: str = "fp64", nu1: int = 2, nu2: int = 1,
+                 inner_cycles: int = 1, bf16_levels: int = 2, use_graph: bool = True):
+        self.kind, self.precision = kind, precision
+        self.ns = [_n_of(c) for c in coefs]
+        self._coefs = list(coefs)
+        nprob = len(coefs)
+        sts = (Stencil * nprob)(*[Stencil(kind, _ptr(c, name="coef")) for c in coefs])
+        ns = (ctypes.c_int * nprob)(*self.ns)
+        o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, _stream())
+        h = ctypes.c_void_p()
+        _check(lib.bmg_setup_batched(nprob, sts, ns, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def _ptrs(self, ts, name):
+        return (ctypes.c_void_p * len(ts))(*[_ptr(t, name=name).value for t in ts])
+
+    def solve(self, rhs, xs=None, tol: float = 1e-10, maxit: int = 100):
+        """Returns (xs, iterations per problem, relative residual per problem, all converged)."""
+        if xs is None:
+            xs = [torch.zeros_like(r) for r in rhs]
+        nprob = len(rhs)
+        it = (ctypes.c_int * nprob)()
+        rr = (ctypes.c_double * nprob)()
+        rc = _check(lib.bmg_solve_batched(self._h, self._ptrs(rhs, "rhs"), self._ptrs(xs, "x"), tol, maxit, it, rr),
+                    allow=(BMG_ENOTCONV,))
+        return xs, list(it), list(rr), rc == BMG_OK
+
+    def history(self, p: int):
+        cnt = lib.bmg_batched_history(self._h, p, None, 0)
+        buf = (ctypes.c_double * max(cnt, 1))()
+        lib.bmg_batched_history(self._h, p, buf, cnt)
+        return list(buf[:cnt])
+
+    def time_cycles(self, rhs, xs, cycles: int) -> float:
+        ms = ctypes.c_double(0.0)
+        _check(lib.bmg_time_cycles_batched(self._h, self._ptrs(rhs, "rhs"), self._ptrs(xs, "x"), cycles,
+                                           ctypes.byref(ms)))
+        return ms.value
+
+    def tuned_cluster(self, stage: int) -> int:
+        return _check_size(lib.bmg_batched_tuned_cluster(self._h, stage))
+
+    @property
+    def launch_count(self) -> int:
+        return lib.bmg_batched_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bmg_free_batched(self._h)
             self._h = None
 
     def __del__(self):

@@ -755,3 +755,501 @@ int bmg_measure_fp64_rate(double* out, void* stream) {
 }
 
 }  // extern "C"
+
+// =====================================================================================
+// Batched solver
+// =====================================================================================
+#include <array>
+#include <map>
+#include <tuple>
+
+namespace {
+// group slot = storage * 2 + (kind == 5): storage 0 double, 1 float, 2 bf16
+constexpr int kGroups = 6;
+}
+
+struct bmg_batch {
+  int nprob = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1;
+  std::vector<bmg_hierarchy*> hs;
+  cudaStream_t user = nullptr, ws = nullptr;
+  cudaEvent_t ev = nullptr;
+  int bmax = 0, maxn = 0;
+  struct Group {
+    int n = 0, count = 0, cl = 1, storage = 0, kind = 9;
+    size_t elem = 0;
+    void* d = nullptr;
+    std::vector<char> host;
+  };
+  std::vector<std::array<Group, kGroups>> stages;   // index b = levels above the coarsest
+  std::vector<int> tuned_cl;                         // per stage, 0 = not tuned
+  std::vector<TopDesc> top;
+  TopDesc* d_top = nullptr;
+  char* ctls = nullptr;
+  size_t ctl_stride = 0;
+  int maxit_cap = 0;
+  std::vector<char> ctl_host;
+  int* d_alldone = nullptr;
+  int* h_alldone = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const double*> g_rhs;
+  std::vector<double*> g_x;
+  long long g_kernels = 0, launches = 0;
+  std::vector<std::vector<double>> hist;
+};
+
+namespace {
+
+Ctl* batch_ctl(bmg_batch* B, int p) { return (Ctl*)(B->ctls + (size_t)p * B->ctl_stride); }
+
+int group_slot(int storage, int kind) { return storage * 2 + (kind == 5 ? 1 : 0); }
+
+template <typename T, typename S>
+void append_desc(bmg_batch::Group& g, const LevelDesc<T, S>& d) {
+  const char* c = (const char*)&d;
+  g.host.insert(g.host.end(), c, c + sizeof(d));
+}
+
+// Fill every stage's descriptor tables and the top-level table for the caller
+// buffers rhs/x and upload them (the device addresses never change, so a
+// captured graph stays valid).  With rhs == NULL only the group sizes are set.
+int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x) {
+  for (auto& st : B->stages)
+    for (auto& g : st) {
+      g.host.clear();
+      if (!rhs) g.count = 0;
+    }
+  B->top.clear();
+  for (int p = 0; p < B->nprob; ++p) {
+    bmg_hierarchy* h = B->hs[p];
+    const int L = h->nlev;
+    const int* done = &batch_ctl(B, p)->done;
+    for (int l = 0; l < L; ++l) {
+      Level& lv = h->lv[l];
+      const int b = L - 1 - l;
+      Level* C = l + 1 < L ? &h->lv[l + 1] : nullptr;
+      int storage = B->precision == BMG_FP64 ? 0 : (lv.bf16 ? 2 : 1);
+      bmg_batch::Group& g = B->stages[b][group_slot(storage, lv.kind)];
+      g.n = lv.n;
+      g.storage = storage;
+      g.kind = lv.kind;
+      if (!rhs) {
+        ++g.count;
+        g.elem = storage == 0 ? sizeof(LevelDesc<double, double>)
+                              : storage == 1 ? sizeof(LevelDesc<float, float>) : sizeof(LevelDesc<float, __nv_bfloat16>);
+        continue;
+      }
+      if (storage == 0) {
+        LevelDesc<double, double> d{view64(lv), lv.ci, l == 0 ? x[p] : lv.x, l == 0 ? rhs[p] : lv.f,
+                                    C ? C->x : nullptr, C ? C->f : nullptr, done, h->Lfac, h->work};
+        append_desc(g, d);
+      } else if (storage == 2) {
+        LevelDesc<float, __nv_bfloat16> d{viewbf(lv), lv.ci32, lv.x32, lv.f32, C ? C->x32 : nullptr,
+                                          C ? C->f32 : nullptr, done, h->Lfac, h->work};
+        append_desc(g, d);
+      } else {
+        LevelDesc<float, float> d{view32(lv), lv.ci32, lv.x32, lv.f32, C ? C->x32 : nullptr, C ? C->f32 : nullptr,
+                                  done, h->Lfac, h->work};
+        append_desc(g, d);
+      }
+    }
+    if (rhs) {
+      Level& l0 = h->lv[0];
+      B->top.push_back(TopDesc{view64(l0), l0.kind, x[p], rhs[p], l0.f32, l0.x32, h->partials, batch_ctl(B, p)});
+    }
+  }
+  if (!rhs) return BMG_OK;
+  for (auto& st : B->stages)
+    for (auto& g : st)
+      if (g.count) {
+        if (g.host.size() != g.elem * (size_t)g.count) return set_error(BMG_ECUDA, "batched: table size mismatch");
+        CK(cudaMemcpyAsync(g.d, g.host.data(), g.host.size(), cudaMemcpyHostToDevice, B->ws));
+      }
+  CK(cudaMemcpyAsync(B->d_top, B->top.data(), sizeof(TopDesc) * B->top.size(), cudaMemcpyHostToDevice, B->ws));
+  return BMG_OK;
+}
+
+template <typename T, typename S>
+const LevelDesc<T, S>* gdesc(const bmg_batch::Group& g) { return (const LevelDesc<T, S>*)g.d; }
+
+void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
+  if (!g.count || !sweeps) return;
+  if (g.storage == 0) launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
+  else if (g.storage == 1) launch_gs_b(gdesc<float, float>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
+  else launch_gs_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
+}
+
+void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
+  if (!g.count) return;
+  if (g.storage == 0) launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws);
+  else if (g.storage == 1) launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws);
+  else launch_resid_restrict_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, B->ws);
+}
+
+void group_interp(bmg_batch* B, bmg_batch::Group& g) {
+  if (!g.count) return;
+  if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws);
+  else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws);
+  else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws);
+}
+
+void group_coarse(bmg_batch* B, bmg_batch::Group& g) {
+  if (!g.count) return;
+  if (g.storage == 0) launch_coarse_b(gdesc<double, double>(g), g.count, B->ws);
+  else if (g.storage == 1) launch_coarse_b(gdesc<float, float>(g), g.count, B->ws);
+  else launch_coarse_b(gdesc<float, __nv_bfloat16>(g), g.count, B->ws);
+}
+
+// One V(nu1, nu2) cycle of every problem: down the stages (largest first), the
+// coarsest solves, back up.
+void batch_vcycle(bmg_batch* B) {
+  for (int b = B->bmax; b >= 1; --b)
+    for (auto& g : B->stages[b]) {
+      group_relax(B, g, B->nu1);
+      group_restrict(B, g);
+    }
+  for (auto& g : B->stages[0]) group_coarse(B, g);
+  for (int b = 1; b <= B->bmax; ++b)
+    for (auto& g : B->stages[b]) {
+      group_interp(B, g);
+      group_relax(B, g, B->nu2);
+    }
+}
+
+void batch_iteration(bmg_batch* B) {
+  if (B->precision == BMG_FP64) {
+    batch_vcycle(B);
+    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+  } else {
+    for (int c = 0; c < B->inner; ++c) batch_vcycle(B);
+    launch_ir_update_b(B->d_top, B->nprob, B->maxn, B->ws);
+    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+  }
+  launch_finalize_b(B->d_top, B->nprob, 1, B->ws);
+}
+
+void batch_initial(bmg_batch* B) {
+  if (B->precision == BMG_FP64)
+    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+  else
+    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+  launch_finalize_b(B->d_top, B->nprob, 0, B->ws);
+}
+
+int batch_ensure_ctl(bmg_batch* B, int maxit) {
+  if (B->ctls && maxit <= B->maxit_cap) return BMG_OK;
+  int cap = maxit < 64 ? 64 : maxit;
+  size_t stride = (sizeof(Ctl) + sizeof(double) * (size_t)(cap + 1) + 255) / 256 * 256;
+  char* c = nullptr;
+  CK(cudaMalloc((void**)&c, stride * B->nprob));
+  if (B->ctls) cudaFree(B->ctls);
+  B->ctls = c;
+  B->ctl_stride = stride;
+  B->maxit_cap = cap;
+  if (B->gexec) {   // tables and graph hold control-block addresses
+    cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+  }
+  B->g_rhs.clear();
+  return BMG_OK;
+}
+
+int batch_reset(bmg_batch* B, double tol, int maxit) {
+  int rc;
+  if ((rc = batch_ensure_ctl(B, maxit))) return rc;
+  B->ctl_host.assign(B->ctl_stride * B->nprob, 0);
+  for (int p = 0; p < B->nprob; ++p) {
+    Ctl* c = (Ctl*)(B->ctl_host.data() + (size_t)p * B->ctl_stride);
+    c->maxit = maxit;
+    c->tol = tol;
+    c->scale_next = 1.0;
+    c->scale_applied = 1.0;
+  }
+  CK(cudaMemcpyAsync(B->ctls, B->ctl_host.data(), B->ctl_host.size(), cudaMemcpyHostToDevice, B->ws));
+  return BMG_OK;
+}
+
+int batch_prepare(bmg_batch* B, const double* const* rhs, double* const* x) {
+  bool same = B->gexec && (int)B->g_rhs.size() == B->nprob;
+  for (int p = 0; same && p < B->nprob; ++p) same = B->g_rhs[p] == rhs[p] && B->g_x[p] == x[p];
+  int rc;
+  if ((rc = build_batch_tables(B, rhs, x))) return rc;
+  if (!B->use_graph || same) return BMG_OK;
+  if (B->gexec) {
+    cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(B->ws, cudaStreamCaptureModeThreadLocal));
+  long long before = B->launches;
+  batch_iteration(B);
+  B->g_kernels = B->launches - before;
+  B->launches = before;
+  CK(cudaStreamEndCapture(B->ws, &g));
+  cudaError_t e = cudaGraphInstantiate(&B->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  B->g_rhs.assign(rhs, rhs + B->nprob);
+  B->g_x.assign(x, x + B->nprob);
+  return BMG_OK;
+}
+
+int batch_launch_iterations(bmg_batch* B, int k) {
+  for (int i = 0; i < k; ++i) {
+    if (B->use_graph) {
+      CK(cudaGraphLaunch(B->gexec, B->ws));
+      B->launches += B->g_kernels;
+    } else {
+      batch_iteration(B);
+    }
+  }
+  return cuda_check(cudaGetLastError(), "batched iteration");
+}
+
+// Autotuner: for every stage of 9-point levels with n >= 127, time two sweeps
+// of the row kernel for each admissible cluster size on scratch copies of the
+// stage's iterates (the stencils are the real ones) and keep the fastest.  The
+// choice changes only how a row is split over CTAs, never a result bit.
+static std::map<std::tuple<int, int, int, int>, int> g_tuned;   // (n, storage, count, sweeps) -> cluster size
+
+template <typename T, typename S>
+int tune_group(bmg_batch* B, bmg_batch::Group& g) {
+  auto key = std::make_tuple(g.n, g.storage, g.count, 2);
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    g.cl = it->second;
+    return BMG_OK;
+  }
+  const int base = rows_cluster<T>(g.n);
+  size_t ps = plane_size(g.n);
+  T* scratch = nullptr;
+  CK(cudaMalloc((void**)&scratch, 2 * ps * sizeof(T) * g.count));
+  CK(cudaMemsetAsync(scratch, 0, 2 * ps * sizeof(T) * g.count, B->ws));
+  std::vector<LevelDesc<T, S>> d((const LevelDesc<T, S>*)g.host.data(),
+                                 (const LevelDesc<T, S>*)g.host.data() + g.count);
+  for (int k = 0; k < g.count; ++k) {
+    d[k].x = scratch + 2 * ps * k;
+    d[k].f = scratch + 2 * ps * k + ps;
+    d[k].done = nullptr;
+  }
+  LevelDesc<T, S>* dd = nullptr;
+  CK(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count));
+  CK(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_cl = base;
+  for (int cl = base; cl <= 8; cl *= 2) {
+    if (cl > base && ((g.n + 1) / 2 + cl - 1) / cl < 32) break;   // fewer than a warp of pairs per CTA
+    launch_gs_b<T, S>(dd, g.count, g.n, 9, 1, cl, B->ws);   // warm-up
+    cudaEventRecord(e0, B->ws);
+    launch_gs_b<T, S>(dd, g.count, g.n, 9, 2, cl, B->ws);
+    cudaEventRecord(e1, B->ws);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_cl = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(dd);
+  cudaFree(scratch);
+  CK(cudaGetLastError());
+  g.cl = best_cl;
+  g_tuned[key] = best_cl;
+  return BMG_OK;
+}
+
+int autotune_batch(bmg_batch* B) {
+  // descriptor contents are needed: build the tables with the internal level
+  // arrays standing in for the caller buffers of level 0
+  std::vector<const double*> rhs(B->nprob);
+  std::vector<double*> x(B->nprob);
+  for (int p = 0; p < B->nprob; ++p) {
+    rhs[p] = B->hs[p]->lv[0].st;   // any valid device address: tuning swaps in scratch iterates
+    x[p] = B->hs[p]->lv[0].st;
+  }
+  int rc;
+  if ((rc = build_batch_tables(B, rhs.data(), x.data()))) return rc;
+  for (int b = 1; b <= B->bmax; ++b) {
+    for (auto& g : B->stages[b]) {
+      if (!g.count || g.kind != 9 || g.n < 127) continue;
+      if (g.storage == 0) rc = tune_group<double, double>(B, g);
+      else if (g.storage == 1) rc = tune_group<float, float>(B, g);
+      else rc = tune_group<float, __nv_bfloat16>(B, g);
+      if (rc) return rc;
+      B->tuned_cl[b] = g.cl;
+    }
+  }
+  return BMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* o, bmg_batch** out) {
+  if (!out) return set_error(BMG_EINVAL, "bmg_setup_batched: out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !A || !n) return set_error(BMG_EINVAL, "bmg_setup_batched: bad argument");
+  if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_setup_batched: stationary cycles only");
+  for (int p = 1; p < nprob; ++p)
+    if (A[p].kind != A[0].kind) return set_error(BMG_EINVAL, "bmg_setup_batched: problems differ in kind");
+  bmg_batch* B = new bmg_batch();
+  B->nprob = nprob;
+  bmg_opts so{};
+  if (o) so = *o;
+  so.use_graph = 0;
+  if (o) {
+    B->precision = o->precision;
+    if (o->nu1 || o->nu2) {
+      B->nu1 = o->nu1;
+      B->nu2 = o->nu2;
+    }
+    B->inner = o->inner_cycles > 0 ? o->inner_cycles : 1;
+    B->use_graph = o->use_graph;
+    B->user = (cudaStream_t)o->stream;
+  }
+  CounterScope cs(&B->launches);
+  int rc = cuda_check(cudaStreamCreateWithFlags(&B->ws, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming), "event");
+  if (!rc) rc = cuda_check(cudaEventRecord(B->ev, B->user), "event");
+  if (!rc) rc = cuda_check(cudaStreamWaitEvent(B->ws, B->ev, 0), "event");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "sync");
+  so.stream = (void*)B->ws;
+  for (int p = 0; p < nprob && !rc; ++p) {
+    bmg_hierarchy* h = nullptr;
+    rc = bmg_setup(&A[p], n[p], n[p], &so, &h);
+    if (!rc) {
+      B->hs.push_back(h);
+      B->launches += h->launches;
+      B->maxn = std::max(B->maxn, n[p]);
+      B->bmax = std::max(B->bmax, h->nlev - 1);
+    }
+  }
+  if (!rc) {
+    B->stages.assign(B->bmax + 1, {});
+    B->tuned_cl.assign(B->bmax + 1, 0);
+    rc = build_batch_tables(B, nullptr, nullptr);   // group sizes
+  }
+  for (auto& st : B->stages)
+    for (auto& g : st) {
+      if (rc || !g.count) continue;
+      g.cl = g.storage == 0 ? rows_cluster<double>(g.n) : rows_cluster<float>(g.n);
+      rc = cuda_check(cudaMalloc(&g.d, g.elem * g.count), "batched tables");
+    }
+  if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_top, sizeof(TopDesc) * nprob), "batched tables");
+  if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
+  if (!rc) rc = cuda_check(cudaMallocHost((void**)&B->h_alldone, sizeof(int)), "pinned");
+  if (!rc) rc = batch_ensure_ctl(B, 64);
+  if (!rc && B->use_graph) rc = autotune_batch(B);
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "bmg_setup_batched");
+  if (rc) {
+    bmg_free_batched(B);
+    return rc;
+  }
+  *out = B;
+  return BMG_OK;
+}
+
+int bmg_solve_batched(bmg_batch* B, const double* const* rhs, double* const* x, double tol, int maxit, int* iters,
+                      double* relres) {
+  if (!B || !rhs || !x) return set_error(BMG_EINVAL, "bmg_solve_batched: NULL argument");
+  if (maxit < 0 || !(tol >= 0.0)) return set_error(BMG_EINVAL, "bmg_solve_batched: bad tol or maxit");
+  for (int p = 0; p < B->nprob; ++p)
+    if (!rhs[p] || !x[p]) return set_error(BMG_EINVAL, "bmg_solve_batched: NULL buffer of problem %d", p);
+  CounterScope cs(&B->launches);
+  int rc;
+  CK(cudaEventRecord(B->ev, B->user));
+  CK(cudaStreamWaitEvent(B->ws, B->ev, 0));
+  if ((rc = batch_reset(B, tol, maxit))) return rc;
+  if ((rc = batch_prepare(B, rhs, x))) return rc;
+  batch_initial(B);
+  const int chunk = 4;
+  int launched = 0;
+  for (;;) {
+    launch_all_done(B->ctls, B->ctl_stride, B->nprob, B->d_alldone, B->ws);
+    CK(cudaMemcpyAsync(B->h_alldone, B->d_alldone, sizeof(int), cudaMemcpyDeviceToHost, B->ws));
+    CK(cudaStreamSynchronize(B->ws));
+    if (*B->h_alldone || launched >= maxit) break;
+    int k = maxit - launched < chunk ? maxit - launched : chunk;
+    if ((rc = batch_launch_iterations(B, k))) return rc;
+    launched += k;
+  }
+  B->ctl_host.resize(B->ctl_stride * B->nprob);
+  CK(cudaMemcpy(B->ctl_host.data(), B->ctls, B->ctl_host.size(), cudaMemcpyDeviceToHost));
+  B->hist.assign(B->nprob, {});
+  int worst = BMG_OK;
+  for (int p = 0; p < B->nprob; ++p) {
+    const Ctl* c = (const Ctl*)(B->ctl_host.data() + (size_t)p * B->ctl_stride);
+    B->hist[p].assign(c->hist, c->hist + c->it + 1);
+    if (iters) iters[p] = c->it;
+    if (relres) relres[p] = c->hist[0] > 0 ? c->hist[c->it] / c->hist[0] : 0.0;
+    if (c->done == 3) worst = BMG_ENAN;
+    else if (c->done != 1 && worst == BMG_OK) worst = BMG_ENOTCONV;
+  }
+  if (worst == BMG_ENAN) return set_error(BMG_ENAN, "bmg_solve_batched: a residual norm is not finite");
+  if (worst == BMG_ENOTCONV) return set_error(BMG_ENOTCONV, "bmg_solve_batched: not every problem converged");
+  return BMG_OK;
+}
+
+int bmg_batched_history(const bmg_batch* B, int p, double* out, int cap) {
+  if (!B || p < 0 || p >= B->nprob) return set_error(BMG_EINVAL, "bmg_batched_history: bad argument");
+  if (p >= (int)B->hist.size()) return 0;
+  int cnt = (int)B->hist[p].size();
+  if (out)
+    for (int k = 0; k < cnt && k < cap; ++k) out[k] = B->hist[p][k];
+  return cnt;
+}
+
+int bmg_time_cycles_batched(bmg_batch* B, const double* const* rhs, double* const* x, int cycles, double* ms) {
+  if (!B || !rhs || !x || !ms || cycles < 1) return set_error(BMG_EINVAL, "bmg_time_cycles_batched: bad argument");
+  CounterScope cs(&B->launches);
+  int rc;
+  CK(cudaEventRecord(B->ev, B->user));
+  CK(cudaStreamWaitEvent(B->ws, B->ev, 0));
+  if ((rc = batch_reset(B, 0.0, cycles))) return rc;
+  if ((rc = batch_prepare(B, rhs, x))) return rc;
+  batch_initial(B);
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, B->ws));
+  if ((rc = batch_launch_iterations(B, cycles))) return rc;
+  CK(cudaEventRecord(b, B->ws));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t;
+  return BMG_OK;
+}
+
+long long bmg_batched_launch_count(const bmg_batch* B) { return B ? B->launches : 0; }
+
+int bmg_batched_tuned_cluster(const bmg_batch* B, int stage) {
+  if (!B || stage < 0 || stage > B->bmax) return set_error(BMG_EINVAL, "bmg_batched_tuned_cluster: bad stage");
+  return B->tuned_cl[stage];
+}
+
+void bmg_free_batched(bmg_batch* B) {
+  if (!B) return;
+  if (B->ws) cudaStreamSynchronize(B->ws);
+  for (auto* h : B->hs) bmg_free(h);
+  for (auto& st : B->stages)
+    for (auto& g : st) cudaFree(g.d);
+  cudaFree(B->d_top);
+  cudaFree(B->ctls);
+  cudaFree(B->d_alldone);
+  if (B->h_alldone) cudaFreeHost(B->h_alldone);
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->ev) cudaEventDestroy(B->ev);
+  if (B->ws) cudaStreamDestroy(B->ws);
+  delete B;
+}
+
+}  // extern "C"

@@ -1,0 +1,370 @@
+// Device bodies of the V-cycle kernels, shared by the single-problem kernels
+// (k_cycle.cu) and the batched kernels (k_batched.cu) so that both run the same
+// arithmetic.  A body takes its block coordinates explicitly; a batched kernel
+// picks its problem from another grid dimension and passes the rest through.
+//
+// T is the compute type (double or float); S the storage type of the
+// off-diagonal stencil planes (T, or bf16 under float).  Every row sum runs in
+// the order O, W, E, S, N, SW, NE, NW, SE with one rounding per operation.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bmg {
+namespace dev {
+
+namespace cg = cooperative_groups;
+
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_BLOCKS_MAX = 1024;
+constexpr int TXC = 32, TYC = 8;                      // coarse tile of residual + restriction
+constexpr int RFX = 2 * TXC + 1, RFY = 2 * TYC + 1;  // its fine block
+
+__device__ __forceinline__ bool stopped(const int* done) { return done != nullptr && *done != 0; }
+
+// s - sum over the listed neighbours of a(p,q) x_q (canonical order).
+template <typename T, typename S, bool NINE, bool WITH_O>
+__device__ __forceinline__ T row_residual(const StencilView<T, S>& v, const T* __restrict__ x, size_t p, T s) {
+  const int ld = v.ld;
+  if (WITH_O) s = rsub(s, rmul(v.O[p], x[p]));
+  s = rsub(s, rmul(cvt<T>(v.W[p]), x[p - 1]));
+  s = rsub(s, rmul(cvt<T>(v.W[p + 1]), x[p + 1]));
+  s = rsub(s, rmul(cvt<T>(v.S_[p]), x[p - ld]));
+  s = rsub(s, rmul(cvt<T>(v.S_[p + ld]), x[p + ld]));
+  if (NINE) {
+    s = rsub(s, rmul(cvt<T>(v.SW[p]), x[p - ld - 1]));
+    s = rsub(s, rmul(cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]));
+    s = rsub(s, rmul(cvt<T>(v.NW[p]), x[p + ld - 1]));
+    s = rsub(s, rmul(cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]));
+  }
+  return s;
+}
+
+// ---- Gauss-Seidel ------------------------------------------------------------------
+// One update: x_p = (f_p - sum_{q != p} a_pq x_q) * d_p, d_p = 1/a_pp (stored, or
+// formed here with the same correctly rounded quotient).
+template <typename T, typename S, bool NINE>
+__device__ __forceinline__ void gs_point(const StencilView<T, S>& v, const T* __restrict__ f, T* x, size_t p) {
+  T s = row_residual<T, S, NINE, false>(v, x, p, f[p]);
+  T d = v.D ? v.D[p] : rdiv(T(1), v.O[p]);
+  x[p] = rmul(s, d);
+}
+
+template <typename T>
+struct PairLoads {
+  T f, d, c[8], xs[8];
+};
+
+template <typename T, typename S>
+__device__ __forceinline__ void load_point(const StencilView<T, S>& v, const T* __restrict__ f, const T* x, size_t p,
+                                           PairLoads<T>& L, bool same_row_x) {
+  const int ld = v.ld;
+  L.f = f[p];
+  L.d = v.D ? v.D[p] : rdiv(T(1), v.O[p]);
+  L.c[0] = cvt<T>(v.W[p]);
+  L.c[1] = cvt<T>(v.W[p + 1]);
+  L.c[2] = cvt<T>(v.S_[p]);
+  L.c[3] = cvt<T>(v.S_[p + ld]);
+  L.c[4] = cvt<T>(v.SW[p]);
+  L.c[5] = cvt<T>(v.SW[p + ld + 1]);
+  L.c[6] = cvt<T>(v.NW[p]);
+  L.c[7] = cvt<T>(v.NW[p + 1 - ld]);
+  if (same_row_x) {
+    L.xs[0] = x[p - 1];
+    L.xs[1] = x[p + 1];
+  }
+  L.xs[2] = x[p - ld];
+  L.xs[3] = x[p + ld];
+  L.xs[4] = x[p - ld - 1];
+  L.xs[5] = x[p + ld + 1];
+  L.xs[6] = x[p + ld - 1];
+  L.xs[7] = x[p + 1 - ld];
+}
+
+// (f - sum_k c_k xs_k) * d in the canonical neighbour order W, E, S, N, SW, NE, NW, SE.
+template <typename T>
+__device__ __forceinline__ T update_from(const PairLoads<T>& L) {
+  T s = L.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s = rsub(s, rmul(L.c[k], L.xs[k]));
+  return rmul(s, L.d);
+}
+
+template <typename T>
+constexpr int rows_threads_max() { return sizeof(T) == 8 ? 512 : 1024; }
+
+// Four-colour sweep, half of it: the rows j with j % 2 == pj.  Rows j +- 1
+// belong to the other parity and are not written by this launch, so a row is
+// independent of every other row here.  Thread t owns the pair of points
+// (i0, i1) = (2t+1, 2t+2) of the row and issues every load of both updates at
+// once; it updates the odd-i point i0 (its same-row neighbours are even-i
+// points, still old), publishes the new value in shared memory, and after the
+// barrier updates the even-i point i1 with the new values at i1 - 1 (its own)
+// and i1 + 1 (the next thread's).  Launching pj = 1 then pj = 0 gives the colour
+// order (odd,odd), (even,odd), (odd,even), (even,even).  A row longer than one
+// CTA is split over a cluster of CL CTAs along x; the pair at a CTA's last
+// thread reads its right neighbour from the next CTA's shared memory after
+// cluster.sync().  `bx` is the CTA's x index; the caller has already returned
+// from CTAs whose problem is finished (uniformly over the cluster).
+template <typename T, typename S, int CL>
+__device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x, int pj,
+                                             int bx) {
+  __shared__ T xo[rows_threads_max<T>()];
+  const int n = v.n, ld = v.ld;
+  const int rowid = bx / CL, seg = bx % CL;
+  const int j = 2 * rowid + (pj ? 1 : 2);
+  const int t = seg * blockDim.x + threadIdx.x;
+  const int i0 = 2 * t + 1, i1 = i0 + 1;
+  const bool has0 = i0 <= n && j <= n, has1 = i1 < n && j <= n;
+  const size_t p0 = (size_t)j * ld + i0, p1 = p0 + 1;
+  PairLoads<T> A, B;
+  if (has0) load_point(v, f, x, p0, A, true);
+  if (has1) load_point(v, f, x, p1, B, false);
+  if (has0) {
+    T xn = update_from(A);
+    x[p0] = xn;
+    xo[threadIdx.x] = xn;
+    B.xs[0] = xn;
+  }
+  T right = T(0);
+  if constexpr (CL == 1) {
+    __syncthreads();
+    if (has1) right = xo[threadIdx.x + 1];
+  } else {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    if (has1) {
+      if (threadIdx.x + 1 < blockDim.x)
+        right = xo[threadIdx.x + 1];
+      else
+        right = *cluster.map_shared_rank(&xo[0], (int)cluster.block_rank() + 1);
+    }
+    cluster.sync();   // keep every CTA's shared memory alive until its neighbour has read it
+  }
+  if (has1) {
+    B.xs[1] = right;
+    x[p1] = update_from(B);
+  }
+}
+
+// Red-black half sweep for 5-point stencils: the points with (i + j) % 2 == c
+// (c = 0 red, c = 1 black), which share no coupling.  Thread grid: x over the
+// points of a row, y over rows.
+template <typename T, typename S>
+__device__ __forceinline__ void gs_checker_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x, int c,
+                                                int bx, int by) {
+  const int n = v.n;
+  const int j = by * blockDim.y + threadIdx.y + 1;
+  if (j > n) return;
+  const int i = 2 * (bx * blockDim.x + threadIdx.x) + 1 + ((j + 1 + c) & 1);
+  if (i > n) return;
+  gs_point<T, S, false>(v, f, x, (size_t)j * v.ld + i);
+}
+
+// ---- residual + restriction ------------------------------------------------------------
+// A CTA owns a TXC x TYC tile of coarse points; it forms the residual on the
+// (2 TXC + 1) x (2 TYC + 1) fine block under the tile in shared memory (each
+// fine residual once, shared columns/rows recomputed at tile seams), then each
+// thread applies the Fig. 2 restriction to one coarse point and zeroes the
+// coarse iterate there.
+template <typename T, typename S, bool NINE>
+__device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, const T* __restrict__ ci,
+                                                    const T* __restrict__ x, const T* __restrict__ f,
+                                                    T* __restrict__ fc, T* __restrict__ xc, int bx, int by) {
+  __shared__ T r[RFY][RFX + 1];
+  const int n = v.n, ld = v.ld, nc = (n - 1) / 2, ldc = nc + 2;
+  const int ic0 = bx * TXC + 1, jc0 = by * TYC + 1;
+  const int i0 = 2 * ic0 - 1, j0 = 2 * jc0 - 1;
+  const int tid = threadIdx.y * TXC + threadIdx.x;
+  for (int k = tid; k < RFX * RFY; k += TXC * TYC) {
+    int li = k % RFX, lj = k / RFX;
+    int i = i0 + li, j = j0 + lj;
+    T val = T(0);
+    if (i <= n && j <= n) {
+      size_t p = (size_t)j * ld + i;
+      val = row_residual<T, S, NINE, true>(v, x, p, f[p]);
+    }
+    r[lj][li] = val;
+  }
+  __syncthreads();
+  int ic = ic0 + threadIdx.x, jc = jc0 + threadIdx.y;
+  if (ic > nc || jc > nc) return;
+  const size_t psc = plane_size(nc);
+  const int li = 2 * threadIdx.x + 1, lj = 2 * threadIdx.y + 1;   // fine (2ic, 2jc) in the tile
+  auto w = [&](int k, int dic, int djc) { return ci[k * psc + (size_t)(jc + djc) * ldc + (ic + dic)]; };
+  T t = rmul(w(CI_LNE, 0, 0), r[lj - 1][li - 1]);
+  t = radd(t, rmul(w(CI_LA, 0, 0), r[lj - 1][li]));
+  t = radd(t, rmul(w(CI_LNW, 1, 0), r[lj - 1][li + 1]));
+  t = radd(t, rmul(w(CI_LR, 0, 0), r[lj][li - 1]));
+  t = radd(t, r[lj][li]);
+  t = radd(t, rmul(w(CI_LL, 1, 0), r[lj][li + 1]));
+  t = radd(t, rmul(w(CI_LSE, 0, 1), r[lj + 1][li - 1]));
+  t = radd(t, rmul(w(CI_LB, 0, 1), r[lj + 1][li]));
+  t = radd(t, rmul(w(CI_LSW, 1, 1), r[lj + 1][li + 1]));
+  size_t pc = (size_t)jc * ldc + ic;
+  fc[pc] = t;
+  if (xc) xc[pc] = T(0);
+}
+
+// ---- interpolation + correction ----------------------------------------------------------
+// One thread per coarse cell (ic, jc), 1..nc+1: its coincident, x-edge, y-edge
+// and centre fine points.  x + (P e)_p, the interpolated value formed first.
+template <typename T>
+__device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, const T* __restrict__ ec,
+                                            T* __restrict__ x, int ic, int jc) {
+  int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
+  if (ic < 1 || jc < 1 || ic > nc + 1 || jc > nc + 1) return;
+  size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
+  T e_sw = ec[pc - ldc - 1], e_se = ec[pc - ldc], e_nw = ec[pc - 1], e_ne = ec[pc];
+  size_t pf = (size_t)(2 * jc) * ld + 2 * ic;   // coincident fine point
+  if (ic <= nc && jc <= nc) x[pf] = radd(x[pf], e_ne);
+  if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
+    T t = rmul(ci[CI_LL * psc + pc], e_nw);
+    t = radd(t, rmul(ci[CI_LR * psc + pc], e_ne));
+    x[pf - 1] = radd(x[pf - 1], t);
+  }
+  if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
+    T t = rmul(ci[CI_LB * psc + pc], e_se);
+    t = radd(t, rmul(ci[CI_LA * psc + pc], e_ne));
+    x[pf - ld] = radd(x[pf - ld], t);
+  }
+  {                                               // centre (2ic-1, 2jc-1)
+    T t = rmul(ci[CI_LSW * psc + pc], e_sw);
+    t = radd(t, rmul(ci[CI_LSE * psc + pc], e_se));
+    t = radd(t, rmul(ci[CI_LNW * psc + pc], e_nw));
+    t = radd(t, rmul(ci[CI_LNE * psc + pc], e_ne));
+    x[pf - ld - 1] = radd(x[pf - ld - 1], t);
+  }
+}
+
+// ---- reductions in the canonical order -------------------------------------------------
+// Block b of G = min(n, 1024) handles rows j = 1 + b, 1 + b + G, ...; thread t
+// the columns i = 1 + t, 1 + t + 256, ...; each thread sums in that order,
+// then a fixed halving tree; the G block sums are reduced the same way.
+__device__ __forceinline__ double block_sum(double acc) {
+  __shared__ double red[NORM_THREADS];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = NORM_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double v = red[0];
+  __syncthreads();   // the buffer may be reused by a following block_sum
+  return v;
+}
+
+__host__ __device__ inline int norm_blocks(int n) { return n < NORM_BLOCKS_MAX ? n : NORM_BLOCKS_MAX; }
+
+template <typename T, typename S, bool NINE>
+__device__ __forceinline__ void residual_body(const StencilView<T, S>& v, const T* __restrict__ x,
+                                              const T* __restrict__ f, T* __restrict__ r,
+                                              double* __restrict__ partials, int b, int G) {
+  const int n = v.n, ld = v.ld;
+  double acc = 0.0;
+  for (int j = 1 + b; j <= n; j += G)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
+      size_t p = (size_t)j * ld + i;
+      T s = row_residual<T, S, NINE, true>(v, x, p, f[p]);
+      if (r) r[p] = s;
+      double d = (double)s;
+      acc = __dadd_rn(acc, __dmul_rn(d, d));
+    }
+  if (partials) {
+    double tot = block_sum(acc);
+    if (threadIdx.x == 0) partials[b] = tot;
+  }
+}
+
+__device__ __forceinline__ double scale_of(double rho) {
+  if (!(rho > 0.0) || !isfinite(rho)) return 1.0;
+  int e;
+  frexp(rho, &e);
+  return ldexp(1.0, e);
+}
+
+// One block: sum the partials in index order per thread, fixed tree, sqrt;
+// record the norm in ctl (phase 0 = initial residual, 1 = after a cycle).
+__device__ __forceinline__ void finalize_body(const double* __restrict__ partials, int np, Ctl* ctl, int phase,
+                                              double* out) {
+  if (phase == 1 && ctl && ctl->done) return;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < np; k += NORM_THREADS) acc = __dadd_rn(acc, partials[k]);
+  double tot = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  double rho = __dsqrt_rn(tot);
+  if (out) *out = rho;
+  if (!ctl) return;
+  if (phase == 0) {
+    ctl->it = 0;
+    ctl->hist[0] = rho;
+    ctl->done = !isfinite(rho) ? 3 : (rho == 0.0 ? 1 : 0);
+    if (ctl->done == 0 && ctl->maxit <= 0) ctl->done = 2;
+  } else {
+    int it = ctl->it + 1;
+    ctl->it = it;
+    ctl->hist[it] = rho;
+    if (!isfinite(rho)) ctl->done = 3;
+    else if (rho / ctl->hist[0] <= ctl->tol) ctl->done = 1;
+    else if (it >= ctl->maxit) ctl->done = 2;
+  }
+  ctl->scale_next = scale_of(rho);
+}
+
+// ---- coarsest solve: forward and back substitution (one thread) -------------------------
+template <typename T>
+__device__ __forceinline__ void coarse_solve_body(int n, const double* __restrict__ L, const T* __restrict__ f,
+                                                  T* __restrict__ x, double* __restrict__ y) {
+  if (threadIdx.x != 0) return;
+  int m = n * n, ld = n + 2;
+  for (int i = 0; i < m; ++i) {
+    double s = (double)f[(size_t)(i / n + 1) * ld + (i % n + 1)];
+    for (int k = 0; k < i; ++k) s = rsub(s, rmul(L[(size_t)i * m + k], y[k]));
+    y[i] = rdiv(s, L[(size_t)i * m + i]);
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(L[(size_t)k * m + i], y[k]));
+    y[i] = rdiv(s, L[(size_t)i * m + i]);
+  }
+  for (int i = 0; i < m; ++i) x[(size_t)(i / n + 1) * ld + (i % n + 1)] = (T)y[i];
+}
+
+// ---- iterative refinement ------------------------------------------------------------------
+__device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, const float* __restrict__ e32,
+                                               const Ctl* ctl, int i, int j) {
+  if (i < 1 || j < 1 || i > n || j > n) return;
+  size_t p = (size_t)j * (n + 2) + i;
+  x[p] = radd(x[p], rmul(ctl->scale_applied, (double)e32[p]));
+}
+
+// r = f - A x (FP64), r32 = fl32(r / scale_next), e32 = 0, partial sums of r^2.
+__device__ __forceinline__ void ir_residual_body(const StencilView<double, double>& v, bool nine,
+                                                 const double* __restrict__ x, const double* __restrict__ f,
+                                                 float* __restrict__ r32, float* __restrict__ e32,
+                                                 double* __restrict__ partials, Ctl* ctl, int b, int G) {
+  const int n = v.n, ld = v.ld;
+  const double s = ctl->scale_next;
+  const double inv = 1.0 / s;   // exact: s is a power of two
+  double acc = 0.0;
+  for (int j = 1 + b; j <= n; j += G)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
+      size_t p = (size_t)j * ld + i;
+      double rr = nine ? row_residual<double, double, true, true>(v, x, p, f[p])
+                       : row_residual<double, double, false, true>(v, x, p, f[p]);
+      r32[p] = __double2float_rn(rmul(rr, inv));
+      e32[p] = 0.0f;
+      acc = __dadd_rn(acc, __dmul_rn(rr, rr));
+    }
+  double tot = block_sum(acc);
+  if (threadIdx.x == 0) {
+    partials[b] = tot;
+    if (b == 0) ctl->scale_applied = s;
+  }
+}
+
+}  // namespace dev
+}  // namespace bmg

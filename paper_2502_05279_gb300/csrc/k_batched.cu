@@ -1,0 +1,207 @@
+// Batched V-cycle kernels: one launch per stage for many independent problems.
+// Stages are levels counted from the coarsest (all problems reach the same
+// coarsest size), so the problems of a stage share n and one grid shape; the
+// problem index is the last grid dimension.  The bodies are those of the
+// single-problem kernels (cycle_device.cuh), so every problem's arithmetic, and
+// with it its residual history, is the same as in a solo solve.
+#include "cycle_device.cuh"
+
+namespace bmg {
+
+using namespace dev;
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+template <typename T, typename S, int CL>
+__global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
+    k_gs_rows_b(const LevelDesc<T, S>* __restrict__ d, int pj) {
+  const LevelDesc<T, S> q = d[blockIdx.y];
+  if (stopped(q.done)) return;   // uniform over the cluster: its CTAs share blockIdx.y
+  gs_rows_body<T, S, CL>(q.v, q.f, q.x, pj, blockIdx.x);
+}
+
+template <typename T, typename S>
+__global__ void k_gs_checker_b(const LevelDesc<T, S>* __restrict__ d, int c) {
+  const LevelDesc<T, S> q = d[blockIdx.z];
+  if (stopped(q.done)) return;
+  gs_checker_body<T, S>(q.v, q.f, q.x, c, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, typename S, bool NINE>
+__global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T, S>* __restrict__ d) {
+  const LevelDesc<T, S> q = d[blockIdx.z];
+  if (stopped(q.done)) return;
+  resid_restrict_body<T, S, NINE>(q.v, q.ci, q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, typename S>
+__global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d) {
+  const LevelDesc<T, S> q = d[blockIdx.z];
+  if (stopped(q.done)) return;
+  interp_body<T>(q.v.n, q.ci, q.xc, q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
+                 blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
+template <typename T, typename S>
+__global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
+  const LevelDesc<T, S> q = d[blockIdx.x];
+  if (stopped(q.done)) return;
+  coarse_solve_body<T>(q.v.n, q.L, q.f, q.x, q.y);
+}
+
+// Top-level kernels: problems of different sizes in one grid; block b of a
+// problem runs only when b < G = min(n, 1024) of that problem, so every
+// problem keeps the reduction order of its solo solve.
+__global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __restrict__ d) {
+  const TopDesc q = d[blockIdx.y];
+  const int G = norm_blocks(q.v.n);
+  if (q.ctl->done || (int)blockIdx.x >= G) return;
+  if (q.kind == 9)
+    residual_body<double, double, true>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+  else
+    residual_body<double, double, false>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+}
+
+__global__ void __launch_bounds__(NORM_THREADS) k_finalize_b(const TopDesc* __restrict__ d, int phase) {
+  const TopDesc q = d[blockIdx.x];
+  finalize_body(q.partials, norm_blocks(q.v.n), q.ctl, phase, nullptr);
+}
+
+__global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
+  const TopDesc q = d[blockIdx.z];
+  if (q.ctl->done) return;
+  ir_update_body(q.v.n, q.x, q.e32, q.ctl, blockIdx.x * blockDim.x + threadIdx.x + 1,
+                 blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
+__global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* __restrict__ d) {
+  const TopDesc q = d[blockIdx.y];
+  const int G = norm_blocks(q.v.n);
+  if (q.ctl->done || (int)blockIdx.x >= G) return;
+  ir_residual_body(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
+}
+
+// 1 when every problem's control flag is set.
+__global__ void k_all_done(const char* __restrict__ ctls, size_t stride, int count, int* out) {
+  __shared__ int any_running;
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < count; p += blockDim.x)
+    if (((const Ctl*)(ctls + (size_t)p * stride))->done == 0) any_running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *out = any_running ? 0 : 1;
+}
+
+template <typename T, typename S, int CL>
+void rows_b(const LevelDesc<T, S>* d, int count, int n, int threads, cudaStream_t s) {
+  for (int pj = 1; pj >= 0; --pj) {
+    const int rows = pj ? (n + 1) / 2 : (n - 1) / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(rows * CL), (unsigned)count);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_gs_rows_b<T, S, CL>, d, pj);
+    count_launch();
+  }
+}
+
+}  // namespace
+
+// cl: cluster size of the row kernel (>= rows_cluster<T>(n); the autotuner may
+// pick a larger one, which splits each row over more, smaller CTAs).
+template <typename T, typename S>
+void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s) {
+  if (count <= 0) return;
+  if (kind == 9) {
+    const int threads = rows_threads(n, cl);
+    for (int k = 0; k < sweeps; ++k) {
+      switch (cl) {
+        case 1: rows_b<T, S, 1>(d, count, n, threads, s); break;
+        case 2: rows_b<T, S, 2>(d, count, n, threads, s); break;
+        case 4: rows_b<T, S, 4>(d, count, n, threads, s); break;
+        default: rows_b<T, S, 8>(d, count, n, threads, s); break;
+      }
+    }
+  } else {
+    dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY, count);
+    for (int k = 0; k < sweeps; ++k) {
+      k_gs_checker_b<T, S><<<g, dim3(BX, BY), 0, s>>>(d, 0);
+      count_launch();
+      k_gs_checker_b<T, S><<<g, dim3(BX, BY), 0, s>>>(d, 1);
+      count_launch();
+    }
+  }
+}
+
+template <typename T, typename S>
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s) {
+  if (count <= 0) return;
+  int nc = (n - 1) / 2;
+  dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC, count);
+  if (kind == 9)
+    k_resid_restrict_b<T, S, true><<<g, dim3(TXC, TYC), 0, s>>>(d);
+  else
+    k_resid_restrict_b<T, S, false><<<g, dim3(TXC, TYC), 0, s>>>(d);
+  count_launch();
+}
+
+template <typename T, typename S>
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s) {
+  if (count <= 0) return;
+  int nc = (n - 1) / 2;
+  k_interp_b<T, S><<<dim3((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d);
+  count_launch();
+}
+
+template <typename T, typename S>
+void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_coarse_b<T, S><<<count, 32, 0, s>>>(d);
+  count_launch();
+}
+
+void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
+  k_residual_b<<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+  count_launch();
+}
+
+void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s) {
+  k_finalize_b<<<count, NORM_THREADS, 0, s>>>(d, phase);
+  count_launch();
+}
+
+void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
+  k_ir_update_b<<<dim3((maxn + BX - 1) / BX, (maxn + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d);
+  count_launch();
+}
+
+void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
+  k_ir_residual_b<<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+  count_launch();
+}
+
+void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s) {
+  k_all_done<<<1, 256, 0, s>>>(ctls, stride, count, out);
+  count_launch();
+}
+
+#define BMG_INST_B(T, S)                                                                                 \
+  template void launch_gs_b<T, S>(const LevelDesc<T, S>*, int, int, int, int, int, cudaStream_t);       \
+  template void launch_resid_restrict_b<T, S>(const LevelDesc<T, S>*, int, int, int, cudaStream_t);     \
+  template void launch_interp_b<T, S>(const LevelDesc<T, S>*, int, int, cudaStream_t);                 \
+  template void launch_coarse_b<T, S>(const LevelDesc<T, S>*, int, cudaStream_t);
+BMG_INST_B(double, double)
+BMG_INST_B(float, float)
+BMG_INST_B(float, __nv_bfloat16)
+#undef BMG_INST_B
+
+}  // namespace bmg

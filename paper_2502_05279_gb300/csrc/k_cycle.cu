@@ -1,63 +1,31 @@
-// V-cycle kernels of the BoxMG solver (Fig. 1): Gauss-Seidel colour passes,
-// fused residual + restriction (Fig. 2), interpolation + correction, residual
-// norms with a fixed reduction order, the coarsest Cholesky solve and the
-// FP64 iterative-refinement steps around an FP32 cycle.
-//
-// T is the compute type (double or float); S the storage type of the
-// off-diagonal stencil planes (T, or bf16 under float).  Every row sum runs in
-// the order O, W, E, S, N, SW, NE, NW, SE with one rounding per operation.
-#include "common.cuh"
-#include "kernels.h"
+// V-cycle kernels of the BoxMG solver (Fig. 1), single problem: Gauss-Seidel
+// half sweeps, fused residual + restriction (Fig. 2), interpolation +
+// correction, residual norms with a fixed reduction order, the coarsest
+// Cholesky solve, FP64 iterative-refinement steps around an FP32 cycle and the
+// flexible-CG outer loop.  The arithmetic lives in cycle_device.cuh, shared with
+// the batched kernels.
+#include "cycle_device.cuh"
 
 namespace bmg {
+
+using namespace dev;
 
 namespace {
 
 constexpr int BX = 32, BY = 8;
-constexpr int NORM_THREADS = 256;
-constexpr int NORM_BLOCKS_MAX = 1024;
 
-__device__ __forceinline__ bool stopped(const int* done) { return done != nullptr && *done != 0; }
-
-// f - sum over the listed neighbours of a(p,q) x_q, starting from s.
-template <typename T, typename S, bool NINE, bool WITH_O>
-__device__ __forceinline__ T row_residual(const StencilView<T, S>& v, const T* __restrict__ x, size_t p, T s) {
-  const int ld = v.ld;
-  if (WITH_O) s = rsub(s, rmul(v.O[p], x[p]));
-  s = rsub(s, rmul(cvt<T>(v.W[p]), x[p - 1]));
-  s = rsub(s, rmul(cvt<T>(v.W[p + 1]), x[p + 1]));
-  s = rsub(s, rmul(cvt<T>(v.S_[p]), x[p - ld]));
-  s = rsub(s, rmul(cvt<T>(v.S_[p + ld]), x[p + ld]));
-  if (NINE) {
-    s = rsub(s, rmul(cvt<T>(v.SW[p]), x[p - ld - 1]));
-    s = rsub(s, rmul(cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]));
-    s = rsub(s, rmul(cvt<T>(v.NW[p]), x[p + ld - 1]));
-    s = rsub(s, rmul(cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]));
-  }
-  return s;
+template <typename T, typename S, int CL>
+__global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
+    k_gs_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, int pj, const int* done) {
+  if (stopped(done)) return;   // uniform over the grid: every CTA of a cluster leaves together
+  gs_rows_body<T, S, CL>(v, f, x, pj, blockIdx.x);
 }
 
-// ---- Gauss-Seidel: one colour (i % 2 == pi, j % 2 == pj) per launch ----------
-template <typename T, typename S, bool NINE>
-__global__ void k_gs_colour(StencilView<T, S> v, const T* __restrict__ f, T* x, int pi, int pj, const int* done) {
+template <typename T, typename S>
+__global__ void k_gs_checker(StencilView<T, S> v, const T* __restrict__ f, T* x, int c, const int* done) {
   if (stopped(done)) return;
-  int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (pi ? 1 : 2);
-  int j = 2 * (blockIdx.y * blockDim.y + threadIdx.y) + (pj ? 1 : 2);
-  if (i > v.n || j > v.n) return;
-  size_t p = (size_t)j * v.ld + i;
-  T s = row_residual<T, S, NINE, false>(v, x, p, f[p]);
-  T d = v.D ? v.D[p] : rdiv(T(1), v.O[p]);   // stored 1/a_pp, or the same quotient formed here
-  x[p] = rmul(s, d);
+  gs_checker_body<T, S>(v, f, x, c, blockIdx.x, blockIdx.y);
 }
-
-// ---- residual + restriction ---------------------------------------------------
-// A CTA owns a TXC x TYC tile of coarse points; it forms the residual on the
-// (2 TXC + 1) x (2 TYC + 1) fine block under the tile in shared memory (each
-// fine residual once, shared columns/rows recomputed at tile seams), then each
-// thread applies the Fig. 2 restriction to one coarse point and zeroes the
-// coarse iterate there.
-constexpr int TXC = 32, TYC = 8;
-constexpr int RFX = 2 * TXC + 1, RFY = 2 * TYC + 1;
 
 template <typename T, typename S, bool NINE>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
@@ -65,89 +33,14 @@ __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v
                                                             T* __restrict__ fc, T* __restrict__ xc,
                                                             const int* done) {
   if (stopped(done)) return;
-  __shared__ T r[RFY][RFX + 1];
-  const int n = v.n, ld = v.ld, nc = (n - 1) / 2, ldc = nc + 2;
-  const int ic0 = blockIdx.x * TXC + 1, jc0 = blockIdx.y * TYC + 1;
-  const int i0 = 2 * ic0 - 1, j0 = 2 * jc0 - 1;
-  const int tid = threadIdx.y * TXC + threadIdx.x;
-  for (int k = tid; k < RFX * RFY; k += TXC * TYC) {
-    int li = k % RFX, lj = k / RFX;
-    int i = i0 + li, j = j0 + lj;
-    T val = T(0);
-    if (i <= n && j <= n) {
-      size_t p = (size_t)j * ld + i;
-      val = row_residual<T, S, NINE, true>(v, x, p, f[p]);
-    }
-    r[lj][li] = val;
-  }
-  __syncthreads();
-  int ic = ic0 + threadIdx.x, jc = jc0 + threadIdx.y;
-  if (ic > nc || jc > nc) return;
-  const size_t psc = plane_size(nc);
-  const int li = 2 * threadIdx.x + 1, lj = 2 * threadIdx.y + 1;   // fine (2ic, 2jc) in the tile
-  auto w = [&](int k, int dic, int djc) { return ci[k * psc + (size_t)(jc + djc) * ldc + (ic + dic)]; };
-  T t = rmul(w(CI_LNE, 0, 0), r[lj - 1][li - 1]);
-  t = radd(t, rmul(w(CI_LA, 0, 0), r[lj - 1][li]));
-  t = radd(t, rmul(w(CI_LNW, 1, 0), r[lj - 1][li + 1]));
-  t = radd(t, rmul(w(CI_LR, 0, 0), r[lj][li - 1]));
-  t = radd(t, r[lj][li]);
-  t = radd(t, rmul(w(CI_LL, 1, 0), r[lj][li + 1]));
-  t = radd(t, rmul(w(CI_LSE, 0, 1), r[lj + 1][li - 1]));
-  t = radd(t, rmul(w(CI_LB, 0, 1), r[lj + 1][li]));
-  t = radd(t, rmul(w(CI_LSW, 1, 1), r[lj + 1][li + 1]));
-  size_t pc = (size_t)jc * ldc + ic;
-  fc[pc] = t;
-  if (xc) xc[pc] = T(0);
+  resid_restrict_body<T, S, NINE>(v, ci, x, f, fc, xc, blockIdx.x, blockIdx.y);
 }
 
-// ---- interpolation + correction -------------------------------------------------
-// One thread per coarse cell (ic, jc), 1..nc+1: its coincident, x-edge, y-edge
-// and centre fine points.  x + (P e)_p, the interpolated value formed first.
 template <typename T>
 __global__ void k_interp_correct(int n, const T* __restrict__ ci, const T* __restrict__ ec, T* __restrict__ x,
                                  const int* done) {
   if (stopped(done)) return;
-  int ic = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  int jc = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
-  if (ic > nc + 1 || jc > nc + 1) return;
-  size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
-  T e_sw = ec[pc - ldc - 1], e_se = ec[pc - ldc], e_nw = ec[pc - 1], e_ne = ec[pc];
-  size_t pf = (size_t)(2 * jc) * ld + 2 * ic;   // coincident fine point
-  if (ic <= nc && jc <= nc) x[pf] = radd(x[pf], e_ne);
-  if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
-    T t = rmul(ci[CI_LL * psc + pc], e_nw);
-    t = radd(t, rmul(ci[CI_LR * psc + pc], e_ne));
-    x[pf - 1] = radd(x[pf - 1], t);
-  }
-  if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
-    T t = rmul(ci[CI_LB * psc + pc], e_se);
-    t = radd(t, rmul(ci[CI_LA * psc + pc], e_ne));
-    x[pf - ld] = radd(x[pf - ld], t);
-  }
-  {                                               // centre (2ic-1, 2jc-1)
-    T t = rmul(ci[CI_LSW * psc + pc], e_sw);
-    t = radd(t, rmul(ci[CI_LSE * psc + pc], e_se));
-    t = radd(t, rmul(ci[CI_LNW * psc + pc], e_nw));
-    t = radd(t, rmul(ci[CI_LNE * psc + pc], e_ne));
-    x[pf - ld - 1] = radd(x[pf - ld - 1], t);
-  }
-}
-
-// ---- residual with deterministic partial sums of r^2 -----------------------------
-// Block b handles rows j = 1 + b, 1 + b + G, ... (G = gridDim.x); thread t the
-// columns i = 1 + t, 1 + t + 256, ...; each thread sums in that order, then a
-// fixed shared-memory tree.  The result depends only on n and G.
-template <typename T>
-__device__ __forceinline__ double block_sum(double acc) {
-  __shared__ double red[NORM_THREADS];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = NORM_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
-    __syncthreads();
-  }
-  return red[0];
+  interp_body<T>(n, ci, ec, x, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
 template <typename T, typename S, bool NINE>
@@ -155,20 +48,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_residual(StencilView<T, S> v, 
                                                            const T* __restrict__ f, T* __restrict__ r,
                                                            double* __restrict__ partials, const int* done) {
   if (stopped(done)) return;
-  const int n = v.n, ld = v.ld;
-  double acc = 0.0;
-  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
-    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
-      size_t p = (size_t)j * ld + i;
-      T s = row_residual<T, S, NINE, true>(v, x, p, f[p]);
-      if (r) r[p] = s;
-      double d = (double)s;
-      acc = __dadd_rn(acc, __dmul_rn(d, d));
-    }
-  if (partials) {
-    double tot = block_sum<T>(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-  }
+  residual_body<T, S, NINE>(v, x, f, r, partials, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_zero_ring(int n, double* r) {
@@ -181,68 +61,22 @@ __global__ void k_zero_ring(int n, double* r) {
   r[(size_t)k * ld + n + 1] = 0.0;
 }
 
-__device__ __forceinline__ double scale_of(double rho) {
-  if (!(rho > 0.0) || !isfinite(rho)) return 1.0;
-  int e;
-  frexp(rho, &e);
-  return ldexp(1.0, e);
-}
-
-// One block: sum the partials in index order per thread, fixed tree, sqrt.
 __global__ void __launch_bounds__(NORM_THREADS) k_norm_finalize(const double* __restrict__ partials, int np,
                                                                 Ctl* ctl, int phase, double* out) {
-  if (phase == 1 && ctl && ctl->done) return;
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < np; k += NORM_THREADS) acc = __dadd_rn(acc, partials[k]);
-  double tot = block_sum<double>(acc);
-  if (threadIdx.x != 0) return;
-  double rho = __dsqrt_rn(tot);
-  if (out) *out = rho;
-  if (!ctl) return;
-  if (phase == 0) {
-    ctl->it = 0;
-    ctl->hist[0] = rho;
-    ctl->done = !isfinite(rho) ? 3 : (rho == 0.0 ? 1 : 0);
-    if (ctl->done == 0 && ctl->maxit <= 0) ctl->done = 2;
-  } else {
-    int it = ctl->it + 1;
-    ctl->it = it;
-    ctl->hist[it] = rho;
-    if (!isfinite(rho)) ctl->done = 3;
-    else if (rho / ctl->hist[0] <= ctl->tol) ctl->done = 1;
-    else if (it >= ctl->maxit) ctl->done = 2;
-  }
-  ctl->scale_next = scale_of(rho);
+  finalize_body(partials, np, ctl, phase, out);
 }
 
-// ---- coarsest solve: forward and back substitution (one thread) ---------------
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ L, const T* __restrict__ f, T* __restrict__ x,
                                double* __restrict__ y, const int* done) {
   if (stopped(done)) return;
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int m = n * n, ld = n + 2;
-  for (int i = 0; i < m; ++i) {
-    double s = (double)f[(size_t)(i / n + 1) * ld + (i % n + 1)];
-    for (int k = 0; k < i; ++k) s = rsub(s, rmul(L[(size_t)i * m + k], y[k]));
-    y[i] = rdiv(s, L[(size_t)i * m + i]);
-  }
-  for (int i = m - 1; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(L[(size_t)k * m + i], y[k]));
-    y[i] = rdiv(s, L[(size_t)i * m + i]);
-  }
-  for (int i = 0; i < m; ++i) x[(size_t)(i / n + 1) * ld + (i % n + 1)] = (T)y[i];
+  if (blockIdx.x != 0) return;
+  coarse_solve_body<T>(n, L, f, x, y);
 }
 
-// ---- iterative refinement ----------------------------------------------------------
 __global__ void k_ir_update(int n, double* __restrict__ x, const float* __restrict__ e32, const Ctl* ctl) {
   if (ctl->done) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > n || j > n) return;
-  size_t p = (size_t)j * (n + 2) + i;
-  x[p] = radd(x[p], rmul(ctl->scale_applied, (double)e32[p]));
+  ir_update_body(n, x, e32, ctl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual(StencilView<double, double> v, int nine,
@@ -251,24 +85,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual(StencilView<double
                                                               float* __restrict__ e32, double* __restrict__ partials,
                                                               Ctl* ctl) {
   if (ctl->done) return;
-  const int n = v.n, ld = v.ld;
-  const double s = ctl->scale_next;
-  const double inv = 1.0 / s;   // exact: s is a power of two
-  double acc = 0.0;
-  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
-    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
-      size_t p = (size_t)j * ld + i;
-      double rr = nine ? row_residual<double, double, true, true>(v, x, p, f[p])
-                       : row_residual<double, double, false, true>(v, x, p, f[p]);
-      r32[p] = __double2float_rn(rmul(rr, inv));
-      e32[p] = 0.0f;
-      acc = __dadd_rn(acc, __dmul_rn(rr, rr));
-    }
-  double tot = block_sum<double>(acc);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = tot;
-    if (blockIdx.x == 0) ctl->scale_applied = s;
-  }
+  ir_residual_body(v, nine != 0, x, f, r32, e32, partials, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---- FP64 throughput probe ---------------------------------------------------------
@@ -284,28 +101,67 @@ __global__ void k_dp_probe(double* out, int iters, double a, double b) {
 
 dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
 
-int norm_blocks(int n) { return n < NORM_BLOCKS_MAX ? n : NORM_BLOCKS_MAX; }
-
 }  // namespace
 
 int norm_partials_max() { return NORM_BLOCKS_MAX; }
 
+// Cluster launch of k_gs_rows: grid = rows * CL CTAs, clusters of CL along x, so
+// cluster rank = blockIdx.x % CL and the CTAs of one row form one cluster.
+template <typename T, typename S, int CL>
+void launch_rows_half(const StencilView<T, S>& v, const T* f, T* x, int pj, int rows, int threads, const int* done,
+                      cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(rows * CL));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k_gs_rows<T, S, CL>, v, f, x, pj, done);
+  count_launch();
+}
+
+// Smallest cluster size (1, 2, 4, 8) whose CTAs cover the (n+1)/2 pairs of a row.
+template <typename T>
+int rows_cluster(int n) {
+  const int pairs = (n + 1) / 2;
+  int cl = 1;
+  while (cl * rows_threads_max<T>() < pairs) cl *= 2;
+  return cl;
+}
+
+int rows_threads(int n, int cl) {
+  int threads = ((n + 1) / 2 + cl - 1) / cl;
+  return (threads + 31) / 32 * 32;
+}
+
 template <typename T, typename S>
 void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s) {
   const int n = v.n;
-  auto pass = [&](int pi, int pj) {
-    int ni = pi ? (n + 1) / 2 : (n - 1) / 2, nj = pj ? (n + 1) / 2 : (n - 1) / 2;
-    if (kind == 9)
-      k_gs_colour<T, S, true><<<grid2(ni, nj), dim3(BX, BY), 0, s>>>(v, f, x, pi, pj, done);
-    else
-      k_gs_colour<T, S, false><<<grid2(ni, nj), dim3(BX, BY), 0, s>>>(v, f, x, pi, pj, done);
-    count_launch();
-  };
-  for (int k = 0; k < sweeps; ++k) {
-    if (kind == 9) {
-      pass(1, 1); pass(0, 1); pass(1, 0); pass(0, 0);
-    } else {
-      pass(1, 1); pass(0, 0); pass(0, 1); pass(1, 0);
+  if (kind == 9) {
+    const int cl = rows_cluster<T>(n), threads = rows_threads(n, cl);
+    for (int k = 0; k < sweeps; ++k)
+      for (int pj = 1; pj >= 0; --pj) {
+        const int rows = pj ? (n + 1) / 2 : (n - 1) / 2;
+        switch (cl) {
+          case 1: launch_rows_half<T, S, 1>(v, f, x, pj, rows, threads, done, s); break;
+          case 2: launch_rows_half<T, S, 2>(v, f, x, pj, rows, threads, done, s); break;
+          case 4: launch_rows_half<T, S, 4>(v, f, x, pj, rows, threads, done, s); break;
+          default: launch_rows_half<T, S, 8>(v, f, x, pj, rows, threads, done, s); break;
+        }
+      }
+  } else {
+    dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY);
+    for (int k = 0; k < sweeps; ++k) {
+      k_gs_checker<T, S><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 0, done);
+      count_launch();
+      k_gs_checker<T, S><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 1, done);
+      count_launch();
     }
   }
 }
@@ -343,7 +199,7 @@ int launch_residual(const StencilView<T, S>& v, int kind, const T* x, const T* f
 
 template <typename T>
 void launch_coarse_solve(int n, const double* L, const T* f, T* x, double* y, const int* done, cudaStream_t s) {
-  k_coarse_solve<T><<<1, 1, 0, s>>>(n, L, f, x, y, done);
+  k_coarse_solve<T><<<1, 32, 0, s>>>(n, L, f, x, y, done);
   count_launch();
 }
 
@@ -411,6 +267,8 @@ template void launch_coarse_solve<double>(int, const double*, const double*, dou
                                           cudaStream_t);
 template void launch_coarse_solve<float>(int, const double*, const float*, float*, double*, const int*,
                                          cudaStream_t);
+template int rows_cluster<double>(int);
+template int rows_cluster<float>(int);
 
 }  // namespace bmg
 
@@ -420,7 +278,10 @@ template void launch_coarse_solve<float>(int, const double*, const float*, float
 //   q = A p; alpha = (p.r)/(p.q); x += alpha p; r -= alpha q.
 // Every inner product uses the reduction order of k_residual / k_norm_finalize.
 namespace bmg {
+using namespace dev;
 namespace {
+
+constexpr int FBX = 32, FBY = 8;
 
 __device__ __forceinline__ double zval(const double* z, const float* z32, double s, size_t p) {
   return z32 ? rmul(s, (double)z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
@@ -432,7 +293,7 @@ __device__ __forceinline__ void ordered_partial(int n, int ld, double* partials,
   double acc = 0.0;
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) acc = __dadd_rn(acc, term((size_t)j * ld + i));
-  double tot = block_sum<double>(acc);
+  double tot = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
@@ -447,7 +308,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __
 __device__ __forceinline__ double reduce_partials(const double* partials, int np) {
   double acc = 0.0;
   for (int k = threadIdx.x; k < np; k += NORM_THREADS) acc = __dadd_rn(acc, partials[k]);
-  return block_sum<double>(acc);
+  return block_sum(acc);
 }
 
 // slot 0: zq; slot 1: pq and pr (second partial array right after the first)
@@ -510,9 +371,9 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double,
       apq = __dadd_rn(apq, rmul(pv[p], acc));
       apr = __dadd_rn(apr, rmul(pv[p], r[p]));
     }
-  double t1 = block_sum<double>(apq);
+  double t1 = block_sum(apq);
   __syncthreads();
-  double t2 = block_sum<double>(apr);
+  double t2 = block_sum(apr);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = t1;
     partials[NORM_BLOCKS_MAX + blockIdx.x] = t2;
@@ -546,7 +407,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
       }
       acc = __dadd_rn(acc, rmul(rr, rr));
     }
-  double tot = block_sum<double>(acc);
+  double tot = block_sum(acc);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = tot;
     if (blockIdx.x == 0) {
@@ -581,7 +442,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
       }
       acc = __dadd_rn(acc, rmul(rr, rr));
     }
-  double tot = block_sum<double>(acc);
+  double tot = block_sum(acc);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = tot;
     if (blockIdx.x == 0) {
@@ -615,7 +476,7 @@ void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, 
   count_launch();
   k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 0);
   count_launch();
-  k_fcg_direction<<<grid2(n, n), dim3(BX, BY), 0, s>>>(n, z, z32, pv, c);
+  k_fcg_direction<<<dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s>>>(n, z, z32, pv, c);
   count_launch();
   if (mark) mark(mark_arg, 1);
   k_fcg_matvec<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, pv, r, q, partials, c);

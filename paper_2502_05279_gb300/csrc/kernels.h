@@ -74,3 +74,53 @@ void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, 
 double measure_fp64_rate(cudaStream_t s);
 
 }  // namespace bmg
+
+// ---- batched (k_batched.cu) -----------------------------------------------------------
+// Many independent problems, one launch per stage.  A stage is a level counted
+// from the coarsest, so every problem in it has the same size n; each CTA reads
+// its problem's descriptor (device array) from another grid dimension.
+namespace bmg {
+
+template <typename T, typename S>
+struct LevelDesc {
+  StencilView<T, S> v;
+  const T* ci;        // weights toward the next coarser level (NULL at the coarsest)
+  T* x;               // this level's iterate and right-hand side
+  const T* f;
+  T* xc;              // next coarser level's iterate and right-hand side
+  T* fc;
+  const int* done;    // the problem's control flag
+  const double* L;    // coarsest level: Cholesky factor and substitution workspace
+  double* y;
+};
+
+// A problem's finest level, for the FP64 outer loop.
+struct TopDesc {
+  StencilView<double, double> v;
+  int kind;
+  double* x;
+  const double* f;
+  float* r32;         // mixed precision: level-0 FP32 right-hand side and iterate
+  float* e32;
+  double* partials;
+  Ctl* ctl;
+};
+
+template <typename T, typename S>
+void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s);
+template <typename T, typename S>
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s);
+template <typename T, typename S>
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s);
+template <typename T, typename S>
+void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s);
+void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
+void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s);
+void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
+void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
+void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s);
+template <typename T>
+int rows_cluster(int n);
+int rows_threads(int n, int cl);
+
+}  // namespace bmg

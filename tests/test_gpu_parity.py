@@ -301,3 +301,62 @@ def test_fcg_high_contrast_converges_where_cycles_stall(bmg):
     levels = bx.setup(kind, planes)
     xw, hw = bx.solve_fcg(levels, f, tol=1e-8, maxit=300)
     assert it == len(hw) - 1 and np.array_equal(host(x), xw)
+
+
+# ---- batched solves -----------------------------------------------------------------
+
+def batch_problems(sizes, std=1.0):
+    out = []
+    for b, n in enumerate(sizes):
+        k = w.lognormal_cells(n, std, 8.0, 20000 + 2 * b)
+        out.append((9, w.fe9_from_cells(k), w.rhs_uniform(n, 20001 + 2 * b)))
+    return out
+
+
+@pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batched_matches_oracle_per_problem(bmg, precision, nbf, graph):
+    """Uneven sizes (several problems per size, sizes from 3 to 255, ragged
+    tiles), every problem's iterate and history equal its oracle solve."""
+    sizes = [63, 255, 7, 127, 63, 3, 255, 31, 15, 127, 63]
+    probs = batch_problems(sizes)
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision=precision, use_graph=graph)
+    xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-9, maxit=100)
+    assert ok
+    for k, (kind, planes, f) in enumerate(probs):
+        levels = bx.setup(kind, planes)
+        if precision == "fp64":
+            xw, hw = bx.solve(levels, f, tol=1e-9, maxit=100)
+        else:
+            xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-9, maxit=100)
+        assert its[k] == len(hw) - 1, k
+        assert np.array_equal(bx.at(host(xs[k]), 0, 0), bx.at(xw, 0, 0)), k
+        check_history(B.history(k), hw)
+    B.close()
+
+
+def test_batched_equals_solo_solve(bmg):
+    sizes = [127, 255, 63]
+    probs = batch_problems(sizes, std=2.0)
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32")
+    xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-9, maxit=200)
+    for k, (kind, planes, f) in enumerate(probs):
+        h = bmg.Hierarchy(kind, dev(planes), precision="fp32")
+        x, it, rr, okk = h.solve(dev(f), tol=1e-9, maxit=200)
+        assert it == its[k] and torch.equal(x, xs[k]) and h.history() == B.history(k)
+        h.close()
+
+
+def test_batched_time_cycles_and_tuner(bmg):
+    probs = batch_problems([255, 255, 511, 127])
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32")
+    rhs = [dev(p[2]) for p in probs]
+    xs = [torch.zeros_like(r) for r in rhs]
+    ms = B.time_cycles(rhs, xs, 3)
+    assert ms > 0
+    # stages of n >= 127 were tuned to an admissible cluster size
+    for stage in range(1, 8):
+        cl = B.tuned_cluster(stage)
+        assert cl in (0, 1, 2, 4, 8)
+    assert B.tuned_cluster(6) in (1, 2, 4, 8)   # n = 255
+    B.close()
