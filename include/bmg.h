@@ -78,7 +78,9 @@ typedef struct {
 
 typedef struct {
   int precision;        /* BMG_FP64 (default), BMG_FP32_IR or BMG_BF16_IR */
-  int interp;           /* BMG_INTERP_DENDY (default) */
+  int interp;           /* BMG_INTERP_DENDY (default), or BMG_INTERP_LEARNED: level 0 uses the
+                           network `mlp`; setup also builds the Dendy hierarchy, measures the
+                           V-cycle factor of both and keeps the better (Dendy is the fallback) */
   int coarsest;         /* coarsest level size, 2^m - 1 >= 3 (0 = 3) */
   int nu1, nu2;         /* pre- and post-smoothing sweeps (0,0 = 2,1) */
   int inner_cycles;     /* FP32 V-cycles per refinement step (0 = 1) */
@@ -86,6 +88,7 @@ typedef struct {
   int use_graph;        /* 1 = replay one captured CUDA graph per cycle (default), 0 = plain launches */
   int krylov;           /* BMG_KRYLOV_NONE (default): stationary V-cycle iteration;
                            BMG_KRYLOV_FCG: flexible CG with one cycle as preconditioner */
+  const void* mlp;      /* bmg_mlp* for interp = BMG_INTERP_LEARNED, else NULL */
   void* stream;         /* cudaStream_t for setup and every later call on the hierarchy */
 } bmg_opts;
 
@@ -200,6 +203,45 @@ long long bmg_batched_launch_count(const bmg_batch* b);
 int bmg_batched_tuned_cluster(const bmg_batch* b, int stage);
 
 void bmg_free_batched(bmg_batch* b);   /* NULL is a no-op */
+
+/* ---- learned interpolation ----------------------------------------------------
+ * An extension, not in the paper: an 18-64-64-4 GELU network maps the 3x3
+ * fine-stencil neighbourhood of each coarse point (features (a_W + a_E)/a_O and
+ * (a_S + a_N)/a_O at each of the 9 points) to four logits, one per edge fine
+ * neighbour.  An edge point between coarse points c1, c2 keeps Dendy's total
+ * weight S_D = -(col_1 + col_2)/D and splits it as w_k = S_D u_k/(u_1 + u_2),
+ * u_k = -col_k exp(logit of c_k); centre points use Dendy's centre formula.
+ * Zero logits give Dendy's weights.  Parameters: MLP_PARAMS = 5636 floats,
+ * W1 (18x64), b1, W2 (64x64), b2, W3 (64x4), b3, row-major (input index first).
+ * Training loss over K test vectors v_k: L = (1/K) sum_k E_k / Eref_k,
+ * E_k = ||v_k - P R v_k||_A^2 (R: values at coarse points). */
+typedef struct bmg_mlp bmg_mlp;
+int bmg_mlp_create(bmg_mlp** out);
+int bmg_mlp_set_params(bmg_mlp* m, const float* host, int count);
+int bmg_mlp_get_params(const bmg_mlp* m, float* host, int count);
+/* One loss and gradient evaluation on one problem (FP32 network, FP64 weights
+ * and loss): coef 5 planes (n+2)^2 (ghost couplings zero), vecs K planes
+ * (n+2)^2 (device), eref K host values (NULL: loss normalised by the weights of
+ * zero logits, which then also come back in eref_out if given).  loss: host.
+ * grad: host array of MLP_PARAMS floats or NULL; the gradient also stays on the
+ * device for bmg_mlp_adam. */
+int bmg_mlp_loss_grad(bmg_mlp* m, int n, const double* coef, int K, const double* vecs, const double* eref,
+                      double* loss, float* grad, double* eref_out, void* stream);
+/* Adam step (beta 0.9, 0.999, eps 1e-8) with the last gradient. */
+int bmg_mlp_adam(bmg_mlp* m, float lr, void* stream);
+/* Logits of every interior coarse point, row-major (jc outer), 4 per point,
+ * from the BF16 tensor-core inference kernel: delta device floats (n_c^2 * 4). */
+int bmg_mlp_infer(const bmg_mlp* m, int n, const double* coef, float* delta, void* stream);
+/* Interpolation weights (8 planes (n_c+2)^2, FP64) from logits delta. */
+int bmg_learned_interp(int n, const double* coef, const float* delta, double* ci, void* stream);
+/* Which interpolation the hierarchy kept at level 0 (BMG_INTERP_*), and the
+ * measured V-cycle factors of the learned and the Dendy hierarchy (0 if not
+ * measured). */
+int bmg_interp_info(const bmg_hierarchy* h, int* used, double* factor_learned, double* factor_dendy);
+/* SplitMix64 uniform[-1,1) values on the interior of an (n+2)^2 device array
+ * (counter form, stream `seed`, interior point k = (j-1) n + (i-1)). */
+int bmg_fill_uniform(int n, unsigned long long seed, double* x, void* stream);
+void bmg_mlp_free(bmg_mlp* m);
 
 /* ---- single steps, for testing and composition -------------------------
  * Stateless: every pointer is caller-owned device memory in the layouts above;

@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -85,6 +85,16 @@ _sig = {
     "bmg_batched_tuned_cluster": (I, [P, I]),
     "bmg_free_batched": (None, [P]),
     "bmg_residual_noalloc": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
+    "bmg_mlp_create": (I, [ctypes.POINTER(P)]),
+    "bmg_mlp_set_params": (I, [P, P, I]),
+    "bmg_mlp_get_params": (I, [P, P, I]),
+    "bmg_mlp_loss_grad": (I, [P, I, P, I, P, P, ctypes.POINTER(D), P, P, P]),
+    "bmg_mlp_adam": (I, [P, ctypes.c_float, P]),
+    "bmg_mlp_infer": (I, [P, I, P, P, P]),
+    "bmg_learned_interp": (I, [I, P, P, P, P]),
+    "bmg_interp_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
+    "bmg_fill_uniform": (I, [I, ctypes.c_ulonglong, P, P]),
+    "bmg_mlp_free": (None, [P]),
     "bmg_profile": (I, [P, P, P, I, P, I]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -120,12 +130,12 @@ class Hierarchy:
 
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
-                 use_graph: bool = True, krylov: str = "none"):
+                 use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None):
         n = _n_of(coef)
         self.n, self.kind, self.precision = n, kind, precision
         st = Stencil(kind, _ptr(coef, name="coef"))
-        o = Opts(_PREC[precision], 0, coarsest, nu1, nu2, inner_cycles, bf16_levels, int(use_graph),
-                 _KRYLOV[krylov], _stream())
+        o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
+                 int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream())
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -183,6 +193,12 @@ class Hierarchy:
         _check(lib.bmg_inner_cycle(self._h, _ptr(r32, torch.float32, "r32"), _ptr(e, torch.float32, "e32")))
         return e
 
+    def interp_info(self):
+        """(kept interpolation: "learned" or "dendy", learned factor, Dendy factor)."""
+        used, fl, fd = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(lib.bmg_interp_info(self._h, ctypes.byref(used), ctypes.byref(fl), ctypes.byref(fd)))
+        return ("learned" if used.value == 1 else "dendy"), fl.value, fd.value
+
     @property
     def launch_count(self) -> int:
         return lib.bmg_launch_count(self._h)
@@ -211,7 +227,7 @@ class Batch:
         nprob = len(coefs)
         sts = (Stencil * nprob)(*[Stencil(kind, _ptr(c, name="coef")) for c in coefs])
         ns = (ctypes.c_int * nprob)(*self.ns)
-        o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, _stream())
+        o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, None, _stream())
         h = ctypes.c_void_p()
         _check(lib.bmg_setup_batched(nprob, sts, ns, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -259,6 +275,82 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+MLP_PARAMS = 18 * 64 + 64 + 64 * 64 + 64 + 64 * 4 + 4
+
+
+class Mlp:
+    """The learned-interpolation network on the device (bmg_mlp_*)."""
+
+    def __init__(self, params=None):
+        h = ctypes.c_void_p()
+        _check(lib.bmg_mlp_create(ctypes.byref(h)))
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == MLP_PARAMS
+        _check(lib.bmg_mlp_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p), MLP_PARAMS))
+
+    def params(self):
+        import numpy as np
+        a = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib.bmg_mlp_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p), MLP_PARAMS))
+        return a
+
+    def loss_grad(self, coef, vecs, eref=None, want_grad=True):
+        """(loss, gradient (numpy float32) or None, eref) on one problem; vecs: (K, n+2, n+2) CUDA float64."""
+        import numpy as np
+        n = _n_of(coef)
+        K = vecs.shape[0]
+        loss = ctypes.c_double(0.0)
+        g = np.empty(MLP_PARAMS, dtype=np.float32) if want_grad else None
+        er_in = None if eref is None else np.ascontiguousarray(eref, dtype=np.float64)
+        er_out = np.empty(K, dtype=np.float64)
+        _check(lib.bmg_mlp_loss_grad(self._h, n, _ptr(coef, name="coef"), K, _ptr(vecs, name="vecs"),
+                                     None if er_in is None else er_in.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(loss), None if g is None else g.ctypes.data_as(ctypes.c_void_p),
+                                     er_out.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return loss.value, g, (er_in if er_in is not None else er_out)
+
+    def adam(self, lr: float):
+        _check(lib.bmg_mlp_adam(self._h, ctypes.c_float(lr), _stream()))
+
+    def infer(self, coef):
+        n = _n_of(coef)
+        nc = (n - 1) // 2
+        out = torch.empty((nc * nc, 4), dtype=torch.float32, device=coef.device)
+        _check(lib.bmg_mlp_infer(self._h, n, _ptr(coef, name="coef"), _ptr(out, torch.float32, "delta"), _stream()))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bmg_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learned_interp(coef, delta):
+    n = _n_of(coef)
+    nc = (n - 1) // 2
+    ci = torch.empty((8, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
+    _check(lib.bmg_learned_interp(n, _ptr(coef), _ptr(delta, torch.float32, "delta"), _ptr(ci), _stream()))
+    return ci
+
+
+def fill_uniform(n: int, seed: int, device="cuda"):
+    x = torch.zeros((n + 2, n + 2), dtype=torch.float64, device=device)
+    _check(lib.bmg_fill_uniform(n, seed, _ptr(x), _stream()))
+    return x
 
 
 def _check_size(v: int) -> int:

@@ -3,12 +3,14 @@
 // device-side convergence control, and the stateless single-step entry points.
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "learned.h"
 
 namespace bmg {
 
@@ -38,6 +40,7 @@ int cuda_check(cudaError_t e, const char* what) {
 }
 
 void zero_ring(int n, double* r, cudaStream_t s);   // k_cycle.cu
+int mlp_level0_interp(const void* m, int n, const double* st, double* ci, cudaStream_t s);   // learned_api.cu
 
 }  // namespace bmg
 
@@ -83,6 +86,9 @@ StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
 
 struct bmg_hierarchy {
   int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3, krylov = 0;
+  int interp = BMG_INTERP_DENDY, interp_used = BMG_INTERP_DENDY;
+  const void* mlp = nullptr;
+  double factor_learned = 0.0, factor_dendy = 0.0;
   double* kr = nullptr;   // flexible CG vectors r, z, p, q (FP64, (n+2)^2 each)
   std::vector<Level> lv;
   cudaStream_t user = nullptr;   // caller stream (ordering only)
@@ -351,7 +357,11 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
     Level& C = h->lv[l + 1];
-    launch_dendy(L.n, L.st, L.ci, h->err, s);
+    if (l == 0 && h->interp == BMG_INTERP_LEARNED) {
+      if ((rc = mlp_level0_interp(h->mlp, L.n, L.st, L.ci, s))) return rc;
+    } else {
+      launch_dendy(L.n, L.st, L.ci, h->err, s);
+    }
     launch_rap(L.n, L.st, L.ci, C.st, s);
     launch_dinv(C.n, C.st, h->err, s);
   }
@@ -391,6 +401,36 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
 
 }  // namespace
 
+extern "C" int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int maxit, int* iters,
+                         double* relres);
+
+namespace {
+// V-cycle factor (r_8 / r_4)^(1/4) from a SplitMix64 uniform[-1,1) start
+// (stream 0x5EED) with a zero right-hand side.
+int measure_factor(bmg_hierarchy* h, double* out) {
+  size_t ps = plane_size(h->n);
+  double *x = nullptr, *f = nullptr;
+  CK(cudaMalloc((void**)&x, ps * sizeof(double)));
+  CK(cudaMalloc((void**)&f, ps * sizeof(double)));
+  CK(cudaMemset(x, 0, ps * sizeof(double)));
+  CK(cudaMemset(f, 0, ps * sizeof(double)));
+  launch_uniform_pm1(h->n, 0x5EEDull, x, nullptr);
+  CK(cudaDeviceSynchronize());
+  int it = 0;
+  double rr = 0;
+  int rc = bmg_solve(h, f, x, 0.0, 8, &it, &rr);
+  cudaFree(x);
+  cudaFree(f);
+  if (rc != BMG_OK && rc != BMG_ENOTCONV) return rc;
+  if (h->hist.size() < 9 || !(h->hist[4] > 0)) {
+    *out = 0.0;
+    return BMG_OK;
+  }
+  *out = std::pow(h->hist[8] / h->hist[4], 0.25);
+  return BMG_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* bmg_strerror(int code) {
@@ -428,10 +468,13 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     h->inner = o->inner_cycles > 0 ? o->inner_cycles : 1;
     h->use_graph = o->use_graph;
     h->krylov = o->krylov;
+    h->interp = o->interp;
+    h->mlp = o->mlp;
     h->user = (cudaStream_t)o->stream;
   }
   if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
-      h->nu1 < 0 || h->nu2 < 0 || (o && o->interp != BMG_INTERP_DENDY) || h->krylov < 0 || h->krylov > 1) {
+      h->nu1 < 0 || h->nu2 < 0 || h->interp < 0 || h->interp > 1 || (h->interp == BMG_INTERP_LEARNED && !h->mlp) ||
+      h->krylov < 0 || h->krylov > 1) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad options");
   }
@@ -447,7 +490,38 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     bmg_free(h);
     return rc;
   }
+  h->interp_used = h->interp;
+  if (h->interp == BMG_INTERP_LEARNED) {
+    // Dendy is the fallback: build it too, measure both factors, keep the better.
+    bmg_opts od = *o;
+    od.interp = BMG_INTERP_DENDY;
+    od.mlp = nullptr;
+    bmg_hierarchy* hd = nullptr;
+    rc = bmg_setup(A, nx, ny, &od, &hd);
+    double fl = 0, fd = 0;
+    if (!rc) rc = measure_factor(h, &fl);
+    if (!rc) rc = measure_factor(hd, &fd);
+    if (rc) {
+      bmg_free(h);
+      bmg_free(hd);
+      return rc;
+    }
+    bmg_hierarchy* keep = fl <= fd ? h : hd;
+    bmg_free(keep == h ? hd : h);
+    keep->interp_used = keep == h ? BMG_INTERP_LEARNED : BMG_INTERP_DENDY;
+    keep->factor_learned = fl;
+    keep->factor_dendy = fd;
+    h = keep;
+  }
   *out = h;
+  return BMG_OK;
+}
+
+int bmg_interp_info(const bmg_hierarchy* h, int* used, double* fl, double* fd) {
+  if (!h) return set_error(BMG_EINVAL, "bmg_interp_info: NULL hierarchy");
+  if (used) *used = h->interp_used;
+  if (fl) *fl = h->factor_learned;
+  if (fd) *fd = h->factor_dendy;
   return BMG_OK;
 }
 
