@@ -85,7 +85,9 @@ typedef struct {
   int nu1, nu2;         /* pre- and post-smoothing sweeps (0,0 = 2,1) */
   int inner_cycles;     /* FP32 V-cycles per refinement step (0 = 1) */
   int bf16_levels;      /* levels with BF16 stencils under BMG_BF16_IR (0 = 2) */
-  int use_graph;        /* 1 = replay one captured CUDA graph per cycle (default), 0 = plain launches */
+  int use_graph;        /* 1 (default): replay one captured CUDA graph per cycle, autotune the
+                           row-kernel tiles and run the coarse levels (n <= 63 FP32, n <= 15 FP64)
+                           as one level-fused launch; 0: plain launches, one per step */
   int krylov;           /* BMG_KRYLOV_NONE (default): stationary V-cycle iteration;
                            BMG_KRYLOV_FCG: flexible CG with one cycle as preconditioner */
   const void* mlp;      /* bmg_mlp* for interp = BMG_INTERP_LEARNED, else NULL */
@@ -137,7 +139,8 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
  * hierarchy's stream (the Fig. 10 breakdown).  Fills up to `cap` rows of the
  * host array `rows` and returns the number of rows. */
 enum { BMG_K_RELAX = 0, BMG_K_RESID_RESTRICT = 1, BMG_K_INTERP = 2, BMG_K_COARSE = 3, BMG_K_NORM = 4,
-       BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7, BMG_K_FCG = 8 };
+       BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7, BMG_K_FCG = 8,
+       BMG_K_TAIL = 9 /* the level-fused coarse levels, counted at their top level */ };
 typedef struct {
   int level;            /* 0 = finest */
   int kernel;           /* BMG_K_* */
@@ -146,6 +149,10 @@ typedef struct {
   double ms;            /* total device time */
 } bmg_prof_row;
 int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_prof_row* rows, int cap);
+
+/* Row-kernel cluster size the setup autotuner chose for level `level` of the
+ * cycle the hierarchy runs (FP64 or FP32), or 0 (default; not tuned). */
+int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 
 /* Number of levels, and the size n of level l (0 = finest). */
 int bmg_num_levels(const bmg_hierarchy* h);

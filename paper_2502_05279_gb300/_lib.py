@@ -42,7 +42,7 @@ class ProfRow(ctypes.Structure):
 
 
 KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
-                "ir_update", "ir_residual", "fcg")
+                "ir_update", "ir_residual", "fcg", "tail")
 _KRYLOV = {"none": 0, "fcg": 1}
 
 
@@ -93,6 +93,7 @@ _sig = {
     "bmg_mlp_infer": (I, [P, I, P, P, P]),
     "bmg_learned_interp": (I, [I, P, P, P, P]),
     "bmg_interp_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
+    "bmg_tuned_cluster": (I, [P, I]),
     "bmg_fill_uniform": (I, [I, ctypes.c_ulonglong, P, P]),
     "bmg_mlp_free": (None, [P]),
     "bmg_profile": (I, [P, P, P, I, P, I]),
@@ -192,6 +193,9 @@ class Hierarchy:
         e = torch.empty_like(r32)
         _check(lib.bmg_inner_cycle(self._h, _ptr(r32, torch.float32, "r32"), _ptr(e, torch.float32, "e32")))
         return e
+
+    def tuned_cluster(self, level: int) -> int:
+        return _check_size(lib.bmg_tuned_cluster(self._h, level))
 
     def interp_info(self):
         """(kept interpolation: "learned" or "dendy", learned factor, Dendy factor)."""

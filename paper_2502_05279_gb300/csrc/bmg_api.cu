@@ -6,9 +6,12 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
+#include "cycle_device.cuh"
 #include "kernels.h"
 #include "learned.h"
 
@@ -61,6 +64,7 @@ struct Level {
   double* x = nullptr;    // levels >= 1
   double* f = nullptr;
   bool bf16 = false;      // FP32 cycle reads BF16 off-diagonals on this level
+  int cl64 = 0, cl32 = 0; // row-kernel cluster sizes chosen by the autotuner (0 = default)
   float* st32 = nullptr;  // O, W, S, SW, NW, D in FP32
   __nv_bfloat16* off16 = nullptr;
   float* od32 = nullptr;  // O32, D32 of a BF16 level
@@ -117,6 +121,9 @@ struct bmg_hierarchy {
   std::vector<Mark>* prof = nullptr;   // non-null while bmg_profile records
   int last_hist = 0;
   std::vector<double> hist;
+  // level-fused tail: levels >= tail_l run in one launch (-1: none)
+  int tail_l = -1;
+  void* d_tail = nullptr;   // TailDesc<double> or TailDesc<float> in device memory
 };
 
 namespace {
@@ -156,23 +163,27 @@ int dalloc(T** p, size_t count) {
 void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* done) {
   Level& L = h->lv[l];
   cudaStream_t s = h->ws;
+  if (l == h->tail_l) {
+    step(h, l, BMG_K_TAIL, 0, [&] { launch_tail<double>((const TailDesc<double>*)h->d_tail, 1, L.kind, done, s); });
+    return;
+  }
   if (l == h->nlev - 1) {
     step(h, l, BMG_K_COARSE, 0, [&] { launch_coarse_solve<double>(L.n, h->Lfac, f, x, h->work, done, s); });
     return;
   }
   auto v = view64(L);
   Level& C = h->lv[l + 1];
-  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu1, done, s); });
+  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu1, done, s, L.cl64); });
   step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, x, f, C.f, C.x, done, s); });
   vcycle64(h, l + 1, C.x, C.f, done);
   step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s); });
-  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu2, done, s); });
+  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu2, done, s, L.cl64); });
 }
 
 template <typename S>
 void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, const int* done) {
   Level& L = h->lv[l];
-  step(h, l, BMG_K_RELAX, 1, [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws); });
+  step(h, l, BMG_K_RELAX, 1, [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws, L.cl32); });
 }
 
 template <typename S>
@@ -187,6 +198,10 @@ void restrict32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, const i
 void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   Level& L = h->lv[l];
   cudaStream_t s = h->ws;
+  if (l == h->tail_l) {
+    step(h, l, BMG_K_TAIL, 1, [&] { launch_tail<float>((const TailDesc<float>*)h->d_tail, 1, L.kind, done, s); });
+    return;
+  }
   if (l == h->nlev - 1) {
     step(h, l, BMG_K_COARSE, 1,
          [&] { launch_coarse_solve<float>(L.n, h->Lfac, (const float*)L.f32, L.x32, h->work, done, s); });
@@ -206,6 +221,103 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
     relax32(h, viewbf(L), l, h->nu2, done);
   else
     relax32(h, view32(L), l, h->nu2, done);
+}
+
+// Autotuner of the solo hierarchy: for every 9-point level with n >= 127 time
+// two Gauss-Seidel sweeps of the row kernel for each admissible cluster size
+// (1, 2, 4, 8 CTAs per row, at least a warp of pairs per CTA) on scratch
+// iterates with the level's real stencil, and keep the fastest.  The choice
+// only changes how a row is split over CTAs, never a result bit.  Results are
+// cached per (n, compute type, storage type) for the life of the process.
+template <typename T, typename S>
+int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out) {
+  static std::map<std::tuple<int, int, int>, int> cache;
+  auto key = std::make_tuple(v.n, (int)sizeof(T), (int)sizeof(S));
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *best_out = it->second;
+    return BMG_OK;
+  }
+  const int base = rows_cluster<T>(v.n);
+  size_t ps = plane_size(v.n);
+  T* scratch = nullptr;
+  CK(cudaMalloc((void**)&scratch, 2 * ps * sizeof(T)));
+  CK(cudaMemsetAsync(scratch, 0, 2 * ps * sizeof(T), s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_cl = base;
+  for (int cl = base; cl <= 8; cl *= 2) {
+    if (cl > base && ((v.n + 1) / 2 + cl - 1) / cl < 32) break;
+    launch_gs(v, 9, (const T*)(scratch + ps), scratch, 1, (const int*)nullptr, s, cl);   // warm-up
+    cudaEventRecord(e0, s);
+    launch_gs(v, 9, (const T*)(scratch + ps), scratch, 2, (const int*)nullptr, s, cl);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_cl = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  CK(cudaGetLastError());
+  cache[key] = best_cl;
+  *best_out = best_cl;
+  return BMG_OK;
+}
+
+// Level-fused tail of the solo hierarchy: the first level l (>= 1 for FP64, and
+// not a BF16 level) with n <= tail_max_n and at least one level below it.
+template <typename T>
+int build_tail(bmg_hierarchy* h, int lmin) {
+  int lt = -1;
+  for (int l = lmin; l + 1 < h->nlev; ++l)
+    if (h->lv[l].n <= tail_max_n<T>() && !h->lv[l].bf16) {
+      lt = l;
+      break;
+    }
+  if (lt < 0 || h->nlev - lt > TAIL_LEVELS) return BMG_OK;
+  TailDesc<T> d{};
+  d.nlev = h->nlev - lt;
+  d.nu1 = h->nu1;
+  d.nu2 = h->nu2;
+  d.top_kind = h->lv[lt].kind;
+  d.done = nullptr;
+  for (int k = 0; k < d.nlev; ++k) {
+    Level& L = h->lv[lt + k];
+    Level* C = lt + k + 1 < h->nlev ? &h->lv[lt + k + 1] : nullptr;
+    if constexpr (sizeof(T) == 8)
+      d.lv[k] = LevelDesc<double, double>{view64(L), L.ci, L.x, L.f, C ? C->x : nullptr, C ? C->f : nullptr,
+                                          nullptr, h->Lfac, h->work};
+    else
+      d.lv[k] = LevelDesc<float, float>{view32(L), L.ci32, L.x32, L.f32, C ? C->x32 : nullptr,
+                                        C ? C->f32 : nullptr, nullptr, h->Lfac, h->work};
+  }
+  CK(cudaMalloc(&h->d_tail, sizeof(d)));
+  CK(cudaMemcpy(h->d_tail, &d, sizeof(d), cudaMemcpyHostToDevice));
+  h->tail_l = lt;
+  return BMG_OK;
+}
+
+int autotune_solo(bmg_hierarchy* h) {
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    Level& L = h->lv[l];
+    if (L.kind != 9 || L.n < 127) continue;
+    int rc = BMG_OK;
+    if (h->precision == BMG_FP64)
+      rc = tune_rows(view64(L), h->ws, &L.cl64);
+    else if (L.bf16)
+      rc = tune_rows(viewbf(L), h->ws, &L.cl32);
+    else
+      rc = tune_rows(view32(L), h->ws, &L.cl32);
+    if (rc) return rc;
+  }
+  return BMG_OK;
 }
 
 // One iteration of the solve loop: a V-cycle (or a refinement step) followed by
@@ -418,7 +530,20 @@ int measure_factor(bmg_hierarchy* h, double* out) {
   CK(cudaDeviceSynchronize());
   int it = 0;
   double rr = 0;
+  // the stationary cycle, whatever solve mode the hierarchy has; a graph
+  // captured in the other mode must not be replayed
+  const int krylov = h->krylov;
+  auto drop_graph = [&] {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_rhs = nullptr;
+    h->g_x = nullptr;
+  };
+  drop_graph();
+  h->krylov = BMG_KRYLOV_NONE;
   int rc = bmg_solve(h, f, x, 0.0, 8, &it, &rr);
+  h->krylov = krylov;
+  drop_graph();
   cudaFree(x);
   cudaFree(f);
   if (rc != BMG_OK && rc != BMG_ENOTCONV) return rc;
@@ -485,6 +610,8 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = setup_impl(h, A, nx, o);
+  if (!rc && h->use_graph) rc = autotune_solo(h);
+  if (!rc && h->use_graph) rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
   if (!rc) rc = ensure_ctl(h, 64);
   if (rc) {
     bmg_free(h);
@@ -515,6 +642,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   }
   *out = h;
   return BMG_OK;
+}
+
+int bmg_tuned_cluster(const bmg_hierarchy* h, int level) {
+  if (!h || level < 0 || level >= h->nlev) return set_error(BMG_EINVAL, "bmg_tuned_cluster: bad level");
+  const Level& L = h->lv[level];
+  return h->precision == BMG_FP64 ? L.cl64 : L.cl32;
 }
 
 int bmg_interp_info(const bmg_hierarchy* h, int* used, double* fl, double* fd) {
@@ -682,6 +815,7 @@ void bmg_free(bmg_hierarchy* h) {
   cudaFree(h->work);
   cudaFree(h->partials);
   cudaFree(h->kr);
+  cudaFree(h->d_tail);
   cudaFree(h->err);
   cudaFree(h->ctl);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
@@ -856,6 +990,10 @@ struct bmg_batch {
   };
   std::vector<std::array<Group, kGroups>> stages;   // index b = levels above the coarsest
   std::vector<int> tuned_cl;                         // per stage, 0 = not tuned
+  // level-fused tails, grouped by the stage they start at
+  std::vector<int> tail_count;
+  std::vector<std::vector<char>> tail_host;
+  std::vector<void*> tail_dev;
   std::vector<TopDesc> top;
   TopDesc* d_top = nullptr;
   char* ctls = nullptr;
@@ -886,18 +1024,69 @@ void append_desc(bmg_batch::Group& g, const LevelDesc<T, S>& d) {
 // Fill every stage's descriptor tables and the top-level table for the caller
 // buffers rhs/x and upload them (the device addresses never change, so a
 // captured graph stays valid).  With rhs == NULL only the group sizes are set.
+// First level of problem p that joins its level-fused tail (-1: none): the
+// rule of the solo hierarchy (FP64 from level 1, n <= 15; FP32 from level 0,
+// n <= 63, not BF16), only when graphs are in use.
+int batch_tail_level(bmg_batch* B, bmg_hierarchy* h) {
+  if (!B->use_graph) return -1;
+  const bool f64 = B->precision == BMG_FP64;
+  const int thr = f64 ? tail_max_n<double>() : tail_max_n<float>();
+  for (int l = f64 ? 1 : 0; l + 1 < h->nlev; ++l)
+    if (h->lv[l].n <= thr && !h->lv[l].bf16) return h->nlev - l <= TAIL_LEVELS ? l : -1;
+  return -1;
+}
+
+template <typename T>
+void append_tail(bmg_batch* B, bmg_hierarchy* h, int lt, const int* done, int b) {
+  TailDesc<T> d{};
+  d.nlev = h->nlev - lt;
+  d.nu1 = B->nu1;
+  d.nu2 = B->nu2;
+  d.top_kind = h->lv[lt].kind;
+  d.done = done;
+  for (int k = 0; k < d.nlev; ++k) {
+    Level& L = h->lv[lt + k];
+    Level* C = lt + k + 1 < h->nlev ? &h->lv[lt + k + 1] : nullptr;
+    if constexpr (sizeof(T) == 8)
+      d.lv[k] = LevelDesc<double, double>{view64(L), L.ci, L.x, L.f, C ? C->x : nullptr, C ? C->f : nullptr,
+                                          nullptr, h->Lfac, h->work};
+    else
+      d.lv[k] = LevelDesc<float, float>{view32(L), L.ci32, L.x32, L.f32, C ? C->x32 : nullptr,
+                                        C ? C->f32 : nullptr, nullptr, h->Lfac, h->work};
+  }
+  const char* c = (const char*)&d;
+  B->tail_host[b].insert(B->tail_host[b].end(), c, c + sizeof(d));
+}
+
+// Fill every stage's descriptor tables, the tails and the top-level table for
+// the caller buffers rhs/x and upload them (the device addresses never change,
+// so a captured graph stays valid).  With rhs == NULL only the sizes are set.
 int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x) {
   for (auto& st : B->stages)
     for (auto& g : st) {
       g.host.clear();
       if (!rhs) g.count = 0;
     }
+  for (auto& t : B->tail_host) t.clear();
+  if (!rhs) std::fill(B->tail_count.begin(), B->tail_count.end(), 0);
   B->top.clear();
+  const size_t tail_elem = B->precision == BMG_FP64 ? sizeof(TailDesc<double>) : sizeof(TailDesc<float>);
   for (int p = 0; p < B->nprob; ++p) {
     bmg_hierarchy* h = B->hs[p];
     const int L = h->nlev;
     const int* done = &batch_ctl(B, p)->done;
+    const int lt = batch_tail_level(B, h);
+    if (lt >= 0) {
+      const int bt = L - 1 - lt;
+      if (!rhs)
+        ++B->tail_count[bt];
+      else if (B->precision == BMG_FP64)
+        append_tail<double>(B, h, lt, done, bt);
+      else
+        append_tail<float>(B, h, lt, done, bt);
+    }
     for (int l = 0; l < L; ++l) {
+      if (lt >= 0 && l >= lt) break;   // these levels run inside the tail
       Level& lv = h->lv[l];
       const int b = L - 1 - l;
       Level* C = l + 1 < L ? &h->lv[l + 1] : nullptr;
@@ -938,6 +1127,13 @@ int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x)
         if (g.host.size() != g.elem * (size_t)g.count) return set_error(BMG_ECUDA, "batched: table size mismatch");
         CK(cudaMemcpyAsync(g.d, g.host.data(), g.host.size(), cudaMemcpyHostToDevice, B->ws));
       }
+  for (size_t b = 0; b < B->tail_host.size(); ++b)
+    if (B->tail_count[b]) {
+      if (B->tail_host[b].size() != tail_elem * B->tail_count[b])
+        return set_error(BMG_ECUDA, "batched: tail table size mismatch");
+      CK(cudaMemcpyAsync(B->tail_dev[b], B->tail_host[b].data(), B->tail_host[b].size(), cudaMemcpyHostToDevice,
+                         B->ws));
+    }
   CK(cudaMemcpyAsync(B->d_top, B->top.data(), sizeof(TopDesc) * B->top.size(), cudaMemcpyHostToDevice, B->ws));
   return BMG_OK;
 }
@@ -976,11 +1172,18 @@ void group_coarse(bmg_batch* B, bmg_batch::Group& g) {
 // One V(nu1, nu2) cycle of every problem: down the stages (largest first), the
 // coarsest solves, back up.
 void batch_vcycle(bmg_batch* B) {
-  for (int b = B->bmax; b >= 1; --b)
+  for (int b = B->bmax; b >= 1; --b) {
     for (auto& g : B->stages[b]) {
       group_relax(B, g, B->nu1);
       group_restrict(B, g);
     }
+    if (B->tail_count[b]) {   // problems whose remaining levels run in one level-fused launch
+      if (B->precision == BMG_FP64)
+        launch_tail<double>((const TailDesc<double>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws);
+      else
+        launch_tail<float>((const TailDesc<float>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws);
+    }
+  }
   for (auto& g : B->stages[0]) group_coarse(B, g);
   for (int b = 1; b <= B->bmax; ++b)
     for (auto& g : B->stages[b]) {
@@ -1207,6 +1410,9 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   if (!rc) {
     B->stages.assign(B->bmax + 1, {});
     B->tuned_cl.assign(B->bmax + 1, 0);
+    B->tail_count.assign(B->bmax + 1, 0);
+    B->tail_host.assign(B->bmax + 1, {});
+    B->tail_dev.assign(B->bmax + 1, nullptr);
     rc = build_batch_tables(B, nullptr, nullptr);   // group sizes
   }
   for (auto& st : B->stages)
@@ -1215,6 +1421,12 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
       g.cl = g.storage == 0 ? rows_cluster<double>(g.n) : rows_cluster<float>(g.n);
       rc = cuda_check(cudaMalloc(&g.d, g.elem * g.count), "batched tables");
     }
+  for (size_t b = 0; !rc && b < B->tail_count.size(); ++b)
+    if (B->tail_count[b])
+      rc = cuda_check(cudaMalloc(&B->tail_dev[b], (B->precision == BMG_FP64 ? sizeof(TailDesc<double>)
+                                                                             : sizeof(TailDesc<float>)) *
+                                                      B->tail_count[b]),
+                      "batched tails");
   if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_top, sizeof(TopDesc) * nprob), "batched tables");
   if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&B->h_alldone, sizeof(int)), "pinned");
@@ -1316,6 +1528,7 @@ void bmg_free_batched(bmg_batch* B) {
   for (auto* h : B->hs) bmg_free(h);
   for (auto& st : B->stages)
     for (auto& g : st) cudaFree(g.d);
+  for (void* t : B->tail_dev) cudaFree(t);
   cudaFree(B->d_top);
   cudaFree(B->ctls);
   cudaFree(B->d_alldone);

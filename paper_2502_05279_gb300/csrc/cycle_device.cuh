@@ -368,3 +368,123 @@ __device__ __forceinline__ void ir_residual_body(const StencilView<double, doubl
 
 }  // namespace dev
 }  // namespace bmg
+
+// ==== level-fused tail: the V-cycle below a small level in one CTA ===========================
+namespace bmg {
+
+constexpr int TAIL_LEVELS = 6;   // levels held by one tail descriptor (n <= 63 down to 3 is 5)
+
+// The levels of one problem from the tail's top level down to the coarsest.
+template <typename T>
+struct TailDesc {
+  LevelDesc<T, T> lv[TAIL_LEVELS];
+  int nlev;     // levels in lv (the last is the coarsest)
+  int nu1, nu2;
+  int top_kind; // stencil kind of lv[0] (5 or 9); the levels below are 9-point
+  const int* done;
+};
+
+namespace dev {
+
+// Half of a four-colour sweep over one CTA: the rows of parity pj, their odd-i
+// points, a barrier, their even-i points, a barrier (the order of k_gs_rows).
+template <typename T, typename S>
+__device__ __forceinline__ void gs_half_block(const StencilView<T, S>& v, const T* f, T* x, int pj) {
+  const int n = v.n;
+  const int R = pj ? (n + 1) / 2 : (n - 1) / 2;
+  const int Po = (n + 1) / 2, Pe = (n - 1) / 2;
+  for (int k = threadIdx.x; k < R * Po; k += blockDim.x) {
+    int j = 2 * (k / Po) + (pj ? 1 : 2), i = 2 * (k % Po) + 1;
+    gs_point<T, S, true>(v, f, x, (size_t)j * v.ld + i);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < R * Pe; k += blockDim.x) {
+    int j = 2 * (k / Pe) + (pj ? 1 : 2), i = 2 * (k % Pe) + 2;
+    gs_point<T, S, true>(v, f, x, (size_t)j * v.ld + i);
+  }
+  __syncthreads();
+}
+
+// One red-black colour over one CTA (5-point levels).
+template <typename T, typename S>
+__device__ __forceinline__ void gs_checker_block(const StencilView<T, S>& v, const T* f, T* x, int c) {
+  const int n = v.n;
+  const int per_row = (n + 1) / 2;
+  for (int k = threadIdx.x; k < n * per_row; k += blockDim.x) {
+    int j = k / per_row + 1;
+    int i = 2 * (k % per_row) + 1 + ((j + 1 + c) & 1);
+    if (i <= n) gs_point<T, S, false>(v, f, x, (size_t)j * v.ld + i);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void relax_block(const LevelDesc<T, T>& q, int kind, int sweeps) {
+  for (int s = 0; s < sweeps; ++s) {
+    if (kind == 9) {
+      gs_half_block<T, T>(q.v, q.f, q.x, 1);
+      gs_half_block<T, T>(q.v, q.f, q.x, 0);
+    } else {
+      gs_checker_block<T, T>(q.v, q.f, q.x, 0);
+      gs_checker_block<T, T>(q.v, q.f, q.x, 1);
+    }
+  }
+}
+
+// Residual + Fig. 2 restriction, one coarse point per thread iteration; the
+// nine fine residuals are formed where they are needed (same values as the
+// tiled kernel: each is the same expression of the same data).
+template <typename T, bool NINE>
+__device__ __forceinline__ void resid_restrict_block(const LevelDesc<T, T>& q) {
+  const StencilView<T, T>& v = q.v;
+  const int n = v.n, ld = v.ld, nc = (n - 1) / 2, ldc = nc + 2;
+  const size_t psc = plane_size(nc);
+  for (int k = threadIdx.x; k < nc * nc; k += blockDim.x) {
+    int ic = k % nc + 1, jc = k / nc + 1;
+    size_t pf = (size_t)(2 * jc) * ld + 2 * ic;
+    auto r = [&](int dx, int dy) {
+      size_t p = pf + (size_t)((long long)dy * ld + dx);
+      return row_residual<T, T, NINE, true>(v, q.x, p, q.f[p]);
+    };
+    auto w = [&](int kk, int dic, int djc) { return q.ci[kk * psc + (size_t)(jc + djc) * ldc + (ic + dic)]; };
+    T t = rmul(w(CI_LNE, 0, 0), r(-1, -1));
+    t = radd(t, rmul(w(CI_LA, 0, 0), r(0, -1)));
+    t = radd(t, rmul(w(CI_LNW, 1, 0), r(1, -1)));
+    t = radd(t, rmul(w(CI_LR, 0, 0), r(-1, 0)));
+    t = radd(t, r(0, 0));
+    t = radd(t, rmul(w(CI_LL, 1, 0), r(1, 0)));
+    t = radd(t, rmul(w(CI_LSE, 0, 1), r(-1, 1)));
+    t = radd(t, rmul(w(CI_LB, 0, 1), r(0, 1)));
+    t = radd(t, rmul(w(CI_LSW, 1, 1), r(1, 1)));
+    size_t pc = (size_t)jc * ldc + ic;
+    q.fc[pc] = t;
+    q.xc[pc] = T(0);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void tail_body(const TailDesc<T>& d, int top_kind) {
+  for (int l = 0; l + 1 < d.nlev; ++l) {
+    const int kind = l == 0 ? top_kind : 9;
+    relax_block<T>(d.lv[l], kind, d.nu1);
+    if (kind == 9)
+      resid_restrict_block<T, true>(d.lv[l]);
+    else
+      resid_restrict_block<T, false>(d.lv[l]);
+  }
+  const LevelDesc<T, T>& c = d.lv[d.nlev - 1];
+  coarse_solve_body<T>(c.v.n, c.L, c.f, c.x, c.y);
+  __syncthreads();
+  for (int l = d.nlev - 2; l >= 0; --l) {
+    const LevelDesc<T, T>& q = d.lv[l];
+    const int nc = (q.v.n - 1) / 2;
+    for (int k = threadIdx.x; k < (nc + 1) * (nc + 1); k += blockDim.x)
+      interp_body<T>(q.v.n, q.ci, q.xc, q.x, k % (nc + 1) + 1, k / (nc + 1) + 1);
+    __syncthreads();
+    relax_block<T>(q, l == 0 ? top_kind : 9, d.nu2);
+  }
+}
+
+}  // namespace dev
+}  // namespace bmg

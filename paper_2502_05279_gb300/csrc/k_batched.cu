@@ -83,6 +83,13 @@ __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* _
   ir_residual_body(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tail(const TailDesc<T>* __restrict__ d, const int* done) {
+  const TailDesc<T>& q = d[blockIdx.x];
+  if (stopped(done) || stopped(q.done)) return;
+  tail_body<T>(q, q.top_kind);
+}
+
 // 1 when every problem's control flag is set.
 __global__ void k_all_done(const char* __restrict__ ctls, size_t stride, int count, int* out) {
   __shared__ int any_running;
@@ -188,6 +195,16 @@ void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s)
   k_ir_residual_b<<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
   count_launch();
 }
+
+template <typename T>
+void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s) {
+  if (count <= 0) return;
+  (void)top_kind;
+  k_tail<T><<<count, 1024, 0, s>>>(d, done_any);
+  count_launch();
+}
+template void launch_tail<double>(const TailDesc<double>*, int, int, const int*, cudaStream_t);
+template void launch_tail<float>(const TailDesc<float>*, int, int, const int*, cudaStream_t);
 
 void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s) {
   k_all_done<<<1, 256, 0, s>>>(ctls, stride, count, out);

@@ -141,10 +141,12 @@ int rows_threads(int n, int cl) {
 }
 
 template <typename T, typename S>
-void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s) {
+void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
+               int cl_req) {
   const int n = v.n;
   if (kind == 9) {
-    const int cl = rows_cluster<T>(n), threads = rows_threads(n, cl);
+    const int cl = cl_req >= rows_cluster<T>(n) && cl_req <= 8 ? cl_req : rows_cluster<T>(n);
+    const int threads = rows_threads(n, cl);
     for (int k = 0; k < sweeps; ++k)
       for (int pj = 1; pj >= 0; --pj) {
         const int rows = pj ? (n + 1) / 2 : (n - 1) / 2;
@@ -252,7 +254,7 @@ double measure_fp64_rate(cudaStream_t s) {
 
 // ---- explicit instantiations ---------------------------------------------------------
 #define BMG_INST(T, S)                                                                                           \
-  template void launch_gs<T, S>(const StencilView<T, S>&, int, const T*, T*, int, const int*, cudaStream_t);    \
+  template void launch_gs<T, S>(const StencilView<T, S>&, int, const T*, T*, int, const int*, cudaStream_t, int);    \
   template void launch_resid_restrict<T, S>(const StencilView<T, S>&, int, const T*, const T*, const T*, T*, T*, \
                                             const int*, cudaStream_t);                                          \
   template int launch_residual<T, S>(const StencilView<T, S>&, int, const T*, const T*, T*, double*, const int*, \

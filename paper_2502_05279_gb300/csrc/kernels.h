@@ -36,7 +36,8 @@ void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od3
 // `done`: device flag of the running solve (NULL = always run); every kernel
 // returns at once when it is nonzero.
 template <typename T, typename S>
-void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s);
+void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
+               int cl = 0);   // cl: row-kernel cluster size, 0 = the smallest that covers a row
 template <typename T, typename S>
 void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,
                            T* xc, const int* done, cudaStream_t s);
@@ -123,4 +124,15 @@ template <typename T>
 int rows_cluster(int n);
 int rows_threads(int n, int cl);
 
+}  // namespace bmg
+
+namespace bmg {
+template <typename T>
+struct TailDesc;
+// The level-fused tail of `count` problems (one CTA each); top_kind is the
+// stencil kind of each descriptor's first level.
+template <typename T>
+void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s);
+template <typename T>
+constexpr int tail_max_n() { return sizeof(T) == 8 ? 15 : 63; }
 }  // namespace bmg
