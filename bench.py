@@ -50,9 +50,14 @@ WORKLOADS = {
         make=lambda: w.lognormal_problem(8191, 2.0, 32.0, seed_k=4, seed_f=7)),
 }
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by
-# (workload, variant, kernel); None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the current kernels, keyed by (workload, variant, kernel); the
+# captures and their commands are summarised in profiles/gs_rows_*_fe2047.md.
+NCU_TRAFFIC = {
+    ("fe2047-binary1e4", "fp64", "relax"): 196.5e6,
+    ("fe2047-binary1e4", "fp32", "relax"): 95.6e6,
+    ("fe2047-binary1e4", "bf16", "relax"): 63.8e6,
+}
 
 
 BATCHED = dict(text="256 independent 9-point Q1 problems, sides uniform from {63,127,255,511,1023} (seed 5), "
