@@ -66,53 +66,156 @@ BATCHED = dict(text="256 independent 9-point Q1 problems, sides uniform from {63
 
 
 def run_batched(args, rank, local_rank, world):
-    """Config of the batched extension: one step = one iteration of every
-    problem (V(2,1) + norm, or one refinement step), all in one CUDA graph."""
+    """The batched extension: one step = one iteration of every problem of the
+    rank's batch (V(2,1) + norm, or one refinement step), all in one CUDA
+    graph.  Weak scaling over ranks: each rank solves its own 256 problems."""
     import torch
     import paper_2502_05279_gb300 as bmg
     torch.cuda.set_device(local_rank)
-    probs = w.batched_problems(256, 5, 1.0, 32.0)
+    ranks = Ranks("nccl")
+    first, count = batched_shard(rank)
+    probs = w.batched_problems(count, 5, 1.0, 32.0, first=first)
     N = sum((p[1].shape[-1] - 2) ** 2 for p in probs)
     coefs = [torch.from_numpy(p[1]).cuda() for p in probs]
     rhs = [torch.from_numpy(p[2]).cuda() for p in probs]
     out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-           "config": {"workload": "batched256", "description": BATCHED["text"], "unknowns": N,
-                      "problems": len(probs)}, "variants": {}}
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic (seeded generators, no datasets)",
+           "config": {"workload": "batched256", "description": BATCHED["text"], "unknowns_per_rank_0": N,
+                      "problems_per_rank": count, "parallelism": "problems sharded over ranks" if world > 1
+                      else "single GPU", "l2": "working set > L2 (FP64 level-0 stencils + vectors = %.0f MB)"
+                      % (N * 64 / 1e6)}, "variants": {}}
+    clock_s = None
     for prec in ("fp64", "fp32", "bf16"):
-        torch.cuda.synchronize()
+        ranks.barrier()
         t0 = time.perf_counter()
         B = bmg.Batch(9, coefs, precision=prec)
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         xs = [torch.zeros_like(r) for r in rhs]
-        B.time_cycles(rhs, xs, args.warmup)
+        B.time_cycles(rhs, xs, max(args.warmup, 3))
+        ranks.barrier()
         before = B.launch_count
-        ms = B.time_cycles(rhs, xs, args.steps)
+        if prec == "fp64":
+            with ClockSampler(local_rank) as cs:
+                ms = B.time_cycles(rhs, xs, args.steps)
+            clock_s = cs.summary()
+        else:
+            ms = B.time_cycles(rhs, xs, args.steps)
         launches = B.launch_count - before
+        ranks.barrier()
+        rate = whole_job_rate(N * args.steps, ms * 1e-3, ranks)
         for x in xs:
             x.zero_()
-        torch.cuda.synchronize()
+        ranks.barrier()
         t0 = time.perf_counter()
         _, its, rrs, ok = B.solve(rhs, xs, tol=1e-8, maxit=100)
         torch.cuda.synchronize()
-        tts = (time.perf_counter() - t0) * 1e3
-        out["variants"][prec] = {"value": N * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-                                 "setup_ms_incl_autotune": round(setup_ms, 1), "time_to_1e-8_ms": round(tts, 2),
-                                 "iterations_max": max(its), "iterations_min": min(its), "all_converged": ok,
-                                 "launches_per_step": launches / args.steps,
-                                 "tuned_cluster_by_stage": [B.tuned_cluster(b) for b in range(9)]}
+        tts = ranks.max((time.perf_counter() - t0) * 1e3)
+        rec = {"value": rate, "ms_per_step": ranks.max(ms) / args.steps,
+               "setup_ms_incl_autotune": round(setup_ms, 1), "time_to_1e-8_ms": round(tts, 2),
+               "iterations_max": max(its), "iterations_min": min(its), "all_converged": ok,
+               "launches_per_step": launches / args.steps,
+               "tuned_cluster_by_stage": [B.tuned_cluster(b) for b in range(9)]}
+        if prec == "fp64":
+            rec["gpu_launches"] = launches
+            # end to end through the public API with host buffers: every step copies all
+            # right-hand sides in from pinned memory, solves to 1e-8, copies all x back
+            rhs_host = [torch.from_numpy(p[2]).pin_memory() for p in probs]
+            x_host = [torch.empty_like(r) .pin_memory() for r in rhs_host]
+            e2e_steps, e2e_its = 2, 0
+            ranks.barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                for d, h_ in zip(rhs, rhs_host):
+                    d.copy_(h_, non_blocking=True)
+                for x in xs:
+                    x.zero_()
+                _, its, _, _ = B.solve(rhs, xs, tol=1e-8, maxit=100)
+                for h_, x in zip(x_host, xs):
+                    h_.copy_(x, non_blocking=True)
+                torch.cuda.synchronize()
+                e2e_its += max(its)
+            e2e_s = time.perf_counter() - t0
+            nbytes = sum(int(r.numel()) * 8 for r in rhs_host)
+            rec["e2e"] = {"value": whole_job_rate(N * e2e_its, e2e_s, ranks), "unit": UNIT,
+                          "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                          "note": "Batch.solve (FP64, every problem to 1e-8) from a zero guess per step; unknowns x "
+                                  "batch iterations / wall time; right-hand sides H2D from pinned memory, x D2H"}
+        out["variants"][prec] = rec
         B.close()
-    v = out["variants"]["fp64"]
+    v = out["variants"].pop("fp64")
     out["value"] = v["value"]
     out["ms_per_step"] = v["ms_per_step"]
+    out["e2e"] = v.pop("e2e")
+    out["gpu_launches"] = int(v.pop("gpu_launches"))
+    out["fp64"] = v
     out["dtype"] = "f64"
+    out["clocks"] = clock_s
     if rank == 0:
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = batched_cpu_baseline(probs)
         print(json.dumps(out))
+    ranks.close()
 
 
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class Ranks:
+    """Rank bookkeeping of an N-process run (one process per GPU, launched by
+    torchrun): a barrier around every timed region and max/sum over ranks.
+    The process group (NCCL on GPUs, gloo in the CPU tests) carries only these
+    scalars; no solver data crosses ranks."""
+
+    def __init__(self, backend: str = "nccl"):
+        import torch
+        self.torch = torch
+        self.rank, self.local_rank, self.world = dist_info()
+        self.cuda = backend == "nccl"
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.cuda:
+            self.torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+
+    def _reduce(self, v: float, op) -> float:
+        if not self.dist:
+            return float(v)
+        t = self.torch.tensor([float(v)], dtype=self.torch.float64, device="cuda" if self.cuda else "cpu")
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, v: float) -> float:
+        return self._reduce(v, self.dist.ReduceOp.MAX if self.dist else None)
+
+    def sum(self, v: float) -> float:
+        return self._reduce(v, self.dist.ReduceOp.SUM if self.dist else None)
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def batched_shard(rank: int, per_rank: int = 256):
+    """Weak scaling of the batched workload: rank r solves problems
+    [r * per_rank, (r + 1) * per_rank) of one seeded sequence, so rank 0 of
+    any run solves the single-GPU batch."""
+    return rank * per_rank, per_rank
+
+
+def whole_job_rate(units_this_rank: float, seconds_this_rank: float, ranks: "Ranks") -> float:
+    """Units processed by all ranks / the slowest rank's time."""
+    return ranks.sum(units_this_rank) / ranks.max(seconds_this_rank)
 
 
 # ----------------------------------------------------------------------------------
@@ -181,28 +284,15 @@ def run_ours(args, rank, local_rank, world):
     import torch
     import paper_2502_05279_gb300 as bmg
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks = Ranks("nccl")
     spec = WORKLOADS[args.workload]
     kind, planes, f = spec["make"]()
     n = planes.shape[-1] - 2
     N = n * n
     coef = torch.from_numpy(planes if kind == 9 else planes[:3].copy()).cuda()
     rhs = torch.from_numpy(f).cuda()
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-
-    def max_over_ranks(v: float) -> float:
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     if args.only:
         # one hierarchy, warm-up and timed cycles only: the small run profiled by ncu
@@ -282,8 +372,7 @@ def run_ours(args, rank, local_rank, world):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
 
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
+        ranks.close()
         return
 
     def dominant(prof, fp32):
@@ -343,13 +432,12 @@ def run_ours(args, rank, local_rank, world):
         p: sorted(([r["level"], r["kernel"] + ("32" if r["fp32"] else ""), round(r["launches"] / 3), round(r["ms"] / 3 * 1e3, 1)]
                    for r in v["prof"]), key=lambda e: -e[3])
         for p, v in variants.items()}
-    out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu else None
+    out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu and world == 1 else None
     print(json.dumps(out))
     for v in variants.values():
         v["h"].close()
         v["hk"].close()
-    if dist:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def measured_peak(key, fallback):
@@ -391,24 +479,76 @@ def cpu_baseline(args, kind, planes, f):
                       f"residual norm on the full {args.workload} problem; median cycle {per * 1e3:.0f} ms"}
 
 
+BATCH_SAMPLE_UNKNOWNS = 2_500_000
+
+
+def batch_sample(probs, budget: int = BATCH_SAMPLE_UNKNOWNS):
+    """The leading problems of a batch whose unknowns add up to at most
+    `budget` (at least one problem): the bounded CPU sample of the batch."""
+    out, tot = [], 0
+    for p in probs:
+        m = (p[1].shape[-1] - 2) ** 2
+        if out and tot + m > budget:
+            break
+        out.append(p)
+        tot += m
+    return out, tot
+
+
+def oracle_batch_cycles(probs, cycles):
+    """Oracle setup of every problem, then `cycles` rounds of one V(2,1) cycle
+    plus residual norm on each; returns (setup_s, per-round seconds)."""
+    from oracle import boxmg as bx
+    t0 = time.perf_counter()
+    hier = [(bx.setup(k, pl), np.zeros_like(f), f) for k, pl, f in probs]
+    setup_s = time.perf_counter() - t0
+    times = []
+    for _ in range(cycles):
+        t0 = time.perf_counter()
+        for levels, x, f in hier:
+            bx.vcycle(levels, 0, x, f)
+            bx.norm(bx.residual(levels[0].planes, x, f))
+        times.append(time.perf_counter() - t0)
+    return setup_s, times
+
+
+def batched_cpu_baseline(probs):
+    sample, m = batch_sample(probs)
+    setup_s, times = oracle_batch_cycles(sample, 3)
+    per = statistics.median(times)
+    return {"value": m / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (numpy FP64, one thread): setup ({setup_s:.1f} s) + 3 rounds of one V(2,1) cycle with "
+                      f"residual norm on the first {len(sample)} problems of the batch ({m} unknowns); median round "
+                      f"{per * 1e3:.0f} ms"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    spec = WORKLOADS[args.workload]
-    kind, planes, f = spec["make"]()
-    n = planes.shape[-1] - 2
-    steps = min(args.steps, 5 if n >= 2047 else 50)
-    setup_s, times = oracle_cycles(kind, planes, f, steps + min(args.warmup, 1))
-    times = times[min(args.warmup, 1):]
+    warm = min(args.warmup, 1)
+    if args.workload == "batched256":
+        sample, m = batch_sample(w.batched_problems(256, 5, 1.0, 32.0))
+        steps = min(args.steps, 5)
+        setup_s, times = oracle_batch_cycles(sample, steps + warm)
+        text, unknowns = BATCHED["text"], m
+        what = f"the first {len(sample)} problems of the batch ({m} unknowns)"
+    else:
+        spec = WORKLOADS[args.workload]
+        kind, planes, f = spec["make"]()
+        n = planes.shape[-1] - 2
+        steps = min(args.steps, 5 if n >= 2047 else 50)
+        setup_s, times = oracle_cycles(kind, planes, f, steps + warm)
+        text, unknowns = spec["text"], n * n
+        what = f"the full {args.workload} problem"
+    times = times[warm:]
     tot = sum(times)
-    value = n * n * len(times) / tot
-    sample = (f"{len(times)} timed V(2,1) cycles (+ {min(args.warmup, 1)} warm-up) of the oracle on the full "
-              f"{args.workload} problem (steps capped from {args.steps} to keep the CPU run to minutes); "
-              f"setup {setup_s:.1f} s")
+    value = unknowns * len(times) / tot
+    sample = (f"{len(times)} timed V(2,1) cycles (+ {warm} warm-up) of the oracle on {what} (steps capped from "
+              f"{args.steps} to keep the CPU run to minutes); setup {setup_s:.1f} s")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times), "warmup": args.warmup,
            "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic (seeded generators, no datasets)", "impl": "reference",
-           "config": {"workload": args.workload, "description": spec["text"], "unknowns": n * n},
+           "config": {"workload": args.workload, "description": text, "unknowns": unknowns},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

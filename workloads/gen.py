@@ -193,19 +193,23 @@ def lognormal_problem(n: int = 8191, std: float = 2.0, corr_len: float = 32.0,
     return 9, fe9_from_cells(k), rhs_uniform(n, seed_f)
 
 
-def batched_sizes(count: int = 256, seed: int = 5, choices=(63, 127, 255, 511, 1023)):
-    """Interior sides drawn uniformly from `choices`."""
-    u = uniform01(seed, count)
+def batched_sizes(count: int = 256, seed: int = 5, choices=(63, 127, 255, 511, 1023), first: int = 0):
+    """Interior sides of problems first .. first+count-1, drawn uniformly from
+    `choices` (one draw per problem from stream `seed`)."""
+    u = uniform01(seed, first + count)[first:]
     idx = np.minimum((u * len(choices)).astype(np.int64), len(choices) - 1)
     return [int(choices[i]) for i in idx]
 
 
 def batched_problems(count: int = 256, seed: int = 5, std: float = 1.0, corr_len: float = 32.0,
-                     choices=(63, 127, 255, 511, 1023)):
-    """Independent 9-point log-normal problems of uneven sizes; problem b uses
-    coefficient seed 10000 + 2b and RHS seed 10001 + 2b."""
+                     choices=(63, 127, 255, 511, 1023), first: int = 0):
+    """Independent 9-point log-normal problems of uneven sizes; problem b
+    (b counted from 0 over the whole sequence, this call returning
+    first .. first+count-1) uses coefficient seed 10000 + 2b and RHS seed
+    10001 + 2b."""
     out = []
-    for b, n in enumerate(batched_sizes(count, seed, choices)):
+    for j, n in enumerate(batched_sizes(count, seed, choices, first)):
+        b = first + j
         k = lognormal_cells(n, std, corr_len, 10000 + 2 * b)
         out.append((9, fe9_from_cells(k), rhs_uniform(n, 10001 + 2 * b)))
     return out
