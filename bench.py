@@ -51,13 +51,15 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernels, keyed by (workload, variant, kernel); the
-# captures and their commands are summarised in profiles/gs_rows_*_fe2047.md.
+# capture of the current kernels, keyed by (workload, kernel); the captures and
+# their commands are summarised in profiles/gs_*_fe2047.md.  A kernel missing
+# here reports traffic null.
 NCU_TRAFFIC = {
-    ("fe2047-binary1e4", "fp64", "relax"): 196.5e6,
-    ("fe2047-binary1e4", "fp32", "relax"): 95.6e6,
-    ("fe2047-binary1e4", "bf16", "relax"): 63.8e6,
+    ("fe2047-binary1e4", "k_gs_rows<double>"): 196.5e6,
+    ("fe2047-binary1e4", "k_gs_rows<float,float>"): 95.6e6,
+    ("fe2047-binary1e4", "k_gs_rows<float,bf16>"): 63.8e6,
 }
+TILE_SHAPES = ("56x32", "56x16", "56x64", "56x128", "56x8")
 
 
 BATCHED = dict(text="256 independent 9-point Q1 problems, sides uniform from {63,127,255,511,1023} (seed 5), "
@@ -296,7 +298,7 @@ def run_ours(args, rank, local_rank, world):
 
     if args.only:
         # one hierarchy, warm-up and timed cycles only: the small run profiled by ncu
-        h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov)
+        h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov, smoother=args.smoother)
         x = torch.zeros_like(rhs)
         h.time_cycles(rhs, x, args.warmup)
         ms = h.time_cycles(rhs, x, args.steps)
@@ -379,31 +381,44 @@ def run_ours(args, rank, local_rank, world):
         rows = [r for r in prof if r["kernel"] == "relax" and r["level"] == 0 and r["fp32"] == fp32]
         return rows[0] if rows else max(prof, key=lambda r: r["ms"])
 
+    sweeps_per_cycle = 3                                        # V(2,1)
+
+    def per_launch(prec, fp32):
+        """Dominant kernel's average device time per launch and the Gauss-Seidel
+        sweeps one launch performs (1/2 for the row kernel, 1 for the tile kernel)."""
+        r = dominant(variants[prec]["prof"], fp32)
+        cycles = 3
+        return r, r["ms"] / r["launches"] * 1e-3, sweeps_per_cycle * cycles / r["launches"]
+
     def roofline_fp64():
-        r = dominant(variants["fp64"]["prof"], False)
-        per_launch_s = r["ms"] / r["launches"] * 1e-3
-        flops = ALG_FLOPS_PER_POINT[kind] * N / 2.0             # one launch = half a sweep = half the grid
+        r, per_launch_s, sweeps = per_launch("fp64", False)
+        flops = ALG_FLOPS_PER_POINT[kind] * N * sweeps
         achieved = flops / per_launch_s / 1e12
         peak = fp64_rate / 1e12
         share = r["ms"] / sum(q["ms"] for q in variants["fp64"]["prof"])
-        byt = SWEEP_BYTES[("fp64", kind)] * N / 2.0
-        return {"bound": "alu", "kernel": "k_gs_rows<double> level 0 (half sweep)", "achieved": round(achieved, 4),
-                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+        byt = SWEEP_BYTES[("fp64", kind)] * N * sweeps
+        name = "k_gs_rows<double>"
+        return {"bound": "alu", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
+                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
                 "peak_source": "FP64 instruction rate measured in this run (bmg_measure_fp64_rate)",
-                "traffic": NCU_TRAFFIC.get((args.workload, "fp64", "relax")),
+                "traffic": NCU_TRAFFIC.get((args.workload, name)),
                 "alg_bytes_per_launch": byt, "hbm_gbs_equiv": round(byt / per_launch_s / 1e9, 1),
                 "time_share": round(share, 3), "avg_launch_us": round(per_launch_s * 1e6, 2)}
 
     def roofline_32(prec):
-        r = dominant(variants[prec]["prof"], True)
-        per_launch_s = r["ms"] / r["launches"] * 1e-3
-        byt = SWEEP_BYTES[(prec, kind)] * N / 2.0                # one launch = half a sweep
+        r, per_launch_s, sweeps = per_launch(prec, True)
+        byt = SWEEP_BYTES[(prec, kind)] * N * sweeps
         achieved = byt / per_launch_s / 1e9
         peak = measured_peak("hbm_gbs", 6800.0)
-        return {"bound": "hbm", "kernel": f"k_gs_rows<float,{'bf16' if prec == 'bf16' else 'float'}> level 0 (half sweep)",
+        st = "bf16" if prec == "bf16" else "float"
+        tuned = variants[prec]["tuned"][0]
+        name = (f"k_gs_strip<{st}> {TILE_SHAPES[tuned - 16]}" if tuned >= 16 else f"k_gs_rows<float,{st}>")
+        share = r["ms"] / sum(q["ms"] for q in variants[prec]["prof"])
+        return {"bound": "hbm", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
                 "achieved": round(achieved, 1), "peak": peak[0], "unit": "GB/s", "frac": round(achieved / peak[0], 4),
-                "peak_source": peak[1], "traffic": NCU_TRAFFIC.get((args.workload, prec, "relax")),
-                "avg_launch_us": round(per_launch_s * 1e6, 2)}
+                "peak_source": peak[1], "traffic": NCU_TRAFFIC.get((args.workload, name)),
+                "alg_bytes_per_launch": byt, "time_share": round(share, 3), "avg_launch_us": round(per_launch_s * 1e6, 2)}
 
     v64 = variants["fp64"]
     value = world * N * args.steps / (v64["ms"] * 1e-3)
@@ -566,6 +581,7 @@ def main():
     ap.add_argument("--only", choices=("fp64", "fp32", "bf16"), default=None,
                     help="time one hierarchy's cycles only (short run for profilers)")
     ap.add_argument("--krylov", choices=("none", "fcg"), default="none", help="solve mode for --only")
+    ap.add_argument("--smoother", default="auto", help="FP32 Gauss-Seidel kernel for --only (auto, rows, tile0..4)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

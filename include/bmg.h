@@ -92,7 +92,17 @@ typedef struct {
                            BMG_KRYLOV_FCG: flexible CG with one cycle as preconditioner */
   const void* mlp;      /* bmg_mlp* for interp = BMG_INTERP_LEARNED, else NULL */
   void* stream;         /* cudaStream_t for setup and every later call on the hierarchy */
+  int smoother;         /* Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all choices
+                           compute the same bits): BMG_SMOOTHER_AUTO (0, default; the autotuner
+                           picks per level when use_graph = 1, else the row kernel),
+                           BMG_SMOOTHER_ROWS (row kernel, in place), or BMG_SMOOTHER_TILE + s
+                           (one-pass tile kernel with tile shape s = 0 .. 4 on every level
+                           outside the level-fused tail and the coarsest) */
 } bmg_opts;
+
+#define BMG_SMOOTHER_AUTO 0
+#define BMG_SMOOTHER_ROWS 1
+#define BMG_SMOOTHER_TILE 2
 
 /* ---- whole solver ------------------------------------------------------ */
 
@@ -150,8 +160,12 @@ typedef struct {
 } bmg_prof_row;
 int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_prof_row* rows, int cap);
 
-/* Row-kernel cluster size the setup autotuner chose for level `level` of the
- * cycle the hierarchy runs (FP64 or FP32), or 0 (default; not tuned). */
+/* Gauss-Seidel kernel the setup autotuner chose for level `level` of the cycle
+ * the hierarchy runs (FP64 or FP32): the row kernel's cluster size (1, 2, 4,
+ * 8), BMG_TILE_SWEEP + s when the one-pass tile kernel with tile shape s won
+ * (FP32 levels only; shapes 0 .. 4: warp strips of 56 x 32, 16, 64, 128, 8
+ * points), or 0 (default; not tuned).  Every choice computes the same bits. */
+#define BMG_TILE_SWEEP 16
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 
 /* Number of levels, and the size n of level l (0 = finest). */

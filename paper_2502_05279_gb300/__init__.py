@@ -8,5 +8,5 @@ missing or cannot load.
 from ._lib import (  # noqa: F401
     BMG_BF16_IR, BMG_FP32_IR, BMG_FP64, Batch, BmgError, Hierarchy, coarse_factor, coarse_solve, dendy_interp,
     interp_correct, learned_interp, fill_uniform, lib, library_path, measure_fp64_rate, Mlp, rap, relax,
-    resid_restrict, residual,
+    resid_restrict, residual, TILE_SWEEP,
 )

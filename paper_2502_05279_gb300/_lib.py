@@ -44,13 +44,16 @@ class ProfRow(ctypes.Structure):
 KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
                 "ir_update", "ir_residual", "fcg", "tail")
 _KRYLOV = {"none": 0, "fcg": 1}
+# Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
+_SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(5)}}
+TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -131,12 +134,13 @@ class Hierarchy:
 
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
-                 use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None):
+                 use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto"):
         n = _n_of(coef)
         self.n, self.kind, self.precision = n, kind, precision
         st = Stencil(kind, _ptr(coef, name="coef"))
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
-                 int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream())
+                 int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
+                 _SMOOTHER[smoother])
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -71,6 +71,8 @@ struct Level {
   float* ci32 = nullptr;
   float* x32 = nullptr;
   float* f32 = nullptr;
+  int tile32 = -1;        // FP32 sweeps: -1 row kernel (in place), else tile shape of the one-pass kernel
+  float* x32b = nullptr;  // second iterate of a tile-swept level (sweeps alternate x32 <-> x32b)
 };
 
 StencilView<double, double> view64(const Level& L) {
@@ -91,6 +93,7 @@ StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
 struct bmg_hierarchy {
   int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3, krylov = 0;
   int interp = BMG_INTERP_DENDY, interp_used = BMG_INTERP_DENDY;
+  int smoother = BMG_SMOOTHER_AUTO;
   const void* mlp = nullptr;
   double factor_learned = 0.0, factor_dendy = 0.0;
   double* kr = nullptr;   // flexible CG vectors r, z, p, q (FP64, (n+2)^2 each)
@@ -180,21 +183,36 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu2, done, s, L.cl64); });
 }
 
+// Sweeps of an FP32 level.  Row kernel: in place on x32.  One-pass tile kernel:
+// each sweep reads *cur and writes the other of x32 / x32b, and *cur follows.
 template <typename S>
-void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, const int* done) {
+void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, float** cur, const int* done) {
   Level& L = h->lv[l];
-  step(h, l, BMG_K_RELAX, 1, [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws, L.cl32); });
+  if (L.tile32 < 0) {
+    step(h, l, BMG_K_RELAX, 1,
+         [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws, L.cl32); });
+    return;
+  }
+  step(h, l, BMG_K_RELAX, 1, [&] {
+    for (int k = 0; k < sweeps; ++k) {
+      float* dst = *cur == L.x32 ? L.x32b : L.x32;
+      launch_gs_tile(v, (const float*)L.f32, (const float*)*cur, dst, L.tile32, done, h->ws);
+      *cur = dst;
+    }
+  });
 }
 
 template <typename S>
-void restrict32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, const int* done) {
+void restrict32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, const float* x, const int* done) {
   Level& L = h->lv[l];
   Level& C = h->lv[l + 1];
   step(h, l, BMG_K_RESID_RESTRICT, 1,
-       [&] { launch_resid_restrict(v, L.kind, (const float*)L.ci32, (const float*)L.x32, (const float*)L.f32,
-                                   C.f32, C.x32, done, h->ws); });
+       [&] { launch_resid_restrict(v, L.kind, (const float*)L.ci32, x, (const float*)L.f32, C.f32, C.x32, done,
+                                   h->ws); });
 }
 
+// The FP32 cycle leaves every level's result in x32.  On a tile-swept level the
+// interpolation writes the array from which nu2 alternating sweeps end in x32.
 void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   Level& L = h->lv[l];
   cudaStream_t s = h->ws;
@@ -208,34 +226,57 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
     return;
   }
   Level& C = h->lv[l + 1];
+  float* cur = L.x32;
   if (L.bf16) {
-    relax32(h, viewbf(L), l, h->nu1, done);
-    restrict32(h, viewbf(L), l, done);
+    relax32(h, viewbf(L), l, h->nu1, &cur, done);
+    restrict32(h, viewbf(L), l, cur, done);
   } else {
-    relax32(h, view32(L), l, h->nu1, done);
-    restrict32(h, view32(L), l, done);
+    relax32(h, view32(L), l, h->nu1, &cur, done);
+    restrict32(h, view32(L), l, cur, done);
   }
   vcycle32(h, l + 1, done);
-  step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_correct<float>(L.n, L.ci32, C.x32, L.x32, done, s); });
+  float* dst = L.tile32 >= 0 && (h->nu2 & 1) ? L.x32b : L.x32;
+  step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_to<float>(L.n, L.ci32, C.x32, cur, dst, done, s); });
+  cur = dst;
   if (L.bf16)
-    relax32(h, viewbf(L), l, h->nu2, done);
+    relax32(h, viewbf(L), l, h->nu2, &cur, done);
   else
-    relax32(h, view32(L), l, h->nu2, done);
+    relax32(h, view32(L), l, h->nu2, &cur, done);
 }
 
-// Autotuner of the solo hierarchy: for every 9-point level with n >= 127 time
-// two Gauss-Seidel sweeps of the row kernel for each admissible cluster size
-// (1, 2, 4, 8 CTAs per row, at least a warp of pairs per CTA) on scratch
-// iterates with the level's real stencil, and keep the fastest.  The choice
-// only changes how a row is split over CTAs, never a result bit.  Results are
+// Device milliseconds of fn(), after one untimed call.
+template <typename F>
+int time_call(cudaStream_t s, F&& fn, float* ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  fn();
+  cudaEventRecord(e0, s);
+  fn();
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  return BMG_OK;
+}
+
+// Autotuner of the solo hierarchy.  For every 9-point level with n >= 127 it
+// times two Gauss-Seidel sweeps on scratch iterates with the level's real
+// stencil: the row kernel for each admissible cluster size (1, 2, 4, 8 CTAs
+// per row, at least a warp of pairs per CTA) and, for FP32 levels, the
+// one-pass tile kernel for each tile shape; the fastest is kept.  Every
+// candidate computes the same bits; only the speed differs.  Results are
 // cached per (n, compute type, storage type) for the life of the process.
 template <typename T, typename S>
-int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out) {
-  static std::map<std::tuple<int, int, int>, int> cache;
+int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* ms_out = nullptr) {
+  static std::map<std::tuple<int, int, int>, std::pair<int, float>> cache;
   auto key = std::make_tuple(v.n, (int)sizeof(T), (int)sizeof(S));
   auto it = cache.find(key);
   if (it != cache.end()) {
-    *best_out = it->second;
+    *best_out = it->second.first;
+    if (ms_out) *ms_out = it->second.second;
     return BMG_OK;
   }
   const int base = rows_cluster<T>(v.n);
@@ -243,31 +284,77 @@ int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out) {
   T* scratch = nullptr;
   CK(cudaMalloc((void**)&scratch, 2 * ps * sizeof(T)));
   CK(cudaMemsetAsync(scratch, 0, 2 * ps * sizeof(T), s));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_cl = base;
-  for (int cl = base; cl <= 8; cl *= 2) {
+  int best_cl = base, rc = BMG_OK;
+  for (int cl = base; cl <= 8 && !rc; cl *= 2) {
     if (cl > base && ((v.n + 1) / 2 + cl - 1) / cl < 32) break;
-    launch_gs(v, 9, (const T*)(scratch + ps), scratch, 1, (const int*)nullptr, s, cl);   // warm-up
-    cudaEventRecord(e0, s);
-    launch_gs(v, 9, (const T*)(scratch + ps), scratch, 2, (const int*)nullptr, s, cl);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
     float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
+    rc = time_call(s, [&] { launch_gs(v, 9, (const T*)(scratch + ps), scratch, 2, (const int*)nullptr, s, cl); }, &ms);
+    ms *= 0.5f;   // per sweep
     if (ms < best) {
       best = ms;
       best_cl = cl;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaFree(scratch);
-  CK(cudaGetLastError());
-  cache[key] = best_cl;
+  if (rc) return rc;
+  cache[key] = {best_cl, best};
   *best_out = best_cl;
+  if (ms_out) *ms_out = best;
+  return BMG_OK;
+}
+
+template <typename S>
+int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, float* ms_out) {
+  static std::map<std::pair<int, int>, std::pair<int, float>> cache;
+  auto key = std::make_pair(v.n, (int)sizeof(S));
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *best_out = it->second.first;
+    *ms_out = it->second.second;
+    return BMG_OK;
+  }
+  size_t ps = plane_size(v.n);
+  float* scratch = nullptr;
+  CK(cudaMalloc((void**)&scratch, 3 * ps * sizeof(float)));
+  CK(cudaMemsetAsync(scratch, 0, 3 * ps * sizeof(float), s));
+  const float* f = scratch + 2 * ps;
+  float best = 1e30f;
+  int best_shape = 0, rc = BMG_OK;
+  for (int shape = 0; shape < GS_TILE_SHAPES && !rc; ++shape) {
+    float ms = 0;
+    rc = time_call(s, [&] {
+      launch_gs_tile(v, f, scratch, scratch + ps, shape, (const int*)nullptr, s);
+      launch_gs_tile(v, f, scratch + ps, scratch, shape, (const int*)nullptr, s);
+    }, &ms);
+    ms *= 0.5f;   // per sweep
+    if (ms < best) {
+      best = ms;
+      best_shape = shape;
+    }
+  }
+  cudaFree(scratch);
+  if (rc) return rc;
+  cache[key] = {best_shape, best};
+  *best_out = best_shape;
+  *ms_out = best;
+  return BMG_OK;
+}
+
+// Row kernel vs one-pass tile kernel for an FP32 level; allocates the second
+// iterate when the tile kernel wins.
+template <typename S>
+int tune_level32(Level& L, const StencilView<float, S>& v, cudaStream_t s) {
+  float ms_rows = 0, ms_tile = 0;
+  int shape = 0, rc = tune_rows(v, s, &L.cl32, &ms_rows);
+  if (!rc) rc = tune_tile(v, s, &shape, &ms_tile);
+  if (rc) return rc;
+  if (ms_tile < ms_rows) {
+    size_t ps = plane_size(L.n);
+    if ((rc = dalloc(&L.x32b, ps))) return rc;
+    CK(cudaMemsetAsync(L.x32b, 0, ps * sizeof(float), s));
+    L.tile32 = shape;
+  }
   return BMG_OK;
 }
 
@@ -304,6 +391,21 @@ int build_tail(bmg_hierarchy* h, int lmin) {
   return BMG_OK;
 }
 
+// BMG_SMOOTHER_TILE + s: the tile kernel with shape s on every 9-point level
+// but the coarsest (levels that end up in the level-fused tail ignore it).
+int force_tile(bmg_hierarchy* h) {
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    Level& L = h->lv[l];
+    if (L.kind != 9) continue;
+    size_t ps = plane_size(L.n);
+    int rc = dalloc(&L.x32b, ps);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(L.x32b, 0, ps * sizeof(float), h->ws));
+    L.tile32 = h->smoother - BMG_SMOOTHER_TILE;
+  }
+  return BMG_OK;
+}
+
 int autotune_solo(bmg_hierarchy* h) {
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
@@ -311,10 +413,12 @@ int autotune_solo(bmg_hierarchy* h) {
     int rc = BMG_OK;
     if (h->precision == BMG_FP64)
       rc = tune_rows(view64(L), h->ws, &L.cl64);
+    else if (h->smoother != BMG_SMOOTHER_AUTO)
+      rc = L.tile32 >= 0 ? BMG_OK : L.bf16 ? tune_rows(viewbf(L), h->ws, &L.cl32) : tune_rows(view32(L), h->ws, &L.cl32);
     else if (L.bf16)
-      rc = tune_rows(viewbf(L), h->ws, &L.cl32);
+      rc = tune_level32(L, viewbf(L), h->ws);
     else
-      rc = tune_rows(view32(L), h->ws, &L.cl32);
+      rc = tune_level32(L, view32(L), h->ws);
     if (rc) return rc;
   }
   return BMG_OK;
@@ -424,6 +528,7 @@ void free_level(Level& L) {
   cudaFree(L.od32);
   cudaFree(L.ci32);
   cudaFree(L.x32);
+  cudaFree(L.x32b);
   cudaFree(L.f32);
   L = Level{};
 }
@@ -596,6 +701,11 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     h->interp = o->interp;
     h->mlp = o->mlp;
     h->user = (cudaStream_t)o->stream;
+    h->smoother = o->smoother;
+  }
+  if (h->smoother < BMG_SMOOTHER_AUTO || h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES) {
+    delete h;
+    return set_error(BMG_EINVAL, "bmg_setup: bad smoother %d", h->smoother);
   }
   if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
       h->nu1 < 0 || h->nu2 < 0 || h->interp < 0 || h->interp > 1 || (h->interp == BMG_INTERP_LEARNED && !h->mlp) ||
@@ -610,6 +720,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = setup_impl(h, A, nx, o);
+  if (!rc && h->precision != BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
   if (!rc && h->use_graph) rc = autotune_solo(h);
   if (!rc && h->use_graph) rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
   if (!rc) rc = ensure_ctl(h, 64);
@@ -647,6 +758,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level) {
   if (!h || level < 0 || level >= h->nlev) return set_error(BMG_EINVAL, "bmg_tuned_cluster: bad level");
   const Level& L = h->lv[level];
+  if (h->precision != BMG_FP64 && L.tile32 >= 0) return BMG_TILE_SWEEP + L.tile32;
   return h->precision == BMG_FP64 ? L.cl64 : L.cl32;
 }
 
@@ -1380,6 +1492,7 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   bmg_opts so{};
   if (o) so = *o;
   so.use_graph = 0;
+  so.smoother = BMG_SMOOTHER_AUTO;
   if (o) {
     B->precision = o->precision;
     if (o->nu1 || o->nu2) {

@@ -164,6 +164,146 @@ __device__ __forceinline__ void gs_checker_body(const StencilView<T, S>& v, cons
   gs_point<T, S, false>(v, f, x, (size_t)j * v.ld + i);
 }
 
+// ---- four-colour sweep in one pass (FP32 compute): warp strips ------------------------
+// A warp owns the strip of 56 x TY points i in [i0, i0 + 56), j in [j0, j1),
+// i0 = 1 + 56 sx, j0 = 1 + TY sy, j1 = j0 + TY (i0, j0 odd; TY even), and
+// produces the values the colour-by-colour sweep leaves there.  Lane l holds
+// the local columns c = 2l (odd i) and 2l + 1 (even i), c = i - (i0 - 4), so
+// the warp covers i in [i0 - 4, i0 + 60).  A colour's update at p reads the
+// new values of the earlier colours and the old values of the later ones, so
+// each colour is computed on the columns its successors read:
+//   c1 (odd i, odd j)    on c in [2, 62]     c3 (odd i, even j)   on c in [4, 60]
+//   c2 (even i, odd j)   on c in [3, 61]     c4 (even i, even j)  on c in [5, 59]
+// and the warp walks down its rows: the odd row a (c1 then c2, reading the old
+// even rows a +- 1), then the even row a - 1 (c3 then c4, reading the new odd
+// rows a - 2 and a).  The odd rows j0 and j1 border the strips above and below
+// and are computed by both.  Every recomputed value takes the same operands in
+// the same order as in the colour-by-colour sweep, so it is bit-identical;
+// values come from xin and the strip's points go to xout (xout != xin), so no
+// warp reads what another wrote in this launch.  Same-row neighbours come from
+// the adjacent lane by shuffle; the rows a - 2 .. a + 1 live in registers and
+// the rows a + 2, a + 3 are loaded while row a is computed.
+template <typename S>
+struct StripRow {           // one row of the strip: lane values at c = 2l (.a) and 2l + 1 (.b)
+  float xa, xb, fa, fb, da, db;
+  S wa, wb, sa, sb, swa, swb, nwa, nwb;
+};
+
+template <typename S>
+__device__ __forceinline__ void strip_load(const StencilView<float, S>& v, const float* __restrict__ f,
+                                           const float* __restrict__ xin, int ic, int j, StripRow<S>& R) {
+  // ic: absolute i of this lane's column c = 2l
+  const int n = v.n, ld = v.ld;
+  const bool rowin = j <= n + 1;
+  const bool ina = rowin && ic >= 0 && ic <= n + 1, inb = rowin && ic + 1 >= 0 && ic + 1 <= n + 1;
+  const size_t pa = ina ? (size_t)j * ld + ic : 0, pb = inb ? (size_t)j * ld + ic + 1 : 0;
+  R.xa = ina ? xin[pa] : 0.f;
+  R.xb = inb ? xin[pb] : 0.f;
+  R.fa = ina ? f[pa] : 0.f;
+  R.fb = inb ? f[pb] : 0.f;
+  R.da = ina ? v.D[pa] : 0.f;
+  R.db = inb ? v.D[pb] : 0.f;
+  R.wa = ina ? v.W[pa] : S(0.f);
+  R.wb = inb ? v.W[pb] : S(0.f);
+  R.sa = ina ? v.S_[pa] : S(0.f);
+  R.sb = inb ? v.S_[pb] : S(0.f);
+  R.swa = ina ? v.SW[pa] : S(0.f);
+  R.swb = inb ? v.SW[pb] : S(0.f);
+  R.nwa = ina ? v.NW[pa] : S(0.f);
+  R.nwb = inb ? v.NW[pb] : S(0.f);
+}
+
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// The two colours of row M (rows L below, U above): first the odd-i points
+// (lane value a), then the even-i points (lane value b), each in the order
+// W, E, S, N, SW, NE, NW, SE; oka / okb say whether this lane's points are
+// updated.
+template <typename S>
+__device__ __forceinline__ void strip_row(const StripRow<S>& L, StripRow<S>& M, const StripRow<S>& U, bool oka,
+                                          bool okb) {
+  {   // odd-i point c = 2l: same-row neighbours c - 1 (lane l - 1's b) and c + 1 (own b)
+    const float xw = shfl_up1(M.xb), xsw = shfl_up1(L.xb), xnw = shfl_up1(U.xb);
+    float s = M.fa;
+    s = rsub(s, rmul(cvt<float>(M.wa), xw));
+    s = rsub(s, rmul(cvt<float>(M.wb), M.xb));
+    s = rsub(s, rmul(cvt<float>(M.sa), L.xa));
+    s = rsub(s, rmul(cvt<float>(U.sa), U.xa));
+    s = rsub(s, rmul(cvt<float>(M.swa), xsw));
+    s = rsub(s, rmul(cvt<float>(U.swb), U.xb));
+    s = rsub(s, rmul(cvt<float>(M.nwa), xnw));
+    s = rsub(s, rmul(cvt<float>(L.nwb), L.xb));
+    const float xn = rmul(s, M.da);
+    M.xa = oka ? xn : M.xa;
+  }
+  {   // even-i point c = 2l + 1: neighbours c - 1 (own a, new) and c + 1 (lane l + 1's a)
+    const float xe = shfl_dn1(M.xa), we = shfl_dn1(cvt<float>(M.wa));
+    const float xne = shfl_dn1(U.xa), swne = shfl_dn1(cvt<float>(U.swa));
+    const float xse = shfl_dn1(L.xa), nwse = shfl_dn1(cvt<float>(L.nwa));
+    float s = M.fb;
+    s = rsub(s, rmul(cvt<float>(M.wb), M.xa));
+    s = rsub(s, rmul(we, xe));
+    s = rsub(s, rmul(cvt<float>(M.sb), L.xb));
+    s = rsub(s, rmul(cvt<float>(U.sb), U.xb));
+    s = rsub(s, rmul(cvt<float>(M.swb), L.xa));
+    s = rsub(s, rmul(swne, xne));
+    s = rsub(s, rmul(cvt<float>(M.nwb), U.xa));
+    s = rsub(s, rmul(nwse, xse));
+    const float xn = rmul(s, M.db);
+    M.xb = okb ? xn : M.xb;
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void strip_store(float* __restrict__ xout, int n, int ld, int ic, int j, bool own,
+                                            const StripRow<S>& R) {
+  if (!own || j > n) return;
+  const size_t p = (size_t)j * ld + ic;
+  if (ic <= n) xout[p] = R.xa;
+  if (ic + 1 <= n) xout[p + 1] = R.xb;
+}
+
+template <typename S, int TY>
+__device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, const float* __restrict__ f,
+                                              const float* __restrict__ xin, float* __restrict__ xout, int sx,
+                                              int sy) {
+  static_assert(TY % 2 == 0, "strip height must be even");
+  const int n = v.n, ld = v.ld;
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 56 * sx, j0 = 1 + TY * sy, j1 = j0 + TY;
+  const int ic = i0 - 4 + 2 * lane;                // i of this lane's odd column
+  // update columns per colour (c = 2l or 2l + 1), clipped to the grid
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
+  const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
+  const bool own = lane >= 2 && lane <= 29;        // c in [4, 59]: the strip's own columns
+  StripRow<S> r0, r1, r2, r3, p0, p1;              // rows a - 2 .. a + 1 and a + 2, a + 3
+  strip_load(v, f, xin, ic, j0 - 1, r1);
+  strip_load(v, f, xin, ic, j0, r2);
+  strip_load(v, f, xin, ic, j0 + 1, r3);
+#pragma unroll 1
+  for (int m = 0; m <= TY / 2; ++m) {
+    const int a = j0 + 2 * m;                      // odd row
+    if (m < TY / 2) {
+      strip_load(v, f, xin, ic, a + 2, p0);
+      strip_load(v, f, xin, ic, a + 3, p1);
+    }
+    if (a <= n) {
+      strip_row(r1, r2, r3, c1, c2);               // row a: c1, c2
+      if (a < j1) strip_store(xout, n, ld, ic, a, own, r2);
+    }
+    if (m >= 1 && a - 1 <= n) {
+      strip_row(r0, r1, r2, c3, c4);               // row a - 1: c3, c4
+      strip_store(xout, n, ld, ic, a - 1, own, r1);
+    }
+    r0 = r2;
+    r1 = r3;
+    r2 = p0;
+    r3 = p1;
+  }
+}
+
 // ---- residual + restriction ------------------------------------------------------------
 // A CTA owns a TXC x TYC tile of coarse points; it forms the residual on the
 // (2 TXC + 1) x (2 TYC + 1) fine block under the tile in shared memory (each
@@ -211,32 +351,34 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
 
 // ---- interpolation + correction ----------------------------------------------------------
 // One thread per coarse cell (ic, jc), 1..nc+1: its coincident, x-edge, y-edge
-// and centre fine points.  x + (P e)_p, the interpolated value formed first.
+// and centre fine points.  xout = xin + (P e)_p, the interpolated value formed
+// first; xin and xout may be the same array (every point is read and written by
+// the same thread only).
 template <typename T>
 __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, const T* __restrict__ ec,
-                                            T* __restrict__ x, int ic, int jc) {
+                                            const T* xin, T* xout, int ic, int jc) {
   int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
   if (ic < 1 || jc < 1 || ic > nc + 1 || jc > nc + 1) return;
   size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
   T e_sw = ec[pc - ldc - 1], e_se = ec[pc - ldc], e_nw = ec[pc - 1], e_ne = ec[pc];
   size_t pf = (size_t)(2 * jc) * ld + 2 * ic;   // coincident fine point
-  if (ic <= nc && jc <= nc) x[pf] = radd(x[pf], e_ne);
+  if (ic <= nc && jc <= nc) xout[pf] = radd(xin[pf], e_ne);
   if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
     T t = rmul(ci[CI_LL * psc + pc], e_nw);
     t = radd(t, rmul(ci[CI_LR * psc + pc], e_ne));
-    x[pf - 1] = radd(x[pf - 1], t);
+    xout[pf - 1] = radd(xin[pf - 1], t);
   }
   if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
     T t = rmul(ci[CI_LB * psc + pc], e_se);
     t = radd(t, rmul(ci[CI_LA * psc + pc], e_ne));
-    x[pf - ld] = radd(x[pf - ld], t);
+    xout[pf - ld] = radd(xin[pf - ld], t);
   }
   {                                               // centre (2ic-1, 2jc-1)
     T t = rmul(ci[CI_LSW * psc + pc], e_sw);
     t = radd(t, rmul(ci[CI_LSE * psc + pc], e_se));
     t = radd(t, rmul(ci[CI_LNW * psc + pc], e_nw));
     t = radd(t, rmul(ci[CI_LNE * psc + pc], e_ne));
-    x[pf - ld - 1] = radd(x[pf - ld - 1], t);
+    xout[pf - ld - 1] = radd(xin[pf - ld - 1], t);
   }
 }
 
@@ -480,7 +622,7 @@ __device__ __forceinline__ void tail_body(const TailDesc<T>& d, int top_kind) {
     const LevelDesc<T, T>& q = d.lv[l];
     const int nc = (q.v.n - 1) / 2;
     for (int k = threadIdx.x; k < (nc + 1) * (nc + 1); k += blockDim.x)
-      interp_body<T>(q.v.n, q.ci, q.xc, q.x, k % (nc + 1) + 1, k / (nc + 1) + 1);
+      interp_body<T>(q.v.n, q.ci, q.xc, q.x, q.x, k % (nc + 1) + 1, k / (nc + 1) + 1);
     __syncthreads();
     relax_block<T>(q, l == 0 ? top_kind : 9, d.nu2);
   }

@@ -40,7 +40,7 @@ template <typename T, typename S>
 __global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  interp_body<T>(q.v.n, q.ci, q.xc, q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
+  interp_body<T>(q.v.n, q.ci, q.xc, q.x, q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
                  blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 

@@ -27,6 +27,20 @@ __global__ void k_gs_checker(StencilView<T, S> v, const T* __restrict__ f, T* x,
   gs_checker_body<T, S>(v, f, x, c, blockIdx.x, blockIdx.y);
 }
 
+// One warp per strip of 56 x TY points; warp g of the grid takes strip
+// (g % nbx, g / nbx), so the warps of a CTA take neighbouring strips of one band.
+constexpr int STRIP_WARPS = 4;
+template <typename S, int TY>
+__global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float, S> v, const float* __restrict__ f,
+                                                               const float* __restrict__ xin,
+                                                               float* __restrict__ xout, const int* done) {
+  if (stopped(done)) return;
+  const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
+  const int g = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
+  if (g >= nbx * nby) return;                     // whole warps only
+  gs_strip_body<S, TY>(v, f, xin, xout, g % nbx, g / nbx);
+}
+
 template <typename T, typename S, bool NINE>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
                                                             const T* __restrict__ x, const T* __restrict__ f,
@@ -37,10 +51,11 @@ __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v
 }
 
 template <typename T>
-__global__ void k_interp_correct(int n, const T* __restrict__ ci, const T* __restrict__ ec, T* __restrict__ x,
+__global__ void k_interp_correct(int n, const T* __restrict__ ci, const T* __restrict__ ec, const T* xin, T* xout,
                                  const int* done) {
   if (stopped(done)) return;
-  interp_body<T>(n, ci, ec, x, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+  interp_body<T>(n, ci, ec, xin, xout, blockIdx.x * blockDim.x + threadIdx.x + 1,
+                 blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
 template <typename T, typename S, bool NINE>
@@ -180,10 +195,35 @@ void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, co
   count_launch();
 }
 
+template <typename S, int TY>
+static void strip_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                         const int* done, cudaStream_t s) {
+  const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
+  k_gs_strip<S, TY><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, s>>>(v, f, xin, xout, done);
+  count_launch();
+}
+
+template <typename S>
+void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip_launch<S, 16>(v, f, xin, xout, done, s); break;
+    case 2: strip_launch<S, 64>(v, f, xin, xout, done, s); break;
+    case 3: strip_launch<S, 128>(v, f, xin, xout, done, s); break;
+    case 4: strip_launch<S, 8>(v, f, xin, xout, done, s); break;
+    default: strip_launch<S, 32>(v, f, xin, xout, done, s); break;
+  }
+}
+
 template <typename T>
 void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s) {
+  launch_interp_to<T>(n, ci, ec, x, x, done, s);
+}
+
+template <typename T>
+void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s) {
   int nc = (n - 1) / 2;
-  k_interp_correct<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, x, done);
+  k_interp_correct<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
   count_launch();
 }
 
@@ -265,6 +305,14 @@ BMG_INST(float, __nv_bfloat16)
 #undef BMG_INST
 template void launch_interp_correct<double>(int, const double*, const double*, double*, const int*, cudaStream_t);
 template void launch_interp_correct<float>(int, const float*, const float*, float*, const int*, cudaStream_t);
+template void launch_gs_tile<float>(const StencilView<float, float>&, const float*, const float*, float*, int,
+                                    const int*, cudaStream_t);
+template void launch_gs_tile<__nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, const float*, const float*,
+                                            float*, int, const int*, cudaStream_t);
+template void launch_interp_to<double>(int, const double*, const double*, const double*, double*, const int*,
+                                       cudaStream_t);
+template void launch_interp_to<float>(int, const float*, const float*, const float*, float*, const int*,
+                                      cudaStream_t);
 template void launch_coarse_solve<double>(int, const double*, const double*, double*, double*, const int*,
                                           cudaStream_t);
 template void launch_coarse_solve<float>(int, const double*, const float*, float*, double*, const int*,

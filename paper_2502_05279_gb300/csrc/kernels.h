@@ -38,11 +38,22 @@ void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od3
 template <typename T, typename S>
 void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
                int cl = 0);   // cl: row-kernel cluster size, 0 = the smallest that covers a row
+// One four-colour Gauss-Seidel sweep of a 9-point FP32 level in one launch:
+// reads xin, writes every interior point of xout (xout != xin; the ghost ring
+// of xout is not written).  One warp per strip of 56 x TY points, TY = 32,
+// 16, 64, 128, 8 for shapes 0 .. 4.
+constexpr int GS_TILE_SHAPES = 5;
+template <typename S>
+void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s);
 template <typename T, typename S>
 void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,
                            T* xc, const int* done, cudaStream_t s);
 template <typename T>
 void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s);
+// xout = xin + P ec over every interior fine point (xin may equal xout).
+template <typename T>
+void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s);
 // r = f - A x (r may be NULL) with per-block partial sums of r^2 (partials may
 // be NULL); returns the number of partials written.
 template <typename T, typename S>

@@ -380,3 +380,80 @@ def test_level_fused_tail_is_bitwise_the_stepwise_cycle(bmg, precision):
                 assert any(r["kernel"] == "tail" for r in prof), (case, n)
             h.close()
         assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+# ---- one-pass four-colour sweep (FP32 levels, warp strips) -----------------------------
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("shape", ["tile0", "tile1", "tile2", "tile3", "tile4"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_tile_sweep_inner_cycle_bitwise(bmg, precision, nbf, shape, graph):
+    """The one-pass kernel recomputes halo points redundantly and alternates
+    two iterates; every level's result must still be the oracle's bits."""
+    for case, n in [("binary", 255), ("lognormal", 127), ("poisson", 63)]:
+        kind, planes, f = problem(case, n)
+        levels = bx.setup(kind, planes)
+        r32 = w.rhs_uniform(n, 95).astype(np.float32)
+        want = mx.inner_cycle(mx.lower(levels, nbf), r32)
+        h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision, smoother=shape,
+                          use_graph=graph)
+        got = host(h.inner_cycle(dev(r32, torch.float32)))
+        assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0)), (case, n)
+        if kind == 9:
+            assert h.tuned_cluster(0) == bmg.TILE_SWEEP + int(shape[-1])
+        h.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (1, 2), (3, 0), (0, 3), (2, 2)])
+def test_tile_sweep_any_sweep_counts_equal_row_kernel(bmg, nu1, nu2):
+    """Odd and even numbers of alternating sweeps before and after the coarse
+    correction: the one-pass refinement solve equals the row-kernel one."""
+    kind, planes, f = problem("lognormal", 255)
+    outs = []
+    for sm in ("rows", "tile"):
+        h = bmg.Hierarchy(kind, dev(planes), precision="fp32", smoother=sm, nu1=nu1, nu2=nu2, use_graph=False)
+        x, it, rr, ok = h.solve(dev(f), tol=1e-9, maxit=60)
+        outs.append((host(x), h.history()))
+        h.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+def test_tile_sweep_fcg_and_bf16_solve_match_oracle(bmg):
+    kind, planes, f = problem("binary", 255)
+    levels = bx.setup(kind, planes)
+    for precision, nbf in (("fp32", 0), ("bf16", 2)):
+        xw, hw = mx.solve_fcg_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=200)
+        h = bmg.Hierarchy(kind, dev(planes), precision=precision, krylov="fcg", smoother="tile")
+        x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+        assert ok and it == len(hw) - 1
+        assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+        check_history(h.history(), hw)
+        h.close()
+
+
+def test_autotuner_picks_a_valid_kernel_per_level(bmg):
+    kind, planes, f = problem("lognormal", 511)
+    for precision in ("fp32", "bf16"):
+        h = bmg.Hierarchy(kind, dev(planes), precision=precision)
+        for l in range(h.num_levels - 1):
+            c = h.tuned_cluster(l)
+            assert c in (0, 1, 2, 4, 8) or bmg.TILE_SWEEP <= c < bmg.TILE_SWEEP + 5, (l, c)
+        assert h.tuned_cluster(0) != 0
+        h.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+def test_bench_workload_fp32_cycle_bitwise(bmg, precision, nbf):
+    """2047^2 bench workload: one FP32 (BF16) inner cycle in the launch
+    configuration the bench times (autotuned kernels, graph), and with the
+    one-pass kernel forced, against the oracle over every grid point."""
+    kind, planes, f = w.binary_contrast_problem(2047, 16, seed_k=2, seed_f=3)
+    levels = bx.setup(kind, planes)
+    r32 = w.rhs_uniform(2047, 96).astype(np.float32)
+    want = mx.inner_cycle(mx.lower(levels, nbf), r32)
+    for sm in ("auto", "tile"):
+        h = bmg.Hierarchy(kind, dev(planes), precision=precision, smoother=sm)
+        got = host(h.inner_cycle(dev(r32, torch.float32)))
+        assert np.array_equal(got, want), sm
+        h.close()
