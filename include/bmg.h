@@ -96,7 +96,7 @@ typedef struct {
                            compute the same bits): BMG_SMOOTHER_AUTO (0, default; the autotuner
                            picks per level when use_graph = 1, else the row kernel),
                            BMG_SMOOTHER_ROWS (row kernel, in place), or BMG_SMOOTHER_TILE + s
-                           (one-pass tile kernel with tile shape s = 0 .. 4 on every level
+                           (one-pass kernel with shape s = 0 .. 5 on every level
                            outside the level-fused tail and the coarsest) */
 } bmg_opts;
 
@@ -163,8 +163,10 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
 /* Gauss-Seidel kernel the setup autotuner chose for level `level` of the cycle
  * the hierarchy runs (FP64 or FP32): the row kernel's cluster size (1, 2, 4,
  * 8), BMG_TILE_SWEEP + s when the one-pass tile kernel with tile shape s won
- * (FP32 levels only; shapes 0 .. 4: warp strips of 56 x 32, 16, 64, 128, 8
- * points), or 0 (default; not tuned).  Every choice computes the same bits. */
+ * (FP32 levels only; warp strips of 56 x TY points: shapes 0 .. 3 stream rows
+ * by bulk copies, TY = 32 with 6 row slots and 8, 16, 32 with 4; shapes 4, 5
+ * load rows into registers, TY = 32, 16), or 0 (default; not tuned).  Every
+ * choice computes the same bits. */
 #define BMG_TILE_SWEEP 16
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 
@@ -263,6 +265,13 @@ int bmg_interp_info(const bmg_hierarchy* h, int* used, double* factor_learned, d
  * (counter form, stream `seed`, interior point k = (j-1) n + (i-1)). */
 int bmg_fill_uniform(int n, unsigned long long seed, double* x, void* stream);
 void bmg_mlp_free(bmg_mlp* m);
+
+/* Self-test of the bounded device-side wait that the bulk-copy form of the
+ * one-pass sweep uses (no counterpart in the paper): one warp waits on an
+ * mbarrier phase that nothing completes.  The wait must give up after its
+ * poll limit (about a second), record the timeout and return, leaving the
+ * context usable.  Returns BMG_OK when that happened, BMG_ECUDA otherwise. */
+int bmg_wait_selftest(void);
 
 /* ---- single steps, for testing and composition -------------------------
  * Stateless: every pointer is caller-owned device memory in the layouts above;

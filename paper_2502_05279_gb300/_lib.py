@@ -45,7 +45,7 @@ KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "re
                 "ir_update", "ir_residual", "fcg", "tail")
 _KRYLOV = {"none": 0, "fcg": 1}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
-_SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(5)}}
+_SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)}}
 TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
 
 
@@ -79,6 +79,7 @@ _sig = {
     "bmg_coarse_solve": (I, [I, P, P, P, P]),
     "bmg_inner_cycle": (I, [P, P, P]),
     "bmg_measure_fp64_rate": (I, [ctypes.POINTER(D), P]),
+    "bmg_wait_selftest": (I, []),
     "bmg_time_cycles": (I, [P, P, P, I, ctypes.POINTER(D)]),
     "bmg_setup_batched": (I, [I, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
     "bmg_solve_batched": (I, [P, P, P, D, I, P, P]),

@@ -36,6 +36,12 @@ int set_error(int code, const char* fmt, ...) {
   return code;
 }
 
+// BMG_ETIMEOUT when a one-pass sweep gave up on its bulk copies since the last check.
+int timeout_check(const char* where) {
+  if (strip_timeouts()) return set_error(BMG_ETIMEOUT, "%s: a one-pass sweep timed out waiting for its copies", where);
+  return BMG_OK;
+}
+
 int cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return BMG_OK;
   if (e == cudaErrorMemoryAllocation) return set_error(BMG_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
@@ -80,11 +86,11 @@ StencilView<double, double> view64(const Level& L) {
   return {L.st, L.st + ps, L.st + 2 * ps, L.st + 3 * ps, L.st + 4 * ps, L.st + 5 * ps, L.n, L.n + 2};
 }
 StencilView<float, float> view32(const Level& L) {
-  size_t ps = plane_size(L.n);
+  size_t ps = plane_stride32(L.n);
   return {L.st32, L.st32 + ps, L.st32 + 2 * ps, L.st32 + 3 * ps, L.st32 + 4 * ps, L.st32 + 5 * ps, L.n, L.n + 2};
 }
 StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
-  size_t ps = plane_size(L.n);
+  size_t ps = plane_stride32(L.n);
   return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2};
 }
 
@@ -161,6 +167,25 @@ int dalloc(T** p, size_t count) {
   if (count == 0) return BMG_OK;
   CK(cudaMalloc((void**)p, count * sizeof(T)));
   return BMG_OK;
+}
+
+// FP32 / BF16 level arrays: `planes` planes of level size n, plane_stride32(n)
+// elements apart, with STRIP_GUARD zeroed elements before the first and after
+// every plane; *p is the first plane (256-byte aligned).  Freed by gfree.
+template <typename T>
+int galloc(T** p, int n, int planes, cudaStream_t s) {
+  *p = nullptr;
+  const size_t count = STRIP_GUARD + planes * plane_stride32(n);
+  T* raw = nullptr;
+  CK(cudaMalloc((void**)&raw, count * sizeof(T)));
+  CK(cudaMemsetAsync(raw, 0, count * sizeof(T), s));
+  *p = raw + STRIP_GUARD;
+  return BMG_OK;
+}
+
+template <typename T>
+void gfree(T* p) {
+  if (p) cudaFree(p - STRIP_GUARD);
 }
 
 void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* done) {
@@ -314,10 +339,10 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
     *ms_out = it->second.second;
     return BMG_OK;
   }
-  size_t ps = plane_size(v.n);
-  float* scratch = nullptr;
-  CK(cudaMalloc((void**)&scratch, 3 * ps * sizeof(float)));
-  CK(cudaMemsetAsync(scratch, 0, 3 * ps * sizeof(float), s));
+  size_t ps = plane_stride32(v.n);
+  float* scratch = nullptr;   // x, x', f laid out like a level's arrays
+  int rc0 = galloc(&scratch, v.n, 3, s);
+  if (rc0) return rc0;
   const float* f = scratch + 2 * ps;
   float best = 1e30f;
   int best_shape = 0, rc = BMG_OK;
@@ -333,7 +358,8 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
       best_shape = shape;
     }
   }
-  cudaFree(scratch);
+  gfree(scratch);
+  if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "one-pass sweep: bulk copies did not complete");
   if (rc) return rc;
   cache[key] = {best_shape, best};
   *best_out = best_shape;
@@ -350,9 +376,7 @@ int tune_level32(Level& L, const StencilView<float, S>& v, cudaStream_t s) {
   if (!rc) rc = tune_tile(v, s, &shape, &ms_tile);
   if (rc) return rc;
   if (ms_tile < ms_rows) {
-    size_t ps = plane_size(L.n);
-    if ((rc = dalloc(&L.x32b, ps))) return rc;
-    CK(cudaMemsetAsync(L.x32b, 0, ps * sizeof(float), s));
+    if ((rc = galloc(&L.x32b, L.n, 1, s))) return rc;
     L.tile32 = shape;
   }
   return BMG_OK;
@@ -397,10 +421,8 @@ int force_tile(bmg_hierarchy* h) {
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
     if (L.kind != 9) continue;
-    size_t ps = plane_size(L.n);
-    int rc = dalloc(&L.x32b, ps);
+    int rc = galloc(&L.x32b, L.n, 1, h->ws);
     if (rc) return rc;
-    CK(cudaMemsetAsync(L.x32b, 0, ps * sizeof(float), h->ws));
     L.tile32 = h->smoother - BMG_SMOOTHER_TILE;
   }
   return BMG_OK;
@@ -523,13 +545,13 @@ void free_level(Level& L) {
   cudaFree(L.ci);
   cudaFree(L.x);
   cudaFree(L.f);
-  cudaFree(L.st32);
-  cudaFree(L.off16);
-  cudaFree(L.od32);
+  gfree(L.st32);
+  gfree(L.off16);
+  gfree(L.od32);
   cudaFree(L.ci32);
-  cudaFree(L.x32);
-  cudaFree(L.x32b);
-  cudaFree(L.f32);
+  gfree(L.x32);
+  gfree(L.x32b);
+  gfree(L.f32);
   L = Level{};
 }
 
@@ -593,18 +615,16 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
       size_t ps = plane_size(L.n);
       L.bf16 = l < nbf && l + 1 < h->nlev;
       if (L.bf16) {
-        if ((rc = dalloc(&L.off16, 4 * ps))) return rc;
-        if ((rc = dalloc(&L.od32, 2 * ps))) return rc;
+        if ((rc = galloc(&L.off16, L.n, 4, s))) return rc;
+        if ((rc = galloc(&L.od32, L.n, 2, s))) return rc;
         launch_lower_bf16(L.n, L.st, L.off16, L.od32, s);
       } else {
-        if ((rc = dalloc(&L.st32, 6 * ps))) return rc;
+        if ((rc = galloc(&L.st32, L.n, 6, s))) return rc;
       }
       if (l + 1 < h->nlev && (rc = dalloc(&L.ci32, 8 * plane_size(h->lv[l + 1].n)))) return rc;
       launch_lower32(L.n, L.bf16 ? nullptr : L.st, L.bf16 ? nullptr : L.st32, L.ci, L.ci32, s);
-      if ((rc = dalloc(&L.x32, ps))) return rc;
-      if ((rc = dalloc(&L.f32, ps))) return rc;
-      CK(cudaMemsetAsync(L.x32, 0, ps * sizeof(float), s));
-      CK(cudaMemsetAsync(L.f32, 0, ps * sizeof(float), s));
+      if ((rc = galloc(&L.x32, L.n, 1, s))) return rc;
+      if ((rc = galloc(&L.f32, L.n, 1, s))) return rc;
     }
   }
   CK(cudaGetLastError());
@@ -810,6 +830,7 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   *ms = t;
+  if ((rc = timeout_check("bmg_time_cycles"))) return rc;
   return cuda_check(cudaGetLastError(), "bmg_time_cycles");
 }
 
@@ -842,6 +863,7 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
   }
   if (rc) return rc;
   for (size_t k = 0; k < acc.size() && (int)k < cap; ++k) rows[k] = acc[k];
+  if ((rc = timeout_check("bmg_profile"))) return rc;
   return (int)acc.size();
 }
 
@@ -880,6 +902,7 @@ int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int ma
                 cudaMemcpyDeviceToHost));
   if (iters) *iters = it;
   if (relres) *relres = h->hist[0] > 0 ? h->hist[it] / h->hist[0] : 0.0;
+  if ((rc = timeout_check("bmg_solve"))) return rc;
   if (c.done == 3) return set_error(BMG_ENAN, "bmg_solve: residual norm is not finite at cycle %d", it);
   if (c.done == 2 || c.done == 0) return set_error(BMG_ENOTCONV, "bmg_solve: %d cycles, relres %g", it,
                                                    h->hist[0] > 0 ? h->hist[it] / h->hist[0] : 0.0);
@@ -951,7 +974,16 @@ int bmg_inner_cycle(bmg_hierarchy* h, const float* r32, float* e32) {
   CK(cudaMemcpyAsync(e32, L0.x32, bytes, cudaMemcpyDeviceToDevice, h->ws));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->ws));
-  return BMG_OK;
+  return timeout_check("bmg_inner_cycle");
+}
+
+int bmg_wait_selftest(void) {
+  strip_timeouts();   // clear
+  launch_wait_selftest(nullptr);
+  CK(cudaDeviceSynchronize());
+  CK(cudaGetLastError());
+  int rc = timeout_check("bmg_wait_selftest");
+  return rc == BMG_ETIMEOUT ? BMG_OK : set_error(BMG_ECUDA, "bmg_wait_selftest: the bounded wait did not give up");
 }
 
 // ---- stateless steps -----------------------------------------------------------------

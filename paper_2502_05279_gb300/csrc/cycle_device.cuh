@@ -304,6 +304,207 @@ __device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, co
   }
 }
 
+// ---- the strip walk fed by bulk copies -------------------------------------------------
+// The same walk, with the strip's rows streamed into a per-warp ring of RING
+// row slots in shared memory by bulk asynchronous copies (one lane issues 7
+// copies per row, one mbarrier per slot counts the bytes), so that rows are
+// requested RING/2 steps before they are used without holding them in
+// registers.  A copy must start on a 16-byte boundary: each array row segment
+// is copied from the aligned address at or below its first column (at most 7
+// elements earlier) for 68 floats / 72 bf16 values, which requires every array
+// base to be 16-byte aligned with STRIP_GUARD readable elements before and
+// after it.  A wait that does not complete within STRIP_WAIT_NS (or
+// STRIP_WAIT_LIMIT polls) sets
+// strip_timeout, waits (bounded) for the warp's copies in flight and returns.
+constexpr long STRIP_WAIT_LIMIT = 1L << 20;                 // polls
+constexpr unsigned long long STRIP_WAIT_NS = 500000000ull;   // 0.5 s
+
+template <typename S>
+struct StripRing {
+  static constexpr int CF = 68, CS = sizeof(S) == 4 ? 68 : 72;      // elements copied per row segment
+  static constexpr unsigned BF = CF * 4, BS = CS * sizeof(S);       // bytes (multiples of 16)
+  static constexpr unsigned SLOT = 3 * BF + 4 * BS;                 // one row of the 7 arrays
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// true once phase `parity` of bar has completed; the warp may be suspended up
+// to about STRIP_SUSPEND_NS while it is pending
+constexpr unsigned STRIP_SUSPEND_NS = 1000;
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(STRIP_SUSPEND_NS)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Warp-uniform bounded wait for phase `parity` of bar: false once
+// STRIP_WAIT_NS of wall-clock time or STRIP_WAIT_LIMIT polls have passed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  for (long it = 0; it < STRIP_WAIT_LIMIT; ++it) {
+    if (__all_sync(0xffffffffu, mbar_try(bar, parity))) return true;
+    if (__any_sync(0xffffffffu, global_ns() - t0 > STRIP_WAIT_NS)) break;
+  }
+  return false;
+}
+
+template <typename S>
+struct StripSrc {           // the 7 arrays the walk reads
+  const float *x, *f, *d;
+  const S *w, *s, *sw, *nw;
+};
+
+// lane 0: request row j into `slot`: arm the slot's mbarrier for the row's
+// bytes and copy the 7 arrays' row segments.  The caller's __syncwarp orders
+// the warp's earlier reads of the slot before the fence.
+template <typename S>
+__device__ __forceinline__ void ring_issue(const StripSrc<S>& A, int ld, int icol, int j, unsigned char* slot,
+                                           unsigned long long* bar) {
+  using RG = StripRing<S>;
+  const long long e = (long long)j * ld + icol;   // first column of the row segment
+  const long long e4 = e - (e & 3), e8 = e - (e & (16 / (long long)sizeof(S) - 1));
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect_tx(bar, RG::SLOT);
+  bulk_copy(slot, A.x + e4, RG::BF, bar);
+  bulk_copy(slot + RG::BF, A.f + e4, RG::BF, bar);
+  bulk_copy(slot + 2 * RG::BF, A.d + e4, RG::BF, bar);
+  unsigned char* q = slot + 3 * RG::BF;
+  bulk_copy(q, A.w + e8, RG::BS, bar);
+  bulk_copy(q + RG::BS, A.s + e8, RG::BS, bar);
+  bulk_copy(q + 2 * RG::BS, A.sw + e8, RG::BS, bar);
+  bulk_copy(q + 3 * RG::BS, A.nw + e8, RG::BS, bar);
+}
+
+// every lane: its two columns of row j from a filled slot.  Columns or rows
+// outside [0, n+1]^2 hold stale values: they feed only lanes and rows whose
+// updates and stores are switched off.
+template <typename S>
+__device__ __forceinline__ void ring_read(const unsigned char* slot, int ld, int icol, int ic, int j, StripRow<S>& R) {
+  using RG = StripRing<S>;
+  const long long e = (long long)j * ld + icol;
+  const int o4 = (int)(e & 3) + (ic - icol), o8 = (int)(e & (16 / (long long)sizeof(S) - 1)) + (ic - icol);
+  const float* xf = reinterpret_cast<const float*>(slot);
+  const float* ff = reinterpret_cast<const float*>(slot + RG::BF);
+  const float* df = reinterpret_cast<const float*>(slot + 2 * RG::BF);
+  const S* wq = reinterpret_cast<const S*>(slot + 3 * RG::BF);
+  const S* sq = wq + RG::CS;
+  const S* swq = sq + RG::CS;
+  const S* nwq = swq + RG::CS;
+  R.xa = xf[o4];
+  R.xb = xf[o4 + 1];
+  R.fa = ff[o4];
+  R.fb = ff[o4 + 1];
+  R.da = df[o4];
+  R.db = df[o4 + 1];
+  R.wa = wq[o8];
+  R.wb = wq[o8 + 1];
+  R.sa = sq[o8];
+  R.sb = sq[o8 + 1];
+  R.swa = swq[o8];
+  R.swb = swq[o8 + 1];
+  R.nwa = nwq[o8];
+  R.nwb = nwq[o8 + 1];
+}
+
+template <typename S, int TY, int RING>
+__device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
+                                                   const float* __restrict__ xin, float* __restrict__ xout,
+                                                   int sx, int sy, unsigned char* ring, unsigned long long* bars) {
+  static_assert(TY % 2 == 0 && RING % 2 == 0 && RING >= 4, "strip shape");
+  using RG = StripRing<S>;
+  const int n = v.n, ld = v.ld;
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 56 * sx, j0 = 1 + TY * sy, j1 = j0 + TY;
+  const int icol = i0 - 4, ic = icol + 2 * lane;
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
+  const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
+  const bool own = lane >= 2 && lane <= 29;
+  const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
+  constexpr int NR = TY + 3;                      // band rows q = 0 .. NR - 1, j = j0 - 1 + q
+  const int last = (n + 1) - (j0 - 1);            // rows q > last lie outside the grid: never copied
+  auto valid = [&](int q) { return q < NR && q <= last; };
+  if (lane == 0) {
+    for (int k = 0; k < RING; ++k) mbar_init(&bars[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int q = 0; q < RING; ++q)
+      if (valid(q)) ring_issue(A, ld, icol, j0 - 1 + q, ring + q * RG::SLOT, &bars[q]);
+  bool ok = true;
+  int taken = 0;                                  // rows 0 .. taken-1 read; rows < taken + RING requested
+  // read band row q into R (waiting for its slot), then hand the slot to row q + RING
+  auto take = [&](int q, StripRow<S>& R) {
+    const int slot = q % RING;
+    if (valid(q) && ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
+    if (!ok) return;
+    ring_read(ring + slot * RG::SLOT, ld, icol, ic, j0 - 1 + q, R);
+    taken = q + 1;
+    __syncwarp();
+    if (lane == 0 && valid(q) && valid(q + RING))
+      ring_issue(A, ld, icol, j0 - 1 + q + RING, ring + slot * RG::SLOT, &bars[slot]);
+  };
+  StripRow<S> P0, P1, Q0, Q1;                     // two row pairs in alternating roles
+  take(0, P1);
+  take(1, Q0);
+  take(2, Q1);
+  if (ok && j0 <= n) {
+    strip_row(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
+    strip_store(xout, n, ld, ic, j0, own, Q0);
+  }
+  // step m: old pair = rows a - 2, a - 1; new pair = rows a, a + 1 (band rows 2m + 1, 2m + 2)
+  auto step = [&](int m, StripRow<S>& E0, StripRow<S>& E1, StripRow<S>& E2, StripRow<S>& E3) {
+    const int a = j0 + 2 * m;
+    take(2 * m + 1, E2);
+    take(2 * m + 2, E3);
+    if (!ok) return;
+    if (a <= n) {
+      strip_row(E1, E2, E3, c1, c2);              // row a: c1, c2
+      if (a < j1) strip_store(xout, n, ld, ic, a, own, E2);
+    }
+    if (a - 1 <= n) {
+      strip_row(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
+      strip_store(xout, n, ld, ic, a - 1, own, E1);
+    }
+  };
+#pragma unroll 1
+  for (int m = 1; m <= TY / 2 && ok; m += 2) {
+    step(m, Q0, Q1, P0, P1);
+    if (m + 1 <= TY / 2 && ok) step(m + 1, P0, P1, Q0, Q1);
+  }
+  if (!ok)                                        // drain the copies still in flight, bounded
+    for (int q = taken; q < taken + RING; ++q)
+      if (valid(q)) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));
+  return ok;
+}
+
 // ---- residual + restriction ------------------------------------------------------------
 // A CTA owns a TXC x TYC tile of coarse points; it forms the residual on the
 // (2 TXC + 1) x (2 TYC + 1) fine block under the tile in shared memory (each

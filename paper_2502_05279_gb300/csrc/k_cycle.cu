@@ -4,6 +4,8 @@
 // Cholesky solve, FP64 iterative-refinement steps around an FP32 cycle and the
 // flexible-CG outer loop.  The arithmetic lives in cycle_device.cuh, shared with
 // the batched kernels.
+#include <cstdint>
+
 #include "cycle_device.cuh"
 
 namespace bmg {
@@ -39,6 +41,26 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float
   const int g = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
   if (g >= nbx * nby) return;                     // whole warps only
   gs_strip_body<S, TY>(v, f, xin, xout, g % nbx, g / nbx);
+}
+
+// Bulk-copy form: warp w of the CTA owns ring slots [w RING, (w + 1) RING) and
+// mbarriers [w RING, (w + 1) RING) of the dynamic shared memory.
+__device__ int g_strip_timeout = 0;
+template <typename S, int TY, int RING>
+__global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<float, S> v,
+                                                                    const float* __restrict__ f,
+                                                                    const float* __restrict__ xin,
+                                                                    float* __restrict__ xout, const int* done) {
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  if (stopped(done)) return;
+  const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
+  const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
+  if (g >= nbx * nby) return;                     // whole warps only
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
+  if (!gs_strip_ring_body<S, TY, RING>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout, 1);
 }
 
 template <typename T, typename S, bool NINE>
@@ -203,16 +225,58 @@ static void strip_launch(const StencilView<float, S>& v, const float* f, const f
   count_launch();
 }
 
+template <typename S, int TY, int RING>
+static void strip_ring_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                              const int* done, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gs_strip_ring<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    attr = true;
+  }
+  const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
+  k_gs_strip_ring<S, TY, RING><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+      v, f, xin, xout, done);
+  count_launch();
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 template <typename S>
 void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
+  const bool ring_ok = aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) &&
+                       aligned16(v.SW) && aligned16(v.NW);
+  if (shape < 4 && !ring_ok) shape = 4;           // bulk copies need 16-byte aligned arrays
   switch (shape) {
-    case 1: strip_launch<S, 16>(v, f, xin, xout, done, s); break;
-    case 2: strip_launch<S, 64>(v, f, xin, xout, done, s); break;
-    case 3: strip_launch<S, 128>(v, f, xin, xout, done, s); break;
-    case 4: strip_launch<S, 8>(v, f, xin, xout, done, s); break;
-    default: strip_launch<S, 32>(v, f, xin, xout, done, s); break;
+    case 1: strip_ring_launch<S, 8, 4>(v, f, xin, xout, done, s); break;
+    case 2: strip_ring_launch<S, 16, 4>(v, f, xin, xout, done, s); break;
+    case 3: strip_ring_launch<S, 32, 4>(v, f, xin, xout, done, s); break;
+    case 4: strip_launch<S, 32>(v, f, xin, xout, done, s); break;
+    case 5: strip_launch<S, 16>(v, f, xin, xout, done, s); break;
+    default: strip_ring_launch<S, 32, 6>(v, f, xin, xout, done, s); break;
   }
+}
+
+// One warp waits, through the same bounded wait as the bulk-copy sweep, on an
+// mbarrier phase that nothing completes; the wait gives up and flags it.
+__global__ void k_wait_selftest() {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncwarp();
+  if (!mbar_wait(&bar, 0) && threadIdx.x == 0) atomicExch(&g_strip_timeout, 1);
+}
+
+void launch_wait_selftest(cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>();
+  count_launch();
+}
+
+int strip_timeouts() {
+  int h = 0, zero = 0;
+  cudaMemcpyFromSymbol(&h, g_strip_timeout, sizeof(int));
+  if (h) cudaMemcpyToSymbol(g_strip_timeout, &zero, sizeof(int));
+  return h;
 }
 
 template <typename T>

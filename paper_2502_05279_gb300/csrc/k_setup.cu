@@ -265,17 +265,17 @@ __device__ __forceinline__ float bf16_of(double v) { return __bfloat162float(__f
 // off16: W, S, SW, NW as bf16(fl32(a)); od32: O32, D32 with
 // O32 = fl32(sum_NBR a) - W_b - E_b - S_b - N_b - SW_b - NE_b - NW_b - SE_b, D32 = 1 / O32.
 __global__ void k_lower_bf16(int n, const double* __restrict__ st, __nv_bfloat16* __restrict__ off16,
-                             float* __restrict__ od32) {
+                             float* __restrict__ od32, size_t pst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int ld = n + 2;
   if (i > n + 1 || j > n + 1) return;
   size_t ps = plane_size(n), p = (size_t)j * ld + i;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) off16[k * ps + p] = __float2bfloat16_rn(__double2float_rn(st[(k + 1) * ps + p]));
+  for (int k = 0; k < 4; ++k) off16[k * pst + p] = __float2bfloat16_rn(__double2float_rn(st[(k + 1) * ps + p]));
   if (i < 1 || i > n || j < 1 || j > n) {
     od32[p] = 0.0f;
-    od32[ps + p] = 0.0f;
+    od32[pst + p] = 0.0f;
     return;
   }
   Planes<double> A = planes_at(st, ps);
@@ -298,7 +298,7 @@ __global__ void k_lower_bf16(int n, const double* __restrict__ st, __nv_bfloat16
   o = rsub(o, bf16_of(A.a<7>(p, ld)));
   o = rsub(o, bf16_of(A.a<8>(p, ld)));
   od32[p] = o;
-  od32[ps + p] = rdiv(1.0f, o);
+  od32[pst + p] = rdiv(1.0f, o);
 }
 
 dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
@@ -335,10 +335,13 @@ void launch_factor(int n, const double* st, double* L, double* work, int* err, c
 }
 
 void launch_lower32(int n, const double* st, float* st32, const double* ci, float* ci32, cudaStream_t s) {
-  if (st) {
-    size_t cnt = 6 * plane_size(n);
-    k_round32<<<(unsigned)((cnt + 255) / 256 < 4096 ? (cnt + 255) / 256 : 4096), 256, 0, s>>>(cnt, st, st32);
-    count_launch();
+  if (st) {   // plane k of st32 starts plane_stride32(n) elements after plane k - 1
+    size_t cnt = plane_size(n), pst = plane_stride32(n);
+    for (int k = 0; k < 6; ++k) {
+      k_round32<<<(unsigned)((cnt + 255) / 256 < 4096 ? (cnt + 255) / 256 : 4096), 256, 0, s>>>(cnt, st + k * cnt,
+                                                                                              st32 + k * pst);
+      count_launch();
+    }
   }
   if (ci) {
     size_t cc = 8 * plane_size((n - 1) / 2);
@@ -348,7 +351,7 @@ void launch_lower32(int n, const double* st, float* st32, const double* ci, floa
 }
 
 void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od32, cudaStream_t s) {
-  k_lower_bf16<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, st, off16, od32);
+  k_lower_bf16<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, st, off16, od32, plane_stride32(n));
   count_launch();
 }
 

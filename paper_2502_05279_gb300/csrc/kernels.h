@@ -29,6 +29,7 @@ void launch_dendy(int n, const double* st, double* ci, int* err, cudaStream_t s)
 void launch_rap(int n, const double* st, const double* ci, double* stc, cudaStream_t s);
 void launch_dinv(int n, double* st, int* err, cudaStream_t s);
 void launch_factor(int n, const double* st, double* L, double* work, int* err, cudaStream_t s);
+// st32 / off16 / od32: planes plane_stride32(n) elements apart.
 void launch_lower32(int n, const double* st, float* st32, const double* ci, float* ci32, cudaStream_t s);
 void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od32, cudaStream_t s);
 
@@ -38,11 +39,24 @@ void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od3
 template <typename T, typename S>
 void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
                int cl = 0);   // cl: row-kernel cluster size, 0 = the smallest that covers a row
+// FP32 / BF16 level arrays are allocated with STRIP_GUARD zeroed elements
+// before and after each array (plane), every array starting on a 256-byte
+// boundary; planes of one level are plane_stride32(n) elements apart.  The
+// bulk-copy form of the one-pass sweep relies on both.
+constexpr int STRIP_GUARD = 128;
+inline size_t plane_stride32(int n) { return (((size_t)(n + 2) * (n + 2) + STRIP_GUARD + 63) / 64) * 64; }
+// Nonzero once a one-pass sweep gave up waiting for its bulk copies (then
+// cleared): the sweep's result is invalid.
+int strip_timeouts();
+// One warp waits on an mbarrier phase that never completes (bounded wait).
+void launch_wait_selftest(cudaStream_t s);
 // One four-colour Gauss-Seidel sweep of a 9-point FP32 level in one launch:
 // reads xin, writes every interior point of xout (xout != xin; the ghost ring
-// of xout is not written).  One warp per strip of 56 x TY points, TY = 32,
-// 16, 64, 128, 8 for shapes 0 .. 4.
-constexpr int GS_TILE_SHAPES = 5;
+// of xout is not written).  One warp per strip of 56 x TY points: shapes
+// 0 .. 3 stream rows by bulk copies (TY 32 with 6 row slots; TY 8, 16, 32
+// with 4), shapes 4, 5 load them into registers (TY 32, 16).  The bulk-copy
+// shapes need the array layout above (else they run as shape 4).
+constexpr int GS_TILE_SHAPES = 6;
 template <typename S>
 void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s);
