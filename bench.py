@@ -58,7 +58,7 @@ NCU_TRAFFIC = {
     ("fe2047-binary1e4", "k_gs_rows<double>"): 196.5e6,
     ("fe2047-binary1e4", "k_gs_rows<float,float>"): 95.6e6,
     ("fe2047-binary1e4", "k_gs_rows<float,bf16>"): 63.8e6,
-    ("fe2047-binary1e4", "k_gs_strip<float> 56x32 bulk/4"): 135.3e6,
+    ("fe2047-binary1e4", "k_gs_strip<float> 56x32 bulk/4"): 135.8e6,
 }
 TILE_SHAPES = ("56x32 bulk/6", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 
