@@ -95,14 +95,17 @@ typedef struct {
   int smoother;         /* Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all choices
                            compute the same bits): BMG_SMOOTHER_AUTO (0, default; the autotuner
                            picks per level when use_graph = 1, else the row kernel),
-                           BMG_SMOOTHER_ROWS (row kernel, in place), or BMG_SMOOTHER_TILE + s
-                           (one-pass kernel with shape s = 0 .. 5 on every level
-                           outside the level-fused tail and the coarsest) */
+                           BMG_SMOOTHER_ROWS (row kernel, in place), BMG_SMOOTHER_TILE + s
+                           (one-pass kernel with shape s = 0 .. 5 on every level outside the
+                           level-fused tail and the coarsest), or BMG_SMOOTHER_PAIR + s
+                           (the same levels, pairs of sweeps as one two-sweep pass) */
 } bmg_opts;
 
 #define BMG_SMOOTHER_AUTO 0
 #define BMG_SMOOTHER_ROWS 1
 #define BMG_SMOOTHER_TILE 2
+#define BMG_SMOOTHER_PAIR 8   /* + s (s = 0 .. 3): pairs of sweeps as one two-sweep pass of shape s,
+                                 single sweeps with one-pass shape 3 */
 
 /* ---- whole solver ------------------------------------------------------ */
 
@@ -150,7 +153,8 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
  * host array `rows` and returns the number of rows. */
 enum { BMG_K_RELAX = 0, BMG_K_RESID_RESTRICT = 1, BMG_K_INTERP = 2, BMG_K_COARSE = 3, BMG_K_NORM = 4,
        BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7, BMG_K_FCG = 8,
-       BMG_K_TAIL = 9 /* the level-fused coarse levels, counted at their top level */ };
+       BMG_K_TAIL = 9 /* the level-fused coarse levels, counted at their top level */,
+       BMG_K_RELAX_PAIR = 10 /* two-sweep passes (each launch = two sweeps) */ };
 typedef struct {
   int level;            /* 0 = finest */
   int kernel;           /* BMG_K_* */
@@ -164,11 +168,18 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
  * the hierarchy runs (FP64 or FP32): the row kernel's cluster size (1, 2, 4,
  * 8), BMG_TILE_SWEEP + s when the one-pass tile kernel with tile shape s won
  * (FP32 levels only; warp strips of 56 x TY points: shapes 0 .. 3 stream rows
- * by bulk copies, TY = 32 with 6 row slots and 8, 16, 32 with 4; shapes 4, 5
+ * by bulk copies into 4 row slots, TY = 26, 8, 16, 32; shapes 4, 5
  * load rows into registers, TY = 32, 16), or 0 (default; not tuned).  Every
  * choice computes the same bits. */
 #define BMG_TILE_SWEEP 16
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
+
+/* Shape (0 .. 3) of the two-sweep pass (temporal blocking: two Gauss-Seidel
+ * sweeps for one read of the level's arrays, 48 x TY warp strips with
+ * TY = 32, 16, 32, 26 and 4, 4, 6, 4 row slots) that runs each pair of sweeps
+ * on level `level` of an FP32 cycle, or -1 (sweeps one at a time).  Same bits
+ * either way. */
+int bmg_tuned_pair(const bmg_hierarchy* h, int level);
 
 /* Number of levels, and the size n of level l (0 = finest). */
 int bmg_num_levels(const bmg_hierarchy* h);

@@ -42,10 +42,11 @@ class ProfRow(ctypes.Structure):
 
 
 KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
-                "ir_update", "ir_residual", "fcg", "tail")
+                "ir_update", "ir_residual", "fcg", "tail", "relax_pair")
 _KRYLOV = {"none": 0, "fcg": 1}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
-_SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)}}
+_SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
+             "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}}
 TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
 
 
@@ -80,6 +81,7 @@ _sig = {
     "bmg_inner_cycle": (I, [P, P, P]),
     "bmg_measure_fp64_rate": (I, [ctypes.POINTER(D), P]),
     "bmg_wait_selftest": (I, []),
+    "bmg_tuned_pair": (I, [P, I]),
     "bmg_time_cycles": (I, [P, P, P, I, ctypes.POINTER(D)]),
     "bmg_setup_batched": (I, [I, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
     "bmg_solve_batched": (I, [P, P, P, D, I, P, P]),
@@ -201,6 +203,10 @@ class Hierarchy:
 
     def tuned_cluster(self, level: int) -> int:
         return _check_size(lib.bmg_tuned_cluster(self._h, level))
+
+    def tuned_pair(self, level: int) -> int:
+        """Two-sweep pass shape used on `level` (-1: sweeps one at a time)."""
+        return lib.bmg_tuned_pair(self._h, level)
 
     def interp_info(self):
         """(kept interpolation: "learned" or "dendy", learned factor, Dendy factor)."""

@@ -78,6 +78,7 @@ struct Level {
   float* x32 = nullptr;
   float* f32 = nullptr;
   int tile32 = -1;        // FP32 sweeps: -1 row kernel (in place), else tile shape of the one-pass kernel
+  int pair32 = -1;        // >= 0: pairs of sweeps run as one two-sweep launch of this shape (needs tile32 >= 0)
   float* x32b = nullptr;  // second iterate of a tile-swept level (sweeps alternate x32 <-> x32b)
 };
 
@@ -218,14 +219,27 @@ void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps
          [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws, L.cl32); });
     return;
   }
-  step(h, l, BMG_K_RELAX, 1, [&] {
-    for (int k = 0; k < sweeps; ++k) {
-      float* dst = *cur == L.x32 ? L.x32b : L.x32;
-      launch_gs_tile(v, (const float*)L.f32, (const float*)*cur, dst, L.tile32, done, h->ws);
-      *cur = dst;
-    }
-  });
+  const int pairs = L.pair32 >= 0 ? sweeps / 2 : 0;
+  if (pairs)
+    step(h, l, BMG_K_RELAX_PAIR, 1, [&] {
+      for (int k = 0; k < pairs; ++k) {
+        float* dst = *cur == L.x32 ? L.x32b : L.x32;
+        launch_gs_pair(v, (const float*)L.f32, (const float*)*cur, dst, L.pair32, done, h->ws);
+        *cur = dst;
+      }
+    });
+  if (sweeps > 2 * pairs)
+    step(h, l, BMG_K_RELAX, 1, [&] {
+      for (int k = 2 * pairs; k < sweeps; ++k) {
+        float* dst = *cur == L.x32 ? L.x32b : L.x32;
+        launch_gs_tile(v, (const float*)L.f32, (const float*)*cur, dst, L.tile32, done, h->ws);
+        *cur = dst;
+      }
+    });
 }
+
+// Launches of `sweeps` sweeps on a one-pass level (each moves the iterate to the other array).
+int sweep_launches(const Level& L, int sweeps) { return L.pair32 >= 0 ? sweeps / 2 + sweeps % 2 : sweeps; }
 
 template <typename S>
 void restrict32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, const float* x, const int* done) {
@@ -260,7 +274,7 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
     restrict32(h, view32(L), l, cur, done);
   }
   vcycle32(h, l + 1, done);
-  float* dst = L.tile32 >= 0 && (h->nu2 & 1) ? L.x32b : L.x32;
+  float* dst = L.tile32 >= 0 && (sweep_launches(L, h->nu2) & 1) ? L.x32b : L.x32;
   step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_to<float>(L.n, L.ci32, C.x32, cur, dst, done, s); });
   cur = dst;
   if (L.bf16)
@@ -367,8 +381,48 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
   return BMG_OK;
 }
 
+template <typename S>
+int tune_pair(const StencilView<float, S>& v, cudaStream_t s, int* best_out, float* ms_out) {
+  static std::map<std::pair<int, int>, std::pair<int, float>> cache;
+  auto key = std::make_pair(v.n, (int)sizeof(S));
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *best_out = it->second.first;
+    *ms_out = it->second.second;
+    return BMG_OK;
+  }
+  size_t ps = plane_stride32(v.n);
+  float* scratch = nullptr;   // x, x', f laid out like a level's arrays
+  int rc = galloc(&scratch, v.n, 3, s);
+  if (rc) return rc;
+  const float* f = scratch + 2 * ps;
+  float best = 1e30f;
+  int best_shape = -1;
+  for (int shape = 0; shape < GS_PAIR_SHAPES && !rc; ++shape) {
+    float ms = 0;
+    bool launched = true;
+    rc = time_call(s, [&] {
+      launched = launch_gs_pair(v, f, scratch, scratch + ps, shape, (const int*)nullptr, s) &&
+                 launch_gs_pair(v, f, scratch + ps, scratch, shape, (const int*)nullptr, s);
+    }, &ms);
+    ms *= 0.5f;   // per pair of sweeps
+    if (launched && ms < best) {
+      best = ms;
+      best_shape = shape;
+    }
+  }
+  gfree(scratch);
+  if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "two-sweep pass: bulk copies did not complete");
+  if (rc) return rc;
+  cache[key] = {best_shape, best};
+  *best_out = best_shape;
+  *ms_out = best;
+  return BMG_OK;
+}
+
 // Row kernel vs one-pass tile kernel for an FP32 level; allocates the second
-// iterate when the tile kernel wins.
+// iterate when the tile kernel wins, and then also weighs one two-sweep pass
+// against two one-pass sweeps.
 template <typename S>
 int tune_level32(Level& L, const StencilView<float, S>& v, cudaStream_t s) {
   float ms_rows = 0, ms_tile = 0;
@@ -378,6 +432,10 @@ int tune_level32(Level& L, const StencilView<float, S>& v, cudaStream_t s) {
   if (ms_tile < ms_rows) {
     if ((rc = galloc(&L.x32b, L.n, 1, s))) return rc;
     L.tile32 = shape;
+    int pshape = -1;
+    float ms_pair = 0;
+    if ((rc = tune_pair(v, s, &pshape, &ms_pair))) return rc;
+    if (pshape >= 0 && ms_pair < 2.0f * ms_tile) L.pair32 = pshape;
   }
   return BMG_OK;
 }
@@ -423,7 +481,12 @@ int force_tile(bmg_hierarchy* h) {
     if (L.kind != 9) continue;
     int rc = galloc(&L.x32b, L.n, 1, h->ws);
     if (rc) return rc;
-    L.tile32 = h->smoother - BMG_SMOOTHER_TILE;
+    if (h->smoother >= BMG_SMOOTHER_PAIR) {
+      L.tile32 = 3;
+      L.pair32 = h->smoother - BMG_SMOOTHER_PAIR;
+    } else {
+      L.tile32 = h->smoother - BMG_SMOOTHER_TILE;
+    }
   }
   return BMG_OK;
 }
@@ -723,7 +786,9 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     h->user = (cudaStream_t)o->stream;
     h->smoother = o->smoother;
   }
-  if (h->smoother < BMG_SMOOTHER_AUTO || h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES) {
+  if (h->smoother < BMG_SMOOTHER_AUTO ||
+      (h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES && h->smoother < BMG_SMOOTHER_PAIR) ||
+      h->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad smoother %d", h->smoother);
   }
@@ -780,6 +845,11 @@ int bmg_tuned_cluster(const bmg_hierarchy* h, int level) {
   const Level& L = h->lv[level];
   if (h->precision != BMG_FP64 && L.tile32 >= 0) return BMG_TILE_SWEEP + L.tile32;
   return h->precision == BMG_FP64 ? L.cl64 : L.cl32;
+}
+
+int bmg_tuned_pair(const bmg_hierarchy* h, int level) {
+  if (!h || level < 0 || level >= h->nlev) return set_error(BMG_EINVAL, "bmg_tuned_pair: bad level");
+  return h->precision != BMG_FP64 ? h->lv[level].pair32 : -1;
 }
 
 int bmg_interp_info(const bmg_hierarchy* h, int* used, double* fl, double* fd) {

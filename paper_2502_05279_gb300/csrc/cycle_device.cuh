@@ -505,6 +505,101 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
   return ok;
 }
 
+// ---- two sweeps in one pass (temporal blocking) -----------------------------------------
+// The strip walk with a second sweep one step behind the first: at the first
+// sweep's odd row a the warp computes, in this order, sweep 1 on rows a (c1, c2)
+// and a - 1 (c3, c4), then sweep 2 on rows a - 2 (c1, c2) and a - 3 (c3, c4).
+// Sweep 2 reads only rows that sweep 1 has finished and updates them in place.
+// Final values on columns [P, Q] need sweep-1 values on [P - 4, Q + 4] and old
+// values on [P - 8, Q + 8], so a 64-column window yields 48 output columns
+// (c in [8, 55]); a band of TY output rows reads its rows j0 - 3 .. j1 + 3.
+// Both sweeps take the same operands in the same order as two colour-by-colour
+// sweeps, so the result is bit-identical to them.  Rows stream through the same
+// per-warp ring as the single sweep; a row outside [0, n+1] is not copied, its
+// slot's phase is completed by a plain arrive so that every slot's fills stay
+// in order.
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename S, int TY, int RING>
+__device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
+                                                    const float* __restrict__ xin, float* __restrict__ xout,
+                                                    int sx, int sy, unsigned char* ring, unsigned long long* bars) {
+  static_assert(TY % 2 == 0 && RING % 2 == 0 && RING >= 4, "strip shape");
+  using RG = StripRing<S>;
+  const int n = v.n, ld = v.ld;
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 48 * sx, j0 = 1 + TY * sy, j1 = j0 + TY;
+  const int icol = i0 - 8, ic = icol + 2 * lane;
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  // sweep 1 on c in [1, 62], sweep 2 on c in [5, 58]; the strip's own columns c in [8, 55]
+  const bool p1 = in_a && lane >= 1, q1 = in_b && lane >= 1 && lane <= 30;
+  const bool r1 = in_a && lane >= 2 && lane <= 30, t1 = in_b && lane >= 2 && lane <= 29;
+  const bool p2 = in_a && lane >= 3 && lane <= 29, q2 = in_b && lane >= 3 && lane <= 28;
+  const bool r2 = in_a && lane >= 4 && lane <= 28, t2 = in_b && lane >= 4 && lane <= 27;
+  const bool own = lane >= 4 && lane <= 27;
+  const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
+  constexpr int NR = TY + 7;                      // band rows q = 0 .. NR - 1, j = j0 - 3 + q
+  auto rowok = [&](int q) { const int j = j0 - 3 + q; return j >= 0 && j <= n + 1; };
+  // lane 0: fill the slot of band row q (copies, or a plain arrive for a row outside the grid)
+  auto issue = [&](int q) {
+    if (q >= NR) return;
+    if (rowok(q))
+      ring_issue(A, ld, icol, j0 - 3 + q, ring + (q % RING) * RG::SLOT, &bars[q % RING]);
+    else
+      mbar_arrive(&bars[q % RING]);
+  };
+  if (lane == 0) {
+    for (int k = 0; k < RING; ++k) mbar_init(&bars[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int q = 0; q < RING; ++q) issue(q);
+  bool ok = true;
+  int taken = 0;
+  auto take = [&](int q, StripRow<S>& R) {
+    const int slot = q % RING;
+    if (ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
+    if (!ok) return;
+    ring_read(ring + slot * RG::SLOT, ld, icol, ic, j0 - 3 + q, R);
+    taken = q + 1;
+    __syncwarp();
+    if (lane == 0) issue(q + RING);
+  };
+  StripRow<S> R0, R1, R2, R3, R4, R5;             // rows a - 4 .. a + 1
+  take(0, R3);
+  take(1, R4);
+  take(2, R5);
+#pragma unroll 1
+  for (int m = 0; m <= TY / 2 + 2 && ok; ++m) {
+    const int a = j0 - 2 + 2 * m, b = a - 2;      // sweep-1 and sweep-2 odd rows
+    if (m >= 1) {
+      take(2 * m + 1, R4);
+      take(2 * m + 2, R5);
+      if (!ok) break;
+    }
+    if (a >= 1 && a <= n) strip_row(R3, R4, R5, p1, q1);                 // sweep 1, row a
+    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
+    if (m >= 2 && b <= n) {                                               // sweep 2, row a - 2
+      strip_row(R1, R2, R3, p2, q2);
+      if (b < j1) strip_store(xout, n, ld, ic, b, own, R2);
+    }
+    if (m >= 3 && b - 1 <= n) {                                           // sweep 2, row a - 3
+      strip_row(R0, R1, R2, r2, t2);
+      strip_store(xout, n, ld, ic, b - 1, own, R1);
+    }
+    R0 = R2;
+    R1 = R3;
+    R2 = R4;
+    R3 = R5;
+  }
+  if (!ok)                                        // drain the copies still in flight, bounded
+    for (int q = taken; q < taken + RING && q < NR; ++q) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));
+  return ok;
+}
+
 // ---- residual + restriction ------------------------------------------------------------
 // A CTA owns a TXC x TYC tile of coarse points; it forms the residual on the
 // (2 TXC + 1) x (2 TYC + 1) fine block under the tile in shared memory (each

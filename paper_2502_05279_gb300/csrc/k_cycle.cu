@@ -63,6 +63,24 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<
     atomicExch(&g_strip_timeout, 1);
 }
 
+// Two sweeps in one pass: warps take 48-column strips, otherwise as above.
+template <typename S, int TY, int RING>
+__global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView<float, S> v,
+                                                                     const float* __restrict__ f,
+                                                                     const float* __restrict__ xin,
+                                                                     float* __restrict__ xout, const int* done) {
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  if (stopped(done)) return;
+  const int nbx = (v.n + 47) / 48, nby = (v.n + TY - 1) / TY;
+  const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
+  if (g >= nbx * nby) return;
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
+  if (!gs_strip2_ring_body<S, TY, RING>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout, 1);
+}
+
 template <typename T, typename S, bool NINE>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
                                                             const T* __restrict__ x, const T* __restrict__ f,
@@ -254,7 +272,7 @@ void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float*
     case 3: strip_ring_launch<S, 32, 4>(v, f, xin, xout, done, s); break;
     case 4: strip_launch<S, 32>(v, f, xin, xout, done, s); break;
     case 5: strip_launch<S, 16>(v, f, xin, xout, done, s); break;
-    default: strip_ring_launch<S, 32, 6>(v, f, xin, xout, done, s); break;
+    default: strip_ring_launch<S, 26, 4>(v, f, xin, xout, done, s); break;
   }
 }
 
@@ -271,6 +289,40 @@ void launch_wait_selftest(cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>();
   count_launch();
 }
+
+template <typename S, int TY, int RING>
+static void strip2_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                          const int* done, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gs_strip2_ring<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    attr = true;
+  }
+  const int warps = ((v.n + 47) / 48) * ((v.n + TY - 1) / TY);
+  k_gs_strip2_ring<S, TY, RING><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+      v, f, xin, xout, done);
+  count_launch();
+}
+
+template <typename S>
+bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s) {
+  if (!(aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) && aligned16(v.SW) &&
+        aligned16(v.NW)))
+    return false;
+  switch (shape) {
+    case 1: strip2_launch<S, 16, 4>(v, f, xin, xout, done, s); break;
+    case 2: strip2_launch<S, 32, 6>(v, f, xin, xout, done, s); break;
+    case 3: strip2_launch<S, 26, 4>(v, f, xin, xout, done, s); break;
+    default: strip2_launch<S, 32, 4>(v, f, xin, xout, done, s); break;
+  }
+  return true;
+}
+template bool launch_gs_pair<float>(const StencilView<float, float>&, const float*, const float*, float*, int,
+                                    const int*, cudaStream_t);
+template bool launch_gs_pair<__nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, const float*, const float*,
+                                            float*, int, const int*, cudaStream_t);
 
 int strip_timeouts() {
   int h = 0, zero = 0;

@@ -53,12 +53,21 @@ void launch_wait_selftest(cudaStream_t s);
 // One four-colour Gauss-Seidel sweep of a 9-point FP32 level in one launch:
 // reads xin, writes every interior point of xout (xout != xin; the ghost ring
 // of xout is not written).  One warp per strip of 56 x TY points: shapes
-// 0 .. 3 stream rows by bulk copies (TY 32 with 6 row slots; TY 8, 16, 32
-// with 4), shapes 4, 5 load them into registers (TY 32, 16).  The bulk-copy
+// 0 .. 3 stream rows by bulk copies into 4 row slots (TY 26, 8, 16, 32),
+// shapes 4, 5 load them into registers (TY 32, 16).  The bulk-copy
 // shapes need the array layout above (else they run as shape 4).
 constexpr int GS_TILE_SHAPES = 6;
 template <typename S>
 void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s);
+// Two four-colour sweeps of a 9-point FP32 level in one launch (temporal
+// blocking): xin -> xout as two launch_gs_tile calls would give through an
+// intermediate array.  One warp per strip of 48 x TY points, rows by bulk
+// copies: shapes 0 .. 3 = TY 32, 16, 32, 26 with 4, 4, 6, 4 row slots.  Needs
+// the guarded, aligned array layout; returns false (nothing launched) without it.
+constexpr int GS_PAIR_SHAPES = 4;
+template <typename S>
+bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s);
 template <typename T, typename S>
 void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,

@@ -51,8 +51,9 @@ def test_binding_imports_and_reports_errors_without_gpu(libpath):
     assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 63, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
     assert "not 2^m - 1" in bmg.lib.bmg_last_error().decode() or "nx" in bmg.lib.bmg_last_error().decode()
     o = bmg._lib.Opts()
-    o.smoother = 9
-    assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 127, ctypes.byref(o), ctypes.byref(h)) == bmg._lib.BMG_EINVAL
-    assert "smoother" in bmg.lib.bmg_last_error().decode()
+    for bad in (12, 99, -1):   # valid: 0 auto, 1 rows, 2 .. 7 one-pass shapes, 8 .. 11 two-sweep shapes
+        o.smoother = bad
+        assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 127, ctypes.byref(o), ctypes.byref(h)) == bmg._lib.BMG_EINVAL
+        assert "smoother" in bmg.lib.bmg_last_error().decode()
     assert bmg.lib.bmg_solve(None, None, None, 1e-10, 10, None, None) == bmg._lib.BMG_EINVAL
     bmg.lib.bmg_free(None)

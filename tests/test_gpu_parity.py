@@ -404,13 +404,34 @@ def test_tile_sweep_inner_cycle_bitwise(bmg, precision, nbf, shape, graph):
         h.close()
 
 
-@pytest.mark.parametrize("nu1,nu2", [(1, 1), (1, 2), (3, 0), (0, 3), (2, 2)])
-def test_tile_sweep_any_sweep_counts_equal_row_kernel(bmg, nu1, nu2):
-    """Odd and even numbers of alternating sweeps before and after the coarse
-    correction: the one-pass refinement solve equals the row-kernel one."""
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("shape", ["pair0", "pair1", "pair2", "pair3"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_two_sweep_pass_inner_cycle_bitwise(bmg, precision, nbf, shape, graph):
+    """Two sweeps in one pass (48-column strips, sweep 2 one step behind
+    sweep 1, rows streamed once): every level's result is the oracle's bits."""
+    for case, n in [("binary", 255), ("lognormal", 127), ("poisson", 63)]:
+        kind, planes, f = problem(case, n)
+        levels = bx.setup(kind, planes)
+        r32 = w.rhs_uniform(n, 97).astype(np.float32)
+        want = mx.inner_cycle(mx.lower(levels, nbf), r32)
+        h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision, smoother=shape,
+                          use_graph=graph)
+        got = host(h.inner_cycle(dev(r32, torch.float32)))
+        assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0)), (case, n)
+        if kind == 9:
+            assert h.tuned_pair(0) == int(shape[-1])
+        h.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (1, 2), (3, 0), (0, 3), (2, 2), (4, 1), (3, 3)])
+@pytest.mark.parametrize("one_pass", ["tile", "pair"])
+def test_tile_sweep_any_sweep_counts_equal_row_kernel(bmg, nu1, nu2, one_pass):
+    """Odd and even numbers of alternating sweeps (single or paired) before and
+    after the coarse correction: the refinement solve equals the row-kernel one."""
     kind, planes, f = problem("lognormal", 255)
     outs = []
-    for sm in ("rows", "tile"):
+    for sm in ("rows", one_pass):
         h = bmg.Hierarchy(kind, dev(planes), precision="fp32", smoother=sm, nu1=nu1, nu2=nu2, use_graph=False)
         x, it, rr, ok = h.solve(dev(f), tol=1e-9, maxit=60)
         outs.append((host(x), h.history()))
@@ -438,6 +459,8 @@ def test_autotuner_picks_a_valid_kernel_per_level(bmg):
         for l in range(h.num_levels - 1):
             c = h.tuned_cluster(l)
             assert c in (0, 1, 2, 4, 8) or bmg.TILE_SWEEP <= c < bmg.TILE_SWEEP + 6, (l, c)
+            assert h.tuned_pair(l) in (-1, 0, 1, 2, 3)
+            assert h.tuned_pair(l) == -1 or c >= bmg.TILE_SWEEP
         assert h.tuned_cluster(0) != 0
         h.close()
 
@@ -452,7 +475,7 @@ def test_bench_workload_fp32_cycle_bitwise(bmg, precision, nbf):
     levels = bx.setup(kind, planes)
     r32 = w.rhs_uniform(2047, 96).astype(np.float32)
     want = mx.inner_cycle(mx.lower(levels, nbf), r32)
-    for sm in ("auto", "tile"):
+    for sm in ("auto", "tile", "pair"):
         h = bmg.Hierarchy(kind, dev(planes), precision=precision, smoother=sm)
         got = host(h.inner_cycle(dev(r32, torch.float32)))
         assert np.array_equal(got, want), sm
