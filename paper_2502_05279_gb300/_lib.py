@@ -235,14 +235,15 @@ class Batch:
     launch per cycle stage over all problems, one CUDA graph per iteration."""
 
     def __init__(self, kind: int, coefs, precision: str = "fp64", nu1: int = 2, nu2: int = 1,
-                 inner_cycles: int = 1, bf16_levels: int = 2, use_graph: bool = True):
+                 inner_cycles: int = 1, bf16_levels: int = 2, use_graph: bool = True, smoother: str = "auto"):
         self.kind, self.precision = kind, precision
         self.ns = [_n_of(c) for c in coefs]
         self._coefs = list(coefs)
         nprob = len(coefs)
         sts = (Stencil * nprob)(*[Stencil(kind, _ptr(c, name="coef")) for c in coefs])
         ns = (ctypes.c_int * nprob)(*self.ns)
-        o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, None, _stream())
+        o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, None, _stream(),
+                 _SMOOTHER[smoother])
         h = ctypes.c_void_p()
         _check(lib.bmg_setup_batched(nprob, sts, ns, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -1192,12 +1192,15 @@ constexpr int kGroups = 6;
 
 struct bmg_batch {
   int nprob = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1;
+  int smoother = BMG_SMOOTHER_AUTO;
   std::vector<bmg_hierarchy*> hs;
   cudaStream_t user = nullptr, ws = nullptr;
   cudaEvent_t ev = nullptr;
   int bmax = 0, maxn = 0;
   struct Group {
     int n = 0, count = 0, cl = 1, storage = 0, kind = 9;
+    int tile = -1, pair = -1;   // one-pass / two-sweep shapes chosen for an FP32 group (-1: row kernel / none)
+    int dir = 0;                // while a cycle is enqueued: 0 = iterate in x, 1 = in x2
     size_t elem = 0;
     void* d = nullptr;
     std::vector<char> host;
@@ -1321,11 +1324,11 @@ int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x)
         append_desc(g, d);
       } else if (storage == 2) {
         LevelDesc<float, __nv_bfloat16> d{viewbf(lv), lv.ci32, lv.x32, lv.f32, C ? C->x32 : nullptr,
-                                          C ? C->f32 : nullptr, done, h->Lfac, h->work};
+                                          C ? C->f32 : nullptr, done, h->Lfac, h->work, lv.x32b};
         append_desc(g, d);
       } else {
         LevelDesc<float, float> d{view32(lv), lv.ci32, lv.x32, lv.f32, C ? C->x32 : nullptr, C ? C->f32 : nullptr,
-                                  done, h->Lfac, h->work};
+                                  done, h->Lfac, h->work, lv.x32b};
         append_desc(g, d);
       }
     }
@@ -1355,9 +1358,26 @@ int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x)
 template <typename T, typename S>
 const LevelDesc<T, S>* gdesc(const bmg_batch::Group& g) { return (const LevelDesc<T, S>*)g.d; }
 
+// Sweeps of a group: the row kernel in place, or one-pass / two-sweep launches
+// that move the iterate between x and x2 (g.dir follows it).
+template <typename S>
+void group_onepass(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
+  const LevelDesc<float, S>* d = gdesc<float, S>(g);
+  int k = 0;
+  for (; g.pair >= 0 && k + 2 <= sweeps; k += 2, g.dir ^= 1) launch_gs_pair_b(d, g.count, g.n, g.pair, g.dir, B->ws);
+  for (; k < sweeps; ++k, g.dir ^= 1) launch_gs_tile_b(d, g.count, g.n, g.tile, g.dir, B->ws);
+}
+
+int group_launches(const bmg_batch::Group& g, int sweeps) {
+  if (g.tile < 0) return 0;
+  return g.pair >= 0 ? sweeps / 2 + sweeps % 2 : sweeps;
+}
+
 void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
   if (!g.count || !sweeps) return;
-  if (g.storage == 0) launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
+  if (g.tile >= 0 && g.storage == 1) group_onepass<float>(B, g, sweeps);
+  else if (g.tile >= 0 && g.storage == 2) group_onepass<__nv_bfloat16>(B, g, sweeps);
+  else if (g.storage == 0) launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
   else if (g.storage == 1) launch_gs_b(gdesc<float, float>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
   else launch_gs_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
 }
@@ -1365,15 +1385,19 @@ void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
 void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
   if (g.storage == 0) launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws);
-  else if (g.storage == 1) launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws);
-  else launch_resid_restrict_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, B->ws);
+  else if (g.storage == 1) launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws, g.dir);
+  else launch_resid_restrict_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, B->ws, g.dir);
 }
 
+// x (or x2) += P e: reads the array g.dir names and writes the one from which
+// the post-smoothing launches end in x.
 void group_interp(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
+  const int din = g.dir, dout = group_launches(g, B->nu2) & 1;
   if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws);
-  else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws);
-  else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws);
+  else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws, din, dout);
+  else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws, din, dout);
+  g.dir = dout;
 }
 
 void group_coarse(bmg_batch* B, bmg_batch::Group& g) {
@@ -1388,6 +1412,7 @@ void group_coarse(bmg_batch* B, bmg_batch::Group& g) {
 void batch_vcycle(bmg_batch* B) {
   for (int b = B->bmax; b >= 1; --b) {
     for (auto& g : B->stages[b]) {
+      g.dir = 0;
       group_relax(B, g, B->nu1);
       group_restrict(B, g);
     }
@@ -1498,59 +1523,121 @@ int batch_launch_iterations(bmg_batch* B, int k) {
 
 // Autotuner: for every stage of 9-point levels with n >= 127, time two sweeps
 // of the row kernel for each admissible cluster size on scratch copies of the
-// stage's iterates (the stencils are the real ones) and keep the fastest.  The
-// choice changes only how a row is split over CTAs, never a result bit.
-static std::map<std::tuple<int, int, int, int>, int> g_tuned;   // (n, storage, count, sweeps) -> cluster size
+// stage's iterates (the stencils are the real ones) and keep the fastest; for
+// FP32 stages with n >= 255 also the one-pass kernel (shapes 0 and 3) and the
+// two-sweep pass (shapes 0 and 3).  Every candidate computes the same bits.
+struct GroupChoice {
+  int cl, tile, pair;
+};
+static std::map<std::tuple<int, int, int, int>, GroupChoice> g_tuned;   // (n, storage, count, kind) -> choice
+
+// Allocates the second iterate of every problem's level in FP32 group g.
+int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
+  for (bmg_hierarchy* h : B->hs) {
+    const int l = h->nlev - 1 - b;
+    if (l < 0) continue;
+    Level& lv = h->lv[l];
+    const int storage = B->precision == BMG_FP64 ? 0 : (lv.bf16 ? 2 : 1);
+    if (lv.n != g.n || lv.kind != g.kind || storage != g.storage || lv.x32b) continue;
+    int rc = galloc(&lv.x32b, lv.n, 1, B->ws);
+    if (rc) return rc;
+  }
+  return BMG_OK;
+}
 
 template <typename T, typename S>
-int tune_group(bmg_batch* B, bmg_batch::Group& g) {
-  auto key = std::make_tuple(g.n, g.storage, g.count, 2);
+int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
+  auto key = std::make_tuple(g.n, g.storage, g.count, g.kind);
   auto it = g_tuned.find(key);
-  if (it != g_tuned.end()) {
-    g.cl = it->second;
-    return BMG_OK;
-  }
-  const int base = rows_cluster<T>(g.n);
-  size_t ps = plane_size(g.n);
-  T* scratch = nullptr;
-  CK(cudaMalloc((void**)&scratch, 2 * ps * sizeof(T) * g.count));
-  CK(cudaMemsetAsync(scratch, 0, 2 * ps * sizeof(T) * g.count, B->ws));
-  std::vector<LevelDesc<T, S>> d((const LevelDesc<T, S>*)g.host.data(),
-                                 (const LevelDesc<T, S>*)g.host.data() + g.count);
-  for (int k = 0; k < g.count; ++k) {
-    d[k].x = scratch + 2 * ps * k;
-    d[k].f = scratch + 2 * ps * k + ps;
-    d[k].done = nullptr;
-  }
-  LevelDesc<T, S>* dd = nullptr;
-  CK(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count));
-  CK(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_cl = base;
-  for (int cl = base; cl <= 8; cl *= 2) {
-    if (cl > base && ((g.n + 1) / 2 + cl - 1) / cl < 32) break;   // fewer than a warp of pairs per CTA
-    launch_gs_b<T, S>(dd, g.count, g.n, 9, 1, cl, B->ws);   // warm-up
-    cudaEventRecord(e0, B->ws);
-    launch_gs_b<T, S>(dd, g.count, g.n, 9, 2, cl, B->ws);
-    cudaEventRecord(e1, B->ws);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      best_cl = cl;
+  if (it == g_tuned.end()) {
+    const int base = rows_cluster<T>(g.n);
+    const size_t ps = plane_stride32(g.n);   // scratch x, x2, f per problem, laid out like level arrays
+    T* scratch = nullptr;
+    int rc = galloc(&scratch, g.n, 3 * g.count, B->ws);
+    if (rc) return rc;
+    std::vector<LevelDesc<T, S>> d((const LevelDesc<T, S>*)g.host.data(),
+                                   (const LevelDesc<T, S>*)g.host.data() + g.count);
+    for (int k = 0; k < g.count; ++k) {
+      d[k].x = scratch + 3 * ps * k;
+      d[k].x2 = scratch + 3 * ps * k + ps;
+      d[k].f = scratch + 3 * ps * k + 2 * ps;
+      d[k].done = nullptr;
     }
+    LevelDesc<T, S>* dd = nullptr;
+    CK(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count));
+    CK(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws));
+    GroupChoice best{base, -1, -1};
+    float best_ms = 1e30f, tile_ms = 1e30f;
+    for (int cl = base; cl <= 8 && !rc; cl *= 2) {
+      if (cl > base && ((g.n + 1) / 2 + cl - 1) / cl < 32) break;   // fewer than a warp of pairs per CTA
+      float ms = 0;
+      rc = time_call(B->ws, [&] { launch_gs_b<T, S>(dd, g.count, g.n, 9, 2, cl, B->ws); }, &ms);
+      if (ms * 0.5f < best_ms) {
+        best_ms = ms * 0.5f;
+        best.cl = cl;
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (!rc && g.n >= 255) {
+        for (int shape : {0, 3}) {
+          float ms = 0;
+          rc = time_call(B->ws, [&] {
+            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 0, B->ws);
+            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 1, B->ws);
+          }, &ms);
+          if (rc) break;
+          if (ms * 0.5f < tile_ms) {
+            tile_ms = ms * 0.5f;
+            if (tile_ms < best_ms) best.tile = shape;
+          }
+        }
+        if (!rc && best.tile >= 0) {
+          best_ms = tile_ms;
+          float pair_best = 1e30f;
+          for (int shape : {0, 3}) {
+            float ms = 0;
+            rc = time_call(B->ws, [&] {
+              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 0, B->ws);
+              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 1, B->ws);
+            }, &ms);
+            if (rc) break;
+            if (ms * 0.25f < pair_best) {   // per sweep: two launches of two sweeps
+              pair_best = ms * 0.25f;
+              if (pair_best < best_ms) best.pair = shape;
+            }
+          }
+        }
+      }
+    }
+    cudaFree(dd);
+    gfree(scratch);
+    if (!rc && strip_timeouts_b()) rc = set_error(BMG_ETIMEOUT, "batched one-pass sweep: bulk copies did not complete");
+    if (rc) return rc;
+    it = g_tuned.emplace(key, best).first;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(dd);
-  cudaFree(scratch);
-  CK(cudaGetLastError());
-  g.cl = best_cl;
-  g_tuned[key] = best_cl;
+  g.cl = it->second.cl;
+  g.tile = it->second.tile;
+  g.pair = it->second.pair;
+  if (g.tile >= 0) return group_alloc_x2(B, g, b);
+  return BMG_OK;
+}
+
+// BMG_SMOOTHER_TILE + s / BMG_SMOOTHER_PAIR + s on a batch: every FP32 group of
+// 9-point levels outside the tails sweeps with the one-pass kernel of shape s
+// (s <= 3), or runs pairs of sweeps as two-sweep passes of shape s.
+int force_batch_onepass(bmg_batch* B) {
+  for (int b = 1; b <= B->bmax; ++b)
+    for (auto& g : B->stages[b]) {
+      if (!g.count || g.kind != 9) continue;
+      if (B->smoother >= BMG_SMOOTHER_PAIR) {
+        g.tile = 3;
+        g.pair = B->smoother - BMG_SMOOTHER_PAIR;
+      } else {
+        g.tile = B->smoother - BMG_SMOOTHER_TILE;
+      }
+      int rc = group_alloc_x2(B, g, b);
+      if (rc) return rc;
+    }
   return BMG_OK;
 }
 
@@ -1567,12 +1654,12 @@ int autotune_batch(bmg_batch* B) {
   if ((rc = build_batch_tables(B, rhs.data(), x.data()))) return rc;
   for (int b = 1; b <= B->bmax; ++b) {
     for (auto& g : B->stages[b]) {
-      if (!g.count || g.kind != 9 || g.n < 127) continue;
-      if (g.storage == 0) rc = tune_group<double, double>(B, g);
-      else if (g.storage == 1) rc = tune_group<float, float>(B, g);
-      else rc = tune_group<float, __nv_bfloat16>(B, g);
+      if (!g.count || g.kind != 9 || g.n < 127 || g.tile >= 0) continue;   // forced groups keep their kernel
+      if (g.storage == 0) rc = tune_group<double, double>(B, g, b);
+      else if (g.storage == 1) rc = tune_group<float, float>(B, g, b);
+      else rc = tune_group<float, __nv_bfloat16>(B, g, b);
       if (rc) return rc;
-      B->tuned_cl[b] = g.cl;
+      B->tuned_cl[b] = g.tile >= 0 ? BMG_TILE_SWEEP + g.tile : g.cl;
     }
   }
   return BMG_OK;
@@ -1595,6 +1682,13 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   if (o) so = *o;
   so.use_graph = 0;
   so.smoother = BMG_SMOOTHER_AUTO;
+  if (o) B->smoother = o->smoother;
+  if (B->smoother < BMG_SMOOTHER_AUTO ||
+      (B->smoother >= BMG_SMOOTHER_TILE + 4 && B->smoother < BMG_SMOOTHER_PAIR) ||
+      B->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES) {
+    delete B;
+    return set_error(BMG_EINVAL, "bmg_setup_batched: bad smoother %d", o->smoother);
+  }
   if (o) {
     B->precision = o->precision;
     if (o->nu1 || o->nu2) {
@@ -1646,6 +1740,7 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&B->h_alldone, sizeof(int)), "pinned");
   if (!rc) rc = batch_ensure_ctl(B, 64);
+  if (!rc && B->precision != BMG_FP64 && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
   if (!rc && B->use_graph) rc = autotune_batch(B);
   if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "bmg_setup_batched");
   if (rc) {
@@ -1692,6 +1787,7 @@ int bmg_solve_batched(bmg_batch* B, const double* const* rhs, double* const* x, 
     if (c->done == 3) worst = BMG_ENAN;
     else if (c->done != 1 && worst == BMG_OK) worst = BMG_ENOTCONV;
   }
+  if (strip_timeouts_b()) return set_error(BMG_ETIMEOUT, "bmg_solve_batched: a one-pass sweep timed out");
   if (worst == BMG_ENAN) return set_error(BMG_ENAN, "bmg_solve_batched: a residual norm is not finite");
   if (worst == BMG_ENOTCONV) return set_error(BMG_ENOTCONV, "bmg_solve_batched: not every problem converged");
   return BMG_OK;
@@ -1727,6 +1823,7 @@ int bmg_time_cycles_batched(bmg_batch* B, const double* const* rhs, double* cons
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   *ms = t;
+  if (strip_timeouts_b()) return set_error(BMG_ETIMEOUT, "bmg_time_cycles_batched: a one-pass sweep timed out");
   return BMG_OK;
 }
 

@@ -30,18 +30,64 @@ __global__ void k_gs_checker_b(const LevelDesc<T, S>* __restrict__ d, int c) {
 }
 
 template <typename T, typename S, bool NINE>
-__global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T, S>* __restrict__ d) {
+__global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T, S>* __restrict__ d, int dir) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  resid_restrict_body<T, S, NINE>(q.v, q.ci, q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
+  resid_restrict_body<T, S, NINE>(q.v, q.ci, dir ? q.x2 : q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, typename S>
-__global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d) {
+__global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d, int din, int dout) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  interp_body<T>(q.v.n, q.ci, q.xc, q.x, q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
+  interp_body<T>(q.v.n, q.ci, q.xc, din ? q.x2 : q.x, dout ? q.x2 : q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
                  blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
+// One-pass sweeps of a group: warp g takes strip g % wpp of problem g / wpp.
+constexpr int STRIP_WARPS_B = 4;
+__device__ int g_strip_timeout_b = 0;
+
+template <typename S, int TY, int RING>
+__global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const LevelDesc<float, S>* __restrict__ d,
+                                                                        int count, int n, int dir) {
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  const int nbx = (n + 55) / 56, wpp = nbx * ((n + TY - 1) / TY);
+  const int w = threadIdx.x >> 5;
+  const long g = (long)blockIdx.x * STRIP_WARPS_B + w;
+  const int p = (int)(g / wpp), sidx = (int)(g % wpp);
+  if (p >= count) return;                         // whole warps only
+  const LevelDesc<float, S> q = d[p];
+  if (stopped(q.done)) return;
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
+      w * RING;
+  if (!gs_strip_ring_body<S, TY, RING>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, ring,
+                                       bars) &&
+      (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout_b, 1);
+}
+
+template <typename S, int TY, int RING>
+__global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const LevelDesc<float, S>* __restrict__ d,
+                                                                         int count, int n, int dir) {
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  const int nbx = (n + 47) / 48, wpp = nbx * ((n + TY - 1) / TY);
+  const int w = threadIdx.x >> 5;
+  const long g = (long)blockIdx.x * STRIP_WARPS_B + w;
+  const int p = (int)(g / wpp), sidx = (int)(g % wpp);
+  if (p >= count) return;
+  const LevelDesc<float, S> q = d[p];
+  if (stopped(q.done)) return;
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
+      w * RING;
+  if (!gs_strip2_ring_body<S, TY, RING>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, ring,
+                                        bars) &&
+      (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout_b, 1);
 }
 
 template <typename T, typename S>
@@ -150,23 +196,78 @@ void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweep
 }
 
 template <typename T, typename S>
-void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s) {
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir) {
   if (count <= 0) return;
   int nc = (n - 1) / 2;
   dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC, count);
   if (kind == 9)
-    k_resid_restrict_b<T, S, true><<<g, dim3(TXC, TYC), 0, s>>>(d);
+    k_resid_restrict_b<T, S, true><<<g, dim3(TXC, TYC), 0, s>>>(d, dir);
   else
-    k_resid_restrict_b<T, S, false><<<g, dim3(TXC, TYC), 0, s>>>(d);
+    k_resid_restrict_b<T, S, false><<<g, dim3(TXC, TYC), 0, s>>>(d, dir);
   count_launch();
 }
 
 template <typename T, typename S>
-void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s) {
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din, int dout) {
   if (count <= 0) return;
   int nc = (n - 1) / 2;
-  k_interp_b<T, S><<<dim3((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d);
+  k_interp_b<T, S><<<dim3((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d, din,
+                                                                                                       dout);
   count_launch();
+}
+
+template <typename S, int TY, int RING, bool PAIR>
+static void strip_b_launch(const LevelDesc<float, S>* d, int count, int n, int dir, cudaStream_t s) {
+  if (count <= 0) return;
+  constexpr size_t bytes = (size_t)STRIP_WARPS_B * RING * (StripRing<S>::SLOT + 8);
+  static bool attr = false;
+  const int width = PAIR ? 48 : 56;
+  const long warps = (long)count * ((n + width - 1) / width) * ((n + TY - 1) / TY);
+  const unsigned blocks = (unsigned)((warps + STRIP_WARPS_B - 1) / STRIP_WARPS_B);
+  if (PAIR) {
+    if (!attr)
+      cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_gs_strip2_ring_b<S, TY, RING><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+  } else {
+    if (!attr)
+      cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_gs_strip_ring_b<S, TY, RING><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+  }
+  attr = true;
+  count_launch();
+}
+
+template <typename S>
+void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip_b_launch<S, 8, 4, false>(d, count, n, dir, s); break;
+    case 2: strip_b_launch<S, 16, 4, false>(d, count, n, dir, s); break;
+    case 3: strip_b_launch<S, 32, 4, false>(d, count, n, dir, s); break;
+    default: strip_b_launch<S, 26, 4, false>(d, count, n, dir, s); break;
+  }
+}
+
+template <typename S>
+void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip_b_launch<S, 16, 4, true>(d, count, n, dir, s); break;
+    case 2: strip_b_launch<S, 32, 6, true>(d, count, n, dir, s); break;
+    case 3: strip_b_launch<S, 26, 4, true>(d, count, n, dir, s); break;
+    default: strip_b_launch<S, 32, 4, true>(d, count, n, dir, s); break;
+  }
+}
+template void launch_gs_tile_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t);
+template void launch_gs_tile_b<__nv_bfloat16>(const LevelDesc<float, __nv_bfloat16>*, int, int, int, int,
+                                              cudaStream_t);
+template void launch_gs_pair_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t);
+template void launch_gs_pair_b<__nv_bfloat16>(const LevelDesc<float, __nv_bfloat16>*, int, int, int, int,
+                                              cudaStream_t);
+
+int strip_timeouts_b() {
+  int h = 0, zero = 0;
+  cudaMemcpyFromSymbol(&h, g_strip_timeout_b, sizeof(int));
+  if (h) cudaMemcpyToSymbol(g_strip_timeout_b, &zero, sizeof(int));
+  return h;
 }
 
 template <typename T, typename S>
@@ -213,8 +314,8 @@ void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaS
 
 #define BMG_INST_B(T, S)                                                                                 \
   template void launch_gs_b<T, S>(const LevelDesc<T, S>*, int, int, int, int, int, cudaStream_t);       \
-  template void launch_resid_restrict_b<T, S>(const LevelDesc<T, S>*, int, int, int, cudaStream_t);     \
-  template void launch_interp_b<T, S>(const LevelDesc<T, S>*, int, int, cudaStream_t);                 \
+  template void launch_resid_restrict_b<T, S>(const LevelDesc<T, S>*, int, int, int, cudaStream_t, int); \
+  template void launch_interp_b<T, S>(const LevelDesc<T, S>*, int, int, cudaStream_t, int, int);       \
   template void launch_coarse_b<T, S>(const LevelDesc<T, S>*, int, cudaStream_t);
 BMG_INST_B(double, double)
 BMG_INST_B(float, float)

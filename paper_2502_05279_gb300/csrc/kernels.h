@@ -127,6 +127,7 @@ struct LevelDesc {
   const int* done;    // the problem's control flag
   const double* L;    // coarsest level: Cholesky factor and substitution workspace
   double* y;
+  T* x2 = nullptr;    // second iterate of a level swept by the one-pass kernels (else NULL)
 };
 
 // A problem's finest level, for the FP64 outer loop.
@@ -144,9 +145,19 @@ struct TopDesc {
 template <typename T, typename S>
 void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s);
 template <typename T, typename S>
-void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s);
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir = 0);
 template <typename T, typename S>
-void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s);
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din = 0, int dout = 0);
+// Batched one-pass sweeps of 9-point FP32 levels (all `count` problems share
+// n): dir 0 reads x and writes x2, dir 1 the reverse (the residual +
+// restriction reads, and the interpolation reads / writes, the array its dir
+// flags name: 0 = x, 1 = x2).  Shapes as launch_gs_tile 0 .. 3 and
+// launch_gs_pair; arrays in the guarded, aligned layout.
+template <typename S>
+void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s);
+template <typename S>
+void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s);
+int strip_timeouts_b();
 template <typename T, typename S>
 void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s);
 void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s);

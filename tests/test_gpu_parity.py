@@ -314,14 +314,17 @@ def batch_problems(sizes, std=1.0):
     return out
 
 
-@pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("precision,nbf,smoother", [("fp64", None, "auto"), ("fp32", 0, "auto"), ("bf16", 2, "auto"),
+                                                    ("fp32", 0, "tile0"), ("fp32", 0, "tile3"), ("bf16", 2, "tile2"),
+                                                    ("fp32", 0, "pair0"), ("bf16", 2, "pair3")])
 @pytest.mark.parametrize("graph", [True, False])
-def test_batched_matches_oracle_per_problem(bmg, precision, nbf, graph):
+def test_batched_matches_oracle_per_problem(bmg, precision, nbf, smoother, graph):
     """Uneven sizes (several problems per size, sizes from 3 to 255, ragged
-    tiles), every problem's iterate and history equal its oracle solve."""
+    tiles), every problem's iterate and history equal its oracle solve; with
+    the one-pass / two-sweep kernels forced on the FP32 stages as well."""
     sizes = [63, 255, 7, 127, 63, 3, 255, 31, 15, 127, 63]
     probs = batch_problems(sizes)
-    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision=precision, use_graph=graph)
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision=precision, use_graph=graph, smoother=smoother)
     xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-9, maxit=100)
     assert ok
     for k, (kind, planes, f) in enumerate(probs):
@@ -336,10 +339,11 @@ def test_batched_matches_oracle_per_problem(bmg, precision, nbf, graph):
     B.close()
 
 
-def test_batched_equals_solo_solve(bmg):
-    sizes = [127, 255, 63]
+@pytest.mark.parametrize("smoother", ["auto", "pair3"])
+def test_batched_equals_solo_solve(bmg, smoother):
+    sizes = [127, 255, 63, 511]
     probs = batch_problems(sizes, std=2.0)
-    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32")
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32", smoother=smoother)
     xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-9, maxit=200)
     for k, (kind, planes, f) in enumerate(probs):
         h = bmg.Hierarchy(kind, dev(planes), precision="fp32")
@@ -355,11 +359,12 @@ def test_batched_time_cycles_and_tuner(bmg):
     xs = [torch.zeros_like(r) for r in rhs]
     ms = B.time_cycles(rhs, xs, 3)
     assert ms > 0
-    # stages of n >= 127 were tuned to an admissible cluster size
+    # stages of n >= 127 were tuned to an admissible row-kernel cluster size
+    # or (FP32, n >= 255) a one-pass shape
     for stage in range(1, 8):
         cl = B.tuned_cluster(stage)
-        assert cl in (0, 1, 2, 4, 8)
-    assert B.tuned_cluster(6) in (1, 2, 4, 8)   # n = 255
+        assert cl in (0, 1, 2, 4, 8, 16, 17, 18, 19)
+    assert B.tuned_cluster(6) in (1, 2, 4, 8, 16, 17, 18, 19)   # n = 255
     B.close()
 
 
