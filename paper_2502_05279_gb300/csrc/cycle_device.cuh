@@ -753,22 +753,28 @@ __device__ __forceinline__ void finalize_body(const double* __restrict__ partial
 }
 
 // ---- coarsest solve: forward and back substitution (one thread) -------------------------
+// The substitutions are one dependent chain; thread 0 runs it with the
+// intermediate vector in shared memory (a chain through global memory would
+// pay an L2 round trip per term).  y is unused (kept for the callers' layout).
+constexpr int COARSE_M_MAX = 225;   // coarsest level n <= 15
 template <typename T>
 __device__ __forceinline__ void coarse_solve_body(int n, const double* __restrict__ L, const T* __restrict__ f,
                                                   T* __restrict__ x, double* __restrict__ y) {
+  __shared__ double ys[COARSE_M_MAX];
+  (void)y;
   if (threadIdx.x != 0) return;
   int m = n * n, ld = n + 2;
   for (int i = 0; i < m; ++i) {
     double s = (double)f[(size_t)(i / n + 1) * ld + (i % n + 1)];
-    for (int k = 0; k < i; ++k) s = rsub(s, rmul(L[(size_t)i * m + k], y[k]));
-    y[i] = rdiv(s, L[(size_t)i * m + i]);
+    for (int k = 0; k < i; ++k) s = rsub(s, rmul(__ldg(&L[(size_t)i * m + k]), ys[k]));
+    ys[i] = rdiv(s, __ldg(&L[(size_t)i * m + i]));
   }
   for (int i = m - 1; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(L[(size_t)k * m + i], y[k]));
-    y[i] = rdiv(s, L[(size_t)i * m + i]);
+    double s = ys[i];
+    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(__ldg(&L[(size_t)k * m + i]), ys[k]));
+    ys[i] = rdiv(s, __ldg(&L[(size_t)i * m + i]));
   }
-  for (int i = 0; i < m; ++i) x[(size_t)(i / n + 1) * ld + (i % n + 1)] = (T)y[i];
+  for (int i = 0; i < m; ++i) x[(size_t)(i / n + 1) * ld + (i % n + 1)] = (T)ys[i];
 }
 
 // ---- iterative refinement ------------------------------------------------------------------
