@@ -218,6 +218,51 @@ def gs_sweep(kind: int, planes, dinv, x, f) -> None:
             gs_colour(planes, dinv, x, f, pi, pj)
 
 
+# Line relaxation (Fig. 1 "Line" relaxation; the smoother BoxMG offers for
+# anisotropic operators)
+def line_sweep(kind: int, planes, x, f) -> None:
+    """One zebra x-line Gauss-Seidel sweep: the odd rows, then the even rows.
+    Each row j is solved exactly along x with the other rows held fixed: the
+    row's equations form a tridiagonal system with diagonal a_O, sub-diagonal
+    a_W and super-diagonal a_E, whose right-hand side is f minus the couplings
+    to rows j - 1 and j + 1 in the canonical order S, N, SW, NE, NW, SE.  The
+    system is solved by the Thomas algorithm (forward elimination
+    m_i = a_O - a_W c_{i-1}, c_i = a_E / m_i, d_i = (g_i - a_W d_{i-1}) / m_i,
+    then x_n = d_n, x_i = d_i - c_i x_{i+1}), one rounding per operation.
+    Rows of one parity share no coupling, so they are solved together."""
+    del kind   # the 5-point planes SW, NW are zero: their terms subtract exact zeros
+    n = size_of(x)
+    for first in (1, 2):                                 # odd rows, then even rows
+        rows = slice(first - 1, n, 2)                    # interior row index j - 1
+        g = at(f, 0, 0)[rows].copy()
+        for di, dj in NBR[3:]:                           # S, N, SW, NE, NW, SE
+            g = g - coupling(planes, di, dj)[rows] * at(x, di, dj)[rows]
+        aO = coupling(planes, 0, 0)[rows]
+        aW = coupling(planes, -1, 0)[rows]
+        aE = coupling(planes, 1, 0)[rows]
+        c = np.empty_like(g)
+        d = np.empty_like(g)
+        c[:, 0] = aE[:, 0] / aO[:, 0]
+        d[:, 0] = g[:, 0] / aO[:, 0]
+        for i in range(1, n):
+            m = aO[:, i] - aW[:, i] * c[:, i - 1]
+            c[:, i] = aE[:, i] / m
+            d[:, i] = (g[:, i] - aW[:, i] * d[:, i - 1]) / m
+        xr = at(x, 0, 0)[rows]                           # a view: written in place
+        xr[:, n - 1] = d[:, n - 1]
+        for i in range(n - 2, -1, -1):
+            xr[:, i] = d[:, i] - c[:, i] * xr[:, i + 1]
+
+
+def relax(lev, x, f) -> None:
+    """One sweep of the level's smoother: point Gauss-Seidel (default) or
+    zebra x-line Gauss-Seidel."""
+    if getattr(lev, "smoother", "point") == "line":
+        line_sweep(lev.kind, lev.planes, x, f)
+    else:
+        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f)
+
+
 # ---------------------------------------------------------------------------
 # Dendy interpolation (A2)
 # ---------------------------------------------------------------------------
@@ -470,9 +515,12 @@ class Level:
         self.L = None
 
 
-def setup(kind: int, planes: np.ndarray, coarsest: int = 3) -> list[Level]:
+def setup(kind: int, planes: np.ndarray, coarsest: int = 3, smoother: str = "point") -> list[Level]:
     """Build the hierarchy: Dendy P and Galerkin A_c level by level, then the
-    Cholesky factor of the coarsest operator."""
+    Cholesky factor of the coarsest operator.  smoother: "point" (Gauss-Seidel
+    by colours) or "line" (zebra x-line Gauss-Seidel) on every level."""
+    if smoother not in ("point", "line"):
+        raise ValueError("smoother must be 'point' or 'line'")
     planes = np.array(planes, dtype=np.float64)
     n = size_of(planes)
     sizes = level_sizes(n, coarsest)
@@ -484,6 +532,7 @@ def setup(kind: int, planes: np.ndarray, coarsest: int = 3) -> list[Level]:
     levels = []
     for li, nl in enumerate(sizes):
         lev = Level(nl, kind, planes)
+        lev.smoother = smoother
         if li == len(sizes) - 1:
             lev.L = cholesky(dense_matrix(planes))
         else:
@@ -511,14 +560,14 @@ def vcycle(levels, l, x, f, nu1=2, nu2=1) -> None:
         coarse_solve(lev, x, f)
         return
     for _ in range(nu1):
-        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f)
+        relax(lev, x, f)
     r = residual(lev.planes, x, f)
     fc = restrict(lev.ci, r)
     xc = np.zeros_like(fc)
     vcycle(levels, l + 1, xc, fc, nu1, nu2)
     interp_correct(lev.ci, xc, x)
     for _ in range(nu2):
-        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f)
+        relax(lev, x, f)
 
 
 def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):

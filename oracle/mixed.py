@@ -65,6 +65,7 @@ def lower(levels, bf16_levels: int = 0) -> list[Level32]:
             bx.at(dinv, 0, 0)[...] = F32(1) / o32
         ci = None if lev.ci is None else lev.ci.astype(F32)
         out.append(Level32(lev.n, lev.kind, planes, dinv, ci, lev.L))
+        out[-1].smoother = getattr(lev, "smoother", "point")
     return out
 
 

@@ -508,3 +508,63 @@ def test_fcg_ir_reaches_fp64_accuracy():
     x, hist = mx.solve_fcg_ir(levels, mx.lower(levels, 2), f, tol=1e-10, maxit=200)
     assert hist[-1] <= 1e-10 * hist[0]
     assert bx.norm(bx.residual(levels[0].planes, x, f)) <= 1e-9 * hist[0]
+
+
+# --------------------------------------------------------------------------
+# Line relaxation (Fig. 1 "Line"; zebra x-lines)
+# --------------------------------------------------------------------------
+
+def _row_coupled_only(n, seed):
+    """Random diagonally dominant stencil with couplings along x only."""
+    planes = np.zeros((5, n + 2, n + 2))
+    u = w.uniform01(seed, 2 * n * n).reshape(2, n, n)
+    planes[1, 1:-1, 1:-1] = -(0.5 + u[0])                 # W
+    planes[0, 1:-1, 1:-1] = 3.0 + u[1]                    # O > |W| + |E|
+    return w.zero_ghost_couplings(planes)
+
+
+def test_line_sweep_solves_rows_without_cross_coupling_exactly():
+    """With no coupling between rows A is block diagonal by rows, so one line
+    sweep is a direct solve (compared with a dense LU solve)."""
+    n = 31
+    planes = _row_coupled_only(n, 41)
+    f = w.rhs_uniform(n, 42)
+    x = w.rhs_uniform(n, 43)                              # any initial guess
+    bx.line_sweep(5, planes, x, f)
+    A = sparse_A(planes).toarray()
+    xs = np.linalg.solve(A, bx.at(f, 0, 0).reshape(-1))
+    assert np.allclose(bx.at(x, 0, 0).reshape(-1), xs, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["lognormal", "binary"])
+def test_line_sweep_leaves_the_last_rows_exact(case):
+    """The even rows are solved last with the odd rows held at their final
+    values, so after a sweep every even row's equations hold to rounding
+    (residual from an independently assembled sparse A); the odd rows' do
+    not (they saw the old even rows)."""
+    n = 31
+    kind, planes, f = (w.lognormal_problem(n, 2.0, 8.0, seed_k=4, seed_f=7) if case == "lognormal"
+                       else w.binary_contrast_problem(n, 4, seed_k=2, seed_f=3))
+    planes = bx.drop_ghost_couplings(np.array(planes))
+    x = w.rhs_uniform(n, 44)
+    bx.line_sweep(kind, planes, x, f)
+    A = sparse_A(planes)
+    r = (bx.at(f, 0, 0).reshape(-1) - A @ bx.at(x, 0, 0).reshape(-1)).reshape(n, n)
+    scale = np.abs(bx.at(f, 0, 0)).max() + np.abs(A).max() * np.abs(x).max()
+    assert np.abs(r[1::2, :]).max() <= 1e-12 * scale      # rows j = 2, 4, ... (index j - 1 odd)
+    assert np.abs(r[0::2, :]).max() > 1e-6 * scale        # odd rows moved afterwards
+
+
+def test_line_relaxation_handles_strong_x_coupling():
+    """-(u_xx + eps u_yy), eps = 1e-3: point Gauss-Seidel V-cycles stall, x-line
+    V-cycles converge fast (measured asymptotic factors)."""
+    n, eps = 63, 1e-3
+    planes = w.anisotropic5(n, eps)
+    f = w.rhs_uniform(n, 5)
+    factors = {}
+    for sm in ("point", "line"):
+        levels = bx.setup(5, planes, smoother=sm)
+        x, hist = bx.solve(levels, f, tol=1e-12, maxit=30)
+        k = min(len(hist) - 1, 8)
+        factors[sm] = (hist[k] / hist[k - 3]) ** (1 / 3)
+    assert factors["point"] > 0.9 and factors["line"] < 0.1, factors

@@ -105,6 +105,16 @@ def poisson5(n: int) -> np.ndarray:
     return zero_ghost_couplings(planes)
 
 
+def anisotropic5(n: int, eps: float) -> np.ndarray:
+    """5-point finite differences of -(u_xx + eps u_yy) (unscaled): O = 2 (1 + eps),
+    W = -1, S = -eps, ghost couplings zero; planes SW, NW are zero."""
+    planes = np.zeros((5, n + 2, n + 2))
+    planes[0, 1:-1, 1:-1] = 2.0 * (1.0 + eps)
+    planes[1, 1:-1, 1:-1] = -1.0
+    planes[2, 1:-1, 1:-1] = -eps
+    return zero_ghost_couplings(planes)
+
+
 def fe9_from_cells(k: np.ndarray) -> np.ndarray:
     """9-point bilinear (Q1) finite-element stiffness stencil of -div(k grad u)
     on a uniform grid, with k constant on each cell.
