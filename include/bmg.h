@@ -106,6 +106,8 @@ typedef struct {
 #define BMG_SMOOTHER_TILE 2
 #define BMG_SMOOTHER_PAIR 8   /* + s (s = 0 .. 3): pairs of sweeps as one two-sweep pass of shape s,
                                  single sweeps with one-pass shape 3 */
+#define BMG_SMOOTHER_LINE 12  /* zebra x-line Gauss-Seidel on every level (FP64 and FP32 cycles, single
+                                 problems): odd rows, then even rows, each solved exactly along x */
 
 /* ---- whole solver ------------------------------------------------------ */
 
@@ -307,6 +309,17 @@ int bmg_rap(int n, const double* coef, const double* ci, double* coarse, void* s
  * red-black for kind 5, four colours (i,j parities (odd,odd), (even,odd),
  * (odd,even), (even,even)) for kind 9; x_p = (f_p - sum_{q!=p} a_pq x_q) * (1/a_pp). */
 int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, int sweeps, void* stream);
+
+/* Zebra x-line Gauss-Seidel (Fig. 1 "Line" relaxation; the smoother for
+ * operators coupled much more strongly along x than along y), `sweeps`
+ * sweeps in place on x: the odd rows, then the even rows, each solved
+ * exactly along x (Thomas algorithm) with the other rows held fixed; the
+ * couplings to rows j - 1, j + 1 move to the right-hand side in the order
+ * S, N, SW, NE, NW, SE.  coef, f, x as bmg_relax; work: device scratch of
+ * (n+2)^2 doubles (the elimination multipliers).  Returns BMG_EINVAL or
+ * BMG_ECUDA. */
+int bmg_relax_line(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
+                   void* stream);
 
 /* f_c = P^T (f - A x) with the Fig. 2 restriction (Fig. 1 "Residual",
  * "Restrict"); fc: out, (n_c+2)^2, interior written, ghost ring zeroed. */

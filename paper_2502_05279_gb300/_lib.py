@@ -46,7 +46,7 @@ KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "re
 _KRYLOV = {"none": 0, "fcg": 1}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
 _SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
-             "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}}
+             "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12}
 TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
 
 
@@ -73,6 +73,7 @@ _sig = {
     "bmg_dendy_interp": (I, [I, P, P, P]),
     "bmg_rap": (I, [I, P, P, P, P]),
     "bmg_relax": (I, [I, I, P, P, P, I, P]),
+    "bmg_relax_line": (I, [I, I, P, P, P, P, I, P]),
     "bmg_resid_restrict": (I, [I, I, P, P, P, P, P, P]),
     "bmg_interp_correct": (I, [I, P, P, P, P]),
     "bmg_residual": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
@@ -393,6 +394,13 @@ def rap(coef: torch.Tensor, ci: torch.Tensor) -> torch.Tensor:
 
 def relax(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
     _check(lib.bmg_relax(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), sweeps, _stream()))
+    return x
+
+
+def relax_line(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
+    """Zebra x-line Gauss-Seidel sweeps in place on x (bmg_relax_line)."""
+    work = torch.empty_like(x)
+    _check(lib.bmg_relax_line(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), _ptr(work), sweeps, _stream()))
     return x
 
 

@@ -79,6 +79,8 @@ struct Level {
   float* f32 = nullptr;
   int tile32 = -1;        // FP32 sweeps: -1 row kernel (in place), else tile shape of the one-pass kernel
   int pair32 = -1;        // >= 0: pairs of sweeps run as one two-sweep launch of this shape (needs tile32 >= 0)
+  double* lcp = nullptr;  // line relaxation: elimination multipliers (FP64 cycle)
+  float* lcp32 = nullptr; // the same for the FP32 cycle
   float* x32b = nullptr;  // second iterate of a tile-swept level (sweeps alternate x32 <-> x32b)
 };
 
@@ -202,11 +204,17 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   }
   auto v = view64(L);
   Level& C = h->lv[l + 1];
-  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu1, done, s, L.cl64); });
+  auto relax64 = [&](int sweeps) {
+    if (h->smoother == BMG_SMOOTHER_LINE)
+      step(h, l, BMG_K_RELAX, 0, [&] { launch_line<double, double>(v, L.kind, f, x, L.lcp, sweeps, done, s); });
+    else
+      step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, sweeps, done, s, L.cl64); });
+  };
+  relax64(h->nu1);
   step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, x, f, C.f, C.x, done, s); });
   vcycle64(h, l + 1, C.x, C.f, done);
   step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s); });
-  step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, h->nu2, done, s, L.cl64); });
+  relax64(h->nu2);
 }
 
 // Sweeps of an FP32 level.  Row kernel: in place on x32.  One-pass tile kernel:
@@ -214,6 +222,11 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
 template <typename S>
 void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, float** cur, const int* done) {
   Level& L = h->lv[l];
+  if (h->smoother == BMG_SMOOTHER_LINE) {
+    step(h, l, BMG_K_RELAX, 1,
+         [&] { launch_line<float, S>(v, L.kind, (const float*)L.f32, L.x32, L.lcp32, sweeps, done, h->ws); });
+    return;
+  }
   if (L.tile32 < 0) {
     step(h, l, BMG_K_RELAX, 1,
          [&] { launch_gs(v, L.kind, (const float*)L.f32, L.x32, sweeps, done, h->ws, L.cl32); });
@@ -491,6 +504,16 @@ int force_tile(bmg_hierarchy* h) {
   return BMG_OK;
 }
 
+// BMG_SMOOTHER_LINE: the multiplier scratch of every relaxed level.
+int alloc_line(bmg_hierarchy* h) {
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    Level& L = h->lv[l];
+    int rc = h->precision == BMG_FP64 ? dalloc(&L.lcp, plane_size(L.n)) : galloc(&L.lcp32, L.n, 1, h->ws);
+    if (rc) return rc;
+  }
+  return BMG_OK;
+}
+
 int autotune_solo(bmg_hierarchy* h) {
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
@@ -608,6 +631,8 @@ void free_level(Level& L) {
   cudaFree(L.ci);
   cudaFree(L.x);
   cudaFree(L.f);
+  cudaFree(L.lcp);
+  gfree(L.lcp32);
   gfree(L.st32);
   gfree(L.off16);
   gfree(L.od32);
@@ -788,7 +813,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   }
   if (h->smoother < BMG_SMOOTHER_AUTO ||
       (h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES && h->smoother < BMG_SMOOTHER_PAIR) ||
-      h->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES) {
+      (h->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES && h->smoother != BMG_SMOOTHER_LINE)) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad smoother %d", h->smoother);
   }
@@ -805,9 +830,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = setup_impl(h, A, nx, o);
-  if (!rc && h->precision != BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
-  if (!rc && h->use_graph) rc = autotune_solo(h);
-  if (!rc && h->use_graph) rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
+  const bool line = h->smoother == BMG_SMOOTHER_LINE;
+  if (!rc && line) rc = alloc_line(h);
+  if (!rc && !line && h->precision != BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
+  if (!rc && !line && h->use_graph) rc = autotune_solo(h);
+  if (!rc && !line && h->use_graph)   // the level-fused tail relaxes by points
+    rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
   if (!rc) rc = ensure_ctl(h, 64);
   if (rc) {
     bmg_free(h);
@@ -1103,6 +1131,15 @@ int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, i
   cudaStream_t s = (cudaStream_t)stream;
   launch_gs(raw_view(n, coef, false), kind, f, x, sweeps, (const int*)nullptr, s);
   return step_done(s, "bmg_relax");
+}
+
+int bmg_relax_line(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
+                   void* stream) {
+  if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !f || !x || !work || sweeps < 0)
+    return set_error(BMG_EINVAL, "bmg_relax_line: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_line<double, double>(raw_view(n, coef, false), kind, f, x, work, sweeps, (const int*)nullptr, s);
+  return step_done(s, "bmg_relax_line");
 }
 
 int bmg_resid_restrict(int n, int kind, const double* coef, const double* ci, const double* x, const double* f,
@@ -1683,6 +1720,10 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   so.use_graph = 0;
   so.smoother = BMG_SMOOTHER_AUTO;
   if (o) B->smoother = o->smoother;
+  if (B->smoother == BMG_SMOOTHER_LINE) {
+    delete B;
+    return set_error(BMG_EINVAL, "bmg_setup_batched: line relaxation is available for single problems only");
+  }
   if (B->smoother < BMG_SMOOTHER_AUTO ||
       (B->smoother >= BMG_SMOOTHER_TILE + 4 && B->smoother < BMG_SMOOTHER_PAIR) ||
       B->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES) {

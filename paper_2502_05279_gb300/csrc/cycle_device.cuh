@@ -150,6 +150,47 @@ __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T
   }
 }
 
+// ---- zebra x-line Gauss-Seidel ------------------------------------------------------------
+// Row j solved exactly along x with the rows j - 1, j + 1 held fixed: right-hand
+// side g = f - (S, N, SW, NE, NW, SE couplings) x in that order (5-point
+// stencils: S, N only), then the Thomas algorithm: m = a_O - a_W c', c' = a_E / m,
+// d' = (g - a_W d') / m forward (c' into cp, d' into x), x_i = d'_i - c'_i x_{i+1}
+// backward.  One rounding per operation, correctly rounded quotients.
+template <typename T, typename S, bool NINE>
+__device__ __forceinline__ void line_row_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x,
+                                              T* __restrict__ cp, int j) {
+  const int n = v.n, ld = v.ld;
+  const size_t r0 = (size_t)j * ld;
+  T c = T(0), d = T(0);
+  for (int i = 1; i <= n; ++i) {
+    const size_t p = r0 + i;
+    T g = f[p];
+    g = rsub(g, rmul(cvt<T>(v.S_[p]), x[p - ld]));
+    g = rsub(g, rmul(cvt<T>(v.S_[p + ld]), x[p + ld]));
+    if (NINE) {
+      g = rsub(g, rmul(cvt<T>(v.SW[p]), x[p - ld - 1]));
+      g = rsub(g, rmul(cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]));
+      g = rsub(g, rmul(cvt<T>(v.NW[p]), x[p + ld - 1]));
+      g = rsub(g, rmul(cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]));
+    }
+    const T aO = v.O[p], aW = cvt<T>(v.W[p]), aE = cvt<T>(v.W[p + 1]);
+    if (i == 1) {
+      c = rdiv(aE, aO);
+      d = rdiv(g, aO);
+    } else {
+      const T m = rsub(aO, rmul(aW, c));
+      c = rdiv(aE, m);
+      d = rdiv(rsub(g, rmul(aW, d)), m);
+    }
+    cp[p] = c;
+    x[p] = d;
+  }
+  for (int i = n - 1; i >= 1; --i) {
+    const size_t p = r0 + i;
+    x[p] = rsub(x[p], rmul(cp[p], x[p + 1]));
+  }
+}
+
 // Red-black half sweep for 5-point stencils: the points with (i + j) % 2 == c
 // (c = 0 red, c = 1 black), which share no coupling.  Thread grid: x over the
 // points of a row, y over rows.

@@ -81,6 +81,16 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView
     atomicExch(&g_strip_timeout, 1);
 }
 
+// Zebra x-lines: one thread per row of the parity (first row 1 or 2).
+template <typename T, typename S, bool NINE>
+__global__ void k_line_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, T* __restrict__ cp, int first,
+                            const int* done) {
+  if (stopped(done)) return;
+  const int j = first + 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j > v.n) return;
+  line_row_body<T, S, NINE>(v, f, x, cp, j);
+}
+
 template <typename T, typename S, bool NINE>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
                                                             const T* __restrict__ x, const T* __restrict__ f,
@@ -330,6 +340,29 @@ int strip_timeouts() {
   if (h) cudaMemcpyToSymbol(g_strip_timeout, &zero, sizeof(int));
   return h;
 }
+
+template <typename T, typename S>
+void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, const int* done,
+                 cudaStream_t s) {
+  constexpr int TPB = 64;
+  for (int k = 0; k < sweeps; ++k)
+    for (int first = 1; first <= 2; ++first) {           // odd rows, then even rows
+      const int rows = first == 1 ? (v.n + 1) / 2 : (v.n - 1) / 2;
+      if (rows <= 0) continue;
+      const unsigned g = (unsigned)((rows + TPB - 1) / TPB);
+      if (kind == 9)
+        k_line_rows<T, S, true><<<g, TPB, 0, s>>>(v, f, x, cp, first, done);
+      else
+        k_line_rows<T, S, false><<<g, TPB, 0, s>>>(v, f, x, cp, first, done);
+      count_launch();
+    }
+}
+template void launch_line<double, double>(const StencilView<double, double>&, int, const double*, double*, double*,
+                                          int, const int*, cudaStream_t);
+template void launch_line<float, float>(const StencilView<float, float>&, int, const float*, float*, float*, int,
+                                        const int*, cudaStream_t);
+template void launch_line<float, __nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, int, const float*, float*,
+                                                float*, int, const int*, cudaStream_t);
 
 template <typename T>
 void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s) {

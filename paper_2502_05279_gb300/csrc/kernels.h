@@ -39,6 +39,12 @@ void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od3
 template <typename T, typename S>
 void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
                int cl = 0);   // cl: row-kernel cluster size, 0 = the smallest that covers a row
+// Zebra x-line Gauss-Seidel sweeps (odd rows, then even rows, each solved
+// exactly along x); cp: scratch of the level's (n+2)^2 layout for the
+// elimination multipliers.
+template <typename T, typename S>
+void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, const int* done,
+                 cudaStream_t s);
 // FP32 / BF16 level arrays are allocated with STRIP_GUARD zeroed elements
 // before and after each array (plane), every array starting on a 256-byte
 // boundary; planes of one level are plane_stride32(n) elements apart.  The

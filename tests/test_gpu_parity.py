@@ -499,3 +499,71 @@ def test_bounded_wait_gives_up_and_context_stays_usable(bmg):
     x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
     assert ok and np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
     h.close()
+
+
+# ---- zebra x-line relaxation ---------------------------------------------------------------
+
+def line_problem(case, n):
+    if case == "aniso":
+        return 5, w.anisotropic5(n, 1e-3), w.rhs_uniform(n, 5)
+    return problem(case, n)
+
+
+@pytest.mark.parametrize("case,n", [("poisson", 63), ("lognormal", 255), ("binary", 127), ("aniso", 127)])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_line_relax_step_bitwise(bmg, case, n, sweeps):
+    kind, planes, f = line_problem(case, n)
+    planes = bx.drop_ghost_couplings(np.array(planes))
+    x0 = w.rhs_uniform(n, 98)
+    want = x0.copy()
+    for _ in range(sweeps):
+        bx.line_sweep(kind, planes, want, f)
+    got = host(bmg.relax_line(kind, dev(planes[:3] if kind == 5 else planes), dev(f), dev(x0), sweeps))
+    assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0))
+
+
+@pytest.mark.parametrize("case,n", [("aniso", 127), ("lognormal", 255), ("binary", 127)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_line_solve_matches_oracle(bmg, case, n, graph):
+    kind, planes, f = line_problem(case, n)
+    levels = bx.setup(kind, planes, smoother="line")
+    xw, hw = bx.solve(levels, f, tol=1e-10, maxit=100)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), smoother="line", use_graph=graph)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+    check_history(h.history(), hw)
+    h.close()
+
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+def test_line_refinement_and_fcg_match_oracle(bmg, precision, nbf):
+    kind, planes, f = line_problem("aniso", 127)
+    levels = bx.setup(kind, planes, smoother="line")
+    xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=100)
+    h = bmg.Hierarchy(kind, dev(planes[:3]), precision=precision, smoother="line")
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+    check_history(h.history(), hw)
+    h.close()
+    kind, planes, f = line_problem("lognormal", 127)
+    levels = bx.setup(kind, planes, smoother="line")
+    xw, hw = bx.solve_fcg(levels, f, tol=1e-10, maxit=100)
+    h = bmg.Hierarchy(kind, dev(planes), smoother="line", krylov="fcg")
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+    assert ok and it == len(hw) - 1 and np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+    h.close()
+
+
+def test_line_relaxation_solves_anisotropy_point_gs_does_not(bmg):
+    kind, planes, f = line_problem("aniso", 255)
+    its = {}
+    for sm in ("auto", "line"):
+        h = bmg.Hierarchy(kind, dev(planes[:3]), smoother=sm)
+        x, it, rr, ok = h.solve(dev(f), tol=1e-8, maxit=60)
+        its[sm] = (it, ok)
+        h.close()
+    assert its["line"][1] and its["line"][0] <= 10 and not its["auto"][1], its
+    with pytest.raises(bmg.BmgError):
+        bmg.Batch(5, [dev(planes[:3])], smoother="line")
