@@ -567,3 +567,25 @@ def test_line_relaxation_solves_anisotropy_point_gs_does_not(bmg):
     assert its["line"][1] and its["line"][0] <= 10 and not its["auto"][1], its
     with pytest.raises(bmg.BmgError):
         bmg.Batch(5, [dev(planes[:3])], smoother="line")
+
+
+@pytest.mark.parametrize("coarsest", [7, 15])
+@pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("case,n", [("lognormal", 255), ("binary", 15), ("poisson", 7)])
+def test_coarsest_size_and_single_level_hierarchies(bmg, coarsest, precision, nbf, case, n):
+    """A larger coarsest level (dense Cholesky of up to 225 unknowns), and
+    hierarchies whose finest level is the coarsest (n <= coarsest: one direct
+    solve per iteration)."""
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes, coarsest=min(coarsest, n))
+    if precision == "fp64":
+        xw, hw = bx.solve(levels, f, tol=1e-10, maxit=100)
+    else:
+        xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=100)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision, coarsest=coarsest)
+    assert h.num_levels == len(levels)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
+    check_history(h.history(), hw)
+    h.close()
