@@ -589,3 +589,48 @@ def test_coarsest_size_and_single_level_hierarchies(bmg, coarsest, precision, nb
     assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
     check_history(h.history(), hw)
     h.close()
+
+
+# ---- full benchmark sizes: properties the oracle can check at that scale -------------------
+
+@pytest.mark.slow
+def test_config3_full_size_setup_and_solves():
+    """8191^2 log-normal (sigma 2, 32-cell correlation): the Galerkin stencil of
+    the second level equals the oracle's bit for bit, and the stationary FP64
+    and BF16-refinement solves (which test the true FP64 residual each
+    iteration) return x whose oracle FP64 residual meets the tolerance."""
+    import paper_2502_05279_gb300 as bmg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kind, planes, f = w.lognormal_problem(8191, 2.0, 32.0, seed_k=4, seed_f=7)
+    p64 = bx.drop_ghost_couplings(np.array(planes))
+    f0 = bx.norm(bx.at(f, 0, 0))
+    coef, rhs = dev(planes), dev(f)
+    h = bmg.Hierarchy(kind, coef)
+    lv0 = bx.Level(8191, kind, p64)
+    lv0.ci = bx.dendy_interp(p64)
+    assert np.array_equal(host(h.interp(0)), lv0.ci)
+    assert np.array_equal(host(h.stencil(1)), bx.rap(p64, lv0.ci))
+    for hh in (h, bmg.Hierarchy(kind, coef, precision="bf16")):
+        x, it, rr, ok = hh.solve(rhs, tol=1e-10, maxit=100)
+        assert ok
+        assert bx.norm(bx.residual(p64, host(x), f)) <= 1e-10 * f0
+        assert hh.history()[-1] == bx.norm(bx.residual(p64, host(x), f))
+        hh.close()
+
+
+@pytest.mark.slow
+def test_config4_full_batch_converges_to_oracle_residuals():
+    """The 256-problem batch (sides 63 .. 1023, 80 M unknowns): every problem's
+    FP32-refinement solution meets tol 1e-8 by the oracle's FP64 residual."""
+    import paper_2502_05279_gb300 as bmg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    probs = w.batched_problems(256, 5, 1.0, 32.0)
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32")
+    xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-8, maxit=100)
+    assert ok
+    for (kind, planes, f), x in zip(probs, xs):
+        p64 = bx.drop_ghost_couplings(np.array(planes))
+        assert bx.norm(bx.residual(p64, host(x), f)) <= 1e-8 * bx.norm(bx.at(f, 0, 0))
+    B.close()
