@@ -219,6 +219,18 @@ typedef struct bmg_batch bmg_batch;   /* opaque, library-owned */
  * timing the candidates on scratch copies of that stage (autotuner). */
 int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* opts, bmg_batch** out);
 
+/* A batch of k right-hand sides for the operator of hierarchy h (built by
+ * bmg_setup, any options): the k members share h's stencils, interpolation
+ * weights and Cholesky factor (read-only; h must outlive the batch and is not
+ * modified) and own their iterates, right-hand sides and norm partials, so k
+ * solves of one operator need one setup and run as one batch
+ * (bmg_solve_batched: one launch per cycle stage for all k, one CUDA graph per
+ * iteration; every member's iterates and history equal h's solve of that
+ * right-hand side bit for bit).  opts as for bmg_setup_batched (stationary
+ * cycles only; precision, if given, must equal h's; coarsest and bf16 levels
+ * come from h).  Returns BMG_EINVAL, BMG_ENOMEM or BMG_ECUDA. */
+int bmg_batch_rhs(const bmg_hierarchy* h, int k, const bmg_opts* opts, bmg_batch** out);
+
 /* rhs[p], x[p]: host arrays of nprob device pointers, layouts as in bmg_solve.
  * iters, relres: host arrays of nprob entries (may be NULL).  Problems stop
  * individually at ||r_k||/||r_0|| <= tol.  Returns BMG_OK when all converged,

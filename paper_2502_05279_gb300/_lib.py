@@ -82,6 +82,7 @@ _sig = {
     "bmg_inner_cycle": (I, [P, P, P]),
     "bmg_measure_fp64_rate": (I, [ctypes.POINTER(D), P]),
     "bmg_wait_selftest": (I, []),
+    "bmg_batch_rhs": (I, [P, I, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
     "bmg_tuned_pair": (I, [P, I]),
     "bmg_time_cycles": (I, [P, P, P, I, ctypes.POINTER(D)]),
     "bmg_setup_batched": (I, [I, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
@@ -248,6 +249,22 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib.bmg_setup_batched(nprob, sts, ns, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def from_hierarchy(cls, h: "Hierarchy", k: int, nu1: int = 2, nu2: int = 1, inner_cycles: int = 1,
+                       use_graph: bool = True, smoother: str = "auto") -> "Batch":
+        """k right-hand sides of h's operator solved together (bmg_batch_rhs);
+        h must stay open while the batch is used."""
+        self = cls.__new__(cls)
+        self.kind, self.precision = h.kind, h.precision
+        self.ns = [h.n] * k
+        self._coefs = [h]   # keeps the hierarchy alive
+        o = Opts(_PREC[h.precision], 0, 0, nu1, nu2, inner_cycles, 0, int(use_graph), 0, None, _stream(),
+                 _SMOOTHER[smoother])
+        b = ctypes.c_void_p()
+        _check(lib.bmg_batch_rhs(h._h, k, ctypes.byref(o), ctypes.byref(b)))
+        self._h = b
+        return self
 
     def _ptrs(self, ts, name):
         return (ctypes.c_void_p * len(ts))(*[_ptr(t, name=name).value for t in ts])

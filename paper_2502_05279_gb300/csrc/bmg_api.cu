@@ -136,6 +136,9 @@ struct bmg_hierarchy {
   // level-fused tail: levels >= tail_l run in one launch (-1: none)
   int tail_l = -1;
   void* d_tail = nullptr;   // TailDesc<double> or TailDesc<float> in device memory
+  // a batch member that borrows the operator arrays (stencils, weights, Cholesky
+  // factor and its workspace) of another hierarchy and owns only its state
+  bool shared_ops = false;
 };
 
 namespace {
@@ -626,7 +629,15 @@ int ensure_ctl(bmg_hierarchy* h, int maxit) {
   return BMG_OK;
 }
 
-void free_level(Level& L) {
+void free_level(Level& L, bool shared_ops = false) {
+  if (shared_ops) {   // borrowed operator arrays stay with their owner
+    L.st = nullptr;
+    L.ci = nullptr;
+    L.st32 = nullptr;
+    L.off16 = nullptr;
+    L.od32 = nullptr;
+    L.ci32 = nullptr;
+  }
   cudaFree(L.st);
   cudaFree(L.ci);
   cudaFree(L.x);
@@ -1043,9 +1054,11 @@ long long bmg_launch_count(const bmg_hierarchy* h) { return h ? h->launches : 0;
 void bmg_free(bmg_hierarchy* h) {
   if (!h) return;
   if (h->ws) cudaStreamSynchronize(h->ws);
-  for (Level& L : h->lv) free_level(L);
-  cudaFree(h->Lfac);
-  cudaFree(h->work);
+  for (Level& L : h->lv) free_level(L, h->shared_ops);
+  if (!h->shared_ops) {
+    cudaFree(h->Lfac);
+    cudaFree(h->work);
+  }
   cudaFree(h->partials);
   cudaFree(h->kr);
   cudaFree(h->d_tail);
@@ -1702,34 +1715,20 @@ int autotune_batch(bmg_batch* B) {
   return BMG_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* o, bmg_batch** out) {
-  if (!out) return set_error(BMG_EINVAL, "bmg_setup_batched: out is NULL");
-  *out = nullptr;
-  if (nprob < 1 || !A || !n) return set_error(BMG_EINVAL, "bmg_setup_batched: bad argument");
-  if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_setup_batched: stationary cycles only");
-  for (int p = 1; p < nprob; ++p)
-    if (A[p].kind != A[0].kind) return set_error(BMG_EINVAL, "bmg_setup_batched: problems differ in kind");
-  bmg_batch* B = new bmg_batch();
-  B->nprob = nprob;
-  bmg_opts so{};
-  if (o) so = *o;
-  so.use_graph = 0;
-  so.smoother = BMG_SMOOTHER_AUTO;
+// Options and streams of a new batch; *so gets the options of its member
+// hierarchies (plain launches, point smoother, the batch's stream).
+int batch_init(bmg_batch* B, const bmg_opts* o, bmg_opts* so) {
+  *so = bmg_opts{};
+  if (o) *so = *o;
+  so->use_graph = 0;
+  so->smoother = BMG_SMOOTHER_AUTO;
   if (o) B->smoother = o->smoother;
-  if (B->smoother == BMG_SMOOTHER_LINE) {
-    delete B;
-    return set_error(BMG_EINVAL, "bmg_setup_batched: line relaxation is available for single problems only");
-  }
+  if (B->smoother == BMG_SMOOTHER_LINE)
+    return set_error(BMG_EINVAL, "batched solves: line relaxation is available for single problems only");
   if (B->smoother < BMG_SMOOTHER_AUTO ||
       (B->smoother >= BMG_SMOOTHER_TILE + 4 && B->smoother < BMG_SMOOTHER_PAIR) ||
-      B->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES) {
-    delete B;
-    return set_error(BMG_EINVAL, "bmg_setup_batched: bad smoother %d", o->smoother);
-  }
+      B->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES)
+    return set_error(BMG_EINVAL, "batched solves: bad smoother %d", B->smoother);
   if (o) {
     B->precision = o->precision;
     if (o->nu1 || o->nu2) {
@@ -1740,23 +1739,69 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
     B->use_graph = o->use_graph;
     B->user = (cudaStream_t)o->stream;
   }
-  CounterScope cs(&B->launches);
   int rc = cuda_check(cudaStreamCreateWithFlags(&B->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming), "event");
   if (!rc) rc = cuda_check(cudaEventRecord(B->ev, B->user), "event");
   if (!rc) rc = cuda_check(cudaStreamWaitEvent(B->ws, B->ev, 0), "event");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "sync");
-  so.stream = (void*)B->ws;
-  for (int p = 0; p < nprob && !rc; ++p) {
-    bmg_hierarchy* h = nullptr;
-    rc = bmg_setup(&A[p], n[p], n[p], &so, &h);
-    if (!rc) {
-      B->hs.push_back(h);
-      B->launches += h->launches;
-      B->maxn = std::max(B->maxn, n[p]);
-      B->bmax = std::max(B->bmax, h->nlev - 1);
+  so->stream = (void*)B->ws;
+  return rc;
+}
+
+// A member hierarchy for one more right-hand side of h0's operator: it borrows
+// h0's stencils, weights and Cholesky factor and owns zeroed iterates,
+// right-hand sides and norm partials.
+int clone_state(const bmg_hierarchy* h0, cudaStream_t s, bmg_hierarchy** out) {
+  bmg_hierarchy* h = new bmg_hierarchy();
+  h->shared_ops = true;
+  h->n = h0->n;
+  h->nlev = h0->nlev;
+  h->precision = h0->precision;
+  h->nu1 = h0->nu1;
+  h->nu2 = h0->nu2;
+  h->inner = h0->inner;
+  h->coarsest = h0->coarsest;
+  h->use_graph = 0;
+  h->m = h0->m;
+  h->Lfac = h0->Lfac;
+  h->work = h0->work;
+  h->lv.resize(h0->lv.size());
+  int rc = BMG_OK;
+  for (size_t l = 0; l < h0->lv.size() && !rc; ++l) {
+    const Level& S = h0->lv[l];
+    Level& L = h->lv[l];
+    L.n = S.n;
+    L.kind = S.kind;
+    L.bf16 = S.bf16;
+    L.st = S.st;
+    L.ci = S.ci;
+    L.st32 = S.st32;
+    L.off16 = S.off16;
+    L.od32 = S.od32;
+    L.ci32 = S.ci32;
+    const size_t ps = plane_size(L.n);
+    if (l >= 1) {
+      if (!(rc = dalloc(&L.x, ps))) rc = dalloc(&L.f, ps);
+      if (!rc) rc = cuda_check(cudaMemsetAsync(L.x, 0, ps * sizeof(double), s), "clone");
+      if (!rc) rc = cuda_check(cudaMemsetAsync(L.f, 0, ps * sizeof(double), s), "clone");
+    }
+    if (!rc && h->precision != BMG_FP64) {
+      if (!(rc = galloc(&L.x32, L.n, 1, s))) rc = galloc(&L.f32, L.n, 1, s);
     }
   }
+  if (!rc) rc = dalloc(&h->partials, 2 * (size_t)norm_partials_max());
+  if (rc) {
+    bmg_free(h);
+    return rc;
+  }
+  *out = h;
+  return BMG_OK;
+}
+
+// Stage tables, tails, control blocks and kernel choices of a batch whose
+// member hierarchies are in B->hs.
+int batch_finish(bmg_batch* B, int rc) {
+  const int nprob = B->nprob;
   if (!rc) {
     B->stages.assign(B->bmax + 1, {});
     B->tuned_cl.assign(B->bmax + 1, 0);
@@ -1783,7 +1828,71 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   if (!rc) rc = batch_ensure_ctl(B, 64);
   if (!rc && B->precision != BMG_FP64 && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
   if (!rc && B->use_graph) rc = autotune_batch(B);
-  if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "bmg_setup_batched");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "batched setup");
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* o, bmg_batch** out) {
+  if (!out) return set_error(BMG_EINVAL, "bmg_setup_batched: out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !A || !n) return set_error(BMG_EINVAL, "bmg_setup_batched: bad argument");
+  if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_setup_batched: stationary cycles only");
+  for (int p = 1; p < nprob; ++p)
+    if (A[p].kind != A[0].kind) return set_error(BMG_EINVAL, "bmg_setup_batched: problems differ in kind");
+  bmg_batch* B = new bmg_batch();
+  B->nprob = nprob;
+  bmg_opts so{};
+  CounterScope cs(&B->launches);
+  int rc = batch_init(B, o, &so);
+  for (int p = 0; p < nprob && !rc; ++p) {
+    bmg_hierarchy* h = nullptr;
+    rc = bmg_setup(&A[p], n[p], n[p], &so, &h);
+    if (!rc) {
+      B->hs.push_back(h);
+      B->launches += h->launches;
+      B->maxn = std::max(B->maxn, n[p]);
+      B->bmax = std::max(B->bmax, h->nlev - 1);
+    }
+  }
+  rc = batch_finish(B, rc);
+  if (rc) {
+    bmg_free_batched(B);
+    return rc;
+  }
+  *out = B;
+  return BMG_OK;
+}
+
+int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch** out) {
+  if (!out) return set_error(BMG_EINVAL, "bmg_batch_rhs: out is NULL");
+  *out = nullptr;
+  if (!h0 || k < 1) return set_error(BMG_EINVAL, "bmg_batch_rhs: bad argument");
+  if (h0->shared_ops) return set_error(BMG_EINVAL, "bmg_batch_rhs: h is itself a batch member");
+  if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_batch_rhs: stationary cycles only");
+  if (o && o->precision != h0->precision)
+    return set_error(BMG_EINVAL, "bmg_batch_rhs: precision %d differs from the hierarchy's %d", o->precision,
+                     h0->precision);
+  bmg_batch* B = new bmg_batch();
+  B->nprob = k;
+  bmg_opts so{};
+  CounterScope cs(&B->launches);
+  int rc = batch_init(B, o, &so);
+  B->precision = h0->precision;
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h0->ws), "bmg_batch_rhs");   // h0's setup has finished
+  for (int p = 0; p < k && !rc; ++p) {
+    bmg_hierarchy* h = nullptr;
+    rc = clone_state(h0, B->ws, &h);
+    if (!rc) {
+      B->hs.push_back(h);
+      B->maxn = h0->n;
+      B->bmax = h0->nlev - 1;
+    }
+  }
+  rc = batch_finish(B, rc);
   if (rc) {
     bmg_free_batched(B);
     return rc;

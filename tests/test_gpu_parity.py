@@ -634,3 +634,45 @@ def test_config4_full_batch_converges_to_oracle_residuals():
         p64 = bx.drop_ghost_couplings(np.array(planes))
         assert bx.norm(bx.residual(p64, host(x), f)) <= 1e-8 * bx.norm(bx.at(f, 0, 0))
     B.close()
+
+
+# ---- many right-hand sides of one operator -------------------------------------------------
+
+@pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_of_right_hand_sides_equals_solo_solves(bmg, precision, nbf, graph):
+    """k right-hand sides share one hierarchy's operator: every member's iterate
+    and history equal the hierarchy's own solve of that right-hand side, which
+    equals the oracle's; the hierarchy is unchanged by the batch."""
+    n, k = 255, 5
+    kind, planes, f = problem("lognormal", n)
+    h = bmg.Hierarchy(kind, dev(planes), precision=precision)
+    rhs = [dev(w.rhs_uniform(n, 300 + q)) for q in range(k)]
+    B = bmg.Batch.from_hierarchy(h, k, use_graph=graph)
+    xs, its, rrs, ok = B.solve(rhs, tol=1e-10, maxit=300)
+    assert ok
+    for q, r in enumerate(rhs):
+        x, it, rr, okk = h.solve(r, tol=1e-10, maxit=300)
+        assert okk and it == its[q] and torch.equal(x, xs[q]) and h.history() == B.history(q)
+    levels = bx.setup(kind, planes)
+    fq = w.rhs_uniform(n, 302)
+    if precision == "fp64":
+        xw, hw = bx.solve(levels, fq, tol=1e-10, maxit=300)
+    else:
+        xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), fq, tol=1e-10, maxit=300)
+    assert np.array_equal(bx.at(host(xs[2]), 0, 0), bx.at(xw, 0, 0))
+    check_history(B.history(2), hw)
+    B.close()
+    h.close()
+
+
+def test_batch_of_right_hand_sides_rejects_bad_arguments(bmg):
+    kind, planes, f = problem("binary", 63)
+    h = bmg.Hierarchy(kind, dev(planes), precision="fp32")
+    with pytest.raises(bmg.BmgError):
+        bmg.Batch.from_hierarchy(h, 0)
+    o = bmg._lib.Opts(bmg._lib._PREC["fp64"], 0, 0, 2, 1, 1, 0, 1, 0, None, None, 0)
+    b = __import__("ctypes").c_void_p()
+    rc = bmg.lib.bmg_batch_rhs(h._h, 3, __import__("ctypes").byref(o), __import__("ctypes").byref(b))
+    assert rc == bmg._lib.BMG_EINVAL and "precision" in bmg.lib.bmg_last_error().decode()
+    h.close()
