@@ -164,6 +164,75 @@ def run_batched(args, rank, local_rank, world):
     ranks.close()
 
 
+RHS_BATCH = dict(text="64 right-hand sides U[-1,1) (seeds 500..563) of one 1023x1023 9-point Q1 problem, k = exp(g), "
+                      "g Gaussian field std 2, correlation 32 cells (seed 4); bmg_batch_rhs vs 64 solo solves, V(2,1)",
+                 n=1023, k=64)
+
+
+def run_rhs_batch(args, rank, local_rank, world):
+    """Many right-hand sides of one operator: one batch sharing the hierarchy
+    (bmg_batch_rhs) against the same hierarchy solving them one at a time."""
+    import torch
+    import paper_2502_05279_gb300 as bmg
+    torch.cuda.set_device(local_rank)
+    ranks = Ranks("nccl")
+    n, k = RHS_BATCH["n"], RHS_BATCH["k"]
+    kind, planes, _ = w.lognormal_problem(n, 2.0, 32.0, seed_k=4, seed_f=7)
+    coef = torch.from_numpy(planes).cuda()
+    rhs = [torch.from_numpy(w.rhs_uniform(n, 500 + q)).cuda() for q in range(k)]
+    N = n * n * k
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded generators)",
+           "config": {"workload": "rhs64-1023", "description": RHS_BATCH["text"], "unknowns": N,
+                      "parallelism": "replicas" if world > 1 else "single GPU"}, "variants": {}}
+    clock_s = None
+    for prec in ("fp64", "fp32"):
+        h = bmg.Hierarchy(kind, coef, precision=prec)
+        B = bmg.Batch.from_hierarchy(h, k)
+        xs = [torch.zeros_like(r) for r in rhs]
+        B.time_cycles(rhs, xs, max(args.warmup, 3))
+        ranks.barrier()
+        before = B.launch_count
+        if prec == "fp64":
+            with ClockSampler(local_rank) as cs:
+                ms = B.time_cycles(rhs, xs, args.steps)
+            clock_s = cs.summary()
+        else:
+            ms = B.time_cycles(rhs, xs, args.steps)
+        launches = B.launch_count - before
+        x1 = torch.zeros_like(rhs[0])
+        h.time_cycles(rhs[0], x1, max(args.warmup, 3))
+        ms_solo = h.time_cycles(rhs[0], x1, args.steps)       # one right-hand side
+        for x in xs:
+            x.zero_()
+        ranks.barrier()
+        t0 = time.perf_counter()
+        _, its, _, ok = B.solve(rhs, xs, tol=1e-10, maxit=300)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        its_solo = []
+        for r in rhs:
+            _, it, _, _ = h.solve(r, torch.zeros_like(r), tol=1e-10, maxit=300)
+            its_solo.append(it)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        out["variants"][prec] = {
+            "value": whole_job_rate(N * args.steps, ms * 1e-3, ranks), "ms_per_step": ms / args.steps,
+            "solo_value": n * n * args.steps / (ms_solo * 1e-3), "solo_ms_per_step_one_rhs": ms_solo / args.steps,
+            "gpu_launches": launches, "time_to_1e-10_all_ms": round(tb * 1e3, 1),
+            "time_to_1e-10_one_by_one_ms": round(ts * 1e3, 1), "iterations_max": max(its),
+            "same_iterations_as_solo": list(its) == its_solo, "all_converged": ok}
+        B.close()
+        h.close()
+    v = out["variants"].pop("fp64")
+    out.update(value=v["value"], ms_per_step=v["ms_per_step"], gpu_launches=int(v.pop("gpu_launches")), dtype="f64",
+               clocks=clock_s, fp64=v)
+    if rank == 0:
+        print(json.dumps(out))
+    ranks.close()
+
+
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -568,6 +637,14 @@ def run_reference(args, rank, world):
         setup_s, times = oracle_batch_cycles(sample, steps + warm)
         text, unknowns = BATCHED["text"], m
         what = f"the first {len(sample)} problems of the batch ({m} unknowns)"
+    elif args.workload == "rhs64-1023":
+        n = RHS_BATCH["n"]
+        kind, planes, _ = w.lognormal_problem(n, 2.0, 32.0, seed_k=4, seed_f=7)
+        sample = [(kind, planes, w.rhs_uniform(n, 500 + q)) for q in range(2)]
+        steps = min(args.steps, 5)
+        setup_s, times = oracle_batch_cycles(sample, steps + warm)
+        text, unknowns = RHS_BATCH["text"], 2 * n * n
+        what = "2 of the 64 right-hand sides (the operator set up once per right-hand side)"
     else:
         spec = WORKLOADS[args.workload]
         kind, planes, f = spec["make"]()
@@ -595,7 +672,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--workload", default="fe2047-binary1e4", choices=sorted(WORKLOADS) + ["batched256"])
+    ap.add_argument("--workload", default="fe2047-binary1e4",
+                    choices=sorted(WORKLOADS) + ["batched256", "rhs64-1023"])
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--maxit-vcycle", type=int, default=200, help="cap of the stationary-cycle solve")
@@ -611,6 +689,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched256":
         run_batched(args, rank, local_rank, world)
+    elif args.workload == "rhs64-1023":
+        run_rhs_batch(args, rank, local_rank, world)
     else:
         run_ours(args, rank, local_rank, world)
 
