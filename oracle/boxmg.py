@@ -23,6 +23,15 @@ never as code):
 * Every sum over a row of A runs over the neighbours in the order
   NBR = O, W, E, S, N, SW, NE, NW, SE, left to right, one rounding per
   operation (no fused multiply-add).
+* Fused arithmetic mode (setup(..., arith="fused")): the same expressions in
+  the same order, but each product that is added to or subtracted from a
+  running sum is one fused multiply-add, fma(a, b, s) = a b + s rounded once
+  (oracle/fused.py): the row sums of residual, Gauss-Seidel and A p, the
+  weighted terms of restriction and interpolation, the squared-norm and
+  inner-product accumulations and the flexible-CG vector updates.  Products
+  that stand alone (the first term of a sum, s * d) and the coincident
+  restriction term keep their single rounding; setup, line relaxation and the
+  coarsest solve are the same in both modes.
 * Interpolation weights are eight planes of shape (n_c+2, n_c+2), indexed by
   the coarse cell (ic, jc) whose north-east corner is coarse point (ic, jc),
   with the labels of Fig. 2:
@@ -38,6 +47,8 @@ from __future__ import annotations
 import math
 
 import numpy as np
+
+from .fused import fma
 
 NBR = ((0, 0), (-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, 1), (-1, 1), (1, -1))
 LSW, LSE, LNW, LNE, LL, LR, LB, LA = range(8)
@@ -116,23 +127,34 @@ def level_sizes(n: int, coarsest: int = 3) -> list[int]:
 # Operator apply and residual (A5/A6/A9 building blocks)
 # ---------------------------------------------------------------------------
 
-def apply(planes: np.ndarray, x: np.ndarray) -> np.ndarray:
+def madd(s, a, b, fused: bool = False):
+    """s + a b: rounded product then rounded sum, or one fused multiply-add."""
+    return fma(a, b, s) if fused else s + a * b
+
+
+def msub(s, a, b, fused: bool = False):
+    """s - a b: rounded product then rounded difference, or fma(-a, b, s)
+    (negation is exact, so this is s - a b rounded once)."""
+    return fma(-a, b, s) if fused else s - a * b
+
+
+def apply(planes: np.ndarray, x: np.ndarray, fused: bool = False) -> np.ndarray:
     """y = A x over the interior (ghost ring of y zero); the row sum runs in
     NBR order."""
     y = np.zeros_like(x)
     acc = coupling(planes, 0, 0) * at(x, 0, 0)
     for d in NBR[1:]:
-        acc = acc + coupling(planes, *d) * at(x, *d)
+        acc = madd(acc, coupling(planes, *d), at(x, *d), fused)
     at(y, 0, 0)[...] = acc
     return y
 
 
-def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray) -> np.ndarray:
+def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray, fused: bool = False) -> np.ndarray:
     """r = f - A x, evaluated as f - a_O x_p - a_W x_W - ... (NBR order)."""
     r = np.zeros_like(x)
     acc = at(f, 0, 0).copy()
     for d in NBR:
-        acc = acc - coupling(planes, *d) * at(x, *d)
+        acc = msub(acc, coupling(planes, *d), at(x, *d), fused)
     at(r, 0, 0)[...] = acc
     return r
 
@@ -141,7 +163,7 @@ REDUCE_BLOCKS = 1024
 REDUCE_THREADS = 256
 
 
-def ordered_sum(v: np.ndarray) -> float:
+def ordered_sum(v: np.ndarray, w: np.ndarray | None = None) -> float:
     """Sum of an (n, n) array of interior values in one fixed order, FP64, one
     rounding per addition:
       1. for b < G = min(n, 1024) and t < 256, a running sum over the rows
@@ -150,8 +172,12 @@ def ordered_sum(v: np.ndarray) -> float:
       3. over the G block sums: running sums over b = t, t+256, ... per t < 256,
          then the same halving tree.
     Any order gives the sum to within n^2 rounding errors; this one is stated so
-    that every implementation of it gets the same bits."""
+    that every implementation of it gets the same bits.  With w given, the sum
+    is of the products v w, each fused into the running sum of step 1
+    (acc = fma(v, w, acc)); steps 2 and 3 are unchanged."""
     v = np.asarray(v, dtype=np.float64)
+    if w is not None:
+        w = np.asarray(w, dtype=np.float64)
     n_rows, n_cols = v.shape
     G = min(n_rows, REDUCE_BLOCKS)
     T = REDUCE_THREADS
@@ -160,7 +186,11 @@ def ordered_sum(v: np.ndarray) -> float:
         rows = v[k * G:(k + 1) * G]                       # row k*G + b for block b
         for m in range(0, (n_cols + T - 1) // T):
             blk = rows[:, m * T:(m + 1) * T]
-            acc[:blk.shape[0], :blk.shape[1]] = acc[:blk.shape[0], :blk.shape[1]] + blk
+            a = acc[:blk.shape[0], :blk.shape[1]]
+            if w is None:
+                a[...] = a + blk
+            else:
+                a[...] = fma(blk, w[k * G:(k + 1) * G, m * T:(m + 1) * T], a)
     acc = _halving_tree(acc)
     parts = np.zeros(((G + T - 1) // T) * T)
     parts[:G] = acc
@@ -179,43 +209,46 @@ def _halving_tree(a: np.ndarray) -> np.ndarray:
     return a[:, 0]
 
 
-def norm(r: np.ndarray) -> float:
-    """Euclidean norm over the interior: sqrt of the ordered sum of squares."""
+def norm(r: np.ndarray, fused: bool = False) -> float:
+    """Euclidean norm over the interior: sqrt of the ordered sum of squares
+    (squares rounded, or fused into the running sums)."""
     v = at(r, 0, 0).astype(np.float64)
-    return math.sqrt(ordered_sum(v * v))
+    return math.sqrt(ordered_sum(v, v) if fused else ordered_sum(v * v))
 
 
-def dot(a: np.ndarray, b: np.ndarray) -> float:
+def dot(a: np.ndarray, b: np.ndarray, fused: bool = False) -> float:
     """Interior inner product in the same order as norm()."""
-    return ordered_sum(at(a, 0, 0).astype(np.float64) * at(b, 0, 0).astype(np.float64))
+    a = at(a, 0, 0).astype(np.float64)
+    b = at(b, 0, 0).astype(np.float64)
+    return ordered_sum(a, b) if fused else ordered_sum(a * b)
 
 
 # ---------------------------------------------------------------------------
 # Gauss-Seidel (A5; Fig. 1 "Gauss Seidel", the highlighted smoother)
 # ---------------------------------------------------------------------------
 
-def gs_colour(planes, dinv, x, f, pi, pj) -> None:
+def gs_colour(planes, dinv, x, f, pi, pj, fused: bool = False) -> None:
     """Update every point of one colour: x_p = (f_p - sum_{q != p} a_pq x_q) * d_p
     with d_p = 1 / a_pp.  Points of one colour share no coupling, so they are
     updated together from the same neighbour values."""
     c = colour(pi, pj)
     s = at(f, 0, 0)[c].copy()
     for d in NBR[1:]:
-        s = s - coupling(planes, *d)[c] * at(x, *d)[c]
+        s = msub(s, coupling(planes, *d)[c], at(x, *d)[c], fused)
     at(x, 0, 0)[c] = s * at(dinv, 0, 0)[c]
 
 
-def gs_sweep(kind: int, planes, dinv, x, f) -> None:
+def gs_sweep(kind: int, planes, dinv, x, f, fused: bool = False) -> None:
     """One Gauss-Seidel sweep: red-black for a 5-point stencil, four colours
     (i, j parities (odd,odd), (even,odd), (odd,even), (even,even)) for a
     9-point stencil."""
     if kind == 5:
         for group in COLOURS5:
             for pi, pj in group:
-                gs_colour(planes, dinv, x, f, pi, pj)
+                gs_colour(planes, dinv, x, f, pi, pj, fused)
     else:
         for pi, pj in COLOURS9:
-            gs_colour(planes, dinv, x, f, pi, pj)
+            gs_colour(planes, dinv, x, f, pi, pj, fused)
 
 
 # Line relaxation (Fig. 1 "Line" relaxation; the smoother BoxMG offers for
@@ -260,7 +293,7 @@ def relax(lev, x, f) -> None:
     if getattr(lev, "smoother", "point") == "line":
         line_sweep(lev.kind, lev.planes, x, f)
     else:
-        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f)
+        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f, getattr(lev, "fused", False))
 
 
 # ---------------------------------------------------------------------------
@@ -350,7 +383,7 @@ def basis(ci: np.ndarray) -> np.ndarray:
 # Restriction (A6; Fig. 2) and interpolation + correction (A8)
 # ---------------------------------------------------------------------------
 
-def restrict(ci: np.ndarray, r: np.ndarray) -> np.ndarray:
+def restrict(ci: np.ndarray, r: np.ndarray, fused: bool = False) -> np.ndarray:
     """f_c = P^T r, term by term in the order of the Fig. 2 loop:
     QC = LNE Q(i-1,j-1) + LA Q(i,j-1) + LNW' Q(i+1,j-1) + LR Q(i-1,j) + Q(i,j)
          + LL' Q(i+1,j) + LSE' Q(i-1,j+1) + LB' Q(i,j+1) + LSW' Q(i+1,j+1)
@@ -365,19 +398,19 @@ def restrict(ci: np.ndarray, r: np.ndarray) -> np.ndarray:
         return ci[k, 1 + djc:nc + 1 + djc, 1 + dic:nc + 1 + dic]
 
     t = w(LNE, 0, 0) * q(-1, -1)
-    t = t + w(LA, 0, 0) * q(0, -1)
-    t = t + w(LNW, 1, 0) * q(1, -1)
-    t = t + w(LR, 0, 0) * q(-1, 0)
+    t = madd(t, w(LA, 0, 0), q(0, -1), fused)
+    t = madd(t, w(LNW, 1, 0), q(1, -1), fused)
+    t = madd(t, w(LR, 0, 0), q(-1, 0), fused)
     t = t + q(0, 0)
-    t = t + w(LL, 1, 0) * q(1, 0)
-    t = t + w(LSE, 0, 1) * q(-1, 1)
-    t = t + w(LB, 0, 1) * q(0, 1)
-    t = t + w(LSW, 1, 1) * q(1, 1)
+    t = madd(t, w(LL, 1, 0), q(1, 0), fused)
+    t = madd(t, w(LSE, 0, 1), q(-1, 1), fused)
+    t = madd(t, w(LB, 0, 1), q(0, 1), fused)
+    t = madd(t, w(LSW, 1, 1), q(1, 1), fused)
     fc[1:nc + 1, 1:nc + 1] = t
     return fc
 
 
-def interp_correct(ci: np.ndarray, ec: np.ndarray, x: np.ndarray) -> None:
+def interp_correct(ci: np.ndarray, ec: np.ndarray, x: np.ndarray, fused: bool = False) -> None:
     """x += P e_c (in place).  The interpolated value is formed first, then
     added: coincident x + e; x-edge x + (LL e_W + LR e_E); y-edge
     x + (LB e_S + LA e_N); centre x + (((LSW e_SW + LSE e_SE) + LNW e_NW) + LNE e_NE)."""
@@ -389,15 +422,15 @@ def interp_correct(ci: np.ndarray, ec: np.ndarray, x: np.ndarray) -> None:
     odd = slice(1, 2 * nc + 2, 2)
     x[even, even] = x[even, even] + ec[A, A]
     t = ci[LL, A, B] * ec[A, Bm]
-    t = t + ci[LR, A, B] * ec[A, B]
+    t = madd(t, ci[LR, A, B], ec[A, B], fused)
     x[even, odd] = x[even, odd] + t
     t = ci[LB, B, A] * ec[Bm, A]
-    t = t + ci[LA, B, A] * ec[B, A]
+    t = madd(t, ci[LA, B, A], ec[B, A], fused)
     x[odd, even] = x[odd, even] + t
     t = ci[LSW, B, B] * ec[Bm, Bm]
-    t = t + ci[LSE, B, B] * ec[Bm, B]
-    t = t + ci[LNW, B, B] * ec[B, Bm]
-    t = t + ci[LNE, B, B] * ec[B, B]
+    t = madd(t, ci[LSE, B, B], ec[Bm, B], fused)
+    t = madd(t, ci[LNW, B, B], ec[B, Bm], fused)
+    t = madd(t, ci[LNE, B, B], ec[B, B], fused)
     x[odd, odd] = x[odd, odd] + t
 
 
@@ -513,14 +546,21 @@ class Level:
         at(self.dinv, 0, 0)[...] = planes.dtype.type(1) / at(planes[0], 0, 0)
         self.ci = None
         self.L = None
+        self.smoother = "point"
+        self.fused = False
 
 
-def setup(kind: int, planes: np.ndarray, coarsest: int = 3, smoother: str = "point") -> list[Level]:
+def setup(kind: int, planes: np.ndarray, coarsest: int = 3, smoother: str = "point",
+          arith: str = "rounded") -> list[Level]:
     """Build the hierarchy: Dendy P and Galerkin A_c level by level, then the
     Cholesky factor of the coarsest operator.  smoother: "point" (Gauss-Seidel
-    by colours) or "line" (zebra x-line Gauss-Seidel) on every level."""
+    by colours) or "line" (zebra x-line Gauss-Seidel) on every level.  arith:
+    "rounded" (one rounding per operation) or "fused" (the cycle's
+    multiply-adds fused, see the module notes); the setup itself is the same."""
     if smoother not in ("point", "line"):
         raise ValueError("smoother must be 'point' or 'line'")
+    if arith not in ("rounded", "fused"):
+        raise ValueError("arith must be 'rounded' or 'fused'")
     planes = np.array(planes, dtype=np.float64)
     n = size_of(planes)
     sizes = level_sizes(n, coarsest)
@@ -533,6 +573,7 @@ def setup(kind: int, planes: np.ndarray, coarsest: int = 3, smoother: str = "poi
     for li, nl in enumerate(sizes):
         lev = Level(nl, kind, planes)
         lev.smoother = smoother
+        lev.fused = arith == "fused"
         if li == len(sizes) - 1:
             lev.L = cholesky(dense_matrix(planes))
         else:
@@ -559,13 +600,14 @@ def vcycle(levels, l, x, f, nu1=2, nu2=1) -> None:
     if lev.L is not None:
         coarse_solve(lev, x, f)
         return
+    fu = lev.fused
     for _ in range(nu1):
         relax(lev, x, f)
-    r = residual(lev.planes, x, f)
-    fc = restrict(lev.ci, r)
+    r = residual(lev.planes, x, f, fu)
+    fc = restrict(lev.ci, r, fu)
     xc = np.zeros_like(fc)
     vcycle(levels, l + 1, xc, fc, nu1, nu2)
-    interp_correct(lev.ci, xc, x)
+    interp_correct(lev.ci, xc, x, fu)
     for _ in range(nu2):
         relax(lev, x, f)
 
@@ -574,14 +616,15 @@ def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
     """V(nu1, nu2) iterations until ||r_k|| / ||r_0|| <= tol or maxit cycles.
     Returns (x, history) with history = [||r_0||, ||r_1||, ...]."""
     lev = levels[0]
+    fu = lev.fused
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
-    hist = [norm(residual(lev.planes, x, f))]
+    hist = [norm(residual(lev.planes, x, f, fu), fu)]
     if hist[0] == 0.0:
         return x, hist
     it = 0
     while it < maxit and hist[-1] / hist[0] > tol:
         vcycle(levels, 0, x, f, nu1, nu2)
-        hist.append(norm(residual(lev.planes, x, f)))
+        hist.append(norm(residual(lev.planes, x, f, fu), fu))
         it += 1
     return x, hist
 
@@ -592,7 +635,8 @@ def solve_fcg(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
       z = V(r); p = z if first else z + beta p with beta = -(z.q)/(p.q) of the
       previous step; q = A p; alpha = (p.r)/(p.q); x += alpha p; r -= alpha q.
     The test uses the recursively updated residual.  Returns (x, history)."""
-    return _fcg(levels[0].planes, lambda r: _precondition64(levels, r, nu1, nu2), f, x0, tol, maxit)
+    return _fcg(levels[0].planes, lambda r: _precondition64(levels, r, nu1, nu2), f, x0, tol, maxit,
+                levels[0].fused)
 
 
 def _precondition64(levels, r, nu1, nu2):
@@ -601,10 +645,11 @@ def _precondition64(levels, r, nu1, nu2):
     return z
 
 
-def _fcg(planes, precond, f, x0, tol, maxit):
+def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False):
+    fu = fused
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
-    r = residual(planes, x, f)
-    hist = [norm(r)]
+    r = residual(planes, x, f, fu)
+    hist = [norm(r, fu)]
     if hist[0] == 0.0:
         return x, hist
     p = q = None
@@ -615,13 +660,13 @@ def _fcg(planes, precond, f, x0, tol, maxit):
         if p is None:
             p = z
         else:
-            beta = -(dot(z, q) / pq)
-            p = z + beta * p
-        q = apply(planes, p)
-        pq = dot(p, q)
-        alpha = dot(p, r) / pq
-        x = x + alpha * p
-        r = r - alpha * q
-        hist.append(norm(r))
+            beta = -(dot(z, q, fu) / pq)
+            p = madd(z, beta, p, fu)
+        q = apply(planes, p, fu)
+        pq = dot(p, q, fu)
+        alpha = dot(p, r, fu) / pq
+        x = madd(x, alpha, p, fu)
+        r = msub(r, alpha, q, fu)
+        hist.append(norm(r, fu))
         it += 1
     return x, hist

@@ -16,7 +16,10 @@ reading:
   even on the float32 bit pattern), and recompute the diagonal in FP32 so that
   row sums stay what they were: O32 = fl32(sum_NBR a) - W_b - E_b - S_b - N_b
   - SW_b - NE_b - NW_b - SE_b, d32 = 1 / O32;
-* the coarsest solve stays FP64: fl32(L^-T L^-1 fl64(f32)).
+* the coarsest solve stays FP64: fl32(L^-T L^-1 fl64(f32));
+* a hierarchy set up with arith="fused" fuses the multiply-adds of both the
+  FP64 outer loop and the FP32 cycle (fmaf for FP32 operands); x + s e32 is
+  the same either way (s e32 is exact).
 """
 from __future__ import annotations
 
@@ -66,6 +69,7 @@ def lower(levels, bf16_levels: int = 0) -> list[Level32]:
         ci = None if lev.ci is None else lev.ci.astype(F32)
         out.append(Level32(lev.n, lev.kind, planes, dinv, ci, lev.L))
         out[-1].smoother = getattr(lev, "smoother", "point")
+        out[-1].fused = getattr(lev, "fused", False)
     return out
 
 
@@ -88,9 +92,10 @@ def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2
     """FP64 iterative refinement around FP32 V-cycles.  Returns (x, history),
     history[k] = ||f - A x_k|| in FP64."""
     p64 = levels[0].planes
+    fu = levels[0].fused
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
-    r = bx.residual(p64, x, f)
-    hist = [bx.norm(r)]
+    r = bx.residual(p64, x, f, fu)
+    hist = [bx.norm(r, fu)]
     if hist[0] == 0.0:
         return x, hist
     it = 0
@@ -99,8 +104,8 @@ def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2
         r32 = (r * (1.0 / s)).astype(F32)
         e32 = inner_cycle(levels32, r32, cycles, nu1, nu2)
         x = x + s * e32.astype(np.float64)
-        r = bx.residual(p64, x, f)
-        hist.append(bx.norm(r))
+        r = bx.residual(p64, x, f, fu)
+        hist.append(bx.norm(r, fu))
         it += 1
     return x, hist
 
@@ -113,4 +118,4 @@ def solve_fcg_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, n
         s = scale_of(bx.norm(r))
         r32 = (r * (1.0 / s)).astype(F32)
         return s * inner_cycle(levels32, r32, cycles, nu1, nu2).astype(np.float64)
-    return bx._fcg(levels[0].planes, precond, f, x0, tol, maxit)
+    return bx._fcg(levels[0].planes, precond, f, x0, tol, maxit, levels[0].fused)
