@@ -94,7 +94,7 @@ def run_batched(args, rank, local_rank, world):
     for prec in ("fp64", "fp32", "bf16"):
         ranks.barrier()
         t0 = time.perf_counter()
-        B = bmg.Batch(9, coefs, precision=prec)
+        B = bmg.Batch(9, coefs, precision=prec, arith=args.arith)
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         xs = [torch.zeros_like(r) for r in rhs]
@@ -187,7 +187,7 @@ def run_rhs_batch(args, rank, local_rank, world):
                       "parallelism": "replicas" if world > 1 else "single GPU"}, "variants": {}}
     clock_s = None
     for prec in ("fp64", "fp32"):
-        h = bmg.Hierarchy(kind, coef, precision=prec)
+        h = bmg.Hierarchy(kind, coef, precision=prec, arith=args.arith)
         B = bmg.Batch.from_hierarchy(h, k)
         xs = [torch.zeros_like(r) for r in rhs]
         B.time_cycles(rhs, xs, max(args.warmup, 3))
@@ -350,7 +350,9 @@ class ClockSampler:
 # the CUDA path
 # ----------------------------------------------------------------------------------
 
-ALG_FLOPS_PER_POINT = {5: 9, 9: 17}        # one GS update: (k-1) mul + (k-1) sub + 1 mul
+# FP64 instructions of one Gauss-Seidel update: rounded, (k-1) mul + (k-1) sub + 1 mul;
+# fused, (k-1) fma + 1 mul
+ALG_FP64_INSTR_PER_POINT = {(5, "rounded"): 9, (9, "rounded"): 17, (5, "fused"): 5, (9, "fused"): 9}
 SWEEP_BYTES = {("fp64", 9): 64, ("fp64", 5): 48, ("fp32", 9): 32, ("fp32", 5): 24, ("bf16", 9): 24, ("bf16", 5): 20}
 
 
@@ -370,13 +372,15 @@ def run_ours(args, rank, local_rank, world):
 
     if args.only:
         # one hierarchy, warm-up and timed cycles only: the small run profiled by ncu
-        h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov, smoother=args.smoother)
+        h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov, smoother=args.smoother,
+                          arith=args.arith)
         x = torch.zeros_like(rhs)
         h.time_cycles(rhs, x, args.warmup)
         ms = h.time_cycles(rhs, x, args.steps)
         if rank == 0:
-            print(json.dumps({"only": args.only, "krylov": args.krylov, "workload": args.workload,
-                              "ms_per_step": ms / args.steps, "launches": h.launch_count}))
+            print(json.dumps({"only": args.only, "krylov": args.krylov, "arith": args.arith,
+                              "workload": args.workload, "ms_per_step": ms / args.steps,
+                              "launches": h.launch_count}))
         h.close()
         return
 
@@ -387,7 +391,7 @@ def run_ours(args, rank, local_rank, world):
     for prec in ("fp64", "fp32", "bf16"):
         barrier()
         t0 = time.perf_counter()
-        h = bmg.Hierarchy(kind, coef, precision=prec)
+        h = bmg.Hierarchy(kind, coef, precision=prec, arith=args.arith)
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         x = torch.zeros_like(rhs)
@@ -407,11 +411,11 @@ def run_ours(args, rank, local_rank, world):
         # time to tolerance from a zero guess (host-timed: includes the host polls),
         # stationary cycles and flexible CG with the same cycle as preconditioner
         tts = {}
-        hk = bmg.Hierarchy(kind, coef, precision=prec, krylov="fcg")
+        hk = bmg.Hierarchy(kind, coef, precision=prec, krylov="fcg", arith=args.arith)
         modes = [("vcycle", h, args.maxit_vcycle), ("fcg", hk, 500)]
         hk2 = None
         if prec != "fp64":   # two FP32 cycles per FP64 outer step amortise the FP64-bound outer work
-            hk2 = bmg.Hierarchy(kind, coef, precision=prec, krylov="fcg", inner_cycles=2)
+            hk2 = bmg.Hierarchy(kind, coef, precision=prec, krylov="fcg", inner_cycles=2, arith=args.arith)
             modes.append(("fcg_2cycles", hk2, 500))
         for mode, hh, cap in modes:
             x.zero_()
@@ -426,6 +430,16 @@ def run_ours(args, rank, local_rank, world):
         variants[prec] = dict(ms=ms, setup_ms=setup_ms, tts=tts, prof=prof, h=h, hk=hk,
                               tuned=[h.tuned_cluster(l) for l in range(h.num_levels)],
                               pairs=[h.tuned_pair(l) for l in range(h.num_levels)])
+
+    # the FP64 cycle in the other arithmetic mode, for comparison (cycle time and profile only)
+    other = "rounded" if args.arith == "fused" else "fused"
+    ho = bmg.Hierarchy(kind, coef, precision="fp64", arith=other)
+    xo = torch.zeros_like(rhs)
+    ho.time_cycles(rhs, xo, max(args.warmup, 3))
+    barrier()
+    ms_other = max_over_ranks(ho.time_cycles(rhs, xo, args.steps))
+    prof_other = ho.profile(rhs, torch.zeros_like(rhs), 3)
+    ho.close()
 
     # end to end through the public API with host buffers (FP64 path, flexible CG to 1e-10)
     h = variants["fp64"]["hk"]
@@ -456,24 +470,25 @@ def run_ours(args, rank, local_rank, world):
 
     sweeps_per_cycle = 3                                        # V(2,1)
 
-    def per_launch(prec, fp32):
+    def per_launch(prec, fp32, prof=None):
         """Dominant kernel's average device time per launch and the Gauss-Seidel
         sweeps one launch performs (1/2 for the row kernel, 1 for the tile kernel)."""
-        r = dominant(variants[prec]["prof"], fp32)
+        r = dominant(variants[prec]["prof"] if prof is None else prof, fp32)
         cycles = 3
         return r, r["ms"] / r["launches"] * 1e-3, sweeps_per_cycle * cycles / r["launches"]
 
-    def roofline_fp64():
-        r, per_launch_s, sweeps = per_launch("fp64", False)
-        flops = ALG_FLOPS_PER_POINT[kind] * N * sweeps
-        achieved = flops / per_launch_s / 1e12
+    def roofline_fp64(arith, prof):
+        r, per_launch_s, sweeps = per_launch("fp64", False, prof)
+        instr = ALG_FP64_INSTR_PER_POINT[(kind, arith)] * N * sweeps
+        achieved = instr / per_launch_s / 1e12
         peak = fp64_rate / 1e12
-        share = r["ms"] / sum(q["ms"] for q in variants["fp64"]["prof"])
+        share = r["ms"] / sum(q["ms"] for q in prof)
         byt = SWEEP_BYTES[("fp64", kind)] * N * sweeps
-        name = "k_gs_rows<double>"
+        name = "k_gs_rows<double>" + (" fused" if arith == "fused" else "")
         return {"bound": "alu", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
-                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "T FP64 instr/s",
                 "frac": round(achieved / peak, 4),
+                "instr_per_point": ALG_FP64_INSTR_PER_POINT[(kind, arith)],
                 "peak_source": "FP64 instruction rate measured in this run (bmg_measure_fp64_rate)",
                 "traffic": NCU_TRAFFIC.get((args.workload, name)),
                 "alg_bytes_per_launch": byt, "hbm_gbs_equiv": round(byt / per_launch_s / 1e9, 1),
@@ -515,10 +530,10 @@ def run_ours(args, rank, local_rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": v64["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generators, no datasets)",
-        "config": {"workload": args.workload, "description": spec["text"], "unknowns": N,
+        "config": {"workload": args.workload, "description": spec["text"], "unknowns": N, "arith": args.arith,
                    "levels": v64["h"].num_levels, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set > L2 (FP64 level-0 stencil + vectors = %.0f MB)" % (N * 64 / 1e6)},
-        "roofline": roofline_fp64(),
+        "roofline": roofline_fp64(args.arith, v64["prof"]),
         "e2e": {"value": world * N * e2e_cycles / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(f.nbytes),
                 "note": "bmg_solve (FP64, flexible CG, one V(2,1) per iteration) to 1e-10 from a zero guess per "
@@ -526,10 +541,13 @@ def run_ours(args, rank, local_rank, world):
         "gpu_launches": int(timed_launches),
         "clocks": clock_s,
         "time_to_tol": {p: dict(setup_ms=round(v["setup_ms"], 1), **v["tts"]) for p, v in variants.items()},
-        "variants": {p: {"value": world * N * args.steps / (v["ms"] * 1e-3), "ms_per_step": v["ms"] / args.steps,
-                         "roofline": roofline_32(p), "tuned_cluster_by_level": v["tuned"],
-                         "two_sweep_pass_by_level": v["pairs"]}
-                     for p, v in variants.items() if p != "fp64"},
+        "variants": {**{p: {"value": world * N * args.steps / (v["ms"] * 1e-3), "ms_per_step": v["ms"] / args.steps,
+                            "roofline": roofline_32(p), "tuned_cluster_by_level": v["tuned"],
+                            "two_sweep_pass_by_level": v["pairs"]}
+                        for p, v in variants.items() if p != "fp64"},
+                     "fp64_" + other: {"value": world * N * args.steps / (ms_other * 1e-3),
+                                       "ms_per_step": ms_other / args.steps,
+                                       "roofline": roofline_fp64(other, prof_other)}},
         "tuned_cluster_by_level": variants["fp64"]["tuned"],
     }
     # per-level, per-kernel device time of one cycle (the paper's Fig. 10 breakdown)
@@ -681,6 +699,8 @@ def main():
                     help="time one hierarchy's cycles only (short run for profilers)")
     ap.add_argument("--krylov", choices=("none", "fcg"), default="none", help="solve mode for --only")
     ap.add_argument("--smoother", default="auto", help="FP32 Gauss-Seidel kernel for --only (auto, rows, tile0..4)")
+    ap.add_argument("--arith", choices=("rounded", "fused"), default="fused",
+                    help="cycle arithmetic: fused multiply-adds (default) or one rounding per operation")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -99,7 +99,18 @@ typedef struct {
                            (one-pass kernel with shape s = 0 .. 5 on every level outside the
                            level-fused tail and the coarsest), or BMG_SMOOTHER_PAIR + s
                            (the same levels, pairs of sweeps as one two-sweep pass) */
+  int arith;            /* BMG_ARITH_ROUNDED (0, default): one rounding per operation, the oracle's
+                           default arithmetic; BMG_ARITH_FUSED: every product that is added to or
+                           subtracted from a running sum in the cycle (stencil row sums of the
+                           residual, Gauss-Seidel and A p; the weighted restriction and
+                           interpolation terms; squared-norm and inner-product accumulation; the
+                           flexible-CG updates) is one fused multiply-add, in FP64 and FP32 alike.
+                           Same expressions, same order, fewer roundings; setup, line relaxation
+                           and the coarsest solve are unchanged */
 } bmg_opts;
+
+#define BMG_ARITH_ROUNDED 0
+#define BMG_ARITH_FUSED 1
 
 #define BMG_SMOOTHER_AUTO 0
 #define BMG_SMOOTHER_ROWS 1

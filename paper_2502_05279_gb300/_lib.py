@@ -48,13 +48,16 @@ _KRYLOV = {"none": 0, "fcg": 1}
 _SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
              "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12}
 TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
+# cycle arithmetic: one rounding per operation, or fused multiply-adds
+_ARITH = {"rounded": 0, "fused": 1}
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("interp", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int),
+                ("arith", ctypes.c_int)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -139,13 +142,14 @@ class Hierarchy:
 
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
-                 use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto"):
+                 use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto",
+                 arith: str = "rounded"):
         n = _n_of(coef)
-        self.n, self.kind, self.precision = n, kind, precision
+        self.n, self.kind, self.precision, self.arith = n, kind, precision, arith
         st = Stencil(kind, _ptr(coef, name="coef"))
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
                  int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
-                 _SMOOTHER[smoother])
+                 _SMOOTHER[smoother], _ARITH[arith])
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -237,7 +241,8 @@ class Batch:
     launch per cycle stage over all problems, one CUDA graph per iteration."""
 
     def __init__(self, kind: int, coefs, precision: str = "fp64", nu1: int = 2, nu2: int = 1,
-                 inner_cycles: int = 1, bf16_levels: int = 2, use_graph: bool = True, smoother: str = "auto"):
+                 inner_cycles: int = 1, bf16_levels: int = 2, use_graph: bool = True, smoother: str = "auto",
+                 arith: str = "rounded"):
         self.kind, self.precision = kind, precision
         self.ns = [_n_of(c) for c in coefs]
         self._coefs = list(coefs)
@@ -245,7 +250,7 @@ class Batch:
         sts = (Stencil * nprob)(*[Stencil(kind, _ptr(c, name="coef")) for c in coefs])
         ns = (ctypes.c_int * nprob)(*self.ns)
         o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, None, _stream(),
-                 _SMOOTHER[smoother])
+                 _SMOOTHER[smoother], _ARITH[arith])
         h = ctypes.c_void_p()
         _check(lib.bmg_setup_batched(nprob, sts, ns, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -260,7 +265,7 @@ class Batch:
         self.ns = [h.n] * k
         self._coefs = [h]   # keeps the hierarchy alive
         o = Opts(_PREC[h.precision], 0, 0, nu1, nu2, inner_cycles, 0, int(use_graph), 0, None, _stream(),
-                 _SMOOTHER[smoother])
+                 _SMOOTHER[smoother], _ARITH[h.arith])
         b = ctypes.c_void_p()
         _check(lib.bmg_batch_rhs(h._h, k, ctypes.byref(o), ctypes.byref(b)))
         self._h = b

@@ -82,19 +82,21 @@ struct Level {
   double* lcp = nullptr;  // line relaxation: elimination multipliers (FP64 cycle)
   float* lcp32 = nullptr; // the same for the FP32 cycle
   float* x32b = nullptr;  // second iterate of a tile-swept level (sweeps alternate x32 <-> x32b)
+  int fused = 0;          // 1: the cycle's multiply-adds on this level are fused (BMG_ARITH_FUSED)
 };
 
 StencilView<double, double> view64(const Level& L) {
   size_t ps = plane_size(L.n);
-  return {L.st, L.st + ps, L.st + 2 * ps, L.st + 3 * ps, L.st + 4 * ps, L.st + 5 * ps, L.n, L.n + 2};
+  return {L.st, L.st + ps, L.st + 2 * ps, L.st + 3 * ps, L.st + 4 * ps, L.st + 5 * ps, L.n, L.n + 2, L.fused};
 }
 StencilView<float, float> view32(const Level& L) {
   size_t ps = plane_stride32(L.n);
-  return {L.st32, L.st32 + ps, L.st32 + 2 * ps, L.st32 + 3 * ps, L.st32 + 4 * ps, L.st32 + 5 * ps, L.n, L.n + 2};
+  return {L.st32, L.st32 + ps, L.st32 + 2 * ps, L.st32 + 3 * ps, L.st32 + 4 * ps, L.st32 + 5 * ps,
+          L.n,    L.n + 2,       L.fused};
 }
 StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
   size_t ps = plane_stride32(L.n);
-  return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2};
+  return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2, L.fused};
 }
 
 }  // namespace
@@ -103,6 +105,7 @@ struct bmg_hierarchy {
   int n = 0, nlev = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, coarsest = 3, krylov = 0;
   int interp = BMG_INTERP_DENDY, interp_used = BMG_INTERP_DENDY;
   int smoother = BMG_SMOOTHER_AUTO;
+  int arith = BMG_ARITH_ROUNDED;
   const void* mlp = nullptr;
   double factor_learned = 0.0, factor_dendy = 0.0;
   double* kr = nullptr;   // flexible CG vectors r, z, p, q (FP64, (n+2)^2 each)
@@ -198,7 +201,8 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   Level& L = h->lv[l];
   cudaStream_t s = h->ws;
   if (l == h->tail_l) {
-    step(h, l, BMG_K_TAIL, 0, [&] { launch_tail<double>((const TailDesc<double>*)h->d_tail, 1, L.kind, done, s); });
+    step(h, l, BMG_K_TAIL, 0,
+         [&] { launch_tail<double>((const TailDesc<double>*)h->d_tail, 1, L.kind, done, s, L.fused); });
     return;
   }
   if (l == h->nlev - 1) {
@@ -216,7 +220,7 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   relax64(h->nu1);
   step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, x, f, C.f, C.x, done, s); });
   vcycle64(h, l + 1, C.x, C.f, done);
-  step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s); });
+  step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s, L.fused); });
   relax64(h->nu2);
 }
 
@@ -272,7 +276,8 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   Level& L = h->lv[l];
   cudaStream_t s = h->ws;
   if (l == h->tail_l) {
-    step(h, l, BMG_K_TAIL, 1, [&] { launch_tail<float>((const TailDesc<float>*)h->d_tail, 1, L.kind, done, s); });
+    step(h, l, BMG_K_TAIL, 1,
+         [&] { launch_tail<float>((const TailDesc<float>*)h->d_tail, 1, L.kind, done, s, L.fused); });
     return;
   }
   if (l == h->nlev - 1) {
@@ -291,7 +296,7 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   }
   vcycle32(h, l + 1, done);
   float* dst = L.tile32 >= 0 && (sweep_launches(L, h->nu2) & 1) ? L.x32b : L.x32;
-  step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_to<float>(L.n, L.ci32, C.x32, cur, dst, done, s); });
+  step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_to<float>(L.n, L.ci32, C.x32, cur, dst, done, s, L.fused); });
   cur = dst;
   if (L.bf16)
     relax32(h, viewbf(L), l, h->nu2, &cur, done);
@@ -323,11 +328,12 @@ int time_call(cudaStream_t s, F&& fn, float* ms) {
 // per row, at least a warp of pairs per CTA) and, for FP32 levels, the
 // one-pass tile kernel for each tile shape; the fastest is kept.  Every
 // candidate computes the same bits; only the speed differs.  Results are
-// cached per (n, compute type, storage type) for the life of the process.
+// cached per (n, compute type, storage type, arithmetic mode) for the life of
+// the process.
 template <typename T, typename S>
 int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* ms_out = nullptr) {
-  static std::map<std::tuple<int, int, int>, std::pair<int, float>> cache;
-  auto key = std::make_tuple(v.n, (int)sizeof(T), (int)sizeof(S));
+  static std::map<std::tuple<int, int, int, int>, std::pair<int, float>> cache;
+  auto key = std::make_tuple(v.n, (int)sizeof(T), (int)sizeof(S), v.fused);
   auto it = cache.find(key);
   if (it != cache.end()) {
     *best_out = it->second.first;
@@ -361,8 +367,8 @@ int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* 
 
 template <typename S>
 int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, float* ms_out) {
-  static std::map<std::pair<int, int>, std::pair<int, float>> cache;
-  auto key = std::make_pair(v.n, (int)sizeof(S));
+  static std::map<std::tuple<int, int, int>, std::pair<int, float>> cache;
+  auto key = std::make_tuple(v.n, (int)sizeof(S), v.fused);
   auto it = cache.find(key);
   if (it != cache.end()) {
     *best_out = it->second.first;
@@ -399,8 +405,8 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
 
 template <typename S>
 int tune_pair(const StencilView<float, S>& v, cudaStream_t s, int* best_out, float* ms_out) {
-  static std::map<std::pair<int, int>, std::pair<int, float>> cache;
-  auto key = std::make_pair(v.n, (int)sizeof(S));
+  static std::map<std::tuple<int, int, int>, std::pair<int, float>> cache;
+  auto key = std::make_tuple(v.n, (int)sizeof(S), v.fused);
   auto it = cache.find(key);
   if (it != cache.end()) {
     *best_out = it->second.first;
@@ -668,6 +674,7 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
     Level& L = h->lv[l];
     L.n = sizes[l];
     L.kind = l == 0 ? A->kind : 9;
+    L.fused = h->arith == BMG_ARITH_FUSED;
     size_t ps = plane_size(L.n);
     if ((rc = dalloc(&L.st, 6 * ps))) return rc;
     if (l + 1 < h->nlev)
@@ -821,6 +828,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     h->mlp = o->mlp;
     h->user = (cudaStream_t)o->stream;
     h->smoother = o->smoother;
+    h->arith = o->arith;
   }
   if (h->smoother < BMG_SMOOTHER_AUTO ||
       (h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES && h->smoother < BMG_SMOOTHER_PAIR) ||
@@ -830,7 +838,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   }
   if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
       h->nu1 < 0 || h->nu2 < 0 || h->interp < 0 || h->interp > 1 || (h->interp == BMG_INTERP_LEARNED && !h->mlp) ||
-      h->krylov < 0 || h->krylov > 1) {
+      h->krylov < 0 || h->krylov > 1 || h->arith < BMG_ARITH_ROUNDED || h->arith > BMG_ARITH_FUSED) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad options");
   }
@@ -1241,7 +1249,7 @@ constexpr int kGroups = 6;
 }
 
 struct bmg_batch {
-  int nprob = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1;
+  int nprob = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, arith = BMG_ARITH_ROUNDED;
   int smoother = BMG_SMOOTHER_AUTO;
   std::vector<bmg_hierarchy*> hs;
   cudaStream_t user = nullptr, ws = nullptr;
@@ -1414,8 +1422,9 @@ template <typename S>
 void group_onepass(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
   const LevelDesc<float, S>* d = gdesc<float, S>(g);
   int k = 0;
-  for (; g.pair >= 0 && k + 2 <= sweeps; k += 2, g.dir ^= 1) launch_gs_pair_b(d, g.count, g.n, g.pair, g.dir, B->ws);
-  for (; k < sweeps; ++k, g.dir ^= 1) launch_gs_tile_b(d, g.count, g.n, g.tile, g.dir, B->ws);
+  for (; g.pair >= 0 && k + 2 <= sweeps; k += 2, g.dir ^= 1)
+    launch_gs_pair_b(d, g.count, g.n, g.pair, g.dir, B->ws, B->arith);
+  for (; k < sweeps; ++k, g.dir ^= 1) launch_gs_tile_b(d, g.count, g.n, g.tile, g.dir, B->ws, B->arith);
 }
 
 int group_launches(const bmg_batch::Group& g, int sweeps) {
@@ -1427,16 +1436,22 @@ void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
   if (!g.count || !sweeps) return;
   if (g.tile >= 0 && g.storage == 1) group_onepass<float>(B, g, sweeps);
   else if (g.tile >= 0 && g.storage == 2) group_onepass<__nv_bfloat16>(B, g, sweeps);
-  else if (g.storage == 0) launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
-  else if (g.storage == 1) launch_gs_b(gdesc<float, float>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
-  else launch_gs_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws);
+  else if (g.storage == 0)
+    launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws, B->arith);
+  else if (g.storage == 1)
+    launch_gs_b(gdesc<float, float>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws, B->arith);
+  else
+    launch_gs_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws, B->arith);
 }
 
 void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
-  if (g.storage == 0) launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws);
-  else if (g.storage == 1) launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws, g.dir);
-  else launch_resid_restrict_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, B->ws, g.dir);
+  if (g.storage == 0)
+    launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws, 0, B->arith);
+  else if (g.storage == 1)
+    launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws, g.dir, B->arith);
+  else
+    launch_resid_restrict_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, g.kind, B->ws, g.dir, B->arith);
 }
 
 // x (or x2) += P e: reads the array g.dir names and writes the one from which
@@ -1444,9 +1459,9 @@ void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
 void group_interp(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
   const int din = g.dir, dout = group_launches(g, B->nu2) & 1;
-  if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws);
-  else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws, din, dout);
-  else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws, din, dout);
+  if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws, 0, 0, B->arith);
+  else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws, din, dout, B->arith);
+  else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws, din, dout, B->arith);
   g.dir = dout;
 }
 
@@ -1468,9 +1483,9 @@ void batch_vcycle(bmg_batch* B) {
     }
     if (B->tail_count[b]) {   // problems whose remaining levels run in one level-fused launch
       if (B->precision == BMG_FP64)
-        launch_tail<double>((const TailDesc<double>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws);
+        launch_tail<double>((const TailDesc<double>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws, B->arith);
       else
-        launch_tail<float>((const TailDesc<float>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws);
+        launch_tail<float>((const TailDesc<float>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws, B->arith);
     }
   }
   for (auto& g : B->stages[0]) group_coarse(B, g);
@@ -1484,20 +1499,20 @@ void batch_vcycle(bmg_batch* B) {
 void batch_iteration(bmg_batch* B) {
   if (B->precision == BMG_FP64) {
     batch_vcycle(B);
-    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
   } else {
     for (int c = 0; c < B->inner; ++c) batch_vcycle(B);
     launch_ir_update_b(B->d_top, B->nprob, B->maxn, B->ws);
-    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
   }
   launch_finalize_b(B->d_top, B->nprob, 1, B->ws);
 }
 
 void batch_initial(bmg_batch* B) {
   if (B->precision == BMG_FP64)
-    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
   else
-    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws);
+    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
   launch_finalize_b(B->d_top, B->nprob, 0, B->ws);
 }
 
@@ -1579,7 +1594,8 @@ int batch_launch_iterations(bmg_batch* B, int k) {
 struct GroupChoice {
   int cl, tile, pair;
 };
-static std::map<std::tuple<int, int, int, int>, GroupChoice> g_tuned;   // (n, storage, count, kind) -> choice
+// (n, storage, count, kind, arith) -> choice
+static std::map<std::tuple<int, int, int, int, int>, GroupChoice> g_tuned;
 
 // Allocates the second iterate of every problem's level in FP32 group g.
 int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
@@ -1597,7 +1613,7 @@ int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
 
 template <typename T, typename S>
 int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
-  auto key = std::make_tuple(g.n, g.storage, g.count, g.kind);
+  auto key = std::make_tuple(g.n, g.storage, g.count, g.kind, B->arith);
   auto it = g_tuned.find(key);
   if (it == g_tuned.end()) {
     const int base = rows_cluster<T>(g.n);
@@ -1621,7 +1637,7 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
     for (int cl = base; cl <= 8 && !rc; cl *= 2) {
       if (cl > base && ((g.n + 1) / 2 + cl - 1) / cl < 32) break;   // fewer than a warp of pairs per CTA
       float ms = 0;
-      rc = time_call(B->ws, [&] { launch_gs_b<T, S>(dd, g.count, g.n, 9, 2, cl, B->ws); }, &ms);
+      rc = time_call(B->ws, [&] { launch_gs_b<T, S>(dd, g.count, g.n, 9, 2, cl, B->ws, B->arith); }, &ms);
       if (ms * 0.5f < best_ms) {
         best_ms = ms * 0.5f;
         best.cl = cl;
@@ -1632,8 +1648,8 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
         for (int shape : {0, 3}) {
           float ms = 0;
           rc = time_call(B->ws, [&] {
-            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 0, B->ws);
-            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 1, B->ws);
+            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 0, B->ws, B->arith);
+            launch_gs_tile_b<S>(dd, g.count, g.n, shape, 1, B->ws, B->arith);
           }, &ms);
           if (rc) break;
           if (ms * 0.5f < tile_ms) {
@@ -1647,8 +1663,8 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
           for (int shape : {0, 3}) {
             float ms = 0;
             rc = time_call(B->ws, [&] {
-              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 0, B->ws);
-              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 1, B->ws);
+              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 0, B->ws, B->arith);
+              launch_gs_pair_b<S>(dd, g.count, g.n, shape, 1, B->ws, B->arith);
             }, &ms);
             if (rc) break;
             if (ms * 0.25f < pair_best) {   // per sweep: two launches of two sweeps
@@ -1738,7 +1754,10 @@ int batch_init(bmg_batch* B, const bmg_opts* o, bmg_opts* so) {
     B->inner = o->inner_cycles > 0 ? o->inner_cycles : 1;
     B->use_graph = o->use_graph;
     B->user = (cudaStream_t)o->stream;
+    B->arith = o->arith;
   }
+  if (B->arith < BMG_ARITH_ROUNDED || B->arith > BMG_ARITH_FUSED)
+    return set_error(BMG_EINVAL, "batched solves: bad arith %d", B->arith);
   int rc = cuda_check(cudaStreamCreateWithFlags(&B->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming), "event");
   if (!rc) rc = cuda_check(cudaEventRecord(B->ev, B->user), "event");
@@ -1762,6 +1781,7 @@ int clone_state(const bmg_hierarchy* h0, cudaStream_t s, bmg_hierarchy** out) {
   h->inner = h0->inner;
   h->coarsest = h0->coarsest;
   h->use_graph = 0;
+  h->arith = h0->arith;
   h->m = h0->m;
   h->Lfac = h0->Lfac;
   h->work = h0->work;
@@ -1773,6 +1793,7 @@ int clone_state(const bmg_hierarchy* h0, cudaStream_t s, bmg_hierarchy** out) {
     L.n = S.n;
     L.kind = S.kind;
     L.bf16 = S.bf16;
+    L.fused = S.fused;
     L.st = S.st;
     L.ci = S.ci;
     L.st32 = S.st32;
@@ -1876,12 +1897,15 @@ int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch**
   if (o && o->precision != h0->precision)
     return set_error(BMG_EINVAL, "bmg_batch_rhs: precision %d differs from the hierarchy's %d", o->precision,
                      h0->precision);
+  if (o && o->arith != h0->arith)
+    return set_error(BMG_EINVAL, "bmg_batch_rhs: arith %d differs from the hierarchy's %d", o->arith, h0->arith);
   bmg_batch* B = new bmg_batch();
   B->nprob = k;
   bmg_opts so{};
   CounterScope cs(&B->launches);
   int rc = batch_init(B, o, &so);
   B->precision = h0->precision;
+  B->arith = h0->arith;
   if (!rc) rc = cuda_check(cudaStreamSynchronize(h0->ws), "bmg_batch_rhs");   // h0's setup has finished
   for (int p = 0; p < k && !rc; ++p) {
     bmg_hierarchy* h = nullptr;

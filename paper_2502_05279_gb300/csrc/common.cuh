@@ -20,6 +20,22 @@ __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
 
+// s + a b and s - a b: a rounded product then a rounded sum (FU = false), or
+// one fused multiply-add rounded once (FU = true; -a is exact).  The cycle's
+// kernels take FU from the hierarchy's arithmetic mode.
+template <bool FU> __device__ __forceinline__ double madd(double s, double a, double b) {
+  return FU ? __fma_rn(a, b, s) : radd(s, rmul(a, b));
+}
+template <bool FU> __device__ __forceinline__ double msub(double s, double a, double b) {
+  return FU ? __fma_rn(-a, b, s) : rsub(s, rmul(a, b));
+}
+template <bool FU> __device__ __forceinline__ float madd(float s, float a, float b) {
+  return FU ? __fmaf_rn(a, b, s) : radd(s, rmul(a, b));
+}
+template <bool FU> __device__ __forceinline__ float msub(float s, float a, float b) {
+  return FU ? __fmaf_rn(-a, b, s) : rsub(s, rmul(a, b));
+}
+
 // ---- storage -> compute conversion (exact for every pair used) ----
 template <typename T> __device__ __forceinline__ T cvt(double v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T cvt(float v) { return (T)v; }

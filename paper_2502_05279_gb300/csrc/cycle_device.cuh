@@ -26,19 +26,19 @@ constexpr int RFX = 2 * TXC + 1, RFY = 2 * TYC + 1;  // its fine block
 __device__ __forceinline__ bool stopped(const int* done) { return done != nullptr && *done != 0; }
 
 // s - sum over the listed neighbours of a(p,q) x_q (canonical order).
-template <typename T, typename S, bool NINE, bool WITH_O>
+template <typename T, typename S, bool NINE, bool WITH_O, bool FU = false>
 __device__ __forceinline__ T row_residual(const StencilView<T, S>& v, const T* __restrict__ x, size_t p, T s) {
   const int ld = v.ld;
-  if (WITH_O) s = rsub(s, rmul(v.O[p], x[p]));
-  s = rsub(s, rmul(cvt<T>(v.W[p]), x[p - 1]));
-  s = rsub(s, rmul(cvt<T>(v.W[p + 1]), x[p + 1]));
-  s = rsub(s, rmul(cvt<T>(v.S_[p]), x[p - ld]));
-  s = rsub(s, rmul(cvt<T>(v.S_[p + ld]), x[p + ld]));
+  if (WITH_O) s = msub<FU>(s, v.O[p], x[p]);
+  s = msub<FU>(s, cvt<T>(v.W[p]), x[p - 1]);
+  s = msub<FU>(s, cvt<T>(v.W[p + 1]), x[p + 1]);
+  s = msub<FU>(s, cvt<T>(v.S_[p]), x[p - ld]);
+  s = msub<FU>(s, cvt<T>(v.S_[p + ld]), x[p + ld]);
   if (NINE) {
-    s = rsub(s, rmul(cvt<T>(v.SW[p]), x[p - ld - 1]));
-    s = rsub(s, rmul(cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]));
-    s = rsub(s, rmul(cvt<T>(v.NW[p]), x[p + ld - 1]));
-    s = rsub(s, rmul(cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]));
+    s = msub<FU>(s, cvt<T>(v.SW[p]), x[p - ld - 1]);
+    s = msub<FU>(s, cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]);
+    s = msub<FU>(s, cvt<T>(v.NW[p]), x[p + ld - 1]);
+    s = msub<FU>(s, cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]);
   }
   return s;
 }
@@ -46,9 +46,9 @@ __device__ __forceinline__ T row_residual(const StencilView<T, S>& v, const T* _
 // ---- Gauss-Seidel ------------------------------------------------------------------
 // One update: x_p = (f_p - sum_{q != p} a_pq x_q) * d_p, d_p = 1/a_pp (stored, or
 // formed here with the same correctly rounded quotient).
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU = false>
 __device__ __forceinline__ void gs_point(const StencilView<T, S>& v, const T* __restrict__ f, T* x, size_t p) {
-  T s = row_residual<T, S, NINE, false>(v, x, p, f[p]);
+  T s = row_residual<T, S, NINE, false, FU>(v, x, p, f[p]);
   T d = v.D ? v.D[p] : rdiv(T(1), v.O[p]);
   x[p] = rmul(s, d);
 }
@@ -85,11 +85,11 @@ __device__ __forceinline__ void load_point(const StencilView<T, S>& v, const T* 
 }
 
 // (f - sum_k c_k xs_k) * d in the canonical neighbour order W, E, S, N, SW, NE, NW, SE.
-template <typename T>
+template <typename T, bool FU = false>
 __device__ __forceinline__ T update_from(const PairLoads<T>& L) {
   T s = L.f;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s = rsub(s, rmul(L.c[k], L.xs[k]));
+  for (int k = 0; k < 8; ++k) s = msub<FU>(s, L.c[k], L.xs[k]);
   return rmul(s, L.d);
 }
 
@@ -109,7 +109,7 @@ constexpr int rows_threads_max() { return sizeof(T) == 8 ? 512 : 1024; }
 // thread reads its right neighbour from the next CTA's shared memory after
 // cluster.sync().  `bx` is the CTA's x index; the caller has already returned
 // from CTAs whose problem is finished (uniformly over the cluster).
-template <typename T, typename S, int CL>
+template <typename T, typename S, int CL, bool FU = false>
 __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x, int pj,
                                              int bx) {
   __shared__ T xo[rows_threads_max<T>()];
@@ -124,7 +124,7 @@ __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T
   if (has0) load_point(v, f, x, p0, A, true);
   if (has1) load_point(v, f, x, p1, B, false);
   if (has0) {
-    T xn = update_from(A);
+    T xn = update_from<T, FU>(A);
     x[p0] = xn;
     xo[threadIdx.x] = xn;
     B.xs[0] = xn;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T
   }
   if (has1) {
     B.xs[1] = right;
-    x[p1] = update_from(B);
+    x[p1] = update_from<T, FU>(B);
   }
 }
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ void line_row_body(const StencilView<T, S>& v, const 
 // Red-black half sweep for 5-point stencils: the points with (i + j) % 2 == c
 // (c = 0 red, c = 1 black), which share no coupling.  Thread grid: x over the
 // points of a row, y over rows.
-template <typename T, typename S>
+template <typename T, typename S, bool FU = false>
 __device__ __forceinline__ void gs_checker_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x, int c,
                                                 int bx, int by) {
   const int n = v.n;
@@ -202,7 +202,7 @@ __device__ __forceinline__ void gs_checker_body(const StencilView<T, S>& v, cons
   if (j > n) return;
   const int i = 2 * (bx * blockDim.x + threadIdx.x) + 1 + ((j + 1 + c) & 1);
   if (i > n) return;
-  gs_point<T, S, false>(v, f, x, (size_t)j * v.ld + i);
+  gs_point<T, S, false, FU>(v, f, x, (size_t)j * v.ld + i);
 }
 
 // ---- four-colour sweep in one pass (FP32 compute): warp strips ------------------------
@@ -261,20 +261,20 @@ __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xf
 // (lane value a), then the even-i points (lane value b), each in the order
 // W, E, S, N, SW, NE, NW, SE; oka / okb say whether this lane's points are
 // updated.
-template <typename S>
+template <typename S, bool FU = false>
 __device__ __forceinline__ void strip_row(const StripRow<S>& L, StripRow<S>& M, const StripRow<S>& U, bool oka,
                                           bool okb) {
   {   // odd-i point c = 2l: same-row neighbours c - 1 (lane l - 1's b) and c + 1 (own b)
     const float xw = shfl_up1(M.xb), xsw = shfl_up1(L.xb), xnw = shfl_up1(U.xb);
     float s = M.fa;
-    s = rsub(s, rmul(cvt<float>(M.wa), xw));
-    s = rsub(s, rmul(cvt<float>(M.wb), M.xb));
-    s = rsub(s, rmul(cvt<float>(M.sa), L.xa));
-    s = rsub(s, rmul(cvt<float>(U.sa), U.xa));
-    s = rsub(s, rmul(cvt<float>(M.swa), xsw));
-    s = rsub(s, rmul(cvt<float>(U.swb), U.xb));
-    s = rsub(s, rmul(cvt<float>(M.nwa), xnw));
-    s = rsub(s, rmul(cvt<float>(L.nwb), L.xb));
+    s = msub<FU>(s, cvt<float>(M.wa), xw);
+    s = msub<FU>(s, cvt<float>(M.wb), M.xb);
+    s = msub<FU>(s, cvt<float>(M.sa), L.xa);
+    s = msub<FU>(s, cvt<float>(U.sa), U.xa);
+    s = msub<FU>(s, cvt<float>(M.swa), xsw);
+    s = msub<FU>(s, cvt<float>(U.swb), U.xb);
+    s = msub<FU>(s, cvt<float>(M.nwa), xnw);
+    s = msub<FU>(s, cvt<float>(L.nwb), L.xb);
     const float xn = rmul(s, M.da);
     M.xa = oka ? xn : M.xa;
   }
@@ -283,14 +283,14 @@ __device__ __forceinline__ void strip_row(const StripRow<S>& L, StripRow<S>& M, 
     const float xne = shfl_dn1(U.xa), swne = shfl_dn1(cvt<float>(U.swa));
     const float xse = shfl_dn1(L.xa), nwse = shfl_dn1(cvt<float>(L.nwa));
     float s = M.fb;
-    s = rsub(s, rmul(cvt<float>(M.wb), M.xa));
-    s = rsub(s, rmul(we, xe));
-    s = rsub(s, rmul(cvt<float>(M.sb), L.xb));
-    s = rsub(s, rmul(cvt<float>(U.sb), U.xb));
-    s = rsub(s, rmul(cvt<float>(M.swb), L.xa));
-    s = rsub(s, rmul(swne, xne));
-    s = rsub(s, rmul(cvt<float>(M.nwb), U.xa));
-    s = rsub(s, rmul(nwse, xse));
+    s = msub<FU>(s, cvt<float>(M.wb), M.xa);
+    s = msub<FU>(s, we, xe);
+    s = msub<FU>(s, cvt<float>(M.sb), L.xb);
+    s = msub<FU>(s, cvt<float>(U.sb), U.xb);
+    s = msub<FU>(s, cvt<float>(M.swb), L.xa);
+    s = msub<FU>(s, swne, xne);
+    s = msub<FU>(s, cvt<float>(M.nwb), U.xa);
+    s = msub<FU>(s, nwse, xse);
     const float xn = rmul(s, M.db);
     M.xb = okb ? xn : M.xb;
   }
@@ -305,7 +305,7 @@ __device__ __forceinline__ void strip_store(float* __restrict__ xout, int n, int
   if (ic + 1 <= n) xout[p + 1] = R.xb;
 }
 
-template <typename S, int TY>
+template <typename S, int TY, bool FU = false>
 __device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, const float* __restrict__ f,
                                               const float* __restrict__ xin, float* __restrict__ xout, int sx,
                                               int sy) {
@@ -331,11 +331,11 @@ __device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, co
       strip_load(v, f, xin, ic, a + 3, p1);
     }
     if (a <= n) {
-      strip_row(r1, r2, r3, c1, c2);               // row a: c1, c2
+      strip_row<S, FU>(r1, r2, r3, c1, c2);               // row a: c1, c2
       if (a < j1) strip_store(xout, n, ld, ic, a, own, r2);
     }
     if (m >= 1 && a - 1 <= n) {
-      strip_row(r0, r1, r2, c3, c4);               // row a - 1: c3, c4
+      strip_row<S, FU>(r0, r1, r2, c3, c4);               // row a - 1: c3, c4
       strip_store(xout, n, ld, ic, a - 1, own, r1);
     }
     r0 = r2;
@@ -473,7 +473,7 @@ __device__ __forceinline__ void ring_read(const unsigned char* slot, int ld, int
   R.nwb = nwq[o8 + 1];
 }
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU = false>
 __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
                                                    const float* __restrict__ xin, float* __restrict__ xout,
                                                    int sx, int sy, unsigned char* ring, unsigned long long* bars) {
@@ -517,7 +517,7 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
   take(1, Q0);
   take(2, Q1);
   if (ok && j0 <= n) {
-    strip_row(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
+    strip_row<S, FU>(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
     strip_store(xout, n, ld, ic, j0, own, Q0);
   }
   // step m: old pair = rows a - 2, a - 1; new pair = rows a, a + 1 (band rows 2m + 1, 2m + 2)
@@ -527,11 +527,11 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
     take(2 * m + 2, E3);
     if (!ok) return;
     if (a <= n) {
-      strip_row(E1, E2, E3, c1, c2);              // row a: c1, c2
+      strip_row<S, FU>(E1, E2, E3, c1, c2);              // row a: c1, c2
       if (a < j1) strip_store(xout, n, ld, ic, a, own, E2);
     }
     if (a - 1 <= n) {
-      strip_row(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
+      strip_row<S, FU>(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
       strip_store(xout, n, ld, ic, a - 1, own, E1);
     }
   };
@@ -563,7 +563,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU = false>
 __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
                                                     const float* __restrict__ xin, float* __restrict__ xout,
                                                     int sx, int sy, unsigned char* ring, unsigned long long* bars) {
@@ -621,14 +621,14 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
       take(2 * m + 2, R5);
       if (!ok) break;
     }
-    if (a >= 1 && a <= n) strip_row(R3, R4, R5, p1, q1);                 // sweep 1, row a
-    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
+    if (a >= 1 && a <= n) strip_row<S, FU>(R3, R4, R5, p1, q1);                 // sweep 1, row a
+    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<S, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
     if (m >= 2 && b <= n) {                                               // sweep 2, row a - 2
-      strip_row(R1, R2, R3, p2, q2);
+      strip_row<S, FU>(R1, R2, R3, p2, q2);
       if (b < j1) strip_store(xout, n, ld, ic, b, own, R2);
     }
     if (m >= 3 && b - 1 <= n) {                                           // sweep 2, row a - 3
-      strip_row(R0, R1, R2, r2, t2);
+      strip_row<S, FU>(R0, R1, R2, r2, t2);
       strip_store(xout, n, ld, ic, b - 1, own, R1);
     }
     R0 = R2;
@@ -647,7 +647,7 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
 // fine residual once, shared columns/rows recomputed at tile seams), then each
 // thread applies the Fig. 2 restriction to one coarse point and zeroes the
 // coarse iterate there.
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU = false>
 __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, const T* __restrict__ ci,
                                                     const T* __restrict__ x, const T* __restrict__ f,
                                                     T* __restrict__ fc, T* __restrict__ xc, int bx, int by) {
@@ -662,7 +662,7 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
     T val = T(0);
     if (i <= n && j <= n) {
       size_t p = (size_t)j * ld + i;
-      val = row_residual<T, S, NINE, true>(v, x, p, f[p]);
+      val = row_residual<T, S, NINE, true, FU>(v, x, p, f[p]);
     }
     r[lj][li] = val;
   }
@@ -673,14 +673,14 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
   const int li = 2 * threadIdx.x + 1, lj = 2 * threadIdx.y + 1;   // fine (2ic, 2jc) in the tile
   auto w = [&](int k, int dic, int djc) { return ci[k * psc + (size_t)(jc + djc) * ldc + (ic + dic)]; };
   T t = rmul(w(CI_LNE, 0, 0), r[lj - 1][li - 1]);
-  t = radd(t, rmul(w(CI_LA, 0, 0), r[lj - 1][li]));
-  t = radd(t, rmul(w(CI_LNW, 1, 0), r[lj - 1][li + 1]));
-  t = radd(t, rmul(w(CI_LR, 0, 0), r[lj][li - 1]));
+  t = madd<FU>(t, w(CI_LA, 0, 0), r[lj - 1][li]);
+  t = madd<FU>(t, w(CI_LNW, 1, 0), r[lj - 1][li + 1]);
+  t = madd<FU>(t, w(CI_LR, 0, 0), r[lj][li - 1]);
   t = radd(t, r[lj][li]);
-  t = radd(t, rmul(w(CI_LL, 1, 0), r[lj][li + 1]));
-  t = radd(t, rmul(w(CI_LSE, 0, 1), r[lj + 1][li - 1]));
-  t = radd(t, rmul(w(CI_LB, 0, 1), r[lj + 1][li]));
-  t = radd(t, rmul(w(CI_LSW, 1, 1), r[lj + 1][li + 1]));
+  t = madd<FU>(t, w(CI_LL, 1, 0), r[lj][li + 1]);
+  t = madd<FU>(t, w(CI_LSE, 0, 1), r[lj + 1][li - 1]);
+  t = madd<FU>(t, w(CI_LB, 0, 1), r[lj + 1][li]);
+  t = madd<FU>(t, w(CI_LSW, 1, 1), r[lj + 1][li + 1]);
   size_t pc = (size_t)jc * ldc + ic;
   fc[pc] = t;
   if (xc) xc[pc] = T(0);
@@ -691,7 +691,7 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
 // and centre fine points.  xout = xin + (P e)_p, the interpolated value formed
 // first; xin and xout may be the same array (every point is read and written by
 // the same thread only).
-template <typename T>
+template <typename T, bool FU = false>
 __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, const T* __restrict__ ec,
                                             const T* xin, T* xout, int ic, int jc) {
   int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
@@ -702,19 +702,19 @@ __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, con
   if (ic <= nc && jc <= nc) xout[pf] = radd(xin[pf], e_ne);
   if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
     T t = rmul(ci[CI_LL * psc + pc], e_nw);
-    t = radd(t, rmul(ci[CI_LR * psc + pc], e_ne));
+    t = madd<FU>(t, ci[CI_LR * psc + pc], e_ne);
     xout[pf - 1] = radd(xin[pf - 1], t);
   }
   if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
     T t = rmul(ci[CI_LB * psc + pc], e_se);
-    t = radd(t, rmul(ci[CI_LA * psc + pc], e_ne));
+    t = madd<FU>(t, ci[CI_LA * psc + pc], e_ne);
     xout[pf - ld] = radd(xin[pf - ld], t);
   }
   {                                               // centre (2ic-1, 2jc-1)
     T t = rmul(ci[CI_LSW * psc + pc], e_sw);
-    t = radd(t, rmul(ci[CI_LSE * psc + pc], e_se));
-    t = radd(t, rmul(ci[CI_LNW * psc + pc], e_nw));
-    t = radd(t, rmul(ci[CI_LNE * psc + pc], e_ne));
+    t = madd<FU>(t, ci[CI_LSE * psc + pc], e_se);
+    t = madd<FU>(t, ci[CI_LNW * psc + pc], e_nw);
+    t = madd<FU>(t, ci[CI_LNE * psc + pc], e_ne);
     xout[pf - ld - 1] = radd(xin[pf - ld - 1], t);
   }
 }
@@ -738,7 +738,7 @@ __device__ __forceinline__ double block_sum(double acc) {
 
 __host__ __device__ inline int norm_blocks(int n) { return n < NORM_BLOCKS_MAX ? n : NORM_BLOCKS_MAX; }
 
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU = false>
 __device__ __forceinline__ void residual_body(const StencilView<T, S>& v, const T* __restrict__ x,
                                               const T* __restrict__ f, T* __restrict__ r,
                                               double* __restrict__ partials, int b, int G) {
@@ -747,10 +747,10 @@ __device__ __forceinline__ void residual_body(const StencilView<T, S>& v, const 
   for (int j = 1 + b; j <= n; j += G)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
-      T s = row_residual<T, S, NINE, true>(v, x, p, f[p]);
+      T s = row_residual<T, S, NINE, true, FU>(v, x, p, f[p]);
       if (r) r[p] = s;
       double d = (double)s;
-      acc = __dadd_rn(acc, __dmul_rn(d, d));
+      acc = madd<FU>(acc, d, d);
     }
   if (partials) {
     double tot = block_sum(acc);
@@ -827,6 +827,7 @@ __device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, co
 }
 
 // r = f - A x (FP64), r32 = fl32(r / scale_next), e32 = 0, partial sums of r^2.
+template <bool FU = false>
 __device__ __forceinline__ void ir_residual_body(const StencilView<double, double>& v, bool nine,
                                                  const double* __restrict__ x, const double* __restrict__ f,
                                                  float* __restrict__ r32, float* __restrict__ e32,
@@ -838,11 +839,11 @@ __device__ __forceinline__ void ir_residual_body(const StencilView<double, doubl
   for (int j = 1 + b; j <= n; j += G)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
-      double rr = nine ? row_residual<double, double, true, true>(v, x, p, f[p])
-                       : row_residual<double, double, false, true>(v, x, p, f[p]);
+      double rr = nine ? row_residual<double, double, true, true, FU>(v, x, p, f[p])
+                       : row_residual<double, double, false, true, FU>(v, x, p, f[p]);
       r32[p] = __double2float_rn(rmul(rr, inv));
       e32[p] = 0.0f;
-      acc = __dadd_rn(acc, __dmul_rn(rr, rr));
+      acc = madd<FU>(acc, rr, rr);
     }
   double tot = block_sum(acc);
   if (threadIdx.x == 0) {
@@ -873,45 +874,45 @@ namespace dev {
 
 // Half of a four-colour sweep over one CTA: the rows of parity pj, their odd-i
 // points, a barrier, their even-i points, a barrier (the order of k_gs_rows).
-template <typename T, typename S>
+template <typename T, typename S, bool FU = false>
 __device__ __forceinline__ void gs_half_block(const StencilView<T, S>& v, const T* f, T* x, int pj) {
   const int n = v.n;
   const int R = pj ? (n + 1) / 2 : (n - 1) / 2;
   const int Po = (n + 1) / 2, Pe = (n - 1) / 2;
   for (int k = threadIdx.x; k < R * Po; k += blockDim.x) {
     int j = 2 * (k / Po) + (pj ? 1 : 2), i = 2 * (k % Po) + 1;
-    gs_point<T, S, true>(v, f, x, (size_t)j * v.ld + i);
+    gs_point<T, S, true, FU>(v, f, x, (size_t)j * v.ld + i);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < R * Pe; k += blockDim.x) {
     int j = 2 * (k / Pe) + (pj ? 1 : 2), i = 2 * (k % Pe) + 2;
-    gs_point<T, S, true>(v, f, x, (size_t)j * v.ld + i);
+    gs_point<T, S, true, FU>(v, f, x, (size_t)j * v.ld + i);
   }
   __syncthreads();
 }
 
 // One red-black colour over one CTA (5-point levels).
-template <typename T, typename S>
+template <typename T, typename S, bool FU = false>
 __device__ __forceinline__ void gs_checker_block(const StencilView<T, S>& v, const T* f, T* x, int c) {
   const int n = v.n;
   const int per_row = (n + 1) / 2;
   for (int k = threadIdx.x; k < n * per_row; k += blockDim.x) {
     int j = k / per_row + 1;
     int i = 2 * (k % per_row) + 1 + ((j + 1 + c) & 1);
-    if (i <= n) gs_point<T, S, false>(v, f, x, (size_t)j * v.ld + i);
+    if (i <= n) gs_point<T, S, false, FU>(v, f, x, (size_t)j * v.ld + i);
   }
   __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool FU = false>
 __device__ __forceinline__ void relax_block(const LevelDesc<T, T>& q, int kind, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
     if (kind == 9) {
-      gs_half_block<T, T>(q.v, q.f, q.x, 1);
-      gs_half_block<T, T>(q.v, q.f, q.x, 0);
+      gs_half_block<T, T, FU>(q.v, q.f, q.x, 1);
+      gs_half_block<T, T, FU>(q.v, q.f, q.x, 0);
     } else {
-      gs_checker_block<T, T>(q.v, q.f, q.x, 0);
-      gs_checker_block<T, T>(q.v, q.f, q.x, 1);
+      gs_checker_block<T, T, FU>(q.v, q.f, q.x, 0);
+      gs_checker_block<T, T, FU>(q.v, q.f, q.x, 1);
     }
   }
 }
@@ -919,7 +920,7 @@ __device__ __forceinline__ void relax_block(const LevelDesc<T, T>& q, int kind, 
 // Residual + Fig. 2 restriction, one coarse point per thread iteration; the
 // nine fine residuals are formed where they are needed (same values as the
 // tiled kernel: each is the same expression of the same data).
-template <typename T, bool NINE>
+template <typename T, bool NINE, bool FU = false>
 __device__ __forceinline__ void resid_restrict_block(const LevelDesc<T, T>& q) {
   const StencilView<T, T>& v = q.v;
   const int n = v.n, ld = v.ld, nc = (n - 1) / 2, ldc = nc + 2;
@@ -929,18 +930,18 @@ __device__ __forceinline__ void resid_restrict_block(const LevelDesc<T, T>& q) {
     size_t pf = (size_t)(2 * jc) * ld + 2 * ic;
     auto r = [&](int dx, int dy) {
       size_t p = pf + (size_t)((long long)dy * ld + dx);
-      return row_residual<T, T, NINE, true>(v, q.x, p, q.f[p]);
+      return row_residual<T, T, NINE, true, FU>(v, q.x, p, q.f[p]);
     };
     auto w = [&](int kk, int dic, int djc) { return q.ci[kk * psc + (size_t)(jc + djc) * ldc + (ic + dic)]; };
     T t = rmul(w(CI_LNE, 0, 0), r(-1, -1));
-    t = radd(t, rmul(w(CI_LA, 0, 0), r(0, -1)));
-    t = radd(t, rmul(w(CI_LNW, 1, 0), r(1, -1)));
-    t = radd(t, rmul(w(CI_LR, 0, 0), r(-1, 0)));
+    t = madd<FU>(t, w(CI_LA, 0, 0), r(0, -1));
+    t = madd<FU>(t, w(CI_LNW, 1, 0), r(1, -1));
+    t = madd<FU>(t, w(CI_LR, 0, 0), r(-1, 0));
     t = radd(t, r(0, 0));
-    t = radd(t, rmul(w(CI_LL, 1, 0), r(1, 0)));
-    t = radd(t, rmul(w(CI_LSE, 0, 1), r(-1, 1)));
-    t = radd(t, rmul(w(CI_LB, 0, 1), r(0, 1)));
-    t = radd(t, rmul(w(CI_LSW, 1, 1), r(1, 1)));
+    t = madd<FU>(t, w(CI_LL, 1, 0), r(1, 0));
+    t = madd<FU>(t, w(CI_LSE, 0, 1), r(-1, 1));
+    t = madd<FU>(t, w(CI_LB, 0, 1), r(0, 1));
+    t = madd<FU>(t, w(CI_LSW, 1, 1), r(1, 1));
     size_t pc = (size_t)jc * ldc + ic;
     q.fc[pc] = t;
     q.xc[pc] = T(0);
@@ -948,15 +949,15 @@ __device__ __forceinline__ void resid_restrict_block(const LevelDesc<T, T>& q) {
   __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool FU = false>
 __device__ __forceinline__ void tail_body(const TailDesc<T>& d, int top_kind) {
   for (int l = 0; l + 1 < d.nlev; ++l) {
     const int kind = l == 0 ? top_kind : 9;
-    relax_block<T>(d.lv[l], kind, d.nu1);
+    relax_block<T, FU>(d.lv[l], kind, d.nu1);
     if (kind == 9)
-      resid_restrict_block<T, true>(d.lv[l]);
+      resid_restrict_block<T, true, FU>(d.lv[l]);
     else
-      resid_restrict_block<T, false>(d.lv[l]);
+      resid_restrict_block<T, false, FU>(d.lv[l]);
   }
   const LevelDesc<T, T>& c = d.lv[d.nlev - 1];
   coarse_solve_body<T>(c.v.n, c.L, c.f, c.x, c.y);
@@ -965,9 +966,9 @@ __device__ __forceinline__ void tail_body(const TailDesc<T>& d, int top_kind) {
     const LevelDesc<T, T>& q = d.lv[l];
     const int nc = (q.v.n - 1) / 2;
     for (int k = threadIdx.x; k < (nc + 1) * (nc + 1); k += blockDim.x)
-      interp_body<T>(q.v.n, q.ci, q.xc, q.x, q.x, k % (nc + 1) + 1, k / (nc + 1) + 1);
+      interp_body<T, FU>(q.v.n, q.ci, q.xc, q.x, q.x, k % (nc + 1) + 1, k / (nc + 1) + 1);
     __syncthreads();
-    relax_block<T>(q, l == 0 ? top_kind : 9, d.nu2);
+    relax_block<T, FU>(q, l == 0 ? top_kind : 9, d.nu2);
   }
 }
 

@@ -14,41 +14,42 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
-template <typename T, typename S, int CL>
+// FU: fused multiply-adds (BMG_ARITH_FUSED), as in the single-problem kernels.
+template <typename T, typename S, int CL, bool FU>
 __global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
     k_gs_rows_b(const LevelDesc<T, S>* __restrict__ d, int pj) {
   const LevelDesc<T, S> q = d[blockIdx.y];
   if (stopped(q.done)) return;   // uniform over the cluster: its CTAs share blockIdx.y
-  gs_rows_body<T, S, CL>(q.v, q.f, q.x, pj, blockIdx.x);
+  gs_rows_body<T, S, CL, FU>(q.v, q.f, q.x, pj, blockIdx.x);
 }
 
-template <typename T, typename S>
+template <typename T, typename S, bool FU>
 __global__ void k_gs_checker_b(const LevelDesc<T, S>* __restrict__ d, int c) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  gs_checker_body<T, S>(q.v, q.f, q.x, c, blockIdx.x, blockIdx.y);
+  gs_checker_body<T, S, FU>(q.v, q.f, q.x, c, blockIdx.x, blockIdx.y);
 }
 
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T, S>* __restrict__ d, int dir) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  resid_restrict_body<T, S, NINE>(q.v, q.ci, dir ? q.x2 : q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
+  resid_restrict_body<T, S, NINE, FU>(q.v, q.ci, dir ? q.x2 : q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
 }
 
-template <typename T, typename S>
+template <typename T, typename S, bool FU>
 __global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d, int din, int dout) {
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
-  interp_body<T>(q.v.n, q.ci, q.xc, din ? q.x2 : q.x, dout ? q.x2 : q.x, blockIdx.x * blockDim.x + threadIdx.x + 1,
-                 blockIdx.y * blockDim.y + threadIdx.y + 1);
+  interp_body<T, FU>(q.v.n, q.ci, q.xc, din ? q.x2 : q.x, dout ? q.x2 : q.x,
+                     blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
 // One-pass sweeps of a group: warp g takes strip g % wpp of problem g / wpp.
 constexpr int STRIP_WARPS_B = 4;
 __device__ int g_strip_timeout_b = 0;
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const LevelDesc<float, S>* __restrict__ d,
                                                                         int count, int n, int dir) {
   extern __shared__ __align__(128) unsigned char strip_smem[];
@@ -63,13 +64,13 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const Le
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
       w * RING;
-  if (!gs_strip_ring_body<S, TY, RING>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, ring,
-                                       bars) &&
+  if (!gs_strip_ring_body<S, TY, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx,
+                                           ring, bars) &&
       (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout_b, 1);
 }
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const LevelDesc<float, S>* __restrict__ d,
                                                                          int count, int n, int dir) {
   extern __shared__ __align__(128) unsigned char strip_smem[];
@@ -84,8 +85,8 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const L
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
       w * RING;
-  if (!gs_strip2_ring_body<S, TY, RING>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, ring,
-                                        bars) &&
+  if (!gs_strip2_ring_body<S, TY, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx,
+                                            ring, bars) &&
       (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout_b, 1);
 }
@@ -100,14 +101,15 @@ __global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
 // Top-level kernels: problems of different sizes in one grid; block b of a
 // problem runs only when b < G = min(n, 1024) of that problem, so every
 // problem keeps the reduction order of its solo solve.
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __restrict__ d) {
   const TopDesc q = d[blockIdx.y];
   const int G = norm_blocks(q.v.n);
   if (q.ctl->done || (int)blockIdx.x >= G) return;
   if (q.kind == 9)
-    residual_body<double, double, true>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+    residual_body<double, double, true, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
   else
-    residual_body<double, double, false>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+    residual_body<double, double, false, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) k_finalize_b(const TopDesc* __restrict__ d, int phase) {
@@ -122,18 +124,19 @@ __global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
                  blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* __restrict__ d) {
   const TopDesc q = d[blockIdx.y];
   const int G = norm_blocks(q.v.n);
   if (q.ctl->done || (int)blockIdx.x >= G) return;
-  ir_residual_body(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
+  ir_residual_body<FU>(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
 }
 
-template <typename T>
+template <typename T, bool FU>
 __global__ void __launch_bounds__(1024) k_tail(const TailDesc<T>* __restrict__ d, const int* done) {
   const TailDesc<T>& q = d[blockIdx.x];
   if (stopped(done) || stopped(q.done)) return;
-  tail_body<T>(q, q.top_kind);
+  tail_body<T, FU>(q, q.top_kind);
 }
 
 // 1 when every problem's control flag is set.
@@ -147,7 +150,7 @@ __global__ void k_all_done(const char* __restrict__ ctls, size_t stride, int cou
   if (threadIdx.x == 0) *out = any_running ? 0 : 1;
 }
 
-template <typename T, typename S, int CL>
+template <typename T, typename S, int CL, bool FU>
 void rows_b(const LevelDesc<T, S>* d, int count, int n, int threads, cudaStream_t s) {
   for (int pj = 1; pj >= 0; --pj) {
     const int rows = pj ? (n + 1) / 2 : (n - 1) / 2;
@@ -162,7 +165,7 @@ void rows_b(const LevelDesc<T, S>* d, int count, int n, int threads, cudaStream_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = CL > 1 ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_gs_rows_b<T, S, CL>, d, pj);
+    cudaLaunchKernelEx(&cfg, k_gs_rows_b<T, S, CL, FU>, d, pj);
     count_launch();
   }
 }
@@ -171,52 +174,70 @@ void rows_b(const LevelDesc<T, S>* d, int count, int n, int threads, cudaStream_
 
 // cl: cluster size of the row kernel (>= rows_cluster<T>(n); the autotuner may
 // pick a larger one, which splits each row over more, smaller CTAs).
-template <typename T, typename S>
-void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s) {
-  if (count <= 0) return;
+template <typename T, typename S, bool FU>
+static void gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s) {
   if (kind == 9) {
     const int threads = rows_threads(n, cl);
     for (int k = 0; k < sweeps; ++k) {
       switch (cl) {
-        case 1: rows_b<T, S, 1>(d, count, n, threads, s); break;
-        case 2: rows_b<T, S, 2>(d, count, n, threads, s); break;
-        case 4: rows_b<T, S, 4>(d, count, n, threads, s); break;
-        default: rows_b<T, S, 8>(d, count, n, threads, s); break;
+        case 1: rows_b<T, S, 1, FU>(d, count, n, threads, s); break;
+        case 2: rows_b<T, S, 2, FU>(d, count, n, threads, s); break;
+        case 4: rows_b<T, S, 4, FU>(d, count, n, threads, s); break;
+        default: rows_b<T, S, 8, FU>(d, count, n, threads, s); break;
       }
     }
   } else {
     dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY, count);
     for (int k = 0; k < sweeps; ++k) {
-      k_gs_checker_b<T, S><<<g, dim3(BX, BY), 0, s>>>(d, 0);
+      k_gs_checker_b<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(d, 0);
       count_launch();
-      k_gs_checker_b<T, S><<<g, dim3(BX, BY), 0, s>>>(d, 1);
+      k_gs_checker_b<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(d, 1);
       count_launch();
     }
   }
 }
 
 template <typename T, typename S>
-void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir) {
+void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s,
+                 int fused) {
+  if (count <= 0) return;
+  if (fused)
+    gs_b<T, S, true>(d, count, n, kind, sweeps, cl, s);
+  else
+    gs_b<T, S, false>(d, count, n, kind, sweeps, cl, s);
+}
+
+template <typename T, typename S>
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir,
+                             int fused) {
   if (count <= 0) return;
   int nc = (n - 1) / 2;
   dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC, count);
-  if (kind == 9)
-    k_resid_restrict_b<T, S, true><<<g, dim3(TXC, TYC), 0, s>>>(d, dir);
+  const dim3 b(TXC, TYC);
+  if (kind == 9 && fused)
+    k_resid_restrict_b<T, S, true, true><<<g, b, 0, s>>>(d, dir);
+  else if (kind == 9)
+    k_resid_restrict_b<T, S, true, false><<<g, b, 0, s>>>(d, dir);
+  else if (fused)
+    k_resid_restrict_b<T, S, false, true><<<g, b, 0, s>>>(d, dir);
   else
-    k_resid_restrict_b<T, S, false><<<g, dim3(TXC, TYC), 0, s>>>(d, dir);
+    k_resid_restrict_b<T, S, false, false><<<g, b, 0, s>>>(d, dir);
   count_launch();
 }
 
 template <typename T, typename S>
-void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din, int dout) {
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din, int dout, int fused) {
   if (count <= 0) return;
   int nc = (n - 1) / 2;
-  k_interp_b<T, S><<<dim3((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d, din,
-                                                                                                       dout);
+  const dim3 g((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count);
+  if (fused)
+    k_interp_b<T, S, true><<<g, dim3(BX, BY), 0, s>>>(d, din, dout);
+  else
+    k_interp_b<T, S, false><<<g, dim3(BX, BY), 0, s>>>(d, din, dout);
   count_launch();
 }
 
-template <typename S, int TY, int RING, bool PAIR>
+template <typename S, int TY, int RING, bool PAIR, bool FU>
 static void strip_b_launch(const LevelDesc<float, S>* d, int count, int n, int dir, cudaStream_t s) {
   if (count <= 0) return;
   constexpr size_t bytes = (size_t)STRIP_WARPS_B * RING * (StripRing<S>::SLOT + 8);
@@ -226,42 +247,60 @@ static void strip_b_launch(const LevelDesc<float, S>* d, int count, int n, int d
   const unsigned blocks = (unsigned)((warps + STRIP_WARPS_B - 1) / STRIP_WARPS_B);
   if (PAIR) {
     if (!attr)
-      cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_gs_strip2_ring_b<S, TY, RING><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+      cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+    k_gs_strip2_ring_b<S, TY, RING, FU><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
   } else {
     if (!attr)
-      cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_gs_strip_ring_b<S, TY, RING><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+      cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+    k_gs_strip_ring_b<S, TY, RING, FU><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
   }
   attr = true;
   count_launch();
 }
 
-template <typename S>
-void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
+template <typename S, bool FU>
+static void gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
   switch (shape) {
-    case 1: strip_b_launch<S, 8, 4, false>(d, count, n, dir, s); break;
-    case 2: strip_b_launch<S, 16, 4, false>(d, count, n, dir, s); break;
-    case 3: strip_b_launch<S, 32, 4, false>(d, count, n, dir, s); break;
-    default: strip_b_launch<S, 26, 4, false>(d, count, n, dir, s); break;
+    case 1: strip_b_launch<S, 8, 4, false, FU>(d, count, n, dir, s); break;
+    case 2: strip_b_launch<S, 16, 4, false, FU>(d, count, n, dir, s); break;
+    case 3: strip_b_launch<S, 32, 4, false, FU>(d, count, n, dir, s); break;
+    default: strip_b_launch<S, 26, 4, false, FU>(d, count, n, dir, s); break;
+  }
+}
+
+template <typename S, bool FU>
+static void gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip_b_launch<S, 16, 4, true, FU>(d, count, n, dir, s); break;
+    case 2: strip_b_launch<S, 32, 6, true, FU>(d, count, n, dir, s); break;
+    case 3: strip_b_launch<S, 26, 4, true, FU>(d, count, n, dir, s); break;
+    default: strip_b_launch<S, 32, 4, true, FU>(d, count, n, dir, s); break;
   }
 }
 
 template <typename S>
-void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s) {
-  switch (shape) {
-    case 1: strip_b_launch<S, 16, 4, true>(d, count, n, dir, s); break;
-    case 2: strip_b_launch<S, 32, 6, true>(d, count, n, dir, s); break;
-    case 3: strip_b_launch<S, 26, 4, true>(d, count, n, dir, s); break;
-    default: strip_b_launch<S, 32, 4, true>(d, count, n, dir, s); break;
-  }
+void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s, int fused) {
+  if (fused)
+    gs_tile_b<S, true>(d, count, n, shape, dir, s);
+  else
+    gs_tile_b<S, false>(d, count, n, shape, dir, s);
 }
-template void launch_gs_tile_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t);
+
+template <typename S>
+void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s, int fused) {
+  if (fused)
+    gs_pair_b<S, true>(d, count, n, shape, dir, s);
+  else
+    gs_pair_b<S, false>(d, count, n, shape, dir, s);
+}
+template void launch_gs_tile_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t, int);
 template void launch_gs_tile_b<__nv_bfloat16>(const LevelDesc<float, __nv_bfloat16>*, int, int, int, int,
-                                              cudaStream_t);
-template void launch_gs_pair_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t);
+                                              cudaStream_t, int);
+template void launch_gs_pair_b<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t, int);
 template void launch_gs_pair_b<__nv_bfloat16>(const LevelDesc<float, __nv_bfloat16>*, int, int, int, int,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 
 int strip_timeouts_b() {
   int h = 0, zero = 0;
@@ -277,8 +316,11 @@ void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s) {
   count_launch();
 }
 
-void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
-  k_residual_b<<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
+  if (fused)
+    k_residual_b<true><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+  else
+    k_residual_b<false><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
   count_launch();
 }
 
@@ -292,20 +334,26 @@ void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
   count_launch();
 }
 
-void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
-  k_ir_residual_b<<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
+  if (fused)
+    k_ir_residual_b<true><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+  else
+    k_ir_residual_b<false><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
   count_launch();
 }
 
 template <typename T>
-void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s) {
+void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s, int fused) {
   if (count <= 0) return;
   (void)top_kind;
-  k_tail<T><<<count, 1024, 0, s>>>(d, done_any);
+  if (fused)
+    k_tail<T, true><<<count, 1024, 0, s>>>(d, done_any);
+  else
+    k_tail<T, false><<<count, 1024, 0, s>>>(d, done_any);
   count_launch();
 }
-template void launch_tail<double>(const TailDesc<double>*, int, int, const int*, cudaStream_t);
-template void launch_tail<float>(const TailDesc<float>*, int, int, const int*, cudaStream_t);
+template void launch_tail<double>(const TailDesc<double>*, int, int, const int*, cudaStream_t, int);
+template void launch_tail<float>(const TailDesc<float>*, int, int, const int*, cudaStream_t, int);
 
 void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s) {
   k_all_done<<<1, 256, 0, s>>>(ctls, stride, count, out);
@@ -313,9 +361,9 @@ void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaS
 }
 
 #define BMG_INST_B(T, S)                                                                                 \
-  template void launch_gs_b<T, S>(const LevelDesc<T, S>*, int, int, int, int, int, cudaStream_t);       \
-  template void launch_resid_restrict_b<T, S>(const LevelDesc<T, S>*, int, int, int, cudaStream_t, int); \
-  template void launch_interp_b<T, S>(const LevelDesc<T, S>*, int, int, cudaStream_t, int, int);       \
+  template void launch_gs_b<T, S>(const LevelDesc<T, S>*, int, int, int, int, int, cudaStream_t, int);       \
+  template void launch_resid_restrict_b<T, S>(const LevelDesc<T, S>*, int, int, int, cudaStream_t, int, int); \
+  template void launch_interp_b<T, S>(const LevelDesc<T, S>*, int, int, cudaStream_t, int, int, int);        \
   template void launch_coarse_b<T, S>(const LevelDesc<T, S>*, int, cudaStream_t);
 BMG_INST_B(double, double)
 BMG_INST_B(float, float)

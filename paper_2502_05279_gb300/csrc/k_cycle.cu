@@ -16,23 +16,25 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
-template <typename T, typename S, int CL>
+// FU (every kernel of the cycle): fused multiply-adds (the hierarchy's
+// arithmetic mode BMG_ARITH_FUSED) instead of rounded products and sums.
+template <typename T, typename S, int CL, bool FU>
 __global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
     k_gs_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, int pj, const int* done) {
   if (stopped(done)) return;   // uniform over the grid: every CTA of a cluster leaves together
-  gs_rows_body<T, S, CL>(v, f, x, pj, blockIdx.x);
+  gs_rows_body<T, S, CL, FU>(v, f, x, pj, blockIdx.x);
 }
 
-template <typename T, typename S>
+template <typename T, typename S, bool FU>
 __global__ void k_gs_checker(StencilView<T, S> v, const T* __restrict__ f, T* x, int c, const int* done) {
   if (stopped(done)) return;
-  gs_checker_body<T, S>(v, f, x, c, blockIdx.x, blockIdx.y);
+  gs_checker_body<T, S, FU>(v, f, x, c, blockIdx.x, blockIdx.y);
 }
 
 // One warp per strip of 56 x TY points; warp g of the grid takes strip
 // (g % nbx, g / nbx), so the warps of a CTA take neighbouring strips of one band.
 constexpr int STRIP_WARPS = 4;
-template <typename S, int TY>
+template <typename S, int TY, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float, S> v, const float* __restrict__ f,
                                                                const float* __restrict__ xin,
                                                                float* __restrict__ xout, const int* done) {
@@ -40,13 +42,13 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float
   const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
   const int g = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
   if (g >= nbx * nby) return;                     // whole warps only
-  gs_strip_body<S, TY>(v, f, xin, xout, g % nbx, g / nbx);
+  gs_strip_body<S, TY, FU>(v, f, xin, xout, g % nbx, g / nbx);
 }
 
 // Bulk-copy form: warp w of the CTA owns ring slots [w RING, (w + 1) RING) and
 // mbarriers [w RING, (w + 1) RING) of the dynamic shared memory.
 __device__ int g_strip_timeout = 0;
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<float, S> v,
                                                                     const float* __restrict__ f,
                                                                     const float* __restrict__ xin,
@@ -59,12 +61,12 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<
   unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
-  if (!gs_strip_ring_body<S, TY, RING>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+  if (!gs_strip_ring_body<S, TY, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout, 1);
 }
 
 // Two sweeps in one pass: warps take 48-column strips, otherwise as above.
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView<float, S> v,
                                                                      const float* __restrict__ f,
                                                                      const float* __restrict__ xin,
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView
   unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
-  if (!gs_strip2_ring_body<S, TY, RING>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+  if (!gs_strip2_ring_body<S, TY, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout, 1);
 }
 
@@ -91,29 +93,29 @@ __global__ void k_line_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, 
   line_row_body<T, S, NINE>(v, f, x, cp, j);
 }
 
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
                                                             const T* __restrict__ x, const T* __restrict__ f,
                                                             T* __restrict__ fc, T* __restrict__ xc,
                                                             const int* done) {
   if (stopped(done)) return;
-  resid_restrict_body<T, S, NINE>(v, ci, x, f, fc, xc, blockIdx.x, blockIdx.y);
+  resid_restrict_body<T, S, NINE, FU>(v, ci, x, f, fc, xc, blockIdx.x, blockIdx.y);
 }
 
-template <typename T>
+template <typename T, bool FU>
 __global__ void k_interp_correct(int n, const T* __restrict__ ci, const T* __restrict__ ec, const T* xin, T* xout,
                                  const int* done) {
   if (stopped(done)) return;
-  interp_body<T>(n, ci, ec, xin, xout, blockIdx.x * blockDim.x + threadIdx.x + 1,
+  interp_body<T, FU>(n, ci, ec, xin, xout, blockIdx.x * blockDim.x + threadIdx.x + 1,
                  blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
-template <typename T, typename S, bool NINE>
+template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_residual(StencilView<T, S> v, const T* __restrict__ x,
                                                            const T* __restrict__ f, T* __restrict__ r,
                                                            double* __restrict__ partials, const int* done) {
   if (stopped(done)) return;
-  residual_body<T, S, NINE>(v, x, f, r, partials, blockIdx.x, gridDim.x);
+  residual_body<T, S, NINE, FU>(v, x, f, r, partials, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_zero_ring(int n, double* r) {
@@ -144,13 +146,14 @@ __global__ void k_ir_update(int n, double* __restrict__ x, const float* __restri
   ir_update_body(n, x, e32, ctl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual(StencilView<double, double> v, int nine,
                                                               const double* __restrict__ x,
                                                               const double* __restrict__ f, float* __restrict__ r32,
                                                               float* __restrict__ e32, double* __restrict__ partials,
                                                               Ctl* ctl) {
   if (ctl->done) return;
-  ir_residual_body(v, nine != 0, x, f, r32, e32, partials, ctl, blockIdx.x, gridDim.x);
+  ir_residual_body<FU>(v, nine != 0, x, f, r32, e32, partials, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---- FP64 throughput probe ---------------------------------------------------------
@@ -172,7 +175,7 @@ int norm_partials_max() { return NORM_BLOCKS_MAX; }
 
 // Cluster launch of k_gs_rows: grid = rows * CL CTAs, clusters of CL along x, so
 // cluster rank = blockIdx.x % CL and the CTAs of one row form one cluster.
-template <typename T, typename S, int CL>
+template <typename T, typename S, int CL, bool FU>
 void launch_rows_half(const StencilView<T, S>& v, const T* f, T* x, int pj, int rows, int threads, const int* done,
                       cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -187,7 +190,7 @@ void launch_rows_half(const StencilView<T, S>& v, const T* f, T* x, int pj, int 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = CL > 1 ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k_gs_rows<T, S, CL>, v, f, x, pj, done);
+  cudaLaunchKernelEx(&cfg, k_gs_rows<T, S, CL, FU>, v, f, x, pj, done);
   count_launch();
 }
 
@@ -205,9 +208,9 @@ int rows_threads(int n, int cl) {
   return (threads + 31) / 32 * 32;
 }
 
-template <typename T, typename S>
-void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
-               int cl_req) {
+template <typename T, typename S, bool FU>
+static void gs_sweeps(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done,
+                      cudaStream_t s, int cl_req) {
   const int n = v.n;
   if (kind == 9) {
     const int cl = cl_req >= rows_cluster<T>(n) && cl_req <= 8 ? cl_req : rows_cluster<T>(n);
@@ -216,21 +219,30 @@ void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweep
       for (int pj = 1; pj >= 0; --pj) {
         const int rows = pj ? (n + 1) / 2 : (n - 1) / 2;
         switch (cl) {
-          case 1: launch_rows_half<T, S, 1>(v, f, x, pj, rows, threads, done, s); break;
-          case 2: launch_rows_half<T, S, 2>(v, f, x, pj, rows, threads, done, s); break;
-          case 4: launch_rows_half<T, S, 4>(v, f, x, pj, rows, threads, done, s); break;
-          default: launch_rows_half<T, S, 8>(v, f, x, pj, rows, threads, done, s); break;
+          case 1: launch_rows_half<T, S, 1, FU>(v, f, x, pj, rows, threads, done, s); break;
+          case 2: launch_rows_half<T, S, 2, FU>(v, f, x, pj, rows, threads, done, s); break;
+          case 4: launch_rows_half<T, S, 4, FU>(v, f, x, pj, rows, threads, done, s); break;
+          default: launch_rows_half<T, S, 8, FU>(v, f, x, pj, rows, threads, done, s); break;
         }
       }
   } else {
     dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY);
     for (int k = 0; k < sweeps; ++k) {
-      k_gs_checker<T, S><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 0, done);
+      k_gs_checker<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 0, done);
       count_launch();
-      k_gs_checker<T, S><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 1, done);
+      k_gs_checker<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 1, done);
       count_launch();
     }
   }
+}
+
+template <typename T, typename S>
+void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
+               int cl_req) {
+  if (v.fused)
+    gs_sweeps<T, S, true>(v, kind, f, x, sweeps, done, s, cl_req);
+  else
+    gs_sweeps<T, S, false>(v, kind, f, x, sweeps, done, s, cl_req);
 }
 
 template <typename T, typename S>
@@ -238,37 +250,56 @@ void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, co
                            const int* done, cudaStream_t s) {
   int nc = (v.n - 1) / 2;
   dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC);
-  if (kind == 9)
-    k_resid_restrict<T, S, true><<<g, dim3(TXC, TYC), 0, s>>>(v, ci, x, f, fc, xc, done);
+  const dim3 b(TXC, TYC);
+  if (kind == 9 && v.fused)
+    k_resid_restrict<T, S, true, true><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+  else if (kind == 9)
+    k_resid_restrict<T, S, true, false><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+  else if (v.fused)
+    k_resid_restrict<T, S, false, true><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
   else
-    k_resid_restrict<T, S, false><<<g, dim3(TXC, TYC), 0, s>>>(v, ci, x, f, fc, xc, done);
+    k_resid_restrict<T, S, false, false><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
   count_launch();
 }
 
-template <typename S, int TY>
+template <typename S, int TY, bool FU>
 static void strip_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                          const int* done, cudaStream_t s) {
   const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
-  k_gs_strip<S, TY><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, s>>>(v, f, xin, xout, done);
+  k_gs_strip<S, TY, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, s>>>(v, f, xin, xout, done);
   count_launch();
 }
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 static void strip_ring_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                               const int* done, cudaStream_t s) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gs_strip_ring<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_gs_strip_ring<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
     attr = true;
   }
   const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
-  k_gs_strip_ring<S, TY, RING><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+  k_gs_strip_ring<S, TY, RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
       v, f, xin, xout, done);
   count_launch();
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+template <typename S, bool FU>
+static void gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip_ring_launch<S, 8, 4, FU>(v, f, xin, xout, done, s); break;
+    case 2: strip_ring_launch<S, 16, 4, FU>(v, f, xin, xout, done, s); break;
+    case 3: strip_ring_launch<S, 32, 4, FU>(v, f, xin, xout, done, s); break;
+    case 4: strip_launch<S, 32, FU>(v, f, xin, xout, done, s); break;
+    case 5: strip_launch<S, 16, FU>(v, f, xin, xout, done, s); break;
+    default: strip_ring_launch<S, 26, 4, FU>(v, f, xin, xout, done, s); break;
+  }
+}
 
 template <typename S>
 void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
@@ -276,14 +307,10 @@ void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float*
   const bool ring_ok = aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) &&
                        aligned16(v.SW) && aligned16(v.NW);
   if (shape < 4 && !ring_ok) shape = 4;           // bulk copies need 16-byte aligned arrays
-  switch (shape) {
-    case 1: strip_ring_launch<S, 8, 4>(v, f, xin, xout, done, s); break;
-    case 2: strip_ring_launch<S, 16, 4>(v, f, xin, xout, done, s); break;
-    case 3: strip_ring_launch<S, 32, 4>(v, f, xin, xout, done, s); break;
-    case 4: strip_launch<S, 32>(v, f, xin, xout, done, s); break;
-    case 5: strip_launch<S, 16>(v, f, xin, xout, done, s); break;
-    default: strip_ring_launch<S, 26, 4>(v, f, xin, xout, done, s); break;
-  }
+  if (v.fused)
+    gs_tile<S, true>(v, f, xin, xout, shape, done, s);
+  else
+    gs_tile<S, false>(v, f, xin, xout, shape, done, s);
 }
 
 // One warp waits, through the same bounded wait as the bulk-copy sweep, on an
@@ -300,19 +327,31 @@ void launch_wait_selftest(cudaStream_t s) {
   count_launch();
 }
 
-template <typename S, int TY, int RING>
+template <typename S, int TY, int RING, bool FU>
 static void strip2_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                           const int* done, cudaStream_t s) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gs_strip2_ring<S, TY, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_gs_strip2_ring<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
     attr = true;
   }
   const int warps = ((v.n + 47) / 48) * ((v.n + TY - 1) / TY);
-  k_gs_strip2_ring<S, TY, RING><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+  k_gs_strip2_ring<S, TY, RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
       v, f, xin, xout, done);
   count_launch();
+}
+
+template <typename S, bool FU>
+static void gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
+                    const int* done, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip2_launch<S, 16, 4, FU>(v, f, xin, xout, done, s); break;
+    case 2: strip2_launch<S, 32, 6, FU>(v, f, xin, xout, done, s); break;
+    case 3: strip2_launch<S, 26, 4, FU>(v, f, xin, xout, done, s); break;
+    default: strip2_launch<S, 32, 4, FU>(v, f, xin, xout, done, s); break;
+  }
 }
 
 template <typename S>
@@ -321,12 +360,10 @@ bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float*
   if (!(aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) && aligned16(v.SW) &&
         aligned16(v.NW)))
     return false;
-  switch (shape) {
-    case 1: strip2_launch<S, 16, 4>(v, f, xin, xout, done, s); break;
-    case 2: strip2_launch<S, 32, 6>(v, f, xin, xout, done, s); break;
-    case 3: strip2_launch<S, 26, 4>(v, f, xin, xout, done, s); break;
-    default: strip2_launch<S, 32, 4>(v, f, xin, xout, done, s); break;
-  }
+  if (v.fused)
+    gs_pair<S, true>(v, f, xin, xout, shape, done, s);
+  else
+    gs_pair<S, false>(v, f, xin, xout, shape, done, s);
   return true;
 }
 template bool launch_gs_pair<float>(const StencilView<float, float>&, const float*, const float*, float*, int,
@@ -365,14 +402,18 @@ template void launch_line<float, __nv_bfloat16>(const StencilView<float, __nv_bf
                                                 float*, int, const int*, cudaStream_t);
 
 template <typename T>
-void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s) {
-  launch_interp_to<T>(n, ci, ec, x, x, done, s);
+void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s, int fused) {
+  launch_interp_to<T>(n, ci, ec, x, x, done, s, fused);
 }
 
 template <typename T>
-void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s) {
+void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s,
+                      int fused) {
   int nc = (n - 1) / 2;
-  k_interp_correct<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
+  if (fused)
+    k_interp_correct<T, true><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
+  else
+    k_interp_correct<T, false><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
   count_launch();
 }
 
@@ -380,10 +421,14 @@ template <typename T, typename S>
 int launch_residual(const StencilView<T, S>& v, int kind, const T* x, const T* f, T* r, double* partials,
                     const int* done, cudaStream_t s) {
   int g = norm_blocks(v.n);
-  if (kind == 9)
-    k_residual<T, S, true><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+  if (kind == 9 && v.fused)
+    k_residual<T, S, true, true><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+  else if (kind == 9)
+    k_residual<T, S, true, false><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+  else if (v.fused)
+    k_residual<T, S, false, true><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
   else
-    k_residual<T, S, false><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+    k_residual<T, S, false, false><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
   count_launch();
   return g;
 }
@@ -407,7 +452,10 @@ void launch_ir_update(int n, double* x, const float* e32, void* ctl, cudaStream_
 int launch_ir_residual(const StencilView<double, double>& v, int kind, const double* x, const double* f, float* r32,
                        float* e32_zero, double* partials, void* ctl, cudaStream_t s) {
   int g = norm_blocks(v.n);
-  k_ir_residual<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
+  if (v.fused)
+    k_ir_residual<true><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
+  else
+    k_ir_residual<false><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
   count_launch();
   return g;
 }
@@ -452,16 +500,17 @@ BMG_INST(double, double)
 BMG_INST(float, float)
 BMG_INST(float, __nv_bfloat16)
 #undef BMG_INST
-template void launch_interp_correct<double>(int, const double*, const double*, double*, const int*, cudaStream_t);
-template void launch_interp_correct<float>(int, const float*, const float*, float*, const int*, cudaStream_t);
+template void launch_interp_correct<double>(int, const double*, const double*, double*, const int*, cudaStream_t,
+                                            int);
+template void launch_interp_correct<float>(int, const float*, const float*, float*, const int*, cudaStream_t, int);
 template void launch_gs_tile<float>(const StencilView<float, float>&, const float*, const float*, float*, int,
                                     const int*, cudaStream_t);
 template void launch_gs_tile<__nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, const float*, const float*,
                                             float*, int, const int*, cudaStream_t);
 template void launch_interp_to<double>(int, const double*, const double*, const double*, double*, const int*,
-                                       cudaStream_t);
+                                       cudaStream_t, int);
 template void launch_interp_to<float>(int, const float*, const float*, const float*, float*, const int*,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 template void launch_coarse_solve<double>(int, const double*, const double*, double*, double*, const int*,
                                           cudaStream_t);
 template void launch_coarse_solve<float>(int, const double*, const float*, float*, double*, const int*,
@@ -486,22 +535,24 @@ __device__ __forceinline__ double zval(const double* z, const float* z32, double
   return z32 ? rmul(s, (double)z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
 }
 
-// p.q over the grid with the canonical order; f(p) gives the product term.
+// An inner product over the grid in the canonical order; step(acc, p) adds
+// point p's product to the running sum.
 template <class F>
-__device__ __forceinline__ void ordered_partial(int n, int ld, double* partials, F term) {
+__device__ __forceinline__ void ordered_partial(int n, int ld, double* partials, F step) {
   double acc = 0.0;
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
-    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) acc = __dadd_rn(acc, term((size_t)j * ld + i));
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) acc = step(acc, (size_t)j * ld + i);
   double tot = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __restrict__ z,
                                                          const float* __restrict__ z32, const double* __restrict__ q,
                                                          double* __restrict__ partials, const Ctl* ctl) {
   if (ctl->done) return;
   const double s = ctl->scale_applied;
-  ordered_partial(n, n + 2, partials, [&](size_t p) { return rmul(zval(z, z32, s, p), q[p]); });
+  ordered_partial(n, n + 2, partials, [&](double acc, size_t p) { return madd<FU>(acc, zval(z, z32, s, p), q[p]); });
 }
 
 __device__ __forceinline__ double reduce_partials(const double* partials, int np) {
@@ -528,6 +579,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __res
   }
 }
 
+template <bool FU>
 __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float* __restrict__ z32,
                                 double* __restrict__ pv, const Ctl* ctl) {
   if (ctl->done) return;
@@ -540,11 +592,12 @@ __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float
     pv[p] = zp;
   } else {
     double beta = -rdiv(ctl->zq, ctl->pq_prev);
-    pv[p] = radd(zp, rmul(beta, pv[p]));
+    pv[p] = madd<FU>(zp, beta, pv[p]);
   }
 }
 
 // q = A p (row sum a_O p + a_W p_W + ... in canonical order), partial p.q and p.r
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double, double> v, int nine,
                                                              const double* __restrict__ pv, const double* __restrict__ r,
                                                              double* __restrict__ q, double* __restrict__ partials,
@@ -556,19 +609,19 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double,
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
       double acc = rmul(v.O[p], pv[p]);
-      acc = radd(acc, rmul(v.W[p], pv[p - 1]));
-      acc = radd(acc, rmul(v.W[p + 1], pv[p + 1]));
-      acc = radd(acc, rmul(v.S_[p], pv[p - ld]));
-      acc = radd(acc, rmul(v.S_[p + ld], pv[p + ld]));
+      acc = madd<FU>(acc, v.W[p], pv[p - 1]);
+      acc = madd<FU>(acc, v.W[p + 1], pv[p + 1]);
+      acc = madd<FU>(acc, v.S_[p], pv[p - ld]);
+      acc = madd<FU>(acc, v.S_[p + ld], pv[p + ld]);
       if (nine) {
-        acc = radd(acc, rmul(v.SW[p], pv[p - ld - 1]));
-        acc = radd(acc, rmul(v.SW[p + ld + 1], pv[p + ld + 1]));
-        acc = radd(acc, rmul(v.NW[p], pv[p + ld - 1]));
-        acc = radd(acc, rmul(v.NW[p + 1 - ld], pv[p + 1 - ld]));
+        acc = madd<FU>(acc, v.SW[p], pv[p - ld - 1]);
+        acc = madd<FU>(acc, v.SW[p + ld + 1], pv[p + ld + 1]);
+        acc = madd<FU>(acc, v.NW[p], pv[p + ld - 1]);
+        acc = madd<FU>(acc, v.NW[p + 1 - ld], pv[p + 1 - ld]);
       }
       q[p] = acc;
-      apq = __dadd_rn(apq, rmul(pv[p], acc));
-      apr = __dadd_rn(apr, rmul(pv[p], r[p]));
+      apq = madd<FU>(apq, pv[p], acc);
+      apr = madd<FU>(apr, pv[p], r[p]);
     }
   double t1 = block_sum(apq);
   __syncthreads();
@@ -581,6 +634,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double,
 
 // x += alpha p, r -= alpha q, partial r.r; zero the preconditioner output and,
 // in mixed precision, write r32 = fl32(r / scale_next).
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __restrict__ x, double* __restrict__ r,
                                                              const double* __restrict__ pv,
                                                              const double* __restrict__ q, float* __restrict__ r32,
@@ -595,8 +649,8 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
-      x[p] = radd(x[p], rmul(alpha, pv[p]));
-      double rr = rsub(r[p], rmul(alpha, q[p]));
+      x[p] = madd<FU>(x[p], alpha, pv[p]);
+      double rr = msub<FU>(r[p], alpha, q[p]);
       r[p] = rr;
       if (r32) {
         r32[p] = __double2float_rn(rmul(rr, inv));
@@ -604,7 +658,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
       } else {
         z[p] = 0.0;
       }
-      acc = __dadd_rn(acc, rmul(rr, rr));
+      acc = madd<FU>(acc, rr, rr);
     }
   double tot = block_sum(acc);
   if (threadIdx.x == 0) {
@@ -618,6 +672,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
 }
 
 // r = f - A x, stored; r32 / zero z as in k_fcg_update; partial r.r.
+template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, double> v, int nine,
                                                            const double* __restrict__ x, const double* __restrict__ f,
                                                            double* __restrict__ r, double* __restrict__ z,
@@ -630,8 +685,8 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
-      double rr = nine ? row_residual<double, double, true, true>(v, x, p, f[p])
-                       : row_residual<double, double, false, true>(v, x, p, f[p]);
+      double rr = nine ? row_residual<double, double, true, true, FU>(v, x, p, f[p])
+                       : row_residual<double, double, false, true, FU>(v, x, p, f[p]);
       r[p] = rr;
       if (r32) {
         r32[p] = __double2float_rn(rmul(rr, inv));
@@ -639,7 +694,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
       } else {
         z[p] = 0.0;
       }
-      acc = __dadd_rn(acc, rmul(rr, rr));
+      acc = madd<FU>(acc, rr, rr);
     }
   double tot = block_sum(acc);
   if (threadIdx.x == 0) {
@@ -656,7 +711,10 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
 int launch_fcg_init(const StencilView<double, double>& v, int kind, const double* x, const double* f, double* r,
                     double* z, float* r32, float* z32, double* partials, void* ctl, cudaStream_t s) {
   int g = norm_blocks(v.n);
-  k_fcg_init<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
+  if (v.fused)
+    k_fcg_init<true><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
+  else
+    k_fcg_init<false><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
   count_launch();
   return g;
 }
@@ -664,28 +722,38 @@ int launch_fcg_init(const StencilView<double, double>& v, int kind, const double
 // One FCG step after the preconditioner: z.q, beta and p, q = A p with p.q and
 // p.r, then the x / r update with r.r partials (finalised by the caller).
 // `mark(arg, k)` (may be NULL) brackets the sub-steps for profiling.
-void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
+template <bool FU>
+static void fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
                      const float* z32, double* pv, double* q, float* r32, float* z32_zero, double* z_zero,
                      double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg) {
   const int n = v.n;
   int g = norm_blocks(n);
   Ctl* c = (Ctl*)ctl;
   if (mark) mark(mark_arg, 0);
-  k_fcg_zq<<<g, NORM_THREADS, 0, s>>>(n, z, z32, q, partials, c);
+  k_fcg_zq<FU><<<g, NORM_THREADS, 0, s>>>(n, z, z32, q, partials, c);
   count_launch();
   k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 0);
   count_launch();
-  k_fcg_direction<<<dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s>>>(n, z, z32, pv, c);
+  k_fcg_direction<FU><<<dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s>>>(n, z, z32, pv, c);
   count_launch();
   if (mark) mark(mark_arg, 1);
-  k_fcg_matvec<<<g, NORM_THREADS, 0, s>>>(v, kind == 9, pv, r, q, partials, c);
+  k_fcg_matvec<FU><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, pv, r, q, partials, c);
   count_launch();
   k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 1);
   count_launch();
   if (mark) mark(mark_arg, 2);
-  k_fcg_update<<<g, NORM_THREADS, 0, s>>>(n, x, r, pv, q, r32, z32_zero, z_zero, partials, c);
+  k_fcg_update<FU><<<g, NORM_THREADS, 0, s>>>(n, x, r, pv, q, r32, z32_zero, z_zero, partials, c);
   count_launch();
   if (mark) mark(mark_arg, 3);
+}
+
+void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
+                     const float* z32, double* pv, double* q, float* r32, float* z32_zero, double* z_zero,
+                     double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg) {
+  if (v.fused)
+    fcg_step<true>(v, kind, x, r, z, z32, pv, q, r32, z32_zero, z_zero, partials, ctl, s, mark, mark_arg);
+  else
+    fcg_step<false>(v, kind, x, r, z, z32, pv, q, r32, z32_zero, z_zero, partials, ctl, s, mark, mark_arg);
 }
 
 }  // namespace bmg

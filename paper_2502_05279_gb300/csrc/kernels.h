@@ -19,6 +19,7 @@ struct StencilView {
   const T* D;
   int n;
   int ld;
+  int fused = 0;   // 1: the cycle's multiply-adds are fused (BMG_ARITH_FUSED)
 };
 
 // ---- setup (k_setup.cu), FP64 ----
@@ -79,10 +80,11 @@ template <typename T, typename S>
 void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,
                            T* xc, const int* done, cudaStream_t s);
 template <typename T>
-void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s);
+void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s, int fused = 0);
 // xout = xin + P ec over every interior fine point (xin may equal xout).
 template <typename T>
-void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s);
+void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, const int* done, cudaStream_t s,
+                      int fused = 0);
 // r = f - A x (r may be NULL) with per-block partial sums of r^2 (partials may
 // be NULL); returns the number of partials written.
 template <typename T, typename S>
@@ -148,28 +150,34 @@ struct TopDesc {
   Ctl* ctl;
 };
 
+// fused (every batched launcher): 1 = the problems' hierarchies use BMG_ARITH_FUSED.
 template <typename T, typename S>
-void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s);
+void launch_gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweeps, int cl, cudaStream_t s,
+                 int fused = 0);
 template <typename T, typename S>
-void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir = 0);
+void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kind, cudaStream_t s, int dir = 0,
+                             int fused = 0);
 template <typename T, typename S>
-void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din = 0, int dout = 0);
+void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s, int din = 0, int dout = 0,
+                     int fused = 0);
 // Batched one-pass sweeps of 9-point FP32 levels (all `count` problems share
 // n): dir 0 reads x and writes x2, dir 1 the reverse (the residual +
 // restriction reads, and the interpolation reads / writes, the array its dir
 // flags name: 0 = x, 1 = x2).  Shapes as launch_gs_tile 0 .. 3 and
 // launch_gs_pair; arrays in the guarded, aligned layout.
 template <typename S>
-void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s);
+void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s,
+                      int fused = 0);
 template <typename S>
-void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s);
+void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s,
+                      int fused = 0);
 int strip_timeouts_b();
 template <typename T, typename S>
 void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s);
-void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
+void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused = 0);
 void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s);
 void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
-void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
+void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused = 0);
 void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s);
 template <typename T>
 int rows_cluster(int n);
@@ -183,7 +191,7 @@ struct TailDesc;
 // The level-fused tail of `count` problems (one CTA each); top_kind is the
 // stencil kind of each descriptor's first level.
 template <typename T>
-void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s);
+void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s, int fused = 0);
 template <typename T>
 constexpr int tail_max_n() { return sizeof(T) == 8 ? 15 : 63; }
 }  // namespace bmg
