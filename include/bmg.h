@@ -92,13 +92,14 @@ typedef struct {
                            BMG_KRYLOV_FCG: flexible CG with one cycle as preconditioner */
   const void* mlp;      /* bmg_mlp* for interp = BMG_INTERP_LEARNED, else NULL */
   void* stream;         /* cudaStream_t for setup and every later call on the hierarchy */
-  int smoother;         /* Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all choices
-                           compute the same bits): BMG_SMOOTHER_AUTO (0, default; the autotuner
-                           picks per level when use_graph = 1, else the row kernel),
-                           BMG_SMOOTHER_ROWS (row kernel, in place), BMG_SMOOTHER_TILE + s
-                           (one-pass kernel with shape s = 0 .. 5 on every level outside the
-                           level-fused tail and the coarsest), or BMG_SMOOTHER_PAIR + s
-                           (the same levels, pairs of sweeps as one two-sweep pass) */
+  int smoother;         /* Gauss-Seidel kernel of the cycle's 9-point levels (all choices compute
+                           the same bits): BMG_SMOOTHER_AUTO (0, default; the autotuner picks per
+                           level when use_graph = 1, else the row kernel), BMG_SMOOTHER_ROWS (row
+                           kernel, in place), BMG_SMOOTHER_TILE + s (one-pass kernel with shape s
+                           on every level outside the level-fused tail and the coarsest: FP32
+                           cycles s = 0 .. 5, FP64 cycles s = 0 .. 3), or BMG_SMOOTHER_PAIR + s
+                           (FP32 cycles only: the same levels, pairs of sweeps as one two-sweep
+                           pass); EINVAL for a choice the precision has no kernel for */
   int arith;            /* BMG_ARITH_ROUNDED (0, default): one rounding per operation, the oracle's
                            default arithmetic; BMG_ARITH_FUSED: every product that is added to or
                            subtracted from a running sum in the cycle (stencil row sums of the
@@ -180,10 +181,12 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
 /* Gauss-Seidel kernel the setup autotuner chose for level `level` of the cycle
  * the hierarchy runs (FP64 or FP32): the row kernel's cluster size (1, 2, 4,
  * 8), BMG_TILE_SWEEP + s when the one-pass tile kernel with tile shape s won
- * (FP32 levels only; warp strips of 56 x TY points: shapes 0 .. 3 stream rows
- * by bulk copies into 4 row slots, TY = 26, 8, 16, 32; shapes 4, 5
- * load rows into registers, TY = 32, 16), or 0 (default; not tuned).  Every
- * choice computes the same bits. */
+ * (warp strips of 56 x TY points; FP32 cycles: shapes 0 .. 3 stream rows by
+ * bulk copies into 4 row slots, TY = 26, 8, 16, 32, shapes 4, 5 load rows
+ * into registers, TY = 32, 16; FP64 cycles: rows copied per lane into RING
+ * slots, (TY, RING) = (W, 4), (16, 4), (W, 6), (8, 4), W the smallest even
+ * height whose strips fit into one wave of resident warps), or 0 (default;
+ * not tuned).  Every choice computes the same bits. */
 #define BMG_TILE_SWEEP 16
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 

@@ -83,6 +83,8 @@ struct Level {
   float* lcp32 = nullptr; // the same for the FP32 cycle
   float* x32b = nullptr;  // second iterate of a tile-swept level (sweeps alternate x32 <-> x32b)
   int fused = 0;          // 1: the cycle's multiply-adds on this level are fused (BMG_ARITH_FUSED)
+  int tile64 = -1;        // FP64 sweeps: -1 row kernel (in place), else shape of the FP64 one-pass kernel
+  double* x64b = nullptr; // second iterate of an FP64 level swept by the one-pass kernel
 };
 
 StencilView<double, double> view64(const Level& L) {
@@ -211,16 +213,27 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   }
   auto v = view64(L);
   Level& C = h->lv[l + 1];
+  // One-pass level: each sweep reads *cur and writes the other of x / x64b;
+  // the interpolation writes the array from which nu2 sweeps end in x.
+  double* cur = x;
   auto relax64 = [&](int sweeps) {
     if (h->smoother == BMG_SMOOTHER_LINE)
       step(h, l, BMG_K_RELAX, 0, [&] { launch_line<double, double>(v, L.kind, f, x, L.lcp, sweeps, done, s); });
+    else if (L.tile64 >= 0)
+      for (int k = 0; k < sweeps; ++k) {
+        double* nxt = cur == x ? L.x64b : x;
+        step(h, l, BMG_K_RELAX, 0, [&] { launch_gs_tile64(v, f, cur, nxt, L.tile64, done, s); });
+        cur = nxt;
+      }
     else
       step(h, l, BMG_K_RELAX, 0, [&] { launch_gs(v, L.kind, f, x, sweeps, done, s, L.cl64); });
   };
   relax64(h->nu1);
-  step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, x, f, C.f, C.x, done, s); });
+  step(h, l, BMG_K_RESID_RESTRICT, 0, [&] { launch_resid_restrict(v, L.kind, L.ci, cur, f, C.f, C.x, done, s); });
   vcycle64(h, l + 1, C.x, C.f, done);
-  step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_correct<double>(L.n, L.ci, C.x, x, done, s, L.fused); });
+  double* dst = L.tile64 >= 0 && (h->nu2 & 1) ? L.x64b : x;
+  step(h, l, BMG_K_INTERP, 0, [&] { launch_interp_to<double>(L.n, L.ci, C.x, cur, dst, done, s, L.fused); });
+  cur = dst;
   relax64(h->nu2);
 }
 
@@ -304,18 +317,25 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
     relax32(h, view32(L), l, h->nu2, &cur, done);
 }
 
-// Device milliseconds of fn(), after one untimed call.
+// Device milliseconds of fn(): the fastest of three timed calls after one
+// untimed call (one sample alone lets noise decide between close candidates).
 template <typename F>
 int time_call(cudaStream_t s, F&& fn, float* ms) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   fn();
-  cudaEventRecord(e0, s);
-  fn();
-  cudaEventRecord(e1, s);
-  cudaEventSynchronize(e1);
-  cudaEventElapsedTime(ms, e0, e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    float t = 0;
+    cudaEventRecord(e0, s);
+    fn();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&t, e0, e1);
+    best = t < best ? t : best;
+  }
+  *ms = best;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
@@ -462,6 +482,57 @@ int tune_level32(Level& L, const StencilView<float, S>& v, cudaStream_t s) {
   return BMG_OK;
 }
 
+// FP64 one-pass kernel: each shape timed over two sweeps on scratch iterates.
+int tune_tile64(const StencilView<double, double>& v, cudaStream_t s, int* best_out, float* ms_out) {
+  static std::map<std::pair<int, int>, std::pair<int, float>> cache;
+  auto key = std::make_pair(v.n, v.fused);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *best_out = it->second.first;
+    *ms_out = it->second.second;
+    return BMG_OK;
+  }
+  const size_t ps = plane_size(v.n);
+  double* scratch = nullptr;   // x, x', f
+  CK(cudaMalloc((void**)&scratch, 3 * ps * sizeof(double)));
+  CK(cudaMemsetAsync(scratch, 0, 3 * ps * sizeof(double), s));
+  const double* f = scratch + 2 * ps;
+  int best_shape = 0, rc = BMG_OK;
+  float best = 1e30f;
+  for (int shape = 0; shape < GS_TILE64_SHAPES && !rc; ++shape) {
+    float ms = 0;
+    rc = time_call(s, [&] {
+      launch_gs_tile64(v, f, scratch, scratch + ps, shape, (const int*)nullptr, s);
+      launch_gs_tile64(v, f, scratch + ps, scratch, shape, (const int*)nullptr, s);
+    }, &ms);
+    if (ms * 0.5f < best) {
+      best = ms * 0.5f;
+      best_shape = shape;
+    }
+  }
+  cudaFree(scratch);
+  if (rc) return rc;
+  cache[key] = {best_shape, best};
+  *best_out = best_shape;
+  *ms_out = best;
+  return BMG_OK;
+}
+
+// Row kernel vs the one-pass kernel for an FP64 level (the second iterate is
+// allocated when the one-pass kernel wins).
+int tune_level64(Level& L, cudaStream_t s) {
+  float ms_rows = 0, ms_tile = 0;
+  int shape = 0, rc = tune_rows(view64(L), s, &L.cl64, &ms_rows);
+  if (!rc) rc = tune_tile64(view64(L), s, &shape, &ms_tile);
+  if (rc) return rc;
+  if (ms_tile < ms_rows) {
+    if ((rc = dalloc(&L.x64b, plane_size(L.n)))) return rc;
+    CK(cudaMemsetAsync(L.x64b, 0, plane_size(L.n) * sizeof(double), s));
+    L.tile64 = shape;
+  }
+  return BMG_OK;
+}
+
 // Level-fused tail of the solo hierarchy: the first level l (>= 1 for FP64, and
 // not a BF16 level) with n <= tail_max_n and at least one level below it.
 template <typename T>
@@ -496,11 +567,19 @@ int build_tail(bmg_hierarchy* h, int lmin) {
 }
 
 // BMG_SMOOTHER_TILE + s: the tile kernel with shape s on every 9-point level
-// but the coarsest (levels that end up in the level-fused tail ignore it).
+// but the coarsest (levels that end up in the level-fused tail ignore it); on
+// an FP64 hierarchy the FP64 one-pass kernel with shape s (s < 4).
 int force_tile(bmg_hierarchy* h) {
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
     if (L.kind != 9) continue;
+    if (h->precision == BMG_FP64) {
+      int rc = dalloc(&L.x64b, plane_size(L.n));
+      if (rc) return rc;
+      CK(cudaMemsetAsync(L.x64b, 0, plane_size(L.n) * sizeof(double), h->ws));
+      L.tile64 = h->smoother - BMG_SMOOTHER_TILE;
+      continue;
+    }
     int rc = galloc(&L.x32b, L.n, 1, h->ws);
     if (rc) return rc;
     if (h->smoother >= BMG_SMOOTHER_PAIR) {
@@ -529,7 +608,9 @@ int autotune_solo(bmg_hierarchy* h) {
     if (L.kind != 9 || L.n < 127) continue;
     int rc = BMG_OK;
     if (h->precision == BMG_FP64)
-      rc = tune_rows(view64(L), h->ws, &L.cl64);
+      rc = h->smoother == BMG_SMOOTHER_AUTO ? tune_level64(L, h->ws)
+           : L.tile64 >= 0                ? BMG_OK
+                                          : tune_rows(view64(L), h->ws, &L.cl64);
     else if (h->smoother != BMG_SMOOTHER_AUTO)
       rc = L.tile32 >= 0 ? BMG_OK : L.bf16 ? tune_rows(viewbf(L), h->ws, &L.cl32) : tune_rows(view32(L), h->ws, &L.cl32);
     else if (L.bf16)
@@ -657,6 +738,7 @@ void free_level(Level& L, bool shared_ops = false) {
   gfree(L.x32);
   gfree(L.x32b);
   gfree(L.f32);
+  cudaFree(L.x64b);
   L = Level{};
 }
 
@@ -836,6 +918,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad smoother %d", h->smoother);
   }
+  if (h->precision == BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE + GS_TILE64_SHAPES &&
+      h->smoother != BMG_SMOOTHER_LINE) {
+    int sm = h->smoother;
+    delete h;
+    return set_error(BMG_EINVAL, "bmg_setup: smoother %d has no FP64 kernel (tile0 .. tile3 do)", sm);
+  }
   if (h->precision < BMG_FP64 || h->precision > BMG_BF16_IR || !is_level_size(h->coarsest) || h->coarsest > 15 ||
       h->nu1 < 0 || h->nu2 < 0 || h->interp < 0 || h->interp > 1 || (h->interp == BMG_INTERP_LEARNED && !h->mlp) ||
       h->krylov < 0 || h->krylov > 1 || h->arith < BMG_ARITH_ROUNDED || h->arith > BMG_ARITH_FUSED) {
@@ -851,7 +939,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc) rc = setup_impl(h, A, nx, o);
   const bool line = h->smoother == BMG_SMOOTHER_LINE;
   if (!rc && line) rc = alloc_line(h);
-  if (!rc && !line && h->precision != BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
+  if (!rc && !line && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
   if (!rc && !line && h->use_graph) rc = autotune_solo(h);
   if (!rc && !line && h->use_graph)   // the level-fused tail relaxes by points
     rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
@@ -891,6 +979,7 @@ int bmg_tuned_cluster(const bmg_hierarchy* h, int level) {
   if (!h || level < 0 || level >= h->nlev) return set_error(BMG_EINVAL, "bmg_tuned_cluster: bad level");
   const Level& L = h->lv[level];
   if (h->precision != BMG_FP64 && L.tile32 >= 0) return BMG_TILE_SWEEP + L.tile32;
+  if (h->precision == BMG_FP64 && L.tile64 >= 0) return BMG_TILE_SWEEP + L.tile64;
   return h->precision == BMG_FP64 ? L.cl64 : L.cl32;
 }
 

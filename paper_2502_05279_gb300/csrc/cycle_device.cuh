@@ -224,11 +224,13 @@ __device__ __forceinline__ void gs_checker_body(const StencilView<T, S>& v, cons
 // warp reads what another wrote in this launch.  Same-row neighbours come from
 // the adjacent lane by shuffle; the rows a - 2 .. a + 1 live in registers and
 // the rows a + 2, a + 3 are loaded while row a is computed.
-template <typename S>
-struct StripRow {           // one row of the strip: lane values at c = 2l (.a) and 2l + 1 (.b)
-  float xa, xb, fa, fb, da, db;
+template <typename T, typename S>
+struct StripRowT {          // one row of the strip: lane values at c = 2l (.a) and 2l + 1 (.b)
+  T xa, xb, fa, fb, da, db;
   S wa, wb, sa, sb, swa, swb, nwa, nwb;
 };
+template <typename S>
+using StripRow = StripRowT<float, S>;
 
 template <typename S>
 __device__ __forceinline__ void strip_load(const StencilView<float, S>& v, const float* __restrict__ f,
@@ -256,49 +258,51 @@ __device__ __forceinline__ void strip_load(const StencilView<float, S>& v, const
 
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
 // The two colours of row M (rows L below, U above): first the odd-i points
 // (lane value a), then the even-i points (lane value b), each in the order
 // W, E, S, N, SW, NE, NW, SE; oka / okb say whether this lane's points are
 // updated.
-template <typename S, bool FU = false>
-__device__ __forceinline__ void strip_row(const StripRow<S>& L, StripRow<S>& M, const StripRow<S>& U, bool oka,
-                                          bool okb) {
+template <typename T, typename S, bool FU = false>
+__device__ __forceinline__ void strip_row(const StripRowT<T, S>& L, StripRowT<T, S>& M, const StripRowT<T, S>& U,
+                                          bool oka, bool okb) {
   {   // odd-i point c = 2l: same-row neighbours c - 1 (lane l - 1's b) and c + 1 (own b)
-    const float xw = shfl_up1(M.xb), xsw = shfl_up1(L.xb), xnw = shfl_up1(U.xb);
-    float s = M.fa;
-    s = msub<FU>(s, cvt<float>(M.wa), xw);
-    s = msub<FU>(s, cvt<float>(M.wb), M.xb);
-    s = msub<FU>(s, cvt<float>(M.sa), L.xa);
-    s = msub<FU>(s, cvt<float>(U.sa), U.xa);
-    s = msub<FU>(s, cvt<float>(M.swa), xsw);
-    s = msub<FU>(s, cvt<float>(U.swb), U.xb);
-    s = msub<FU>(s, cvt<float>(M.nwa), xnw);
-    s = msub<FU>(s, cvt<float>(L.nwb), L.xb);
-    const float xn = rmul(s, M.da);
+    const T xw = shfl_up1(M.xb), xsw = shfl_up1(L.xb), xnw = shfl_up1(U.xb);
+    T s = M.fa;
+    s = msub<FU>(s, cvt<T>(M.wa), xw);
+    s = msub<FU>(s, cvt<T>(M.wb), M.xb);
+    s = msub<FU>(s, cvt<T>(M.sa), L.xa);
+    s = msub<FU>(s, cvt<T>(U.sa), U.xa);
+    s = msub<FU>(s, cvt<T>(M.swa), xsw);
+    s = msub<FU>(s, cvt<T>(U.swb), U.xb);
+    s = msub<FU>(s, cvt<T>(M.nwa), xnw);
+    s = msub<FU>(s, cvt<T>(L.nwb), L.xb);
+    const T xn = rmul(s, M.da);
     M.xa = oka ? xn : M.xa;
   }
   {   // even-i point c = 2l + 1: neighbours c - 1 (own a, new) and c + 1 (lane l + 1's a)
-    const float xe = shfl_dn1(M.xa), we = shfl_dn1(cvt<float>(M.wa));
-    const float xne = shfl_dn1(U.xa), swne = shfl_dn1(cvt<float>(U.swa));
-    const float xse = shfl_dn1(L.xa), nwse = shfl_dn1(cvt<float>(L.nwa));
-    float s = M.fb;
-    s = msub<FU>(s, cvt<float>(M.wb), M.xa);
+    const T xe = shfl_dn1(M.xa), we = shfl_dn1(cvt<T>(M.wa));
+    const T xne = shfl_dn1(U.xa), swne = shfl_dn1(cvt<T>(U.swa));
+    const T xse = shfl_dn1(L.xa), nwse = shfl_dn1(cvt<T>(L.nwa));
+    T s = M.fb;
+    s = msub<FU>(s, cvt<T>(M.wb), M.xa);
     s = msub<FU>(s, we, xe);
-    s = msub<FU>(s, cvt<float>(M.sb), L.xb);
-    s = msub<FU>(s, cvt<float>(U.sb), U.xb);
-    s = msub<FU>(s, cvt<float>(M.swb), L.xa);
+    s = msub<FU>(s, cvt<T>(M.sb), L.xb);
+    s = msub<FU>(s, cvt<T>(U.sb), U.xb);
+    s = msub<FU>(s, cvt<T>(M.swb), L.xa);
     s = msub<FU>(s, swne, xne);
-    s = msub<FU>(s, cvt<float>(M.nwb), U.xa);
+    s = msub<FU>(s, cvt<T>(M.nwb), U.xa);
     s = msub<FU>(s, nwse, xse);
-    const float xn = rmul(s, M.db);
+    const T xn = rmul(s, M.db);
     M.xb = okb ? xn : M.xb;
   }
 }
 
-template <typename S>
-__device__ __forceinline__ void strip_store(float* __restrict__ xout, int n, int ld, int ic, int j, bool own,
-                                            const StripRow<S>& R) {
+template <typename T, typename S>
+__device__ __forceinline__ void strip_store(T* __restrict__ xout, int n, int ld, int ic, int j, bool own,
+                                            const StripRowT<T, S>& R) {
   if (!own || j > n) return;
   const size_t p = (size_t)j * ld + ic;
   if (ic <= n) xout[p] = R.xa;
@@ -331,11 +335,11 @@ __device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, co
       strip_load(v, f, xin, ic, a + 3, p1);
     }
     if (a <= n) {
-      strip_row<S, FU>(r1, r2, r3, c1, c2);               // row a: c1, c2
+      strip_row<float, S, FU>(r1, r2, r3, c1, c2);               // row a: c1, c2
       if (a < j1) strip_store(xout, n, ld, ic, a, own, r2);
     }
     if (m >= 1 && a - 1 <= n) {
-      strip_row<S, FU>(r0, r1, r2, c3, c4);               // row a - 1: c3, c4
+      strip_row<float, S, FU>(r0, r1, r2, c3, c4);               // row a - 1: c3, c4
       strip_store(xout, n, ld, ic, a - 1, own, r1);
     }
     r0 = r2;
@@ -517,7 +521,7 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
   take(1, Q0);
   take(2, Q1);
   if (ok && j0 <= n) {
-    strip_row<S, FU>(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
+    strip_row<float, S, FU>(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
     strip_store(xout, n, ld, ic, j0, own, Q0);
   }
   // step m: old pair = rows a - 2, a - 1; new pair = rows a, a + 1 (band rows 2m + 1, 2m + 2)
@@ -527,11 +531,11 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
     take(2 * m + 2, E3);
     if (!ok) return;
     if (a <= n) {
-      strip_row<S, FU>(E1, E2, E3, c1, c2);              // row a: c1, c2
+      strip_row<float, S, FU>(E1, E2, E3, c1, c2);              // row a: c1, c2
       if (a < j1) strip_store(xout, n, ld, ic, a, own, E2);
     }
     if (a - 1 <= n) {
-      strip_row<S, FU>(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
+      strip_row<float, S, FU>(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
       strip_store(xout, n, ld, ic, a - 1, own, E1);
     }
   };
@@ -621,14 +625,14 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
       take(2 * m + 2, R5);
       if (!ok) break;
     }
-    if (a >= 1 && a <= n) strip_row<S, FU>(R3, R4, R5, p1, q1);                 // sweep 1, row a
-    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<S, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
+    if (a >= 1 && a <= n) strip_row<float, S, FU>(R3, R4, R5, p1, q1);                 // sweep 1, row a
+    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<float, S, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
     if (m >= 2 && b <= n) {                                               // sweep 2, row a - 2
-      strip_row<S, FU>(R1, R2, R3, p2, q2);
+      strip_row<float, S, FU>(R1, R2, R3, p2, q2);
       if (b < j1) strip_store(xout, n, ld, ic, b, own, R2);
     }
     if (m >= 3 && b - 1 <= n) {                                           // sweep 2, row a - 3
-      strip_row<S, FU>(R0, R1, R2, r2, t2);
+      strip_row<float, S, FU>(R0, R1, R2, r2, t2);
       strip_store(xout, n, ld, ic, b - 1, own, R1);
     }
     R0 = R2;
@@ -639,6 +643,126 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   if (!ok)                                        // drain the copies still in flight, bounded
     for (int q = taken; q < taken + RING && q < NR; ++q) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));
   return ok;
+}
+
+// ---- four-colour sweep in one pass (FP64): per-lane asynchronous row copies ----------------
+// The walk of gs_strip_ring_body (56 x TY strips, lane l holding the columns
+// c = 2l, 2l + 1 of a 64-column window, the same colour regions, rows and
+// stores) for FP64 levels.  Their arrays carry no guard band and no 16-byte
+// alignment (the caller's x and f; every other stencil plane, (n+2)^2 doubles
+// apart), so rows are not streamed by bulk copies: each lane copies its own two
+// columns of a row's seven arrays with 8-byte cp.async copies into its part of
+// the warp's ring slot (zero-filled outside [0, n+1]^2, where nothing is read),
+// one commit group per band row, and reads them back after cp.async.wait_group.
+// A lane reads only what it copied, so the ring needs no barrier.  The FP64
+// pipe, not memory, bounds this kernel: the ring keeps RING - 1 rows of copies
+// in flight behind the arithmetic.  The strip height ty is a launch argument
+// (even, >= 2), so that the launcher can cut a level into as many strips as
+// there are resident warps: a warp walks its strip serially, and a second,
+// partial wave of strips would leave most of the FP64 pipes idle.
+struct StripSrc64 {         // the 7 arrays the walk reads
+  const double *x, *f, *d, *w, *s, *sw, *nw;
+};
+constexpr unsigned STRIP64_SLOT = 7 * 64 * sizeof(double);   // one row of the 7 arrays, 64 columns
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool in) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(in ? 8 : 0)
+               : "memory");
+}
+
+// this lane's columns ic, ic + 1 of row j into its part of `slot`, as one commit group
+__device__ __forceinline__ void row64_issue(const StripSrc64& A, int n, int ld, int ic, int j, unsigned char* slot,
+                                            int lane) {
+  const bool rowin = j >= 0 && j <= n + 1;
+  const bool ina = rowin && ic >= 0 && ic <= n + 1, inb = rowin && ic + 1 >= 0 && ic + 1 <= n + 1;
+  const size_t pa = ina ? (size_t)j * ld + ic : 0, pb = inb ? (size_t)j * ld + ic + 1 : 0;
+  double* d = reinterpret_cast<double*>(slot) + 2 * lane;
+  const double* src[7] = {A.x, A.f, A.d, A.w, A.s, A.sw, A.nw};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    cp_async8(d + 64 * k, src[k] + pa, ina);
+    cp_async8(d + 64 * k + 1, src[k] + pb, inb);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void row64_read(const unsigned char* slot, int lane, StripRowT<double, double>& R) {
+  const double2* d = reinterpret_cast<const double2*>(slot) + lane;
+  double2 v = d[0];
+  R.xa = v.x, R.xb = v.y;
+  v = d[32];
+  R.fa = v.x, R.fb = v.y;
+  v = d[64];
+  R.da = v.x, R.db = v.y;
+  v = d[96];
+  R.wa = v.x, R.wb = v.y;
+  v = d[128];
+  R.sa = v.x, R.sb = v.y;
+  v = d[160];
+  R.swa = v.x, R.swb = v.y;
+  v = d[192];
+  R.nwa = v.x, R.nwb = v.y;
+}
+
+template <int RING, bool FU = false>
+__device__ __forceinline__ void gs_strip64_body(const StencilView<double, double>& v, const double* __restrict__ f,
+                                                const double* __restrict__ xin, double* __restrict__ xout, int sx,
+                                                int sy, int ty, unsigned char* ring) {
+  static_assert(RING >= 2, "ring size");
+  using Row = StripRowT<double, double>;
+  const int n = v.n, ld = v.ld;
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 56 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
+  const int icol = i0 - 4, ic = icol + 2 * lane;
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
+  const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
+  const bool own = lane >= 2 && lane <= 29;
+  const StripSrc64 A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
+  const int NR = ty + 3;                          // band rows q = 0 .. NR - 1, j = j0 - 1 + q
+  // every lane: request band row q (an empty group past the band keeps one group per row)
+  auto issue = [&](int q) {
+    if (q < NR)
+      row64_issue(A, n, ld, ic, j0 - 1 + q, ring + (q % RING) * STRIP64_SLOT, lane);
+    else
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+#pragma unroll
+  for (int q = 0; q < RING; ++q) issue(q);
+  // band row q into R: its group is the oldest of the RING outstanding ones
+  auto take = [&](int q, Row& R) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(RING - 1) : "memory");
+    row64_read(ring + (q % RING) * STRIP64_SLOT, lane, R);
+    issue(q + RING);
+  };
+  Row P0, P1, Q0, Q1;                             // two row pairs in alternating roles
+  take(0, P1);
+  take(1, Q0);
+  take(2, Q1);
+  if (j0 <= n) {
+    strip_row<double, double, FU>(P1, Q0, Q1, c1, c2);     // row j0: c1, c2
+    strip_store(xout, n, ld, ic, j0, own, Q0);
+  }
+  // step m: old pair = rows a - 2, a - 1; new pair = rows a, a + 1 (band rows 2m + 1, 2m + 2)
+  auto step = [&](int m, Row& E0, Row& E1, Row& E2, Row& E3) {
+    const int a = j0 + 2 * m;
+    take(2 * m + 1, E2);
+    take(2 * m + 2, E3);
+    if (a <= n) {
+      strip_row<double, double, FU>(E1, E2, E3, c1, c2);   // row a: c1, c2
+      if (a < j1) strip_store(xout, n, ld, ic, a, own, E2);
+    }
+    if (a - 1 <= n) {
+      strip_row<double, double, FU>(E0, E1, E2, c3, c4);   // row a - 1: c3, c4
+      strip_store(xout, n, ld, ic, a - 1, own, E1);
+    }
+  };
+#pragma unroll 1
+  for (int m = 1; m <= ty / 2; m += 2) {
+    step(m, Q0, Q1, P0, P1);
+    if (m + 1 <= ty / 2) step(m + 1, P0, P1, Q0, Q1);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // no copy outlives the warp
 }
 
 // ---- residual + restriction ------------------------------------------------------------

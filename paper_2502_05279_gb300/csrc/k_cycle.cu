@@ -83,6 +83,21 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView
     atomicExch(&g_strip_timeout, 1);
 }
 
+// FP64 one-pass sweep with strips of 56 x ty points: warp w of the CTA owns
+// ring slots [w RING, (w + 1) RING).
+template <int RING, bool FU>
+__global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip64(StencilView<double, double> v,
+                                                                 const double* __restrict__ f,
+                                                                 const double* __restrict__ xin,
+                                                                 double* __restrict__ xout, const int* done, int ty) {
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  if (stopped(done)) return;
+  const int nbx = (v.n + 55) / 56, nby = (v.n + ty - 1) / ty;
+  const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
+  if (g >= nbx * nby) return;                     // whole warps only
+  gs_strip64_body<RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ty, strip_smem + (size_t)w * RING * STRIP64_SLOT);
+}
+
 // Zebra x-lines: one thread per row of the parity (first row 1 or 2).
 template <typename T, typename S, bool NINE>
 __global__ void k_line_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, T* __restrict__ cp, int first,
@@ -311,6 +326,52 @@ void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float*
     gs_tile<S, true>(v, f, xin, xout, shape, done, s);
   else
     gs_tile<S, false>(v, f, xin, xout, shape, done, s);
+}
+
+// ty = 0: the smallest even height whose strips fit into one wave of the
+// kernel's resident warps (occupancy x SMs x warps per CTA).
+template <int RING, bool FU>
+static void strip64_launch(const StencilView<double, double>& v, const double* f, const double* xin, double* xout,
+                           const int* done, cudaStream_t s, int ty) {
+  constexpr size_t bytes = (size_t)STRIP_WARPS * RING * STRIP64_SLOT;
+  static int resident_warps = 0;
+  if (!resident_warps) {
+    cudaFuncSetAttribute(k_gs_strip64<RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip64<RING, FU>, 32 * STRIP_WARPS, bytes);
+    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
+  }
+  const int nbx = (v.n + 55) / 56;
+  if (ty <= 0) {
+    const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
+    const int half = (v.n + 2 * nby_max - 1) / (2 * nby_max);
+    ty = 2 * (half > 1 ? half : 1);
+  }
+  const int warps = nbx * ((v.n + ty - 1) / ty);
+  k_gs_strip64<RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(v, f, xin, xout,
+                                                                                                   done, ty);
+  count_launch();
+}
+
+template <bool FU>
+static void gs_tile64(const StencilView<double, double>& v, const double* f, const double* xin, double* xout,
+                      int shape, const int* done, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip64_launch<4, FU>(v, f, xin, xout, done, s, 16); break;
+    case 2: strip64_launch<6, FU>(v, f, xin, xout, done, s, 0); break;
+    case 3: strip64_launch<4, FU>(v, f, xin, xout, done, s, 8); break;
+    default: strip64_launch<4, FU>(v, f, xin, xout, done, s, 0); break;
+  }
+}
+
+void launch_gs_tile64(const StencilView<double, double>& v, const double* f, const double* xin, double* xout,
+                      int shape, const int* done, cudaStream_t s) {
+  if (v.fused)
+    gs_tile64<true>(v, f, xin, xout, shape, done, s);
+  else
+    gs_tile64<false>(v, f, xin, xout, shape, done, s);
 }
 
 // One warp waits, through the same bounded wait as the bulk-copy sweep, on an

@@ -76,6 +76,16 @@ constexpr int GS_PAIR_SHAPES = 4;
 template <typename S>
 bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s);
+// One four-colour Gauss-Seidel sweep of a 9-point FP64 level in one launch,
+// xin -> xout as launch_gs_tile (xout != xin, its ghost ring not written), for
+// the plain FP64 layout (no guard band or alignment needed): warp strips of
+// 56 x TY points, rows copied per lane into RING row slots; shapes 0 .. 3 =
+// (TY, RING) = (one wave, 4), (16, 4), (one wave, 6), (8, 4), where "one
+// wave" is the smallest even TY whose strips all fit into the resident warps.
+// Needs v.D.
+constexpr int GS_TILE64_SHAPES = 4;
+void launch_gs_tile64(const StencilView<double, double>& v, const double* f, const double* xin, double* xout,
+                      int shape, const int* done, cudaStream_t s);
 template <typename T, typename S>
 void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, const T* x, const T* f, T* fc,
                            T* xc, const int* done, cudaStream_t s);

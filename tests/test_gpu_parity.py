@@ -459,15 +459,56 @@ def test_tile_sweep_fcg_and_bf16_solve_match_oracle(bmg):
 
 def test_autotuner_picks_a_valid_kernel_per_level(bmg):
     kind, planes, f = problem("lognormal", 511)
-    for precision in ("fp32", "bf16"):
+    for precision in ("fp32", "bf16", "fp64"):
         h = bmg.Hierarchy(kind, dev(planes), precision=precision)
+        shapes = 4 if precision == "fp64" else 6
         for l in range(h.num_levels - 1):
             c = h.tuned_cluster(l)
-            assert c in (0, 1, 2, 4, 8) or bmg.TILE_SWEEP <= c < bmg.TILE_SWEEP + 6, (l, c)
+            assert c in (0, 1, 2, 4, 8) or bmg.TILE_SWEEP <= c < bmg.TILE_SWEEP + shapes, (l, c)
             assert h.tuned_pair(l) in (-1, 0, 1, 2, 3)
             assert h.tuned_pair(l) == -1 or c >= bmg.TILE_SWEEP
         assert h.tuned_cluster(0) != 0
         h.close()
+
+
+@pytest.mark.parametrize("shape", ["tile0", "tile1", "tile2", "tile3"])
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+@pytest.mark.parametrize("case,n", [("lognormal", 511), ("binary", 127), ("poisson", 63)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_fp64_one_pass_sweep_solve_bitwise(bmg, shape, arith, case, n, graph):
+    """The FP64 one-pass kernel forced on every 9-point level (strips of 56
+    columns over 511, 127 and 63 points: several strips, ragged right and top
+    edges, a grid narrower than one strip): iterates and histories equal the
+    oracle's, in both arithmetic modes."""
+    kind, planes, f = problem(case, n)
+    levels = bx.setup(kind, planes, arith=arith)
+    xw, hw = bx.solve(levels, f, tol=1e-10, maxit=200)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), smoother=shape, use_graph=graph, arith=arith)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(host(x), xw)
+    check_history(h.history(), hw)
+    h.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (3, 0), (0, 3), (2, 2), (1, 2)])
+def test_fp64_one_pass_any_sweep_counts_and_fcg(bmg, nu1, nu2):
+    kind, planes, f = problem("lognormal", 255)
+    levels = bx.setup(kind, planes)
+    xw, hw = bx.solve_fcg(levels, f, tol=1e-10, maxit=200, nu1=nu1, nu2=nu2)
+    h = bmg.Hierarchy(kind, dev(planes), smoother="tile1", nu1=nu1, nu2=nu2, krylov="fcg")
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(host(x), xw)
+    check_history(h.history(), hw)
+    h.close()
+
+
+def test_fp64_rejects_smoothers_without_an_fp64_kernel(bmg):
+    kind, planes, f = problem("binary", 63)
+    for sm in ("tile4", "tile5", "pair0", "pair3"):
+        with pytest.raises(bmg.BmgError):
+            bmg.Hierarchy(kind, dev(planes), smoother=sm)
 
 
 @pytest.mark.slow
