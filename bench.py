@@ -62,6 +62,7 @@ NCU_TRAFFIC = {
     ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48x26 bulk/4"): 136.2e6,
 }
 TILE_SHAPES = ("56x26 bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
+TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
 PAIR_SHAPES = ("48x32 bulk/4", "48x16 bulk/4", "48x32 bulk/6", "48x26 bulk/4")
 
 
@@ -439,6 +440,7 @@ def run_ours(args, rank, local_rank, world):
     barrier()
     ms_other = max_over_ranks(ho.time_cycles(rhs, xo, args.steps))
     prof_other = ho.profile(rhs, torch.zeros_like(rhs), 3)
+    tuned_other = [ho.tuned_cluster(l) for l in range(ho.num_levels)]
     ho.close()
 
     # end to end through the public API with host buffers (FP64 path, flexible CG to 1e-10)
@@ -477,14 +479,15 @@ def run_ours(args, rank, local_rank, world):
         cycles = 3
         return r, r["ms"] / r["launches"] * 1e-3, sweeps_per_cycle * cycles / r["launches"]
 
-    def roofline_fp64(arith, prof):
+    def roofline_fp64(arith, prof, tuned):
         r, per_launch_s, sweeps = per_launch("fp64", False, prof)
         instr = ALG_FP64_INSTR_PER_POINT[(kind, arith)] * N * sweeps
         achieved = instr / per_launch_s / 1e12
         peak = fp64_rate / 1e12
         share = r["ms"] / sum(q["ms"] for q in prof)
         byt = SWEEP_BYTES[("fp64", kind)] * N * sweeps
-        name = "k_gs_rows<double>" + (" fused" if arith == "fused" else "")
+        name = (f"k_gs_strip64 {TILE64_SHAPES[tuned[0] - 16]}" if tuned[0] >= 16 else "k_gs_rows<double>") + \
+            (" fused" if arith == "fused" else "")
         return {"bound": "alu", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
                 "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "T FP64 instr/s",
                 "frac": round(achieved / peak, 4),
@@ -533,7 +536,7 @@ def run_ours(args, rank, local_rank, world):
         "config": {"workload": args.workload, "description": spec["text"], "unknowns": N, "arith": args.arith,
                    "levels": v64["h"].num_levels, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set > L2 (FP64 level-0 stencil + vectors = %.0f MB)" % (N * 64 / 1e6)},
-        "roofline": roofline_fp64(args.arith, v64["prof"]),
+        "roofline": roofline_fp64(args.arith, v64["prof"], v64["tuned"]),
         "e2e": {"value": world * N * e2e_cycles / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(f.nbytes),
                 "note": "bmg_solve (FP64, flexible CG, one V(2,1) per iteration) to 1e-10 from a zero guess per "
@@ -547,7 +550,8 @@ def run_ours(args, rank, local_rank, world):
                         for p, v in variants.items() if p != "fp64"},
                      "fp64_" + other: {"value": world * N * args.steps / (ms_other * 1e-3),
                                        "ms_per_step": ms_other / args.steps,
-                                       "roofline": roofline_fp64(other, prof_other)}},
+                                       "roofline": roofline_fp64(other, prof_other, tuned_other),
+                                       "tuned_cluster_by_level": tuned_other}},
         "tuned_cluster_by_level": variants["fp64"]["tuned"],
     }
     # per-level, per-kernel device time of one cycle (the paper's Fig. 10 breakdown)
