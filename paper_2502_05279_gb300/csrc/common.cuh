@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/bmg.h"
 
 namespace bmg {
@@ -75,6 +77,37 @@ struct Planes {
 template <typename S>
 __host__ __device__ inline Planes<S> planes_at(const S* base, size_t ps) {
   return Planes<S>{base, base + ps, base + 2 * ps, base + 3 * ps, base + 4 * ps};
+}
+
+// ---- programmatic dependent launch ----
+// Every kernel of the cycle is launched with programmatic stream serialization
+// and opens with pdl_enter(): it waits for its predecessor to complete and its
+// writes to be visible before it touches global memory, then lets the next
+// kernel on the stream be scheduled once all of its own CTAs have got that
+// far.  The next kernel's CTAs thus take the SMs this one leaves while it
+// drains, instead of starting after it; waiting first keeps that overlap to one
+// kernel deep (a chain of kernels each triggering before its wait would fill
+// the SMs with waiting CTAs).  Launched without the attribute, both
+// instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 // Interpolation plane indices (Fig. 2 labels).

@@ -18,6 +18,7 @@ constexpr int BX = 32, BY = 8;
 template <typename T, typename S, int CL, bool FU>
 __global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
     k_gs_rows_b(const LevelDesc<T, S>* __restrict__ d, int pj) {
+  pdl_enter();
   const LevelDesc<T, S> q = d[blockIdx.y];
   if (stopped(q.done)) return;   // uniform over the cluster: its CTAs share blockIdx.y
   gs_rows_body<T, S, CL, FU>(q.v, q.f, q.x, pj, blockIdx.x);
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
 
 template <typename T, typename S, bool FU>
 __global__ void k_gs_checker_b(const LevelDesc<T, S>* __restrict__ d, int c) {
+  pdl_enter();
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
   gs_checker_body<T, S, FU>(q.v, q.f, q.x, c, blockIdx.x, blockIdx.y);
@@ -32,6 +34,7 @@ __global__ void k_gs_checker_b(const LevelDesc<T, S>* __restrict__ d, int c) {
 
 template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T, S>* __restrict__ d, int dir) {
+  pdl_enter();
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
   resid_restrict_body<T, S, NINE, FU>(q.v, q.ci, dir ? q.x2 : q.x, q.f, q.fc, q.xc, blockIdx.x, blockIdx.y);
@@ -39,6 +42,7 @@ __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict_b(const LevelDesc<T
 
 template <typename T, typename S, bool FU>
 __global__ void k_interp_b(const LevelDesc<T, S>* __restrict__ d, int din, int dout) {
+  pdl_enter();
   const LevelDesc<T, S> q = d[blockIdx.z];
   if (stopped(q.done)) return;
   interp_body<T, FU>(q.v.n, q.ci, q.xc, din ? q.x2 : q.x, dout ? q.x2 : q.x,
@@ -52,6 +56,7 @@ __device__ int g_strip_timeout_b = 0;
 template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const LevelDesc<float, S>* __restrict__ d,
                                                                         int count, int n, int dir) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   const int nbx = (n + 55) / 56, wpp = nbx * ((n + TY - 1) / TY);
   const int w = threadIdx.x >> 5;
@@ -73,6 +78,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const Le
 template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const LevelDesc<float, S>* __restrict__ d,
                                                                          int count, int n, int dir) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   const int nbx = (n + 47) / 48, wpp = nbx * ((n + TY - 1) / TY);
   const int w = threadIdx.x >> 5;
@@ -93,6 +99,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const L
 
 template <typename T, typename S>
 __global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
+  pdl_enter();
   const LevelDesc<T, S> q = d[blockIdx.x];
   if (stopped(q.done)) return;
   coarse_solve_body<T>(q.v.n, q.L, q.f, q.x, q.y);
@@ -103,6 +110,7 @@ __global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
 // problem keeps the reduction order of its solo solve.
 template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __restrict__ d) {
+  pdl_enter();
   const TopDesc q = d[blockIdx.y];
   const int G = norm_blocks(q.v.n);
   if (q.ctl->done || (int)blockIdx.x >= G) return;
@@ -113,11 +121,13 @@ __global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __re
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) k_finalize_b(const TopDesc* __restrict__ d, int phase) {
+  pdl_enter();
   const TopDesc q = d[blockIdx.x];
   finalize_body(q.partials, norm_blocks(q.v.n), q.ctl, phase, nullptr);
 }
 
 __global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
+  pdl_enter();
   const TopDesc q = d[blockIdx.z];
   if (q.ctl->done) return;
   ir_update_body(q.v.n, q.x, q.e32, q.ctl, blockIdx.x * blockDim.x + threadIdx.x + 1,
@@ -126,6 +136,7 @@ __global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
 
 template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* __restrict__ d) {
+  pdl_enter();
   const TopDesc q = d[blockIdx.y];
   const int G = norm_blocks(q.v.n);
   if (q.ctl->done || (int)blockIdx.x >= G) return;
@@ -134,6 +145,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* _
 
 template <typename T, bool FU>
 __global__ void __launch_bounds__(1024) k_tail(const TailDesc<T>* __restrict__ d, const int* done) {
+  pdl_enter();
   const TailDesc<T>& q = d[blockIdx.x];
   if (stopped(done) || stopped(q.done)) return;
   tail_body<T, FU>(q, q.top_kind);
@@ -141,6 +153,7 @@ __global__ void __launch_bounds__(1024) k_tail(const TailDesc<T>* __restrict__ d
 
 // 1 when every problem's control flag is set.
 __global__ void k_all_done(const char* __restrict__ ctls, size_t stride, int count, int* out) {
+  pdl_enter();
   __shared__ int any_running;
   if (threadIdx.x == 0) any_running = 0;
   __syncthreads();
@@ -158,13 +171,15 @@ void rows_b(const LevelDesc<T, S>* d, int count, int n, int threads, cudaStream_
     cfg.gridDim = dim3((unsigned)(rows * CL), (unsigned)count);
     cfg.blockDim = dim3((unsigned)threads);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = CL;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = CL > 1 ? 1 : 0;
+    cfg.numAttrs = CL > 1 ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k_gs_rows_b<T, S, CL, FU>, d, pj);
     count_launch();
   }
@@ -189,9 +204,9 @@ static void gs_b(const LevelDesc<T, S>* d, int count, int n, int kind, int sweep
   } else {
     dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY, count);
     for (int k = 0; k < sweeps; ++k) {
-      k_gs_checker_b<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(d, 0);
+      pdl_launch(k_gs_checker_b<T, S, FU>, g, dim3(BX, BY), 0, s, d, 0);
       count_launch();
-      k_gs_checker_b<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(d, 1);
+      pdl_launch(k_gs_checker_b<T, S, FU>, g, dim3(BX, BY), 0, s, d, 1);
       count_launch();
     }
   }
@@ -215,13 +230,13 @@ void launch_resid_restrict_b(const LevelDesc<T, S>* d, int count, int n, int kin
   dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC, count);
   const dim3 b(TXC, TYC);
   if (kind == 9 && fused)
-    k_resid_restrict_b<T, S, true, true><<<g, b, 0, s>>>(d, dir);
+    pdl_launch(k_resid_restrict_b<T, S, true, true>, g, b, 0, s, d, dir);
   else if (kind == 9)
-    k_resid_restrict_b<T, S, true, false><<<g, b, 0, s>>>(d, dir);
+    pdl_launch(k_resid_restrict_b<T, S, true, false>, g, b, 0, s, d, dir);
   else if (fused)
-    k_resid_restrict_b<T, S, false, true><<<g, b, 0, s>>>(d, dir);
+    pdl_launch(k_resid_restrict_b<T, S, false, true>, g, b, 0, s, d, dir);
   else
-    k_resid_restrict_b<T, S, false, false><<<g, b, 0, s>>>(d, dir);
+    pdl_launch(k_resid_restrict_b<T, S, false, false>, g, b, 0, s, d, dir);
   count_launch();
 }
 
@@ -231,9 +246,9 @@ void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s,
   int nc = (n - 1) / 2;
   const dim3 g((nc + 1 + BX - 1) / BX, (nc + 1 + BY - 1) / BY, count);
   if (fused)
-    k_interp_b<T, S, true><<<g, dim3(BX, BY), 0, s>>>(d, din, dout);
+    pdl_launch(k_interp_b<T, S, true>, g, dim3(BX, BY), 0, s, d, din, dout);
   else
-    k_interp_b<T, S, false><<<g, dim3(BX, BY), 0, s>>>(d, din, dout);
+    pdl_launch(k_interp_b<T, S, false>, g, dim3(BX, BY), 0, s, d, din, dout);
   count_launch();
 }
 
@@ -249,12 +264,12 @@ static void strip_b_launch(const LevelDesc<float, S>* d, int count, int n, int d
     if (!attr)
       cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes);
-    k_gs_strip2_ring_b<S, TY, RING, FU><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+    pdl_launch(k_gs_strip2_ring_b<S, TY, RING, FU>, blocks, 32 * STRIP_WARPS_B, bytes, s, d, count, n, dir);
   } else {
     if (!attr)
       cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes);
-    k_gs_strip_ring_b<S, TY, RING, FU><<<blocks, 32 * STRIP_WARPS_B, bytes, s>>>(d, count, n, dir);
+    pdl_launch(k_gs_strip_ring_b<S, TY, RING, FU>, blocks, 32 * STRIP_WARPS_B, bytes, s, d, count, n, dir);
   }
   attr = true;
   count_launch();
@@ -312,33 +327,33 @@ int strip_timeouts_b() {
 template <typename T, typename S>
 void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s) {
   if (count <= 0) return;
-  k_coarse_b<T, S><<<count, 32, 0, s>>>(d);
+  pdl_launch(k_coarse_b<T, S>, count, 32, 0, s, d);
   count_launch();
 }
 
 void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
   if (fused)
-    k_residual_b<true><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+    pdl_launch(k_residual_b<true>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
   else
-    k_residual_b<false><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+    pdl_launch(k_residual_b<false>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
   count_launch();
 }
 
 void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s) {
-  k_finalize_b<<<count, NORM_THREADS, 0, s>>>(d, phase);
+  pdl_launch(k_finalize_b, count, NORM_THREADS, 0, s, d, phase);
   count_launch();
 }
 
 void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
-  k_ir_update_b<<<dim3((maxn + BX - 1) / BX, (maxn + BY - 1) / BY, count), dim3(BX, BY), 0, s>>>(d);
+  pdl_launch(k_ir_update_b, dim3((maxn + BX - 1) / BX, (maxn + BY - 1) / BY, count), dim3(BX, BY), 0, s, d);
   count_launch();
 }
 
 void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
   if (fused)
-    k_ir_residual_b<true><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+    pdl_launch(k_ir_residual_b<true>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
   else
-    k_ir_residual_b<false><<<dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s>>>(d);
+    pdl_launch(k_ir_residual_b<false>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
   count_launch();
 }
 
@@ -347,16 +362,16 @@ void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_
   if (count <= 0) return;
   (void)top_kind;
   if (fused)
-    k_tail<T, true><<<count, 1024, 0, s>>>(d, done_any);
+    pdl_launch(k_tail<T, true>, count, 1024, 0, s, d, done_any);
   else
-    k_tail<T, false><<<count, 1024, 0, s>>>(d, done_any);
+    pdl_launch(k_tail<T, false>, count, 1024, 0, s, d, done_any);
   count_launch();
 }
 template void launch_tail<double>(const TailDesc<double>*, int, int, const int*, cudaStream_t, int);
 template void launch_tail<float>(const TailDesc<float>*, int, int, const int*, cudaStream_t, int);
 
 void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s) {
-  k_all_done<<<1, 256, 0, s>>>(ctls, stride, count, out);
+  pdl_launch(k_all_done, 1, 256, 0, s, ctls, stride, count, out);
   count_launch();
 }
 

@@ -21,12 +21,14 @@ constexpr int BX = 32, BY = 8;
 template <typename T, typename S, int CL, bool FU>
 __global__ void __launch_bounds__(rows_threads_max<T>(), sizeof(T) == 8 ? 2 : 1)
     k_gs_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, int pj, const int* done) {
+  pdl_enter();
   if (stopped(done)) return;   // uniform over the grid: every CTA of a cluster leaves together
   gs_rows_body<T, S, CL, FU>(v, f, x, pj, blockIdx.x);
 }
 
 template <typename T, typename S, bool FU>
 __global__ void k_gs_checker(StencilView<T, S> v, const T* __restrict__ f, T* x, int c, const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   gs_checker_body<T, S, FU>(v, f, x, c, blockIdx.x, blockIdx.y);
 }
@@ -38,6 +40,7 @@ template <typename S, int TY, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float, S> v, const float* __restrict__ f,
                                                                const float* __restrict__ xin,
                                                                float* __restrict__ xout, const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
   const int g = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<
                                                                     const float* __restrict__ f,
                                                                     const float* __restrict__ xin,
                                                                     float* __restrict__ xout, const int* done) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   if (stopped(done)) return;
   const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
@@ -71,6 +75,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView
                                                                      const float* __restrict__ f,
                                                                      const float* __restrict__ xin,
                                                                      float* __restrict__ xout, const int* done) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   if (stopped(done)) return;
   const int nbx = (v.n + 47) / 48, nby = (v.n + TY - 1) / TY;
@@ -90,6 +95,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip64(StencilView<dou
                                                                  const double* __restrict__ f,
                                                                  const double* __restrict__ xin,
                                                                  double* __restrict__ xout, const int* done, int ty) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   if (stopped(done)) return;
   const int nbx = (v.n + 55) / 56, nby = (v.n + ty - 1) / ty;
@@ -102,6 +108,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip64(StencilView<dou
 template <typename T, typename S, bool NINE>
 __global__ void k_line_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, T* __restrict__ cp, int first,
                             const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   const int j = first + 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (j > v.n) return;
@@ -113,6 +120,7 @@ __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v
                                                             const T* __restrict__ x, const T* __restrict__ f,
                                                             T* __restrict__ fc, T* __restrict__ xc,
                                                             const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   resid_restrict_body<T, S, NINE, FU>(v, ci, x, f, fc, xc, blockIdx.x, blockIdx.y);
 }
@@ -120,6 +128,7 @@ __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v
 template <typename T, bool FU>
 __global__ void k_interp_correct(int n, const T* __restrict__ ci, const T* __restrict__ ec, const T* xin, T* xout,
                                  const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   interp_body<T, FU>(n, ci, ec, xin, xout, blockIdx.x * blockDim.x + threadIdx.x + 1,
                  blockIdx.y * blockDim.y + threadIdx.y + 1);
@@ -129,6 +138,7 @@ template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_residual(StencilView<T, S> v, const T* __restrict__ x,
                                                            const T* __restrict__ f, T* __restrict__ r,
                                                            double* __restrict__ partials, const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   residual_body<T, S, NINE, FU>(v, x, f, r, partials, blockIdx.x, gridDim.x);
 }
@@ -145,18 +155,21 @@ __global__ void k_zero_ring(int n, double* r) {
 
 __global__ void __launch_bounds__(NORM_THREADS) k_norm_finalize(const double* __restrict__ partials, int np,
                                                                 Ctl* ctl, int phase, double* out) {
+  pdl_enter();
   finalize_body(partials, np, ctl, phase, out);
 }
 
 template <typename T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ L, const T* __restrict__ f, T* __restrict__ x,
                                double* __restrict__ y, const int* done) {
+  pdl_enter();
   if (stopped(done)) return;
   if (blockIdx.x != 0) return;
   coarse_solve_body<T>(n, L, f, x, y);
 }
 
 __global__ void k_ir_update(int n, double* __restrict__ x, const float* __restrict__ e32, const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   ir_update_body(n, x, e32, ctl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
@@ -167,6 +180,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual(StencilView<double
                                                               const double* __restrict__ f, float* __restrict__ r32,
                                                               float* __restrict__ e32, double* __restrict__ partials,
                                                               Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   ir_residual_body<FU>(v, nine != 0, x, f, r32, e32, partials, ctl, blockIdx.x, gridDim.x);
 }
@@ -198,13 +212,15 @@ void launch_rows_half(const StencilView<T, S>& v, const T* f, T* x, int pj, int 
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = CL;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = CL > 1 ? 1 : 0;
+  cfg.numAttrs = CL > 1 ? 2 : 1;
   cudaLaunchKernelEx(&cfg, k_gs_rows<T, S, CL, FU>, v, f, x, pj, done);
   count_launch();
 }
@@ -243,9 +259,9 @@ static void gs_sweeps(const StencilView<T, S>& v, int kind, const T* f, T* x, in
   } else {
     dim3 g(((n + 1) / 2 + BX - 1) / BX, (n + BY - 1) / BY);
     for (int k = 0; k < sweeps; ++k) {
-      k_gs_checker<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 0, done);
+      pdl_launch(k_gs_checker<T, S, FU>, g, dim3(BX, BY), 0, s, v, f, x, 0, done);
       count_launch();
-      k_gs_checker<T, S, FU><<<g, dim3(BX, BY), 0, s>>>(v, f, x, 1, done);
+      pdl_launch(k_gs_checker<T, S, FU>, g, dim3(BX, BY), 0, s, v, f, x, 1, done);
       count_launch();
     }
   }
@@ -267,13 +283,13 @@ void launch_resid_restrict(const StencilView<T, S>& v, int kind, const T* ci, co
   dim3 g((nc + TXC - 1) / TXC, (nc + TYC - 1) / TYC);
   const dim3 b(TXC, TYC);
   if (kind == 9 && v.fused)
-    k_resid_restrict<T, S, true, true><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+    pdl_launch(k_resid_restrict<T, S, true, true>, g, b, 0, s, v, ci, x, f, fc, xc, done);
   else if (kind == 9)
-    k_resid_restrict<T, S, true, false><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+    pdl_launch(k_resid_restrict<T, S, true, false>, g, b, 0, s, v, ci, x, f, fc, xc, done);
   else if (v.fused)
-    k_resid_restrict<T, S, false, true><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+    pdl_launch(k_resid_restrict<T, S, false, true>, g, b, 0, s, v, ci, x, f, fc, xc, done);
   else
-    k_resid_restrict<T, S, false, false><<<g, b, 0, s>>>(v, ci, x, f, fc, xc, done);
+    pdl_launch(k_resid_restrict<T, S, false, false>, g, b, 0, s, v, ci, x, f, fc, xc, done);
   count_launch();
 }
 
@@ -281,7 +297,8 @@ template <typename S, int TY, bool FU>
 static void strip_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                          const int* done, cudaStream_t s) {
   const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
-  k_gs_strip<S, TY, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, s>>>(v, f, xin, xout, done);
+  pdl_launch(k_gs_strip<S, TY, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, s, v, f, xin,
+             xout, done);
   count_launch();
 }
 
@@ -296,7 +313,7 @@ static void strip_ring_launch(const StencilView<float, S>& v, const float* f, co
     attr = true;
   }
   const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
-  k_gs_strip_ring<S, TY, RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+  pdl_launch(k_gs_strip_ring<S, TY, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
       v, f, xin, xout, done);
   count_launch();
 }
@@ -350,8 +367,8 @@ static void strip64_launch(const StencilView<double, double>& v, const double* f
     ty = 2 * (half > 1 ? half : 1);
   }
   const int warps = nbx * ((v.n + ty - 1) / ty);
-  k_gs_strip64<RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(v, f, xin, xout,
-                                                                                                   done, ty);
+  pdl_launch(k_gs_strip64<RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s, v, f,
+             xin, xout, done, ty);
   count_launch();
 }
 
@@ -399,7 +416,7 @@ static void strip2_launch(const StencilView<float, S>& v, const float* f, const 
     attr = true;
   }
   const int warps = ((v.n + 47) / 48) * ((v.n + TY - 1) / TY);
-  k_gs_strip2_ring<S, TY, RING, FU><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s>>>(
+  pdl_launch(k_gs_strip2_ring<S, TY, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
       v, f, xin, xout, done);
   count_launch();
 }
@@ -449,9 +466,9 @@ void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, 
       if (rows <= 0) continue;
       const unsigned g = (unsigned)((rows + TPB - 1) / TPB);
       if (kind == 9)
-        k_line_rows<T, S, true><<<g, TPB, 0, s>>>(v, f, x, cp, first, done);
+        pdl_launch(k_line_rows<T, S, true>, g, TPB, 0, s, v, f, x, cp, first, done);
       else
-        k_line_rows<T, S, false><<<g, TPB, 0, s>>>(v, f, x, cp, first, done);
+        pdl_launch(k_line_rows<T, S, false>, g, TPB, 0, s, v, f, x, cp, first, done);
       count_launch();
     }
 }
@@ -472,9 +489,9 @@ void launch_interp_to(int n, const T* ci, const T* ec, const T* xin, T* xout, co
                       int fused) {
   int nc = (n - 1) / 2;
   if (fused)
-    k_interp_correct<T, true><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
+    pdl_launch(k_interp_correct<T, true>, grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s, n, ci, ec, xin, xout, done);
   else
-    k_interp_correct<T, false><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(n, ci, ec, xin, xout, done);
+    pdl_launch(k_interp_correct<T, false>, grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s, n, ci, ec, xin, xout, done);
   count_launch();
 }
 
@@ -483,30 +500,30 @@ int launch_residual(const StencilView<T, S>& v, int kind, const T* x, const T* f
                     const int* done, cudaStream_t s) {
   int g = norm_blocks(v.n);
   if (kind == 9 && v.fused)
-    k_residual<T, S, true, true><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+    pdl_launch(k_residual<T, S, true, true>, g, NORM_THREADS, 0, s, v, x, f, r, partials, done);
   else if (kind == 9)
-    k_residual<T, S, true, false><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+    pdl_launch(k_residual<T, S, true, false>, g, NORM_THREADS, 0, s, v, x, f, r, partials, done);
   else if (v.fused)
-    k_residual<T, S, false, true><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+    pdl_launch(k_residual<T, S, false, true>, g, NORM_THREADS, 0, s, v, x, f, r, partials, done);
   else
-    k_residual<T, S, false, false><<<g, NORM_THREADS, 0, s>>>(v, x, f, r, partials, done);
+    pdl_launch(k_residual<T, S, false, false>, g, NORM_THREADS, 0, s, v, x, f, r, partials, done);
   count_launch();
   return g;
 }
 
 template <typename T>
 void launch_coarse_solve(int n, const double* L, const T* f, T* x, double* y, const int* done, cudaStream_t s) {
-  k_coarse_solve<T><<<1, 32, 0, s>>>(n, L, f, x, y, done);
+  pdl_launch(k_coarse_solve<T>, 1, 32, 0, s, n, L, f, x, y, done);
   count_launch();
 }
 
 void launch_norm_finalize(const double* partials, int np, void* ctl, int phase, double* out, cudaStream_t s) {
-  k_norm_finalize<<<1, NORM_THREADS, 0, s>>>(partials, np, (Ctl*)ctl, phase, out);
+  pdl_launch(k_norm_finalize, 1, NORM_THREADS, 0, s, partials, np, (Ctl*)ctl, phase, out);
   count_launch();
 }
 
 void launch_ir_update(int n, double* x, const float* e32, void* ctl, cudaStream_t s) {
-  k_ir_update<<<grid2(n, n), dim3(BX, BY), 0, s>>>(n, x, e32, (const Ctl*)ctl);
+  pdl_launch(k_ir_update, grid2(n, n), dim3(BX, BY), 0, s, n, x, e32, (const Ctl*)ctl);
   count_launch();
 }
 
@@ -514,9 +531,9 @@ int launch_ir_residual(const StencilView<double, double>& v, int kind, const dou
                        float* e32_zero, double* partials, void* ctl, cudaStream_t s) {
   int g = norm_blocks(v.n);
   if (v.fused)
-    k_ir_residual<true><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
+    pdl_launch(k_ir_residual<true>, g, NORM_THREADS, 0, s, v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
   else
-    k_ir_residual<false><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
+    pdl_launch(k_ir_residual<false>, g, NORM_THREADS, 0, s, v, kind == 9, x, f, r32, e32_zero, partials, (Ctl*)ctl);
   count_launch();
   return g;
 }
@@ -611,6 +628,7 @@ template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __restrict__ z,
                                                          const float* __restrict__ z32, const double* __restrict__ q,
                                                          double* __restrict__ partials, const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   const double s = ctl->scale_applied;
   ordered_partial(n, n + 2, partials, [&](double acc, size_t p) { return madd<FU>(acc, zval(z, z32, s, p), q[p]); });
@@ -625,6 +643,7 @@ __device__ __forceinline__ double reduce_partials(const double* partials, int np
 // slot 0: zq; slot 1: pq and pr (second partial array right after the first)
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __restrict__ partials, int np, Ctl* ctl,
                                                              int which) {
+  pdl_enter();
   if (ctl->done) return;
   if (which == 0) {
     double v = reduce_partials(partials, np);
@@ -643,6 +662,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __res
 template <bool FU>
 __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float* __restrict__ z32,
                                 double* __restrict__ pv, const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -663,6 +683,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double,
                                                              const double* __restrict__ pv, const double* __restrict__ r,
                                                              double* __restrict__ q, double* __restrict__ partials,
                                                              const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   const int n = v.n, ld = v.ld;
   double apq = 0.0, apr = 0.0;
@@ -701,6 +722,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
                                                              const double* __restrict__ q, float* __restrict__ r32,
                                                              float* __restrict__ z32, double* __restrict__ z,
                                                              double* __restrict__ partials, Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   const int ld = n + 2;
   const double alpha = rdiv(ctl->pr, ctl->pq);
@@ -739,6 +761,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
                                                            double* __restrict__ r, double* __restrict__ z,
                                                            float* __restrict__ r32, float* __restrict__ z32,
                                                            double* __restrict__ partials, Ctl* ctl) {
+  pdl_enter();
   const int n = v.n, ld = v.ld;
   const double s = ctl->scale_next;
   const double inv = 1.0 / s;
@@ -773,9 +796,9 @@ int launch_fcg_init(const StencilView<double, double>& v, int kind, const double
                     double* z, float* r32, float* z32, double* partials, void* ctl, cudaStream_t s) {
   int g = norm_blocks(v.n);
   if (v.fused)
-    k_fcg_init<true><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
+    pdl_launch(k_fcg_init<true>, g, NORM_THREADS, 0, s, v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
   else
-    k_fcg_init<false><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
+    pdl_launch(k_fcg_init<false>, g, NORM_THREADS, 0, s, v, kind == 9, x, f, r, z, r32, z32, partials, (Ctl*)ctl);
   count_launch();
   return g;
 }
@@ -791,19 +814,20 @@ static void fcg_step(const StencilView<double, double>& v, int kind, double* x, 
   int g = norm_blocks(n);
   Ctl* c = (Ctl*)ctl;
   if (mark) mark(mark_arg, 0);
-  k_fcg_zq<FU><<<g, NORM_THREADS, 0, s>>>(n, z, z32, q, partials, c);
+  pdl_launch(k_fcg_zq<FU>, g, NORM_THREADS, 0, s, n, z, z32, q, partials, c);
   count_launch();
-  k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 0);
+  pdl_launch(k_fcg_reduce, 1, NORM_THREADS, 0, s, partials, g, c, 0);
   count_launch();
-  k_fcg_direction<FU><<<dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s>>>(n, z, z32, pv, c);
+  pdl_launch(k_fcg_direction<FU>, dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s, n, z, z32,
+             pv, c);
   count_launch();
   if (mark) mark(mark_arg, 1);
-  k_fcg_matvec<FU><<<g, NORM_THREADS, 0, s>>>(v, kind == 9, pv, r, q, partials, c);
+  pdl_launch(k_fcg_matvec<FU>, g, NORM_THREADS, 0, s, v, kind == 9, pv, r, q, partials, c);
   count_launch();
-  k_fcg_reduce<<<1, NORM_THREADS, 0, s>>>(partials, g, c, 1);
+  pdl_launch(k_fcg_reduce, 1, NORM_THREADS, 0, s, partials, g, c, 1);
   count_launch();
   if (mark) mark(mark_arg, 2);
-  k_fcg_update<FU><<<g, NORM_THREADS, 0, s>>>(n, x, r, pv, q, r32, z32_zero, z_zero, partials, c);
+  pdl_launch(k_fcg_update<FU>, g, NORM_THREADS, 0, s, n, x, r, pv, q, r32, z32_zero, z_zero, partials, c);
   count_launch();
   if (mark) mark(mark_arg, 3);
 }
