@@ -95,20 +95,64 @@ def colour(pi: int, pj: int):
 
 def drop_ghost_couplings(planes: np.ndarray) -> np.ndarray:
     """Zero the ghost ring and every coupling from an interior point to a ghost
-    point (Dirichlet rows hold no such entries).  In place."""
-    n = size_of(planes)
+    point (Dirichlet rows hold no such entries).  In place; planes may be
+    rectangular, (ny+2) x (nx+2)."""
+    ny, nx = planes.shape[-2] - 2, planes.shape[-1] - 2
     for a in planes:
         a[0, :] = 0
-        a[n + 1, :] = 0
+        a[ny + 1, :] = 0
         a[:, 0] = 0
-        a[:, n + 1] = 0
+        a[:, nx + 1] = 0
     planes[1][:, 1] = 0     # W  of i = 1
     planes[2][1, :] = 0     # S  of j = 1
     planes[3][:, 1] = 0     # SW of i = 1
     planes[3][1, :] = 0     # SW of j = 1
     planes[4][:, 1] = 0     # NW of i = 1
-    planes[4][n, :] = 0     # NW of j = n
+    planes[4][ny, :] = 0    # NW of j = ny
     return planes
+
+
+# ---------------------------------------------------------------------------
+# General grid sizes: embedding into the next 2^m - 1 square
+# ---------------------------------------------------------------------------
+
+def embed_size(nx: int, ny: int) -> int:
+    """The smallest n = 2^m - 1 >= max(nx, ny, 3)."""
+    n = 3
+    while n < max(nx, ny):
+        n = 2 * n + 1
+    return n
+
+
+def embed(planes: np.ndarray, f: np.ndarray):
+    """A problem on an nx x ny interior grid of any size, as one on the n x n
+    grid, n = embed_size(nx, ny) (reading; the paper states only 2^m - 1
+    sizes).  The caller's points keep their indices (i, j) in [1, nx] x
+    [1, ny] and their equations, with the couplings across the caller's
+    Dirichlet boundary dropped; every other interior point of the n x n grid
+    gets the identity row (a_O = 1, no couplings, f = 0).  The extra unknowns
+    are decoupled from the caller's and are zero in the solution, so the
+    caller's unknowns solve the caller's system.  planes: (5, ny+2, nx+2);
+    f: (ny+2, nx+2).  Returns (planes_n, f_n), both on the (n+2)^2 grid."""
+    planes = drop_ghost_couplings(np.array(planes, dtype=np.float64))
+    ny, nx = planes.shape[-2] - 2, planes.shape[-1] - 2
+    n = embed_size(nx, ny)
+    pn = np.zeros((5, n + 2, n + 2))
+    pn[:, 1:ny + 1, 1:nx + 1] = planes[:, 1:ny + 1, 1:nx + 1]
+    pad = np.zeros((n + 2, n + 2), dtype=bool)
+    pad[1:n + 1, 1:n + 1] = True
+    pad[1:ny + 1, 1:nx + 1] = False
+    pn[0][pad] = 1.0
+    fn = np.zeros((n + 2, n + 2))
+    fn[1:ny + 1, 1:nx + 1] = np.asarray(f, dtype=np.float64)[1:ny + 1, 1:nx + 1]
+    return pn, fn
+
+
+def extract(x_n: np.ndarray, nx: int, ny: int) -> np.ndarray:
+    """The caller's (ny+2) x (nx+2) grid of an embedded solution (ghost ring 0)."""
+    x = np.zeros((ny + 2, nx + 2))
+    x[1:ny + 1, 1:nx + 1] = x_n[1:ny + 1, 1:nx + 1]
+    return x
 
 
 def level_sizes(n: int, coarsest: int = 3) -> list[int]:

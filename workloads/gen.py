@@ -70,29 +70,31 @@ def grid_zeros(n: int) -> np.ndarray:
     return np.zeros((n + 2, n + 2), dtype=np.float64)
 
 
-def rhs_uniform(n: int, seed: int) -> np.ndarray:
-    """Right-hand side: interior i.i.d. uniform[-1, 1), ghost ring zero."""
-    f = grid_zeros(n)
-    f[1:n + 1, 1:n + 1] = uniform_pm1(seed, n * n).reshape(n, n)
+def rhs_uniform(n: int, seed: int, ny: int | None = None) -> np.ndarray:
+    """Right-hand side: interior i.i.d. uniform[-1, 1), ghost ring zero; an
+    (n+2)^2 grid, or (ny+2) x (n+2) when ny is given."""
+    ny = n if ny is None else ny
+    f = np.zeros((ny + 2, n + 2), dtype=np.float64)
+    f[1:ny + 1, 1:n + 1] = uniform_pm1(seed, n * ny).reshape(ny, n)
     return f
 
 
 def zero_ghost_couplings(planes: np.ndarray) -> np.ndarray:
     """Zero the ghost ring of all planes and the couplings of interior points to
-    ghost points (in place; returns planes)."""
+    ghost points (in place; returns planes).  Planes are (ny+2, nx+2)."""
     O, W, S, SW, NW = planes
-    n = planes.shape[1] - 2
+    ny, nx = planes.shape[1] - 2, planes.shape[2] - 2
     for a in planes:
         a[0, :] = 0.0
-        a[n + 1, :] = 0.0
+        a[ny + 1, :] = 0.0
         a[:, 0] = 0.0
-        a[:, n + 1] = 0.0
+        a[:, nx + 1] = 0.0
     W[:, 1] = 0.0          # (1, j) -> (0, j)
     S[1, :] = 0.0          # (i, 1) -> (i, 0)
     SW[:, 1] = 0.0
     SW[1, :] = 0.0
     NW[:, 1] = 0.0
-    NW[n, :] = 0.0         # (i, n) -> (i-1, n+1)
+    NW[ny, :] = 0.0        # (i, ny) -> (i-1, ny+1)
     return planes
 
 
@@ -102,6 +104,15 @@ def poisson5(n: int) -> np.ndarray:
     planes[0, 1:n + 1, 1:n + 1] = 4.0
     planes[1, 1:n + 1, 1:n + 1] = -1.0
     planes[2, 1:n + 1, 1:n + 1] = -1.0
+    return zero_ghost_couplings(planes)
+
+
+def poisson5_rect(nx: int, ny: int) -> np.ndarray:
+    """5-point Laplacian (4, -1) on an nx x ny interior grid: planes (5, ny+2, nx+2)."""
+    planes = np.zeros((5, ny + 2, nx + 2), dtype=np.float64)
+    planes[0, 1:ny + 1, 1:nx + 1] = 4.0
+    planes[1, 1:ny + 1, 1:nx + 1] = -1.0
+    planes[2, 1:ny + 1, 1:nx + 1] = -1.0
     return zero_ghost_couplings(planes)
 
 
@@ -119,8 +130,8 @@ def fe9_from_cells(k: np.ndarray) -> np.ndarray:
     """9-point bilinear (Q1) finite-element stiffness stencil of -div(k grad u)
     on a uniform grid, with k constant on each cell.
 
-    k has shape (n+1, n+1), k[cj, ci] on the cell whose lower-left node is
-    (ci, cj).  The Q1 element matrix of a square cell, scaled by k, has 2k/3 on
+    k has shape (ny+1, nx+1) (square: (n+1, n+1)), k[cj, ci] on the cell whose
+    lower-left node is (ci, cj); the planes are (5, ny+2, nx+2).  The Q1 element matrix of a square cell, scaled by k, has 2k/3 on
     its diagonal, -k/6 between nodes sharing a cell edge and -k/3 between
     opposite corners.  Summing the cells around each node gives
       O(i,j)  = (2/3) (k[j-1,i-1] + k[j-1,i] + k[j,i-1] + k[j,i])
@@ -129,14 +140,13 @@ def fe9_from_cells(k: np.ndarray) -> np.ndarray:
       SW(i,j) = -k[j-1,i-1] / 3
       NW(i,j) = -k[j,i-1] / 3
     """
-    n = k.shape[0] - 1
-    assert k.shape == (n + 1, n + 1)
-    planes = np.zeros((5, n + 2, n + 2), dtype=np.float64)
-    kll = k[0:n, 0:n]          # cell (i-1, j-1) for interior node (i, j)
-    klr = k[0:n, 1:n + 1]      # cell (i,   j-1)
-    kul = k[1:n + 1, 0:n]      # cell (i-1, j)
-    kur = k[1:n + 1, 1:n + 1]  # cell (i,   j)
-    I = (slice(1, n + 1), slice(1, n + 1))
+    ny, nx = k.shape[0] - 1, k.shape[1] - 1
+    planes = np.zeros((5, ny + 2, nx + 2), dtype=np.float64)
+    kll = k[0:ny, 0:nx]              # cell (i-1, j-1) for interior node (i, j)
+    klr = k[0:ny, 1:nx + 1]          # cell (i,   j-1)
+    kul = k[1:ny + 1, 0:nx]          # cell (i-1, j)
+    kur = k[1:ny + 1, 1:nx + 1]      # cell (i,   j)
+    I = (slice(1, ny + 1), slice(1, nx + 1))
     planes[0][I] = (2.0 / 3.0) * (kll + klr + kul + kur)
     planes[1][I] = -(kll + kul) / 6.0
     planes[2][I] = -(kll + klr) / 6.0
@@ -223,6 +233,19 @@ def batched_problems(count: int = 256, seed: int = 5, std: float = 1.0, corr_len
         k = lognormal_cells(n, std, corr_len, 10000 + 2 * b)
         out.append((9, fe9_from_cells(k), rhs_uniform(n, 10001 + 2 * b)))
     return out
+
+
+def general_size_problem(nx: int, ny: int, kind: int = 9, std: float = 1.0, corr_len: float = 8.0,
+                         seed_k: int = 30, seed_f: int = 31):
+    """(kind, planes, f) on an nx x ny interior grid of any size: 9-point Q1 with
+    k = exp(g) (g the Gaussian field of the square of side max(nx, ny) + 1 cells,
+    cropped), or the 5-point Laplacian; RHS uniform[-1, 1)."""
+    if kind == 5:
+        planes = poisson5_rect(nx, ny)
+    else:
+        g = gaussian_field(max(nx, ny) + 1, std, corr_len, seed_k)
+        planes = fe9_from_cells(np.exp(g)[:ny + 1, :nx + 1].copy())
+    return kind, planes, rhs_uniform(nx, seed_f, ny)
 
 
 def high_contrast_problem(n: int = 4095, block: int = 8, lo: float = 1.0, hi: float = 1e6,
