@@ -20,6 +20,16 @@
  * Couplings from an interior point to a ghost point are not entries of A; the
  * library ignores (zeroes) them and the ghost ring of every plane.
  *
+ * General sizes.  bmg_setup also takes any nx x ny grid (1 <= nx, ny <= 65535):
+ * the caller's arrays are then (ny+2) x (nx+2), row-major with row length nx+2,
+ * and the hierarchy embeds the problem in the n x n level 0 with
+ * n = the smallest 2^m - 1 >= max(nx, ny, 3): the caller's points keep their
+ * (i, j) and equations, and every other interior point of level 0 gets the
+ * identity row a_O = 1 with no couplings (its unknown is zero in the solution).
+ * bmg_solve, bmg_time_cycles and bmg_profile take rhs and x in the caller's
+ * layout; every other call on the hierarchy speaks of its levels (level 0 of
+ * size n, bmg_level_size).  Batched solves take 2^m - 1 squares only.
+ *
  * Interpolation weights.  Eight planes of (n_c+2)^2 doubles in the order
  * LSW, LSE, LNW, LNE, LL, LR, LB, LA (the labels of Fig. 2), indexed by the
  * coarse cell (ic, jc) whose north-east corner is coarse point (ic, jc):
@@ -28,9 +38,11 @@
  *   fine (2ic-1, 2jc):   LL, LR = toward (ic-1,jc), (ic,jc);
  *   fine (2ic, 2jc-1):   LB, LA = toward (ic,jc-1), (ic,jc).
  *
- * Arithmetic.  The FP64 path rounds every multiply, add and subtract
- * separately (no fused multiply-add) and sums each row of A in the order
- * O, W, E, S, N, SW, NE, NW, SE, so its iterates are reproducible bit for bit.
+ * Arithmetic.  By default (BMG_ARITH_ROUNDED) the cycle rounds every multiply,
+ * add and subtract separately (no fused multiply-add) and sums each row of A
+ * in the order O, W, E, S, N, SW, NE, NW, SE, so its iterates are reproducible
+ * bit for bit; BMG_ARITH_FUSED (bmg_opts.arith) keeps the order and fuses
+ * each multiply-add.
  *
  * Pointers.  "device" = memory the calling process allocated on the current
  * CUDA device; "host" = ordinary host memory.  `stream` is a cudaStream_t
@@ -127,9 +139,11 @@ typedef struct {
  * stencil operations"): Dendy interpolation and the Galerkin operator
  * A_c = P^T A P level by level down to `coarsest`, then the Cholesky factor of
  * the coarsest operator (Fig. 1 "Cholesky").  The stencil is copied; the caller
- * may free it on return.  nx == ny == n = 2^m - 1 >= 3.  opts may be NULL.
- * Returns BMG_EINVAL (sizes, kind, options), BMG_ENOMEM, BMG_ECUDA or
- * BMG_ESINGULAR; *out is NULL on failure. */
+ * may free it on return.  nx x ny interior points: nx == ny == 2^m - 1 >= 3
+ * natively, any 1 <= nx, ny <= 65535 by embedding (see "General sizes"; not
+ * with learned interpolation).  Stencil planes are (ny+2) x (nx+2).  opts may
+ * be NULL.  Returns BMG_EINVAL (sizes, kind, options), BMG_ENOMEM, BMG_ECUDA
+ * or BMG_ESINGULAR; *out is NULL on failure. */
 int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* opts, bmg_hierarchy** out);
 
 /* Solve A x = rhs by V(nu1,nu2) cycles (Fig. 1) until ||r_k||/||r_0|| <= tol
@@ -140,8 +154,9 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* opts, bmg_hi
  * one fixed order (rows b, b+G, ... per block b < G = min(n,1024), columns
  * t, t+256, ... per thread t < 256, then halving trees), so histories repeat
  * bit for bit.
- * rhs: device, (n+2)^2, read only.  x: device, (n+2)^2, in: initial guess,
- * out: solution (its ghost ring is not written).  iters, relres: host, may be
+ * rhs: device, (ny+2) x (nx+2) (the grid given to bmg_setup), read only.
+ * x: device, same layout, in: initial guess, out: solution (its ghost ring is
+ * not written).  iters, relres: host, may be
  * NULL.  Under BMG_FP32_IR / BMG_BF16_IR one "cycle" is one FP64 refinement
  * step around `inner_cycles` FP32 V-cycles.  Returns BMG_OK, BMG_ENOTCONV,
  * BMG_ENAN, BMG_EINVAL or BMG_ECUDA. */

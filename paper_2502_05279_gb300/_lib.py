@@ -144,15 +144,16 @@ class Hierarchy:
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
                  use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto",
                  arith: str = "rounded"):
-        n = _n_of(coef)
-        self.n, self.kind, self.precision, self.arith = n, kind, precision, arith
+        nx, ny = coef.shape[-1] - 2, coef.shape[-2] - 2     # any size; 2^m - 1 squares natively
+        self.nx, self.ny, self.kind, self.precision, self.arith = nx, ny, kind, precision, arith
         st = Stencil(kind, _ptr(coef, name="coef"))
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
                  int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
                  _SMOOTHER[smoother], _ARITH[arith])
         h = ctypes.c_void_p()
-        _check(lib.bmg_setup(ctypes.byref(st), n, n, ctypes.byref(o), ctypes.byref(h)))
+        _check(lib.bmg_setup(ctypes.byref(st), nx, ny, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+        self.n = self.level_size(0)   # level 0: nx = ny = n, or the embedding square
 
     def solve(self, rhs: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-10, maxit: int = 100):
         """Returns (x, iterations, relative residual, converged)."""

@@ -144,6 +144,11 @@ struct bmg_hierarchy {
   // a batch member that borrows the operator arrays (stencils, weights, Cholesky
   // factor and its workspace) of another hierarchy and owns only its state
   bool shared_ops = false;
+  // general sizes: the caller's grid nx x ny, embedded in the n x n level 0; the
+  // solve runs on the embedded right-hand side and iterate (NULL when nx = ny = n)
+  int nx = 0, ny = 0;
+  double* fpad = nullptr;
+  double* xpad = nullptr;
 };
 
 namespace {
@@ -744,6 +749,13 @@ void free_level(Level& L, bool shared_ops = false) {
 
 bool is_level_size(int n) { return n >= 3 && ((n + 1) & n) == 0; }
 
+// The smallest n = 2^m - 1 >= max(nx, ny, 3): the level-0 size of an nx x ny problem.
+int embed_size(int nx, int ny) {
+  int n = 3;
+  while (n < nx || n < ny) n = 2 * n + 1;
+  return n;
+}
+
 int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o) {
   cudaStream_t s = h->ws;
   // level sizes
@@ -780,7 +792,13 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
   if ((rc = dalloc(&h->err, 1))) return rc;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
 
-  launch_prepare(n, A->kind, A->coef, h->lv[0].st, h->err, s);
+  launch_prepare(n, h->nx, h->ny, A->kind, A->coef, h->lv[0].st, h->err, s);
+  if (h->nx != n || h->ny != n) {   // embedded problem: the solve's own f and x on the n x n grid
+    if ((rc = dalloc(&h->fpad, plane_size(n)))) return rc;
+    if ((rc = dalloc(&h->xpad, plane_size(n)))) return rc;
+    CK(cudaMemsetAsync(h->fpad, 0, plane_size(n) * sizeof(double), s));
+    CK(cudaMemsetAsync(h->xpad, 0, plane_size(n) * sizeof(double), s));
+  }
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
     Level& C = h->lv[l + 1];
@@ -892,10 +910,15 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   *out = nullptr;
   if (!A || !A->coef) return set_error(BMG_EINVAL, "bmg_setup: stencil is NULL");
   if (A->kind != 5 && A->kind != 9) return set_error(BMG_EINVAL, "bmg_setup: kind %d is not 5 or 9", A->kind);
-  if (nx != ny) return set_error(BMG_EINVAL, "bmg_setup: nx %d != ny %d", nx, ny);
-  if (!is_level_size(nx)) return set_error(BMG_EINVAL, "bmg_setup: n = %d is not 2^m - 1 >= 3", nx);
+  if (nx < 1 || ny < 1 || nx > 65535 || ny > 65535)
+    return set_error(BMG_EINVAL, "bmg_setup: grid %d x %d outside 1 .. 65535", nx, ny);
+  const bool embedded = nx != ny || !is_level_size(nx);
+  if (embedded && o && o->interp == BMG_INTERP_LEARNED)
+    return set_error(BMG_EINVAL, "bmg_setup: learned interpolation needs nx = ny = 2^m - 1");
   bmg_hierarchy* h = new bmg_hierarchy();
-  h->n = nx;
+  h->nx = nx;
+  h->ny = ny;
+  h->n = embed_size(nx, ny);
   if (o) {
     h->precision = o->precision;
     h->coarsest = o->coarsest ? o->coarsest : 3;
@@ -930,13 +953,13 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad options");
   }
-  if (h->coarsest > nx) h->coarsest = nx;
+  if (h->coarsest > h->n) h->coarsest = h->n;
   CounterScope cs(&h->launches);
   int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
-  if (!rc) rc = setup_impl(h, A, nx, o);
+  if (!rc) rc = setup_impl(h, A, h->n, o);
   const bool line = h->smoother == BMG_SMOOTHER_LINE;
   if (!rc && line) rc = alloc_line(h);
   if (!rc && !line && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
@@ -996,6 +1019,22 @@ int bmg_interp_info(const bmg_hierarchy* h, int* used, double* fl, double* fd) {
   return BMG_OK;
 }
 
+// General sizes: the embedded problem's right-hand side and iterate for the
+// caller's rhs and x (nx x ny layout): their interiors copied into fpad / xpad.
+// Without embedding, the caller's arrays themselves.
+static void map_in(bmg_hierarchy* h, const double*& rhs, double*& x) {
+  if (!h->fpad) return;
+  launch_embed_vec(h->nx, h->ny, h->n, rhs, h->fpad, false, h->ws);
+  launch_embed_vec(h->nx, h->ny, h->n, x, h->xpad, false, h->ws);
+  rhs = h->fpad;
+  x = h->xpad;
+}
+
+// The caller's x from the embedded iterate.
+static void map_out(bmg_hierarchy* h, double* x_caller) {
+  if (h->fpad) launch_embed_vec(h->nx, h->ny, h->n, h->xpad, x_caller, true, h->ws);
+}
+
 static int reset_ctl(bmg_hierarchy* h, double tol, int maxit) {
   int rc;
   if ((rc = ensure_ctl(h, maxit))) return rc;
@@ -1015,6 +1054,8 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
   int rc;
   if ((rc = order_after_user(h))) return rc;
   if ((rc = reset_ctl(h, 0.0, cycles))) return rc;
+  double* x_caller = x;
+  map_in(h, rhs, x);
   enqueue_initial(h, rhs, x);
   if (h->use_graph && (rc = capture_graph(h, rhs, x))) return rc;
   cudaEvent_t a, b;
@@ -1030,11 +1071,13 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
     }
   }
   CK(cudaEventRecord(b, h->ws));
+  map_out(h, x_caller);
   CK(cudaEventSynchronize(b));
   float t = 0;
   CK(cudaEventElapsedTime(&t, a, b));
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  CK(cudaStreamSynchronize(h->ws));
   *ms = t;
   if ((rc = timeout_check("bmg_time_cycles"))) return rc;
   return cuda_check(cudaGetLastError(), "bmg_time_cycles");
@@ -1046,11 +1089,14 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
   int rc;
   if ((rc = order_after_user(h))) return rc;
   if ((rc = reset_ctl(h, 0.0, cycles))) return rc;
+  double* x_caller = x;
+  map_in(h, rhs, x);
   enqueue_initial(h, rhs, x);
   std::vector<bmg_hierarchy::Mark> marks;
   h->prof = &marks;
   for (int i = 0; i < cycles; ++i) enqueue_iteration(h, rhs, x);
   h->prof = nullptr;
+  map_out(h, x_caller);
   rc = cuda_check(cudaStreamSynchronize(h->ws), "bmg_profile");
   std::vector<bmg_prof_row> acc;
   for (auto& m : marks) {
@@ -1080,6 +1126,8 @@ int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int ma
   int rc;
   if ((rc = order_after_user(h))) return rc;
   if ((rc = reset_ctl(h, tol, maxit))) return rc;
+  double* x_caller = x;
+  map_in(h, rhs, x);
   enqueue_initial(h, rhs, x);
   CK(cudaGetLastError());
   if (h->use_graph && (rc = capture_graph(h, rhs, x))) return rc;
@@ -1101,6 +1149,8 @@ int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int ma
     CK(cudaGetLastError());
     launched += k;
   }
+  map_out(h, x_caller);
+  CK(cudaStreamSynchronize(h->ws));
   Ctl& c = *h->ctl_host;
   int it = c.it;
   h->hist.assign((size_t)it + 1, 0.0);
@@ -1158,6 +1208,8 @@ void bmg_free(bmg_hierarchy* h) {
   }
   cudaFree(h->partials);
   cudaFree(h->kr);
+  cudaFree(h->fpad);
+  cudaFree(h->xpad);
   cudaFree(h->d_tail);
   cudaFree(h->err);
   cudaFree(h->ctl);
@@ -1953,6 +2005,8 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
   if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_setup_batched: stationary cycles only");
   for (int p = 1; p < nprob; ++p)
     if (A[p].kind != A[0].kind) return set_error(BMG_EINVAL, "bmg_setup_batched: problems differ in kind");
+  for (int p = 0; p < nprob; ++p)
+    if (!is_level_size(n[p])) return set_error(BMG_EINVAL, "bmg_setup_batched: n = %d is not 2^m - 1 >= 3", n[p]);
   bmg_batch* B = new bmg_batch();
   B->nprob = nprob;
   bmg_opts so{};
@@ -1982,6 +2036,7 @@ int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch**
   *out = nullptr;
   if (!h0 || k < 1) return set_error(BMG_EINVAL, "bmg_batch_rhs: bad argument");
   if (h0->shared_ops) return set_error(BMG_EINVAL, "bmg_batch_rhs: h is itself a batch member");
+  if (h0->fpad) return set_error(BMG_EINVAL, "bmg_batch_rhs: h holds an embedded (general-size) problem");
   if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_batch_rhs: stationary cycles only");
   if (o && o->precision != h0->precision)
     return set_error(BMG_EINVAL, "bmg_batch_rhs: precision %d differs from the hierarchy's %d", o->precision,

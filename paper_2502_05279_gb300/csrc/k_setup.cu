@@ -14,23 +14,28 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
-// Copy a caller stencil (kind 5: O, W, S; kind 9: O, W, S, SW, NW) into the
-// six-plane level layout, dropping the ghost ring and ghost couplings.
-__global__ void k_prepare(int n, int kind, const double* __restrict__ in, double* __restrict__ st) {
+// Copy a caller stencil (kind 5: O, W, S; kind 9: O, W, S, SW, NW) on an
+// nx x ny grid ((ny+2) x (nx+2) planes) into the six-plane layout of the
+// n x n level 0, dropping the ghost ring and ghost couplings.  With nx, ny < n
+// the caller's points keep their (i, j) and every other interior point gets
+// the identity row O = 1 (general sizes: the embedding reading).
+__global__ void k_prepare(int n, int nx, int ny, int kind, const double* __restrict__ in, double* __restrict__ st) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int ld = n + 2;
   if (i > n + 1 || j > n + 1) return;
   size_t ps = plane_size(n), p = (size_t)j * ld + i;
-  bool interior = i >= 1 && i <= n && j >= 1 && j <= n;
-  double o = 0, w = 0, s = 0, sw = 0, nw = 0;
-  if (interior) {
-    o = in[p];
-    if (i > 1) w = in[ps + p];
-    if (j > 1) s = in[2 * ps + p];
+  const size_t psi = (size_t)(nx + 2) * (ny + 2), q = (size_t)j * (nx + 2) + i;
+  const bool caller = i >= 1 && i <= nx && j >= 1 && j <= ny;
+  const bool extra = !caller && i >= 1 && i <= n && j >= 1 && j <= n;
+  double o = extra ? 1.0 : 0.0, w = 0, s = 0, sw = 0, nw = 0;
+  if (caller) {
+    o = in[q];
+    if (i > 1) w = in[psi + q];
+    if (j > 1) s = in[2 * psi + q];
     if (kind == 9) {
-      if (i > 1 && j > 1) sw = in[3 * ps + p];
-      if (i > 1 && j < n) nw = in[4 * ps + p];
+      if (i > 1 && j > 1) sw = in[3 * psi + q];
+      if (i > 1 && j < ny) nw = in[4 * psi + q];
     }
   }
   st[p] = o;
@@ -305,8 +310,26 @@ dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY)
 
 }  // namespace
 
-void launch_prepare(int n, int kind, const double* coef_in, double* st, int* err, cudaStream_t s) {
-  k_prepare<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, kind, coef_in, st);
+// Interior of an nx x ny grid array into / out of the n x n layout (the other
+// points of the destination are left as they are).
+__global__ void k_embed_vec(int nx, int ny, int n, const double* __restrict__ in, double* __restrict__ out, int back) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > nx || j > ny) return;
+  const size_t pc = (size_t)j * (nx + 2) + i, pn = (size_t)j * (n + 2) + i;
+  if (back)
+    out[pc] = in[pn];
+  else
+    out[pn] = in[pc];
+}
+
+void launch_embed_vec(int nx, int ny, int n, const double* in, double* out, bool back, cudaStream_t s) {
+  k_embed_vec<<<grid2(nx, ny), dim3(BX, BY), 0, s>>>(nx, ny, n, in, out, back ? 1 : 0);
+  count_launch();
+}
+
+void launch_prepare(int n, int nx, int ny, int kind, const double* coef_in, double* st, int* err, cudaStream_t s) {
+  k_prepare<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, nx, ny, kind, coef_in, st);
   count_launch();
   k_dinv<<<grid2(n, n), dim3(BX, BY), 0, s>>>(n, st, err);
   count_launch();

@@ -25,7 +25,11 @@ struct StencilView {
 // ---- setup (k_setup.cu), FP64 ----
 // st: 6 planes O, W, S, SW, NW, D of (n+2)^2.  err: device int, set nonzero on
 // a zero or negative diagonal / denominator / pivot.
-void launch_prepare(int n, int kind, const double* coef_in, double* st, int* err, cudaStream_t s);
+// coef_in: the caller's planes on an nx x ny grid; st: level 0 of size n
+// (n = nx = ny, or the embedding size; see k_prepare).
+void launch_prepare(int n, int nx, int ny, int kind, const double* coef_in, double* st, int* err, cudaStream_t s);
+// Interior of an nx x ny array into the n x n layout (back = false) or out of it.
+void launch_embed_vec(int nx, int ny, int n, const double* in, double* out, bool back, cudaStream_t s);
 void launch_dendy(int n, const double* st, double* ci, int* err, cudaStream_t s);
 void launch_rap(int n, const double* st, const double* ci, double* stc, cudaStream_t s);
 void launch_dinv(int n, double* st, int* err, cudaStream_t s);

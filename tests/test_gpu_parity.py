@@ -198,8 +198,8 @@ def test_nan_rhs_reports_enan(bmg):
 
 def test_setup_rejects_bad_sizes_and_indefinite(bmg):
     planes = w.poisson5(63)
-    with pytest.raises(bmg.BmgError):
-        bmg.Hierarchy(5, dev(planes[:3, :64, :64].copy()))
+    with pytest.raises(bmg.BmgError):                     # a learned hierarchy needs a 2^m - 1 square
+        bmg.Hierarchy(5, dev(planes[:3, :64, :64].copy()), mlp=bmg.Mlp(np.zeros(bmg._lib.MLP_PARAMS, np.float32)))
     bad = planes.copy()
     bad[0] *= -1
     with pytest.raises(bmg.BmgError) as e:
