@@ -209,7 +209,7 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   cudaStream_t s = h->ws;
   if (l == h->tail_l) {
     step(h, l, BMG_K_TAIL, 0,
-         [&] { launch_tail<double>((const TailDesc<double>*)h->d_tail, 1, L.kind, done, s, L.fused); });
+         [&] { launch_tail<double>((const TailDesc<double>*)h->d_tail, 1, L.n, done, s, L.fused); });
     return;
   }
   if (l == h->nlev - 1) {
@@ -295,7 +295,7 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   cudaStream_t s = h->ws;
   if (l == h->tail_l) {
     step(h, l, BMG_K_TAIL, 1,
-         [&] { launch_tail<float>((const TailDesc<float>*)h->d_tail, 1, L.kind, done, s, L.fused); });
+         [&] { launch_tail<float>((const TailDesc<float>*)h->d_tail, 1, L.n, done, s, L.fused); });
     return;
   }
   if (l == h->nlev - 1) {
@@ -1408,6 +1408,7 @@ struct bmg_batch {
   std::vector<int> tuned_cl;                         // per stage, 0 = not tuned
   // level-fused tails, grouped by the stage they start at
   std::vector<int> tail_count;
+  std::vector<int> tail_n;      // per stage: size of the first level of the tails starting there
   std::vector<std::vector<char>> tail_host;
   std::vector<void*> tail_dev;
   std::vector<TopDesc> top;
@@ -1494,6 +1495,7 @@ int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x)
     const int lt = batch_tail_level(B, h);
     if (lt >= 0) {
       const int bt = L - 1 - lt;
+      B->tail_n[bt] = std::max(B->tail_n[bt], h->lv[lt].n);
       if (!rhs)
         ++B->tail_count[bt];
       else if (B->precision == BMG_FP64)
@@ -1624,9 +1626,11 @@ void batch_vcycle(bmg_batch* B) {
     }
     if (B->tail_count[b]) {   // problems whose remaining levels run in one level-fused launch
       if (B->precision == BMG_FP64)
-        launch_tail<double>((const TailDesc<double>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws, B->arith);
+        launch_tail<double>((const TailDesc<double>*)B->tail_dev[b], B->tail_count[b], B->tail_n[b], nullptr, B->ws,
+                            B->arith);
       else
-        launch_tail<float>((const TailDesc<float>*)B->tail_dev[b], B->tail_count[b], 0, nullptr, B->ws, B->arith);
+        launch_tail<float>((const TailDesc<float>*)B->tail_dev[b], B->tail_count[b], B->tail_n[b], nullptr, B->ws,
+                           B->arith);
     }
   }
   for (auto& g : B->stages[0]) group_coarse(B, g);
@@ -1968,6 +1972,7 @@ int batch_finish(bmg_batch* B, int rc) {
     B->stages.assign(B->bmax + 1, {});
     B->tuned_cl.assign(B->bmax + 1, 0);
     B->tail_count.assign(B->bmax + 1, 0);
+    B->tail_n.assign(B->bmax + 1, 0);
     B->tail_host.assign(B->bmax + 1, {});
     B->tail_dev.assign(B->bmax + 1, nullptr);
     rc = build_batch_tables(B, nullptr, nullptr);   // group sizes

@@ -917,29 +917,44 @@ __device__ __forceinline__ void finalize_body(const double* __restrict__ partial
   ctl->scale_next = scale_of(rho);
 }
 
-// ---- coarsest solve: forward and back substitution (one thread) -------------------------
-// The substitutions are one dependent chain; thread 0 runs it with the
-// intermediate vector in shared memory (a chain through global memory would
-// pay an L2 round trip per term).  y is unused (kept for the callers' layout).
+// ---- coarsest solve: forward and back substitution ------------------------------------
+// L L^T x = f with every thread of the block taking part.  Forward, right-looking:
+// once y_k = s_k / L_kk is known, every row i > k subtracts L_ik y_k; each row still
+// receives its terms in increasing k, the order of the row-by-row loop, so the
+// result is the same bits.  Backward, thread 0: row i's sum runs over k = i+1 .. m-1
+// in increasing order and starts with x_{i+1}, so the rows form one chain.  The
+// factor is staged in shared memory when it is small (a chain through L2 would
+// pay a round trip per term).  y is unused (kept for the callers' layout).
 constexpr int COARSE_M_MAX = 225;   // coarsest level n <= 15
+constexpr int COARSE_M_SMEM = 9;    // factors of m <= 9 unknowns (n = 3) go to shared memory
 template <typename T>
 __device__ __forceinline__ void coarse_solve_body(int n, const double* __restrict__ L, const T* __restrict__ f,
                                                   T* __restrict__ x, double* __restrict__ y) {
   __shared__ double ys[COARSE_M_MAX];
+  __shared__ double Ls[COARSE_M_SMEM * COARSE_M_SMEM];
   (void)y;
-  if (threadIdx.x != 0) return;
-  int m = n * n, ld = n + 2;
-  for (int i = 0; i < m; ++i) {
-    double s = (double)f[(size_t)(i / n + 1) * ld + (i % n + 1)];
-    for (int k = 0; k < i; ++k) s = rsub(s, rmul(__ldg(&L[(size_t)i * m + k]), ys[k]));
-    ys[i] = rdiv(s, __ldg(&L[(size_t)i * m + i]));
+  const int m = n * n, ld = n + 2;
+  const bool staged = m <= COARSE_M_SMEM;
+  const double* Lp = staged ? Ls : L;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) ys[k] = (double)f[(size_t)(k / n + 1) * ld + (k % n + 1)];
+  if (staged)
+    for (int k = threadIdx.x; k < m * m; k += blockDim.x) Ls[k] = L[k];
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) ys[k] = rdiv(ys[k], Lp[(size_t)k * m + k]);
+    __syncthreads();
+    const double yk = ys[k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) ys[i] = rsub(ys[i], rmul(Lp[(size_t)i * m + k], yk));
+    __syncthreads();
   }
-  for (int i = m - 1; i >= 0; --i) {
-    double s = ys[i];
-    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(__ldg(&L[(size_t)k * m + i]), ys[k]));
-    ys[i] = rdiv(s, __ldg(&L[(size_t)i * m + i]));
-  }
-  for (int i = 0; i < m; ++i) x[(size_t)(i / n + 1) * ld + (i % n + 1)] = (T)ys[i];
+  if (threadIdx.x == 0)
+    for (int i = m - 1; i >= 0; --i) {
+      double s = ys[i];
+      for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(Lp[(size_t)k * m + i], ys[k]));   // ys[k] = x_k
+      ys[i] = rdiv(s, Lp[(size_t)i * m + i]);
+    }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) x[(size_t)(k / n + 1) * ld + (k % n + 1)] = (T)ys[k];
 }
 
 // ---- iterative refinement ------------------------------------------------------------------

@@ -143,12 +143,48 @@ __global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* _
   ir_residual_body<FU>(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
 }
 
+// One problem's level-fused tail per CTA.  The iterates and right-hand sides
+// the tail writes live in shared memory for its duration (the top level's
+// iterate is loaded at entry and written back at exit; the coarser levels' x
+// and f exist only here), so a colour phase reads the previous phase's values
+// from shared memory instead of L2; the read-only stencils, weights and the
+// top level's right-hand side stay in global memory (cached in L1).
+template <typename T>
+__host__ __device__ inline size_t tail_smem_elems(int n0) {
+  size_t e = (size_t)(n0 + 2) * (n0 + 2);
+  for (int n = (n0 - 1) / 2; n >= 3; n = (n - 1) / 2) e += 2 * (size_t)(n + 2) * (n + 2);
+  return e;
+}
+
 template <typename T, bool FU>
 __global__ void __launch_bounds__(1024) k_tail(const TailDesc<T>* __restrict__ d, const int* done) {
   pdl_enter();
-  const TailDesc<T>& q = d[blockIdx.x];
-  if (stopped(done) || stopped(q.done)) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ TailDesc<T> q;
+  const TailDesc<T>& g = d[blockIdx.x];
+  if (stopped(done) || stopped(g.done)) return;
+  T* sm = reinterpret_cast<T*>(tail_smem);
+  const size_t ps0 = plane_size(g.lv[0].v.n);
+  if (threadIdx.x == 0) {
+    q = g;
+    size_t off = ps0;
+    for (int l = 1; l < g.nlev; ++l) {
+      const size_t ps = plane_size(g.lv[l].v.n);
+      q.lv[l].x = sm + off;
+      q.lv[l].f = sm + off + ps;
+      q.lv[l - 1].xc = sm + off;
+      q.lv[l - 1].fc = sm + off + ps;
+      off += 2 * ps;
+    }
+    q.lv[0].x = sm;
+  }
+  size_t total = ps0;
+  for (int l = 1; l < g.nlev; ++l) total += 2 * plane_size(g.lv[l].v.n);
+  for (size_t k = threadIdx.x; k < ps0; k += blockDim.x) sm[k] = g.lv[0].x[k];
+  for (size_t k = ps0 + threadIdx.x; k < total; k += blockDim.x) sm[k] = T(0);
+  __syncthreads();
   tail_body<T, FU>(q, q.top_kind);
+  for (size_t k = threadIdx.x; k < ps0; k += blockDim.x) g.lv[0].x[k] = sm[k];
 }
 
 // 1 when every problem's control flag is set.
@@ -358,13 +394,19 @@ void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s,
 }
 
 template <typename T>
-void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s, int fused) {
+void launch_tail(const TailDesc<T>* d, int count, int top_n, const int* done_any, cudaStream_t s, int fused) {
   if (count <= 0) return;
-  (void)top_kind;
+  const size_t bytes = tail_smem_elems<T>(top_n) * sizeof(T);
+  static size_t attr_bytes[2] = {0, 0};
+  if (bytes > attr_bytes[fused ? 1 : 0]) {   // raise the dynamic shared-memory limit once per size
+    cudaFuncSetAttribute(fused ? (const void*)k_tail<T, true> : (const void*)k_tail<T, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    attr_bytes[fused ? 1 : 0] = bytes;
+  }
   if (fused)
-    pdl_launch(k_tail<T, true>, count, 1024, 0, s, d, done_any);
+    pdl_launch(k_tail<T, true>, count, 1024, bytes, s, d, done_any);
   else
-    pdl_launch(k_tail<T, false>, count, 1024, 0, s, d, done_any);
+    pdl_launch(k_tail<T, false>, count, 1024, bytes, s, d, done_any);
   count_launch();
 }
 template void launch_tail<double>(const TailDesc<double>*, int, int, const int*, cudaStream_t, int);

@@ -202,10 +202,11 @@ int rows_threads(int n, int cl);
 namespace bmg {
 template <typename T>
 struct TailDesc;
-// The level-fused tail of `count` problems (one CTA each); top_kind is the
-// stencil kind of each descriptor's first level.
+// The level-fused tail of `count` problems (one CTA each) whose first level
+// has size top_n (the same for all); the tail's iterates and right-hand sides
+// are held in dynamic shared memory, sized from top_n.
 template <typename T>
-void launch_tail(const TailDesc<T>* d, int count, int top_kind, const int* done_any, cudaStream_t s, int fused = 0);
+void launch_tail(const TailDesc<T>* d, int count, int top_n, const int* done_any, cudaStream_t s, int fused = 0);
 template <typename T>
 constexpr int tail_max_n() { return sizeof(T) == 8 ? 15 : 63; }
 }  // namespace bmg
