@@ -108,3 +108,19 @@ def test_batched_and_rhs_batches_need_level_sizes(bmg):
     with pytest.raises(bmg.BmgError):
         bmg.Batch.from_hierarchy(h, 2)
     h.close()
+
+
+@pytest.mark.parametrize("sides", ["E", "EN", "WS"])
+@pytest.mark.parametrize("nx,ny,precision", [(255, 255, "fp64"), (200, 129, "fp64"), (255, 255, "fp32")])
+def test_neumann_sides_bitwise(bmg, sides, nx, ny, precision):
+    """Natural boundary conditions enter through the stencil (zero-k cells
+    beyond the Neumann sides): the library solves them like any other stencil."""
+    kind, planes, f = w.neumann_problem(nx, ny, sides)
+    nbf = None if precision == "fp64" else 0
+    xw, hw = oracle_solve(kind, planes, f, precision, nbf, "none", "fused")
+    h = bmg.Hierarchy(kind, dev(planes), precision=precision, arith="fused")
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(host(x)[1:ny + 1, 1:nx + 1], xw[1:ny + 1, 1:nx + 1])
+    check_history(h.history(), hw)
+    h.close()

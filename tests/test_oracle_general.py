@@ -88,3 +88,38 @@ def test_extra_rows_are_identity_and_decoupled():
     assert np.all(A[np.ix_(~r, ~r)] == np.eye((~r).sum()))
     assert np.all(A[np.ix_(r, ~r)] == 0) and np.all(A[np.ix_(~r, r)] == 0)
     assert np.all(fn[1:n + 1, 1:n + 1].reshape(-1)[~r] == 0)
+
+
+# ---- Neumann sides through the stencil ---------------------------------------------------
+
+@pytest.mark.parametrize("sides", ["E", "EN", "WS"])
+@pytest.mark.parametrize("nx,ny", [(31, 31), (40, 23)])
+def test_neumann_sides_solve_the_caller_system(sides, nx, ny):
+    """Natural boundary conditions enter through the stencil (zero-k cells
+    beyond the side): the multigrid solution equals the dense solve of the
+    assembled system, and the cycle keeps a square-like factor."""
+    kind, planes, f = w.neumann_problem(nx, ny, sides)
+    pn, fn = bx.embed(planes, f)
+    x_n, h = bx.solve(bx.setup(kind, pn), fn, tol=1e-12, maxit=100)
+    assert h[-1] <= 1e-12 * h[0]
+    factor = (h[-1] / h[0]) ** (1.0 / (len(h) - 1))
+    assert factor < 0.3                               # 0.05 - 0.22 measured
+    x = bx.extract(x_n, nx, ny)
+    A = caller_matrix(w.zero_ghost_couplings(planes.copy()))
+    ref = np.linalg.solve(A, f[1:ny + 1, 1:nx + 1].reshape(-1)).reshape(ny, nx)
+    assert np.allclose(x[1:ny + 1, 1:nx + 1], ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_neumann_rows_have_zero_row_sum_and_no_outward_coupling():
+    """A Neumann node of constant k: its stencil row sums to zero (no Dirichlet
+    term) and has no coupling across the side; a Dirichlet-side node keeps a
+    positive row sum."""
+    nx, ny = 12, 10
+    k = np.ones((ny + 1, nx + 1))
+    k[:, nx] = 0.0                                    # Neumann on the east side
+    planes = w.fe9_from_cells(k)
+    A = caller_matrix(w.zero_ghost_couplings(planes.copy()))
+    rows = A.sum(axis=1).reshape(ny, nx)
+    assert np.allclose(rows[1:-1, nx - 1], 0.0, atol=1e-14)     # east nodes away from the corners
+    assert np.all(rows[1:-1, 0] > 0.1)                           # west (Dirichlet) nodes
+    assert np.all(planes[1][:, nx + 1] == 0.0) and np.all(planes[3][:, nx + 1] == 0.0)

@@ -248,6 +248,27 @@ def general_size_problem(nx: int, ny: int, kind: int = 9, std: float = 1.0, corr
     return kind, planes, rhs_uniform(nx, seed_f, ny)
 
 
+def neumann_problem(nx: int, ny: int, sides: str = "EN", std: float = 1.0, corr_len: float = 8.0,
+                    seed_k: int = 40, seed_f: int = 41):
+    """9-point Q1 problem of -div(k grad u) = f with natural (Neumann) boundary
+    conditions on the listed sides (E, W, N, S) and u = 0 on the others.  The
+    nodes of a Neumann side are unknowns (the outermost interior row or column
+    of the nx x ny grid) and the cells beyond them have k = 0, so their
+    stencils sum over the cells inside the domain only, the element-by-element
+    assembly of the natural condition.  k = exp(g) inside, RHS uniform[-1, 1)."""
+    g = gaussian_field(max(nx, ny) + 1, std, corr_len, seed_k)
+    k = np.exp(g)[:ny + 1, :nx + 1].copy()
+    if "E" in sides:
+        k[:, nx] = 0.0       # cells east of the column i = nx
+    if "W" in sides:
+        k[:, 0] = 0.0        # cells west of the column i = 1
+    if "N" in sides:
+        k[ny, :] = 0.0
+    if "S" in sides:
+        k[0, :] = 0.0
+    return 9, fe9_from_cells(k), rhs_uniform(nx, seed_f, ny)
+
+
 def high_contrast_problem(n: int = 4095, block: int = 8, lo: float = 1.0, hi: float = 1e6,
                           seed: int = 6):
     """Binary blocks k in {1, 1e6} on 8 x 8 cell tiles (the learned-interpolation
