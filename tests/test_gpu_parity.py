@@ -652,23 +652,27 @@ def test_config3_full_size_setup_and_solves():
     lv0.ci = bx.dendy_interp(p64)
     assert np.array_equal(host(h.interp(0)), lv0.ci)
     assert np.array_equal(host(h.stencil(1)), bx.rap(p64, lv0.ci))
-    for hh in (h, bmg.Hierarchy(kind, coef, precision="bf16")):
+    for hh, fu in ((h, False), (bmg.Hierarchy(kind, coef, precision="bf16"), False),
+                   (bmg.Hierarchy(kind, coef, arith="fused"), True),
+                   (bmg.Hierarchy(kind, coef, precision="fp32", arith="fused"), True)):
         x, it, rr, ok = hh.solve(rhs, tol=1e-10, maxit=100)
         assert ok
         assert bx.norm(bx.residual(p64, host(x), f)) <= 1e-10 * f0
-        assert hh.history()[-1] == bx.norm(bx.residual(p64, host(x), f))
+        # the last history entry is the norm of the true FP64 residual, in the solve's own arithmetic
+        assert hh.history()[-1] == bx.norm(bx.residual(p64, host(x), f, fused=fu), fused=fu)
         hh.close()
 
 
 @pytest.mark.slow
-def test_config4_full_batch_converges_to_oracle_residuals():
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+def test_config4_full_batch_converges_to_oracle_residuals(arith):
     """The 256-problem batch (sides 63 .. 1023, 80 M unknowns): every problem's
     FP32-refinement solution meets tol 1e-8 by the oracle's FP64 residual."""
     import paper_2502_05279_gb300 as bmg
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     probs = w.batched_problems(256, 5, 1.0, 32.0)
-    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32")
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], precision="fp32", arith=arith)
     xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-8, maxit=100)
     assert ok
     for (kind, planes, f), x in zip(probs, xs):
