@@ -62,9 +62,9 @@ NCU_TRAFFIC = {
     ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48x26 bulk/4"): 136.2e6,
     ("fe2047-binary1e4", "k_gs_strip64 56xW cp.async/6 fused"): 268.8e6,
 }
-TILE_SHAPES = ("56x26 bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
+TILE_SHAPES = ("56xW bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
-PAIR_SHAPES = ("48x32 bulk/4", "48x16 bulk/4", "48x32 bulk/6", "48x26 bulk/4")
+PAIR_SHAPES = ("48xW bulk/4", "48x16 bulk/4", "48x32 bulk/6", "48x26 bulk/4")   # W: one wave
 
 
 BATCHED = dict(text="256 independent 9-point Q1 problems, sides uniform from {63,127,255,511,1023} (seed 5), "

@@ -197,8 +197,9 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
  * the hierarchy runs (FP64 or FP32): the row kernel's cluster size (1, 2, 4,
  * 8), BMG_TILE_SWEEP + s when the one-pass tile kernel with tile shape s won
  * (warp strips of 56 x TY points; FP32 cycles: shapes 0 .. 3 stream rows by
- * bulk copies into 4 row slots, TY = 26, 8, 16, 32, shapes 4, 5 load rows
- * into registers, TY = 32, 16; FP64 cycles: rows copied per lane into RING
+ * bulk copies into 4 row slots, TY = W, 8, 16, 32 (W: the smallest even
+ * height whose strips fit into one wave of resident warps), shapes 4, 5 load
+ * rows into registers, TY = 32, 16; FP64 cycles: rows copied per lane into RING
  * slots, (TY, RING) = (W, 4), (16, 4), (W, 6), (8, 4), W the smallest even
  * height whose strips fit into one wave of resident warps), or 0 (default;
  * not tuned).  Every choice computes the same bits. */
@@ -207,7 +208,7 @@ int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 
 /* Shape (0 .. 3) of the two-sweep pass (temporal blocking: two Gauss-Seidel
  * sweeps for one read of the level's arrays, 48 x TY warp strips with
- * TY = 32, 16, 32, 26 and 4, 4, 6, 4 row slots) that runs each pair of sweeps
+ * TY = W (one wave), 16, 32, 26 and 4, 4, 6, 4 row slots) that runs each pair of sweeps
  * on level `level` of an FP32 cycle, or -1 (sweeps one at a time).  Same bits
  * either way. */
 int bmg_tuned_pair(const bmg_hierarchy* h, int level);

@@ -477,22 +477,24 @@ __device__ __forceinline__ void ring_read(const unsigned char* slot, int ld, int
   R.nwb = nwq[o8 + 1];
 }
 
-template <typename S, int TY, int RING, bool FU = false>
+// The strip height ty (even, >= 2) is a launch argument, as in the FP64 sweep.
+template <typename S, int RING, bool FU = false>
 __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
                                                    const float* __restrict__ xin, float* __restrict__ xout,
-                                                   int sx, int sy, unsigned char* ring, unsigned long long* bars) {
-  static_assert(TY % 2 == 0 && RING % 2 == 0 && RING >= 4, "strip shape");
+                                                   int sx, int sy, int ty, unsigned char* ring,
+                                                   unsigned long long* bars) {
+  static_assert(RING % 2 == 0 && RING >= 4, "ring size");
   using RG = StripRing<S>;
   const int n = v.n, ld = v.ld;
   const int lane = threadIdx.x & 31;
-  const int i0 = 1 + 56 * sx, j0 = 1 + TY * sy, j1 = j0 + TY;
+  const int i0 = 1 + 56 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
   const int icol = i0 - 4, ic = icol + 2 * lane;
   const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
   const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
   const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
   const bool own = lane >= 2 && lane <= 29;
   const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
-  constexpr int NR = TY + 3;                      // band rows q = 0 .. NR - 1, j = j0 - 1 + q
+  const int NR = ty + 3;                          // band rows q = 0 .. NR - 1, j = j0 - 1 + q
   const int last = (n + 1) - (j0 - 1);            // rows q > last lie outside the grid: never copied
   auto valid = [&](int q) { return q < NR && q <= last; };
   if (lane == 0) {
@@ -540,9 +542,9 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
     }
   };
 #pragma unroll 1
-  for (int m = 1; m <= TY / 2 && ok; m += 2) {
+  for (int m = 1; m <= ty / 2 && ok; m += 2) {
     step(m, Q0, Q1, P0, P1);
-    if (m + 1 <= TY / 2 && ok) step(m + 1, P0, P1, Q0, Q1);
+    if (m + 1 <= ty / 2 && ok) step(m + 1, P0, P1, Q0, Q1);
   }
   if (!ok)                                        // drain the copies still in flight, bounded
     for (int q = taken; q < taken + RING; ++q)
@@ -567,15 +569,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <typename S, int TY, int RING, bool FU = false>
+template <typename S, int RING, bool FU = false>
 __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
                                                     const float* __restrict__ xin, float* __restrict__ xout,
-                                                    int sx, int sy, unsigned char* ring, unsigned long long* bars) {
-  static_assert(TY % 2 == 0 && RING % 2 == 0 && RING >= 4, "strip shape");
+                                                    int sx, int sy, int ty, unsigned char* ring,
+                                                    unsigned long long* bars) {
+  static_assert(RING % 2 == 0 && RING >= 4, "ring size");
   using RG = StripRing<S>;
   const int n = v.n, ld = v.ld;
   const int lane = threadIdx.x & 31;
-  const int i0 = 1 + 48 * sx, j0 = 1 + TY * sy, j1 = j0 + TY;
+  const int i0 = 1 + 48 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
   const int icol = i0 - 8, ic = icol + 2 * lane;
   const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
   // sweep 1 on c in [1, 62], sweep 2 on c in [5, 58]; the strip's own columns c in [8, 55]
@@ -585,7 +588,7 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   const bool r2 = in_a && lane >= 4 && lane <= 28, t2 = in_b && lane >= 4 && lane <= 27;
   const bool own = lane >= 4 && lane <= 27;
   const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
-  constexpr int NR = TY + 7;                      // band rows q = 0 .. NR - 1, j = j0 - 3 + q
+  const int NR = ty + 7;                      // band rows q = 0 .. NR - 1, j = j0 - 3 + q
   auto rowok = [&](int q) { const int j = j0 - 3 + q; return j >= 0 && j <= n + 1; };
   // lane 0: fill the slot of band row q (copies, or a plain arrive for a row outside the grid)
   auto issue = [&](int q) {
@@ -618,7 +621,7 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   take(1, R4);
   take(2, R5);
 #pragma unroll 1
-  for (int m = 0; m <= TY / 2 + 2 && ok; ++m) {
+  for (int m = 0; m <= ty / 2 + 2 && ok; ++m) {
     const int a = j0 - 2 + 2 * m, b = a - 2;      // sweep-1 and sweep-2 odd rows
     if (m >= 1) {
       take(2 * m + 1, R4);

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const Le
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
       w * RING;
-  if (!gs_strip_ring_body<S, TY, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx,
-                                           ring, bars) &&
+  if (!gs_strip_ring_body<S, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, TY,
+                                       ring, bars) &&
       (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout_b, 1);
 }
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const L
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRing<S>::SLOT) +
       w * RING;
-  if (!gs_strip2_ring_body<S, TY, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx,
-                                            ring, bars) &&
+  if (!gs_strip2_ring_body<S, RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, TY,
+                                        ring, bars) &&
       (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout_b, 1);
 }

@@ -51,40 +51,43 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip(StencilView<float
 // Bulk-copy form: warp w of the CTA owns ring slots [w RING, (w + 1) RING) and
 // mbarriers [w RING, (w + 1) RING) of the dynamic shared memory.
 __device__ int g_strip_timeout = 0;
-template <typename S, int TY, int RING, bool FU>
+template <typename S, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip_ring(StencilView<float, S> v,
                                                                     const float* __restrict__ f,
                                                                     const float* __restrict__ xin,
-                                                                    float* __restrict__ xout, const int* done) {
+                                                                    float* __restrict__ xout, const int* done,
+                                                                    int ty) {
   pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   if (stopped(done)) return;
-  const int nbx = (v.n + 55) / 56, nby = (v.n + TY - 1) / TY;
+  const int nbx = (v.n + 55) / 56, nby = (v.n + ty - 1) / ty;
   const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
   if (g >= nbx * nby) return;                     // whole warps only
   unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
-  if (!gs_strip_ring_body<S, TY, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+  if (!gs_strip_ring_body<S, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ty, ring, bars) && (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout, 1);
 }
 
 // Two sweeps in one pass: warps take 48-column strips, otherwise as above.
-template <typename S, int TY, int RING, bool FU>
+template <typename S, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView<float, S> v,
                                                                      const float* __restrict__ f,
                                                                      const float* __restrict__ xin,
-                                                                     float* __restrict__ xout, const int* done) {
+                                                                     float* __restrict__ xout, const int* done,
+                                                                     int ty) {
   pdl_enter();
   extern __shared__ __align__(128) unsigned char strip_smem[];
   if (stopped(done)) return;
-  const int nbx = (v.n + 47) / 48, nby = (v.n + TY - 1) / TY;
+  const int nbx = (v.n + 47) / 48, nby = (v.n + ty - 1) / ty;
   const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
   if (g >= nbx * nby) return;
   unsigned char* ring = strip_smem + (size_t)w * RING * StripRing<S>::SLOT;
   unsigned long long* bars =
       reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRing<S>::SLOT) + w * RING;
-  if (!gs_strip2_ring_body<S, TY, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ring, bars) && (threadIdx.x & 31) == 0)
+  if (!gs_strip2_ring_body<S, RING, FU>(v, f, xin, xout, g % nbx, g / nbx, ty, ring, bars) &&
+      (threadIdx.x & 31) == 0)
     atomicExch(&g_strip_timeout, 1);
 }
 
@@ -302,19 +305,30 @@ static void strip_launch(const StencilView<float, S>& v, const float* f, const f
   count_launch();
 }
 
-template <typename S, int TY, int RING, bool FU>
+// ty = 0: the smallest even strip height whose strips fit into one wave of
+// the kernel's resident warps.
+template <typename S, int RING, bool FU>
 static void strip_ring_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
-                              const int* done, cudaStream_t s) {
+                              const int* done, cudaStream_t s, int ty) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gs_strip_ring<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bytes);
-    attr = true;
+  static int resident_warps = 0;
+  if (!resident_warps) {
+    cudaFuncSetAttribute(k_gs_strip_ring<S, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip_ring<S, RING, FU>, 32 * STRIP_WARPS, bytes);
+    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
   }
-  const int warps = ((v.n + 55) / 56) * ((v.n + TY - 1) / TY);
-  pdl_launch(k_gs_strip_ring<S, TY, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
-      v, f, xin, xout, done);
+  const int nbx = (v.n + 55) / 56;
+  if (ty <= 0) {
+    const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
+    const int half = (v.n + 2 * nby_max - 1) / (2 * nby_max);
+    ty = 2 * (half > 1 ? half : 1);
+  }
+  const int warps = nbx * ((v.n + ty - 1) / ty);
+  pdl_launch(k_gs_strip_ring<S, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
+             v, f, xin, xout, done, ty);
   count_launch();
 }
 
@@ -324,12 +338,12 @@ template <typename S, bool FU>
 static void gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
   switch (shape) {
-    case 1: strip_ring_launch<S, 8, 4, FU>(v, f, xin, xout, done, s); break;
-    case 2: strip_ring_launch<S, 16, 4, FU>(v, f, xin, xout, done, s); break;
-    case 3: strip_ring_launch<S, 32, 4, FU>(v, f, xin, xout, done, s); break;
+    case 1: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 8); break;
+    case 2: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 16); break;
+    case 3: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 32); break;
     case 4: strip_launch<S, 32, FU>(v, f, xin, xout, done, s); break;
     case 5: strip_launch<S, 16, FU>(v, f, xin, xout, done, s); break;
-    default: strip_ring_launch<S, 26, 4, FU>(v, f, xin, xout, done, s); break;
+    default: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 0); break;   // one wave
   }
 }
 
@@ -405,19 +419,29 @@ void launch_wait_selftest(cudaStream_t s) {
   count_launch();
 }
 
-template <typename S, int TY, int RING, bool FU>
+// ty = 0: the one-wave strip height, as strip_ring_launch.
+template <typename S, int RING, bool FU>
 static void strip2_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
-                          const int* done, cudaStream_t s) {
+                          const int* done, cudaStream_t s, int ty) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gs_strip2_ring<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bytes);
-    attr = true;
+  static int resident_warps = 0;
+  if (!resident_warps) {
+    cudaFuncSetAttribute(k_gs_strip2_ring<S, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip2_ring<S, RING, FU>, 32 * STRIP_WARPS, bytes);
+    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
   }
-  const int warps = ((v.n + 47) / 48) * ((v.n + TY - 1) / TY);
-  pdl_launch(k_gs_strip2_ring<S, TY, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
-      v, f, xin, xout, done);
+  const int nbx = (v.n + 47) / 48;
+  if (ty <= 0) {
+    const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
+    const int half = (v.n + 2 * nby_max - 1) / (2 * nby_max);
+    ty = 2 * (half > 1 ? half : 1);
+  }
+  const int warps = nbx * ((v.n + ty - 1) / ty);
+  pdl_launch(k_gs_strip2_ring<S, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
+             v, f, xin, xout, done, ty);
   count_launch();
 }
 
@@ -425,10 +449,10 @@ template <typename S, bool FU>
 static void gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
   switch (shape) {
-    case 1: strip2_launch<S, 16, 4, FU>(v, f, xin, xout, done, s); break;
-    case 2: strip2_launch<S, 32, 6, FU>(v, f, xin, xout, done, s); break;
-    case 3: strip2_launch<S, 26, 4, FU>(v, f, xin, xout, done, s); break;
-    default: strip2_launch<S, 32, 4, FU>(v, f, xin, xout, done, s); break;
+    case 1: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 16); break;
+    case 2: strip2_launch<S, 6, FU>(v, f, xin, xout, done, s, 32); break;
+    case 3: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 26); break;
+    default: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 0); break;   // one wave
   }
 }
 

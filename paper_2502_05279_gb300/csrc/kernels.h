@@ -64,7 +64,8 @@ void launch_wait_selftest(cudaStream_t s);
 // One four-colour Gauss-Seidel sweep of a 9-point FP32 level in one launch:
 // reads xin, writes every interior point of xout (xout != xin; the ghost ring
 // of xout is not written).  One warp per strip of 56 x TY points: shapes
-// 0 .. 3 stream rows by bulk copies into 4 row slots (TY 26, 8, 16, 32),
+// 0 .. 3 stream rows by bulk copies into 4 row slots (TY = W, 8, 16, 32, W the
+// smallest even height whose strips fit into one wave of resident warps),
 // shapes 4, 5 load them into registers (TY 32, 16).  The bulk-copy
 // shapes need the array layout above (else they run as shape 4).
 constexpr int GS_TILE_SHAPES = 6;
@@ -74,7 +75,7 @@ void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float*
 // Two four-colour sweeps of a 9-point FP32 level in one launch (temporal
 // blocking): xin -> xout as two launch_gs_tile calls would give through an
 // intermediate array.  One warp per strip of 48 x TY points, rows by bulk
-// copies: shapes 0 .. 3 = TY 32, 16, 32, 26 with 4, 4, 6, 4 row slots.  Needs
+// copies: shapes 0 .. 3 = TY W (one wave), 16, 32, 26 with 4, 4, 6, 4 row slots.  Needs
 // the guarded, aligned array layout; returns false (nothing launched) without it.
 constexpr int GS_PAIR_SHAPES = 4;
 template <typename S>
