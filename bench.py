@@ -61,6 +61,8 @@ NCU_TRAFFIC = {
     ("fe2047-binary1e4", "k_gs_strip<float> 56x32 bulk/4"): 135.8e6,
     ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48x26 bulk/4"): 136.2e6,
     ("fe2047-binary1e4", "k_gs_strip64 56xW cp.async/6 fused"): 268.8e6,
+    ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48xW bulk/4"): 145.9e6,
+    ("fe2047-binary1e4", "k_gs_strip<float> 56xW bulk/4"): 138.1e6,
 }
 TILE_SHAPES = ("56xW bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
