@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -607,7 +608,15 @@ int alloc_line(bmg_hierarchy* h) {
   return BMG_OK;
 }
 
+// The tuners' result caches are process-wide; setups running on several host
+// threads take turns through this lock.
+std::mutex& tune_lock() {
+  static std::mutex m;
+  return m;
+}
+
 int autotune_solo(bmg_hierarchy* h) {
+  std::lock_guard<std::mutex> guard(tune_lock());
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
     if (L.kind != 9 || L.n < 127) continue;
@@ -1853,6 +1862,7 @@ int force_batch_onepass(bmg_batch* B) {
 }
 
 int autotune_batch(bmg_batch* B) {
+  std::lock_guard<std::mutex> guard(tune_lock());
   // descriptor contents are needed: build the tables with the internal level
   // arrays standing in for the caller buffers of level 0
   std::vector<const double*> rhs(B->nprob);

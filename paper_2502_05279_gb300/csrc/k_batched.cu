@@ -292,22 +292,24 @@ template <typename S, int TY, int RING, bool PAIR, bool FU>
 static void strip_b_launch(const LevelDesc<float, S>* d, int count, int n, int dir, cudaStream_t s) {
   if (count <= 0) return;
   constexpr size_t bytes = (size_t)STRIP_WARPS_B * RING * (StripRing<S>::SLOT + 8);
-  static bool attr = false;
+  // the shared-memory limit is raised once per kernel (thread-safe static initialisation)
+  static const bool attr = [] {
+    if (PAIR)
+      cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+    else
+      cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes);
+    return true;
+  }();
+  (void)attr;
   const int width = PAIR ? 48 : 56;
   const long warps = (long)count * ((n + width - 1) / width) * ((n + TY - 1) / TY);
   const unsigned blocks = (unsigned)((warps + STRIP_WARPS_B - 1) / STRIP_WARPS_B);
-  if (PAIR) {
-    if (!attr)
-      cudaFuncSetAttribute(k_gs_strip2_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bytes);
+  if (PAIR)
     pdl_launch(k_gs_strip2_ring_b<S, TY, RING, FU>, blocks, 32 * STRIP_WARPS_B, bytes, s, d, count, n, dir);
-  } else {
-    if (!attr)
-      cudaFuncSetAttribute(k_gs_strip_ring_b<S, TY, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bytes);
+  else
     pdl_launch(k_gs_strip_ring_b<S, TY, RING, FU>, blocks, 32 * STRIP_WARPS_B, bytes, s, d, count, n, dir);
-  }
-  attr = true;
   count_launch();
 }
 
@@ -396,13 +398,9 @@ void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s,
 template <typename T>
 void launch_tail(const TailDesc<T>* d, int count, int top_n, const int* done_any, cudaStream_t s, int fused) {
   if (count <= 0) return;
+  // tails start at n <= tail_max_n: at most 28.8 KB (FP32, n = 63) or 4 KB (FP64,
+  // n = 15), inside the default 48 KB dynamic shared-memory limit
   const size_t bytes = tail_smem_elems<T>(top_n) * sizeof(T);
-  static size_t attr_bytes[2] = {0, 0};
-  if (bytes > attr_bytes[fused ? 1 : 0]) {   // raise the dynamic shared-memory limit once per size
-    cudaFuncSetAttribute(fused ? (const void*)k_tail<T, true> : (const void*)k_tail<T, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    attr_bytes[fused ? 1 : 0] = bytes;
-  }
   if (fused)
     pdl_launch(k_tail<T, true>, count, 1024, bytes, s, d, done_any);
   else

@@ -305,21 +305,27 @@ static void strip_launch(const StencilView<float, S>& v, const float* f, const f
   count_launch();
 }
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` and return how many
+// warps of it (CTAs of STRIP_WARPS warps) fit on the device at once.  Callers
+// keep the result in a function-local static, whose initialisation C++ makes
+// thread-safe.
+template <typename K>
+static int resident_strip_warps(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * STRIP_WARPS, bytes);
+  return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
+}
+
 // ty = 0: the smallest even strip height whose strips fit into one wave of
 // the kernel's resident warps.
 template <typename S, int RING, bool FU>
 static void strip_ring_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                               const int* done, cudaStream_t s, int ty) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
-  static int resident_warps = 0;
-  if (!resident_warps) {
-    cudaFuncSetAttribute(k_gs_strip_ring<S, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip_ring<S, RING, FU>, 32 * STRIP_WARPS, bytes);
-    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
-  }
+  static const int resident_warps = resident_strip_warps(k_gs_strip_ring<S, RING, FU>, bytes);
   const int nbx = (v.n + 55) / 56;
   if (ty <= 0) {
     const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
@@ -365,15 +371,7 @@ template <int RING, bool FU>
 static void strip64_launch(const StencilView<double, double>& v, const double* f, const double* xin, double* xout,
                            const int* done, cudaStream_t s, int ty) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * STRIP64_SLOT;
-  static int resident_warps = 0;
-  if (!resident_warps) {
-    cudaFuncSetAttribute(k_gs_strip64<RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip64<RING, FU>, 32 * STRIP_WARPS, bytes);
-    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
-  }
+  static const int resident_warps = resident_strip_warps(k_gs_strip64<RING, FU>, bytes);
   const int nbx = (v.n + 55) / 56;
   if (ty <= 0) {
     const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
@@ -424,15 +422,7 @@ template <typename S, int RING, bool FU>
 static void strip2_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
                           const int* done, cudaStream_t s, int ty) {
   constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRing<S>::SLOT + 8);
-  static int resident_warps = 0;
-  if (!resident_warps) {
-    cudaFuncSetAttribute(k_gs_strip2_ring<S, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip2_ring<S, RING, FU>, 32 * STRIP_WARPS, bytes);
-    resident_warps = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS;
-  }
+  static const int resident_warps = resident_strip_warps(k_gs_strip2_ring<S, RING, FU>, bytes);
   const int nbx = (v.n + 47) / 48;
   if (ty <= 0) {
     const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
