@@ -721,3 +721,32 @@ def test_batch_of_right_hand_sides_rejects_bad_arguments(bmg):
     rc = bmg.lib.bmg_batch_rhs(h._h, 3, __import__("ctypes").byref(o), __import__("ctypes").byref(b))
     assert rc == bmg._lib.BMG_EINVAL and "precision" in bmg.lib.bmg_last_error().decode()
     h.close()
+
+
+def test_concurrent_setups_on_two_host_threads(bmg):
+    """Two hierarchies set up at once from two host threads (ctypes releases the
+    GIL; the autotuner caches are shared): both solve exactly as one built alone."""
+    import threading
+    kind, planes, f = problem("lognormal", 511)
+    hs, errs = [None, None], []
+
+    def build(k, precision):
+        try:
+            torch.cuda.set_device(0)
+            hs[k] = bmg.Hierarchy(kind, dev(planes), precision=precision, arith="fused")
+        except Exception as e:   # surfaced below
+            errs.append(e)
+
+    ts = [threading.Thread(target=build, args=(0, "fp32")), threading.Thread(target=build, args=(1, "fp64"))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs
+    for h, precision in zip(hs, ("fp32", "fp64")):
+        x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+        ref = bmg.Hierarchy(kind, dev(planes), precision=precision, arith="fused")
+        x2, it2, rr2, ok2 = ref.solve(dev(f), tol=1e-10, maxit=100)
+        assert ok and it == it2 and torch.equal(x, x2) and h.history() == ref.history()
+        ref.close()
+        h.close()
