@@ -246,7 +246,12 @@ typedef struct bmg_batch bmg_batch;   /* opaque, library-owned */
 /* nprob problems; A[p] and n[p] as in bmg_setup (n[p] = 2^m - 1 >= coarsest).
  * opts (may be NULL) apply to every problem.  With opts->use_graph the row
  * tile of the Gauss-Seidel kernels of every stage with n >= 127 is chosen by
- * timing the candidates on scratch copies of that stage (autotuner). */
+ * timing the candidates on scratch copies of that stage (autotuner); stages
+ * with n >= 255 also time the one-pass kernel (FP64 and FP32/BF16) and the
+ * two-sweep pass (FP32/BF16).  opts->smoother may force BMG_SMOOTHER_ROWS,
+ * BMG_SMOOTHER_TILE + s (s = 0 .. 3, every precision) or BMG_SMOOTHER_PAIR + s
+ * (FP32/BF16 only) on every stage outside the level-fused tails; line
+ * relaxation and the other shapes are EINVAL. */
 int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* opts, bmg_batch** out);
 
 /* A batch of k right-hand sides for the operator of hierarchy h (built by

@@ -1530,7 +1530,7 @@ int build_batch_tables(bmg_batch* B, const double* const* rhs, double* const* x)
       }
       if (storage == 0) {
         LevelDesc<double, double> d{view64(lv), lv.ci, l == 0 ? x[p] : lv.x, l == 0 ? rhs[p] : lv.f,
-                                    C ? C->x : nullptr, C ? C->f : nullptr, done, h->Lfac, h->work};
+                                    C ? C->x : nullptr, C ? C->f : nullptr, done, h->Lfac, h->work, lv.x64b};
         append_desc(g, d);
       } else if (storage == 2) {
         LevelDesc<float, __nv_bfloat16> d{viewbf(lv), lv.ci32, lv.x32, lv.f32, C ? C->x32 : nullptr,
@@ -1586,7 +1586,10 @@ int group_launches(const bmg_batch::Group& g, int sweeps) {
 
 void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
   if (!g.count || !sweeps) return;
-  if (g.tile >= 0 && g.storage == 1) group_onepass<float>(B, g, sweeps);
+  if (g.tile >= 0 && g.storage == 0)
+    for (int k = 0; k < sweeps; ++k, g.dir ^= 1)
+      launch_gs_tile64_b(gdesc<double, double>(g), g.count, g.n, g.tile, g.dir, B->ws, B->arith);
+  else if (g.tile >= 0 && g.storage == 1) group_onepass<float>(B, g, sweeps);
   else if (g.tile >= 0 && g.storage == 2) group_onepass<__nv_bfloat16>(B, g, sweeps);
   else if (g.storage == 0)
     launch_gs_b(gdesc<double, double>(g), g.count, g.n, g.kind, sweeps, g.cl, B->ws, B->arith);
@@ -1599,7 +1602,7 @@ void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
 void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
   if (g.storage == 0)
-    launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws, 0, B->arith);
+    launch_resid_restrict_b(gdesc<double, double>(g), g.count, g.n, g.kind, B->ws, g.dir, B->arith);
   else if (g.storage == 1)
     launch_resid_restrict_b(gdesc<float, float>(g), g.count, g.n, g.kind, B->ws, g.dir, B->arith);
   else
@@ -1611,7 +1614,7 @@ void group_restrict(bmg_batch* B, bmg_batch::Group& g) {
 void group_interp(bmg_batch* B, bmg_batch::Group& g) {
   if (!g.count) return;
   const int din = g.dir, dout = group_launches(g, B->nu2) & 1;
-  if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws, 0, 0, B->arith);
+  if (g.storage == 0) launch_interp_b(gdesc<double, double>(g), g.count, g.n, B->ws, din, dout, B->arith);
   else if (g.storage == 1) launch_interp_b(gdesc<float, float>(g), g.count, g.n, B->ws, din, dout, B->arith);
   else launch_interp_b(gdesc<float, __nv_bfloat16>(g), g.count, g.n, B->ws, din, dout, B->arith);
   g.dir = dout;
@@ -1758,8 +1761,14 @@ int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
     if (l < 0) continue;
     Level& lv = h->lv[l];
     const int storage = B->precision == BMG_FP64 ? 0 : (lv.bf16 ? 2 : 1);
-    if (lv.n != g.n || lv.kind != g.kind || storage != g.storage || lv.x32b) continue;
-    int rc = galloc(&lv.x32b, lv.n, 1, B->ws);
+    if (lv.n != g.n || lv.kind != g.kind || storage != g.storage || lv.x32b || lv.x64b) continue;
+    int rc = BMG_OK;
+    if (storage == 0) {
+      if (!(rc = dalloc(&lv.x64b, plane_size(lv.n))))
+        rc = cuda_check(cudaMemsetAsync(lv.x64b, 0, plane_size(lv.n) * sizeof(double), B->ws), "batched x2");
+    } else {
+      rc = galloc(&lv.x32b, lv.n, 1, B->ws);
+    }
     if (rc) return rc;
   }
   return BMG_OK;
@@ -1795,6 +1804,22 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
       if (ms * 0.5f < best_ms) {
         best_ms = ms * 0.5f;
         best.cl = cl;
+      }
+    }
+    if constexpr (sizeof(T) == 8) {
+      if (!rc && g.n >= 255) {
+        for (int shape : {0, 2}) {   // the one-wave heights with 4- and 6-row rings
+          float ms = 0;
+          rc = time_call(B->ws, [&] {
+            launch_gs_tile64_b((const LevelDesc<double, double>*)dd, g.count, g.n, shape, 0, B->ws, B->arith);
+            launch_gs_tile64_b((const LevelDesc<double, double>*)dd, g.count, g.n, shape, 1, B->ws, B->arith);
+          }, &ms);
+          if (rc) break;
+          if (ms * 0.5f < tile_ms) {
+            tile_ms = ms * 0.5f;
+            if (tile_ms < best_ms) best.tile = shape;
+          }
+        }
       }
     }
     if constexpr (sizeof(T) == 4) {
@@ -1842,9 +1867,10 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
   return BMG_OK;
 }
 
-// BMG_SMOOTHER_TILE + s / BMG_SMOOTHER_PAIR + s on a batch: every FP32 group of
+// BMG_SMOOTHER_TILE + s / BMG_SMOOTHER_PAIR + s on a batch: every group of
 // 9-point levels outside the tails sweeps with the one-pass kernel of shape s
-// (s <= 3), or runs pairs of sweeps as two-sweep passes of shape s.
+// (s <= 3; FP64 groups use the FP64 one-pass kernel), or (FP32 only) runs pairs
+// of sweeps as two-sweep passes of shape s.
 int force_batch_onepass(bmg_batch* B) {
   for (int b = 1; b <= B->bmax; ++b)
     for (auto& g : B->stages[b]) {
@@ -1913,6 +1939,8 @@ int batch_init(bmg_batch* B, const bmg_opts* o, bmg_opts* so) {
   }
   if (B->arith < BMG_ARITH_ROUNDED || B->arith > BMG_ARITH_FUSED)
     return set_error(BMG_EINVAL, "batched solves: bad arith %d", B->arith);
+  if (B->precision == BMG_FP64 && B->smoother >= BMG_SMOOTHER_PAIR)
+    return set_error(BMG_EINVAL, "batched solves: two-sweep passes are FP32 only");
   int rc = cuda_check(cudaStreamCreateWithFlags(&B->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming), "event");
   if (!rc) rc = cuda_check(cudaEventRecord(B->ev, B->user), "event");
@@ -2003,7 +2031,7 @@ int batch_finish(bmg_batch* B, int rc) {
   if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
   if (!rc) rc = cuda_check(cudaMallocHost((void**)&B->h_alldone, sizeof(int)), "pinned");
   if (!rc) rc = batch_ensure_ctl(B, 64);
-  if (!rc && B->precision != BMG_FP64 && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
+  if (!rc && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
   if (!rc && B->use_graph) rc = autotune_batch(B);
   if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "batched setup");
   return rc;

@@ -97,6 +97,24 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const L
     atomicExch(&g_strip_timeout_b, 1);
 }
 
+// FP64 one-pass sweeps of a group (strips of 56 x ty, rows copied per lane; see
+// gs_strip64_body): warp g takes strip g % wpp of problem g / wpp.
+template <int RING, bool FU>
+__global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip64_b(const LevelDesc<double, double>* __restrict__ d,
+                                                                     int count, int n, int dir, int ty) {
+  pdl_enter();
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  const int nbx = (n + 55) / 56, wpp = nbx * ((n + ty - 1) / ty);
+  const int w = threadIdx.x >> 5;
+  const long g = (long)blockIdx.x * STRIP_WARPS_B + w;
+  const int p = (int)(g / wpp), sidx = (int)(g % wpp);
+  if (p >= count) return;                         // whole warps only
+  const LevelDesc<double, double> q = d[p];
+  if (stopped(q.done)) return;
+  gs_strip64_body<RING, FU>(q.v, q.f, dir ? q.x2 : q.x, dir ? q.x : q.x2, sidx % nbx, sidx / nbx, ty,
+                            strip_smem + (size_t)w * RING * STRIP64_SLOT);
+}
+
 template <typename T, typename S>
 __global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
   pdl_enter();
@@ -331,6 +349,50 @@ static void gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape,
     case 3: strip_b_launch<S, 26, 4, true, FU>(d, count, n, dir, s); break;
     default: strip_b_launch<S, 32, 4, true, FU>(d, count, n, dir, s); break;
   }
+}
+
+// ty = 0: the smallest even strip height whose strips, over all `count`
+// problems, fit into one wave of resident warps.
+template <int RING, bool FU>
+static void strip64_b_launch(const LevelDesc<double, double>* d, int count, int n, int dir, cudaStream_t s, int ty) {
+  if (count <= 0) return;
+  constexpr size_t bytes = (size_t)STRIP_WARPS_B * RING * STRIP64_SLOT;
+  static const int resident_warps = [] {
+    cudaFuncSetAttribute(k_gs_strip64_b<RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip64_b<RING, FU>, 32 * STRIP_WARPS_B, bytes);
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS_B;
+  }();
+  const long cols = (long)count * ((n + 55) / 56);
+  if (ty <= 0) {
+    const long nby_max = resident_warps / cols > 1 ? resident_warps / cols : 1;
+    const long half = (n + 2 * nby_max - 1) / (2 * nby_max);
+    ty = (int)(2 * (half > 1 ? half : 1));
+  }
+  const long warps = cols * ((n + ty - 1) / ty);
+  pdl_launch(k_gs_strip64_b<RING, FU>, (unsigned)((warps + STRIP_WARPS_B - 1) / STRIP_WARPS_B), 32 * STRIP_WARPS_B,
+             bytes, s, d, count, n, dir, ty);
+  count_launch();
+}
+
+template <bool FU>
+static void gs_tile64_b(const LevelDesc<double, double>* d, int count, int n, int shape, int dir, cudaStream_t s) {
+  switch (shape) {
+    case 1: strip64_b_launch<4, FU>(d, count, n, dir, s, 16); break;
+    case 2: strip64_b_launch<6, FU>(d, count, n, dir, s, 0); break;
+    case 3: strip64_b_launch<4, FU>(d, count, n, dir, s, 8); break;
+    default: strip64_b_launch<4, FU>(d, count, n, dir, s, 0); break;
+  }
+}
+
+void launch_gs_tile64_b(const LevelDesc<double, double>* d, int count, int n, int shape, int dir, cudaStream_t s,
+                        int fused) {
+  if (fused)
+    gs_tile64_b<true>(d, count, n, shape, dir, s);
+  else
+    gs_tile64_b<false>(d, count, n, shape, dir, s);
 }
 
 template <typename S>

@@ -186,6 +186,10 @@ void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape,
 template <typename S>
 void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s,
                       int fused = 0);
+// Batched FP64 one-pass sweeps (dir as launch_gs_tile_b); shapes as
+// launch_gs_tile64, with the one-wave height taken over all `count` problems.
+void launch_gs_tile64_b(const LevelDesc<double, double>* d, int count, int n, int shape, int dir, cudaStream_t s,
+                        int fused = 0);
 int strip_timeouts_b();
 template <typename T, typename S>
 void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s);

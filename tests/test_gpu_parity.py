@@ -316,7 +316,9 @@ def batch_problems(sizes, std=1.0):
 
 @pytest.mark.parametrize("precision,nbf,smoother", [("fp64", None, "auto"), ("fp32", 0, "auto"), ("bf16", 2, "auto"),
                                                     ("fp32", 0, "tile0"), ("fp32", 0, "tile3"), ("bf16", 2, "tile2"),
-                                                    ("fp32", 0, "pair0"), ("bf16", 2, "pair3")])
+                                                    ("fp32", 0, "pair0"), ("bf16", 2, "pair3"), ("fp64", None, "tile0"),
+                                                    ("fp64", None, "tile1"), ("fp64", None, "tile2"),
+                                                    ("fp64", None, "tile3")])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batched_matches_oracle_per_problem(bmg, precision, nbf, smoother, graph):
     """Uneven sizes (several problems per size, sizes from 3 to 255, ragged
@@ -337,6 +339,58 @@ def test_batched_matches_oracle_per_problem(bmg, precision, nbf, smoother, graph
         assert np.array_equal(bx.at(host(xs[k]), 0, 0), bx.at(xw, 0, 0)), k
         check_history(B.history(k), hw)
     B.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (1, 2), (3, 0), (0, 3), (2, 2)])
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+def test_batched_fp64_one_pass_any_sweep_counts(bmg, nu1, nu2, arith):
+    """The batched FP64 one-pass sweep moves each iterate between x and a
+    second array; odd and even sweep counts on both sides of the coarse
+    correction must leave the oracle's iterate in the caller's x."""
+    sizes = [255, 127, 511, 63, 255]
+    probs = batch_problems(sizes)
+    B = bmg.Batch(9, [dev(p[1]) for p in probs], nu1=nu1, nu2=nu2, smoother="tile0", arith=arith)
+    xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-14, maxit=4)
+    for k, (kind, planes, f) in enumerate(probs):
+        xw, hw = bx.solve(bx.setup(kind, planes, arith=arith), f, tol=1e-14, maxit=4, nu1=nu1, nu2=nu2)
+        assert its[k] == len(hw) - 1, k
+        assert np.array_equal(bx.at(host(xs[k]), 0, 0), bx.at(xw, 0, 0)), k
+        check_history(B.history(k), hw)
+    B.close()
+
+
+def test_batched_fp64_tuner_and_right_hand_sides(bmg):
+    """Autotuned FP64 batch (row kernel or one-pass shape per stage) and an
+    FP64 batch of right-hand sides with the one-pass kernel forced: both equal
+    the solo solves bit for bit."""
+    probs = batch_problems([511, 255, 255, 1023])
+    B = bmg.Batch(9, [dev(p[1]) for p in probs])
+    xs, its, rrs, ok = B.solve([dev(p[2]) for p in probs], tol=1e-10, maxit=100)
+    assert ok
+    assert B.tuned_cluster(8) in (1, 2, 4, 8, 16, 17, 18, 19)   # n = 1023
+    for k, (kind, planes, f) in enumerate(probs):
+        h = bmg.Hierarchy(kind, dev(planes))
+        x, it, rr, okk = h.solve(dev(f), tol=1e-10, maxit=100)
+        assert it == its[k] and torch.equal(x, xs[k]) and h.history() == B.history(k)
+        h.close()
+    B.close()
+    kind, planes, f = problem("lognormal", 511)
+    h = bmg.Hierarchy(kind, dev(planes))
+    rhs = [dev(w.rhs_uniform(511, 500 + q)) for q in range(3)]
+    R = bmg.Batch.from_hierarchy(h, 3, smoother="tile2")
+    xs, its, rrs, ok = R.solve(rhs, tol=1e-10, maxit=100)
+    assert ok
+    for q, r in enumerate(rhs):
+        x, it, rr, okk = h.solve(r, tol=1e-10, maxit=100)
+        assert okk and it == its[q] and torch.equal(x, xs[q]) and h.history() == R.history(q)
+    R.close()
+    h.close()
+
+
+def test_batched_fp64_pair_is_rejected(bmg):
+    probs = batch_problems([63, 127])
+    with pytest.raises(bmg.BmgError):
+        bmg.Batch(9, [dev(p[1]) for p in probs], smoother="pair0")
 
 
 @pytest.mark.parametrize("smoother", ["auto", "pair3"])
