@@ -314,6 +314,78 @@ def test_cholesky_rejects_indefinite():
 # Smoother and cycle (A5-A9)
 # --------------------------------------------------------------------------
 
+def poisson5_dense(n):
+    """Dense 5-point Laplacian (4 on the diagonal, -1 to the four neighbours),
+    unknown p = (j - 1) n + (i - 1), as a Kronecker sum of 1D second differences."""
+    T = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    return np.kron(np.eye(n), T) + np.kron(T, np.eye(n))
+
+
+# Colour order of the sweeps (Fig. 1): four colours by (i mod 2, j mod 2) for
+# the 9-point stencil, (odd, odd), (even, odd), (odd, even), (even, even);
+# red (i + j even) then black for the 5-point one.
+ORDER9 = [[(1, 1)], [(0, 1)], [(1, 0)], [(0, 0)]]
+ORDER5 = [[(1, 1), (0, 0)], [(0, 1), (1, 0)]]
+
+
+def pointwise_gauss_seidel(A, x, f, n, order):
+    """Textbook Gauss-Seidel on the dense matrix: the points of each colour in
+    turn, each x_p = (f_p - sum_{q != p} a_pq x_q) / a_pp from the latest values."""
+    u, b = interior(x).reshape(-1).copy(), interior(f).reshape(-1)
+    for group in order:
+        for j in range(1, n + 1):
+            for i in range(1, n + 1):
+                if (i % 2, j % 2) in group:
+                    p = (j - 1) * n + i - 1
+                    u[p] = (b[p] - A[p] @ u + A[p, p] * u[p]) / A[p, p]
+    return u
+
+
+def smoother_case(kind, n=15):
+    if kind == 5:
+        return w.poisson5(n), poisson5_dense(n)
+    k = w.binary_blocks(n, 4, 1.0, 1e4, 5)
+    return w.fe9_from_cells(k), q1_assembled_matrix(k)
+
+
+@pytest.mark.parametrize("kind", [5, 9])
+def test_sweep_is_pointwise_gauss_seidel_in_the_stated_colour_order(kind):
+    """One sweep equals the dense point-by-point Gauss-Seidel of the stated
+    colour order (to rounding); the reversed order is far from it, so the pin
+    fixes the order as well as the update."""
+    n = 15
+    planes, A = smoother_case(kind, n)
+    lev = bx.setup(kind, planes)[0]
+    x0, f = w.rhs_uniform(n, 31), w.rhs_uniform(n, 32)
+    x = x0.copy()
+    bx.gs_sweep(kind, lev.planes, lev.dinv, x, f)
+    order = ORDER5 if kind == 5 else ORDER9
+    want = pointwise_gauss_seidel(A, x0, f, n, order)
+    scale = np.abs(want).max()
+    assert np.abs(interior(x).reshape(-1) - want).max() <= 1e-12 * scale
+    other = pointwise_gauss_seidel(A, x0, f, n, order[::-1])
+    assert np.abs(other - want).max() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("kind", [5, 9])
+def test_colour_pass_solves_its_own_equations(kind):
+    """After one colour's pass the residual of the dense system vanishes (to
+    rounding) on that colour's points, and no other point has moved."""
+    n = 15
+    planes, A = smoother_case(kind, n)
+    lev = bx.setup(kind, planes)[0]
+    x, f = w.rhs_uniform(n, 33), w.rhs_uniform(n, 34)
+    J, I = np.meshgrid(np.arange(1, n + 1), np.arange(1, n + 1), indexing="ij")
+    for pi, pj in (ORDER5[0] + ORDER5[1] if kind == 5 else [g[0] for g in ORDER9]):
+        before = x.copy()
+        bx.gs_colour(lev.planes, lev.dinv, x, f, pi, pj)
+        mine = ((I % 2 == pi) & (J % 2 == pj)).reshape(-1)
+        u = interior(x).reshape(-1)
+        r = interior(f).reshape(-1) - A @ u
+        assert np.abs(r[mine]).max() <= 1e-12 * np.abs(A).max() * np.abs(u).max()
+        assert np.array_equal(u[~mine], interior(before).reshape(-1)[~mine])
+        assert not np.array_equal(u[mine], interior(before).reshape(-1)[mine])
+
 @pytest.mark.parametrize("n", [3, 7, 15])
 @pytest.mark.parametrize("case", ["binary", "lognormal"])
 def test_solution_matches_dense_direct_solve(n, case):
