@@ -961,11 +961,34 @@ __device__ __forceinline__ void coarse_solve_body(int n, const double* __restric
 }
 
 // ---- iterative refinement ------------------------------------------------------------------
+// s * fl64(e) for a positive normal power of two s (the refinement scales).
+// The product is exact, so it is formed from the bit fields: the float's
+// exponent, re-biased and raised by log2(s), and its mantissa widened. Only
+// when e is subnormal, infinite or NaN, when the product is not a normal
+// double, or when s is not such a power of two, does it take the FP64 multiply.
+// Both routes give the same bits; the bit route spares the FP64 pipe two
+// operations.
+__device__ __forceinline__ double pow2_times_widened(double s, float e) {
+  const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+  const int es = (int)((sb >> 52) & 0x7ff);
+  if (!(sb >> 63) && es != 0 && es != 0x7ff && (sb & 0xfffffffffffffULL) == 0) {
+    const unsigned u = __float_as_uint(e);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);   // s * (+-0) = +-0
+    const int ef = (int)((u >> 23) & 0xff);
+    const int ed = ef - 127 + es;   // (ef - 127) + (es - 1023) + 1023
+    if (ef != 0 && ef != 0xff && ed > 0 && ed < 0x7ff)
+      return __longlong_as_double(
+          (long long)(sign | ((unsigned long long)ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+  }
+  return rmul(s, (double)e);
+}
+
 __device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, const float* __restrict__ e32,
                                                const Ctl* ctl, int i, int j) {
   if (i < 1 || j < 1 || i > n || j > n) return;
   size_t p = (size_t)j * (n + 2) + i;
-  x[p] = radd(x[p], rmul(ctl->scale_applied, (double)e32[p]));
+  x[p] = radd(x[p], pow2_times_widened(ctl->scale_applied, e32[p]));
 }
 
 // r = f - A x (FP64), r32 = fl32(r / scale_next), e32 = 0, partial sums of r^2.

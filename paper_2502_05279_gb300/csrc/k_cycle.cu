@@ -624,7 +624,7 @@ namespace {
 constexpr int FBX = 32, FBY = 8;
 
 __device__ __forceinline__ double zval(const double* z, const float* z32, double s, size_t p) {
-  return z32 ? rmul(s, (double)z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
+  return z32 ? pow2_times_widened(s, z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
 }
 
 // An inner product over the grid in the canonical order; step(acc, p) adds
