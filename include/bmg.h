@@ -282,9 +282,9 @@ int bmg_time_cycles_batched(bmg_batch* b, const double* const* rhs, double* cons
 
 /* Kernel launches issued for the batch since setup; the Gauss-Seidel kernel
  * the autotuner chose for stage `stage` (0 = coarsest): the row kernel's
- * cluster size, BMG_TILE_SWEEP + s for the one-pass kernel of shape s (FP32
- * stages with n >= 255; pairs of sweeps may then run as two-sweep passes),
- * or 0 (not tuned). */
+ * cluster size, BMG_TILE_SWEEP + s for the one-pass kernel of shape s (stages
+ * with n >= 255, FP64 or FP32/BF16; in FP32/BF16 stages pairs of sweeps may then
+ * run as two-sweep passes), or 0 (not tuned). */
 long long bmg_batched_launch_count(const bmg_batch* b);
 int bmg_batched_tuned_cluster(const bmg_batch* b, int stage);
 
