@@ -186,6 +186,18 @@ int dalloc(T** p, size_t count) {
   return BMG_OK;
 }
 
+// dalloc, zeroed on stream s; nothing stays allocated when either step fails.
+template <typename T>
+int dalloc_zero(T** p, size_t count, cudaStream_t s) {
+  int rc = dalloc(p, count);
+  if (!rc && count) rc = cuda_check(cudaMemsetAsync(*p, 0, count * sizeof(T), s), "cudaMemsetAsync");
+  if (rc) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  return rc;
+}
+
 // FP32 / BF16 level arrays: `planes` planes of level size n, plane_stride32(n)
 // elements apart, with STRIP_GUARD zeroed elements before the first and after
 // every plane; *p is the first plane (256-byte aligned).  Freed by gfree.
@@ -194,8 +206,7 @@ int galloc(T** p, int n, int planes, cudaStream_t s) {
   *p = nullptr;
   const size_t count = STRIP_GUARD + planes * plane_stride32(n);
   T* raw = nullptr;
-  CK(cudaMalloc((void**)&raw, count * sizeof(T)));
-  CK(cudaMemsetAsync(raw, 0, count * sizeof(T), s));
+  if (int e = dalloc_zero(&raw, count, s)) return e;
   *p = raw + STRIP_GUARD;
   return BMG_OK;
 }
@@ -369,8 +380,7 @@ int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* 
   const int base = rows_cluster<T>(v.n);
   size_t ps = plane_size(v.n);
   T* scratch = nullptr;
-  CK(cudaMalloc((void**)&scratch, 2 * ps * sizeof(T)));
-  CK(cudaMemsetAsync(scratch, 0, 2 * ps * sizeof(T), s));
+  if (int e = dalloc_zero(&scratch, 2 * ps, s)) return e;
   float best = 1e30f;
   int best_cl = base, rc = BMG_OK;
   for (int cl = base; cl <= 8 && !rc; cl *= 2) {
@@ -500,8 +510,7 @@ int tune_tile64(const StencilView<double, double>& v, cudaStream_t s, int* best_
   }
   const size_t ps = plane_size(v.n);
   double* scratch = nullptr;   // x, x', f
-  CK(cudaMalloc((void**)&scratch, 3 * ps * sizeof(double)));
-  CK(cudaMemsetAsync(scratch, 0, 3 * ps * sizeof(double), s));
+  if (int e = dalloc_zero(&scratch, 3 * ps, s)) return e;
   const double* f = scratch + 2 * ps;
   int best_shape = 0, rc = BMG_OK;
   float best = 1e30f;
@@ -532,8 +541,7 @@ int tune_level64(Level& L, cudaStream_t s) {
   if (!rc) rc = tune_tile64(view64(L), s, &shape, &ms_tile);
   if (rc) return rc;
   if (ms_tile < ms_rows) {
-    if ((rc = dalloc(&L.x64b, plane_size(L.n)))) return rc;
-    CK(cudaMemsetAsync(L.x64b, 0, plane_size(L.n) * sizeof(double), s));
+    if ((rc = dalloc_zero(&L.x64b, plane_size(L.n), s))) return rc;
     L.tile64 = shape;
   }
   return BMG_OK;
@@ -580,9 +588,7 @@ int force_tile(bmg_hierarchy* h) {
     Level& L = h->lv[l];
     if (L.kind != 9) continue;
     if (h->precision == BMG_FP64) {
-      int rc = dalloc(&L.x64b, plane_size(L.n));
-      if (rc) return rc;
-      CK(cudaMemsetAsync(L.x64b, 0, plane_size(L.n) * sizeof(double), h->ws));
+      if (int rc = dalloc_zero(&L.x64b, plane_size(L.n), h->ws)) return rc;
       L.tile64 = h->smoother - BMG_SMOOTHER_TILE;
       continue;
     }
@@ -1764,8 +1770,7 @@ int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
     if (lv.n != g.n || lv.kind != g.kind || storage != g.storage || lv.x32b || lv.x64b) continue;
     int rc = BMG_OK;
     if (storage == 0) {
-      if (!(rc = dalloc(&lv.x64b, plane_size(lv.n))))
-        rc = cuda_check(cudaMemsetAsync(lv.x64b, 0, plane_size(lv.n) * sizeof(double), B->ws), "batched x2");
+      rc = dalloc_zero(&lv.x64b, plane_size(lv.n), B->ws);
     } else {
       rc = galloc(&lv.x32b, lv.n, 1, B->ws);
     }
@@ -1793,8 +1798,10 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
       d[k].done = nullptr;
     }
     LevelDesc<T, S>* dd = nullptr;
-    CK(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count));
-    CK(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws));
+    rc = cuda_check(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count), "tuning descriptors");
+    if (!rc)
+      rc = cuda_check(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws),
+                      "tuning descriptors");
     GroupChoice best{base, -1, -1};
     float best_ms = 1e30f, tile_ms = 1e30f;
     for (int cl = base; cl <= 8 && !rc; cl *= 2) {
