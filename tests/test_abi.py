@@ -58,3 +58,35 @@ def test_binding_imports_and_reports_errors_without_gpu(libpath):
         assert "smoother" in bmg.lib.bmg_last_error().decode()
     assert bmg.lib.bmg_solve(None, None, None, 1e-10, 10, None, None) == bmg._lib.BMG_EINVAL
     bmg.lib.bmg_free(None)
+
+
+def test_batched_setup_validates_on_the_host(libpath):
+    """bmg_setup_batched rejects bad batches before any device work: no
+    problems, a size that is not 2^m - 1, mixed stencil kinds, Krylov
+    acceleration, line relaxation, one-pass shapes above 3, two-sweep passes
+    in FP64, and an unknown arithmetic mode; the handle stays NULL."""
+    import paper_2502_05279_gb300 as bmg
+    L = bmg._lib
+    B = ctypes.c_void_p()
+    nine = (L.Stencil * 2)(L.Stencil(9, ctypes.c_void_p(16)), L.Stencil(9, ctypes.c_void_p(32)))
+    mixed = (L.Stencil * 2)(L.Stencil(9, ctypes.c_void_p(16)), L.Stencil(5, ctypes.c_void_p(32)))
+    sizes = (ctypes.c_int * 2)(63, 127)
+
+    def opts(**kw):
+        o = L.Opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return ctypes.byref(o)
+
+    cases = [(0, nine, sizes, None, "bad argument"),
+             (2, nine, (ctypes.c_int * 2)(63, 100), None, "2^m - 1"),
+             (2, mixed, sizes, None, "differ in kind"),
+             (2, nine, sizes, opts(krylov=1), "stationary"),
+             (2, nine, sizes, opts(smoother=12), "line relaxation"),
+             (2, nine, sizes, opts(smoother=6), "bad smoother"),
+             (2, nine, sizes, opts(smoother=8), "FP32 only"),
+             (2, nine, sizes, opts(arith=3), "bad arith")]
+    for nprob, st, n, o, msg in cases:
+        assert L.lib.bmg_setup_batched(nprob, st, n, o, ctypes.byref(B)) == L.BMG_EINVAL
+        assert msg in L.lib.bmg_last_error().decode()
+        assert B.value is None
