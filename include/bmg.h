@@ -19,6 +19,10 @@
  * SE(p) = NW(p+x-y).  A 5-point stencil (kind 5) passes three planes O, W, S.
  * Couplings from an interior point to a ghost point are not entries of A; the
  * library ignores (zeroes) them and the ghost ring of every plane.
+ * Natural (Neumann) sides need no option: a stencil whose couplings across a
+ * side vanish (for -div(k grad u), zero k in the cells beyond it) has rows
+ * with no Dirichlet term there, and the solver treats it like any other
+ * stencil.  The all-Neumann (singular) operator is not supported.
  *
  * General sizes.  bmg_setup also takes any nx x ny grid (1 <= nx, ny <= 65535):
  * the caller's arrays are then (ny+2) x (nx+2), row-major with row length nx+2,
