@@ -11,8 +11,11 @@ Modules:
              Cholesky, V(2,1) and the solve loop.
   mixed   -- FP32 / BF16-stencil V(2,1) inside FP64 iterative refinement
              (rounding emulated with numpy float32 and bit manipulation).
-  mlp     -- the learned-interpolation network in FP64 with a hand-written
-             backward pass, and the learned prolongation built from it.
+  learned -- the learned-interpolation network in FP64 with a hand-written
+             backward pass, the learned prolongation built from it, and the
+             training losses with their gradients.
+  fused   -- element-wise fused multiply-add (C99 fma / fmaf from fma.c,
+             compiled with gcc) for the fused arithmetic mode.
 
 The paper (Nytko et al., "Teaching an old dog new tricks", arXiv 2502.05279)
 states BoxMG through its kernel sequence (Fig. 1) and the restriction loop

@@ -2,6 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
+Pins (tests/test_learned_oracle.py): zero logits reproduce Dendy's weights;
+any logits keep constants on zero-row-sum rows; the basis energy equals the
+Galerkin diagonal; the test-vector energy is the dense quadratic form; the
+gradients equal central finite differences.  What training gains over Dendy
+has no number in the paper: parity unpinned for that claim.
+
 The paper has no learned component; this follows the stated reading of the
 extension:
 

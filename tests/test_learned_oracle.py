@@ -136,3 +136,22 @@ def test_tv_network_gradient_matches_fd():
         tm[k] -= h
         fd = (ln.model_tv_loss_grad(tp, planes, vecs, e_ref)[0] - ln.model_tv_loss_grad(tm, planes, vecs, e_ref)[0]) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(abs(fd), 1e-4), k
+
+
+@pytest.mark.parametrize("scale", [0.5, 3.0])
+def test_learned_weights_keep_constants_for_any_logits(scale):
+    """For a zero-row-sum operator, any logits keep each edge point's Dendy
+    weight sum (1 there) and the centre rows solve their local equation, so
+    interpolating a constant gives that constant at every fine point whose
+    row is zero-sum and sees only interior coarse points, while the weights
+    themselves differ from Dendy's."""
+    n, nc = 63, 31
+    planes = hc_planes(n, seed=9, block=4)
+    delta = w.normal(12, nc * nc * 4).reshape(nc * nc, 4) * scale
+    ci = ln.learned_interp(planes, delta)
+    assert np.abs(ci - bx.dendy_interp(planes)).max() > 1e-2
+    ec = np.zeros((nc + 2, nc + 2))
+    ec[1:nc + 1, 1:nc + 1] = 1.0
+    x = np.zeros((n + 2, n + 2))
+    bx.interp_correct(ci, ec, x)
+    assert np.abs(x[3:n - 1, 3:n - 1] - 1.0).max() <= 1e-12
