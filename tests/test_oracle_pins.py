@@ -527,6 +527,31 @@ def test_iterative_refinement_reaches_fp64_accuracy(bf16):
     assert abs(len(hist) - len(h64)) <= 3
 
 
+@pytest.mark.parametrize("case", ["binary", "lognormal", "poisson"])
+def test_fp32_cycle_is_the_fp64_cycle_to_fp32_rounding(case):
+    """One FP32 V(2,1) cycle from zero is the FP64 cycle to FP32 rounding
+    (1e-5 relative); with BF16-stored stencils on the two finest levels it
+    moves by the BF16 coefficient rounding (between 1e-5 and 1e-2), and not at
+    all when every coefficient is a BF16 number (Poisson: 4 and -1)."""
+    if case == "binary":
+        kind, planes, f = w.binary_contrast_problem(63, 8, seed_k=2, seed_f=3)
+    elif case == "lognormal":
+        kind, planes, f = 9, w.fe9_from_cells(w.lognormal_cells(63, 2.0, 8.0, 4)), w.rhs_uniform(63, 5)
+    else:
+        kind, planes, f = w.poisson_problem(63, 1)
+    levels = bx.setup(kind, planes)
+    e64 = np.zeros_like(f)
+    bx.vcycle(levels, 0, e64, f, 2, 1)
+    e32 = mx.inner_cycle(mx.lower(levels, 0), f.astype(np.float32))
+    ebf = mx.inner_cycle(mx.lower(levels, 2), f.astype(np.float32))
+    rel = lambda e: np.linalg.norm(e.astype(np.float64) - e64) / np.linalg.norm(e64)
+    assert e32.dtype == np.float32 and rel(e32) <= 1e-5
+    if case == "poisson":
+        assert np.array_equal(ebf, e32)
+    else:
+        assert 1e-5 < rel(ebf) <= 1e-2
+
+
 def test_ir_scale_is_power_of_two():
     for rho in (1.0, 0.75, 3e-11, 123456.0):
         s = mx.scale_of(rho)
