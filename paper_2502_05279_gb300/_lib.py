@@ -137,6 +137,24 @@ def _n_of(t: torch.Tensor) -> int:
     return t.shape[-1] - 2
 
 
+def _need(t: torch.Tensor, count: int, name: str) -> torch.Tensor:
+    """Refuse a tensor holding fewer values than the library reads or writes
+    through its pointer: the C ABI takes bare pointers, so the sizes are
+    checked here."""
+    if t is not None and t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} values; {count} are needed")
+    return t
+
+
+def _planes(kind: int) -> int:
+    """Stencil planes a kernel of this kind reads: O, W, S (5-point) or also SW, NW."""
+    return 5 if kind == 9 else 3
+
+
+def _grid(n: int) -> int:
+    return (n + 2) * (n + 2)
+
+
 class Hierarchy:
     """A BoxMG hierarchy built on the GPU (bmg_setup) and its solver (bmg_solve)."""
 
@@ -146,6 +164,8 @@ class Hierarchy:
                  arith: str = "rounded"):
         nx, ny = coef.shape[-1] - 2, coef.shape[-2] - 2     # any size; 2^m - 1 squares natively
         self.nx, self.ny, self.kind, self.precision, self.arith = nx, ny, kind, precision, arith
+        if kind in (5, 9):
+            _need(coef, _planes(kind) * (nx + 2) * (ny + 2), "coef")
         st = Stencil(kind, _ptr(coef, name="coef"))
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
                  int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
@@ -159,6 +179,7 @@ class Hierarchy:
         """Returns (x, iterations, relative residual, converged)."""
         if x is None:
             x = torch.zeros_like(rhs)
+        self._need_grid(rhs, x)
         it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
         rc = _check(lib.bmg_solve(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), tol, maxit,
                                   ctypes.byref(it), ctypes.byref(rr)), allow=(BMG_ENOTCONV,))
@@ -166,6 +187,7 @@ class Hierarchy:
 
     def time_cycles(self, rhs: torch.Tensor, x: torch.Tensor, cycles: int) -> float:
         """Device milliseconds of `cycles` solve iterations (no convergence test)."""
+        self._need_grid(rhs, x)
         ms = ctypes.c_double(0.0)
         _check(lib.bmg_time_cycles(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), cycles, ctypes.byref(ms)))
         return ms.value
@@ -173,10 +195,16 @@ class Hierarchy:
     def profile(self, rhs: torch.Tensor, x: torch.Tensor, cycles: int):
         """Per (level, kernel, fp32) device time of `cycles` iterations: a list of
         dicts with keys level, kernel, fp32, launches, ms."""
+        self._need_grid(rhs, x)
         rows = (ProfRow * 256)()
         cnt = _check_size(lib.bmg_profile(self._h, _ptr(rhs, name="rhs"), _ptr(x, name="x"), cycles, rows, 256))
         return [dict(level=r.level, kernel=KERNEL_NAMES[r.kernel], fp32=bool(r.fp32), launches=r.launches, ms=r.ms)
                 for r in rows[:cnt]]
+
+    def _need_grid(self, rhs, x):
+        """rhs and x in the caller's (ny+2) x (nx+2) layout."""
+        _need(rhs, (self.nx + 2) * (self.ny + 2), "rhs")
+        _need(x, (self.nx + 2) * (self.ny + 2), "x")
 
     def history(self):
         cnt = lib.bmg_history(self._h, None, 0)
@@ -204,6 +232,7 @@ class Hierarchy:
         return out
 
     def inner_cycle(self, r32: torch.Tensor) -> torch.Tensor:
+        _need(r32, _grid(self.n), "r32")
         e = torch.empty_like(r32)
         _check(lib.bmg_inner_cycle(self._h, _ptr(r32, torch.float32, "r32"), _ptr(e, torch.float32, "e32")))
         return e
@@ -248,6 +277,9 @@ class Batch:
         self.ns = [_n_of(c) for c in coefs]
         self._coefs = list(coefs)
         nprob = len(coefs)
+        if kind in (5, 9):
+            for c, n in zip(coefs, self.ns):
+                _need(c, _planes(kind) * _grid(n), "coef")
         sts = (Stencil * nprob)(*[Stencil(kind, _ptr(c, name="coef")) for c in coefs])
         ns = (ctypes.c_int * nprob)(*self.ns)
         o = Opts(_PREC[precision], 0, 0, nu1, nu2, inner_cycles, bf16_levels, int(use_graph), 0, None, _stream(),
@@ -273,17 +305,22 @@ class Batch:
         return self
 
     def _ptrs(self, ts, name):
+        """One pointer per problem; each tensor must hold its problem's grid."""
+        if len(ts) != len(self.ns):
+            raise ValueError(f"{len(ts)} {name} tensors for {len(self.ns)} problems")
+        for t, n in zip(ts, self.ns):
+            _need(t, _grid(n), name)
         return (ctypes.c_void_p * len(ts))(*[_ptr(t, name=name).value for t in ts])
 
     def solve(self, rhs, xs=None, tol: float = 1e-10, maxit: int = 100):
         """Returns (xs, iterations per problem, relative residual per problem, all converged)."""
         if xs is None:
             xs = [torch.zeros_like(r) for r in rhs]
+        prhs, pxs = self._ptrs(rhs, "rhs"), self._ptrs(xs, "x")
         nprob = len(rhs)
         it = (ctypes.c_int * nprob)()
         rr = (ctypes.c_double * nprob)()
-        rc = _check(lib.bmg_solve_batched(self._h, self._ptrs(rhs, "rhs"), self._ptrs(xs, "x"), tol, maxit, it, rr),
-                    allow=(BMG_ENOTCONV,))
+        rc = _check(lib.bmg_solve_batched(self._h, prhs, pxs, tol, maxit, it, rr), allow=(BMG_ENOTCONV,))
         return xs, list(it), list(rr), rc == BMG_OK
 
     def history(self, p: int):
@@ -363,6 +400,7 @@ class Mlp:
     def infer(self, coef):
         n = _n_of(coef)
         nc = (n - 1) // 2
+        _need(coef, 5 * _grid(n), "coef")
         out = torch.empty((nc * nc, 4), dtype=torch.float32, device=coef.device)
         _check(lib.bmg_mlp_infer(self._h, n, _ptr(coef, name="coef"), _ptr(out, torch.float32, "delta"), _stream()))
         return out
@@ -382,6 +420,8 @@ class Mlp:
 def learned_interp(coef, delta):
     n = _n_of(coef)
     nc = (n - 1) // 2
+    _need(coef, 5 * _grid(n), "coef")
+    _need(delta, nc * nc * 4, "delta")
     ci = torch.empty((8, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
     _check(lib.bmg_learned_interp(n, _ptr(coef), _ptr(delta, torch.float32, "delta"), _ptr(ci), _stream()))
     return ci
@@ -393,6 +433,14 @@ def fill_uniform(n: int, seed: int, device="cuda"):
     return x
 
 
+def _need_level(kind: int, coef, f, x):
+    """One level's stencil (the planes its kind reads), right-hand side and iterate."""
+    n = _n_of(coef)
+    _need(coef, _planes(kind) * _grid(n), "coef")
+    _need(f, _grid(n), "f")
+    _need(x, _grid(n), "x")
+
+
 def _check_size(v: int) -> int:
     if v < 0:
         _check(v)
@@ -402,6 +450,7 @@ def _check_size(v: int) -> int:
 def dendy_interp(coef: torch.Tensor) -> torch.Tensor:
     n = _n_of(coef)
     nc = (n - 1) // 2
+    _need(coef, 5 * _grid(n), "coef")
     ci = torch.empty((8, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
     _check(lib.bmg_dendy_interp(n, _ptr(coef), _ptr(ci), _stream()))
     return ci
@@ -410,18 +459,22 @@ def dendy_interp(coef: torch.Tensor) -> torch.Tensor:
 def rap(coef: torch.Tensor, ci: torch.Tensor) -> torch.Tensor:
     n = _n_of(coef)
     nc = (n - 1) // 2
+    _need(coef, 5 * _grid(n), "coef")
+    _need(ci, 8 * _grid(nc), "ci")
     out = torch.empty((5, nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
     _check(lib.bmg_rap(n, _ptr(coef), _ptr(ci), _ptr(out), _stream()))
     return out
 
 
 def relax(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
+    _need_level(kind, coef, f, x)
     _check(lib.bmg_relax(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), sweeps, _stream()))
     return x
 
 
 def relax_line(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
     """Zebra x-line Gauss-Seidel sweeps in place on x (bmg_relax_line)."""
+    _need_level(kind, coef, f, x)
     work = torch.empty_like(x)
     _check(lib.bmg_relax_line(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), _ptr(work), sweeps, _stream()))
     return x
@@ -430,12 +483,18 @@ def relax_line(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, 
 def resid_restrict(kind: int, coef, ci, x, f) -> torch.Tensor:
     n = _n_of(coef)
     nc = (n - 1) // 2
+    _need_level(kind, coef, f, x)
+    _need(ci, 8 * _grid(nc), "ci")
     fc = torch.empty((nc + 2, nc + 2), dtype=torch.float64, device=coef.device)
     _check(lib.bmg_resid_restrict(n, kind, _ptr(coef), _ptr(ci), _ptr(x), _ptr(f), _ptr(fc), _stream()))
     return fc
 
 
 def interp_correct(ci, ec, x) -> torch.Tensor:
+    nc = (_n_of(x) - 1) // 2
+    _need(x, _grid(_n_of(x)), "x")
+    _need(ci, 8 * _grid(nc), "ci")
+    _need(ec, _grid(nc), "ec")
     _check(lib.bmg_interp_correct(_n_of(x), _ptr(ci), _ptr(ec), _ptr(x), _stream()))
     return x
 
@@ -443,6 +502,7 @@ def interp_correct(ci, ec, x) -> torch.Tensor:
 def residual(kind: int, coef, x, f, want_r: bool = True):
     """Returns (r or None, ||r||)."""
     n = _n_of(coef)
+    _need_level(kind, coef, f, x)
     r = torch.empty_like(f) if want_r else None
     nrm = ctypes.c_double(0.0)
     _check(lib.bmg_residual(n, kind, _ptr(coef), _ptr(x), _ptr(f), _ptr(r) if want_r else None,
@@ -452,12 +512,17 @@ def residual(kind: int, coef, x, f, want_r: bool = True):
 
 def coarse_factor(coef: torch.Tensor) -> torch.Tensor:
     n = _n_of(coef)
+    _need(coef, 5 * _grid(n), "coef")
     L = torch.empty((n * n, n * n), dtype=torch.float64, device=coef.device)
     _check(lib.bmg_coarse_factor(n, _ptr(coef), _ptr(L), _stream()))
     return L
 
 
 def coarse_solve(L: torch.Tensor, f: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    n = _n_of(f)
+    _need(f, _grid(n), "f")
+    _need(x, _grid(n), "x")
+    _need(L, n * n * n * n, "L")
     _check(lib.bmg_coarse_solve(_n_of(f), _ptr(L), _ptr(f), _ptr(x), _stream()))
     return x
 

@@ -90,3 +90,40 @@ def test_batched_setup_validates_on_the_host(libpath):
         assert L.lib.bmg_setup_batched(nprob, st, n, o, ctypes.byref(B)) == L.BMG_EINVAL
         assert msg in L.lib.bmg_last_error().decode()
         assert B.value is None
+
+
+def test_binding_checks_sizes_before_the_library(libpath):
+    """The C ABI takes bare pointers, so the binding refuses tensors smaller
+    than what the library would read or write through them, and too few or
+    too many per-problem tensors for a batch, before any call."""
+    import torch
+    import paper_2502_05279_gb300 as bmg
+    z = lambda *s: torch.zeros(s, dtype=torch.float64)
+    with pytest.raises(ValueError, match="coef holds"):
+        bmg.Hierarchy(9, z(3, 17, 17))                 # a 9-point stencil needs 5 planes
+    with pytest.raises(ValueError, match="CUDA"):
+        bmg.Hierarchy(5, z(3, 17, 17))                 # sizes fine: stops at the device check
+    h = bmg.Hierarchy.__new__(bmg.Hierarchy)
+    h.nx, h.ny, h.n, h._h = 20, 10, 31, None
+    with pytest.raises(ValueError, match="rhs holds 252 values; 264 are needed"):
+        h.solve(z(12, 21))
+    with pytest.raises(ValueError, match="x holds"):
+        h.time_cycles(z(12, 22), z(12, 21), 1)
+    with pytest.raises(ValueError, match="r32 holds"):
+        h.inner_cycle(torch.zeros((33, 32), dtype=torch.float32))
+    b = bmg.Batch.__new__(bmg.Batch)
+    b.ns, b._h = [7, 15], None
+    with pytest.raises(ValueError, match="1 rhs tensors for 2 problems"):
+        b.solve([z(9, 9)])
+    with pytest.raises(ValueError, match="rhs holds 81 values; 289 are needed"):
+        b.time_cycles([z(9, 9), z(9, 9)], [z(9, 9), z(17, 17)], 1)
+    with pytest.raises(ValueError, match="coef holds"):
+        bmg.relax(9, z(3, 9, 9), z(9, 9), z(9, 9))
+    with pytest.raises(ValueError, match="f holds"):
+        bmg.residual(5, z(3, 9, 9), z(9, 9), z(9, 8))
+    with pytest.raises(ValueError, match="ci holds"):
+        bmg.rap(z(5, 9, 9), z(8, 4, 4))
+    with pytest.raises(ValueError, match="ec holds"):
+        bmg.interp_correct(z(8, 5, 5), z(4, 5), z(9, 9))
+    with pytest.raises(ValueError, match="L holds"):
+        bmg.coarse_solve(z(8, 10), z(5, 5), z(5, 5))   # n = 3: L is 9 x 9
