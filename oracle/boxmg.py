@@ -27,8 +27,9 @@ never as code):
   the same order, but each product that is added to or subtracted from a
   running sum is one fused multiply-add, fma(a, b, s) = a b + s rounded once
   (oracle/fused.py): the row sums of residual, Gauss-Seidel and A p, the
-  weighted terms of restriction and interpolation, the squared-norm and
-  inner-product accumulations and the flexible-CG vector updates.  Products
+  weighted terms of restriction and interpolation and the flexible-CG
+  vector updates.  Norms and inner products are plain sums (numpy) in both
+  modes: their definition has no arithmetic mode.  Products
   that stand alone (the first term of a sum, s * d) and the coincident
   restriction term keep their single rounding; setup, line relaxation and the
   coarsest solve are the same in both modes.
@@ -203,68 +204,21 @@ def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray, fused: bool = Fal
     return r
 
 
-REDUCE_BLOCKS = 1024
-REDUCE_THREADS = 256
-
-
-def ordered_sum(v: np.ndarray, w: np.ndarray | None = None) -> float:
-    """Sum of an (n, n) array of interior values in one fixed order, FP64, one
-    rounding per addition:
-      1. for b < G = min(n, 1024) and t < 256, a running sum over the rows
-         j = b, b+G, ... (outer) and the columns i = t, t+256, ... (inner);
-      2. per b, a halving tree over t: s[t] += s[t + h] for h = 128, 64, ..., 1;
-      3. over the G block sums: running sums over b = t, t+256, ... per t < 256,
-         then the same halving tree.
-    Any order gives the sum to within n^2 rounding errors; this one is stated so
-    that every implementation of it gets the same bits.  With w given, the sum
-    is of the products v w, each fused into the running sum of step 1
-    (acc = fma(v, w, acc)); steps 2 and 3 are unchanged."""
-    v = np.asarray(v, dtype=np.float64)
-    if w is not None:
-        w = np.asarray(w, dtype=np.float64)
-    n_rows, n_cols = v.shape
-    G = min(n_rows, REDUCE_BLOCKS)
-    T = REDUCE_THREADS
-    acc = np.zeros((G, T))
-    for k in range(0, (n_rows + G - 1) // G):
-        rows = v[k * G:(k + 1) * G]                       # row k*G + b for block b
-        for m in range(0, (n_cols + T - 1) // T):
-            blk = rows[:, m * T:(m + 1) * T]
-            a = acc[:blk.shape[0], :blk.shape[1]]
-            if w is None:
-                a[...] = a + blk
-            else:
-                a[...] = fma(blk, w[k * G:(k + 1) * G, m * T:(m + 1) * T], a)
-    acc = _halving_tree(acc)
-    parts = np.zeros(((G + T - 1) // T) * T)
-    parts[:G] = acc
-    fin = np.zeros((1, T))
-    for m in range(0, len(parts) // T):
-        fin[0] = fin[0] + parts[m * T:(m + 1) * T]
-    return float(_halving_tree(fin)[0])
-
-
-def _halving_tree(a: np.ndarray) -> np.ndarray:
-    a = a.copy()
-    h = a.shape[1] // 2
-    while h >= 1:
-        a[:, :h] = a[:, :h] + a[:, h:2 * h]
-        h //= 2
-    return a[:, 0]
-
-
-def norm(r: np.ndarray, fused: bool = False) -> float:
-    """Euclidean norm over the interior: sqrt of the ordered sum of squares
-    (squares rounded, or fused into the running sums)."""
+def norm(r: np.ndarray) -> float:
+    """Euclidean norm over the interior points (Sec. 4: the solver takes the
+    l2 norm of the residual, there through cuBLAS): the square root of the sum of the
+    squares, summed by numpy (pairwise).  The definition is the same in both
+    arithmetic modes; any summation order gives it to within a few rounding
+    errors of the exact value."""
     v = at(r, 0, 0).astype(np.float64)
-    return math.sqrt(ordered_sum(v, v) if fused else ordered_sum(v * v))
+    return math.sqrt(float(np.sum(v * v)))
 
 
-def dot(a: np.ndarray, b: np.ndarray, fused: bool = False) -> float:
-    """Interior inner product in the same order as norm()."""
+def dot(a: np.ndarray, b: np.ndarray) -> float:
+    """Interior inner product: the sum of the products, summed by numpy."""
     a = at(a, 0, 0).astype(np.float64)
     b = at(b, 0, 0).astype(np.float64)
-    return ordered_sum(a, b) if fused else ordered_sum(a * b)
+    return float(np.sum(a * b))
 
 
 # ---------------------------------------------------------------------------
@@ -656,31 +610,43 @@ def vcycle(levels, l, x, f, nu1=2, nu2=1) -> None:
         relax(lev, x, f)
 
 
-def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
+def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1, inner=None):
     """V(nu1, nu2) iterations until ||r_k|| / ||r_0|| <= tol or maxit cycles.
-    Returns (x, history) with history = [||r_0||, ||r_1||, ...]."""
+    Returns (x, history) with history = [||r_0||, ||r_1||, ...].  inner(a, b):
+    the interior inner product the history's norms take (default dot); the
+    norms do not feed back into the iterates."""
     lev = levels[0]
     fu = lev.fused
+    nrm = _norm_of(inner)
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
-    hist = [norm(residual(lev.planes, x, f, fu), fu)]
+    hist = [nrm(residual(lev.planes, x, f, fu))]
     if hist[0] == 0.0:
         return x, hist
     it = 0
     while it < maxit and hist[-1] / hist[0] > tol:
         vcycle(levels, 0, x, f, nu1, nu2)
-        hist.append(norm(residual(lev.planes, x, f, fu), fu))
+        hist.append(nrm(residual(lev.planes, x, f, fu)))
         it += 1
     return x, hist
 
 
-def solve_fcg(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
+def _norm_of(inner):
+    if inner is None:
+        return norm
+    return lambda r: math.sqrt(inner(r, r))
+
+
+def solve_fcg(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1, inner=None):
     """Flexible conjugate gradients (one-term recurrence, Notay's FCG(1)) with
     one V(nu1, nu2) cycle from a zero guess as the preconditioner.  Per step:
       z = V(r); p = z if first else z + beta p with beta = -(z.q)/(p.q) of the
       previous step; q = A p; alpha = (p.r)/(p.q); x += alpha p; r -= alpha q.
-    The test uses the recursively updated residual.  Returns (x, history)."""
+    The test uses the recursively updated residual.  inner(a, b): the interior
+    inner product (default dot); here it feeds back into the iterates through
+    alpha and beta, so another summation order of the same sum gives other
+    iterates at rounding level.  Returns (x, history)."""
     return _fcg(levels[0].planes, lambda r: _precondition64(levels, r, nu1, nu2), f, x0, tol, maxit,
-                levels[0].fused)
+                levels[0].fused, inner)
 
 
 def _precondition64(levels, r, nu1, nu2):
@@ -689,11 +655,13 @@ def _precondition64(levels, r, nu1, nu2):
     return z
 
 
-def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False):
+def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False, inner=None):
     fu = fused
+    ip = dot if inner is None else inner
+    nrm = _norm_of(inner)
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
     r = residual(planes, x, f, fu)
-    hist = [norm(r, fu)]
+    hist = [nrm(r)]
     if hist[0] == 0.0:
         return x, hist
     p = q = None
@@ -704,13 +672,13 @@ def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False):
         if p is None:
             p = z
         else:
-            beta = -(dot(z, q, fu) / pq)
+            beta = -(ip(z, q) / pq)
             p = madd(z, beta, p, fu)
         q = apply(planes, p, fu)
-        pq = dot(p, q, fu)
-        alpha = dot(p, r, fu) / pq
+        pq = ip(p, q)
+        alpha = ip(p, r) / pq
         x = madd(x, alpha, p, fu)
         r = msub(r, alpha, q, fu)
-        hist.append(norm(r, fu))
+        hist.append(nrm(r))
         it += 1
     return x, hist

@@ -88,14 +88,17 @@ def inner_cycle(levels32, r32, cycles: int = 1, nu1=2, nu2=1) -> np.ndarray:
     return e
 
 
-def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2, nu2=1):
+def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2, nu2=1, inner=None):
     """FP64 iterative refinement around FP32 V-cycles.  Returns (x, history),
-    history[k] = ||f - A x_k|| in FP64."""
+    history[k] = ||f - A x_k|| in FP64.  inner: as in boxmg.solve (the norm's
+    summation order; the power-of-two scale drawn from it changes no bit of
+    the iterates)."""
     p64 = levels[0].planes
     fu = levels[0].fused
+    nrm = bx._norm_of(inner)
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
     r = bx.residual(p64, x, f, fu)
-    hist = [bx.norm(r, fu)]
+    hist = [nrm(r)]
     if hist[0] == 0.0:
         return x, hist
     it = 0
@@ -105,12 +108,12 @@ def solve_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2
         e32 = inner_cycle(levels32, r32, cycles, nu1, nu2)
         x = x + s * e32.astype(np.float64)
         r = bx.residual(p64, x, f, fu)
-        hist.append(bx.norm(r, fu))
+        hist.append(nrm(r))
         it += 1
     return x, hist
 
 
-def solve_fcg_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2, nu2=1):
+def solve_fcg_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, nu1=2, nu2=1, inner=None):
     """Flexible CG in FP64 whose preconditioner is the FP32 cycle:
     z = s fl64(V32(fl32(r / s))) with s = 2^e the power of two of ||r||
     (any power of two gives the same z bit for bit)."""
@@ -118,4 +121,4 @@ def solve_fcg_ir(levels, levels32, f, x0=None, tol=1e-10, maxit=100, cycles=1, n
         s = scale_of(bx.norm(r))
         r32 = (r * (1.0 / s)).astype(F32)
         return s * inner_cycle(levels32, r32, cycles, nu1, nu2).astype(np.float64)
-    return bx._fcg(levels[0].planes, precond, f, x0, tol, maxit, levels[0].fused)
+    return bx._fcg(levels[0].planes, precond, f, x0, tol, maxit, levels[0].fused, inner)

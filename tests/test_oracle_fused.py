@@ -194,38 +194,6 @@ def test_fused_restriction_and_interpolation_are_the_point_loops():
     assert np.array_equal(x, want)
 
 
-@pytest.mark.parametrize("shape", [(3, 600), (1100, 3)])
-def test_fused_ordered_sum_is_the_stated_order(shape):
-    rng = np.random.default_rng(4)
-    v = rng.standard_normal(shape)
-    u = rng.standard_normal(shape)
-    rows, cols = shape
-    G, T = min(rows, 1024), 256
-    acc = [[0.0] * T for _ in range(G)]
-    for b in range(G):
-        for j in range(b, rows, G):
-            for i in range(cols):
-                acc[b][i % T] = fma_exact64(v[j, i], u[j, i], acc[b][i % T])
-
-    def tree(s):
-        s = list(s)
-        h = len(s) // 2
-        while h >= 1:
-            for t in range(h):
-                s[t] = s[t] + s[t + h]
-            h //= 2
-        return s[0]
-
-    parts = [tree(a) for a in acc]
-    parts += [0.0] * (-len(parts) % T)
-    fin = [0.0] * T
-    for m in range(len(parts) // T):
-        for t in range(T):
-            fin[t] = fin[t] + parts[m * T + t]
-    assert bx.ordered_sum(v, u) == tree(fin)
-    assert bx.ordered_sum(v, u) == pytest.approx(float(np.sum(v * u)), rel=1e-12)
-
-
 # ---- the fused cycle against the rounded one -----------------------------------------------
 
 def problem(name, n):

@@ -563,12 +563,19 @@ def test_ir_scale_is_power_of_two():
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n", [3, 7, 255, 1023, 1500])
-def test_ordered_sum_is_the_sum(n):
+def test_norm_and_dot_are_the_sums(n):
+    """The l2 norm and the inner product against math.fsum, the correctly
+    rounded sum: within n^2 rounding errors of the sum of magnitudes (numpy's
+    pairwise sum is far inside that), exact on integer-valued data."""
     v = w.normal(900 + n, n * n).reshape(n, n)
-    exact = math.fsum(v.reshape(-1))
-    assert abs(bx.ordered_sum(v) - exact) <= 4 * n * n * 2.3e-16 * np.abs(v).sum()
+    u = w.normal(1900 + n, n * n).reshape(n, n)
+    pad = lambda a: np.pad(a, 1)
+    exact = math.fsum((v * v).reshape(-1))
+    assert abs(bx.norm(pad(v)) ** 2 - exact) <= 4 * n * n * 2.3e-16 * exact
+    assert abs(bx.dot(pad(v), pad(u)) - math.fsum((v * u).reshape(-1))) <= 4 * n * n * 2.3e-16 * np.abs(v * u).sum()
     ints = np.round(v * 1000)                      # integer-valued: every order is exact
-    assert bx.ordered_sum(ints) == math.fsum(ints.reshape(-1))
+    assert bx.norm(pad(ints)) == math.sqrt(math.fsum((ints * ints).reshape(-1)))
+    assert bx.dot(pad(ints), pad(ints + 1)) == math.fsum((ints * (ints + 1)).reshape(-1))
 
 
 def test_fcg_single_level_is_one_direct_step():
