@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """BoxMG V(2,1) throughput on one GB300 (or N replicas), one JSON line.
 
-Workload (default): 2D -div(k grad u) on a 2047 x 2047 interior grid, 9-point
-Q1 finite-element stencil, k in {1, 1e4} on 16 x 16 cell blocks (Bernoulli 0.5,
-seed 2), RHS uniform[-1, 1) (seed 3), four-colour Gauss-Seidel V(2,1), ten
-levels down to 3 x 3, synthetic seeded inputs.
+Workload (default): the largest single-GPU problem, 2D -div(k grad u) on an
+8191 x 8191 interior grid (67.1 M unknowns), 9-point Q1 finite-element
+stencil, k = exp(g) with g a Gaussian random field (std 2, correlation length
+32 cells, seed 4), RHS uniform[-1, 1) (seed 7), four-colour Gauss-Seidel
+V(2,1), twelve levels down to 3 x 3, synthetic seeded inputs.
 
 A step is one iteration of the solve loop: one V(2,1) cycle (FP64) followed by
 the residual norm and the device-side convergence test.  `value` is the FP64
@@ -14,7 +15,8 @@ a 1e-10 relative residual of every variant are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
-`--impl reference` times the CPU oracle (numpy, FP64) on the same workload.
+`--impl reference` times the CPU oracle (numpy, FP64, its colour passes and
+residuals over row bands on every host core) on the same workload.
 """
 from __future__ import annotations
 
@@ -48,21 +50,25 @@ WORKLOADS = {
         text="8191x8191 interior, 9-point Q1 FE, k = exp(g), g Gaussian field std 2, correlation 32 cells, "
              "seed 4; RHS U[-1,1) seed 7; 12 levels",
         make=lambda: w.lognormal_problem(8191, 2.0, 32.0, seed_k=4, seed_f=7)),
+    "lognormal4095": dict(
+        text="4095x4095 interior, 9-point Q1 FE, k = exp(g), g Gaussian field std 2, correlation 32 cells, "
+             "seed 4; RHS U[-1,1) seed 7; 11 levels (the 8191^2 workload's recipe at a size ncu captures)",
+        make=lambda: w.lognormal_problem(4095, 2.0, 32.0, seed_k=4, seed_f=7)),
 }
+DEFAULT_WORKLOAD = "lognormal8191"
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernels, keyed by (workload, kernel); the captures and
-# their commands are summarised in profiles/gs_*_fe2047.md.  A kernel missing
-# here reports traffic null.
-NCU_TRAFFIC = {
-    ("fe2047-binary1e4", "k_gs_rows<double>"): 196.5e6,
-    ("fe2047-binary1e4", "k_gs_rows<float,float>"): 95.6e6,
-    ("fe2047-binary1e4", "k_gs_rows<float,bf16>"): 63.8e6,
-    ("fe2047-binary1e4", "k_gs_strip<float> 56x32 bulk/4"): 135.8e6,
-    ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48x26 bulk/4"): 136.2e6,
-    ("fe2047-binary1e4", "k_gs_strip64 56xW cp.async/6 fused"): 268.8e6,
-    ("fe2047-binary1e4", "k_gs_strip2_ring<float> 48xW bulk/4"): 145.9e6,
-    ("fe2047-binary1e4", "k_gs_strip<float> 56xW bulk/4"): 138.1e6,
+# DRAM bytes (read + write) per fine point of one launch of a level-0 kernel,
+# from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum over the launch / the level's unknowns) on the named
+# workload, keyed by kernel (and shape).  A launch's traffic is this figure x
+# the unknowns of the bench's level 0: the kernels stream their arrays, so
+# traffic grows in proportion to the grid.  A kernel missing here, or changed
+# since its capture, reports traffic null.
+NCU_DRAM_BYTES_PER_POINT = {
+    "k_gs_strip64 56xW cp.async/6 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4"),
+    "k_gs_strip64 56xW cp.async/4 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4 (shape 2 capture; same rows)"),
+    "k_gs_strip2_ring<float> 48xW bulk/4": (145.9e6 / 2047 ** 2, "fe2047-binary1e4"),
+    "k_gs_strip<float> 56xW bulk/4": (138.1e6 / 2047 ** 2, "fe2047-binary1e4"),
 }
 TILE_SHAPES = ("56xW bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
@@ -107,7 +113,8 @@ def run_batched(args, rank, local_rank, world):
         before = B.launch_count
         if prec == "fp64":
             with ClockSampler(local_rank) as cs:
-                ms = B.time_cycles(rhs, xs, args.steps)
+                with cs.timed():
+                    ms = B.time_cycles(rhs, xs, args.steps)
             clock_s = cs.summary()
         else:
             ms = B.time_cycles(rhs, xs, args.steps)
@@ -199,7 +206,8 @@ def run_rhs_batch(args, rank, local_rank, world):
         before = B.launch_count
         if prec == "fp64":
             with ClockSampler(local_rank) as cs:
-                ms = B.time_cycles(rhs, xs, args.steps)
+                with cs.timed():
+                    ms = B.time_cycles(rhs, xs, args.steps)
             clock_s = cs.summary()
         else:
             ms = B.time_cycles(rhs, xs, args.steps)
@@ -301,6 +309,9 @@ def whole_job_rate(units_this_rank: float, seconds_this_rank: float, ranks: "Ran
 # ----------------------------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 50 ms in the background;
+    only samples that arrive while a timed region is open (timed() context)
+    enter the summary."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -308,32 +319,60 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []
+        self.windows = []
+        self.reader = None
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return self
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
         return self
 
     def __exit__(self, *exc):
         if self.proc:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
+            if self.reader:
+                self.reader.join(timeout=5)
         return False
+
+    class _Window:
+        def __init__(self, owner):
+            self.owner = owner
+
+        def __enter__(self):
+            self.t0 = time.perf_counter()
+
+        def __exit__(self, *exc):
+            self.owner.windows.append((self.t0, time.perf_counter()))
+            return False
+
+    def timed(self):
+        return ClockSampler._Window(self)
 
     def summary(self):
         if not self.proc:
             return None
         sms, mx, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in (self.out or "").strip().splitlines():
+        for t, line in list(self.lines):
+            if not any(a <= t <= b for a, b in self.windows):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -347,7 +386,8 @@ class ClockSampler:
                     reasons.add(nm)
         if not sms:
             return None
-        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "samples": len(sms), "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "samples": len(sms), "reasons": sorted(reasons),
+                "timed_regions_s": round(sum(b - a for a, b in self.windows), 3)}
 
 
 # ----------------------------------------------------------------------------------
@@ -389,9 +429,9 @@ def run_ours(args, rank, local_rank, world):
         return
 
     variants = {}
-    clock_s = None
     timed_launches = 0
     fp64_rate = bmg.measure_fp64_rate() * 1e9        # DP instructions per second, measured here
+    sampler = ClockSampler(local_rank).__enter__()
     for prec in ("fp64", "fp32", "bf16"):
         barrier()
         t0 = time.perf_counter()
@@ -402,13 +442,10 @@ def run_ours(args, rank, local_rank, world):
         h.time_cycles(rhs, x, max(args.warmup, 3))
         barrier()
         before = h.launch_count
-        if prec == "fp64":
-            with ClockSampler(local_rank) as cs:
-                ms = h.time_cycles(rhs, x, args.steps)
-            clock_s = cs.summary()
-            timed_launches = h.launch_count - before
-        else:
+        with sampler.timed():
             ms = h.time_cycles(rhs, x, args.steps)
+        if prec == "fp64":
+            timed_launches = h.launch_count - before
         barrier()
         ms = max_over_ranks(ms)
         prof = h.profile(rhs, torch.zeros_like(rhs), 3)
@@ -423,17 +460,23 @@ def run_ours(args, rank, local_rank, world):
             modes.append(("fcg_2cycles", hk2, 500))
         for mode, hh, cap in modes:
             x.zero_()
+            hh.solve(rhs, x, tol=1e-10, maxit=2)                 # graph capture and first launches, untimed
+            x.zero_()
             barrier()
-            t0 = time.perf_counter()
-            _, iters, relres, ok = hh.solve(rhs, x, tol=1e-10, maxit=cap)
-            torch.cuda.synchronize()
-            tts[mode] = dict(solve_ms=round(max_over_ranks((time.perf_counter() - t0) * 1e3), 3), iterations=iters,
+            with sampler.timed():
+                t0 = time.perf_counter()
+                _, iters, relres, ok = hh.solve(rhs, x, tol=1e-10, maxit=cap)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+            tts[mode] = dict(solve_ms=round(max_over_ranks((t1 - t0) * 1e3), 3), iterations=iters,
                              relres=relres, converged=ok)
         if hk2 is not None:
             hk2.close()
         variants[prec] = dict(ms=ms, setup_ms=setup_ms, tts=tts, prof=prof, h=h, hk=hk,
                               tuned=[h.tuned_cluster(l) for l in range(h.num_levels)],
                               pairs=[h.tuned_pair(l) for l in range(h.num_levels)])
+    sampler.__exit__(None, None, None)
+    clock_s = sampler.summary()
 
     # the FP64 cycle in the other arithmetic mode, for comparison (cycle time and profile only)
     other = "rounded" if args.arith == "fused" else "fused"
@@ -474,6 +517,7 @@ def run_ours(args, rank, local_rank, world):
         return rows[0] if rows else max(prof, key=lambda r: r["ms"])
 
     sweeps_per_cycle = 3                                        # V(2,1)
+    hbm_peak = measured_peak("hbm_gbs", 6800.0)
 
     def per_launch(prec, fp32, prof=None):
         """Dominant kernel's average device time per launch and the Gauss-Seidel
@@ -482,22 +526,35 @@ def run_ours(args, rank, local_rank, world):
         cycles = 3
         return r, r["ms"] / r["launches"] * 1e-3, sweeps_per_cycle * cycles / r["launches"]
 
+    def traffic(name, sweeps):
+        """DRAM bytes of one launch: the captured bytes per fine point (of a
+        launch of the same kernel and shape) x the level's unknowns."""
+        got = NCU_DRAM_BYTES_PER_POINT.get(name)
+        if got is None:
+            return None, None
+        return round(got[0] * N), f"ncu capture on {got[1]}, {got[0]:.2f} B per fine point, x {N} points"
+
     def roofline_fp64(arith, prof, tuned):
+        """The FP64 sweep against both roofs: its algorithmic bytes against the
+        measured HBM copy bandwidth (the headline fraction) and its useful
+        FP64 instructions against the measured FP64 instruction rate (the roof
+        that binds it on this GPU)."""
         r, per_launch_s, sweeps = per_launch("fp64", False, prof)
         instr = ALG_FP64_INSTR_PER_POINT[(kind, arith)] * N * sweeps
-        achieved = instr / per_launch_s / 1e12
-        peak = fp64_rate / 1e12
-        share = r["ms"] / sum(q["ms"] for q in prof)
         byt = SWEEP_BYTES[("fp64", kind)] * N * sweeps
+        share = r["ms"] / sum(q["ms"] for q in prof)
         name = (f"k_gs_strip64 {TILE64_SHAPES[tuned[0] - 16]}" if tuned[0] >= 16 else "k_gs_rows<double>") + \
             (" fused" if arith == "fused" else "")
-        return {"bound": "alu", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
-                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "T FP64 instr/s",
-                "frac": round(achieved / peak, 4),
-                "instr_per_point": ALG_FP64_INSTR_PER_POINT[(kind, arith)],
-                "peak_source": "FP64 instruction rate measured in this run (bmg_measure_fp64_rate)",
-                "traffic": NCU_TRAFFIC.get((args.workload, name)),
-                "alg_bytes_per_launch": byt, "hbm_gbs_equiv": round(byt / per_launch_s / 1e9, 1),
+        gbs = byt / per_launch_s / 1e9
+        tr, tr_src = traffic(name, sweeps)
+        return {"bound": "hbm", "kernel": f"{name} level 0 ({'half ' if sweeps < 1 else ''}sweep per launch)",
+                "achieved": round(gbs, 1), "peak": hbm_peak[0], "unit": "GB/s", "frac": round(gbs / hbm_peak[0], 4),
+                "peak_source": hbm_peak[1], "traffic": tr, "traffic_source": tr_src,
+                "alg_bytes_per_launch": byt, "alg_bytes_per_point": SWEEP_BYTES[("fp64", kind)],
+                "fp64_pipe": {"achieved": round(instr / per_launch_s / 1e12, 4), "peak": round(fp64_rate / 1e12, 4),
+                              "unit": "T FP64 instr/s", "frac": round(instr / per_launch_s / fp64_rate, 4),
+                              "instr_per_point": ALG_FP64_INSTR_PER_POINT[(kind, arith)],
+                              "peak_source": "FP64 instruction rate measured in this run (bmg_measure_fp64_rate)"},
                 "time_share": round(share, 3), "avg_launch_us": round(per_launch_s * 1e6, 2)}
 
     def roofline_32(prec):
@@ -508,7 +565,6 @@ def run_ours(args, rank, local_rank, world):
         prof = variants[prec]["prof"]
         st = "bf16" if prec == "bf16" else "float"
         pair = [q for q in prof if q["kernel"] == "relax_pair" and q["level"] == 0 and q["fp32"]]
-        peak = measured_peak("hbm_gbs", 6800.0)
         if pair:
             r = pair[0]
             sweeps = 2.0
@@ -523,10 +579,11 @@ def run_ours(args, rank, local_rank, world):
         achieved = byt / per_launch_s / 1e9
         share = r["ms"] / sum(q["ms"] for q in prof)
         what = "two sweeps" if sweeps == 2.0 else ("half sweep" if sweeps < 1 else "sweep")
+        tr, tr_src = traffic(name, sweeps)
         return {"bound": "hbm", "kernel": f"{name} level 0 ({what} per launch)",
-                "achieved": round(achieved, 1), "peak": peak[0], "unit": "GB/s", "frac": round(achieved / peak[0], 4),
-                "peak_source": peak[1], "traffic": NCU_TRAFFIC.get((args.workload, name)),
-                "alg_bytes_per_launch": byt, "sweeps_per_launch": sweeps,
+                "achieved": round(achieved, 1), "peak": hbm_peak[0], "unit": "GB/s",
+                "frac": round(achieved / hbm_peak[0], 4), "peak_source": hbm_peak[1], "traffic": tr,
+                "traffic_source": tr_src, "alg_bytes_per_launch": byt, "sweeps_per_launch": sweeps,
                 "per_sweep_equiv_gbs": round(SWEEP_BYTES[(prec, kind)] * N * sweeps / per_launch_s / 1e9, 1),
                 "time_share": round(share, 3), "avg_launch_us": round(per_launch_s * 1e6, 2)}
 
@@ -562,11 +619,11 @@ def run_ours(args, rank, local_rank, world):
         p: sorted(([r["level"], r["kernel"] + ("32" if r["fp32"] else ""), round(r["launches"] / 3), round(r["ms"] / 3 * 1e3, 1)]
                    for r in v["prof"]), key=lambda e: -e[3])
         for p, v in variants.items()}
-    out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu and world == 1 else None
-    print(json.dumps(out))
     for v in variants.values():
         v["h"].close()
         v["hk"].close()
+    out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu and world == 1 else None
+    print(json.dumps(out))
     ranks.close()
 
 
@@ -582,31 +639,54 @@ def measured_peak(key, fallback):
 # the CPU oracle (baseline and reference arm)
 # ----------------------------------------------------------------------------------
 
-def oracle_cycles(kind, planes, f, cycles):
-    """Oracle setup, then `cycles` V(2,1) cycles each followed by the residual
-    norm; returns (setup_s, per-cycle seconds)."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_cycles(kind, planes, f, cycles, threads=1, levels=None):
+    """Oracle setup (unless given), then `cycles` V(2,1) cycles each followed
+    by the residual norm, the colour passes and residuals over row bands on
+    `threads` host threads (bit for bit the one-thread cycle); returns
+    (setup_s, per-cycle seconds, levels)."""
     from oracle import boxmg as bx
     t0 = time.perf_counter()
-    levels = bx.setup(kind, planes)
+    if levels is None:
+        levels = bx.setup(kind, planes)
     setup_s = time.perf_counter() - t0
+    bands = bx.RowBands(threads)
     x = np.zeros_like(f)
     times = []
-    for _ in range(cycles):
-        t0 = time.perf_counter()
-        bx.vcycle(levels, 0, x, f)
-        bx.norm(bx.residual(levels[0].planes, x, f))
-        times.append(time.perf_counter() - t0)
-    return setup_s, times
+    try:
+        for _ in range(cycles):
+            t0 = time.perf_counter()
+            bx.vcycle(levels, 0, x, f, bands=bands)
+            bx.norm(bx.residual(levels[0].planes, x, f, bands=bands))
+            times.append(time.perf_counter() - t0)
+    finally:
+        bands.close()
+    return setup_s, times, levels
 
 
 def cpu_baseline(args, kind, planes, f):
+    """The oracle on the host cores, all of them and one: one setup, then the
+    same V(2,1) cycle + residual norm on the full problem (a bounded sample:
+    one or a few cycles per leg)."""
     n = planes.shape[-1] - 2
-    cycles = 3 if n >= 2047 else 20
-    setup_s, times = oracle_cycles(kind, planes, f, cycles)
-    per = statistics.median(times)
-    return {"value": n * n / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (numpy FP64, one thread) setup ({setup_s:.1f} s) + {cycles} V(2,1) cycles with "
-                      f"residual norm on the full {args.workload} problem; median cycle {per * 1e3:.0f} ms"}
+    cores = host_cores()
+    cycles = 1 if n >= 4095 else (3 if n >= 2047 else 20)
+    setup_s, t_all, levels = oracle_cycles(kind, planes, f, cycles, threads=cores)
+    _, t_one, _ = oracle_cycles(kind, planes, f, cycles, threads=1, levels=levels)
+    per_all, per_one = statistics.median(t_all), statistics.median(t_one)
+    return {"value": n * n / per_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (numpy FP64; colour passes and residuals over row bands on {cores} threads, the same "
+                      f"bits as one) setup ({setup_s:.1f} s, one thread) + {cycles} V(2,1) cycle(s) with residual "
+                      f"norm on the full {args.workload} problem per leg; median cycle {per_all * 1e3:.0f} ms on "
+                      f"{cores} cores, {per_one * 1e3:.0f} ms on one",
+            "one_thread": {"value": n * n / per_one, "unit": UNIT, "cores": 1}}
 
 
 BATCH_SAMPLE_UNKNOWNS = 2_500_000
@@ -625,41 +705,54 @@ def batch_sample(probs, budget: int = BATCH_SAMPLE_UNKNOWNS):
     return out, tot
 
 
-def oracle_batch_cycles(probs, cycles):
-    """Oracle setup of every problem, then `cycles` rounds of one V(2,1) cycle
-    plus residual norm on each; returns (setup_s, per-round seconds)."""
+def oracle_batch_cycles(probs, cycles, threads=1, hier=None):
+    """Oracle setup of every problem (unless given), then `cycles` rounds of
+    one V(2,1) cycle plus residual norm on each, the colour passes and
+    residuals over row bands on `threads` host threads; returns (setup_s,
+    per-round seconds, hierarchies)."""
     from oracle import boxmg as bx
     t0 = time.perf_counter()
-    hier = [(bx.setup(k, pl), np.zeros_like(f), f) for k, pl, f in probs]
+    if hier is None:
+        hier = [(bx.setup(k, pl), f) for k, pl, f in probs]
     setup_s = time.perf_counter() - t0
+    bands = bx.RowBands(threads)
+    xs = [np.zeros_like(f) for _, f in hier]
     times = []
-    for _ in range(cycles):
-        t0 = time.perf_counter()
-        for levels, x, f in hier:
-            bx.vcycle(levels, 0, x, f)
-            bx.norm(bx.residual(levels[0].planes, x, f))
-        times.append(time.perf_counter() - t0)
-    return setup_s, times
+    try:
+        for _ in range(cycles):
+            t0 = time.perf_counter()
+            for (levels, f), x in zip(hier, xs):
+                bx.vcycle(levels, 0, x, f, bands=bands)
+                bx.norm(bx.residual(levels[0].planes, x, f, bands=bands))
+            times.append(time.perf_counter() - t0)
+    finally:
+        bands.close()
+    return setup_s, times, hier
 
 
 def batched_cpu_baseline(probs):
     sample, m = batch_sample(probs)
-    setup_s, times = oracle_batch_cycles(sample, 3)
-    per = statistics.median(times)
-    return {"value": m / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (numpy FP64, one thread): setup ({setup_s:.1f} s) + 3 rounds of one V(2,1) cycle with "
-                      f"residual norm on the first {len(sample)} problems of the batch ({m} unknowns); median round "
-                      f"{per * 1e3:.0f} ms"}
+    cores = host_cores()
+    setup_s, t_all, hier = oracle_batch_cycles(sample, 3, threads=cores)
+    _, t_one, _ = oracle_batch_cycles(sample, 3, threads=1, hier=hier)
+    per_all, per_one = statistics.median(t_all), statistics.median(t_one)
+    return {"value": m / per_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (numpy FP64; colour passes and residuals over row bands on {cores} threads): setup "
+                      f"({setup_s:.1f} s) + 3 rounds of one V(2,1) cycle with residual norm on the first "
+                      f"{len(sample)} problems of the batch ({m} unknowns) per leg; median round "
+                      f"{per_all * 1e3:.0f} ms on {cores} cores, {per_one * 1e3:.0f} ms on one",
+            "one_thread": {"value": m / per_one, "unit": UNIT, "cores": 1}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     warm = min(args.warmup, 1)
+    cores = host_cores()
     if args.workload == "batched256":
         sample, m = batch_sample(w.batched_problems(256, 5, 1.0, 32.0))
         steps = min(args.steps, 5)
-        setup_s, times = oracle_batch_cycles(sample, steps + warm)
+        setup_s, times, _ = oracle_batch_cycles(sample, steps + warm, threads=cores)
         text, unknowns = BATCHED["text"], m
         what = f"the first {len(sample)} problems of the batch ({m} unknowns)"
     elif args.workload == "rhs64-1023":
@@ -667,27 +760,28 @@ def run_reference(args, rank, world):
         kind, planes, _ = w.lognormal_problem(n, 2.0, 32.0, seed_k=4, seed_f=7)
         sample = [(kind, planes, w.rhs_uniform(n, 500 + q)) for q in range(2)]
         steps = min(args.steps, 5)
-        setup_s, times = oracle_batch_cycles(sample, steps + warm)
+        setup_s, times, _ = oracle_batch_cycles(sample, steps + warm, threads=cores)
         text, unknowns = RHS_BATCH["text"], 2 * n * n
         what = "2 of the 64 right-hand sides (the operator set up once per right-hand side)"
     else:
         spec = WORKLOADS[args.workload]
         kind, planes, f = spec["make"]()
         n = planes.shape[-1] - 2
-        steps = min(args.steps, 5 if n >= 2047 else 50)
-        setup_s, times = oracle_cycles(kind, planes, f, steps + warm)
+        steps = min(args.steps, 2 if n >= 4095 else (5 if n >= 2047 else 50))
+        setup_s, times, _ = oracle_cycles(kind, planes, f, steps + warm, threads=cores)
         text, unknowns = spec["text"], n * n
         what = f"the full {args.workload} problem"
     times = times[warm:]
     tot = sum(times)
     value = unknowns * len(times) / tot
-    sample = (f"{len(times)} timed V(2,1) cycles (+ {warm} warm-up) of the oracle on {what} (steps capped from "
-              f"{args.steps} to keep the CPU run to minutes); setup {setup_s:.1f} s")
+    sample = (f"{len(times)} timed V(2,1) cycles (+ {warm} warm-up) of the oracle on {what}, colour passes and "
+              f"residuals over row bands on {cores} host threads (steps capped from {args.steps} to keep the CPU run "
+              f"to minutes); setup {setup_s:.1f} s")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times), "warmup": args.warmup,
            "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic (seeded generators, no datasets)", "impl": "reference",
            "config": {"workload": args.workload, "description": text, "unknowns": unknowns},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -697,7 +791,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--workload", default="fe2047-binary1e4",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + ["batched256", "rhs64-1023"])
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")

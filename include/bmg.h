@@ -168,8 +168,13 @@ int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int ma
               int* iters, double* relres);
 
 /* Residual norms [||r_0||, ||r_1||, ...] of the last solve, copied to the host
- * array out (capacity cap).  Returns the number of entries available (which may
- * exceed cap) or a negative code. */
+ * array out (capacity cap): the l2 norms the convergence test of the solve
+ * loop takes after every cycle (Fig. 1's V-cycle repeated until the norm test
+ * of Sec. 4 passes; ||r_k|| = ||f - A x_k|| over the interior points).  out is
+ * caller-owned host memory (NULL: nothing is written); the hierarchy keeps
+ * the history until the next solve or bmg_free.  Returns the number of entries
+ * available (which may exceed cap; min(cap, that number) are written) or
+ * BMG_EINVAL for a NULL hierarchy. */
 int bmg_history(const bmg_hierarchy* h, double* out, int cap);
 
 /* Measurement: enqueue `cycles` solve iterations (one V-cycle, or one
@@ -231,7 +236,11 @@ int bmg_get_interp(const bmg_hierarchy* h, int level, double* out);
  * by the host side of the library). */
 long long bmg_launch_count(const bmg_hierarchy* h);
 
-/* Release everything the hierarchy owns.  NULL is a no-op. */
+/* Release everything the hierarchy owns: the level arrays of the setup
+ * (stencils, the Fig. 2 interpolation weights, the coarsest Cholesky factor),
+ * the solve loop's vectors, CUDA graphs, events and its stream, after waiting
+ * for the hierarchy's queued work.  The caller's arrays (stencil, rhs, x) are
+ * not touched.  NULL is a no-op; h must not be used afterwards. */
 void bmg_free(bmg_hierarchy* h);
 
 const char* bmg_strerror(int code);
@@ -389,16 +398,18 @@ int bmg_residual(int n, int kind, const double* coef, const double* x, const dou
  * this entry point serves callers that cannot let the library allocate device
  * memory (a host framework that owns the device memory pool, allocation-free
  * real-time or callback paths, checks that forbid allocator calls in a region
- * of work).  Arguments, layouts and results are those of bmg_residual.  The
- * partial sums of the norm live in one fixed device array of the library
- * (1024 partial sums + the result, 8 KiB, held by every GPU that loads the
- * library until the process exits); the kernel uses min(n, 1024) of them, so
- * every valid n fits, and a partial count beyond the array is rejected with
- * BMG_EINVAL.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array: calls whose GPU work overlaps (other streams or
- * host threads) race on it, so serialise them.  Calls no cudaMalloc/cudaFree
- * or allocating routine. */
+ * of work).  Arguments, layouts and results are those of bmg_residual; r and
+ * norm may each be NULL.  The partial sums of the norm live in one fixed
+ * device array of the library (1024 partial sums + the result, 8 KiB, held by
+ * every GPU that loads the library until the process exits); the kernel uses
+ * min(n, 1024) of them, so every valid n fits, and a partial count beyond the
+ * array is rejected with BMG_EINVAL.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and keeps it for the process;
+ * make that first call before any stream capture, and do not call the entry
+ * point again after a cudaDeviceReset of that device.  The call synchronizes
+ * its stream before it returns.  All calls share the array: calls whose GPU
+ * work overlaps (other streams or host threads) race on it, so serialise them.
+ * Calls no cudaMalloc/cudaFree or allocating routine. */
 int bmg_residual_noalloc(int n, int kind, const double* coef, const double* x, const double* f,
                          double* r, double* norm, void* stream);
 

@@ -73,9 +73,10 @@ def size_of(a: np.ndarray) -> int:
 
 
 def at(a: np.ndarray, di: int, dj: int) -> np.ndarray:
-    """View of a(i+di, j+dj) over all interior (i, j), shape (n, n)."""
-    n = size_of(a)
-    return a[1 + dj:n + 1 + dj, 1 + di:n + 1 + di]
+    """View of a(i+di, j+dj) over all interior (i, j): shape (n, n) for a
+    level array; a band of rows (a view of rows j0-1 .. j1+1 of a level
+    array) gives its rows j0 .. j1."""
+    return a[1 + dj:a.shape[-2] - 1 + dj, 1 + di:a.shape[-1] - 1 + di]
 
 
 def coupling(planes: np.ndarray, di: int, dj: int) -> np.ndarray:
@@ -168,6 +169,40 @@ def level_sizes(n: int, coarsest: int = 3) -> list[int]:
     return out
 
 
+class RowBands:
+    """Runs a function of a band of rows on every band of a level, the bands
+    in a thread pool (numpy releases the interpreter lock inside its array
+    loops), and waits for all of them.  A band b = slice(j0 - 1, j1 + 2) of a
+    level array holds its interior rows j0 .. j1 (j0 odd, so colours keep their
+    parity) and one neighbour row on each side.  Used only where the rows of
+    one call are independent: one Gauss-Seidel colour, the residual.  Levels
+    smaller than min_rows run as one band in the calling thread."""
+
+    def __init__(self, threads: int, min_rows: int = 256):
+        from concurrent.futures import ThreadPoolExecutor
+        self.threads = max(1, int(threads))
+        self.min_rows = min_rows
+        self.pool = ThreadPoolExecutor(self.threads) if self.threads > 1 else None
+
+    def slices(self, n: int):
+        if self.pool is None or n < self.min_rows:
+            return [slice(0, n + 2)]
+        step = 2 * max(1, -(-n // (2 * self.threads)))          # even band height: every j0 odd
+        return [slice(j0 - 1, min(j0 + step - 1, n) + 2) for j0 in range(1, n + 1, step)]
+
+    def run(self, n: int, fn) -> None:
+        bands = self.slices(n)
+        if len(bands) == 1:
+            fn(bands[0])
+            return
+        for fut in [self.pool.submit(fn, b) for b in bands]:
+            fut.result()
+
+    def close(self) -> None:
+        if self.pool is not None:
+            self.pool.shutdown()
+
+
 # ---------------------------------------------------------------------------
 # Operator apply and residual (A5/A6/A9 building blocks)
 # ---------------------------------------------------------------------------
@@ -194,14 +229,23 @@ def apply(planes: np.ndarray, x: np.ndarray, fused: bool = False) -> np.ndarray:
     return y
 
 
-def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray, fused: bool = False) -> np.ndarray:
-    """r = f - A x, evaluated as f - a_O x_p - a_W x_W - ... (NBR order)."""
+def residual(planes: np.ndarray, x: np.ndarray, f: np.ndarray, fused: bool = False, bands=None) -> np.ndarray:
+    """r = f - A x, evaluated as f - a_O x_p - a_W x_W - ... (NBR order).
+    bands: a RowBands runner (the rows are independent), or None."""
     r = np.zeros_like(x)
+    if bands is None:
+        residual_into(planes, x, f, r, fused)
+    else:
+        bands.run(size_of(x), lambda b: residual_into(planes[:, b], x[b], f[b], r[b], fused))
+    return r
+
+
+def residual_into(planes, x, f, r, fused: bool = False) -> None:
+    """The interior of r = f - A x, written into r (rows of a band or of a level)."""
     acc = at(f, 0, 0).copy()
     for d in NBR:
         acc = msub(acc, coupling(planes, *d), at(x, *d), fused)
     at(r, 0, 0)[...] = acc
-    return r
 
 
 def norm(r: np.ndarray) -> float:
@@ -236,17 +280,18 @@ def gs_colour(planes, dinv, x, f, pi, pj, fused: bool = False) -> None:
     at(x, 0, 0)[c] = s * at(dinv, 0, 0)[c]
 
 
-def gs_sweep(kind: int, planes, dinv, x, f, fused: bool = False) -> None:
+def gs_sweep(kind: int, planes, dinv, x, f, fused: bool = False, bands=None) -> None:
     """One Gauss-Seidel sweep: red-black for a 5-point stencil, four colours
     (i, j parities (odd,odd), (even,odd), (odd,even), (even,even)) for a
-    9-point stencil."""
-    if kind == 5:
-        for group in COLOURS5:
-            for pi, pj in group:
-                gs_colour(planes, dinv, x, f, pi, pj, fused)
-    else:
-        for pi, pj in COLOURS9:
+    9-point stencil.  bands: a RowBands runner, or None; within one colour the
+    points are decoupled, so bands of rows update together and give the same
+    values."""
+    order = [c for group in COLOURS5 for c in group] if kind == 5 else COLOURS9
+    for pi, pj in order:
+        if bands is None:
             gs_colour(planes, dinv, x, f, pi, pj, fused)
+        else:
+            bands.run(size_of(x), lambda b: gs_colour(planes[:, b], dinv[b], x[b], f[b], pi, pj, fused))
 
 
 # Line relaxation (Fig. 1 "Line" relaxation; the smoother BoxMG offers for
@@ -285,13 +330,13 @@ def line_sweep(kind: int, planes, x, f) -> None:
             xr[:, i] = d[:, i] - c[:, i] * xr[:, i + 1]
 
 
-def relax(lev, x, f) -> None:
+def relax(lev, x, f, bands=None) -> None:
     """One sweep of the level's smoother: point Gauss-Seidel (default) or
     zebra x-line Gauss-Seidel."""
     if getattr(lev, "smoother", "point") == "line":
         line_sweep(lev.kind, lev.planes, x, f)
     else:
-        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f, getattr(lev, "fused", False))
+        gs_sweep(lev.kind, lev.planes, lev.dinv, x, f, getattr(lev, "fused", False), bands)
 
 
 # ---------------------------------------------------------------------------
@@ -590,24 +635,25 @@ def coarse_solve(lev: Level, x: np.ndarray, f: np.ndarray) -> None:
     at(x, 0, 0)[...] = sol.reshape(n, n).astype(x.dtype)
 
 
-def vcycle(levels, l, x, f, nu1=2, nu2=1) -> None:
+def vcycle(levels, l, x, f, nu1=2, nu2=1, bands=None) -> None:
     """V(nu1, nu2) on level l (Fig. 1): relax, restrict the residual, recurse
     with a zero initial guess (or solve directly on the coarsest level),
-    interpolate and correct, relax."""
+    interpolate and correct, relax.  bands: a RowBands runner for the
+    colour passes and residuals (same values as without), or None."""
     lev = levels[l]
     if lev.L is not None:
         coarse_solve(lev, x, f)
         return
     fu = lev.fused
     for _ in range(nu1):
-        relax(lev, x, f)
-    r = residual(lev.planes, x, f, fu)
+        relax(lev, x, f, bands)
+    r = residual(lev.planes, x, f, fu, bands)
     fc = restrict(lev.ci, r, fu)
     xc = np.zeros_like(fc)
-    vcycle(levels, l + 1, xc, fc, nu1, nu2)
+    vcycle(levels, l + 1, xc, fc, nu1, nu2, bands)
     interp_correct(lev.ci, xc, x, fu)
     for _ in range(nu2):
-        relax(lev, x, f)
+        relax(lev, x, f, bands)
 
 
 def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1, inner=None):

@@ -9,16 +9,23 @@
 // the library: every GPU that loads the library holds it (8 KiB) until the
 // process exits.
 //
-// The array holds up to kPartials partial sums plus the result.  The residual
-// kernel uses min(n, kPartials) blocks, so every n the ABI accepts fits; a
-// partial count beyond the array is still checked and rejected with BMG_EINVAL.
+// The array holds up to kPartials partial sums plus the result.  kPartials is
+// the residual kernel's own block limit (min(n, that limit) blocks), so every n
+// the ABI accepts fits; a partial count beyond the array is still checked and
+// rejected with BMG_EINVAL.
 // Every call shares the one array, so calls whose work overlaps on the GPU
 // (other streams, other host threads) race on it and must be serialised by
 // the caller.  Each call writes every slot it later reads, so nothing left by
 // an earlier call needs clearing.
+//
+// The device address of the array is looked up once per device and kept for
+// the life of the process; a cudaDeviceReset on that device unloads the
+// library's device code, after which this entry point must not be called
+// again in the process.
 #include <mutex>
 
 #include "common.cuh"
+#include "cycle_device.cuh"
 #include "kernels.h"
 
 namespace bmg {
@@ -29,7 +36,8 @@ using namespace bmg;
 
 namespace {
 
-constexpr int kPartials = 1024;
+constexpr int kPartials = dev::NORM_BLOCKS_MAX;
+static_assert(kPartials >= dev::NORM_BLOCKS_MAX, "the static scratch must hold every partial sum of the norm");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kPartials + 1];
