@@ -326,16 +326,49 @@ int bmg_mlp_get_params(const bmg_mlp* m, float* host, int count);
  * device for bmg_mlp_adam. */
 int bmg_mlp_loss_grad(bmg_mlp* m, int n, const double* coef, int K, const double* vecs, const double* eref,
                       double* loss, float* grad, double* eref_out, void* stream);
+/* The two-grid training loss and its gradient on a batch of crops (the
+ * training objective of the learned interpolation; not in the paper).  For
+ * each crop c (an n x n Dirichlet problem, n = 7, 15 or 31) and error vector
+ * e_ck, with the crop's learned P (network outputs on its features), A_c =
+ * P^T A P and the two-grid error propagation of V(2,1) with an exact coarse
+ * solve, E = S (I - P A_c^{-1} P^T A) S^2 (S: one four-colour Gauss-Seidel
+ * sweep of A e = 0), the energy E_ck = ||E e_ck||_A^2 and
+ *     loss = 1/(ncrop K) sum_ck E_ck / eref_ck.
+ * The gradient with respect to P is (A P v - g) u^T - (A e2) v^T with
+ * u = A_c^{-1} P^T A S^2 e, e2 = S^2 e - P u, g = S^T dloss/d(E e) and the
+ * adjoint solve v = A_c^{-1} P^T g; it is chained to the logits and through
+ * the network.  FP64 throughout except the FP32 network.
+ *   coefs: device, ncrop x 5 planes (n+2)^2 (O, W, S, SW, NW; ghost ring and
+ *          couplings to it ignored).  vecs: device, ncrop x K vectors
+ *          (n+2)^2 (ghost ring ignored).  Caller-owned, read only.
+ *   eref:  device, ncrop x K normalisers; NULL: only the energies of Dendy's
+ *          weights (zero logits) are computed, into `energies` (loss and grad
+ *          untouched) -- the normalisers of later calls.
+ *   energies: device, ncrop x K, out.  loss: host, out (with eref).
+ *   grad: host array of MLP_PARAMS floats or NULL; the gradient also stays on
+ *          the device for bmg_mlp_adam.
+ * Returns BMG_EINVAL (sizes, NULLs), BMG_ESINGULAR (a non-positive pivot of a
+ * crop's A_c), BMG_ENAN (a non-finite loss) or BMG_ECUDA.  Synchronizes the
+ * stream. */
+int bmg_mlp_twogrid(bmg_mlp* m, int ncrop, int n, const double* coefs, int K, const double* vecs,
+                    const double* eref, double* energies, double* loss, float* grad, void* stream);
 /* Adam step (beta 0.9, 0.999, eps 1e-8) with the last gradient. */
 int bmg_mlp_adam(bmg_mlp* m, float lr, void* stream);
 /* Logits of every interior coarse point, row-major (jc outer), 4 per point,
  * from the BF16 tensor-core inference kernel: delta device floats (n_c^2 * 4). */
 int bmg_mlp_infer(const bmg_mlp* m, int n, const double* coef, float* delta, void* stream);
+/* The network's inputs: for every interior coarse point (rows jc outer), the
+ * 18 features (a_W + a_E)/a_O and (a_S + a_N)/a_O at the 9 fine points of its
+ * 3x3 block (dy outer, dx inner), formed in FP64 and rounded to FP32.
+ * coef: device, 5 planes (n+2)^2, ghost couplings zero; X: device floats
+ * (n_c^2 x 18). */
+int bmg_mlp_features(int n, const double* coef, float* X, void* stream);
 /* Interpolation weights (8 planes (n_c+2)^2, FP64) from logits delta. */
 int bmg_learned_interp(int n, const double* coef, const float* delta, double* ci, void* stream);
 /* Which interpolation the hierarchy kept at level 0 (BMG_INTERP_*), and the
- * measured V-cycle factors of the learned and the Dendy hierarchy (0 if not
- * measured). */
+ * measured V-cycle factors of the learned and the Dendy hierarchy: 15
+ * stationary V(2,1) cycles on A x = 0 from a SplitMix64 start (stream
+ * 0x5EED), factor (||r_15|| / ||r_5||)^(1/10); 0 if not measured. */
 int bmg_interp_info(const bmg_hierarchy* h, int* used, double* factor_learned, double* factor_dendy);
 /* SplitMix64 uniform[-1,1) values on the interior of an (n+2)^2 device array
  * (counter form, stream `seed`, interior point k = (j-1) n + (i-1)). */

@@ -300,33 +300,31 @@ def tv_energies(planes: np.ndarray, ci: np.ndarray, vecs) -> np.ndarray:
     return np.array(out)
 
 
-def tv_loss_grad(planes: np.ndarray, delta: np.ndarray, vecs, e_ref: np.ndarray):
-    """L(delta) of the test-vector loss and dL/d delta, shape (M, 4)."""
-    n = bx.size_of(planes)
-    nc = (n - 1) // 2
-    M = nc * nc
-    K = len(vecs)
-    ci, (SDx, qx, SDy, qy) = edge_split(planes, delta)
-    centre_weights(planes, ci)
-    dW = np.zeros((8, nc + 2, nc + 2))
+def _add_outer(dW: np.ndarray, g: np.ndarray, ec: np.ndarray) -> None:
+    """dW += the derivative of <g, P ec> with respect to the weight planes:
+    for every weight w(p -> c) of P, g(p) ec(c), in the label layout."""
+    nc = dW.shape[-1] - 2
     A, B, Bm = slice(1, nc + 1), slice(1, nc + 2), slice(0, nc + 1)
     even, odd = slice(2, 2 * nc + 1, 2), slice(1, 2 * nc + 2, 2)
-    L = 0.0
-    for v, er in zip(vecs, e_ref):
-        pv, ec = inject_interp(ci, v)
-        err = v - pv
-        Ae = bx.apply(planes, err)
-        L += bx.dot(err, Ae) / er / K
-        g = -2.0 * Ae / (er * K)                      # dL / d(P R v)(p)
-        dW[LL, A, B] += g[even, odd] * ec[A, Bm]
-        dW[LR, A, B] += g[even, odd] * ec[A, B]
-        dW[LB, B, A] += g[odd, even] * ec[Bm, A]
-        dW[LA, B, A] += g[odd, even] * ec[B, A]
-        dW[LSW, B, B] += g[odd, odd] * ec[Bm, Bm]
-        dW[LSE, B, B] += g[odd, odd] * ec[Bm, B]
-        dW[LNW, B, B] += g[odd, odd] * ec[B, Bm]
-        dW[LNE, B, B] += g[odd, odd] * ec[B, B]
-    # centre weights -> edge weights (Dendy's centre formula is linear in them)
+    dW[LL, A, B] += g[even, odd] * ec[A, Bm]
+    dW[LR, A, B] += g[even, odd] * ec[A, B]
+    dW[LB, B, A] += g[odd, even] * ec[Bm, A]
+    dW[LA, B, A] += g[odd, even] * ec[B, A]
+    dW[LSW, B, B] += g[odd, odd] * ec[Bm, Bm]
+    dW[LSE, B, B] += g[odd, odd] * ec[Bm, B]
+    dW[LNW, B, B] += g[odd, odd] * ec[B, Bm]
+    dW[LNE, B, B] += g[odd, odd] * ec[B, B]
+
+
+def _weights_grad_to_delta(planes: np.ndarray, dW: np.ndarray, split) -> np.ndarray:
+    """dL/d delta, shape (M, 4), from dL/dw of the eight weight planes:
+    through Dendy's centre formula (linear in the edge weights) to the edge
+    weights, then through the split w1 = S_D q, w2 = S_D (1 - q)."""
+    SDx, qx, SDy, qy = split
+    n = bx.size_of(planes)
+    nc = (n - 1) // 2
+    B, Bm = slice(1, nc + 2), slice(0, nc + 1)
+    dW = dW.copy()
     a = {d: bx.coupling(planes, *d) for d in bx.NBR}
     C = (slice(0, n, 2), slice(0, n, 2))
     o = a[(0, 0)][C]
@@ -340,7 +338,6 @@ def tv_loss_grad(planes: np.ndarray, delta: np.ndarray, vecs, e_ref: np.ndarray)
     dW[LL, B, B] += -cN * gnw
     dW[LA, B, B] += -cE * gne
     dW[LR, B, B] += -cN * gne
-    # edge weights -> delta through the split w1 = S_D q, w2 = S_D (1 - q)
     dg = np.zeros((4, nc + 2, nc + 2))
     t = (dW[LL, 1:nc + 1, 1:nc + 2] - dW[LR, 1:nc + 1, 1:nc + 2]) * SDx * qx * (1.0 - qx)
     dg[1, 1:nc + 1, 0:nc + 1] += t
@@ -348,7 +345,25 @@ def tv_loss_grad(planes: np.ndarray, delta: np.ndarray, vecs, e_ref: np.ndarray)
     t = (dW[LB, 1:nc + 2, 1:nc + 1] - dW[LA, 1:nc + 2, 1:nc + 1]) * SDy * qy * (1.0 - qy)
     dg[3, 0:nc + 1, 1:nc + 1] += t
     dg[2, 1:nc + 2, 1:nc + 1] -= t
-    return L, dg[:, 1:nc + 1, 1:nc + 1].reshape(4, M).T
+    return dg[:, 1:nc + 1, 1:nc + 1].reshape(4, nc * nc).T
+
+
+def tv_loss_grad(planes: np.ndarray, delta: np.ndarray, vecs, e_ref: np.ndarray):
+    """L(delta) of the test-vector loss and dL/d delta, shape (M, 4)."""
+    n = bx.size_of(planes)
+    nc = (n - 1) // 2
+    K = len(vecs)
+    ci, split = edge_split(planes, delta)
+    centre_weights(planes, ci)
+    dW = np.zeros((8, nc + 2, nc + 2))
+    L = 0.0
+    for v, er in zip(vecs, e_ref):
+        pv, ec = inject_interp(ci, v)
+        err = v - pv
+        Ae = bx.apply(planes, err)
+        L += bx.dot(err, Ae) / er / K
+        _add_outer(dW, -2.0 * Ae / (er * K), ec)     # dL / d(P R v)(p) times v(c)
+    return L, _weights_grad_to_delta(planes, dW, split)
 
 
 def smooth_vectors(planes: np.ndarray, randoms, sweeps: int = 10):
@@ -370,3 +385,126 @@ def model_tv_loss_grad(theta, planes, vecs, e_ref):
     out, cache = forward(theta, X)
     L, d_out = tv_loss_grad(planes, out, vecs, e_ref)
     return L, backward(theta, cache, d_out)
+
+
+# ---------------------------------------------------------------------------
+# Two-grid loss: the A-energy of the two-grid error propagation
+#   E = S^nu2 (I - P A_c^{-1} P^T A) S^nu1,   A_c = P^T A P,
+# the measured quantity the learned interpolation is trained to reduce.
+# ---------------------------------------------------------------------------
+
+def error_sweep(planes: np.ndarray, dinv: np.ndarray, e: np.ndarray) -> None:
+    """One four-colour Gauss-Seidel sweep of A e = 0, in place: the error
+    propagation S = M_4 M_3 M_2 M_1 of a sweep, M_c = I - J_c D^{-1} A (J_c
+    keeps the points of colour c)."""
+    bx.gs_sweep(9, planes, dinv, e, np.zeros_like(e))
+
+
+def error_sweep_adjoint(planes: np.ndarray, dinv: np.ndarray, y: np.ndarray) -> None:
+    """y <- S^T y, in place.  A is symmetric, so M_c^T = I - A D^{-1} J_c, and
+    S^T = M_1^T M_2^T M_3^T M_4^T applies the colours in reverse order: for each,
+    z = D^{-1} y on the colour's points (zero elsewhere), then y = y - A z."""
+    for pi, pj in reversed(bx.COLOURS9):
+        c = bx.colour(pi, pj)
+        z = np.zeros_like(y)
+        bx.at(z, 0, 0)[c] = bx.at(y, 0, 0)[c] * bx.at(dinv, 0, 0)[c]
+        y -= bx.apply(planes, z)
+
+
+def _dinv(planes: np.ndarray) -> np.ndarray:
+    d = np.zeros_like(planes[0])
+    bx.at(d, 0, 0)[...] = 1.0 / bx.at(planes[0], 0, 0)
+    return d
+
+
+def coarse_operator(planes: np.ndarray, ci: np.ndarray) -> np.ndarray:
+    """The dense Galerkin operator A_c = P^T A P (interior coarse unknowns,
+    lexicographic)."""
+    return bx.dense_matrix(bx.rap(planes, ci))
+
+
+def _coarse_solve(Ac: np.ndarray, fc: np.ndarray) -> np.ndarray:
+    """A_c^{-1} fc for an (nc+2)^2 coarse array (any exact solve: numpy's)."""
+    nc = fc.shape[-1] - 2
+    u = np.zeros_like(fc)
+    u[1:nc + 1, 1:nc + 1] = np.linalg.solve(Ac, fc[1:nc + 1, 1:nc + 1].reshape(-1)).reshape(nc, nc)
+    return u
+
+
+def two_grid(planes: np.ndarray, ci: np.ndarray, e: np.ndarray, Ac: np.ndarray, nu1: int = 2, nu2: int = 1):
+    """E e for one error vector e (ghost ring zero) and the vectors on the way:
+    e1 = S^nu1 e; u = A_c^{-1} P^T A e1; e2 = e1 - P u; e3 = S^nu2 e2."""
+    dinv = _dinv(planes)
+    e1 = np.array(e, dtype=np.float64)
+    for _ in range(nu1):
+        error_sweep(planes, dinv, e1)
+    u = _coarse_solve(Ac, bx.restrict(ci, bx.apply(planes, e1)))
+    e2 = e1.copy()
+    bx.interp_correct(ci, -u, e2)
+    e3 = e2.copy()
+    for _ in range(nu2):
+        error_sweep(planes, dinv, e3)
+    return e1, u, e2, e3
+
+
+def two_grid_energies(planes: np.ndarray, ci: np.ndarray, vecs, nu1: int = 2, nu2: int = 1) -> np.ndarray:
+    """||E e_k||_A^2 for every vector."""
+    Ac = coarse_operator(planes, ci)
+    out = []
+    for e in vecs:
+        e3 = two_grid(planes, ci, e, Ac, nu1, nu2)[3]
+        out.append(bx.dot(e3, bx.apply(planes, e3)))
+    return np.array(out)
+
+
+def two_grid_loss_grad(planes: np.ndarray, delta: np.ndarray, vecs, e_ref: np.ndarray, nu1: int = 2,
+                       nu2: int = 1, weight: float = 1.0):
+    """L = weight/K sum_k ||E e_k||_A^2 / e_ref_k and dL/d delta, shape (M, 4).
+
+    With g2 = S^{nu2 T} (dL/d e3) and the adjoint coarse solve
+    v = A_c^{-1} P^T g2, every term of E through P (the restriction P^T, the
+    coarse operator P^T A P and the interpolation P) gives
+        dL/dP = (A P v - g2) u^T - (A e2) v^T,
+    taken on P's sparsity pattern, then chained to delta."""
+    n = bx.size_of(planes)
+    nc = (n - 1) // 2
+    K = len(vecs)
+    ci, split = edge_split(planes, delta)
+    centre_weights(planes, ci)
+    Ac = coarse_operator(planes, ci)
+    dinv = _dinv(planes)
+    dW = np.zeros((8, nc + 2, nc + 2))
+    L = 0.0
+    for e, er in zip(vecs, e_ref):
+        _, u, e2, e3 = two_grid(planes, ci, e, Ac, nu1, nu2)
+        Ae3 = bx.apply(planes, e3)
+        L += weight * bx.dot(e3, Ae3) / (K * er)
+        g = 2.0 * weight / (K * er) * Ae3                # dL/d e3
+        for _ in range(nu2):
+            error_sweep_adjoint(planes, dinv, g)          # dL/d e2
+        v = _coarse_solve(Ac, bx.restrict(ci, g))
+        pv = np.zeros_like(e2)
+        bx.interp_correct(ci, v, pv)
+        _add_outer(dW, bx.apply(planes, pv) - g, u)
+        _add_outer(dW, -bx.apply(planes, e2), v)
+    return L, _weights_grad_to_delta(planes, dW, split)
+
+
+def two_grid_reference(planes: np.ndarray, vecs, nu1: int = 2, nu2: int = 1) -> np.ndarray:
+    """The loss normalisers: Dendy's two-grid energies (delta = 0)."""
+    nc = (bx.size_of(planes) - 1) // 2
+    return two_grid_energies(planes, learned_interp(planes, np.zeros((nc * nc, 4))), vecs, nu1, nu2)
+
+
+def model_two_grid_loss_grad(theta: np.ndarray, crops, nu1: int = 2, nu2: int = 1):
+    """Loss of the network over a batch of crops (planes, vectors, e_ref):
+    the mean over crops of their two-grid losses, and its gradient w.r.t. theta."""
+    C = len(crops)
+    L = 0.0
+    g = np.zeros_like(theta)
+    for planes, vecs, e_ref in crops:
+        out, cache = forward(theta, features(planes))
+        l, d_out = two_grid_loss_grad(planes, out, vecs, e_ref, nu1, nu2, weight=1.0 / C)
+        L += l
+        g += backward(theta, cache, d_out)
+    return L, g

@@ -100,9 +100,11 @@ _sig = {
     "bmg_mlp_set_params": (I, [P, P, I]),
     "bmg_mlp_get_params": (I, [P, P, I]),
     "bmg_mlp_loss_grad": (I, [P, I, P, I, P, P, ctypes.POINTER(D), P, P, P]),
+    "bmg_mlp_twogrid": (I, [P, I, I, P, I, P, P, P, ctypes.POINTER(D), P, P]),
     "bmg_mlp_adam": (I, [P, ctypes.c_float, P]),
     "bmg_mlp_infer": (I, [P, I, P, P, P]),
     "bmg_learned_interp": (I, [I, P, P, P, P]),
+    "bmg_mlp_features": (I, [I, P, P, P]),
     "bmg_interp_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
     "bmg_tuned_cluster": (I, [P, I]),
     "bmg_fill_uniform": (I, [I, ctypes.c_ulonglong, P, P]),
@@ -394,6 +396,28 @@ class Mlp:
                                      er_out.ctypes.data_as(ctypes.c_void_p), _stream()))
         return loss.value, g, (er_in if er_in is not None else er_out)
 
+    def twogrid(self, coefs, vecs, eref=None, want_grad=True):
+        """The two-grid loss over a batch of crops: coefs (C, 5, n+2, n+2) and
+        vecs (C, K, n+2, n+2) CUDA float64, n = 7, 15 or 31; eref (C, K) CUDA
+        float64 or None.  With eref: (loss, gradient (numpy float32) or None,
+        energies (C, K) tensor); without: (None, None, Dendy's energies)."""
+        import numpy as np
+        if coefs.dim() != 4 or vecs.dim() != 4 or coefs.shape[0] != vecs.shape[0] or coefs.shape[1] != 5:
+            raise ValueError("coefs must be (C, 5, n+2, n+2) and vecs (C, K, n+2, n+2)")
+        C, K, m = vecs.shape[0], vecs.shape[1], vecs.shape[-1]
+        if coefs.shape[-1] != m or coefs.shape[-2] != m or vecs.shape[-2] != m:
+            raise ValueError("coefs and vecs must share the crop grid")
+        energies = torch.empty((C, K), dtype=torch.float64, device=vecs.device)
+        if eref is not None and tuple(eref.shape) != (C, K):
+            raise ValueError("eref must be (C, K)")
+        loss = ctypes.c_double(0.0)
+        g = np.empty(MLP_PARAMS, dtype=np.float32) if (want_grad and eref is not None) else None
+        _check(lib.bmg_mlp_twogrid(self._h, C, m - 2, _ptr(coefs, name="coefs"), K, _ptr(vecs, name="vecs"),
+                                   None if eref is None else _ptr(eref, name="eref"), _ptr(energies, name="energies"),
+                                   ctypes.byref(loss), None if g is None else g.ctypes.data_as(ctypes.c_void_p),
+                                   _stream()))
+        return (loss.value if eref is not None else None), g, energies
+
     def adam(self, lr: float):
         _check(lib.bmg_mlp_adam(self._h, ctypes.c_float(lr), _stream()))
 
@@ -415,6 +439,16 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def mlp_features(coef):
+    """(n_c^2, 18) FP32 features of every interior coarse point (bmg_mlp_features)."""
+    n = _n_of(coef)
+    nc = (n - 1) // 2
+    _need(coef, 5 * _grid(n), "coef")
+    X = torch.empty((nc * nc, 18), dtype=torch.float32, device=coef.device)
+    _check(lib.bmg_mlp_features(n, _ptr(coef, name="coef"), _ptr(X, torch.float32, "X"), _stream()))
+    return X
 
 
 def learned_interp(coef, delta):

@@ -887,17 +887,18 @@ int measure_factor(bmg_hierarchy* h, double* out) {
   };
   drop_graph();
   h->krylov = BMG_KRYLOV_NONE;
-  int rc = bmg_solve(h, f, x, 0.0, 8, &it, &rr);
+  int rc = bmg_solve(h, f, x, 0.0, 15, &it, &rr);
   h->krylov = krylov;
   drop_graph();
   cudaFree(x);
   cudaFree(f);
   if (rc != BMG_OK && rc != BMG_ENOTCONV) return rc;
-  if (h->hist.size() < 9 || !(h->hist[4] > 0)) {
+  // the asymptotic factor read off iterations 5 .. 15
+  if (h->hist.size() < 16 || !(h->hist[5] > 0)) {
     *out = 0.0;
     return BMG_OK;
   }
-  *out = std::pow(h->hist[8] / h->hist[4], 0.25);
+  *out = std::pow(h->hist[15] / h->hist[5], 0.1);
   return BMG_OK;
 }
 }  // namespace

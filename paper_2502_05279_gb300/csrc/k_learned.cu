@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "learned.h"
+#include "learned_device.cuh"
 
 namespace bmg {
 namespace {
@@ -157,83 +158,23 @@ __global__ void k_adam(float* __restrict__ par, const float* __restrict__ grad, 
 }
 
 // ---- learned weights (FP64) --------------------------------------------------------------
-// delta: (nc*nc, 4) logits (W, E, S, N edge of each interior coarse point).
-__device__ __forceinline__ double delta_at(const float* delta, int nc, int ic, int jc, int k) {
-  if (ic < 1 || jc < 1 || ic > nc || jc > nc) return 0.0;
-  return (double)delta[((size_t)(jc - 1) * nc + (ic - 1)) * NO + k];
-}
-
-// Edge points of cell (ic, jc): x-edge (2ic-1, 2jc) between (ic-1, jc) [E output]
-// and (ic, jc) [W output]; y-edge (2ic, 2jc-1) between (ic, jc-1) [N output] and
-// (ic, jc) [S output].  aux (optional) keeps S_D and q for the gradient.
+// delta: (nc*nc, 4) logits (W, E, S, N edge of each interior coarse point);
+// the per-cell formulas are in learned_device.cuh.
 __global__ void k_learned_edges(int n, const double* __restrict__ st, const float* __restrict__ delta,
                                 double* __restrict__ ci, double* __restrict__ aux) {
   int ic = blockIdx.x * blockDim.x + threadIdx.x;
   int jc = blockIdx.y * blockDim.y + threadIdx.y;
-  int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
+  int nc = (n - 1) / 2;
   if (ic > nc + 1 || jc > nc + 1) return;
-  size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
-  double ll = 0, lr = 0, lb = 0, la = 0, sdx = 0, qx = 0, sdy = 0, qy = 0;
-  Planes<double> A = planes_at(st, plane_size(n));
-  if (ic >= 1 && jc >= 1 && jc <= nc) {
-    size_t p = (size_t)(2 * jc) * ld + (2 * ic - 1);
-    double colW = radd(radd(A.a<5>(p, ld), A.a<1>(p, ld)), A.a<7>(p, ld));
-    double colE = radd(radd(A.a<8>(p, ld), A.a<2>(p, ld)), A.a<6>(p, ld));
-    double D = radd(radd(A.a<3>(p, ld), A.a<0>(p, ld)), A.a<4>(p, ld));
-    sdx = -rdiv(radd(colW, colE), D);
-    double uW = rmul(-colW, exp(delta_at(delta, nc, ic - 1, jc, 1)));
-    double uE = rmul(-colE, exp(delta_at(delta, nc, ic, jc, 0)));
-    qx = rdiv(uW, radd(uW, uE));
-    ll = rmul(sdx, qx);
-    lr = rmul(sdx, rsub(1.0, qx));
-  }
-  if (ic >= 1 && ic <= nc && jc >= 1) {
-    size_t p = (size_t)(2 * jc - 1) * ld + 2 * ic;
-    double rowS = radd(radd(A.a<5>(p, ld), A.a<3>(p, ld)), A.a<8>(p, ld));
-    double rowN = radd(radd(A.a<7>(p, ld), A.a<4>(p, ld)), A.a<6>(p, ld));
-    double D = radd(radd(A.a<1>(p, ld), A.a<0>(p, ld)), A.a<2>(p, ld));
-    sdy = -rdiv(radd(rowS, rowN), D);
-    double uS = rmul(-rowS, exp(delta_at(delta, nc, ic, jc - 1, 3)));
-    double uN = rmul(-rowN, exp(delta_at(delta, nc, ic, jc, 2)));
-    qy = rdiv(uS, radd(uS, uN));
-    lb = rmul(sdy, qy);
-    la = rmul(sdy, rsub(1.0, qy));
-  }
-  ci[CI_LL * psc + pc] = ll;
-  ci[CI_LR * psc + pc] = lr;
-  ci[CI_LB * psc + pc] = lb;
-  ci[CI_LA * psc + pc] = la;
-  if (aux) {
-    aux[0 * psc + pc] = sdx;
-    aux[1 * psc + pc] = qx;
-    aux[2 * psc + pc] = sdy;
-    aux[3 * psc + pc] = qy;
-  }
+  learned::edge_cell(planes_at(st, plane_size(n)), n + 2, nc, delta, ic, jc, ci, aux);
 }
 
-// Dendy's centre formula with the edge planes of ci.
 __global__ void k_learned_centres(int n, const double* __restrict__ st, double* __restrict__ ci) {
   int ic = blockIdx.x * blockDim.x + threadIdx.x;
   int jc = blockIdx.y * blockDim.y + threadIdx.y;
-  int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
+  int nc = (n - 1) / 2;
   if (ic > nc + 1 || jc > nc + 1) return;
-  size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
-  if (ic == 0 || jc == 0) {
-    for (int k = 0; k < 4; ++k) ci[k * psc + pc] = 0.0;
-    return;
-  }
-  Planes<double> A = planes_at(st, plane_size(n));
-  size_t p = (size_t)(2 * jc - 1) * ld + (2 * ic - 1);
-  double aO = A.a<0>(p, ld), aW = A.a<1>(p, ld), aE = A.a<2>(p, ld), aS = A.a<3>(p, ld), aN = A.a<4>(p, ld);
-  double aSW = A.a<5>(p, ld), aNE = A.a<6>(p, ld), aNW = A.a<7>(p, ld), aSE = A.a<8>(p, ld);
-  double lb_w = ci[CI_LB * psc + pc - 1], la_w = ci[CI_LA * psc + pc - 1];
-  double lb_e = ci[CI_LB * psc + pc], la_e = ci[CI_LA * psc + pc];
-  double ll_s = ci[CI_LL * psc + pc - ldc], lr_s = ci[CI_LR * psc + pc - ldc];
-  double ll_n = ci[CI_LL * psc + pc], lr_n = ci[CI_LR * psc + pc];
-  ci[CI_LSW * psc + pc] = -rdiv(radd(radd(aSW, rmul(aW, lb_w)), rmul(aS, ll_s)), aO);
-  ci[CI_LSE * psc + pc] = -rdiv(radd(radd(aSE, rmul(aE, lb_e)), rmul(aS, lr_s)), aO);
-  ci[CI_LNW * psc + pc] = -rdiv(radd(radd(aNW, rmul(aW, la_w)), rmul(aN, ll_n)), aO);
-  ci[CI_LNE * psc + pc] = -rdiv(radd(radd(aNE, rmul(aE, la_e)), rmul(aN, lr_n)), aO);
+  learned::centre_cell(planes_at(st, plane_size(n)), n + 2, nc, ic, jc, ci);
 }
 
 // ---- test-vector loss ------------------------------------------------------------------

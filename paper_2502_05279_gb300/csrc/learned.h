@@ -21,5 +21,10 @@ void launch_mlp_bwd(const float* X, int M, const float* par, const float* Z1, co
                     float* partial, float* grad, cudaStream_t s);
 void launch_adam(float* par, const float* grad, float* m, float* v, float lr, int step, cudaStream_t s);
 int mlp_backward_blocks(int M);
+// Two-grid training loss on crops (k_twogrid.cu): n = 7, 15 or 31.
+bool twogrid_size_ok(int n);
+int launch_twogrid(int n, int ncrop, int K, const double* coefs, const double* vecs, const float* delta,
+                   const double* eref, double weight, double* energies, float* ddelta, int* err, cudaStream_t s);
+void launch_features_crops(int n, int ncrop, const double* coefs, float* X, cudaStream_t s);
 
 }  // namespace bmg

@@ -22,6 +22,11 @@ struct bmg_mlp {
   float* zero_delta = nullptr;
   double *ci = nullptr, *aux = nullptr, *errs = nullptr, *Aes = nullptr, *dW = nullptr, *tx = nullptr, *ty = nullptr;
   double *partials = nullptr, *energies = nullptr, *scale = nullptr;
+  // two-grid training workspace (rows = crops x coarse points)
+  size_t tg_rows = 0;
+  float *tg_X = nullptr, *tg_Z1 = nullptr, *tg_Z2 = nullptr, *tg_out = nullptr, *tg_dout = nullptr,
+        *tg_partial = nullptr;
+  int* tg_err = nullptr;
 };
 
 #define CK(call)                               \
@@ -69,6 +74,30 @@ int ensure_ws(bmg_mlp* m, int n, int K) {
 }
 
 bool level_size_ok(int n) { return n >= 3 && ((n + 1) & n) == 0; }
+
+void free_tg(bmg_mlp* m) {
+  void* ptrs[] = {m->tg_X, m->tg_Z1, m->tg_Z2, m->tg_out, m->tg_dout, m->tg_partial, m->tg_err};
+  for (void* p : ptrs) cudaFree(p);
+  m->tg_X = m->tg_Z1 = m->tg_Z2 = m->tg_out = m->tg_dout = m->tg_partial = nullptr;
+  m->tg_err = nullptr;
+  m->tg_rows = 0;
+}
+
+int ensure_tg(bmg_mlp* m, size_t rows) {
+  if (rows <= m->tg_rows) return BMG_OK;
+  free_tg(m);
+  int rc;
+  if ((rc = alloc0(&m->tg_X, rows * MLP_IN)) || (rc = alloc0(&m->tg_Z1, rows * MLP_HID)) ||
+      (rc = alloc0(&m->tg_Z2, rows * MLP_HID)) || (rc = alloc0(&m->tg_out, rows * MLP_OUT)) ||
+      (rc = alloc0(&m->tg_dout, rows * MLP_OUT)) ||
+      (rc = alloc0(&m->tg_partial, (size_t)mlp_backward_blocks((int)rows) * MLP_PARAMS)) ||
+      (rc = alloc0(&m->tg_err, 1))) {
+    free_tg(m);
+    return rc;
+  }
+  m->tg_rows = rows;
+  return BMG_OK;
+}
 
 }  // namespace
 
@@ -162,6 +191,44 @@ int bmg_mlp_loss_grad(bmg_mlp* m, int n, const double* coef, int K, const double
   return std::isfinite(L) ? BMG_OK : set_error(BMG_ENAN, "bmg_mlp_loss_grad: loss is not finite");
 }
 
+int bmg_mlp_twogrid(bmg_mlp* m, int ncrop, int n, const double* coefs, int K, const double* vecs,
+                    const double* eref, double* energies, double* loss, float* grad, void* stream) {
+  if (!m || ncrop < 1 || !twogrid_size_ok(n) || !coefs || K < 1 || !vecs || !energies || (eref && !loss))
+    return set_error(BMG_EINVAL, "bmg_mlp_twogrid: bad argument (n must be 7, 15 or 31)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nc = (n - 1) / 2;
+  const size_t rows = (size_t)ncrop * nc * nc;
+  if (rows > (size_t)1 << 30) return set_error(BMG_EINVAL, "bmg_mlp_twogrid: too many crops");
+  int rc;
+  if ((rc = ensure_tg(m, rows))) return rc;
+  CK(cudaMemsetAsync(m->tg_err, 0, sizeof(int), s));
+  const float* delta = nullptr;
+  if (eref) {
+    launch_features_crops(n, ncrop, coefs, m->tg_X, s);
+    launch_mlp_fwd(m->tg_X, (int)rows, m->par, m->tg_Z1, m->tg_Z2, m->tg_out, s);
+    delta = m->tg_out;
+  }
+  if ((rc = launch_twogrid(n, ncrop, K, coefs, vecs, delta, eref, 1.0 / ncrop, energies, m->tg_dout, m->tg_err, s)))
+    return rc;
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, m->tg_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return set_error(BMG_ESINGULAR, "bmg_mlp_twogrid: a crop's coarse operator has a non-positive pivot");
+  if (!eref) return BMG_OK;
+  std::vector<double> e((size_t)ncrop * K), r((size_t)ncrop * K);
+  CK(cudaMemcpyAsync(e.data(), energies, sizeof(double) * e.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r.data(), eref, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, s));
+  launch_mlp_bwd(m->tg_X, (int)rows, m->par, m->tg_Z1, m->tg_Z2, m->tg_dout, m->tg_partial, m->grad, s);
+  if (grad) CK(cudaMemcpyAsync(grad, m->grad, sizeof(float) * MLP_PARAMS, cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  double L = 0.0;
+  for (size_t k = 0; k < e.size(); ++k) L += e[k] / r[k];
+  L /= (double)e.size();
+  *loss = L;
+  return std::isfinite(L) ? BMG_OK : set_error(BMG_ENAN, "bmg_mlp_twogrid: loss is not finite");
+}
+
 int bmg_mlp_adam(bmg_mlp* m, float lr, void* stream) {
   if (!m || !(lr > 0.0f)) return set_error(BMG_EINVAL, "bmg_mlp_adam: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -185,6 +252,14 @@ int bmg_mlp_infer(const bmg_mlp* m, int n, const double* coef, float* delta, voi
   return cuda_check(cudaStreamSynchronize(s), "bmg_mlp_infer");
 }
 
+int bmg_mlp_features(int n, const double* coef, float* X, void* stream) {
+  if (!level_size_ok(n) || !coef || !X) return set_error(BMG_EINVAL, "bmg_mlp_features: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_features(n, coef, X, s);
+  CK(cudaGetLastError());
+  return cuda_check(cudaStreamSynchronize(s), "bmg_mlp_features");
+}
+
 int bmg_learned_interp(int n, const double* coef, const float* delta, double* ci, void* stream) {
   if (!level_size_ok(n) || !coef || !delta || !ci) return set_error(BMG_EINVAL, "bmg_learned_interp: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -204,6 +279,7 @@ int bmg_fill_uniform(int n, unsigned long long seed, double* x, void* stream) {
 void bmg_mlp_free(bmg_mlp* m) {
   if (!m) return;
   free_ws(m);
+  free_tg(m);
   cudaFree(m->par);
   cudaFree(m->grad);
   cudaFree(m->m);

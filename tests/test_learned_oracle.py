@@ -155,3 +155,171 @@ def test_learned_weights_keep_constants_for_any_logits(scale):
     x = np.zeros((n + 2, n + 2))
     bx.interp_correct(ci, ec, x)
     assert np.abs(x[3:n - 1, 3:n - 1] - 1.0).max() <= 1e-12
+
+
+# ---- the two-grid loss ---------------------------------------------------------------------
+
+def _dense_two_grid(planes, ci, nu1=2, nu2=1):
+    """E = S^nu2 (I - P (P^T A P)^{-1} P^T A) S^nu1 from dense matrices built
+    from their definitions, independently of the oracle's sweeps and
+    transfers: A entry by entry from the stencil planes and their symmetry;
+    P column by column from the eight weight labels (the coarse point's own
+    fine point 1, edge points toward it, centre points toward it); S as the
+    product over the colours of I - J_c D^{-1} A."""
+    n = bx.size_of(planes)
+    nc = (n - 1) // 2
+    m, mc = n * n, nc * nc
+    O, W, S, SW, NW = planes
+    A = np.zeros((m, m))
+    idx = lambda i, j: (j - 1) * n + (i - 1)
+    for j in range(1, n + 1):
+        for i in range(1, n + 1):
+            p = idx(i, j)
+            A[p, p] = O[j, i]
+            for di, dj, val in ((-1, 0, W[j, i]), (1, 0, W[j, i + 1]), (0, -1, S[j, i]), (0, 1, S[j + 1, i]),
+                                (-1, -1, SW[j, i]), (1, 1, SW[j + 1, i + 1]), (-1, 1, NW[j, i]),
+                                (1, -1, NW[j - 1, i + 1])):
+                if 1 <= i + di <= n and 1 <= j + dj <= n:
+                    A[p, idx(i + di, j + dj)] = val
+    P = np.zeros((m, mc))
+    for jc in range(1, nc + 1):
+        for ic in range(1, nc + 1):
+            c = (jc - 1) * nc + (ic - 1)
+            I, J = 2 * ic, 2 * jc
+            P[idx(I, J), c] = 1.0
+            # edge points: x-edge (I-1, J) of cell (ic, jc) toward its east point LR; (I+1, J) of cell (ic+1, jc)
+            # toward its west point LL; y-edges likewise with LA (cell (ic, jc)) and LB (cell (ic, jc+1))
+            P[idx(I - 1, J), c] = ci[bx.LR, jc, ic]
+            P[idx(I + 1, J), c] = ci[bx.LL, jc, ic + 1]
+            P[idx(I, J - 1), c] = ci[bx.LA, jc, ic]
+            P[idx(I, J + 1), c] = ci[bx.LB, jc + 1, ic]
+            # centre points of the four cells around the coarse point
+            P[idx(I - 1, J - 1), c] = ci[bx.LNE, jc, ic]
+            P[idx(I + 1, J - 1), c] = ci[bx.LNW, jc, ic + 1]
+            P[idx(I - 1, J + 1), c] = ci[bx.LSE, jc + 1, ic]
+            P[idx(I + 1, J + 1), c] = ci[bx.LSW, jc + 1, ic + 1]
+    Sm = np.eye(m)
+    Dinv = np.diag(1.0 / np.diag(A))
+    for pi, pj in bx.COLOURS9:
+        J = np.zeros((m, m))
+        for j in range(1, n + 1):
+            for i in range(1, n + 1):
+                if i % 2 == pi and j % 2 == pj:
+                    J[idx(i, j), idx(i, j)] = 1.0
+        Sm = (np.eye(m) - J @ Dinv @ A) @ Sm
+    Ac = P.T @ A @ P
+    CGC = np.eye(m) - P @ np.linalg.solve(Ac, P.T @ A)
+    return np.linalg.matrix_power(Sm, nu2) @ CGC @ np.linalg.matrix_power(Sm, nu1), A, Sm
+
+
+def _interior(v):
+    return v[1:-1, 1:-1].reshape(-1)
+
+
+def test_two_grid_is_the_dense_error_propagation():
+    """E e from the oracle's sweeps, transfers and coarse solve equals the
+    dense two-grid matrix applied to e, and the loss's energies equal
+    e^T E^T A E e, for Dendy's and for learned weights."""
+    planes = hc_planes(15, seed=9, block=2)
+    nc = 7
+    vecs = [w.rhs_uniform(15, 300 + k) for k in range(3)]
+    for delta in (np.zeros((nc * nc, 4)), w.normal(5, nc * nc * 4).reshape(nc * nc, 4) * 0.7):
+        ci = ln.learned_interp(planes, delta)
+        E, A, _ = _dense_two_grid(planes, ci)
+        Ac = ln.coarse_operator(planes, ci)
+        energies = ln.two_grid_energies(planes, ci, vecs)
+        for e, en in zip(vecs, energies):
+            want = E @ _interior(e)
+            got = _interior(ln.two_grid(planes, ci, e, Ac)[3])
+            assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+            assert abs(en - want @ A @ want) <= 1e-12 * abs(en)
+
+
+def test_two_grid_is_the_two_level_vcycle_and_its_spectral_radius():
+    """With Dendy's weights the two-grid operator is the oracle's own V(2,1)
+    on a two-level hierarchy (coarsest = (n-1)/2) applied to e with f = 0, and
+    the solve on that hierarchy converges at the dense operator's spectral
+    radius (measured asymptotic factor within 5 %)."""
+    n, nc = 15, 7
+    planes = hc_planes(n, seed=10, block=2)
+    levels = bx.setup(9, planes, coarsest=nc)
+    assert len(levels) == 2
+    ci = levels[0].ci
+    Ac = ln.coarse_operator(planes, ci)
+    for k in range(3):
+        e = w.rhs_uniform(n, 400 + k)
+        x = e.copy()
+        bx.vcycle(levels, 0, x, np.zeros_like(e))
+        got = ln.two_grid(planes, ci, e, Ac)[3]
+        assert np.abs(got - x).max() <= 1e-12 * np.abs(x).max()
+    E, _, _ = _dense_two_grid(planes, ci)
+    rho = max(abs(np.linalg.eigvals(E)))
+    _, hist = bx.solve(levels, w.rhs_uniform(n, 5), tol=1e-300, maxit=15)
+    measured = (hist[15] / hist[5]) ** 0.1                  # iterations 5 .. 15, above the rounding floor
+    assert abs(measured - rho) <= 0.05 * rho, (measured, rho)
+
+
+def test_error_sweep_adjoint_is_the_transpose():
+    planes = hc_planes(15, seed=11, block=2)
+    d = np.zeros_like(planes[0])
+    bx.at(d, 0, 0)[...] = 1.0 / bx.at(planes[0], 0, 0)
+    _, _, Sm = _dense_two_grid(planes, bx.dendy_interp(planes))
+    for k in range(3):
+        x, y = w.rhs_uniform(15, 500 + k), w.rhs_uniform(15, 600 + k)
+        sx = x.copy()
+        ln.error_sweep(planes, d, sx)
+        sty = y.copy()
+        ln.error_sweep_adjoint(planes, d, sty)
+        assert np.abs(_interior(sx) - Sm @ _interior(x)).max() <= 1e-12 * np.abs(_interior(sx)).max()
+        assert np.abs(_interior(sty) - Sm.T @ _interior(y)).max() <= 1e-12 * np.abs(_interior(sty)).max()
+        assert abs(bx.dot(sx, y) - bx.dot(x, sty)) <= 1e-12 * abs(bx.dot(sx, y))
+
+
+def test_two_grid_gradient_matches_finite_differences():
+    n, nc = 15, 7
+    planes = hc_planes(n, seed=12, block=2)
+    vecs = [w.rhs_uniform(n, 700 + k) for k in range(3)]
+    ref = ln.two_grid_reference(planes, vecs)
+    L0, _ = ln.two_grid_loss_grad(planes, np.zeros((nc * nc, 4)), vecs, ref)
+    assert abs(L0 - 1.0) <= 1e-12
+    delta = w.normal(13, nc * nc * 4).reshape(nc * nc, 4) * 0.4
+    L, g = ln.two_grid_loss_grad(planes, delta, vecs, ref)
+    h = 1e-6
+    for idx in [(0, 0), (8, 1), (24, 2), (31, 3), (48, 0), (17, 1), (40, 2)]:
+        dp, dm = delta.copy(), delta.copy()
+        dp[idx] += h
+        dm[idx] -= h
+        fd = (ln.two_grid_loss_grad(planes, dp, vecs, ref)[0] - ln.two_grid_loss_grad(planes, dm, vecs, ref)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-8 * np.abs(g).max(), (idx, fd, g[idx])
+
+
+def test_model_two_grid_gradient_matches_finite_differences():
+    n, nc = 15, 7
+    crops = []
+    for s in range(2):
+        planes = hc_planes(n, seed=20 + s, block=2)
+        vecs = [w.rhs_uniform(n, 800 + 10 * s + k) for k in range(2)]
+        crops.append((planes, vecs, ln.two_grid_reference(planes, vecs)))
+    theta = ln.init_params(w.normal(21, ln.N_IN * ln.N_HID + ln.N_HID * ln.N_HID))
+    p = ln.unpack(theta)
+    p["W3"][...] = w.normal(22, ln.N_HID * ln.N_OUT).reshape(ln.N_HID, ln.N_OUT) * 0.1
+    theta = ln.pack(p)
+    L, g = ln.model_two_grid_loss_grad(theta, crops)
+    h = 1e-6
+    off_w3 = ln.N_IN * ln.N_HID + ln.N_HID + ln.N_HID * ln.N_HID + ln.N_HID
+    for k in (0, 100, ln.N_IN * ln.N_HID + 3, off_w3 + 5, off_w3 + 200, ln.N_PARAMS - 2):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (ln.model_two_grid_loss_grad(tp, crops)[0] - ln.model_two_grid_loss_grad(tm, crops)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-5 * abs(fd) + 1e-8 * np.abs(g).max(), (k, fd, g[k])
+
+
+def test_training_crops_are_dirichlet_problems_of_the_family():
+    crops = w.training_crops(4, crops_per_problem=2)
+    assert len(crops) == 8
+    for planes, vecs in crops:
+        assert planes.shape == (5, 33, 33) and vecs.shape == (4, 33, 33)
+        k = -3.0 * planes[3][2:-1, 2:-1]                       # SW = -k/3 of the cell below-left
+        assert set(np.unique(np.round(k, 6))) <= {1.0, 1e6}
+        assert not vecs[:, 0].any() and not vecs[:, -1].any()

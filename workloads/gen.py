@@ -274,3 +274,28 @@ def high_contrast_problem(n: int = 4095, block: int = 8, lo: float = 1.0, hi: fl
     """Binary blocks k in {1, 1e6} on 8 x 8 cell tiles (the learned-interpolation
     family); RHS seed = seed + 100000."""
     return binary_contrast_problem(n, block, lo, hi, seed_k=seed, seed_f=seed + 100000)
+
+
+def training_crops(count: int, first_seed: int = 1000, n: int = 255, m: int = 31, block: int = 8,
+                   lo: float = 1.0, hi: float = 1e6, vectors: int = 4, crops_per_problem: int = 1):
+    """Training inputs of the learned interpolation: for each of `count`
+    problems of the family (n x n interior, k in {lo, hi} on block x block
+    cell tiles, Bernoulli 0.5, cell field seed first_seed + s), crops of
+    (m+1) x (m+1) cells at offsets that are multiples of the tile size (so the
+    tile edges fall on the crop's coarse grid lines as they do in the full
+    problem), each assembled as its own m x m Dirichlet problem, with `vectors`
+    uniform[-1,1) error vectors.  Offsets: draws of stream 7_000_000 + s;
+    vectors: seeds 8_000_000 + (s * crops_per_problem + c) * vectors + k.
+    Returns a list of (planes (5, m+2, m+2), vectors (vectors, m+2, m+2))."""
+    out = []
+    slots = (n + 1 - (m + 1)) // block + 1
+    for s in range(first_seed, first_seed + count):
+        cells = binary_blocks(n, block, lo, hi, s)
+        off = (splitmix64(7_000_000 + s, 2 * crops_per_problem) % np.uint64(slots)).astype(np.int64) * block
+        for c in range(crops_per_problem):
+            j0, i0 = int(off[2 * c]), int(off[2 * c + 1])
+            planes = fe9_from_cells(cells[j0:j0 + m + 1, i0:i0 + m + 1].copy())
+            base = 8_000_000 + (s * crops_per_problem + c) * vectors
+            vecs = np.stack([rhs_uniform(m, base + k) for k in range(vectors)])
+            out.append((planes, vecs))
+    return out
