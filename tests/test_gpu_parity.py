@@ -160,23 +160,21 @@ def check_fcg(bmg_x, got_hist, want, want_dev, mixed, planes=None, f=None, tol=N
     want_dev = the oracle's FCG run with the device's summation order
     (tests/reduction_order.py): iterates and history equal bit for bit.
     want = the oracle's plain-sum run: the reading for FCG, identical
-    iteration counts and every entry within 1e-9 r0, within 1e-6 relative
-    while above 1e-3 r0.  The rounding of alpha and beta propagates through
-    the recurrences, amplified by the conditioning (measured up to 3e-11 r0
-    in FP64 at contrast 1e6) and, with an FP32/BF16 preconditioner, by the
-    FP32 rounding of z (up to 1e-10 r0).  With planes and f given, the
-    oracle's FP64 residual of the returned x meets the tolerance."""
+    iteration counts, entries above 1e-3 r0 within 1e-6 relative and the
+    others within 1e-9 r0.  The rounding of alpha and beta propagates through
+    the recurrences, amplified by the conditioning (measured up to 4e-9
+    relative in FP64 at contrast 1e6, where the history is not monotone) and,
+    with an FP32/BF16 preconditioner, by the FP32 rounding of z (up to 9e-9
+    relative, 1e-10 r0).  With planes and f given, the oracle's FP64 residual
+    of the returned x meets the tolerance."""
     xd, hd = want_dev
     assert np.array_equal(host(bmg_x)[1:-1, 1:-1], xd[1:-1, 1:-1])
     assert list(got_hist) == list(hd)
     xw, hw = want
     assert len(got_hist) == len(hw)
-    a, b = 1e-9, 1e-6
     r0 = hw[0]
     for g, t in zip(got_hist, hw):
-        assert abs(g - t) <= a * r0
-        if t >= 1e-3 * r0:
-            assert abs(g - t) <= b * t
+        assert abs(g - t) <= (1e-6 * t if t >= 1e-3 * r0 else 1e-9 * r0)
     if planes is not None:
         p64 = bx.drop_ghost_couplings(np.array(planes, dtype=np.float64))
         assert bx.norm(bx.residual(p64, host(bmg_x), f)) <= 2 * tol * r0

@@ -69,8 +69,8 @@ def test_fcg_reading_holds_between_summation_orders(case, n, prec):
     take different iterates at rounding level, amplified by the conditioning
     and, with an FP32/BF16 preconditioner, by the FP32 rounding of z.  The
     stated reading for FCG holds between them: identical iteration counts,
-    every entry within 1e-9 ||r_0|| and within 1e-6 relative while above
-    1e-3 ||r_0||."""
+    entries above 1e-3 ||r_0|| within 1e-6 relative, the others within
+    1e-9 ||r_0||."""
     from oracle import boxmg as bx
     from oracle import mixed as mx
     from reduction_order import device_inner
@@ -90,6 +90,4 @@ def test_fcg_reading_holds_between_summation_orders(case, n, prec):
     (xa, ha), (xb, hb) = run(), run(device_inner())
     assert len(ha) == len(hb)
     for g, t in zip(hb, ha):
-        assert abs(g - t) <= 1e-9 * ha[0]
-        if t >= 1e-3 * ha[0]:
-            assert abs(g - t) <= 1e-6 * t
+        assert abs(g - t) <= (1e-6 * t if t >= 1e-3 * ha[0] else 1e-9 * ha[0])
