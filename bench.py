@@ -55,6 +55,11 @@ WORKLOADS = {
              "seed 4; RHS U[-1,1) seed 7; 11 levels (the 8191^2 workload's recipe at a size ncu captures)",
         make=lambda: w.lognormal_problem(4095, 2.0, 32.0, seed_k=4, seed_f=7)),
 }
+WORKLOADS["learned4095"] = dict(
+    text="4095x4095 interior, 9-point Q1 FE, k in {1,1e6} on 8x8 cell tiles (Bernoulli 0.5, seed 6), RHS U[-1,1) "
+         "seed 100006; the learned-interpolation family: the network is trained on the GPU on 31^2 crops of 255^2 "
+         "problems of the family (seeds 1000..) with the two-grid loss, then bmg_setup measures learned vs Dendy",
+    make=lambda: w.high_contrast_problem(4095, seed=6))
 DEFAULT_WORKLOAD = "lognormal8191"
 
 # DRAM bytes (read + write) per fine point of one launch of a level-0 kernel,
@@ -619,12 +624,42 @@ def run_ours(args, rank, local_rank, world):
         p: sorted(([r["level"], r["kernel"] + ("32" if r["fp32"] else ""), round(r["launches"] / 3), round(r["ms"] / 3 * 1e3, 1)]
                    for r in v["prof"]), key=lambda e: -e[3])
         for p, v in variants.items()}
+    if args.workload == "learned4095":
+        out["variants"]["learned"] = learned_variant(args, kind, coef, rhs, n, N, world)
     for v in variants.values():
         v["h"].close()
         v["hk"].close()
     out["cpu_baseline"] = cpu_baseline(args, kind, planes, f) if not args.no_cpu and world == 1 else None
     print(json.dumps(out))
     ranks.close()
+
+
+def learned_variant(args, kind, coef, rhs, n, N, world):
+    """Train the network on the GPU (two-grid loss on 31^2 crops of the 255^2
+    family), then set up the evaluation problem with it: bmg_setup measures the
+    learned and the Dendy V(2,1) factors and keeps the better; report both,
+    the training and setup times, flexible-CG time to 1e-10 (or the residual
+    reached) and the cycle rate of the hierarchy the setup kept."""
+    import torch
+    import paper_2502_05279_gb300 as bmg
+    from paper_2502_05279_gb300 import learned_training as lt
+    t0 = time.perf_counter()
+    mlp, hist, _, train_s = lt.train(n_problems=args.learned_problems, epochs=args.learned_epochs, batch=152,
+                                     log=lambda *_: None)
+    prep_train_s = time.perf_counter() - t0
+    ev = lt.evaluate(mlp, n=n, seed=6, tol=1e-10, maxit=500)
+    h = bmg.Hierarchy(kind, coef, mlp=mlp, arith=args.arith)
+    x = torch.zeros_like(rhs)
+    h.time_cycles(rhs, x, max(args.warmup, 3))
+    ms = h.time_cycles(rhs, x, args.steps)
+    used = h.interp_info()[0]
+    h.close()
+    mlp.close()
+    return {"value": world * N * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps, "kept": used,
+            "train": {"problems": args.learned_problems, "crops": args.learned_problems, "epochs": args.learned_epochs,
+                      "two_grid_loss_by_epoch": hist, "train_s": round(train_s, 3),
+                      "prepare_and_train_s": round(prep_train_s, 2)},
+            "evaluation": ev}
 
 
 def measured_peak(key, fallback):
@@ -800,6 +835,8 @@ def main():
                     help="time one hierarchy's cycles only (short run for profilers)")
     ap.add_argument("--krylov", choices=("none", "fcg"), default="none", help="solve mode for --only")
     ap.add_argument("--smoother", default="auto", help="FP32 Gauss-Seidel kernel for --only (auto, rows, tile0..4)")
+    ap.add_argument("--learned-problems", type=int, default=2000, help="training problems (one crop each)")
+    ap.add_argument("--learned-epochs", type=int, default=8, help="training epochs of the learned variant")
     ap.add_argument("--arith", choices=("rounded", "fused"), default="fused",
                     help="cycle arithmetic: fused multiply-adds (default) or one rounding per operation")
     args = ap.parse_args()
