@@ -72,12 +72,10 @@ DEFAULT_WORKLOAD = "lognormal8191"
 NCU_DRAM_BYTES_PER_POINT = {
     "k_gs_strip64 56xW cp.async/6 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4"),
     "k_gs_strip64 56xW cp.async/4 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4 (shape 2 capture; same rows)"),
-    "k_gs_strip2_ring<float> 48xW bulk/4": (145.9e6 / 2047 ** 2, "fe2047-binary1e4"),
-    "k_gs_strip<float> 56xW bulk/4": (138.1e6 / 2047 ** 2, "fe2047-binary1e4"),
 }
-TILE_SHAPES = ("56xW bulk/4", "56x8 bulk/4", "56x16 bulk/4", "56x32 bulk/4", "56x32 regs", "56x16 regs")
+TILE_SHAPES = ("56xW bulk/4", "56xW bulk/6", "56xW bulk/8", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
-PAIR_SHAPES = ("48xW bulk/4", "48x16 bulk/4", "48x32 bulk/6", "48x26 bulk/4")   # W: one wave
+PAIR_SHAPES = ("48xW bulk/4", "48xW bulk/6", "48xW bulk/8", "48x26 bulk/4")   # W: one wave
 
 
 BATCHED = dict(text="256 independent 9-point Q1 problems, sides uniform from {63,127,255,511,1023} (seed 5), "

@@ -86,6 +86,7 @@ struct Level {
   int fused = 0;          // 1: the cycle's multiply-adds on this level are fused (BMG_ARITH_FUSED)
   int tile64 = -1;        // FP64 sweeps: -1 row kernel (in place), else shape of the FP64 one-pass kernel
   double* x64b = nullptr; // second iterate of an FP64 level swept by the one-pass kernel
+  float* pk32 = nullptr;  // the FP32 / BF16 stencil packed per point (StencilView::pk)
 };
 
 StencilView<double, double> view64(const Level& L) {
@@ -95,11 +96,12 @@ StencilView<double, double> view64(const Level& L) {
 StencilView<float, float> view32(const Level& L) {
   size_t ps = plane_stride32(L.n);
   return {L.st32, L.st32 + ps, L.st32 + 2 * ps, L.st32 + 3 * ps, L.st32 + 4 * ps, L.st32 + 5 * ps,
-          L.n,    L.n + 2,       L.fused};
+          L.n,    L.n + 2,       L.fused,         L.pk32};
 }
 StencilView<float, __nv_bfloat16> viewbf(const Level& L) {
   size_t ps = plane_stride32(L.n);
-  return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2, L.fused};
+  return {L.od32, L.off16, L.off16 + ps, L.off16 + 2 * ps, L.off16 + 3 * ps, L.od32 + ps, L.n, L.n + 2, L.fused,
+          L.pk32};
 }
 
 }  // namespace
@@ -744,6 +746,7 @@ void free_level(Level& L, bool shared_ops = false) {
     L.off16 = nullptr;
     L.od32 = nullptr;
     L.ci32 = nullptr;
+    L.pk32 = nullptr;
   }
   cudaFree(L.st);
   cudaFree(L.ci);
@@ -754,6 +757,7 @@ void free_level(Level& L, bool shared_ops = false) {
   gfree(L.st32);
   gfree(L.off16);
   gfree(L.od32);
+  gfree(L.pk32);
   cudaFree(L.ci32);
   gfree(L.x32);
   gfree(L.x32b);
@@ -844,6 +848,13 @@ int setup_impl(bmg_hierarchy* h, const bmg_stencil* A, int n, const bmg_opts* o)
       }
       if (l + 1 < h->nlev && (rc = dalloc(&L.ci32, 8 * plane_size(h->lv[l + 1].n)))) return rc;
       launch_lower32(L.n, L.bf16 ? nullptr : L.st, L.bf16 ? nullptr : L.st32, L.ci, L.ci32, s);
+      if (l + 1 < h->nlev) {   // the packed copy the bulk-copy sweeps stream (guard band after it too)
+        if ((rc = galloc(&L.pk32, L.n, L.bf16 ? PK_WORDS_BF16 : PK_WORDS_F32, s))) return rc;
+        if (L.bf16)
+          launch_pack_bf16(L.n, L.off16, L.od32, L.pk32, s);
+        else
+          launch_pack32(L.n, L.st32, L.pk32, s);
+      }
       if ((rc = galloc(&L.x32, L.n, 1, s))) return rc;
       if ((rc = galloc(&L.f32, L.n, 1, s))) return rc;
     }
@@ -1988,6 +1999,7 @@ int clone_state(const bmg_hierarchy* h0, cudaStream_t s, bmg_hierarchy** out) {
     L.st = S.st;
     L.ci = S.ci;
     L.st32 = S.st32;
+    L.pk32 = S.pk32;
     L.off16 = S.off16;
     L.od32 = S.od32;
     L.ci32 = S.ci32;

@@ -351,14 +351,17 @@ __device__ __forceinline__ void gs_strip_body(const StencilView<float, S>& v, co
 
 // ---- the strip walk fed by bulk copies -------------------------------------------------
 // The same walk, with the strip's rows streamed into a per-warp ring of RING
-// row slots in shared memory by bulk asynchronous copies (one lane issues 7
-// copies per row, one mbarrier per slot counts the bytes), so that rows are
+// row slots in shared memory by bulk asynchronous copies (three copies per
+// row: x, f and the level's packed stencil, one point's d, w, s, sw, nw
+// together; one mbarrier per slot counts the bytes), so that rows are
 // requested RING/2 steps before they are used without holding them in
-// registers.  A copy must start on a 16-byte boundary: each array row segment
-// is copied from the aligned address at or below its first column (at most 7
-// elements earlier) for 68 floats / 72 bf16 values, which requires every array
-// base to be 16-byte aligned with STRIP_GUARD readable elements before and
-// after it.  A wait that does not complete within STRIP_WAIT_NS (or
+// registers.  Few large copies matter: the copy unit accepts them at a
+// limited rate, and seven copies per row (one per array) kept the warps
+// waiting on the copy issue more than on the data.  A copy must start on a
+// 16-byte boundary: each row segment is copied from the point at or below its
+// first column whose index is a multiple of 4 (at most 3 points earlier) for
+// 68 points, which requires every array base to be 16-byte aligned with
+// STRIP_GUARD readable points before and after it.  A wait that does not complete within STRIP_WAIT_NS (or
 // STRIP_WAIT_LIMIT polls) sets
 // strip_timeout, waits (bounded) for the warp's copies in flight and returns.
 constexpr long STRIP_WAIT_LIMIT = 1L << 20;                 // polls
@@ -366,9 +369,10 @@ constexpr unsigned long long STRIP_WAIT_NS = 500000000ull;   // 0.5 s
 
 template <typename S>
 struct StripRing {
-  static constexpr int CF = 68, CS = sizeof(S) == 4 ? 68 : 72;      // elements copied per row segment
-  static constexpr unsigned BF = CF * 4, BS = CS * sizeof(S);       // bytes (multiples of 16)
-  static constexpr unsigned SLOT = 3 * BF + 4 * BS;                 // one row of the 7 arrays
+  static constexpr int CP = 68;                                     // points copied per row segment
+  static constexpr int PK = sizeof(S) == 4 ? PK_WORDS_F32 : PK_WORDS_BF16;   // packed words per point
+  static constexpr unsigned BF = CP * 4, BP = CP * PK * 4;          // bytes (multiples of 16)
+  static constexpr unsigned SLOT = 2 * BF + BP;                     // one row: x, f, packed stencil
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -411,6 +415,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Warp-uniform bounded wait for phase `parity` of bar: false once
 // STRIP_WAIT_NS of wall-clock time or STRIP_WAIT_LIMIT polls have passed.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (__all_sync(0xffffffffu, mbar_try(bar, parity))) return true;   // the usual case: the row is there
   const unsigned long long t0 = global_ns();
   for (long it = 0; it < STRIP_WAIT_LIMIT; ++it) {
     if (__all_sync(0xffffffffu, mbar_try(bar, parity))) return true;
@@ -419,63 +424,83 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
-template <typename S>
-struct StripSrc {           // the 7 arrays the walk reads
-  const float *x, *f, *d;
-  const S *w, *s, *sw, *nw;
+struct StripSrc {           // the 3 arrays the walk reads
+  const float *x, *f, *pk;
 };
 
-// lane 0: request row j into `slot`: arm the slot's mbarrier for the row's
-// bytes and copy the 7 arrays' row segments.  The caller's __syncwarp orders
-// the warp's earlier reads of the slot before the fence.
+// Request row j into `slot`, called by the whole warp: lane 0 arms the slot's
+// mbarrier for the row's bytes, then lanes 0, 1, 2 copy the row segments of
+// x, f and the packed stencil.  The caller's __syncwarp orders the warp's
+// earlier reads of the slot before the fences.
 template <typename S>
-__device__ __forceinline__ void ring_issue(const StripSrc<S>& A, int ld, int icol, int j, unsigned char* slot,
-                                           unsigned long long* bar) {
+__device__ __forceinline__ void ring_issue_warp(const StripSrc& A, int ld, int icol, int j, unsigned char* slot,
+                                                unsigned long long* bar) {
   using RG = StripRing<S>;
-  const long long e = (long long)j * ld + icol;   // first column of the row segment
-  const long long e4 = e - (e & 3), e8 = e - (e & (16 / (long long)sizeof(S) - 1));
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  mbar_expect_tx(bar, RG::SLOT);
-  bulk_copy(slot, A.x + e4, RG::BF, bar);
-  bulk_copy(slot + RG::BF, A.f + e4, RG::BF, bar);
-  bulk_copy(slot + 2 * RG::BF, A.d + e4, RG::BF, bar);
-  unsigned char* q = slot + 3 * RG::BF;
-  bulk_copy(q, A.w + e8, RG::BS, bar);
-  bulk_copy(q + RG::BS, A.s + e8, RG::BS, bar);
-  bulk_copy(q + 2 * RG::BS, A.sw + e8, RG::BS, bar);
-  bulk_copy(q + 3 * RG::BS, A.nw + e8, RG::BS, bar);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, RG::SLOT);
+  }
+  __syncwarp();
+  if (lane < 3) {
+    const long long e = (long long)j * ld + icol;   // first point of the row segment
+    const long long e4 = e - (e & 3);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (lane < 2)
+      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + e4, RG::BF, bar);
+    else
+      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * e4, RG::BP, bar);
+  }
 }
 
 // every lane: its two columns of row j from a filled slot.  Columns or rows
 // outside [0, n+1]^2 hold stale values: they feed only lanes and rows whose
 // updates and stores are switched off.
+__device__ __forceinline__ void packed_read(const float* q, float& d, float& w, float& s, float& sw, float& nw) {
+  d = q[0];
+  w = q[1];
+  s = q[2];
+  sw = q[3];
+  nw = q[4];
+}
+
+// The BF16 halves widened to FP32 once, when the row is read (exact), so that
+// the walk's row sums take FP32 coefficients from registers.
+__device__ __forceinline__ void packed_read_wide(const float* q, bool bf16, float& d, float& w, float& s, float& sw,
+                                                 float& nw) {
+  if (!bf16) {
+    packed_read(q, d, w, s, sw, nw);
+    return;
+  }
+  const unsigned* u = reinterpret_cast<const unsigned*>(q);
+  d = __uint_as_float(u[0]);
+  const unsigned a = u[1], b = u[2];
+  w = __uint_as_float(a << 16);
+  s = __uint_as_float(a & 0xffff0000u);
+  sw = __uint_as_float(b << 16);
+  nw = __uint_as_float(b & 0xffff0000u);
+}
+
+// A row of the walk with every value in FP32 (BF16 coefficients widened).
+using StripRowW = StripRowT<float, float>;
+
 template <typename S>
-__device__ __forceinline__ void ring_read(const unsigned char* slot, int ld, int icol, int ic, int j, StripRow<S>& R) {
+__device__ __forceinline__ void ring_read(const unsigned char* slot, int ld, int icol, int ic, int j, StripRowW& R) {
   using RG = StripRing<S>;
   const long long e = (long long)j * ld + icol;
-  const int o4 = (int)(e & 3) + (ic - icol), o8 = (int)(e & (16 / (long long)sizeof(S) - 1)) + (ic - icol);
+  const int o = (int)(e & 3) + (ic - icol);
   const float* xf = reinterpret_cast<const float*>(slot);
   const float* ff = reinterpret_cast<const float*>(slot + RG::BF);
-  const float* df = reinterpret_cast<const float*>(slot + 2 * RG::BF);
-  const S* wq = reinterpret_cast<const S*>(slot + 3 * RG::BF);
-  const S* sq = wq + RG::CS;
-  const S* swq = sq + RG::CS;
-  const S* nwq = swq + RG::CS;
-  R.xa = xf[o4];
-  R.xb = xf[o4 + 1];
-  R.fa = ff[o4];
-  R.fb = ff[o4 + 1];
-  R.da = df[o4];
-  R.db = df[o4 + 1];
-  R.wa = wq[o8];
-  R.wb = wq[o8 + 1];
-  R.sa = sq[o8];
-  R.sb = sq[o8 + 1];
-  R.swa = swq[o8];
-  R.swb = swq[o8 + 1];
-  R.nwa = nwq[o8];
-  R.nwb = nwq[o8 + 1];
+  const float* pq = reinterpret_cast<const float*>(slot + 2 * RG::BF) + RG::PK * o;
+  constexpr bool BF = sizeof(S) == 2;
+  R.xa = xf[o];
+  R.xb = xf[o + 1];
+  R.fa = ff[o];
+  R.fb = ff[o + 1];
+  packed_read_wide(pq, BF, R.da, R.wa, R.sa, R.swa, R.nwa);
+  packed_read_wide(pq + RG::PK, BF, R.db, R.wb, R.sb, R.swb, R.nwb);
 }
+
 
 // The strip height ty (even, >= 2) is a launch argument, as in the FP64 sweep.
 template <typename S, int RING, bool FU = false>
@@ -493,7 +518,7 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
   const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
   const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
   const bool own = lane >= 2 && lane <= 29;
-  const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
+  const StripSrc A{xin, f, static_cast<const float*>(v.pk)};
   const int NR = ty + 3;                          // band rows q = 0 .. NR - 1, j = j0 - 1 + q
   const int last = (n + 1) - (j0 - 1);            // rows q > last lie outside the grid: never copied
   auto valid = [&](int q) { return q < NR && q <= last; };
@@ -502,42 +527,41 @@ __device__ __forceinline__ bool gs_strip_ring_body(const StencilView<float, S>& 
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncwarp();
-  if (lane == 0)
-    for (int q = 0; q < RING; ++q)
-      if (valid(q)) ring_issue(A, ld, icol, j0 - 1 + q, ring + q * RG::SLOT, &bars[q]);
+  for (int q = 0; q < RING; ++q)
+    if (valid(q)) ring_issue_warp<S>(A, ld, icol, j0 - 1 + q, ring + q * RG::SLOT, &bars[q]);
   bool ok = true;
   int taken = 0;                                  // rows 0 .. taken-1 read; rows < taken + RING requested
   // read band row q into R (waiting for its slot), then hand the slot to row q + RING
-  auto take = [&](int q, StripRow<S>& R) {
+  auto take = [&](int q, StripRowW& R) {
     const int slot = q % RING;
     if (valid(q) && ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
     if (!ok) return;
-    ring_read(ring + slot * RG::SLOT, ld, icol, ic, j0 - 1 + q, R);
+    ring_read<S>(ring + slot * RG::SLOT, ld, icol, ic, j0 - 1 + q, R);
     taken = q + 1;
     __syncwarp();
-    if (lane == 0 && valid(q) && valid(q + RING))
-      ring_issue(A, ld, icol, j0 - 1 + q + RING, ring + slot * RG::SLOT, &bars[slot]);
+    if (valid(q) && valid(q + RING))
+      ring_issue_warp<S>(A, ld, icol, j0 - 1 + q + RING, ring + slot * RG::SLOT, &bars[slot]);
   };
-  StripRow<S> P0, P1, Q0, Q1;                     // two row pairs in alternating roles
+  StripRowW P0, P1, Q0, Q1;                     // two row pairs in alternating roles
   take(0, P1);
   take(1, Q0);
   take(2, Q1);
   if (ok && j0 <= n) {
-    strip_row<float, S, FU>(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
+    strip_row<float, float, FU>(P1, Q0, Q1, c1, c2);                // row j0: c1, c2
     strip_store(xout, n, ld, ic, j0, own, Q0);
   }
   // step m: old pair = rows a - 2, a - 1; new pair = rows a, a + 1 (band rows 2m + 1, 2m + 2)
-  auto step = [&](int m, StripRow<S>& E0, StripRow<S>& E1, StripRow<S>& E2, StripRow<S>& E3) {
+  auto step = [&](int m, StripRowW& E0, StripRowW& E1, StripRowW& E2, StripRowW& E3) {
     const int a = j0 + 2 * m;
     take(2 * m + 1, E2);
     take(2 * m + 2, E3);
     if (!ok) return;
     if (a <= n) {
-      strip_row<float, S, FU>(E1, E2, E3, c1, c2);              // row a: c1, c2
+      strip_row<float, float, FU>(E1, E2, E3, c1, c2);              // row a: c1, c2
       if (a < j1) strip_store(xout, n, ld, ic, a, own, E2);
     }
     if (a - 1 <= n) {
-      strip_row<float, S, FU>(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
+      strip_row<float, float, FU>(E0, E1, E2, c3, c4);              // row a - 1: c3, c4
       strip_store(xout, n, ld, ic, a - 1, own, E1);
     }
   };
@@ -587,15 +611,16 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   const bool p2 = in_a && lane >= 3 && lane <= 29, q2 = in_b && lane >= 3 && lane <= 28;
   const bool r2 = in_a && lane >= 4 && lane <= 28, t2 = in_b && lane >= 4 && lane <= 27;
   const bool own = lane >= 4 && lane <= 27;
-  const StripSrc<S> A{xin, f, v.D, v.W, v.S_, v.SW, v.NW};
+  const StripSrc A{xin, f, static_cast<const float*>(v.pk)};
   const int NR = ty + 7;                      // band rows q = 0 .. NR - 1, j = j0 - 3 + q
   auto rowok = [&](int q) { const int j = j0 - 3 + q; return j >= 0 && j <= n + 1; };
-  // lane 0: fill the slot of band row q (copies, or a plain arrive for a row outside the grid)
+  // the warp fills the slot of band row q (copies, or lane 0's plain arrive for
+  // a row outside the grid)
   auto issue = [&](int q) {
     if (q >= NR) return;
     if (rowok(q))
-      ring_issue(A, ld, icol, j0 - 3 + q, ring + (q % RING) * RG::SLOT, &bars[q % RING]);
-    else
+      ring_issue_warp<S>(A, ld, icol, j0 - 3 + q, ring + (q % RING) * RG::SLOT, &bars[q % RING]);
+    else if (lane == 0)
       mbar_arrive(&bars[q % RING]);
   };
   if (lane == 0) {
@@ -603,45 +628,50 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncwarp();
-  if (lane == 0)
-    for (int q = 0; q < RING; ++q) issue(q);
+  for (int q = 0; q < RING; ++q) issue(q);
   bool ok = true;
   int taken = 0;
-  auto take = [&](int q, StripRow<S>& R) {
+  auto take = [&](int q, StripRowW& R) {
     const int slot = q % RING;
     if (ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
     if (!ok) return;
-    ring_read(ring + slot * RG::SLOT, ld, icol, ic, j0 - 3 + q, R);
+    ring_read<S>(ring + slot * RG::SLOT, ld, icol, ic, j0 - 3 + q, R);
     taken = q + 1;
     __syncwarp();
-    if (lane == 0) issue(q + RING);
+    issue(q + RING);
   };
-  StripRow<S> R0, R1, R2, R3, R4, R5;             // rows a - 4 .. a + 1
-  take(0, R3);
-  take(1, R4);
-  take(2, R5);
-#pragma unroll 1
-  for (int m = 0; m <= ty / 2 + 2 && ok; ++m) {
+  // step m on the rows a - 4 .. a + 1 held in R0 .. R5 (R4, R5 taken here for
+  // m >= 1).  The rows move down by two per step, so the six registers sets
+  // take their roles in a cycle of three steps instead of being copied.
+  auto step = [&](int m, StripRowW& R0, StripRowW& R1, StripRowW& R2, StripRowW& R3, StripRowW& R4,
+                  StripRowW& R5) {
     const int a = j0 - 2 + 2 * m, b = a - 2;      // sweep-1 and sweep-2 odd rows
     if (m >= 1) {
       take(2 * m + 1, R4);
       take(2 * m + 2, R5);
-      if (!ok) break;
+      if (!ok) return;
     }
-    if (a >= 1 && a <= n) strip_row<float, S, FU>(R3, R4, R5, p1, q1);                 // sweep 1, row a
-    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<float, S, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
+    if (a >= 1 && a <= n) strip_row<float, float, FU>(R3, R4, R5, p1, q1);                 // sweep 1, row a
+    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<float, float, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
     if (m >= 2 && b <= n) {                                               // sweep 2, row a - 2
-      strip_row<float, S, FU>(R1, R2, R3, p2, q2);
+      strip_row<float, float, FU>(R1, R2, R3, p2, q2);
       if (b < j1) strip_store(xout, n, ld, ic, b, own, R2);
     }
     if (m >= 3 && b - 1 <= n) {                                           // sweep 2, row a - 3
-      strip_row<float, S, FU>(R0, R1, R2, r2, t2);
+      strip_row<float, float, FU>(R0, R1, R2, r2, t2);
       strip_store(xout, n, ld, ic, b - 1, own, R1);
     }
-    R0 = R2;
-    R1 = R3;
-    R2 = R4;
-    R3 = R5;
+  };
+  StripRowW S0, S1, S2, S3, S4, S5;
+  take(0, S3);
+  take(1, S4);
+  take(2, S5);
+  const int msteps = ty / 2 + 2;                  // steps m = 0 .. msteps
+#pragma unroll 1
+  for (int m = 0; m <= msteps && ok; m += 3) {
+    step(m, S0, S1, S2, S3, S4, S5);
+    if (m + 1 <= msteps && ok) step(m + 1, S2, S3, S4, S5, S0, S1);
+    if (m + 2 <= msteps && ok) step(m + 2, S4, S5, S0, S1, S2, S3);
   }
   if (!ok)                                        // drain the copies still in flight, bounded
     for (int q = taken; q < taken + RING && q < NR; ++q) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));

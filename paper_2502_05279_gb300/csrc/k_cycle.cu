@@ -344,8 +344,8 @@ template <typename S, bool FU>
 static void gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
   switch (shape) {
-    case 1: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 8); break;
-    case 2: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 16); break;
+    case 1: strip_ring_launch<S, 6, FU>(v, f, xin, xout, done, s, 0); break;   // one wave, deeper rings
+    case 2: strip_ring_launch<S, 8, FU>(v, f, xin, xout, done, s, 0); break;
     case 3: strip_ring_launch<S, 4, FU>(v, f, xin, xout, done, s, 32); break;
     case 4: strip_launch<S, 32, FU>(v, f, xin, xout, done, s); break;
     case 5: strip_launch<S, 16, FU>(v, f, xin, xout, done, s); break;
@@ -356,9 +356,8 @@ static void gs_tile(const StencilView<float, S>& v, const float* f, const float*
 template <typename S>
 void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
-  const bool ring_ok = aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) &&
-                       aligned16(v.SW) && aligned16(v.NW);
-  if (shape < 4 && !ring_ok) shape = 4;           // bulk copies need 16-byte aligned arrays
+  const bool ring_ok = aligned16(f) && aligned16(xin) && v.pk && aligned16(v.pk);
+  if (shape < 4 && !ring_ok) shape = 4;           // bulk copies need 16-byte aligned arrays and the packed stencil
   if (v.fused)
     gs_tile<S, true>(v, f, xin, xout, shape, done, s);
   else
@@ -439,8 +438,8 @@ template <typename S, bool FU>
 static void gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
   switch (shape) {
-    case 1: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 16); break;
-    case 2: strip2_launch<S, 6, FU>(v, f, xin, xout, done, s, 32); break;
+    case 1: strip2_launch<S, 6, FU>(v, f, xin, xout, done, s, 0); break;   // one wave, deeper rings
+    case 2: strip2_launch<S, 8, FU>(v, f, xin, xout, done, s, 0); break;
     case 3: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 26); break;
     default: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 0); break;   // one wave
   }
@@ -449,9 +448,7 @@ static void gs_pair(const StencilView<float, S>& v, const float* f, const float*
 template <typename S>
 bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s) {
-  if (!(aligned16(f) && aligned16(xin) && aligned16(v.D) && aligned16(v.W) && aligned16(v.S_) && aligned16(v.SW) &&
-        aligned16(v.NW)))
-    return false;
+  if (!(aligned16(f) && aligned16(xin) && v.pk && aligned16(v.pk))) return false;
   if (v.fused)
     gs_pair<S, true>(v, f, xin, xout, shape, done, s);
   else

@@ -244,6 +244,36 @@ __global__ void k_lower_bf16(int n, const double* __restrict__ st, __nv_bfloat16
 
 dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
 
+// The packed stencils read by the bulk-copy sweeps: one point's five FP32
+// words d, w, s, sw, nw, or three words d, w | s << 16, sw | nw << 16 of a
+// BF16 level (the bf16 bit patterns as stored).  The same values as the
+// planes, in another layout.
+__global__ void k_pack32(int n, const float* __restrict__ st32, float* __restrict__ pk, size_t pst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n + 1 || j > n + 1) return;
+  const size_t p = (size_t)j * (n + 2) + i;
+  float* o = pk + PK_WORDS_F32 * p;
+  o[0] = st32[5 * pst + p];
+  o[1] = st32[pst + p];
+  o[2] = st32[2 * pst + p];
+  o[3] = st32[3 * pst + p];
+  o[4] = st32[4 * pst + p];
+}
+
+__global__ void k_pack_bf16(int n, const __nv_bfloat16* __restrict__ off16, const float* __restrict__ od32,
+                            float* __restrict__ pk, size_t pst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n + 1 || j > n + 1) return;
+  const size_t p = (size_t)j * (n + 2) + i;
+  auto bits = [](__nv_bfloat16 v) { return (unsigned)__bfloat16_as_ushort(v); };
+  unsigned* o = reinterpret_cast<unsigned*>(pk + PK_WORDS_BF16 * p);
+  o[0] = __float_as_uint(od32[pst + p]);
+  o[1] = bits(off16[p]) | (bits(off16[pst + p]) << 16);
+  o[2] = bits(off16[2 * pst + p]) | (bits(off16[3 * pst + p]) << 16);
+}
+
 }  // namespace
 
 // Interior of an nx x ny grid array into / out of the n x n layout (the other
@@ -311,6 +341,16 @@ void launch_lower32(int n, const double* st, float* st32, const double* ci, floa
 
 void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od32, cudaStream_t s) {
   k_lower_bf16<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, st, off16, od32, plane_stride32(n));
+  count_launch();
+}
+
+void launch_pack32(int n, const float* st32, float* pk, cudaStream_t s) {
+  k_pack32<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, st32, pk, plane_stride32(n));
+  count_launch();
+}
+
+void launch_pack_bf16(int n, const __nv_bfloat16* off16, const float* od32, float* pk, cudaStream_t s) {
+  k_pack_bf16<<<grid2(n + 2, n + 2), dim3(BX, BY), 0, s>>>(n, off16, od32, pk, plane_stride32(n));
   count_launch();
 }
 

@@ -20,6 +20,10 @@ struct StencilView {
   int n;
   int ld;
   int fused = 0;   // 1: the cycle's multiply-adds are fused (BMG_ARITH_FUSED)
+  // FP32 / BF16 levels: the same stencil packed per point for the bulk-copy
+  // sweeps, point p at pk[PK * p]: PK = 5 words d, w, s, sw, nw (FP32) or 3
+  // words d, (w | s << 16), (sw | nw << 16) (BF16 halves); NULL if absent.
+  const void* pk = nullptr;
 };
 
 // ---- setup (k_setup.cu), FP64 ----
@@ -37,6 +41,11 @@ void launch_factor(int n, const double* st, double* L, double* work, int* err, c
 // st32 / off16 / od32: planes plane_stride32(n) elements apart.
 void launch_lower32(int n, const double* st, float* st32, const double* ci, float* ci32, cudaStream_t s);
 void launch_lower_bf16(int n, const double* st, __nv_bfloat16* off16, float* od32, cudaStream_t s);
+// The packed stencil of an FP32 level (words d, w, s, sw, nw per point) or a
+// BF16 level (words d, w|s, sw|nw) over all (n+2)^2 points, from its planes.
+void launch_pack32(int n, const float* st32, float* pk, cudaStream_t s);
+void launch_pack_bf16(int n, const __nv_bfloat16* off16, const float* od32, float* pk, cudaStream_t s);
+constexpr int PK_WORDS_F32 = 5, PK_WORDS_BF16 = 3;
 
 // ---- cycle (k_cycle.cu) ----
 // `done`: device flag of the running solve (NULL = always run); every kernel
