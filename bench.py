@@ -401,6 +401,10 @@ class ClockSampler:
 # fused, (k-1) fma + 1 mul
 ALG_FP64_INSTR_PER_POINT = {(5, "rounded"): 9, (9, "rounded"): 17, (5, "fused"): 5, (9, "fused"): 9}
 SWEEP_BYTES = {("fp64", 9): 64, ("fp64", 5): 48, ("fp32", 9): 32, ("fp32", 5): 24, ("bf16", 9): 24, ("bf16", 5): 20}
+# Two sweeps + residual + restriction in one pass, per fine point: the stencil with both a_O and 1/a_O
+# (FP32: 6 x 4 B; BF16: 2 x 4 + 4 x 2 B), f, x read and written, the eight weights of a coarse point
+# (8 x 4 B per 4 fine points) and the coarse right-hand side and iterate written (2 x 4 B per 4).
+PAIR_RESTRICT_BYTES = {"fp32": 24 + 4 + 8 + 8 + 2, "bf16": 16 + 4 + 8 + 8 + 2}
 
 
 def run_ours(args, rank, local_rank, world):
@@ -568,7 +572,13 @@ def run_ours(args, rank, local_rank, world):
         prof = variants[prec]["prof"]
         st = "bf16" if prec == "bf16" else "float"
         pair = [q for q in prof if q["kernel"] == "relax_pair" and q["level"] == 0 and q["fp32"]]
-        if pair:
+        fused = [q for q in prof if q["kernel"] == "pair_restrict" and q["level"] == 0 and q["fp32"]]
+        if fused:
+            r = fused[0]
+            sweeps = 2.0
+            byt = PAIR_RESTRICT_BYTES[prec] * N
+            name = f"k_gs_strip2r_ring<{st}> 44xW bulk/{4 if variants[prec]['pairs'][0] != 1 else 6}"
+        elif pair:
             r = pair[0]
             sweeps = 2.0
             byt = SWEEP_BYTES[(prec, kind)] * N
@@ -581,7 +591,8 @@ def run_ours(args, rank, local_rank, world):
         per_launch_s = r["ms"] / r["launches"] * 1e-3
         achieved = byt / per_launch_s / 1e9
         share = r["ms"] / sum(q["ms"] for q in prof)
-        what = "two sweeps" if sweeps == 2.0 else ("half sweep" if sweeps < 1 else "sweep")
+        what = ("two sweeps + residual + restriction" if fused else "two sweeps") if sweeps == 2.0 else \
+            ("half sweep" if sweeps < 1 else "sweep")
         tr, tr_src = traffic(name, sweeps)
         return {"bound": "hbm", "kernel": f"{name} level 0 ({what} per launch)",
                 "achieved": round(achieved, 1), "peak": hbm_peak[0], "unit": "GB/s",

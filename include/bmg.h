@@ -124,7 +124,16 @@ typedef struct {
                            flexible-CG updates) is one fused multiply-add, in FP64 and FP32 alike.
                            Same expressions, same order, fewer roundings; setup, line relaxation
                            and the coarsest solve are unchanged */
+  int fuse_restrict;    /* FP32 / BF16 levels whose two pre-smoothing sweeps run as one two-sweep
+                           pass (nu1 = 2): BMG_FUSE_AUTO (0, default; the autotuner weighs one pass
+                           that also forms the residual and restricts it -- temporal blocking --
+                           against the two-sweep pass plus the separate residual + restriction),
+                           BMG_FUSE_OFF, or BMG_FUSE_ON (always the fused pass).  Same bits. */
 } bmg_opts;
+
+#define BMG_FUSE_AUTO 0
+#define BMG_FUSE_OFF 1
+#define BMG_FUSE_ON 2
 
 #define BMG_ARITH_ROUNDED 0
 #define BMG_ARITH_FUSED 1
@@ -192,7 +201,8 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
 enum { BMG_K_RELAX = 0, BMG_K_RESID_RESTRICT = 1, BMG_K_INTERP = 2, BMG_K_COARSE = 3, BMG_K_NORM = 4,
        BMG_K_FINALIZE = 5, BMG_K_IR_UPDATE = 6, BMG_K_IR_RESIDUAL = 7, BMG_K_FCG = 8,
        BMG_K_TAIL = 9 /* the level-fused coarse levels, counted at their top level */,
-       BMG_K_RELAX_PAIR = 10 /* two-sweep passes (each launch = two sweeps) */ };
+       BMG_K_RELAX_PAIR = 10 /* two-sweep passes (each launch = two sweeps) */,
+       BMG_K_PAIR_RESTRICT = 11 /* two sweeps + residual + restriction in one pass */ };
 typedef struct {
   int level;            /* 0 = finest */
   int kernel;           /* BMG_K_* */

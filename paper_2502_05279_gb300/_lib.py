@@ -42,8 +42,10 @@ class ProfRow(ctypes.Structure):
 
 
 KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "residual_norm", "norm_finalize",
-                "ir_update", "ir_residual", "fcg", "tail", "relax_pair")
+                "ir_update", "ir_residual", "fcg", "tail", "relax_pair", "pair_restrict")
 _KRYLOV = {"none": 0, "fcg": 1}
+# the two pre-smoothing sweeps with the residual and restriction in one pass (BMG_FUSE_*)
+_FUSE = {"auto": 0, "off": 1, "on": 2}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
 _SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
              "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12}
@@ -57,7 +59,7 @@ class Opts(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int),
-                ("arith", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("fuse_restrict", ctypes.c_int)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -163,7 +165,7 @@ class Hierarchy:
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
                  use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto",
-                 arith: str = "rounded"):
+                 arith: str = "rounded", fuse_restrict: str = "auto"):
         nx, ny = coef.shape[-1] - 2, coef.shape[-2] - 2     # any size; 2^m - 1 squares natively
         self.nx, self.ny, self.kind, self.precision, self.arith = nx, ny, kind, precision, arith
         if kind in (5, 9):
@@ -171,7 +173,7 @@ class Hierarchy:
         st = Stencil(kind, _ptr(coef, name="coef"))
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
                  int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
-                 _SMOOTHER[smoother], _ARITH[arith])
+                 _SMOOTHER[smoother], _ARITH[arith], _FUSE[fuse_restrict])
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), nx, ny, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -87,6 +87,7 @@ struct Level {
   int tile64 = -1;        // FP64 sweeps: -1 row kernel (in place), else shape of the FP64 one-pass kernel
   double* x64b = nullptr; // second iterate of an FP64 level swept by the one-pass kernel
   float* pk32 = nullptr;  // the FP32 / BF16 stencil packed per point (StencilView::pk)
+  int pair_rr = 0;        // 1: the two pre-smoothing sweeps, the residual and the restriction in one pass
 };
 
 StencilView<double, double> view64(const Level& L) {
@@ -111,6 +112,7 @@ struct bmg_hierarchy {
   int interp = BMG_INTERP_DENDY, interp_used = BMG_INTERP_DENDY;
   int smoother = BMG_SMOOTHER_AUTO;
   int arith = BMG_ARITH_ROUNDED;
+  int fuse_restrict = BMG_FUSE_AUTO;
   const void* mlp = nullptr;
   double factor_learned = 0.0, factor_dendy = 0.0;
   double* kr = nullptr;   // flexible CG vectors r, z, p, q (FP64, (n+2)^2 each)
@@ -319,13 +321,27 @@ void vcycle32(bmg_hierarchy* h, int l, const int* done) {
   }
   Level& C = h->lv[l + 1];
   float* cur = L.x32;
-  if (L.bf16) {
-    relax32(h, viewbf(L), l, h->nu1, &cur, done);
-    restrict32(h, viewbf(L), l, cur, done);
-  } else {
-    relax32(h, view32(L), l, h->nu1, &cur, done);
-    restrict32(h, view32(L), l, cur, done);
-  }
+  auto pre = [&](const auto& v) {
+    if (L.pair_rr && h->nu1 == 2) {   // temporal blocking: sweeps, residual and restriction in one pass
+      float* dst = cur == L.x32 ? L.x32b : L.x32;
+      step(h, l, BMG_K_PAIR_RESTRICT, 1, [&] {
+        if (!launch_gs_pair_restrict(v, (const float*)L.f32, (const float*)cur, dst, (const float*)L.ci32, C.f32,
+                                     C.x32, L.pair32 == 1 ? 1 : 0, done, s)) {
+          launch_gs_pair(v, (const float*)L.f32, (const float*)cur, dst, L.pair32, done, s);
+          launch_resid_restrict(v, L.kind, (const float*)L.ci32, (const float*)dst, (const float*)L.f32, C.f32,
+                                C.x32, done, s);
+        }
+      });
+      cur = dst;
+      return;
+    }
+    relax32(h, v, l, h->nu1, &cur, done);
+    restrict32(h, v, l, cur, done);
+  };
+  if (L.bf16)
+    pre(viewbf(L));
+  else
+    pre(view32(L));
   vcycle32(h, l + 1, done);
   float* dst = L.tile32 >= 0 && (sweep_launches(L, h->nu2) & 1) ? L.x32b : L.x32;
   step(h, l, BMG_K_INTERP, 1, [&] { launch_interp_to<float>(L.n, L.ci32, C.x32, cur, dst, done, s, L.fused); });
@@ -639,6 +655,59 @@ int autotune_solo(bmg_hierarchy* h) {
       rc = tune_level32(L, viewbf(L), h->ws);
     else
       rc = tune_level32(L, view32(L), h->ws);
+    if (rc) return rc;
+  }
+  return BMG_OK;
+}
+
+// A level whose two pre-smoothing sweeps run as one two-sweep pass: the pass
+// that also forms the residual and restricts it (temporal blocking) against
+// the two-sweep pass plus the separate residual + restriction, timed on
+// scratch iterates with the level's stencil; the coarse level's right-hand
+// side and iterate are written by both (they are rewritten every cycle).
+template <typename S>
+int tune_pair_restrict(Level& L, Level& C, const StencilView<float, S>& v, cudaStream_t s) {
+  size_t ps = plane_stride32(v.n);
+  float* scratch = nullptr;   // x, x', f laid out like a level's arrays
+  int rc = galloc(&scratch, v.n, 3, s);
+  if (rc) return rc;
+  const float* f = scratch + 2 * ps;
+  float ms_sep = 0, ms_fused = 0;
+  bool fused_ok = true;
+  rc = time_call(s, [&] {
+    launch_gs_pair(v, f, scratch, scratch + ps, L.pair32, (const int*)nullptr, s);
+    launch_resid_restrict(v, L.kind, (const float*)L.ci32, (const float*)(scratch + ps), f, C.f32, C.x32,
+                          (const int*)nullptr, s);
+  }, &ms_sep);
+  if (!rc)
+    rc = time_call(s, [&] {
+      fused_ok = launch_gs_pair_restrict(v, f, scratch, scratch + ps, (const float*)L.ci32, C.f32, C.x32,
+                                         L.pair32 == 1 ? 1 : 0, (const int*)nullptr, s);
+    }, &ms_fused);
+  gfree(scratch);
+  if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "two-sweep pass: bulk copies did not complete");
+  if (rc) return rc;
+  L.pair_rr = fused_ok && ms_fused < ms_sep ? 1 : 0;
+  return BMG_OK;
+}
+
+// Levels outside the level-fused tail whose two pre-smoothing sweeps are one
+// two-sweep pass (nu1 = 2): the fused pass when forced, or when the tuner
+// finds it faster (graphs on).
+int choose_pair_restrict(bmg_hierarchy* h) {
+  if (h->precision == BMG_FP64 || h->nu1 != 2 || h->fuse_restrict == BMG_FUSE_OFF) return BMG_OK;
+  if (h->fuse_restrict == BMG_FUSE_AUTO && !h->use_graph) return BMG_OK;
+  std::lock_guard<std::mutex> guard(tune_lock());
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    if (h->tail_l >= 0 && l >= h->tail_l) break;
+    Level& L = h->lv[l];
+    if (L.kind != 9 || L.tile32 < 0 || L.pair32 < 0) continue;
+    if (h->fuse_restrict == BMG_FUSE_ON) {
+      L.pair_rr = 1;
+      continue;
+    }
+    int rc = L.bf16 ? tune_pair_restrict(L, h->lv[l + 1], viewbf(L), h->ws)
+                    : tune_pair_restrict(L, h->lv[l + 1], view32(L), h->ws);
     if (rc) return rc;
   }
   return BMG_OK;
@@ -961,6 +1030,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     h->user = (cudaStream_t)o->stream;
     h->smoother = o->smoother;
     h->arith = o->arith;
+    h->fuse_restrict = o->fuse_restrict;
+  }
+  if (h->fuse_restrict < BMG_FUSE_AUTO || h->fuse_restrict > BMG_FUSE_ON) {
+    int fr = h->fuse_restrict;
+    delete h;
+    return set_error(BMG_EINVAL, "bmg_setup: bad fuse_restrict %d", fr);
   }
   if (h->smoother < BMG_SMOOTHER_AUTO ||
       (h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES && h->smoother < BMG_SMOOTHER_PAIR) ||
@@ -993,6 +1068,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc && !line && h->use_graph) rc = autotune_solo(h);
   if (!rc && !line && h->use_graph)   // the level-fused tail relaxes by points
     rc = h->precision == BMG_FP64 ? build_tail<double>(h, 1) : build_tail<float>(h, 0);
+  if (!rc && !line) rc = choose_pair_restrict(h);
   if (!rc) rc = ensure_ctl(h, 64);
   if (rc) {
     bmg_free(h);

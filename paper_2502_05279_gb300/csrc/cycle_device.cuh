@@ -678,6 +678,230 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   return ok;
 }
 
+// ---- two sweeps, then the residual and its restriction, in one pass ---------------------
+// The two-sweep walk, narrowed to 44 owned columns so that every owned coarse
+// point's 3x3 fine footprint has final values around it: the window of 64
+// columns starts 10 columns left of the strip (c = 0 .. 63), the strip owns
+// c in [10, 53] and the coarse points at its even fine columns (c = 11, 13,
+// .., 53), whose restriction reads residuals on [10, 54], which need final x
+// on [9, 55] -- exactly where the two sweeps leave final values.  The walk
+// starts one step earlier and runs three steps longer than the two-sweep
+// pass, so that the final rows j0 - 1 .. j1 + 1 around the band exist; it
+// reads the band's rows j0 - 5 .. j1 + 5.  At step m, after the sweeps, the
+// residuals of rows b - 2 (odd) and b - 1 (even) are formed from final rows
+// (b = a - 2, a the first sweep's odd row; the x and NW values of row b - 3
+// are kept from the previous step), and the coarse row whose fine row is
+// b - 3 is restricted from the residual rows b - 4, b - 3 (kept) and b - 2.
+// Residual and restriction take the operands and the order of the separate
+// residual + restriction kernel (r = f - a_O x - a_W x_W - ..., the nine terms
+// of Fig. 2 left to right), so the coarse right-hand side is bit-identical.
+// A slot holds x, f, the packed stencil and the diagonal a_O of one row.
+struct StripRowR : StripRowW {
+  float oa, ob;               // a_O at the lane's two columns
+};
+
+template <typename S>
+struct StripRingR {
+  static constexpr unsigned SLOT = StripRing<S>::SLOT + StripRing<S>::BF;   // + the a_O row segment
+};
+
+// residuals of row M from final values of rows L, M, U (the order of
+// row_residual: O, W, E, S, N, SW, NE, NW, SE)
+template <bool FU>
+__device__ __forceinline__ void strip_resid(const StripRowW& L, const StripRowR& M, const StripRowW& U, float& ra,
+                                            float& rb) {
+  {   // odd-i point c = 2l
+    const float xw = shfl_up1(M.xb), xsw = shfl_up1(L.xb), xnw = shfl_up1(U.xb);
+    float s = M.fa;
+    s = msub<FU>(s, M.oa, M.xa);
+    s = msub<FU>(s, M.wa, xw);
+    s = msub<FU>(s, M.wb, M.xb);
+    s = msub<FU>(s, M.sa, L.xa);
+    s = msub<FU>(s, U.sa, U.xa);
+    s = msub<FU>(s, M.swa, xsw);
+    s = msub<FU>(s, U.swb, U.xb);
+    s = msub<FU>(s, M.nwa, xnw);
+    s = msub<FU>(s, L.nwb, L.xb);
+    ra = s;
+  }
+  {   // even-i point c = 2l + 1
+    const float xe = shfl_dn1(M.xa), we = shfl_dn1(M.wa);
+    const float xne = shfl_dn1(U.xa), swne = shfl_dn1(U.swa);
+    const float xse = shfl_dn1(L.xa), nwse = shfl_dn1(L.nwa);
+    float s = M.fb;
+    s = msub<FU>(s, M.ob, M.xb);
+    s = msub<FU>(s, M.wb, M.xa);
+    s = msub<FU>(s, we, xe);
+    s = msub<FU>(s, M.sb, L.xb);
+    s = msub<FU>(s, U.sb, U.xb);
+    s = msub<FU>(s, M.swb, L.xa);
+    s = msub<FU>(s, swne, xne);
+    s = msub<FU>(s, M.nwb, U.xa);
+    s = msub<FU>(s, nwse, xse);
+    rb = s;
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void ring_issue_warp_r(const StripSrc& A, const float* O, int ld, int icol, int j,
+                                                  unsigned char* slot, unsigned long long* bar) {
+  using RG = StripRing<S>;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, StripRingR<S>::SLOT);
+  }
+  __syncwarp();
+  if (lane < 4) {
+    const long long e = (long long)j * ld + icol;
+    const long long e4 = e - (e & 3);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (lane < 2)
+      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + e4, RG::BF, bar);
+    else if (lane == 2)
+      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * e4, RG::BP, bar);
+    else
+      bulk_copy(slot + RG::SLOT, O + e4, RG::BF, bar);
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void ring_read_r(const unsigned char* slot, int ld, int icol, int ic, int j, StripRowR& R) {
+  ring_read<S>(slot, ld, icol, ic, j, R);
+  const long long e = (long long)j * ld + icol;
+  const int o = (int)(e & 3) + (ic - icol);
+  const float* of = reinterpret_cast<const float*>(slot + StripRing<S>::SLOT);
+  R.oa = of[o];
+  R.ob = of[o + 1];
+}
+
+// ci: the level's FP32 interpolation weights (8 planes of the coarse level);
+// fc, xc: the coarse right-hand side (written on owned coarse points) and
+// iterate (zeroed there).
+template <typename S, int RING, bool FU = false>
+__device__ __forceinline__ bool gs_strip2r_ring_body(const StencilView<float, S>& v, const float* __restrict__ f,
+                                                     const float* __restrict__ xin, float* __restrict__ xout,
+                                                     const float* __restrict__ ci, float* __restrict__ fc,
+                                                     float* __restrict__ xc, int sx, int sy, int ty,
+                                                     unsigned char* ring, unsigned long long* bars) {
+  static_assert(RING % 2 == 0 && RING >= 4, "ring size");
+  constexpr unsigned SLOT = StripRingR<S>::SLOT;
+  const int n = v.n, ld = v.ld, nc = (n - 1) / 2, ldc = nc + 2;
+  const size_t psc = plane_size(nc);
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 44 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
+  const int icol = i0 - 10, ic = icol + 2 * lane;
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  const bool p1 = in_a && lane >= 1, q1 = in_b && lane >= 1 && lane <= 30;
+  const bool r1 = in_a && lane >= 2 && lane <= 30, t1 = in_b && lane >= 2 && lane <= 29;
+  const bool p2 = in_a && lane >= 3 && lane <= 29, q2 = in_b && lane >= 3 && lane <= 28;
+  const bool r2 = in_a && lane >= 4 && lane <= 28, t2 = in_b && lane >= 4 && lane <= 27;
+  const bool own = lane >= 5 && lane <= 26;       // c in [10, 53]
+  const int icc = (ic + 1) / 2;                   // this lane's coarse column (its even fine column ic + 1)
+  const bool own_c = own && icc >= 1 && icc <= nc;
+  const StripSrc A{xin, f, static_cast<const float*>(v.pk)};
+  const int NR = ty + 11;                         // band rows q = 0 .. NR - 1, j = j0 - 5 + q
+  auto rowok = [&](int q) { const int j = j0 - 5 + q; return j >= 0 && j <= n + 1; };
+  auto issue = [&](int q) {
+    if (q >= NR) return;
+    if (rowok(q))
+      ring_issue_warp_r<S>(A, v.O, ld, icol, j0 - 5 + q, ring + (q % RING) * SLOT, &bars[q % RING]);
+    else if (lane == 0)
+      mbar_arrive(&bars[q % RING]);
+  };
+  if (lane == 0) {
+    for (int k = 0; k < RING; ++k) mbar_init(&bars[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  for (int q = 0; q < RING; ++q) issue(q);
+  bool ok = true;
+  int taken = 0;
+  auto take = [&](int q, StripRowR& R) {
+    const int slot = q % RING;
+    if (ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
+    if (!ok) return;
+    ring_read_r<S>(ring + slot * SLOT, ld, icol, ic, j0 - 5 + q, R);
+    taken = q + 1;
+    __syncwarp();
+    issue(q + RING);
+  };
+  StripRowW K;                                    // final x and NW of row b - 3
+  float rpa = 0.f, rpb = 0.f, rea = 0.f, reb = 0.f;   // residual rows b - 4 (odd) and b - 3 (even)
+  // step m on the rows a - 4 .. a + 1 held in R0 .. R5, a = j0 - 4 + 2m
+  auto step = [&](int m, StripRowR& R0, StripRowR& R1, StripRowR& R2, StripRowR& R3, StripRowR& R4,
+                  StripRowR& R5) {
+    const int a = j0 - 4 + 2 * m, b = a - 2;
+    if (m >= 1) {
+      take(2 * m + 1, R4);
+      take(2 * m + 2, R5);
+      if (!ok) return;
+    }
+    if (a >= 1 && a <= n) strip_row<float, float, FU>(R3, R4, R5, p1, q1);                   // sweep 1, row a
+    if (m >= 1 && a - 1 >= 1 && a - 1 <= n) strip_row<float, float, FU>(R2, R3, R4, r1, t1);   // sweep 1, row a - 1
+    if (m >= 2 && b >= 1 && b <= n) {                                                        // sweep 2, row b
+      strip_row<float, float, FU>(R1, R2, R3, p2, q2);
+      if (b >= j0 && b < j1) strip_store(xout, n, ld, ic, b, own, R2);
+    }
+    if (m >= 3 && b - 1 >= 1 && b - 1 <= n) {                                                // sweep 2, row b - 1
+      strip_row<float, float, FU>(R0, R1, R2, r2, t2);
+      if (b - 1 >= j0 && b - 1 < j1) strip_store(xout, n, ld, ic, b - 1, own, R1);
+    }
+    if (m >= 4) {
+      // residuals of rows b - 2 (odd: rows K, R0, R1) and b - 1 (even: rows R0, R1, R2)
+      float oa, ob, ea, eb;
+      strip_resid<FU>(K, R0, R1, oa, ob);
+      strip_resid<FU>(R0, R1, R2, ea, eb);
+      if (b - 2 > n) oa = ob = 0.f;
+      if (b - 1 > n) ea = eb = 0.f;
+      if (ic > n) oa = ea = 0.f;
+      if (ic + 1 > n) ob = eb = 0.f;
+      // restriction of the coarse row whose fine row is b - 3 (odd rows b - 4, b - 2 around it)
+      const int jc = (b - 3) / 2;
+      if (m >= 5) {
+        const float pa_n = shfl_dn1(rpa), ea_n = shfl_dn1(rea), oa_n = shfl_dn1(oa);   // columns 2 icc + 1
+        if (own_c && b - 3 >= j0 + 1 && b - 3 <= j1 - 1 && jc >= 1 && jc <= nc) {
+          auto w = [&](int k, int dic, int djc) { return ci[k * psc + (size_t)(jc + djc) * ldc + (icc + dic)]; };
+          float t = rmul(w(CI_LNE, 0, 0), rpa);
+          t = madd<FU>(t, w(CI_LA, 0, 0), rpb);
+          t = madd<FU>(t, w(CI_LNW, 1, 0), pa_n);
+          t = madd<FU>(t, w(CI_LR, 0, 0), rea);
+          t = radd(t, reb);
+          t = madd<FU>(t, w(CI_LL, 1, 0), ea_n);
+          t = madd<FU>(t, w(CI_LSE, 0, 1), oa);
+          t = madd<FU>(t, w(CI_LB, 0, 1), ob);
+          t = madd<FU>(t, w(CI_LSW, 1, 1), oa_n);
+          const size_t pc = (size_t)jc * ldc + icc;
+          fc[pc] = t;
+          xc[pc] = 0.f;
+        }
+      }
+      rpa = oa;
+      rpb = ob;
+      rea = ea;
+      reb = eb;
+    }
+    K.xa = R1.xa;
+    K.xb = R1.xb;
+    K.nwa = R1.nwa;
+    K.nwb = R1.nwb;
+  };
+  StripRowR S0, S1, S2, S3, S4, S5;
+  take(0, S3);
+  take(1, S4);
+  take(2, S5);
+  const int msteps = ty / 2 + 4;                  // steps m = 0 .. msteps
+#pragma unroll 1
+  for (int m = 0; m <= msteps && ok; m += 3) {
+    step(m, S0, S1, S2, S3, S4, S5);
+    if (m + 1 <= msteps && ok) step(m + 1, S2, S3, S4, S5, S0, S1);
+    if (m + 2 <= msteps && ok) step(m + 2, S4, S5, S0, S1, S2, S3);
+  }
+  if (!ok)                                        // drain the copies still in flight, bounded
+    for (int q = taken; q < taken + RING && q < NR; ++q) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));
+  return ok;
+}
+
 // ---- four-colour sweep in one pass (FP64): per-lane asynchronous row copies ----------------
 // The walk of gs_strip_ring_body (56 x TY strips, lane l holding the columns
 // c = 2l, 2l + 1 of a 64-column window, the same colour regions, rows and

@@ -91,6 +91,31 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2_ring(StencilView
     atomicExch(&g_strip_timeout, 1);
 }
 
+// Two sweeps, residual and restriction in one pass: warps take 44-column
+// strips; the coarse right-hand side and iterate of the next level are written
+// at the strip's coarse points.
+template <typename S, int RING, bool FU>
+__global__ void __launch_bounds__(32 * STRIP_WARPS) k_gs_strip2r_ring(StencilView<float, S> v,
+                                                                      const float* __restrict__ f,
+                                                                      const float* __restrict__ xin,
+                                                                      float* __restrict__ xout,
+                                                                      const float* __restrict__ ci,
+                                                                      float* __restrict__ fc, float* __restrict__ xc,
+                                                                      const int* done, int ty) {
+  pdl_enter();
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  if (stopped(done)) return;
+  const int nbx = (v.n + 43) / 44, nby = (v.n + ty - 1) / ty;
+  const int w = threadIdx.x >> 5, g = blockIdx.x * STRIP_WARPS + w;
+  if (g >= nbx * nby) return;
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRingR<S>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS * RING * StripRingR<S>::SLOT) + w * RING;
+  if (!gs_strip2r_ring_body<S, RING, FU>(v, f, xin, xout, ci, fc, xc, g % nbx, g / nbx, ty, ring, bars) &&
+      (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout, 1);
+}
+
 // FP64 one-pass sweep with strips of 56 x ty points: warp w of the CTA owns
 // ring slots [w RING, (w + 1) RING).
 template <int RING, bool FU>
@@ -444,6 +469,47 @@ static void gs_pair(const StencilView<float, S>& v, const float* f, const float*
     default: strip2_launch<S, 4, FU>(v, f, xin, xout, done, s, 0); break;   // one wave
   }
 }
+
+// ty = 0: the one-wave strip height, as strip_ring_launch.
+template <typename S, int RING, bool FU>
+static void strip2r_launch(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                           const float* ci, float* fc, float* xc, const int* done, cudaStream_t s) {
+  constexpr size_t bytes = (size_t)STRIP_WARPS * RING * (StripRingR<S>::SLOT + 8);
+  static const int resident_warps = resident_strip_warps(k_gs_strip2r_ring<S, RING, FU>, bytes);
+  const int nbx = (v.n + 43) / 44;
+  const int nby_max = resident_warps / nbx > 1 ? resident_warps / nbx : 1;
+  const int half = (v.n + 2 * nby_max - 1) / (2 * nby_max);
+  const int ty = 2 * (half > 1 ? half : 1);
+  const int warps = nbx * ((v.n + ty - 1) / ty);
+  pdl_launch(k_gs_strip2r_ring<S, RING, FU>, (warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, bytes, s,
+             v, f, xin, xout, ci, fc, xc, done, ty);
+  count_launch();
+}
+
+template <typename S>
+bool launch_gs_pair_restrict(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                             const float* ci, float* fc, float* xc, int shape, const int* done, cudaStream_t s) {
+  if (!(aligned16(f) && aligned16(xin) && v.pk && aligned16(v.pk) && aligned16(v.O) && ci && fc && xc))
+    return false;
+  const bool deep = shape == 1;
+  if (v.fused) {
+    if (deep)
+      strip2r_launch<S, 6, true>(v, f, xin, xout, ci, fc, xc, done, s);
+    else
+      strip2r_launch<S, 4, true>(v, f, xin, xout, ci, fc, xc, done, s);
+  } else {
+    if (deep)
+      strip2r_launch<S, 6, false>(v, f, xin, xout, ci, fc, xc, done, s);
+    else
+      strip2r_launch<S, 4, false>(v, f, xin, xout, ci, fc, xc, done, s);
+  }
+  return true;
+}
+template bool launch_gs_pair_restrict<float>(const StencilView<float, float>&, const float*, const float*, float*,
+                                             const float*, float*, float*, int, const int*, cudaStream_t);
+template bool launch_gs_pair_restrict<__nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, const float*,
+                                                     const float*, float*, const float*, float*, float*, int,
+                                                     const int*, cudaStream_t);
 
 template <typename S>
 bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,

@@ -87,6 +87,13 @@ void launch_gs_tile(const StencilView<float, S>& v, const float* f, const float*
 // copies: shapes 0 .. 3 = TY W (one wave), 16, 32, 26 with 4, 4, 6, 4 row slots.  Needs
 // the guarded, aligned array layout; returns false (nothing launched) without it.
 constexpr int GS_PAIR_SHAPES = 4;
+// The two pre-smoothing sweeps, the residual and its restriction in one pass
+// (44-column strips): fc, xc are the next level's right-hand side and iterate
+// (written / zeroed at its interior points).  Shape 0 or 1 (4- or 6-slot row
+// rings).  Returns false when the arrays do not allow the bulk copies.
+template <typename S>
+bool launch_gs_pair_restrict(const StencilView<float, S>& v, const float* f, const float* xin, float* xout,
+                             const float* ci, float* fc, float* xc, int shape, const int* done, cudaStream_t s);
 template <typename S>
 bool launch_gs_pair(const StencilView<float, S>& v, const float* f, const float* xin, float* xout, int shape,
                     const int* done, cudaStream_t s);

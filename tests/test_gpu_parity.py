@@ -837,3 +837,63 @@ def test_concurrent_setups_on_two_host_threads(bmg):
         assert ok and it == it2 and torch.equal(x, x2) and h.history() == ref.history()
         ref.close()
         h.close()
+
+
+# ---- temporal blocking: two sweeps, residual and restriction in one pass --------------------
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("shape", ["pair0", "pair1"])
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_pair_restrict_pass_inner_cycle_bitwise(bmg, precision, nbf, shape, arith, graph):
+    """The one-pass pre-smoothing with the residual and its restriction (44-
+    column strips, coarse right-hand sides written from the walk) forced on
+    every level: the inner cycle is the oracle's bit for bit, over grids with
+    several strips and bands, ragged right and top edges, and a grid narrower
+    than one strip."""
+    for case, n in [("lognormal", 511), ("binary", 255), ("lognormal", 127), ("poisson", 63)]:
+        kind, planes, f = problem(case, n)
+        levels = bx.setup(kind, planes, arith=arith)
+        r32 = w.rhs_uniform(n, 91).astype(np.float32)
+        want = mx.inner_cycle(mx.lower(levels, nbf), r32)
+        h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), precision=precision, smoother=shape,
+                          use_graph=graph, arith=arith, fuse_restrict="on")
+        got = host(h.inner_cycle(dev(r32, torch.float32)))
+        assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0)), (case, n)
+        if kind == 9 and not graph:
+            prof = h.profile(dev(f), torch.zeros_like(dev(f)), 1)
+            assert any(r["kernel"] == "pair_restrict" for r in prof), (case, n)
+        h.close()
+
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+def test_pair_restrict_solve_matches_oracle_and_tuner_choice(bmg, precision, nbf):
+    """Refinement solves with the fused pass forced equal the oracle's
+    iterates bit for bit; with the autotuner the pass is chosen or not per
+    level and the solve is the same bits either way."""
+    kind, planes, f = problem("lognormal", 1023)
+    levels = bx.setup(kind, planes, arith="fused")
+    xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=100)
+    outs = []
+    for fr in ("on", "auto", "off"):
+        h = bmg.Hierarchy(kind, dev(planes), precision=precision, smoother="pair0" if fr == "on" else "auto",
+                          arith="fused", fuse_restrict=fr)
+        x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+        assert ok and it == len(hw) - 1
+        assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0)), fr
+        check_history(h.history(), hw)
+        outs.append(h.history())
+        h.close()
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_pair_restrict_rejects_bad_option(bmg):
+    kind, planes, f = problem("binary", 63)
+    with pytest.raises(KeyError):
+        bmg.Hierarchy(kind, dev(planes), fuse_restrict="maybe")
+    import ctypes
+    o = bmg._lib.Opts()
+    o.fuse_restrict = 3
+    st = bmg._lib.Stencil(kind, bmg._lib._ptr(dev(planes)))
+    hh = ctypes.c_void_p()
+    assert bmg._lib.lib.bmg_setup(ctypes.byref(st), 63, 63, ctypes.byref(o), ctypes.byref(hh)) == bmg._lib.BMG_EINVAL
