@@ -178,9 +178,15 @@ def run_batched(args, rank, local_rank, world):
     ranks.close()
 
 
-RHS_BATCH = dict(text="64 right-hand sides U[-1,1) (seeds 500..563) of one 1023x1023 9-point Q1 problem, k = exp(g), "
-                      "g Gaussian field std 2, correlation 32 cells (seed 4); bmg_batch_rhs vs 64 solo solves, V(2,1)",
-                 n=1023, k=64)
+RHS_BATCHES = {
+    "rhs64-1023": dict(text="64 right-hand sides U[-1,1) (seeds 500..563) of one 1023x1023 9-point Q1 problem, "
+                            "k = exp(g), g Gaussian field std 2, correlation 32 cells (seed 4); bmg_batch_rhs vs 64 "
+                            "solo solves, V(2,1)", n=1023, k=64),
+    "rhs8-4095": dict(text="8 right-hand sides U[-1,1) (seeds 500..507) of one 4095x4095 9-point Q1 problem (its FP32 "
+                           "stencil exceeds L2), k = exp(g), g Gaussian field std 2, correlation 32 cells (seed 4); "
+                           "bmg_batch_rhs with one-pass sweeps taking 2 or 4 right-hand sides per warp (autotuned) "
+                           "and with one per warp, vs 8 solo solves, V(2,1)", n=4095, k=8),
+}
 
 
 def run_rhs_batch(args, rank, local_rank, world):
@@ -190,6 +196,7 @@ def run_rhs_batch(args, rank, local_rank, world):
     import paper_2502_05279_gb300 as bmg
     torch.cuda.set_device(local_rank)
     ranks = Ranks("nccl")
+    RHS_BATCH = RHS_BATCHES[args.workload]
     n, k = RHS_BATCH["n"], RHS_BATCH["k"]
     kind, planes, _ = w.lognormal_problem(n, 2.0, 32.0, seed_k=4, seed_f=7)
     coef = torch.from_numpy(planes).cuda()
@@ -197,7 +204,7 @@ def run_rhs_batch(args, rank, local_rank, world):
     N = n * n * k
     out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded generators)",
-           "config": {"workload": "rhs64-1023", "description": RHS_BATCH["text"], "unknowns": N,
+           "config": {"workload": args.workload, "description": RHS_BATCH["text"], "unknowns": N,
                       "parallelism": "replicas" if world > 1 else "single GPU"}, "variants": {}}
     clock_s = None
     for prec in ("fp64", "fp32"):
@@ -232,8 +239,15 @@ def run_rhs_batch(args, rank, local_rank, world):
             its_solo.append(it)
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
+        # the same batch with one right-hand side per warp in the one-pass sweeps
+        Boff = bmg.Batch.from_hierarchy(h, k, rhs_block="off")
+        xs_off = [torch.zeros_like(r) for r in rhs]
+        Boff.time_cycles(rhs, xs_off, max(args.warmup, 3))
+        ms_off = Boff.time_cycles(rhs, xs_off, args.steps)
+        Boff.close()
         out["variants"][prec] = {
             "value": whole_job_rate(N * args.steps, ms * 1e-3, ranks), "ms_per_step": ms / args.steps,
+            "ms_per_step_one_rhs_per_warp": ms_off / args.steps,
             "solo_value": n * n * args.steps / (ms_solo * 1e-3), "solo_ms_per_step_one_rhs": ms_solo / args.steps,
             "gpu_launches": launches, "time_to_1e-10_all_ms": round(tb * 1e3, 1),
             "time_to_1e-10_one_by_one_ms": round(ts * 1e3, 1), "iterations_max": max(its),
@@ -799,14 +813,15 @@ def run_reference(args, rank, world):
         setup_s, times, _ = oracle_batch_cycles(sample, steps + warm, threads=cores)
         text, unknowns = BATCHED["text"], m
         what = f"the first {len(sample)} problems of the batch ({m} unknowns)"
-    elif args.workload == "rhs64-1023":
+    elif args.workload in RHS_BATCHES:
+        RHS_BATCH = RHS_BATCHES[args.workload]
         n = RHS_BATCH["n"]
         kind, planes, _ = w.lognormal_problem(n, 2.0, 32.0, seed_k=4, seed_f=7)
         sample = [(kind, planes, w.rhs_uniform(n, 500 + q)) for q in range(2)]
-        steps = min(args.steps, 5)
+        steps = min(args.steps, 2 if n >= 4095 else 5)
         setup_s, times, _ = oracle_batch_cycles(sample, steps + warm, threads=cores)
         text, unknowns = RHS_BATCH["text"], 2 * n * n
-        what = "2 of the 64 right-hand sides (the operator set up once per right-hand side)"
+        what = f"2 of the {RHS_BATCH['k']} right-hand sides (the operator set up once per right-hand side)"
     else:
         spec = WORKLOADS[args.workload]
         kind, planes, f = spec["make"]()
@@ -836,7 +851,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(WORKLOADS) + ["batched256", "rhs64-1023"])
+                    choices=sorted(WORKLOADS) + ["batched256"] + sorted(RHS_BATCHES))
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--maxit-vcycle", type=int, default=200, help="cap of the stationary-cycle solve")
@@ -856,7 +871,7 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched256":
         run_batched(args, rank, local_rank, world)
-    elif args.workload == "rhs64-1023":
+    elif args.workload in RHS_BATCHES:
         run_rhs_batch(args, rank, local_rank, world)
     else:
         run_ours(args, rank, local_rank, world)

@@ -129,7 +129,15 @@ typedef struct {
                            that also forms the residual and restricts it -- temporal blocking --
                            against the two-sweep pass plus the separate residual + restriction),
                            BMG_FUSE_OFF, or BMG_FUSE_ON (always the fused pass).  Same bits. */
+  int rhs_block;        /* batches of right-hand sides of one operator (bmg_batch_rhs), FP32 / BF16
+                           levels swept by the one-pass kernel: BMG_RHS_BLOCK_AUTO (0, default; the
+                           autotuner weighs sweeping 2 or 4 members per warp, each stencil value read
+                           once for them, against one member per warp), BMG_RHS_BLOCK_OFF, or 2 / 4
+                           (always that many per warp).  Same bits. */
 } bmg_opts;
+
+#define BMG_RHS_BLOCK_AUTO 0
+#define BMG_RHS_BLOCK_OFF 1
 
 #define BMG_FUSE_AUTO 0
 #define BMG_FUSE_OFF 1

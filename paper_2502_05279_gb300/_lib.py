@@ -46,6 +46,8 @@ KERNEL_NAMES = ("relax", "resid_restrict", "interp_correct", "coarse_solve", "re
 _KRYLOV = {"none": 0, "fcg": 1}
 # the two pre-smoothing sweeps with the residual and restriction in one pass (BMG_FUSE_*)
 _FUSE = {"auto": 0, "off": 1, "on": 2}
+# right-hand sides per warp in the one-pass sweeps of a batch of right-hand sides (BMG_RHS_BLOCK_*)
+_RHS_BLOCK = {"auto": 0, "off": 1, 2: 2, 4: 4}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
 _SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
              "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12}
@@ -59,7 +61,7 @@ class Opts(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int),
-                ("arith", ctypes.c_int), ("fuse_restrict", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("fuse_restrict", ctypes.c_int), ("rhs_block", ctypes.c_int)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -294,15 +296,17 @@ class Batch:
 
     @classmethod
     def from_hierarchy(cls, h: "Hierarchy", k: int, nu1: int = 2, nu2: int = 1, inner_cycles: int = 1,
-                       use_graph: bool = True, smoother: str = "auto") -> "Batch":
+                       use_graph: bool = True, smoother: str = "auto", rhs_block="auto") -> "Batch":
         """k right-hand sides of h's operator solved together (bmg_batch_rhs);
-        h must stay open while the batch is used."""
+        h must stay open while the batch is used.  rhs_block: "auto", "off",
+        2 or 4 members per warp in the one-pass sweeps (each stencil value read
+        once for them)."""
         self = cls.__new__(cls)
         self.kind, self.precision = h.kind, h.precision
         self.ns = [h.n] * k
         self._coefs = [h]   # keeps the hierarchy alive
         o = Opts(_PREC[h.precision], 0, 0, nu1, nu2, inner_cycles, 0, int(use_graph), 0, None, _stream(),
-                 _SMOOTHER[smoother], _ARITH[h.arith])
+                 _SMOOTHER[smoother], _ARITH[h.arith], 0, _RHS_BLOCK[rhs_block])
         b = ctypes.c_void_p()
         _check(lib.bmg_batch_rhs(h._h, k, ctypes.byref(o), ctypes.byref(b)))
         self._h = b

@@ -1495,6 +1495,7 @@ constexpr int kGroups = 6;
 struct bmg_batch {
   int nprob = 0, precision = BMG_FP64, nu1 = 2, nu2 = 1, inner = 1, use_graph = 1, arith = BMG_ARITH_ROUNDED;
   int smoother = BMG_SMOOTHER_AUTO;
+  int rhs_block = BMG_RHS_BLOCK_AUTO;
   std::vector<bmg_hierarchy*> hs;
   cudaStream_t user = nullptr, ws = nullptr;
   cudaEvent_t ev = nullptr;
@@ -1502,6 +1503,7 @@ struct bmg_batch {
   struct Group {
     int n = 0, count = 0, cl = 1, storage = 0, kind = 9;
     int tile = -1, pair = -1;   // one-pass / two-sweep shapes chosen for an FP32 group (-1: row kernel / none)
+    int multi = 0;              // 2 or 4: one-pass sweeps with that many members per warp (shared operator)
     int dir = 0;                // while a cycle is enqueued: 0 = iterate in x, 1 = in x2
     size_t elem = 0;
     void* d = nullptr;
@@ -1668,6 +1670,10 @@ template <typename S>
 void group_onepass(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
   const LevelDesc<float, S>* d = gdesc<float, S>(g);
   int k = 0;
+  if (g.multi) {
+    for (; k < sweeps; ++k, g.dir ^= 1) launch_gs_tile_bk(d, g.count, g.n, g.multi, g.dir, B->ws, B->arith);
+    return;
+  }
   for (; g.pair >= 0 && k + 2 <= sweeps; k += 2, g.dir ^= 1)
     launch_gs_pair_b(d, g.count, g.n, g.pair, g.dir, B->ws, B->arith);
   for (; k < sweeps; ++k, g.dir ^= 1) launch_gs_tile_b(d, g.count, g.n, g.tile, g.dir, B->ws, B->arith);
@@ -1675,7 +1681,7 @@ void group_onepass(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
 
 int group_launches(const bmg_batch::Group& g, int sweeps) {
   if (g.tile < 0) return 0;
-  return g.pair >= 0 ? sweeps / 2 + sweeps % 2 : sweeps;
+  return g.pair >= 0 && !g.multi ? sweeps / 2 + sweeps % 2 : sweeps;
 }
 
 void group_relax(bmg_batch* B, bmg_batch::Group& g, int sweeps) {
@@ -1843,10 +1849,30 @@ int batch_launch_iterations(bmg_batch* B, int k) {
 // FP32 stages with n >= 255 also the one-pass kernel (shapes 0 and 3) and the
 // two-sweep pass (shapes 0 and 3).  Every candidate computes the same bits.
 struct GroupChoice {
-  int cl, tile, pair;
+  int cl, tile, pair, multi;
 };
-// (n, storage, count, kind, arith) -> choice
-static std::map<std::tuple<int, int, int, int, int>, GroupChoice> g_tuned;
+// (n, storage, count, kind, arith, shared operator) -> choice
+static std::map<std::tuple<int, int, int, int, int, int>, GroupChoice> g_tuned;
+
+// Whether the members of group g (stage b) share one operator -- a batch of
+// right-hand sides, whose members borrow one hierarchy's level arrays.
+bool group_shared(const bmg_batch* B, const bmg_batch::Group& g, int b) {
+  const void* pk = nullptr;
+  int cnt = 0;
+  for (const bmg_hierarchy* h : B->hs) {
+    const int l = h->nlev - 1 - b;
+    if (l < 0) continue;
+    const Level& lv = h->lv[l];
+    const int storage = B->precision == BMG_FP64 ? 0 : (lv.bf16 ? 2 : 1);
+    if (lv.n != g.n || lv.kind != g.kind || storage != g.storage) continue;
+    if (!lv.pk32) return false;
+    if (cnt++ == 0)
+      pk = lv.pk32;
+    else if (lv.pk32 != pk)
+      return false;
+  }
+  return cnt >= 2;
+}
 
 // Allocates the second iterate of every problem's level in FP32 group g.
 int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
@@ -1869,7 +1895,8 @@ int group_alloc_x2(bmg_batch* B, const bmg_batch::Group& g, int b) {
 
 template <typename T, typename S>
 int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
-  auto key = std::make_tuple(g.n, g.storage, g.count, g.kind, B->arith);
+  const bool shared = sizeof(T) == 4 && B->rhs_block != BMG_RHS_BLOCK_OFF && group_shared(B, g, b);
+  auto key = std::make_tuple(g.n, g.storage, g.count, g.kind, B->arith, shared ? 1 : 0);
   auto it = g_tuned.find(key);
   if (it == g_tuned.end()) {
     const int base = rows_cluster<T>(g.n);
@@ -1890,7 +1917,7 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
     if (!rc)
       rc = cuda_check(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws),
                       "tuning descriptors");
-    GroupChoice best{base, -1, -1};
+    GroupChoice best{base, -1, -1, 0};
     float best_ms = 1e30f, tile_ms = 1e30f;
     for (int cl = base; cl <= 8 && !rc; cl *= 2) {
       if (cl > base && ((g.n + 1) / 2 + cl - 1) / cl < 32) break;   // fewer than a warp of pairs per CTA
@@ -1946,6 +1973,22 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
               if (pair_best < best_ms) best.pair = shape;
             }
           }
+          if (pair_best < best_ms) best_ms = pair_best;
+        }
+        // members of one operator: sweeps with 2 or 4 of them per warp
+        for (int k : {2, 4}) {
+          if (rc || !shared || g.count < k) break;
+          float ms = 0;
+          rc = time_call(B->ws, [&] {
+            launch_gs_tile_bk<S>((const LevelDesc<float, S>*)dd, g.count, g.n, k, 0, B->ws, B->arith);
+            launch_gs_tile_bk<S>((const LevelDesc<float, S>*)dd, g.count, g.n, k, 1, B->ws, B->arith);
+          }, &ms);
+          if (!rc && ms * 0.5f < best_ms) {
+            best_ms = ms * 0.5f;
+            best.multi = k;
+            best.pair = -1;
+            if (best.tile < 0) best.tile = 0;
+          }
         }
       }
     }
@@ -1958,6 +2001,7 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
   g.cl = it->second.cl;
   g.tile = it->second.tile;
   g.pair = it->second.pair;
+  g.multi = it->second.multi;
   if (g.tile >= 0) return group_alloc_x2(B, g, b);
   return BMG_OK;
 }
@@ -1978,6 +2022,21 @@ int force_batch_onepass(bmg_batch* B) {
       }
       int rc = group_alloc_x2(B, g, b);
       if (rc) return rc;
+    }
+  return BMG_OK;
+}
+
+// rhs_block = 2 or 4: every FP32 group of a shared operator sweeps with that
+// many members per warp (allocating the second iterates it needs).
+int force_rhs_block(bmg_batch* B) {
+  if (B->precision == BMG_FP64 || (B->rhs_block != 2 && B->rhs_block != 4)) return BMG_OK;
+  for (int b = 1; b <= B->bmax; ++b)
+    for (auto& g : B->stages[b]) {
+      if (!g.count || g.kind != 9 || g.storage == 0 || !group_shared(B, g, b)) continue;
+      g.multi = B->rhs_block;
+      g.pair = -1;
+      if (g.tile < 0) g.tile = 0;
+      if (int rc = group_alloc_x2(B, g, b)) return rc;
     }
   return BMG_OK;
 }
@@ -2031,7 +2090,11 @@ int batch_init(bmg_batch* B, const bmg_opts* o, bmg_opts* so) {
     B->use_graph = o->use_graph;
     B->user = (cudaStream_t)o->stream;
     B->arith = o->arith;
+    B->rhs_block = o->rhs_block;
   }
+  if (B->rhs_block != BMG_RHS_BLOCK_AUTO && B->rhs_block != BMG_RHS_BLOCK_OFF && B->rhs_block != 2 &&
+      B->rhs_block != 4)
+    return set_error(BMG_EINVAL, "batched solves: bad rhs_block %d", B->rhs_block);
   if (B->arith < BMG_ARITH_ROUNDED || B->arith > BMG_ARITH_FUSED)
     return set_error(BMG_EINVAL, "batched solves: bad arith %d", B->arith);
   if (B->precision == BMG_FP64 && B->smoother >= BMG_SMOOTHER_PAIR)
@@ -2129,6 +2192,7 @@ int batch_finish(bmg_batch* B, int rc) {
   if (!rc) rc = batch_ensure_ctl(B, 64);
   if (!rc && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
   if (!rc && B->use_graph) rc = autotune_batch(B);
+  if (!rc) rc = force_rhs_block(B);
   if (!rc) rc = cuda_check(cudaStreamSynchronize(B->ws), "batched setup");
   return rc;
 }

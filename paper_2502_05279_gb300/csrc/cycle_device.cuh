@@ -678,6 +678,193 @@ __device__ __forceinline__ bool gs_strip2_ring_body(const StencilView<float, S>&
   return ok;
 }
 
+// ---- one sweep of K right-hand sides of one operator per warp -------------------------------
+// The walk of gs_strip_ring_body for K iterates that share a stencil (the
+// members of a batch of right-hand sides): a row slot holds the packed
+// stencil row once and the x and f rows of every member, so each stencil value
+// is read once for the K right-hand sides; the coefficient shuffles are shared
+// and the K members' row sums are independent chains.  Each member's
+// operations and their order are those of strip_row, so every member's sweep
+// is bit-identical to its own one-pass sweep.
+template <int K>
+struct StripRowK {
+  float xa[K], xb[K], fa[K], fb[K];
+  float da, db, wa, wb, sa, sb, swa, swb, nwa, nwb;
+};
+
+template <int K, bool FU>
+__device__ __forceinline__ void strip_row_k(const StripRowK<K>& L, StripRowK<K>& M, const StripRowK<K>& U, bool oka,
+                                            bool okb) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) {   // odd-i points c = 2l
+    const float xw = shfl_up1(M.xb[q]), xsw = shfl_up1(L.xb[q]), xnw = shfl_up1(U.xb[q]);
+    float s = M.fa[q];
+    s = msub<FU>(s, M.wa, xw);
+    s = msub<FU>(s, M.wb, M.xb[q]);
+    s = msub<FU>(s, M.sa, L.xa[q]);
+    s = msub<FU>(s, U.sa, U.xa[q]);
+    s = msub<FU>(s, M.swa, xsw);
+    s = msub<FU>(s, U.swb, U.xb[q]);
+    s = msub<FU>(s, M.nwa, xnw);
+    s = msub<FU>(s, L.nwb, L.xb[q]);
+    const float xn = rmul(s, M.da);
+    M.xa[q] = oka ? xn : M.xa[q];
+  }
+  const float we = shfl_dn1(M.wa), swne = shfl_dn1(U.swa), nwse = shfl_dn1(L.nwa);
+#pragma unroll
+  for (int q = 0; q < K; ++q) {   // even-i points c = 2l + 1
+    const float xe = shfl_dn1(M.xa[q]), xne = shfl_dn1(U.xa[q]), xse = shfl_dn1(L.xa[q]);
+    float s = M.fb[q];
+    s = msub<FU>(s, M.wb, M.xa[q]);
+    s = msub<FU>(s, we, xe);
+    s = msub<FU>(s, M.sb, L.xb[q]);
+    s = msub<FU>(s, U.sb, U.xb[q]);
+    s = msub<FU>(s, M.swb, L.xa[q]);
+    s = msub<FU>(s, swne, xne);
+    s = msub<FU>(s, M.nwb, U.xa[q]);
+    s = msub<FU>(s, nwse, xse);
+    const float xn = rmul(s, M.db);
+    M.xb[q] = okb ? xn : M.xb[q];
+  }
+}
+
+template <typename S, int K>
+struct StripRingK {
+  static constexpr unsigned SLOT = StripRing<S>::BP + 2 * K * StripRing<S>::BF;   // packed row, then x_q, f_q
+};
+
+// the warp requests row j: lane 0 copies the packed stencil segment, lanes
+// 1 + 2q and 2 + 2q member q's x and f segments
+template <typename S, int K>
+__device__ __forceinline__ void ring_issue_warp_k(const float* pk, const float* const* xs, const float* const* fs,
+                                                  int ld, int icol, int j, unsigned char* slot,
+                                                  unsigned long long* bar) {
+  using RG = StripRing<S>;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, StripRingK<S, K>::SLOT);
+  }
+  __syncwarp();
+  if (lane <= 2 * K) {
+    const long long e = (long long)j * ld + icol;
+    const long long e4 = e - (e & 3);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (lane == 0) {
+      bulk_copy(slot, pk + RG::PK * e4, RG::BP, bar);
+    } else {
+      const int q = (lane - 1) >> 1;
+      const float* src = (lane & 1) ? xs[q] : fs[q];
+      bulk_copy(slot + RG::BP + (lane - 1) * RG::BF, src + e4, RG::BF, bar);
+    }
+  }
+}
+
+template <typename S, int K>
+__device__ __forceinline__ void ring_read_k(const unsigned char* slot, int ld, int icol, int ic, int j,
+                                            StripRowK<K>& R) {
+  using RG = StripRing<S>;
+  const long long e = (long long)j * ld + icol;
+  const int o = (int)(e & 3) + (ic - icol);
+  const float* pq = reinterpret_cast<const float*>(slot) + RG::PK * o;
+  constexpr bool BF = sizeof(S) == 2;
+  packed_read_wide(pq, BF, R.da, R.wa, R.sa, R.swa, R.nwa);
+  packed_read_wide(pq + RG::PK, BF, R.db, R.wb, R.sb, R.swb, R.nwb);
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const float* xf = reinterpret_cast<const float*>(slot + RG::BP + 2 * q * RG::BF);
+    const float* ff = reinterpret_cast<const float*>(slot + RG::BP + (2 * q + 1) * RG::BF);
+    R.xa[q] = xf[o];
+    R.xb[q] = xf[o + 1];
+    R.fa[q] = ff[o];
+    R.fb[q] = ff[o + 1];
+  }
+}
+
+// xin, f, xout: the K members' arrays; member q's points are stored only if
+// bit q of `active` is set (a converged member, or a padding slot of the last
+// group, computes but writes nothing).
+template <typename S, int K, int RING, bool FU>
+__device__ __forceinline__ bool gs_strip_ring_k_body(const StencilView<float, S>& v, const float* const* f,
+                                                     const float* const* xin, float* const* xout, unsigned active,
+                                                     int sx, int sy, int ty, unsigned char* ring,
+                                                     unsigned long long* bars) {
+  static_assert(RING % 2 == 0 && RING >= 4, "ring size");
+  constexpr unsigned SLOT = StripRingK<S, K>::SLOT;
+  const int n = v.n, ld = v.ld;
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 56 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
+  const int icol = i0 - 4, ic = icol + 2 * lane;
+  const bool in_a = ic >= 1 && ic <= n, in_b = ic + 1 >= 1 && ic + 1 <= n;
+  const bool c1 = in_a && lane >= 1, c2 = in_b && lane >= 1 && lane <= 30;
+  const bool c3 = in_a && lane >= 2 && lane <= 30, c4 = in_b && lane >= 2 && lane <= 29;
+  const bool own = lane >= 2 && lane <= 29;
+  const float* pk = static_cast<const float*>(v.pk);
+  const int NR = ty + 3;
+  const int last = (n + 1) - (j0 - 1);
+  auto valid = [&](int q) { return q < NR && q <= last; };
+  if (lane == 0) {
+    for (int k = 0; k < RING; ++k) mbar_init(&bars[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  for (int q = 0; q < RING; ++q)
+    if (valid(q)) ring_issue_warp_k<S, K>(pk, xin, f, ld, icol, j0 - 1 + q, ring + q * SLOT, &bars[q]);
+  bool ok = true;
+  int taken = 0;
+  auto take = [&](int q, StripRowK<K>& R) {
+    const int slot = q % RING;
+    if (valid(q) && ok) ok = mbar_wait(&bars[slot], (unsigned)((q / RING) & 1));
+    if (!ok) return;
+    ring_read_k<S, K>(ring + slot * SLOT, ld, icol, ic, j0 - 1 + q, R);
+    taken = q + 1;
+    __syncwarp();
+    if (valid(q) && valid(q + RING))
+      ring_issue_warp_k<S, K>(pk, xin, f, ld, icol, j0 - 1 + q + RING, ring + slot * SLOT, &bars[slot]);
+  };
+  auto store = [&](int j, const StripRowK<K>& R) {
+    if (!own || j > n) return;
+    const size_t p = (size_t)j * ld + ic;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      if (!((active >> q) & 1u)) continue;
+      if (ic <= n) xout[q][p] = R.xa[q];
+      if (ic + 1 <= n) xout[q][p + 1] = R.xb[q];
+    }
+  };
+  StripRowK<K> P0, P1, Q0, Q1;
+  take(0, P1);
+  take(1, Q0);
+  take(2, Q1);
+  if (ok && j0 <= n) {
+    strip_row_k<K, FU>(P1, Q0, Q1, c1, c2);
+    store(j0, Q0);
+  }
+  auto step = [&](int m, StripRowK<K>& E0, StripRowK<K>& E1, StripRowK<K>& E2, StripRowK<K>& E3) {
+    const int a = j0 + 2 * m;
+    take(2 * m + 1, E2);
+    take(2 * m + 2, E3);
+    if (!ok) return;
+    if (a <= n) {
+      strip_row_k<K, FU>(E1, E2, E3, c1, c2);
+      if (a < j1) store(a, E2);
+    }
+    if (a - 1 <= n) {
+      strip_row_k<K, FU>(E0, E1, E2, c3, c4);
+      store(a - 1, E1);
+    }
+  };
+#pragma unroll 1
+  for (int m = 1; m <= ty / 2 && ok; m += 2) {
+    step(m, Q0, Q1, P0, P1);
+    if (m + 1 <= ty / 2 && ok) step(m + 1, P0, P1, Q0, Q1);
+  }
+  if (!ok)
+    for (int q = taken; q < taken + RING; ++q)
+      if (valid(q)) mbar_wait(&bars[q % RING], (unsigned)((q / RING) & 1));
+  return ok;
+}
+
 // ---- two sweeps, then the residual and its restriction, in one pass ---------------------
 // The two-sweep walk, narrowed to 44 owned columns so that every owned coarse
 // point's 3x3 fine footprint has final values around it: the window of 64

@@ -75,6 +75,43 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_b(const Le
     atomicExch(&g_strip_timeout_b, 1);
 }
 
+// One sweep of a group whose members share one operator, K members per warp:
+// warp g takes strip g % wpp of members K (g / wpp) .. K (g / wpp) + K - 1 (the
+// last group padded with the last member, which it does not store).
+template <typename S, int K, int RING, bool FU>
+__global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip_ring_bk(const LevelDesc<float, S>* __restrict__ d,
+                                                                         int count, int n, int dir, int ty) {
+  pdl_enter();
+  extern __shared__ __align__(128) unsigned char strip_smem[];
+  const int nbx = (n + 55) / 56, wpp = nbx * ((n + ty - 1) / ty);
+  const int w = threadIdx.x >> 5;
+  const long g = (long)blockIdx.x * STRIP_WARPS_B + w;
+  const int p0 = (int)(g / wpp) * K, sidx = (int)(g % wpp);
+  if (p0 >= count) return;
+  const float* fs[K];
+  const float* xi[K];
+  float* xo[K];
+  unsigned active = 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int p = p0 + q < count ? p0 + q : count - 1;
+    const LevelDesc<float, S>& e = d[p];
+    if (p0 + q < count && !stopped(e.done)) active |= 1u << q;
+    fs[q] = e.f;
+    xi[q] = dir ? e.x2 : e.x;
+    xo[q] = dir ? e.x : e.x2;
+  }
+  if (!active) return;
+  const StencilView<float, S> v = d[p0].v;
+  unsigned char* ring = strip_smem + (size_t)w * RING * StripRingK<S, K>::SLOT;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(strip_smem + (size_t)STRIP_WARPS_B * RING * StripRingK<S, K>::SLOT) +
+      w * RING;
+  if (!gs_strip_ring_k_body<S, K, RING, FU>(v, fs, xi, xo, active, sidx % nbx, sidx / nbx, ty, ring, bars) &&
+      (threadIdx.x & 31) == 0)
+    atomicExch(&g_strip_timeout_b, 1);
+}
+
 template <typename S, int TY, int RING, bool FU>
 __global__ void __launch_bounds__(32 * STRIP_WARPS_B) k_gs_strip2_ring_b(const LevelDesc<float, S>* __restrict__ d,
                                                                          int count, int n, int dir) {
@@ -402,6 +439,54 @@ void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape,
   else
     gs_tile_b<S, false>(d, count, n, shape, dir, s);
 }
+
+// ty: the smallest even strip height whose strips, over all groups of K
+// members, fit into one wave of resident warps.
+template <typename S, int K, bool FU>
+static void strip_bk_launch(const LevelDesc<float, S>* d, int count, int n, int dir, cudaStream_t s) {
+  if (count <= 0) return;
+  constexpr int RING = 4;
+  constexpr size_t bytes = (size_t)STRIP_WARPS_B * RING * (StripRingK<S, K>::SLOT + 8);
+  static const int resident_warps = [] {
+    cudaFuncSetAttribute(k_gs_strip_ring_bk<S, K, RING, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_strip_ring_bk<S, K, RING, FU>, 32 * STRIP_WARPS_B,
+                                                  bytes);
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * STRIP_WARPS_B;
+  }();
+  const int groups = (count + K - 1) / K, nbx = (n + 55) / 56;
+  const long cols = (long)groups * nbx;
+  const int nby_max = resident_warps / cols > 1 ? (int)(resident_warps / cols) : 1;
+  const int half = (n + 2 * nby_max - 1) / (2 * nby_max);
+  const int ty = 2 * (half > 1 ? half : 1);
+  const long warps = cols * ((n + ty - 1) / ty);
+  const unsigned blocks = (unsigned)((warps + STRIP_WARPS_B - 1) / STRIP_WARPS_B);
+  pdl_launch(k_gs_strip_ring_bk<S, K, RING, FU>, blocks, 32 * STRIP_WARPS_B, bytes, s, d, count, n, dir, ty);
+  count_launch();
+}
+
+template <typename S>
+bool launch_gs_tile_bk(const LevelDesc<float, S>* d, int count, int n, int k, int dir, cudaStream_t s, int fused) {
+  if (k == 2) {
+    if (fused)
+      strip_bk_launch<S, 2, true>(d, count, n, dir, s);
+    else
+      strip_bk_launch<S, 2, false>(d, count, n, dir, s);
+  } else if (k == 4) {
+    if (fused)
+      strip_bk_launch<S, 4, true>(d, count, n, dir, s);
+    else
+      strip_bk_launch<S, 4, false>(d, count, n, dir, s);
+  } else {
+    return false;
+  }
+  return true;
+}
+template bool launch_gs_tile_bk<float>(const LevelDesc<float, float>*, int, int, int, int, cudaStream_t, int);
+template bool launch_gs_tile_bk<__nv_bfloat16>(const LevelDesc<float, __nv_bfloat16>*, int, int, int, int,
+                                               cudaStream_t, int);
 
 template <typename S>
 void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s, int fused) {

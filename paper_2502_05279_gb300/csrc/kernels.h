@@ -199,6 +199,12 @@ void launch_interp_b(const LevelDesc<T, S>* d, int count, int n, cudaStream_t s,
 template <typename S>
 void launch_gs_tile_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s,
                       int fused = 0);
+// One sweep of a group whose members share one operator (a batch of
+// right-hand sides), k = 2 or 4 members per warp: each stencil value is read
+// once for the k members.  Needs the operator's packed stencil; false for
+// another k.
+template <typename S>
+bool launch_gs_tile_bk(const LevelDesc<float, S>* d, int count, int n, int k, int dir, cudaStream_t s, int fused);
 template <typename S>
 void launch_gs_pair_b(const LevelDesc<float, S>* d, int count, int n, int shape, int dir, cudaStream_t s,
                       int fused = 0);

@@ -897,3 +897,45 @@ def test_pair_restrict_rejects_bad_option(bmg):
     st = bmg._lib.Stencil(kind, bmg._lib._ptr(dev(planes)))
     hh = ctypes.c_void_p()
     assert bmg._lib.lib.bmg_setup(ctypes.byref(st), 63, 63, ctypes.byref(o), ctypes.byref(hh)) == bmg._lib.BMG_EINVAL
+
+
+# ---- block right-hand sides: one-pass sweeps with K members of one operator per warp ------------
+
+@pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
+@pytest.mark.parametrize("block,k", [(2, 5), (4, 5), (4, 8), ("auto", 6)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_rhs_block_sweeps_equal_solo_solves(bmg, precision, nbf, block, k, graph):
+    """A batch of k right-hand sides of one operator whose one-pass sweeps
+    take 2 or 4 members per warp (the stencil row read once for them; k not a
+    multiple of the block, so the last warp group is padded): every member's
+    iterate and history equal the hierarchy's own solve, and one member the
+    oracle's refinement solve."""
+    n = 511
+    kind, planes, f = problem("lognormal", n)
+    h = bmg.Hierarchy(kind, dev(planes), precision=precision, arith="fused")
+    rhs = [dev(w.rhs_uniform(n, 600 + q)) for q in range(k)]
+    B = bmg.Batch.from_hierarchy(h, k, use_graph=graph, rhs_block=block,
+                                 smoother="auto" if graph else "tile0")
+    xs, its, rrs, ok = B.solve(rhs, tol=1e-10, maxit=300)
+    assert ok
+    for q, r in enumerate(rhs):
+        x, it, rr, okk = h.solve(r, tol=1e-10, maxit=300)
+        assert okk and it == its[q] and torch.equal(x, xs[q]) and h.history() == B.history(q), q
+    levels = bx.setup(kind, planes, arith="fused")
+    xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), w.rhs_uniform(n, 603), tol=1e-10, maxit=300)
+    assert np.array_equal(bx.at(host(xs[3]), 0, 0), bx.at(xw, 0, 0))
+    check_history(B.history(3), hw)
+    B.close()
+    h.close()
+
+
+def test_rhs_block_rejects_bad_value(bmg):
+    kind, planes, f = problem("binary", 63)
+    h = bmg.Hierarchy(kind, dev(planes), precision="fp32")
+    with pytest.raises(KeyError):
+        bmg.Batch.from_hierarchy(h, 2, rhs_block=3)
+    import ctypes
+    o = bmg._lib.Opts(bmg._lib._PREC["fp32"], 0, 0, 2, 1, 1, 0, 1, 0, None, None, 0, 0, 0, 3)
+    b = ctypes.c_void_p()
+    assert bmg.lib.bmg_batch_rhs(h._h, 2, ctypes.byref(o), ctypes.byref(b)) == bmg._lib.BMG_EINVAL
+    h.close()
