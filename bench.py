@@ -70,8 +70,12 @@ DEFAULT_WORKLOAD = "lognormal8191"
 # traffic grows in proportion to the grid.  A kernel missing here, or changed
 # since its capture, reports traffic null.
 NCU_DRAM_BYTES_PER_POINT = {
-    "k_gs_strip64 56xW cp.async/6 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4"),
-    "k_gs_strip64 56xW cp.async/4 fused": (268.8e6 / 2047 ** 2, "fe2047-binary1e4 (shape 2 capture; same rows)"),
+    # captured with the 4-row ring; the ring depth does not change which rows and columns a strip reads
+    **{f"k_gs_strip64 56xW cp.async/{r} fused": (1089.14e6 / 4095 ** 2, "lognormal4095") for r in (4, 6)},
+    **{f"k_gs_strip<float> 56xW bulk/{r}": (540.66e6 / 4095 ** 2, "lognormal4095") for r in (4, 6)},
+    **{f"k_gs_strip<bf16> 56xW bulk/{r}": (398.64e6 / 4095 ** 2, "lognormal4095") for r in (4, 6)},
+    **{f"k_gs_strip2_ring<float> 48xW bulk/{r}": (549.46e6 / 4095 ** 2, "lognormal4095") for r in (4, 6)},
+    **{f"k_gs_strip2_ring<bf16> 48xW bulk/{r}": (404.43e6 / 4095 ** 2, "lognormal4095") for r in (4, 6)},
 }
 TILE_SHAPES = ("56xW bulk/4", "56xW bulk/6", "56xW bulk/8", "56x32 bulk/4", "56x32 regs", "56x16 regs")
 TILE64_SHAPES = ("56xW cp.async/4", "56x16 cp.async/4", "56xW cp.async/6", "56x8 cp.async/4")   # W: one wave
