@@ -140,6 +140,12 @@ def fe9_from_cells(k: np.ndarray) -> np.ndarray:
       SW(i,j) = -k[j-1,i-1] / 3
       NW(i,j) = -k[j,i-1] / 3
     """
+    return zero_ghost_couplings(_fe9_assemble(k))
+
+
+def _fe9_assemble(k: np.ndarray) -> np.ndarray:
+    """The node sums of fe9_from_cells over every interior node, ghost
+    couplings kept."""
     ny, nx = k.shape[0] - 1, k.shape[1] - 1
     planes = np.zeros((5, ny + 2, nx + 2), dtype=np.float64)
     kll = k[0:ny, 0:nx]              # cell (i-1, j-1) for interior node (i, j)
@@ -152,7 +158,39 @@ def fe9_from_cells(k: np.ndarray) -> np.ndarray:
     planes[2][I] = -(kll + klr) / 6.0
     planes[3][I] = -kll / 3.0
     planes[4][I] = -kul / 3.0
-    return zero_ghost_couplings(planes)
+    return planes
+
+
+def fe9_periodic(k: np.ndarray, px: bool, py: bool) -> np.ndarray:
+    """9-point Q1 stencil of -div(k grad u) (the sums of fe9_from_cells) on a
+    grid whose periodic axes wrap around.  k[cj, ci] is the cell whose
+    lower-left node is (ci, cj); along a periodic axis of N nodes there are N
+    cells, cell 0 lying between node N and node 1, along a Dirichlet axis of
+    N nodes there are N + 1.  Planes (5, ny+2, nx+2): the ghost lines zero,
+    couplings toward a Dirichlet ghost zero, couplings across a periodic side
+    kept (W at i = 1 couples node 1 to node N through cell 0)."""
+    ke = np.asarray(k, dtype=np.float64)
+    if px:
+        ke = np.concatenate([ke, ke[:, :1]], axis=1)
+    if py:
+        ke = np.concatenate([ke, ke[:1, :]], axis=0)
+    planes = _fe9_assemble(ke)
+    O, W, S, SW, NW = planes
+    ny, nx = planes.shape[1] - 2, planes.shape[2] - 2
+    for a in planes:
+        a[0, :] = 0.0
+        a[ny + 1, :] = 0.0
+        a[:, 0] = 0.0
+        a[:, nx + 1] = 0.0
+    if not px:
+        W[:, 1] = 0.0
+        SW[:, 1] = 0.0
+        NW[:, 1] = 0.0
+    if not py:
+        S[1, :] = 0.0
+        SW[1, :] = 0.0
+        NW[ny, :] = 0.0
+    return planes
 
 
 def binary_blocks(n: int, block: int, lo: float, hi: float, seed: int, p: float = 0.5) -> np.ndarray:
@@ -267,6 +305,29 @@ def neumann_problem(nx: int, ny: int, sides: str = "EN", std: float = 1.0, corr_
     if "S" in sides:
         k[0, :] = 0.0
     return 9, fe9_from_cells(k), rhs_uniform(nx, seed_f, ny)
+
+
+def periodic_shape(n: int, axes: str) -> tuple[int, int]:
+    """(nx, ny) of a grid with side n = 2^m - 1 whose `axes` ("x", "y" or
+    "xy") are periodic: a periodic axis has n + 1 = 2^m nodes."""
+    return (n + 1 if "x" in axes else n), (n + 1 if "y" in axes else n)
+
+
+def periodic_problem(n: int = 4095, axes: str = "x", std: float = 2.0, corr_len: float = 32.0,
+                     seed_k: int = 50, seed_f: int = 51, shift: float = 0.0):
+    """-div(k grad u) (+ shift u) on a grid periodic along `axes` (sizes from
+    periodic_shape), zero Dirichlet on the other sides: k = exp(g) on the
+    (n+1)^2 cells, g the periodic Gaussian field of gaussian_field (so k
+    itself wraps smoothly across a periodic side), 9-point Q1 stencil, `shift`
+    added to every diagonal (needed when both axes are periodic, where the
+    diffusion operator annihilates constants); RHS uniform[-1, 1).
+    Returns (kind, planes, rhs, px, py)."""
+    nx, ny = periodic_shape(n, axes)
+    px, py = "x" in axes, "y" in axes
+    k = np.exp(gaussian_field(n + 1, std, corr_len, seed_k))
+    planes = fe9_periodic(k, px, py)
+    planes[0, 1:ny + 1, 1:nx + 1] += shift
+    return 9, planes, rhs_uniform(nx, seed_f, ny), px, py
 
 
 def high_contrast_problem(n: int = 4095, block: int = 8, lo: float = 1.0, hi: float = 1e6,
