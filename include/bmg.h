@@ -34,6 +34,22 @@
  * layout; every other call on the hierarchy speaks of its levels (level 0 of
  * size n, bmg_level_size).  Batched solves take 2^m - 1 squares only.
  *
+ * Periodic sides (bmg_opts.periodic; the paper states Dirichlet grids only, and
+ * periodic axes are the black-box method's capability that Sec. 2 defers to).
+ * A periodic axis has N = 2^m points (point N + 1 is point 1 and point 0 is
+ * point N), a Dirichlet axis 2^m - 1, both axes the same m >= 2, so
+ * nx = ny + 1 (periodic in x), ny = nx + 1 (in y) or nx = ny = 2^m (both).
+ * Arrays keep the (ny+2) x (nx+2) layout; a coupling across a periodic side is
+ * an entry of A (W at i = 1 couples point 1 to point N, S at j = 1 point 1 to
+ * point N, SW and NW likewise), and the ghost lines are ignored.  Coarse point
+ * c still sits on fine point 2c, so a periodic axis of N points coarsens to a
+ * periodic axis of N / 2, down to 4 points (3 on a Dirichlet axis).  The
+ * interpolation planes of such a hierarchy have N_c cells along a periodic
+ * axis (ic = 1..N_c) and N_c + 1 along a Dirichlet one.  With both axes
+ * periodic a diffusion operator annihilates constants: the caller makes it
+ * non-singular (for instance with a positive term on the diagonal), else the
+ * coarsest factorisation may fail with BMG_ESINGULAR.
+ *
  * Interpolation weights.  Eight planes of (n_c+2)^2 doubles in the order
  * LSW, LSE, LNW, LNE, LL, LR, LB, LA (the labels of Fig. 2), indexed by the
  * coarse cell (ic, jc) whose north-east corner is coarse point (ic, jc):
@@ -134,7 +150,15 @@ typedef struct {
                            autotuner weighs sweeping 2 or 4 members per warp, each stencil value read
                            once for them, against one member per warp), BMG_RHS_BLOCK_OFF, or 2 / 4
                            (always that many per warp).  Same bits. */
+  int periodic;         /* 0 (default): Dirichlet sides; BMG_PERIODIC_X | BMG_PERIODIC_Y: those axes
+                           wrap around (see Periodic sides above).  Periodic hierarchies run FP64
+                           stationary V(nu1, nu2) cycles with point Gauss-Seidel (smoother AUTO or
+                           ROWS), Dendy interpolation and the default coarsest level, in either
+                           arithmetic mode, with or without graphs; other options give EINVAL */
 } bmg_opts;
+
+#define BMG_PERIODIC_X 1
+#define BMG_PERIODIC_Y 2
 
 #define BMG_RHS_BLOCK_AUTO 0
 #define BMG_RHS_BLOCK_OFF 1
@@ -240,13 +264,20 @@ int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
  * either way. */
 int bmg_tuned_pair(const bmg_hierarchy* h, int level);
 
-/* Number of levels, and the size n of level l (0 = finest). */
+/* Number of levels, and the size n of level l (0 = finest; EINVAL for a
+ * hierarchy with periodic sides, whose levels are not square). */
 int bmg_num_levels(const bmg_hierarchy* h);
 int bmg_level_size(const bmg_hierarchy* h, int level);
 
+/* Interior points of level l along x and y (host outputs, either may be NULL):
+ * n and n for a Dirichlet hierarchy, the two axes' counts with periodic sides.
+ * EINVAL for a bad level. */
+int bmg_level_shape(const bmg_hierarchy* h, int level, int* nx, int* ny);
+
 /* Copy level `level`'s stencil (5 planes O,W,S,SW,NW, FP64, ghost couplings
  * zero) or its interpolation weights (8 planes, FP64; not for the coarsest
- * level) into device memory `out` of the matching size. */
+ * level) into device memory `out` of the matching size: planes of
+ * (ny+2) x (nx+2) for level l's or level l+1's bmg_level_shape. */
 int bmg_get_stencil(const bmg_hierarchy* h, int level, double* out);
 int bmg_get_interp(const bmg_hierarchy* h, int level, double* out);
 

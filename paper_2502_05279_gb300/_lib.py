@@ -17,6 +17,7 @@ library_path = os.path.join(_HERE, "libbmg.so")
 
 BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ESINGULAR, BMG_ENAN, BMG_ENOTCONV, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 BMG_FP64, BMG_FP32_IR, BMG_BF16_IR = 0, 1, 2
+BMG_PERIODIC_X, BMG_PERIODIC_Y = 1, 2
 _PREC = {"fp64": BMG_FP64, "fp32": BMG_FP32_IR, "bf16": BMG_BF16_IR}
 
 
@@ -61,7 +62,8 @@ class Opts(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("bf16_levels", ctypes.c_int), ("use_graph", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("smoother", ctypes.c_int),
-                ("arith", ctypes.c_int), ("fuse_restrict", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("fuse_restrict", ctypes.c_int), ("rhs_block", ctypes.c_int),
+                ("periodic", ctypes.c_int)]
 
 
 P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -71,6 +73,7 @@ _sig = {
     "bmg_history": (I, [P, ctypes.POINTER(D), I]),
     "bmg_num_levels": (I, [P]),
     "bmg_level_size": (I, [P, I]),
+    "bmg_level_shape": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
     "bmg_get_stencil": (I, [P, I, P]),
     "bmg_get_interp": (I, [P, I, P]),
     "bmg_launch_count": (L, [P]),
@@ -167,7 +170,9 @@ class Hierarchy:
     def __init__(self, kind: int, coef: torch.Tensor, precision: str = "fp64", coarsest: int = 3,
                  nu1: int = 2, nu2: int = 1, inner_cycles: int = 1, bf16_levels: int = 2,
                  use_graph: bool = True, krylov: str = "none", mlp: "Mlp | None" = None, smoother: str = "auto",
-                 arith: str = "rounded", fuse_restrict: str = "auto"):
+                 arith: str = "rounded", fuse_restrict: str = "auto", periodic: str = ""):
+        """periodic: "" (Dirichlet sides), "x", "y" or "xy" (those axes wrap
+        around; a periodic axis has 2^m points, a Dirichlet one 2^m - 1)."""
         nx, ny = coef.shape[-1] - 2, coef.shape[-2] - 2     # any size; 2^m - 1 squares natively
         self.nx, self.ny, self.kind, self.precision, self.arith = nx, ny, kind, precision, arith
         if kind in (5, 9):
@@ -176,10 +181,14 @@ class Hierarchy:
         o = Opts(_PREC[precision], 1 if mlp is not None else 0, coarsest, nu1, nu2, inner_cycles, bf16_levels,
                  int(use_graph), _KRYLOV[krylov], mlp._h if mlp is not None else None, _stream(),
                  _SMOOTHER[smoother], _ARITH[arith], _FUSE[fuse_restrict])
+        if set(periodic) - set("xy"):
+            raise ValueError(f"periodic must be a combination of 'x' and 'y', not {periodic!r}")
+        o.periodic = (BMG_PERIODIC_X if "x" in periodic else 0) | (BMG_PERIODIC_Y if "y" in periodic else 0)
+        self.periodic = periodic
         h = ctypes.c_void_p()
         _check(lib.bmg_setup(ctypes.byref(st), nx, ny, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
-        self.n = self.level_size(0)   # level 0: nx = ny = n, or the embedding square
+        self.n = self.level_shape(0)[0]   # level 0: nx = ny = n, the embedding square, or the periodic nx
 
     def solve(self, rhs: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-10, maxit: int = 100):
         """Returns (x, iterations, relative residual, converged)."""
@@ -225,15 +234,21 @@ class Hierarchy:
     def level_size(self, level: int) -> int:
         return _check_size(lib.bmg_level_size(self._h, level))
 
+    def level_shape(self, level: int) -> tuple[int, int]:
+        """(nx, ny) of a level: (n, n) for Dirichlet hierarchies."""
+        nx, ny = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib.bmg_level_shape(self._h, level, ctypes.byref(nx), ctypes.byref(ny)))
+        return nx.value, ny.value
+
     def stencil(self, level: int) -> torch.Tensor:
-        m = self.level_size(level) + 2
-        out = torch.empty((5, m, m), dtype=torch.float64, device="cuda")
+        nx, ny = self.level_shape(level)
+        out = torch.empty((5, ny + 2, nx + 2), dtype=torch.float64, device="cuda")
         _check(lib.bmg_get_stencil(self._h, level, _ptr(out)))
         return out
 
     def interp(self, level: int) -> torch.Tensor:
-        m = self.level_size(level + 1) + 2
-        out = torch.empty((8, m, m), dtype=torch.float64, device="cuda")
+        nx, ny = self.level_shape(level + 1)
+        out = torch.empty((8, ny + 2, nx + 2), dtype=torch.float64, device="cuda")
         _check(lib.bmg_get_interp(self._h, level, _ptr(out)))
         return out
 

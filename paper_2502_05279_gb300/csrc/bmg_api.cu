@@ -15,6 +15,7 @@
 #include "cycle_device.cuh"
 #include "kernels.h"
 #include "learned.h"
+#include "periodic.h"
 
 namespace bmg {
 
@@ -154,6 +155,8 @@ struct bmg_hierarchy {
   int nx = 0, ny = 0;
   double* fpad = nullptr;
   double* xpad = nullptr;
+  // periodic sides: the hierarchy of periodic.cu (nlev stays 0, lv empty)
+  PerHier* per = nullptr;
 };
 
 namespace {
@@ -723,6 +726,10 @@ int choose_pair_restrict(bmg_hierarchy* h) {
 // One iteration of the solve loop: a V-cycle (or a refinement step) followed by
 // the residual norm and the convergence test, all on the device.
 void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
+  if (h->per) {
+    per_enqueue_iteration(h->per, rhs, x, h->partials, h->ctl, h->ws);
+    return;
+  }
   const int* done = &h->ctl->done;
   Level& L0 = h->lv[0];
   int np = 0;
@@ -756,6 +763,10 @@ void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
 }
 
 int enqueue_initial(bmg_hierarchy* h, const double* rhs, double* x) {
+  if (h->per) {
+    per_enqueue_initial(h->per, rhs, x, h->partials, h->ctl, h->ws);
+    return BMG_OK;
+  }
   Level& L0 = h->lv[0];
   if (h->krylov == BMG_KRYLOV_FCG) {
     size_t ps = plane_size(L0.n);
@@ -1008,6 +1019,45 @@ const char* bmg_strerror(int code) {
 
 const char* bmg_last_error(void) { return g_err; }
 
+namespace {
+// Periodic sides (periodic.cu): FP64 stationary V-cycles with point Gauss-Seidel
+// and Dendy interpolation; the solve loop, graph capture and control block are
+// the Dirichlet hierarchy's.
+int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int periodic, bmg_hierarchy** out) {
+  const char* why = nullptr;
+  if (periodic & ~(BMG_PERIODIC_X | BMG_PERIODIC_Y)) why = "bad periodic flags";
+  else if (h->precision != BMG_FP64) why = "periodic sides take FP64 cycles only";
+  else if (h->interp != BMG_INTERP_DENDY) why = "periodic sides take Dendy interpolation only";
+  else if (h->krylov != BMG_KRYLOV_NONE) why = "periodic sides take stationary cycles only";
+  else if (h->smoother != BMG_SMOOTHER_AUTO && h->smoother != BMG_SMOOTHER_ROWS)
+    why = "periodic sides take point Gauss-Seidel only";
+  else if (h->coarsest != 3) why = "periodic sides take the default coarsest level";
+  else if (!per_levels_for(nx, ny, periodic))
+    why = "a periodic axis needs 2^m points, a Dirichlet axis 2^m - 1, both axes the same m >= 2";
+  if (why) {
+    delete h;
+    return set_error(BMG_EINVAL, "bmg_setup (periodic %d, %d x %d): %s", periodic, nx, ny, why);
+  }
+  h->n = 0;
+  h->nlev = 0;
+  CounterScope cs(&h->launches);
+  int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
+  if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
+  if (!rc) rc = order_after_user(h);
+  if (!rc) rc = dalloc(&h->partials, 2 * (size_t)norm_partials_max());
+  if (!rc) rc = per_setup(&h->per, A->kind, A->coef, nx, ny, periodic, h->arith == BMG_ARITH_FUSED, h->nu1, h->nu2,
+                          h->ws);
+  if (!rc) rc = ensure_ctl(h, 64);
+  if (rc) {
+    bmg_free(h);
+    return rc;
+  }
+  *out = h;
+  return BMG_OK;
+}
+}  // namespace
+
 int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hierarchy** out) {
   if (!out) return set_error(BMG_EINVAL, "bmg_setup: out is NULL");
   *out = nullptr;
@@ -1063,6 +1113,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
     return set_error(BMG_EINVAL, "bmg_setup: bad options");
   }
   if (h->coarsest > h->n) h->coarsest = h->n;
+  if (o && o->periodic) return setup_periodic(h, A, nx, ny, o->periodic, out);
   CounterScope cs(&h->launches);
   int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
@@ -1283,7 +1334,19 @@ int bmg_history(const bmg_hierarchy* h, double* out, int cap) {
   return cnt;
 }
 
-int bmg_num_levels(const bmg_hierarchy* h) { return h ? h->nlev : set_error(BMG_EINVAL, "NULL hierarchy"); }
+int bmg_num_levels(const bmg_hierarchy* h) {
+  if (!h) return set_error(BMG_EINVAL, "NULL hierarchy");
+  return h->per ? per_num_levels(h->per) : h->nlev;
+}
+
+int bmg_level_shape(const bmg_hierarchy* h, int l, int* nx, int* ny) {
+  if (!h) return set_error(BMG_EINVAL, "bmg_level_shape: NULL hierarchy");
+  if (h->per) return per_level_shape(h->per, l, nx, ny);
+  if (l < 0 || l >= h->nlev) return set_error(BMG_EINVAL, "bmg_level_shape: bad level %d", l);
+  if (nx) *nx = h->lv[l].n;
+  if (ny) *ny = h->lv[l].n;
+  return BMG_OK;
+}
 
 int bmg_level_size(const bmg_hierarchy* h, int l) {
   if (!h || l < 0 || l >= h->nlev) return set_error(BMG_EINVAL, "bmg_level_size: bad level");
@@ -1291,6 +1354,7 @@ int bmg_level_size(const bmg_hierarchy* h, int l) {
 }
 
 int bmg_get_stencil(const bmg_hierarchy* h, int l, double* out) {
+  if (h && out && h->per) return per_get_stencil(h->per, l, out, h->ws);
   if (!h || !out || l < 0 || l >= h->nlev) return set_error(BMG_EINVAL, "bmg_get_stencil: bad argument");
   CK(cudaMemcpyAsync(out, h->lv[l].st, 5 * plane_size(h->lv[l].n) * sizeof(double), cudaMemcpyDeviceToDevice,
                      h->ws));
@@ -1299,6 +1363,7 @@ int bmg_get_stencil(const bmg_hierarchy* h, int l, double* out) {
 }
 
 int bmg_get_interp(const bmg_hierarchy* h, int l, double* out) {
+  if (h && out && h->per) return per_get_interp(h->per, l, out, h->ws);
   if (!h || !out || l < 0 || l + 1 >= h->nlev) return set_error(BMG_EINVAL, "bmg_get_interp: bad argument");
   CK(cudaMemcpyAsync(out, h->lv[l].ci, 8 * plane_size(h->lv[l + 1].n) * sizeof(double), cudaMemcpyDeviceToDevice,
                      h->ws));
@@ -1320,6 +1385,7 @@ void bmg_free(bmg_hierarchy* h) {
   cudaFree(h->kr);
   cudaFree(h->fpad);
   cudaFree(h->xpad);
+  per_free(h->per);
   cudaFree(h->d_tail);
   cudaFree(h->err);
   cudaFree(h->ctl);
@@ -2247,6 +2313,7 @@ int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch**
   if (!h0 || k < 1) return set_error(BMG_EINVAL, "bmg_batch_rhs: bad argument");
   if (h0->shared_ops) return set_error(BMG_EINVAL, "bmg_batch_rhs: h is itself a batch member");
   if (h0->fpad) return set_error(BMG_EINVAL, "bmg_batch_rhs: h holds an embedded (general-size) problem");
+  if (h0->per) return set_error(BMG_EINVAL, "bmg_batch_rhs: h has periodic sides");
   if (o && o->krylov != BMG_KRYLOV_NONE) return set_error(BMG_EINVAL, "bmg_batch_rhs: stationary cycles only");
   if (o && o->precision != h0->precision)
     return set_error(BMG_EINVAL, "bmg_batch_rhs: precision %d differs from the hierarchy's %d", o->precision,

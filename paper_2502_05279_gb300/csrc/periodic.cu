@@ -1,0 +1,685 @@
+// BoxMG with periodic sides: setup (stencil preparation, Dendy interpolation,
+// Galerkin coarse operators, coarsest Cholesky) and the FP64 V(nu1, nu2)
+// cycle over grids whose periodic axes wrap around.
+//
+// The formulas, term orders and arithmetic modes are those of the Dirichlet
+// kernels (k_setup.cu, cycle_device.cuh, rap_device.cuh): Dendy's collapsed-
+// stencil weights in the Fig. 2 layout, the Fig. 2 restriction, A_c = P^T A P
+// entry by entry, Gauss-Seidel by colours, residual and interpolation rows
+// in the order O, W, E, S, N, SW, NE, NW, SE.  What differs is the index map:
+// a neighbour across a periodic side is the point on the opposite side (the
+// kernels wrap the index; the ghost lines stay zero), and a coarse grid of a
+// periodic axis is periodic again.  Dirichlet axes read their zero ghosts as
+// the Dirichlet kernels do.
+//
+// Layout of a level: six planes O, W, S, SW, NW, D = 1/O of (ny+2) x (nx+2)
+// doubles; interpolation weights: eight planes of (ny_c+2) x (nx_c+2), the
+// cell (ic, jc) whose north-east corner is coarse point (ic, jc) holding the
+// weights of fine points (2ic-1, 2jc-1), (2ic-1, 2jc) and (2ic, 2jc-1); a
+// periodic axis has N_c cells (1..N_c), a Dirichlet one N_c + 1.
+#include <vector>
+
+#include "common.cuh"
+#include "cycle_device.cuh"
+#include "kernels.h"
+#include "periodic.h"
+
+namespace bmg {
+
+namespace {
+
+constexpr int PBX = 32, PBY = 8;
+
+// Index map of one level.
+struct PGeom {
+  int nx, ny, px, py;
+  __device__ __forceinline__ int wi(int i) const { return px ? (i < 1 ? i + nx : (i > nx ? i - nx : i)) : i; }
+  __device__ __forceinline__ int wj(int j) const { return py ? (j < 1 ? j + ny : (j > ny ? j - ny : j)) : j; }
+  // linear index of point (i, j), i in 0..nx+1, j in 0..ny+1, wrapped on periodic axes
+  __device__ __forceinline__ size_t at(int i, int j) const { return (size_t)wj(j) * (nx + 2) + wi(i); }
+  __host__ __device__ __forceinline__ size_t ps() const { return (size_t)(nx + 2) * (ny + 2); }
+};
+
+// Coarse cells of an axis: 1..N_c (periodic, cell N_c + 1 is cell 1) or
+// 1..N_c + 1 (Dirichlet).
+struct CellMap {
+  int ncx, ncy, px, py;
+  __device__ __forceinline__ int ci(int k) const { return px ? (k < 1 ? k + ncx : (k > ncx ? k - ncx : k)) : k; }
+  __device__ __forceinline__ int cj(int k) const { return py ? (k < 1 ? k + ncy : (k > ncy ? k - ncy : k)) : k; }
+  __device__ __forceinline__ size_t at(int ic, int jc) const { return (size_t)cj(jc) * (ncx + 2) + ci(ic); }
+  __device__ __forceinline__ size_t ps() const { return (size_t)(ncx + 2) * (ncy + 2); }
+  __device__ __forceinline__ int kx() const { return px ? ncx : ncx + 1; }
+  __device__ __forceinline__ int ky() const { return py ? ncy : ncy + 1; }
+};
+
+__host__ __device__ inline int coarse_n(int n, int periodic) { return periodic ? n / 2 : (n - 1) / 2; }
+
+__device__ __forceinline__ PGeom coarse_geom(const PGeom& g) {
+  return PGeom{coarse_n(g.nx, g.px), coarse_n(g.ny, g.py), g.px, g.py};
+}
+
+__device__ __forceinline__ CellMap cells_of(const PGeom& g) {
+  return CellMap{coarse_n(g.nx, g.px), coarse_n(g.ny, g.py), g.px, g.py};
+}
+
+// a(p, p + (dx_K, dy_K)) at point (i, j), the K-th neighbour in the canonical
+// order, through the symmetric storage: E = W(i+1, j), N = S(i, j+1),
+// NE = SW(i+1, j+1), SE = NW(i+1, j-1).
+template <int K>
+__device__ __forceinline__ double coup(const double* __restrict__ st, const PGeom& g, int i, int j) {
+  const size_t ps = g.ps();
+  if (K == 0) return st[g.at(i, j)];
+  if (K == 1) return st[ps + g.at(i, j)];
+  if (K == 2) return st[ps + g.at(i + 1, j)];
+  if (K == 3) return st[2 * ps + g.at(i, j)];
+  if (K == 4) return st[2 * ps + g.at(i, j + 1)];
+  if (K == 5) return st[3 * ps + g.at(i, j)];
+  if (K == 6) return st[3 * ps + g.at(i + 1, j + 1)];
+  if (K == 7) return st[4 * ps + g.at(i, j)];
+  return st[4 * ps + g.at(i + 1, j - 1)];
+}
+
+template <int K, bool FU>
+__device__ __forceinline__ double sub_term(double s, const double* __restrict__ st, const double* __restrict__ x,
+                                          const PGeom& g, int i, int j) {
+  return msub<FU>(s, coup<K>(st, g, i, j), x[g.at(i + nbr_dx(K), j + nbr_dy(K))]);
+}
+
+// s - sum over the row of A at (i, j) of a x, canonical order (O first when WITH_O).
+template <bool NINE, bool WITH_O, bool FU>
+__device__ __forceinline__ double prow(const double* __restrict__ st, const double* __restrict__ x, const PGeom& g,
+                                       int i, int j, double s) {
+  if (WITH_O) s = sub_term<0, FU>(s, st, x, g, i, j);
+  s = sub_term<1, FU>(s, st, x, g, i, j);
+  s = sub_term<2, FU>(s, st, x, g, i, j);
+  s = sub_term<3, FU>(s, st, x, g, i, j);
+  s = sub_term<4, FU>(s, st, x, g, i, j);
+  if (NINE) {
+    s = sub_term<5, FU>(s, st, x, g, i, j);
+    s = sub_term<6, FU>(s, st, x, g, i, j);
+    s = sub_term<7, FU>(s, st, x, g, i, j);
+    s = sub_term<8, FU>(s, st, x, g, i, j);
+  }
+  return s;
+}
+
+// ---- setup -------------------------------------------------------------------------
+// The caller's planes into the level-0 layout: ghost lines zero, couplings
+// toward a Dirichlet ghost zero, couplings across a periodic side kept.
+__global__ void k_p_prepare(PGeom g, int kind, const double* __restrict__ in, double* __restrict__ st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.nx + 1 || j > g.ny + 1) return;
+  const size_t ps = g.ps(), p = (size_t)j * (g.nx + 2) + i;
+  const bool inside = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny;
+  double o = 0, w = 0, s = 0, sw = 0, nw = 0;
+  if (inside) {
+    o = in[p];
+    if (g.px || i > 1) w = in[ps + p];
+    if (g.py || j > 1) s = in[2 * ps + p];
+    if (kind == 9) {
+      if ((g.px || i > 1) && (g.py || j > 1)) sw = in[3 * ps + p];
+      if ((g.px || i > 1) && (g.py || j < g.ny)) nw = in[4 * ps + p];
+    }
+  }
+  st[p] = o;
+  st[ps + p] = w;
+  st[2 * ps + p] = s;
+  st[3 * ps + p] = sw;
+  st[4 * ps + p] = nw;
+  st[5 * ps + p] = 0.0;
+}
+
+__global__ void k_p_dinv(PGeom g, double* __restrict__ st, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > g.nx || j > g.ny) return;
+  const size_t p = (size_t)j * (g.nx + 2) + i;
+  const double o = st[p];
+  if (!(o > 0.0)) atomicExch(err, 1);
+  st[5 * g.ps() + p] = rdiv(1.0, o);
+}
+
+struct EdgeW {
+  double lo, hi;
+};
+
+// x-edge point of cell (ic, jc) = fine (2ic-1, 2jc): LL, LR.  Zero outside the cells.
+__device__ __forceinline__ EdgeW p_xedge(const double* __restrict__ st, const PGeom& g, const CellMap& c, int ic,
+                                         int jc, int* err) {
+  if (ic < 1 || ic > c.kx() || jc < 1 || jc > c.ncy) return EdgeW{0.0, 0.0};
+  const int i = 2 * ic - 1, j = 2 * jc;
+  double D = radd(radd(coup<3>(st, g, i, j), coup<0>(st, g, i, j)), coup<4>(st, g, i, j));
+  if (!(fabs(D) > 0.0) || isinf(D)) atomicExch(err, 2);
+  double ll = -rdiv(radd(radd(coup<5>(st, g, i, j), coup<1>(st, g, i, j)), coup<7>(st, g, i, j)), D);
+  double lr = -rdiv(radd(radd(coup<8>(st, g, i, j), coup<2>(st, g, i, j)), coup<6>(st, g, i, j)), D);
+  return EdgeW{ll, lr};
+}
+
+// y-edge point of cell (ic, jc) = fine (2ic, 2jc-1): LB, LA.
+__device__ __forceinline__ EdgeW p_yedge(const double* __restrict__ st, const PGeom& g, const CellMap& c, int ic,
+                                         int jc, int* err) {
+  if (ic < 1 || ic > c.ncx || jc < 1 || jc > c.ky()) return EdgeW{0.0, 0.0};
+  const int i = 2 * ic, j = 2 * jc - 1;
+  double D = radd(radd(coup<1>(st, g, i, j), coup<0>(st, g, i, j)), coup<2>(st, g, i, j));
+  if (!(fabs(D) > 0.0) || isinf(D)) atomicExch(err, 2);
+  double lb = -rdiv(radd(radd(coup<5>(st, g, i, j), coup<3>(st, g, i, j)), coup<8>(st, g, i, j)), D);
+  double la = -rdiv(radd(radd(coup<7>(st, g, i, j), coup<4>(st, g, i, j)), coup<6>(st, g, i, j)), D);
+  return EdgeW{lb, la};
+}
+
+// One thread per cell (ic, jc) of the (nx_c+2) x (ny_c+2) weight planes: the
+// cell's edge points and its centre point, whose row of A is solved with the
+// four edge neighbours interpolated (the west and south neighbours belong to
+// cells ic - 1 and jc - 1, wrapped on a periodic axis and recomputed here with
+// the same code).  Entries outside the cells are zero.
+__global__ void k_p_dendy(PGeom g, const double* __restrict__ st, double* __restrict__ ci, int* err) {
+  const int ic = blockIdx.x * blockDim.x + threadIdx.x, jc = blockIdx.y * blockDim.y + threadIdx.y;
+  const CellMap c = cells_of(g);
+  if (ic > c.ncx + 1 || jc > c.ncy + 1) return;
+  const size_t psc = c.ps(), pc = (size_t)jc * (c.ncx + 2) + ic;
+  if (ic < 1 || jc < 1 || ic > c.kx() || jc > c.ky()) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ci[k * psc + pc] = 0.0;
+    return;
+  }
+  const EdgeW xe = p_xedge(st, g, c, ic, jc, err);
+  const EdgeW ye = p_yedge(st, g, c, ic, jc, err);
+  const EdgeW yw = p_yedge(st, g, c, g.px ? c.ci(ic - 1) : ic - 1, jc, err);   // west neighbour of the centre
+  const EdgeW xs = p_xedge(st, g, c, ic, g.py ? c.cj(jc - 1) : jc - 1, err);   // south neighbour
+  const int i = 2 * ic - 1, j = 2 * jc - 1;
+  const double aO = coup<0>(st, g, i, j), aW = coup<1>(st, g, i, j), aE = coup<2>(st, g, i, j);
+  const double aS = coup<3>(st, g, i, j), aN = coup<4>(st, g, i, j), aSW = coup<5>(st, g, i, j);
+  const double aNE = coup<6>(st, g, i, j), aNW = coup<7>(st, g, i, j), aSE = coup<8>(st, g, i, j);
+  if (!(aO > 0.0)) atomicExch(err, 2);
+  ci[CI_LSW * psc + pc] = -rdiv(radd(radd(aSW, rmul(aW, yw.lo)), rmul(aS, xs.lo)), aO);
+  ci[CI_LSE * psc + pc] = -rdiv(radd(radd(aSE, rmul(aE, ye.lo)), rmul(aS, xs.hi)), aO);
+  ci[CI_LNW * psc + pc] = -rdiv(radd(radd(aNW, rmul(aW, yw.hi)), rmul(aN, xe.lo)), aO);
+  ci[CI_LNE * psc + pc] = -rdiv(radd(radd(aNE, rmul(aE, ye.hi)), rmul(aN, xe.hi)), aO);
+  ci[CI_LL * psc + pc] = xe.lo;
+  ci[CI_LR * psc + pc] = xe.hi;
+  ci[CI_LB * psc + pc] = ye.lo;
+  ci[CI_LA * psc + pc] = ye.hi;
+}
+
+// phi(c', dx, dy): weight of fine point 2c' + (dx, dy) toward coarse point c'.
+// On a periodic axis c' wraps; on a Dirichlet axis a ghost c' has weight 0.
+template <int DX, int DY>
+__device__ __forceinline__ double p_phi(const double* __restrict__ ci, const CellMap& c, int ic, int jc) {
+  if (c.px) ic = c.ci(ic);
+  else if (ic < 1 || ic > c.ncx) return 0.0;
+  if (c.py) jc = c.cj(jc);
+  else if (jc < 1 || jc > c.ncy) return 0.0;
+  const size_t psc = c.ps();
+  if (DX == 0 && DY == 0) return 1.0;
+  if (DX == -1 && DY == 0) return ci[CI_LR * psc + c.at(ic, jc)];
+  if (DX == 1 && DY == 0) return ci[CI_LL * psc + c.at(ic + 1, jc)];
+  if (DX == 0 && DY == -1) return ci[CI_LA * psc + c.at(ic, jc)];
+  if (DX == 0 && DY == 1) return ci[CI_LB * psc + c.at(ic, jc + 1)];
+  if (DX == -1 && DY == -1) return ci[CI_LNE * psc + c.at(ic, jc)];
+  if (DX == 1 && DY == -1) return ci[CI_LNW * psc + c.at(ic + 1, jc)];
+  if (DX == -1 && DY == 1) return ci[CI_LSE * psc + c.at(ic, jc + 1)];
+  return ci[CI_LSW * psc + c.at(ic + 1, jc + 1)];
+}
+
+// A_c(c, c+t) = sum_u phi_c(u) sum_v a(2c+u, v) phi_{c+t}(u + v - 2t), u over the
+// 3x3 block (dy outer, dx inner), v in the canonical order, structural zeros
+// skipped at compile time; one rounding per operation (the order of the
+// Dirichlet kernel, indices wrapped).
+template <int TX, int TY, int UX, int UY, int K>
+struct PInner {
+  __device__ __forceinline__ static void run(const double* st, const PGeom& g, const double* ci, const CellMap& c,
+                                             int ic, int jc, double& acc, bool& any) {
+    constexpr int OX = UX + nbr_dx(K) - 2 * TX;
+    constexpr int OY = UY + nbr_dy(K) - 2 * TY;
+    if constexpr (OX >= -1 && OX <= 1 && OY >= -1 && OY <= 1) {
+      double term = rmul(coup<K>(st, g, 2 * ic + UX, 2 * jc + UY), p_phi<OX, OY>(ci, c, ic + TX, jc + TY));
+      acc = any ? radd(acc, term) : term;
+      any = true;
+    }
+    if constexpr (K < 8) PInner<TX, TY, UX, UY, K + 1>::run(st, g, ci, c, ic, jc, acc, any);
+  }
+};
+
+template <int TX, int TY, int B>
+struct POuter {
+  __device__ __forceinline__ static void run(const double* st, const PGeom& g, const double* ci, const CellMap& c,
+                                             int ic, int jc, double& acc, bool& any) {
+    constexpr int UX = (B % 3) - 1, UY = (B / 3) - 1;
+    double inner = 0.0;
+    bool iany = false;
+    PInner<TX, TY, UX, UY, 0>::run(st, g, ci, c, ic, jc, inner, iany);
+    if (iany) {
+      double term = rmul(p_phi<UX, UY>(ci, c, ic, jc), inner);
+      acc = any ? radd(acc, term) : term;
+      any = true;
+    }
+    if constexpr (B < 8) POuter<TX, TY, B + 1>::run(st, g, ci, c, ic, jc, acc, any);
+  }
+};
+
+template <int TX, int TY>
+__device__ __forceinline__ double p_rap_entry(const double* st, const PGeom& g, const double* ci, const CellMap& c,
+                                              int ic, int jc) {
+  double acc = 0.0;
+  bool any = false;
+  POuter<TX, TY, 0>::run(st, g, ci, c, ic, jc, acc, any);
+  return acc;
+}
+
+// One thread per coarse point of the (nx_c+2) x (ny_c+2) planes; couplings
+// toward a Dirichlet ghost zero, ghost lines zero, D left for k_p_dinv.
+__global__ void k_p_rap(PGeom g, const double* __restrict__ st, const double* __restrict__ ci,
+                        double* __restrict__ stc) {
+  const int ic = blockIdx.x * blockDim.x + threadIdx.x, jc = blockIdx.y * blockDim.y + threadIdx.y;
+  const CellMap c = cells_of(g);
+  if (ic > c.ncx + 1 || jc > c.ncy + 1) return;
+  const size_t psc = c.ps(), pc = (size_t)jc * (c.ncx + 2) + ic;
+  if (ic < 1 || jc < 1 || ic > c.ncx || jc > c.ncy) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) stc[k * psc + pc] = 0.0;
+    return;
+  }
+  const bool w_in = g.px || ic > 1, s_in = g.py || jc > 1, n_in = g.py || jc < c.ncy;
+  stc[pc] = p_rap_entry<0, 0>(st, g, ci, c, ic, jc);
+  stc[psc + pc] = w_in ? p_rap_entry<-1, 0>(st, g, ci, c, ic, jc) : 0.0;
+  stc[2 * psc + pc] = s_in ? p_rap_entry<0, -1>(st, g, ci, c, ic, jc) : 0.0;
+  stc[3 * psc + pc] = (w_in && s_in) ? p_rap_entry<-1, -1>(st, g, ci, c, ic, jc) : 0.0;
+  stc[4 * psc + pc] = (w_in && n_in) ? p_rap_entry<-1, 1>(st, g, ci, c, ic, jc) : 0.0;
+  stc[5 * psc + pc] = 0.0;
+}
+
+// Coarsest Cholesky (one thread, m = nx ny <= 16): the dense matrix over
+// lexicographic unknowns (a coupling across a periodic side lands on the
+// wrapped unknown, entries landing on one unknown add), then right-looking
+// Cholesky in the Dirichlet kernel's order.
+__global__ void k_p_factor(PGeom g, const double* __restrict__ st, double* __restrict__ L, double* __restrict__ a,
+                           int* err) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int m = g.nx * g.ny;
+  for (int k = 0; k < m * m; ++k) {
+    a[k] = 0.0;
+    L[k] = 0.0;
+  }
+  for (int j = 1; j <= g.ny; ++j)
+    for (int i = 1; i <= g.nx; ++i) {
+      const int r = (j - 1) * g.nx + (i - 1);
+      const double v[9] = {coup<0>(st, g, i, j), coup<1>(st, g, i, j), coup<2>(st, g, i, j),
+                           coup<3>(st, g, i, j), coup<4>(st, g, i, j), coup<5>(st, g, i, j),
+                           coup<6>(st, g, i, j), coup<7>(st, g, i, j), coup<8>(st, g, i, j)};
+      for (int k = 0; k < 9; ++k) {
+        const int ii = g.wi(i + nbr_dx(k)), jj = g.wj(j + nbr_dy(k));
+        if (ii >= 1 && ii <= g.nx && jj >= 1 && jj <= g.ny) {
+          double& e = a[(size_t)r * m + (jj - 1) * g.nx + (ii - 1)];
+          e = radd(e, v[k]);
+        }
+      }
+    }
+  for (int k = 0; k < m; ++k) {
+    const double akk = a[(size_t)k * m + k];
+    if (!(akk > 0.0)) {
+      atomicExch(err, 3);
+      return;
+    }
+    const double lkk = __dsqrt_rn(akk);
+    L[(size_t)k * m + k] = lkk;
+    for (int i = k + 1; i < m; ++i) L[(size_t)i * m + k] = rdiv(a[(size_t)i * m + k], lkk);
+    for (int j = k + 1; j < m; ++j)
+      for (int i = j; i < m; ++i)
+        a[(size_t)i * m + j] = rsub(a[(size_t)i * m + j], rmul(L[(size_t)i * m + k], L[(size_t)j * m + k]));
+  }
+}
+
+// ---- cycle -------------------------------------------------------------------------
+// One colour (i % 2 == pi, j % 2 == pj) of a Gauss-Seidel sweep: x_p = (f_p -
+// sum_{q != p} a_pq x_q) * D_p.  Points of one colour share no coupling (N is
+// even on a periodic axis, so the colouring holds across the seam).
+template <bool NINE, bool FU>
+__global__ void k_p_gs(PGeom g, const double* __restrict__ st, const double* __restrict__ f, double* x, int pi,
+                       int pj, const int* done) {
+  if (dev::stopped(done)) return;
+  const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + (pi ? 1 : 2);
+  const int j = 2 * (int)(blockIdx.y * blockDim.y + threadIdx.y) + (pj ? 1 : 2);
+  if (i > g.nx || j > g.ny) return;
+  const size_t p = (size_t)j * (g.nx + 2) + i;
+  const double s = prow<NINE, false, FU>(st, x, g, i, j, f[p]);
+  x[p] = rmul(s, st[5 * g.ps() + p]);
+}
+
+// r = f - A x (when r != NULL) and the partial sums of r^2 in the canonical
+// reduction order (block b of G = min(ny, 1024): rows 1 + b, 1 + b + G, ...;
+// thread t: columns 1 + t, 1 + t + 256, ...; then the halving tree).
+template <bool NINE, bool FU>
+__global__ void __launch_bounds__(dev::NORM_THREADS) k_p_residual(PGeom g, const double* __restrict__ st,
+                                                                  const double* __restrict__ x,
+                                                                  const double* __restrict__ f, double* __restrict__ r,
+                                                                  double* __restrict__ partials, const int* done) {
+  if (dev::stopped(done)) return;
+  const int b = blockIdx.x, G = gridDim.x;
+  double acc = 0.0;
+  for (int j = 1 + b; j <= g.ny; j += G)
+    for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
+      const size_t p = (size_t)j * (g.nx + 2) + i;
+      const double s = prow<NINE, true, FU>(st, x, g, i, j, f[p]);
+      if (r) r[p] = s;
+      acc = madd<FU>(acc, s, s);
+    }
+  if (partials) {
+    const double tot = dev::block_sum(acc);
+    if (threadIdx.x == 0) partials[b] = tot;
+  }
+}
+
+// f_c = P^T r at coarse point (ic, jc), term by term in the order of the Fig. 2
+// loop (a primed weight read at the neighbouring cell, wrapped on a periodic
+// axis); the coincident term has weight 1.
+template <bool FU>
+__global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const double* __restrict__ r,
+                             double* __restrict__ fc, const int* done) {
+  if (dev::stopped(done)) return;
+  const CellMap c = cells_of(g);
+  const int ic = blockIdx.x * blockDim.x + threadIdx.x + 1, jc = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (ic > c.ncx || jc > c.ncy) return;
+  const size_t psc = c.ps();
+  const int i = 2 * ic, j = 2 * jc;
+  auto q = [&](int di, int dj) { return r[g.at(i + di, j + dj)]; };
+  auto w = [&](int k, int dic, int djc) { return ci[k * psc + c.at(ic + dic, jc + djc)]; };
+  double t = rmul(w(CI_LNE, 0, 0), q(-1, -1));
+  t = madd<FU>(t, w(CI_LA, 0, 0), q(0, -1));
+  t = madd<FU>(t, w(CI_LNW, 1, 0), q(1, -1));
+  t = madd<FU>(t, w(CI_LR, 0, 0), q(-1, 0));
+  t = radd(t, q(0, 0));
+  t = madd<FU>(t, w(CI_LL, 1, 0), q(1, 0));
+  t = madd<FU>(t, w(CI_LSE, 0, 1), q(-1, 1));
+  t = madd<FU>(t, w(CI_LB, 0, 1), q(0, 1));
+  t = madd<FU>(t, w(CI_LSW, 1, 1), q(1, 1));
+  fc[(size_t)jc * (c.ncx + 2) + ic] = t;
+}
+
+// x += P e_c at fine point (i, j): the interpolated value is formed first, then
+// added (coincident e; x-edge LL e_W + LR e_E; y-edge LB e_S + LA e_N; centre
+// ((LSW e_SW + LSE e_SE) + LNW e_NW) + LNE e_NE), coarse neighbours wrapped on a
+// periodic axis, a Dirichlet ghost reading its zero.
+template <bool FU>
+__global__ void k_p_interp(PGeom g, const double* __restrict__ ci, const double* __restrict__ ec,
+                           double* __restrict__ x, const int* done) {
+  if (dev::stopped(done)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > g.nx || j > g.ny) return;
+  const PGeom gc = coarse_geom(g);
+  const CellMap c = cells_of(g);
+  const size_t psc = c.ps(), p = (size_t)j * (g.nx + 2) + i;
+  auto e = [&](int a, int b) { return ec[gc.at(a, b)]; };
+  auto w = [&](int k, int ic, int jc) { return ci[k * psc + (size_t)jc * (c.ncx + 2) + ic]; };
+  double t;
+  if (!(i & 1) && !(j & 1)) {
+    t = e(i / 2, j / 2);
+  } else if ((i & 1) && !(j & 1)) {
+    const int ic = (i + 1) / 2, jc = j / 2;
+    t = rmul(w(CI_LL, ic, jc), e(ic - 1, jc));
+    t = madd<FU>(t, w(CI_LR, ic, jc), e(ic, jc));
+  } else if (!(i & 1) && (j & 1)) {
+    const int ic = i / 2, jc = (j + 1) / 2;
+    t = rmul(w(CI_LB, ic, jc), e(ic, jc - 1));
+    t = madd<FU>(t, w(CI_LA, ic, jc), e(ic, jc));
+  } else {
+    const int ic = (i + 1) / 2, jc = (j + 1) / 2;
+    t = rmul(w(CI_LSW, ic, jc), e(ic - 1, jc - 1));
+    t = madd<FU>(t, w(CI_LSE, ic, jc), e(ic, jc - 1));
+    t = madd<FU>(t, w(CI_LNW, ic, jc), e(ic - 1, jc));
+    t = madd<FU>(t, w(CI_LNE, ic, jc), e(ic, jc));
+  }
+  x[p] = radd(x[p], t);
+}
+
+// L L^T x = f on the coarsest level (one thread, m <= 16): forward then backward
+// substitution, inner sums in increasing index order.
+__global__ void k_p_coarse_solve(PGeom g, const double* __restrict__ L, const double* __restrict__ f,
+                                 double* __restrict__ x, const int* done) {
+  if (dev::stopped(done)) return;
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int m = g.nx * g.ny;
+  double y[16], z[16];
+  for (int i = 0; i < m; ++i) {
+    double s = f[(size_t)(i / g.nx + 1) * (g.nx + 2) + (i % g.nx + 1)];
+    for (int k = 0; k < i; ++k) s = rsub(s, rmul(L[(size_t)i * m + k], y[k]));
+    y[i] = rdiv(s, L[(size_t)i * m + i]);
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < m; ++k) s = rsub(s, rmul(L[(size_t)k * m + i], z[k]));
+    z[i] = rdiv(s, L[(size_t)i * m + i]);
+  }
+  for (int i = 0; i < m; ++i) x[(size_t)(i / g.nx + 1) * (g.nx + 2) + (i % g.nx + 1)] = z[i];
+}
+
+dim3 pgrid(int nx, int ny) { return dim3((unsigned)((nx + PBX - 1) / PBX), (unsigned)((ny + PBY - 1) / PBY)); }
+
+int m_of(int n, int periodic) {
+  const int v = periodic ? n : n + 1;
+  if (v < 4 || (v & (v - 1))) return -1;
+  int m = 0;
+  while ((1 << m) < v) ++m;
+  return m;
+}
+
+}  // namespace
+
+struct PerLevel {
+  PGeom g{};
+  int kind = 9;
+  double* st = nullptr;   // O, W, S, SW, NW, D
+  double* ci = nullptr;   // weights toward the next level
+  double* x = nullptr;    // iterate and right-hand side of a coarse level
+  double* f = nullptr;
+  double* r = nullptr;    // residual of a level above the coarsest
+};
+
+struct PerHier {
+  int periodic = 0, fused = 0, nu1 = 2, nu2 = 1;
+  std::vector<PerLevel> lv;
+  double* L = nullptr;
+  double* work = nullptr;
+  int* err = nullptr;
+};
+
+int per_levels_for(int nx, int ny, int periodic) {
+  const int mx = m_of(nx, periodic & 1), my = m_of(ny, periodic & 2);
+  if (mx < 2 || mx != my) return 0;
+  return mx - 1;   // m, m-1, ..., 2
+}
+
+static int palloc(double** p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (cudaMalloc((void**)p, count * sizeof(double)) != cudaSuccess) {
+    *p = nullptr;
+    return set_error(BMG_ENOMEM, "periodic setup: device allocation of %zu doubles failed", count);
+  }
+  return cuda_check(cudaMemsetAsync(*p, 0, count * sizeof(double), s), "periodic setup: memset");
+}
+
+void per_free(PerHier* P) {
+  if (!P) return;
+  for (PerLevel& L : P->lv) {
+    cudaFree(L.st);
+    cudaFree(L.ci);
+    cudaFree(L.x);
+    cudaFree(L.f);
+    cudaFree(L.r);
+  }
+  cudaFree(P->L);
+  cudaFree(P->work);
+  cudaFree(P->err);
+  delete P;
+}
+
+int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int periodic, int fused, int nu1,
+              int nu2, cudaStream_t s) {
+  *out = nullptr;
+  const int nlev = per_levels_for(nx, ny, periodic);
+  if (nlev < 1)
+    return set_error(BMG_EINVAL,
+                     "bmg_setup: %d x %d with periodic flags %d: a periodic axis needs 2^m points, a Dirichlet "
+                     "axis 2^m - 1, both axes the same m >= 2",
+                     nx, ny, periodic);
+  PerHier* P = new PerHier();
+  P->periodic = periodic;
+  P->fused = fused;
+  P->nu1 = nu1;
+  P->nu2 = nu2;
+  P->lv.resize(nlev);
+  const int px = periodic & 1 ? 1 : 0, py = periodic & 2 ? 1 : 0;
+  int rc = BMG_OK;
+  for (int l = 0; l < nlev && !rc; ++l) {
+    PerLevel& L = P->lv[l];
+    L.g = l == 0 ? PGeom{nx, ny, px, py} : PGeom{coarse_n(P->lv[l - 1].g.nx, px), coarse_n(P->lv[l - 1].g.ny, py), px, py};
+    L.kind = l == 0 ? kind : 9;
+    const size_t ps = L.g.ps();
+    rc = palloc(&L.st, 6 * ps, s);
+    if (!rc && l + 1 < nlev) {
+      const size_t psc = (size_t)(coarse_n(L.g.nx, px) + 2) * (coarse_n(L.g.ny, py) + 2);
+      rc = palloc(&L.ci, 8 * psc, s);
+      if (!rc) rc = palloc(&L.r, ps, s);
+    }
+    if (!rc && l > 0) rc = palloc(&L.x, ps, s);
+    if (!rc && l > 0) rc = palloc(&L.f, ps, s);
+  }
+  const PGeom gc = P->lv[nlev - 1].g;
+  const int m = gc.nx * gc.ny;
+  if (!rc) rc = palloc(&P->L, (size_t)m * m, s);
+  if (!rc) rc = palloc(&P->work, (size_t)m * m, s);
+  if (!rc && cudaMalloc((void**)&P->err, sizeof(int)) != cudaSuccess) rc = set_error(BMG_ENOMEM, "periodic setup");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(P->err, 0, sizeof(int), s), "periodic setup: memset");
+  if (rc) {
+    per_free(P);
+    return rc;
+  }
+  const PGeom g0 = P->lv[0].g;
+  k_p_prepare<<<pgrid(g0.nx + 2, g0.ny + 2), dim3(PBX, PBY), 0, s>>>(g0, kind, coef, P->lv[0].st);
+  count_launch();
+  k_p_dinv<<<pgrid(g0.nx, g0.ny), dim3(PBX, PBY), 0, s>>>(g0, P->lv[0].st, P->err);
+  count_launch();
+  for (int l = 0; l + 1 < nlev; ++l) {
+    PerLevel &F = P->lv[l], &C = P->lv[l + 1];
+    const int ncx = C.g.nx, ncy = C.g.ny;
+    k_p_dendy<<<pgrid(ncx + 2, ncy + 2), dim3(PBX, PBY), 0, s>>>(F.g, F.st, F.ci, P->err);
+    count_launch();
+    k_p_rap<<<pgrid(ncx + 2, ncy + 2), dim3(PBX, PBY), 0, s>>>(F.g, F.st, F.ci, C.st);
+    count_launch();
+    k_p_dinv<<<pgrid(ncx, ncy), dim3(PBX, PBY), 0, s>>>(C.g, C.st, P->err);
+    count_launch();
+  }
+  k_p_factor<<<1, 1, 0, s>>>(gc, P->lv[nlev - 1].st, P->L, P->work, P->err);
+  count_launch();
+  int herr = 0;
+  rc = cuda_check(cudaGetLastError(), "periodic setup");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, s), "periodic setup");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "periodic setup");
+  if (!rc && herr)
+    rc = set_error(BMG_ESINGULAR, "periodic setup: non-positive %s (a grid periodic along both axes needs a "
+                                  "non-singular operator)",
+                   herr == 1 ? "diagonal" : herr == 2 ? "interpolation denominator" : "Cholesky pivot");
+  if (rc) {
+    per_free(P);
+    return rc;
+  }
+  *out = P;
+  return BMG_OK;
+}
+
+namespace {
+
+template <bool FU>
+void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, cudaStream_t s) {
+  // colour order: 9-point (odd,odd), (even,odd), (odd,even), (even,even); 5-point red then black
+  static const int c9[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
+  static const int c5[4][2] = {{1, 1}, {0, 0}, {0, 1}, {1, 0}};
+  const bool nine = L.kind == 9;
+  for (int k = 0; k < 4; ++k) {
+    const int pi = nine ? c9[k][0] : c5[k][0], pj = nine ? c9[k][1] : c5[k][1];
+    const int cx = pi ? (L.g.nx + 1) / 2 : L.g.nx / 2, cy = pj ? (L.g.ny + 1) / 2 : L.g.ny / 2;
+    if (nine)
+      k_p_gs<true, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
+    else
+      k_p_gs<false, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
+    count_launch();
+  }
+}
+
+template <bool FU>
+int per_residual(const PerLevel& L, const double* x, const double* f, double* r, double* partials, const int* done,
+                 cudaStream_t s) {
+  const int G = L.g.ny < dev::NORM_BLOCKS_MAX ? L.g.ny : dev::NORM_BLOCKS_MAX;
+  if (L.kind == 9)
+    k_p_residual<true, FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, L.st, x, f, r, partials, done);
+  else
+    k_p_residual<false, FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, L.st, x, f, r, partials, done);
+  count_launch();
+  return G;
+}
+
+template <bool FU>
+void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, cudaStream_t s) {
+  PerLevel& L = P->lv[l];
+  if (l + 1 == (int)P->lv.size()) {
+    k_p_coarse_solve<<<1, 1, 0, s>>>(L.g, P->L, f, x, done);
+    count_launch();
+    return;
+  }
+  PerLevel& C = P->lv[l + 1];
+  for (int k = 0; k < P->nu1; ++k) per_sweep<FU>(L, f, x, done, s);
+  per_residual<FU>(L, x, f, L.r, nullptr, done, s);
+  k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, done);
+  count_launch();
+  cudaMemsetAsync(C.x, 0, C.g.ps() * sizeof(double), s);
+  per_vcycle<FU>(P, l + 1, C.x, C.f, done, s);
+  k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, x, done);
+  count_launch();
+  for (int k = 0; k < P->nu2; ++k) per_sweep<FU>(L, f, x, done, s);
+}
+
+}  // namespace
+
+void per_enqueue_initial(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s) {
+  const int G = P->fused ? per_residual<true>(P->lv[0], x, rhs, nullptr, partials, nullptr, s)
+                         : per_residual<false>(P->lv[0], x, rhs, nullptr, partials, nullptr, s);
+  launch_norm_finalize(partials, G, ctl, 0, nullptr, s);
+}
+
+void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s) {
+  const int* done = &ctl->done;
+  int G;
+  if (P->fused) {
+    per_vcycle<true>(P, 0, x, rhs, done, s);
+    G = per_residual<true>(P->lv[0], x, rhs, nullptr, partials, done, s);
+  } else {
+    per_vcycle<false>(P, 0, x, rhs, done, s);
+    G = per_residual<false>(P->lv[0], x, rhs, nullptr, partials, done, s);
+  }
+  launch_norm_finalize(partials, G, ctl, 1, nullptr, s);
+}
+
+int per_num_levels(const PerHier* P) { return (int)P->lv.size(); }
+
+int per_level_shape(const PerHier* P, int l, int* nx, int* ny) {
+  if (l < 0 || l >= (int)P->lv.size()) return set_error(BMG_EINVAL, "bmg_level_shape: bad level %d", l);
+  if (nx) *nx = P->lv[l].g.nx;
+  if (ny) *ny = P->lv[l].g.ny;
+  return BMG_OK;
+}
+
+int per_get_stencil(const PerHier* P, int l, double* out, cudaStream_t s) {
+  if (l < 0 || l >= (int)P->lv.size()) return set_error(BMG_EINVAL, "bmg_get_stencil: bad level %d", l);
+  const PerLevel& L = P->lv[l];
+  int rc = cuda_check(cudaMemcpyAsync(out, L.st, 5 * L.g.ps() * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                      "bmg_get_stencil");
+  return rc ? rc : cuda_check(cudaStreamSynchronize(s), "bmg_get_stencil");
+}
+
+int per_get_interp(const PerHier* P, int l, double* out, cudaStream_t s) {
+  if (l < 0 || l + 1 >= (int)P->lv.size()) return set_error(BMG_EINVAL, "bmg_get_interp: bad level %d", l);
+  const PerLevel& C = P->lv[l + 1];
+  int rc = cuda_check(cudaMemcpyAsync(out, P->lv[l].ci, 8 * C.g.ps() * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                      "bmg_get_interp");
+  return rc ? rc : cuda_check(cudaStreamSynchronize(s), "bmg_get_interp");
+}
+
+}  // namespace bmg

@@ -1,0 +1,173 @@
+"""Periodic sides on the GPU (bmg_opts.periodic) against the periodic oracle
+(oracle/periodic.py): the hierarchy bit for bit, the iterates of the V(2,1)
+cycles bit for bit, the residual histories bit for bit in the device's
+summation order and at the stated reading against the plain norm, and the
+solve to 1e-10 confirmed by the oracle's own residual."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle import boxmg as bx
+from oracle import periodic as pr
+from reduction_order import device_norm
+
+pytestmark = pytest.mark.gpu
+
+AXES = ["x", "y", "xy"]
+
+
+def problem(n, axes, seed=52, kind=9):
+    shift = 0.3 if axes == "xy" else 0.0
+    if kind == 5:
+        nx, ny = w.periodic_shape(n, axes)
+        planes = np.zeros((5, ny + 2, nx + 2))
+        planes[0, 1:-1, 1:-1] = 4.0 + shift
+        planes[1, 1:-1, 1:-1] = -1.0
+        planes[2, 1:-1, 1:-1] = -1.0
+        return 5, planes, w.rhs_uniform(nx, seed + 1, ny), "x" in axes, "y" in axes
+    return w.periodic_problem(n, axes, std=2.0, corr_len=8.0, seed_k=seed, seed_f=seed + 1, shift=shift)
+
+
+def hierarchy(bmg, kind, planes, axes, **kw):
+    return bmg.Hierarchy(kind, torch.from_numpy(planes).cuda(), periodic=axes, **kw)
+
+
+def interior(a):
+    return np.asarray(a)[..., 1:-1, 1:-1]
+
+
+@pytest.mark.parametrize("axes", AXES)
+@pytest.mark.parametrize("n", [15, 63, 255])
+def test_hierarchy_bitwise(bmg, axes, n):
+    kind, planes, f, px, py = problem(n, axes)
+    levels = pr.setup(kind, planes, px, py)
+    h = hierarchy(bmg, kind, planes, axes)
+    assert h.num_levels == len(levels)
+    for l, lev in enumerate(levels):
+        assert h.level_shape(l) == (lev.nx, lev.ny)
+        assert np.array_equal(interior(h.stencil(l).cpu().numpy()), interior(lev.planes))
+        if lev.ci is not None:
+            ci = h.interp(l).cpu().numpy()
+            kx, ky = pr.cell_count(lev.nx, px), pr.cell_count(lev.ny, py)
+            assert np.array_equal(ci[:, 1:ky + 1, 1:kx + 1], lev.ci[:, 1:ky + 1, 1:kx + 1])
+            assert not ci[:, 0].any() and not ci[:, :, 0].any()
+    h.close()
+
+
+def oracle_cycles(levels, f, cycles, fused):
+    """Iterates and device-order residual norms of `cycles` V(2,1) cycles."""
+    lev = levels[0]
+    x = np.zeros_like(f)
+    r = pr.residual(lev.planes, x, f, lev.px, lev.py, fused)
+    hist = [device_norm(r, fused)]
+    plain = [bx.norm(r)]
+    for _ in range(cycles):
+        pr.vcycle(levels, 0, x, f)
+        r = pr.residual(lev.planes, x, f, lev.px, lev.py, fused)
+        hist.append(device_norm(r, fused))
+        plain.append(bx.norm(r))
+    return x, hist, plain
+
+
+@pytest.mark.parametrize("axes", AXES)
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_cycles_bitwise(bmg, axes, arith, use_graph):
+    n = 127
+    kind, planes, f, px, py = problem(n, axes, seed=56)
+    levels = pr.setup(kind, planes, px, py, arith=arith)
+    x_o, hist_o, plain_o = oracle_cycles(levels, f, 5, arith == "fused")
+    h = hierarchy(bmg, kind, planes, axes, arith=arith, use_graph=use_graph)
+    rhs = torch.from_numpy(f).cuda()
+    x, it, rr, ok = h.solve(rhs, tol=0.0, maxit=5)
+    assert it == 5 and not ok
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
+    hist = h.history()
+    assert hist == hist_o
+    for g, t in zip(hist, plain_o):
+        assert abs(g - t) <= 1e-12 * plain_o[0]
+        if t >= 1e-3 * plain_o[0]:
+            assert abs(g - t) <= 1e-12 * t
+    h.close()
+
+
+@pytest.mark.parametrize("axes", ["x", "y"])
+def test_five_point_cycles_bitwise(bmg, axes):
+    kind, planes, f, px, py = problem(63, axes, kind=5)
+    levels = pr.setup(kind, planes, px, py)
+    x_o, hist_o, _ = oracle_cycles(levels, f, 4, False)
+    h = hierarchy(bmg, kind, planes, axes)
+    x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=4)
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
+    assert h.history() == hist_o
+    h.close()
+
+
+@pytest.mark.parametrize("axes", AXES)
+def test_solve_to_tolerance(bmg, axes):
+    n = 511
+    kind, planes, f, px, py = problem(n, axes, seed=58)
+    h = hierarchy(bmg, kind, planes, axes, arith="fused")
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=100)
+    assert ok and rr <= 1e-10 and it < 60
+    P = pr.prepare(kind, planes, px, py)
+    xo = x.cpu().numpy()
+    r = pr.residual(P, xo, f, px, py)
+    assert bx.norm(r) <= 1.01e-10 * bx.norm(pr.residual(P, np.zeros_like(f), f, px, py))
+    h.close()
+
+
+def test_full_size_cycles_bitwise(bmg):
+    """4096 x 4095, periodic in x: two cycles bitwise, the same launch
+    configuration the bench times."""
+    kind, planes, f, px, py = w.periodic_problem(4095, "x", seed_k=50, seed_f=51)
+    levels = pr.setup(kind, planes, px, py, arith="fused")
+    h = hierarchy(bmg, kind, planes, "x", arith="fused")
+    x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=2)
+    x_o = np.zeros_like(f)
+    for _ in range(2):
+        pr.vcycle(levels, 0, x_o, f)
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
+    h.close()
+
+
+def test_singular_torus_is_reported(bmg):
+    kind, planes, f, px, py = w.periodic_problem(15, "xy", std=1.0, corr_len=4.0)
+    with pytest.raises(bx.SingularError):
+        pr.setup(kind, planes, px, py)
+    with pytest.raises(bmg.BmgError) as e:
+        hierarchy(bmg, kind, planes, "xy")
+    assert e.value.code == bmg.BMG_ESINGULAR
+
+
+@pytest.mark.parametrize("shape,axes", [((15, 15), "x"), ((32, 15), "x"), ((16, 16), "x"), ((16, 15), "y"),
+                                        ((16, 15), "xy")])
+def test_bad_periodic_sizes(bmg, shape, axes):
+    nx, ny = shape
+    planes = np.zeros((5, ny + 2, nx + 2))
+    planes[0] = 4.0
+    with pytest.raises(bmg.BmgError) as e:
+        hierarchy(bmg, 9, planes, axes)
+    assert e.value.code == bmg.BMG_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(krylov="fcg"), dict(smoother="tile0"),
+                                dict(coarsest=7)])
+def test_unsupported_options(bmg, kw):
+    kind, planes, f, px, py = problem(63, "x")
+    with pytest.raises(bmg.BmgError) as e:
+        hierarchy(bmg, kind, planes, "x", **kw)
+    assert e.value.code == bmg.BMG_EINVAL
+
+
+def test_square_only_calls_refuse(bmg):
+    kind, planes, f, px, py = problem(63, "x")
+    h = hierarchy(bmg, kind, planes, "x")
+    assert bmg.lib.bmg_level_size(h._h, 0) == bmg.BMG_EINVAL
+    out = ctypes.c_void_p()
+    assert bmg.lib.bmg_batch_rhs(h._h, 2, None, ctypes.byref(out)) == bmg.BMG_EINVAL
+    assert bmg.lib.bmg_tuned_cluster(h._h, 0) == bmg.BMG_EINVAL
+    h.close()
