@@ -193,6 +193,133 @@ RHS_BATCHES = {
 }
 
 
+PERIODIC = {
+    "periodic4095": dict(text="4096x4095 interior points, periodic in x (4096 = 2^12 columns, point 4097 is point 1), "
+                              "zero Dirichlet in y; 9-point Q1 FE of -div(k grad u), k = exp(g), g the periodic "
+                              "Gaussian field std 2, correlation 32 cells (seed 50) on the 4096^2 cells; RHS U[-1,1) "
+                              "seed 51; FP64 V(2,1), four-colour GS, 11 levels down to 4 x 3", n=4095, axes="x"),
+}
+
+
+def run_periodic(args, rank, local_rank, world):
+    """Periodic sides: the FP64 V(2,1) of the periodic hierarchy (one launch
+    per colour of each sweep, indices wrapped), its throughput, its time to
+    1e-10 and the level-0 sweep against the copy bandwidth."""
+    import torch
+    import paper_2502_05279_gb300 as bmg
+    torch.cuda.set_device(local_rank)
+    ranks = Ranks("nccl")
+    spec = PERIODIC[args.workload]
+    kind, planes, f, px, py = w.periodic_problem(spec["n"], spec["axes"], seed_k=50, seed_f=51)
+    nx, ny = planes.shape[-1] - 2, planes.shape[-2] - 2
+    N = nx * ny
+    coef = torch.from_numpy(planes).cuda()
+    rhs = torch.from_numpy(f).cuda()
+    t0 = time.perf_counter()
+    h = bmg.Hierarchy(kind, coef, arith=args.arith, periodic=spec["axes"])
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    x = torch.zeros_like(rhs)
+    h.time_cycles(rhs, x, max(args.warmup, 3))
+    ranks.barrier()
+    before = h.launch_count
+    with ClockSampler(local_rank) as cs:
+        with cs.timed():
+            ms = h.time_cycles(rhs, x, args.steps)
+        launches = h.launch_count - before
+        ms = ranks.max(ms)
+        prof = h.profile(rhs, torch.zeros_like(rhs), 3)
+        x.zero_()
+        h.solve(rhs, x, tol=1e-10, maxit=2)                 # graph capture, untimed
+        x.zero_()
+        ranks.barrier()
+        with cs.timed():
+            t0 = time.perf_counter()
+            _, iters, relres, ok = h.solve(rhs, x, tol=1e-10, maxit=args.maxit_vcycle)
+            torch.cuda.synchronize()
+            t_solve = ranks.max(time.perf_counter() - t0)
+    clocks = cs.summary()
+    # end to end through the public API with host buffers
+    rhs_host = torch.from_numpy(f).pin_memory()
+    x_host = torch.empty_like(rhs_host).pin_memory()
+    rhs_dev, x_dev = torch.empty_like(rhs), torch.empty_like(rhs)
+    e2e_cycles = 0
+    ranks.barrier()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        rhs_dev.copy_(rhs_host, non_blocking=True)
+        x_dev.zero_()
+        _, it, _, _ = h.solve(rhs_dev, x_dev, tol=1e-10, maxit=args.maxit_vcycle)
+        x_host.copy_(x_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_cycles += it
+    e2e_s = ranks.max(time.perf_counter() - t0)
+    levels = h.num_levels
+    h.close()
+    if rank != 0:
+        ranks.close()
+        return
+    hbm_peak = measured_peak("hbm_gbs", 6800.0)
+    relax0 = [r for r in prof if r["kernel"] == "relax" and r["level"] == 0][0]
+    sweeps = 3 * 3                                            # V(2,1), three profiled cycles
+    per_sweep_s = relax0["ms"] / sweeps * 1e-3
+    byt = SWEEP_BYTES[("fp64", kind)] * N
+    gbs = byt / per_sweep_s / 1e9
+    out = {"metric": METRIC, "value": whole_job_rate(N * args.steps, ms * 1e-3, ranks), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generators, no datasets)",
+           "config": {"workload": args.workload, "description": spec["text"], "unknowns": N, "arith": args.arith,
+                      "levels": levels, "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "working set > L2 (FP64 level-0 stencil + vectors = %.0f MB)" % (N * 64 / 1e6)},
+           "roofline": {"bound": "hbm", "kernel": "k_p_gs<true> level 0 (four colour launches per sweep)",
+                        "achieved": round(gbs, 1), "peak": hbm_peak[0], "unit": "GB/s",
+                        "frac": round(gbs / hbm_peak[0], 4), "peak_source": hbm_peak[1], "traffic": None,
+                        "traffic_source": None, "alg_bytes_per_sweep": byt,
+                        "alg_bytes_per_point": SWEEP_BYTES[("fp64", kind)],
+                        "time_share": round(relax0["ms"] / sum(q["ms"] for q in prof), 3),
+                        "avg_sweep_us": round(per_sweep_s * 1e6, 2)},
+           "e2e": {"value": world * N * e2e_cycles / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
+                   "d2h_bytes_per_step": int(f.nbytes),
+                   "note": "bmg_solve (FP64 V(2,1)) to 1e-10 from a zero guess per step; rhs H2D from pinned "
+                           "memory, x D2H"},
+           "gpu_launches": int(launches), "clocks": clocks,
+           "time_to_tol": {"fp64": {"setup_ms": round(setup_ms, 1),
+                                    "vcycle": dict(solve_ms=round(t_solve * 1e3, 3), iterations=iters, relres=relres,
+                                                   converged=ok)}},
+           "profile_per_cycle_us": sorted(([r["level"], r["kernel"], round(r["launches"] / 3),
+                                            round(r["ms"] / 3 * 1e3, 1)] for r in prof), key=lambda e: -e[3])}
+    out["cpu_baseline"] = periodic_cpu_baseline(args, kind, planes, f, px, py) if not args.no_cpu and world == 1 \
+        else None
+    print(json.dumps(out))
+    ranks.close()
+
+
+def periodic_cpu_baseline(args, kind, planes, f, px, py):
+    """The periodic oracle on one host thread: setup, then one V(2,1) cycle +
+    residual norm on the full problem (a bounded sample)."""
+    _, times, _ = periodic_oracle_cycles(kind, planes, f, px, py, 1)
+    return {"value": f[1:-1, 1:-1].size / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"periodic oracle (numpy FP64, one thread): setup + 1 V(2,1) cycle with residual norm on the "
+                      f"full {args.workload} problem; cycle {times[0] * 1e3:.0f} ms"}
+
+
+def periodic_oracle_cycles(kind, planes, f, px, py, cycles):
+    from oracle import boxmg as bx
+    from oracle import periodic as pr
+    t0 = time.perf_counter()
+    levels = pr.setup(kind, planes, px, py)
+    setup_s = time.perf_counter() - t0
+    x = np.zeros_like(f)
+    times = []
+    for _ in range(cycles):
+        t0 = time.perf_counter()
+        pr.vcycle(levels, 0, x, f)
+        bx.norm(pr.residual(levels[0].planes, x, f, px, py))
+        times.append(time.perf_counter() - t0)
+    return setup_s, times, levels
+
+
 def run_rhs_batch(args, rank, local_rank, world):
     """Many right-hand sides of one operator: one batch sharing the hierarchy
     (bmg_batch_rhs) against the same hierarchy solving them one at a time."""
@@ -817,6 +944,14 @@ def run_reference(args, rank, world):
         setup_s, times, _ = oracle_batch_cycles(sample, steps + warm, threads=cores)
         text, unknowns = BATCHED["text"], m
         what = f"the first {len(sample)} problems of the batch ({m} unknowns)"
+    elif args.workload in PERIODIC:
+        spec = PERIODIC[args.workload]
+        kind, planes, f, px, py = w.periodic_problem(spec["n"], spec["axes"], seed_k=50, seed_f=51)
+        steps = min(args.steps, 2)
+        setup_s, times, _ = periodic_oracle_cycles(kind, planes, f, px, py, steps + warm)
+        cores = 1
+        text, unknowns = spec["text"], f[1:-1, 1:-1].size
+        what = f"the full {args.workload} problem (one thread: the periodic oracle has no row-band runner)"
     elif args.workload in RHS_BATCHES:
         RHS_BATCH = RHS_BATCHES[args.workload]
         n = RHS_BATCH["n"]
@@ -837,9 +972,9 @@ def run_reference(args, rank, world):
     times = times[warm:]
     tot = sum(times)
     value = unknowns * len(times) / tot
-    sample = (f"{len(times)} timed V(2,1) cycles (+ {warm} warm-up) of the oracle on {what}, colour passes and "
-              f"residuals over row bands on {cores} host threads (steps capped from {args.steps} to keep the CPU run "
-              f"to minutes); setup {setup_s:.1f} s")
+    spread = "one host thread" if cores == 1 else f"colour passes and residuals over row bands on {cores} host threads"
+    sample = (f"{len(times)} timed V(2,1) cycles (+ {warm} warm-up) of the oracle on {what}, {spread} (steps capped "
+              f"from {args.steps} to keep the CPU run to minutes); setup {setup_s:.1f} s")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times), "warmup": args.warmup,
            "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic (seeded generators, no datasets)", "impl": "reference",
@@ -855,7 +990,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(WORKLOADS) + ["batched256"] + sorted(RHS_BATCHES))
+                    choices=sorted(WORKLOADS) + ["batched256"] + sorted(RHS_BATCHES) + sorted(PERIODIC))
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--maxit-vcycle", type=int, default=200, help="cap of the stationary-cycle solve")
@@ -877,6 +1012,8 @@ def main():
         run_batched(args, rank, local_rank, world)
     elif args.workload in RHS_BATCHES:
         run_rhs_batch(args, rank, local_rank, world)
+    elif args.workload in PERIODIC:
+        run_periodic(args, rank, local_rank, world)
     else:
         run_ours(args, rank, local_rank, world)
 

@@ -725,9 +725,32 @@ int choose_pair_restrict(bmg_hierarchy* h) {
 
 // One iteration of the solve loop: a V-cycle (or a refinement step) followed by
 // the residual norm and the convergence test, all on the device.
+// bmg_profile's brackets for the periodic hierarchy's steps (the marks of step()).
+void per_mark_begin(void* ctx, int level, int kernel) {
+  bmg_hierarchy* h = (bmg_hierarchy*)ctx;
+  bmg_hierarchy::Mark m{level, kernel, 0, h->launches, nullptr, nullptr};
+  cudaEventCreate(&m.a);
+  cudaEventCreate(&m.b);
+  cudaEventRecord(m.a, h->ws);
+  h->prof->push_back(m);
+}
+
+void per_mark_end(void* ctx) {
+  bmg_hierarchy* h = (bmg_hierarchy*)ctx;
+  bmg_hierarchy::Mark& m = h->prof->back();
+  m.launches = h->launches - m.launches;
+  cudaEventRecord(m.b, h->ws);
+}
+
 void enqueue_iteration(bmg_hierarchy* h, const double* rhs, double* x) {
   if (h->per) {
-    per_enqueue_iteration(h->per, rhs, x, h->partials, h->ctl, h->ws);
+    PerMarks mk;
+    if (h->prof) {
+      mk.ctx = h;
+      mk.begin = per_mark_begin;
+      mk.end = per_mark_end;
+    }
+    per_enqueue_iteration(h->per, rhs, x, h->partials, h->ctl, h->ws, h->prof ? &mk : nullptr);
     return;
   }
   const int* done = &h->ctl->done;

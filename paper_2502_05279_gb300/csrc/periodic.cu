@@ -587,6 +587,16 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
 
 namespace {
 
+struct Bracket {
+  const PerMarks* m;
+  Bracket(const PerMarks* mk, int level, int kernel) : m(mk) {
+    if (m && m->begin) m->begin(m->ctx, level, kernel);
+  }
+  ~Bracket() {
+    if (m && m->end) m->end(m->ctx);
+  }
+};
+
 template <bool FU>
 void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, cudaStream_t s) {
   // colour order: 9-point (odd,odd), (even,odd), (odd,even), (even,even); 5-point red then black
@@ -617,23 +627,37 @@ int per_residual(const PerLevel& L, const double* x, const double* f, double* r,
 }
 
 template <bool FU>
-void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, cudaStream_t s) {
+void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, cudaStream_t s,
+                const PerMarks* mk) {
   PerLevel& L = P->lv[l];
   if (l + 1 == (int)P->lv.size()) {
+    Bracket b(mk, l, BMG_K_COARSE);
     k_p_coarse_solve<<<1, 1, 0, s>>>(L.g, P->L, f, x, done);
     count_launch();
     return;
   }
   PerLevel& C = P->lv[l + 1];
-  for (int k = 0; k < P->nu1; ++k) per_sweep<FU>(L, f, x, done, s);
-  per_residual<FU>(L, x, f, L.r, nullptr, done, s);
-  k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, done);
-  count_launch();
-  cudaMemsetAsync(C.x, 0, C.g.ps() * sizeof(double), s);
-  per_vcycle<FU>(P, l + 1, C.x, C.f, done, s);
-  k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, x, done);
-  count_launch();
-  for (int k = 0; k < P->nu2; ++k) per_sweep<FU>(L, f, x, done, s);
+  for (int k = 0; k < P->nu1; ++k) {
+    Bracket b(mk, l, BMG_K_RELAX);
+    per_sweep<FU>(L, f, x, done, s);
+  }
+  {
+    Bracket b(mk, l, BMG_K_RESID_RESTRICT);
+    per_residual<FU>(L, x, f, L.r, nullptr, done, s);
+    k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, done);
+    count_launch();
+    cudaMemsetAsync(C.x, 0, C.g.ps() * sizeof(double), s);
+  }
+  per_vcycle<FU>(P, l + 1, C.x, C.f, done, s, mk);
+  {
+    Bracket b(mk, l, BMG_K_INTERP);
+    k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, x, done);
+    count_launch();
+  }
+  for (int k = 0; k < P->nu2; ++k) {
+    Bracket b(mk, l, BMG_K_RELAX);
+    per_sweep<FU>(L, f, x, done, s);
+  }
 }
 
 }  // namespace
@@ -644,16 +668,20 @@ void per_enqueue_initial(PerHier* P, const double* rhs, double* x, double* parti
   launch_norm_finalize(partials, G, ctl, 0, nullptr, s);
 }
 
-void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s) {
+void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s,
+                           const PerMarks* mk) {
   const int* done = &ctl->done;
   int G;
-  if (P->fused) {
-    per_vcycle<true>(P, 0, x, rhs, done, s);
-    G = per_residual<true>(P->lv[0], x, rhs, nullptr, partials, done, s);
-  } else {
-    per_vcycle<false>(P, 0, x, rhs, done, s);
-    G = per_residual<false>(P->lv[0], x, rhs, nullptr, partials, done, s);
+  if (P->fused)
+    per_vcycle<true>(P, 0, x, rhs, done, s, mk);
+  else
+    per_vcycle<false>(P, 0, x, rhs, done, s, mk);
+  {
+    Bracket b(mk, 0, BMG_K_NORM);
+    G = P->fused ? per_residual<true>(P->lv[0], x, rhs, nullptr, partials, done, s)
+                 : per_residual<false>(P->lv[0], x, rhs, nullptr, partials, done, s);
   }
+  Bracket b(mk, 0, BMG_K_FINALIZE);
   launch_norm_finalize(partials, G, ctl, 1, nullptr, s);
 }
 

@@ -29,11 +29,20 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
               int nu2, cudaStream_t s);
 void per_free(PerHier* P);
 
+// Profiling brackets around each step's launches (begin: level and BMG_K_*
+// kind of the step; end: after its last launch); NULL members are skipped.
+struct PerMarks {
+  void* ctx = nullptr;
+  void (*begin)(void* ctx, int level, int kernel) = nullptr;
+  void (*end)(void* ctx) = nullptr;
+};
+
 // The solve loop's device work: the initial residual norm (phase 0 of the
 // control block), and one iteration = V-cycle + residual norm + convergence
 // test (phase 1).  partials holds at least min(ny, 1024) doubles.
 void per_enqueue_initial(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s);
-void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s);
+void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s,
+                           const PerMarks* marks = nullptr);
 
 int per_num_levels(const PerHier* P);
 int per_level_shape(const PerHier* P, int l, int* nx, int* ny);
