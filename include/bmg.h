@@ -367,6 +367,14 @@ typedef struct bmg_mlp bmg_mlp;
 int bmg_mlp_create(bmg_mlp** out);
 int bmg_mlp_set_params(bmg_mlp* m, const float* host, int count);
 int bmg_mlp_get_params(const bmg_mlp* m, float* host, int count);
+
+/* The optimizer state of bmg_mlp_adam, for checkpoints: the first and second
+ * moment estimates (count = MLP_PARAMS floats each, host) and the step
+ * count.  get copies them out; set restores them (bmg_mlp_set_params resets
+ * them to zero and the step to 0, so a resumed run sets the parameters first,
+ * then the state).  EINVAL for NULL pointers, a wrong count or a negative step. */
+int bmg_mlp_get_adam(const bmg_mlp* m, float* moment1, float* moment2, int* step, int count);
+int bmg_mlp_set_adam(bmg_mlp* m, const float* moment1, const float* moment2, int step, int count);
 /* One loss and gradient evaluation on one problem (FP32 network, FP64 weights
  * and loss): coef 5 planes (n+2)^2 (ghost couplings zero), vecs K planes
  * (n+2)^2 (device), eref K host values (NULL: loss normalised by the weights of

@@ -106,6 +106,8 @@ _sig = {
     "bmg_mlp_create": (I, [ctypes.POINTER(P)]),
     "bmg_mlp_set_params": (I, [P, P, I]),
     "bmg_mlp_get_params": (I, [P, P, I]),
+    "bmg_mlp_get_adam": (I, [P, P, P, ctypes.POINTER(I), I]),
+    "bmg_mlp_set_adam": (I, [P, P, P, I, I]),
     "bmg_mlp_loss_grad": (I, [P, I, P, I, P, P, ctypes.POINTER(D), P, P, P]),
     "bmg_mlp_twogrid": (I, [P, I, I, P, I, P, P, P, ctypes.POINTER(D), P, P]),
     "bmg_mlp_adam": (I, [P, ctypes.c_float, P]),
@@ -401,6 +403,22 @@ class Mlp:
         a = np.empty(MLP_PARAMS, dtype=np.float32)
         _check(lib.bmg_mlp_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p), MLP_PARAMS))
         return a
+
+    def adam_state(self):
+        """(first moments, second moments, step) of the optimizer (numpy float32)."""
+        import numpy as np
+        m1, m2, st = np.empty(MLP_PARAMS, np.float32), np.empty(MLP_PARAMS, np.float32), ctypes.c_int(0)
+        _check(lib.bmg_mlp_get_adam(self._h, m1.ctypes.data_as(ctypes.c_void_p), m2.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.byref(st), MLP_PARAMS))
+        return m1, m2, st.value
+
+    def set_adam_state(self, m1, m2, step: int):
+        import numpy as np
+        a = np.ascontiguousarray(m1, dtype=np.float32)
+        b = np.ascontiguousarray(m2, dtype=np.float32)
+        assert a.size == MLP_PARAMS and b.size == MLP_PARAMS
+        _check(lib.bmg_mlp_set_adam(self._h, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                                    int(step), MLP_PARAMS))
 
     def loss_grad(self, coef, vecs, eref=None, want_grad=True):
         """(loss, gradient (numpy float32) or None, eref) on one problem; vecs: (K, n+2, n+2) CUDA float64."""

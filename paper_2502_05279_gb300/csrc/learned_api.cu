@@ -150,6 +150,24 @@ int bmg_mlp_get_params(const bmg_mlp* m, float* host, int count) {
   return BMG_OK;
 }
 
+int bmg_mlp_get_adam(const bmg_mlp* m, float* moment1, float* moment2, int* step, int count) {
+  if (!m || !moment1 || !moment2 || !step || count != MLP_PARAMS)
+    return set_error(BMG_EINVAL, "bmg_mlp_get_adam: need two arrays of %d floats and a step", MLP_PARAMS);
+  CK(cudaMemcpy(moment1, m->m, sizeof(float) * MLP_PARAMS, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(moment2, m->v, sizeof(float) * MLP_PARAMS, cudaMemcpyDeviceToHost));
+  *step = m->step;
+  return BMG_OK;
+}
+
+int bmg_mlp_set_adam(bmg_mlp* m, const float* moment1, const float* moment2, int step, int count) {
+  if (!m || !moment1 || !moment2 || step < 0 || count != MLP_PARAMS)
+    return set_error(BMG_EINVAL, "bmg_mlp_set_adam: need two arrays of %d floats and a step >= 0", MLP_PARAMS);
+  CK(cudaMemcpy(m->m, moment1, sizeof(float) * MLP_PARAMS, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->v, moment2, sizeof(float) * MLP_PARAMS, cudaMemcpyHostToDevice));
+  m->step = step;
+  return BMG_OK;
+}
+
 int bmg_mlp_loss_grad(bmg_mlp* m, int n, const double* coef, int K, const double* vecs, const double* eref,
                       double* loss, float* grad, double* eref_out, void* stream) {
   if (!m || !level_size_ok(n) || !coef || K < 1 || !vecs || !loss)

@@ -9,9 +9,12 @@ per problem.  The loss is the two-grid one: on 31 x 31 Dirichlet crops of the
 problems (tile-aligned offsets), the A-energy of the two-grid error
 propagation of V(2,1) applied to uniform[-1,1) error vectors, relative to
 Dendy's weights (loss 1 = Dendy).  Checkpoints are .npz files holding the
-parameter vector, the Adam step count and the loss history.
+parameter vector, the Adam moments and step count, the epochs run and the loss
+history; --resume continues from one (the next epoch draws the permutation it
+would have drawn in an uninterrupted run).
 
     python -m paper_2502_05279_gb300.learned_training --problems 2000 --epochs 8 --out model.npz
+    python -m paper_2502_05279_gb300.learned_training --resume model.npz --epochs 4 --out model2.npz
 """
 from __future__ import annotations
 
@@ -55,12 +58,31 @@ def crops_on_device(n_problems: int, crops_per_problem: int = 1, first_seed: int
     return coefs, vecs
 
 
+def save_checkpoint(path: str, mlp, history, epochs_done: int, problems: int) -> None:
+    """Parameters, Adam moments and step, epochs run and loss history."""
+    m1, m2, step = mlp.adam_state()
+    np.savez(path, params=mlp.params(), adam_m=m1, adam_v=m2, adam_step=step, epochs_done=epochs_done,
+             loss_history=np.asarray(history, dtype=np.float64), problems=problems)
+
+
+def load_checkpoint(path: str):
+    """(network with its parameters and Adam state restored, loss history,
+    epochs run)."""
+    z = np.load(path)
+    mlp = B.Mlp(z["params"])
+    mlp.set_adam_state(z["adam_m"], z["adam_v"], int(z["adam_step"]))
+    return mlp, list(z["loss_history"]), int(z["epochs_done"])
+
+
 def train(n_problems: int = 2000, epochs: int = 8, batch: int = 152, lr: float = 2e-2, seed: int = 2024,
-          first_seed: int = 1000, crops_per_problem: int = 1, log=print):
+          first_seed: int = 1000, crops_per_problem: int = 1, log=print, mlp=None, first_epoch: int = 0):
     """Adam on the two-grid loss over mini-batches of crops (a SplitMix64
-    permutation per epoch).  Returns (network, mean loss per epoch, Dendy's
-    energies, seconds spent in training steps)."""
-    mlp = B.Mlp(init_params(seed))
+    permutation per epoch, epoch e drawing stream seed + 1 + e).  mlp: a
+    network to continue training (from load_checkpoint) and first_epoch its
+    epochs run; else a fresh network.  Returns (network, mean loss per epoch,
+    Dendy's energies, seconds spent in training steps)."""
+    if mlp is None:
+        mlp = B.Mlp(init_params(seed))
     t0 = time.perf_counter()
     coefs, vecs = crops_on_device(n_problems, crops_per_problem, first_seed)
     _, _, eref = mlp.twogrid(coefs, vecs)
@@ -69,7 +91,7 @@ def train(n_problems: int = 2000, epochs: int = 8, batch: int = 152, lr: float =
     C = coefs.shape[0]
     history = []
     train_s = 0.0
-    for ep in range(epochs):
+    for ep in range(first_epoch, first_epoch + epochs):
         order = torch.from_numpy(np.argsort(w.uniform01(seed + 1 + ep, C), kind="stable")).cuda()
         t0 = time.perf_counter()
         losses = []
@@ -132,10 +154,12 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-2)
     ap.add_argument("--eval-n", type=int, default=4095)
     ap.add_argument("--out", default="learned_model.npz")
+    ap.add_argument("--resume", default=None, help="checkpoint to continue from")
     args = ap.parse_args()
-    mlp, hist, _, train_s = train(args.problems, args.epochs, args.batch, args.lr)
-    np.savez(args.out, params=mlp.params(), loss_history=np.array(hist), problems=args.problems, epochs=args.epochs)
-    print(json.dumps({"train_loss": hist, "train_s": train_s, "eval": evaluate(mlp, args.eval_n)}))
+    mlp, past, done = (None, [], 0) if args.resume is None else load_checkpoint(args.resume)
+    mlp, hist, _, train_s = train(args.problems, args.epochs, args.batch, args.lr, mlp=mlp, first_epoch=done)
+    save_checkpoint(args.out, mlp, past + hist, done + args.epochs, args.problems)
+    print(json.dumps({"train_loss": past + hist, "train_s": train_s, "eval": evaluate(mlp, args.eval_n)}))
 
 
 if __name__ == "__main__":

@@ -207,6 +207,30 @@ def test_twogrid_rejects_bad_arguments(bmg):
     m.close()
 
 
+def test_checkpoint_resume_continues_bit_for_bit(bmg, tmp_path):
+    """A run interrupted after one epoch and resumed from its checkpoint
+    (parameters, Adam moments and step, epochs run) ends with the parameters of
+    the uninterrupted two-epoch run, bit for bit."""
+    from paper_2502_05279_gb300 import learned_training as lt
+    quiet = dict(n_problems=24, batch=8, log=lambda *_: None)
+    full, hist_full, _, _ = lt.train(epochs=2, **quiet)
+    part, hist_part, _, _ = lt.train(epochs=1, **quiet)
+    ck = str(tmp_path / "ck.npz")
+    lt.save_checkpoint(ck, part, hist_part, 1, 24)
+    part.close()
+    back, past, done = lt.load_checkpoint(ck)
+    assert done == 1 and past == hist_part
+    m1, m2, step = back.adam_state()
+    assert step == 3 and np.any(m1 != 0) and np.all(m2 >= 0)
+    back, hist_rest, _, _ = lt.train(epochs=1, mlp=back, first_epoch=done, **quiet)
+    assert np.array_equal(back.params(), full.params())
+    assert past + hist_rest == hist_full
+    with pytest.raises(bmg.BmgError):
+        back.set_adam_state(m1, m2, -1)
+    back.close()
+    full.close()
+
+
 @pytest.mark.slow
 def test_learned_interpolation_gain_at_4095(bmg):
     """What the trained network gains over Dendy's interpolation.  Train on a
