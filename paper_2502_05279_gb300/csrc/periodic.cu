@@ -344,6 +344,38 @@ __global__ void k_p_gs(PGeom g, const double* __restrict__ st, const double* __r
   x[p] = rmul(s, st[5 * g.ps() + p]);
 }
 
+// Half of a 9-point sweep: one CTA per row j of parity pj, its odd-i points
+// (colour (1, pj)) before its even-i points (colour (0, pj)).  The four-colour
+// order (odd,odd), (even,odd), (odd,even), (even,even) is row-parity major, so
+// the launch for pj = 1 followed by the one for pj = 0 is one sweep, point for
+// point the colour-by-colour one: rows of one parity do not couple (N is even
+// on a periodic axis), and a whole row, seam included, belongs to one CTA.
+// The row goes in chunks of 2 x 256 columns, the odd points of chunk c + 1
+// before the even points of chunk c (an even point reads the new odd values
+// beside it, an odd point the old even ones), so a chunk's stencil is read by
+// both colours while it is still in the caches.
+template <bool FU>
+__global__ void __launch_bounds__(256) k_p_gs_rows(PGeom g, const double* __restrict__ st,
+                                                   const double* __restrict__ f, double* x, int pj, const int* done) {
+  if (dev::stopped(done)) return;
+  const int j = 2 * (int)blockIdx.x + (pj ? 1 : 2);
+  if (j > g.ny) return;
+  const size_t row = (size_t)j * (g.nx + 2), dp = 5 * g.ps();
+  constexpr int CW = 512;                                   // chunk width (columns)
+  const int chunks = (g.nx + CW - 1) / CW;
+  auto point = [&](int i) {
+    if (i > g.nx) return;
+    const size_t p = row + i;
+    x[p] = rmul(prow<true, false, FU>(st, x, g, i, j, f[p]), st[dp + p]);
+  };
+  point(1 + 2 * (int)threadIdx.x);                          // odd points of chunk 0
+  for (int c = 0; c < chunks; ++c) {
+    if (c + 1 < chunks) point((c + 1) * CW + 1 + 2 * (int)threadIdx.x);
+    __syncthreads();
+    point(c * CW + 2 + 2 * (int)threadIdx.x);               // even points of chunk c
+  }
+}
+
 // r = f - A x (when r != NULL) and the partial sums of r^2 in the canonical
 // reduction order (block b of G = min(ny, 1024): rows 1 + b, 1 + b + G, ...;
 // thread t: columns 1 + t, 1 + t + 256, ...; then the halving tree).
@@ -599,17 +631,22 @@ struct Bracket {
 
 template <bool FU>
 void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, cudaStream_t s) {
-  // colour order: 9-point (odd,odd), (even,odd), (odd,even), (even,even); 5-point red then black
-  static const int c9[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
+  // 9-point: the two row-parity halves; 5-point (level 0 only): one launch per
+  // colour, red ((odd,odd), (even,even)) then black
   static const int c5[4][2] = {{1, 1}, {0, 0}, {0, 1}, {1, 0}};
   const bool nine = L.kind == 9;
+  if (nine) {   // two row-parity halves
+    for (int pj = 1; pj >= 0; --pj) {
+      const int rows = pj ? (L.g.ny + 1) / 2 : L.g.ny / 2;
+      k_p_gs_rows<FU><<<rows, 256, 0, s>>>(L.g, L.st, f, x, pj, done);
+      count_launch();
+    }
+    return;
+  }
   for (int k = 0; k < 4; ++k) {
-    const int pi = nine ? c9[k][0] : c5[k][0], pj = nine ? c9[k][1] : c5[k][1];
+    const int pi = c5[k][0], pj = c5[k][1];
     const int cx = pi ? (L.g.nx + 1) / 2 : L.g.nx / 2, cy = pj ? (L.g.ny + 1) / 2 : L.g.ny / 2;
-    if (nine)
-      k_p_gs<true, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
-    else
-      k_p_gs<false, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
+    k_p_gs<false, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
     count_launch();
   }
 }

@@ -8,7 +8,8 @@
 // (N_y + 2) x (N_x + 2) with zero ghost lines: the kernels wrap indices on
 // the periodic axes instead of reading ghost copies.  The cycle is the FP64
 // V(nu1, nu2) of the Dirichlet hierarchy (the same formulas, term orders and
-// arithmetic modes) with one launch per colour of each Gauss-Seidel sweep.
+// arithmetic modes); a 9-point sweep is two row-parity launches, a 5-point one
+// (level 0) one launch per colour.
 #pragma once
 
 #include <cuda_runtime.h>
