@@ -6,7 +6,7 @@ There is no CPU fallback: importing the binding fails when the library is
 missing or cannot load.
 """
 from ._lib import (  # noqa: F401
-    BMG_BF16_IR, BMG_EINVAL, BMG_ESINGULAR, BMG_FP32_IR, BMG_FP64, BMG_PERIODIC_X, BMG_PERIODIC_Y, Batch, BmgError,
+    BMG_BF16_IR, BMG_EINVAL, BMG_ENOMEM, BMG_ESINGULAR, BMG_FP32_IR, BMG_FP64, BMG_PERIODIC_X, BMG_PERIODIC_Y, Batch, BmgError,
     Hierarchy, coarse_factor, coarse_solve, dendy_interp,
     interp_correct, learned_interp, fill_uniform, lib, library_path, measure_fp64_rate, Mlp, mlp_features, rap, relax,
     relax_line,

@@ -17,6 +17,8 @@
 #include "learned.h"
 #include "periodic.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace bmg {
 
 static thread_local char g_err[512] = "";
@@ -36,6 +38,47 @@ int set_error(int code, const char* fmt, ...) {
   vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
   return code;
+}
+
+// A named NVTX range around an entry point's host work (tools that record NVTX
+// show the library's setup, solve and timing calls as ranges; without such a
+// tool the calls cost a few nanoseconds).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
+namespace {
+bool alloc_fault() {
+  static std::mutex mu;
+  static std::string seen;
+  static long count = 0;
+  const char* e = getenv("BMG_FAIL_ALLOC");
+  const std::string v = e ? e : "";
+  std::lock_guard<std::mutex> guard(mu);
+  if (v != seen) {
+    seen = v;
+    count = 0;
+  }
+  const long k = v.empty() ? 0 : strtol(v.c_str(), nullptr, 10);
+  return k > 0 && ++count == k;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (alloc_fault()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc(void** p, size_t bytes) {
+  if (alloc_fault()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
 }
 
 // BMG_ETIMEOUT when a one-pass sweep gave up on its bulk copies since the last check.
@@ -189,7 +232,7 @@ template <typename T>
 int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return BMG_OK;
-  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  CK(dev_malloc((void**)p, count * sizeof(T)));
   return BMG_OK;
 }
 
@@ -595,7 +638,7 @@ int build_tail(bmg_hierarchy* h, int lmin) {
       d.lv[k] = LevelDesc<float, float>{view32(L), L.ci32, L.x32, L.f32, C ? C->x32 : nullptr,
                                         C ? C->f32 : nullptr, nullptr, h->Lfac, h->work};
   }
-  CK(cudaMalloc(&h->d_tail, sizeof(d)));
+  CK(dev_malloc((void**)&h->d_tail, sizeof(d)));
   CK(cudaMemcpy(h->d_tail, &d, sizeof(d), cudaMemcpyHostToDevice));
   h->tail_l = lt;
   return BMG_OK;
@@ -839,7 +882,7 @@ int ensure_ctl(bmg_hierarchy* h, int maxit) {
   if (h->ctl) cudaFree(h->ctl);
   h->ctl = nullptr;
   int cap = maxit < 64 ? 64 : maxit;
-  CK(cudaMalloc((void**)&h->ctl, sizeof(Ctl) + sizeof(double) * (size_t)(cap + 1)));
+  CK(dev_malloc((void**)&h->ctl, sizeof(Ctl) + sizeof(double) * (size_t)(cap + 1)));
   h->maxit_cap = cap;
   if (h->gexec) {   // the graph holds the old control block address
     cudaGraphExecDestroy(h->gexec);
@@ -989,10 +1032,15 @@ namespace {
 int measure_factor(bmg_hierarchy* h, double* out) {
   size_t ps = plane_size(h->n);
   double *x = nullptr, *f = nullptr;
-  CK(cudaMalloc((void**)&x, ps * sizeof(double)));
-  CK(cudaMalloc((void**)&f, ps * sizeof(double)));
-  CK(cudaMemset(x, 0, ps * sizeof(double)));
-  CK(cudaMemset(f, 0, ps * sizeof(double)));
+  int rc0 = cuda_check(dev_malloc((void**)&x, ps * sizeof(double)), "factor measurement");
+  if (!rc0) rc0 = cuda_check(dev_malloc((void**)&f, ps * sizeof(double)), "factor measurement");
+  if (!rc0) rc0 = cuda_check(cudaMemset(x, 0, ps * sizeof(double)), "factor measurement");
+  if (!rc0) rc0 = cuda_check(cudaMemset(f, 0, ps * sizeof(double)), "factor measurement");
+  if (rc0) {
+    cudaFree(x);
+    cudaFree(f);
+    return rc0;
+  }
   launch_uniform_pm1(h->n, 0x5EEDull, x, nullptr);
   CK(cudaDeviceSynchronize());
   int it = 0;
@@ -1066,7 +1114,7 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
   CounterScope cs(&h->launches);
   int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
-  if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
+  if (!rc) rc = cuda_check(host_malloc((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = dalloc(&h->partials, 2 * (size_t)norm_partials_max());
   if (!rc) rc = per_setup(&h->per, A->kind, A->coef, nx, ny, periodic, h->arith == BMG_ARITH_FUSED, h->nu1, h->nu2,
@@ -1082,6 +1130,7 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
 }  // namespace
 
 int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hierarchy** out) {
+  Range nvtx("bmg_setup");
   if (!out) return set_error(BMG_EINVAL, "bmg_setup: out is NULL");
   *out = nullptr;
   if (!A || !A->coef) return set_error(BMG_EINVAL, "bmg_setup: stencil is NULL");
@@ -1140,7 +1189,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   CounterScope cs(&h->launches);
   int rc = cuda_check(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking), "stream");
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming), "event");
-  if (!rc) rc = cuda_check(cudaMallocHost((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
+  if (!rc) rc = cuda_check(host_malloc((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = setup_impl(h, A, h->n, o);
   const bool line = h->smoother == BMG_SMOOTHER_LINE;
@@ -1233,6 +1282,7 @@ static int reset_ctl(bmg_hierarchy* h, double tol, int maxit) {
 }
 
 int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, double* ms) {
+  Range nvtx("bmg_time_cycles");
   if (!h || !rhs || !x || !ms || cycles < 1) return set_error(BMG_EINVAL, "bmg_time_cycles: bad argument");
   CounterScope cs(&h->launches);
   int rc;
@@ -1268,6 +1318,7 @@ int bmg_time_cycles(bmg_hierarchy* h, const double* rhs, double* x, int cycles, 
 }
 
 int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_prof_row* rows, int cap) {
+  Range nvtx("bmg_profile");
   if (!h || !rhs || !x || cycles < 1) return set_error(BMG_EINVAL, "bmg_profile: bad argument");
   CounterScope cs(&h->launches);
   int rc;
@@ -1304,6 +1355,7 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
 }
 
 int bmg_solve(bmg_hierarchy* h, const double* rhs, double* x, double tol, int maxit, int* iters, double* relres) {
+  Range nvtx("bmg_solve");
   if (!h || !rhs || !x) return set_error(BMG_EINVAL, "bmg_solve: NULL argument");
   if (maxit < 0 || !(tol >= 0.0)) return set_error(BMG_EINVAL, "bmg_solve: bad tol or maxit");
   CounterScope cs(&h->launches);
@@ -1874,7 +1926,7 @@ int batch_ensure_ctl(bmg_batch* B, int maxit) {
   int cap = maxit < 64 ? 64 : maxit;
   size_t stride = (sizeof(Ctl) + sizeof(double) * (size_t)(cap + 1) + 255) / 256 * 256;
   char* c = nullptr;
-  CK(cudaMalloc((void**)&c, stride * B->nprob));
+  CK(dev_malloc((void**)&c, stride * B->nprob));
   if (B->ctls) cudaFree(B->ctls);
   B->ctls = c;
   B->ctl_stride = stride;
@@ -2009,7 +2061,7 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
       d[k].done = nullptr;
     }
     LevelDesc<T, S>* dd = nullptr;
-    rc = cuda_check(cudaMalloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count), "tuning descriptors");
+    rc = cuda_check(dev_malloc((void**)&dd, sizeof(LevelDesc<T, S>) * g.count), "tuning descriptors");
     if (!rc)
       rc = cuda_check(cudaMemcpyAsync(dd, d.data(), sizeof(LevelDesc<T, S>) * g.count, cudaMemcpyHostToDevice, B->ws),
                       "tuning descriptors");
@@ -2274,17 +2326,17 @@ int batch_finish(bmg_batch* B, int rc) {
     for (auto& g : st) {
       if (rc || !g.count) continue;
       g.cl = g.storage == 0 ? rows_cluster<double>(g.n) : rows_cluster<float>(g.n);
-      rc = cuda_check(cudaMalloc(&g.d, g.elem * g.count), "batched tables");
+      rc = cuda_check(dev_malloc((void**)&g.d, g.elem * g.count), "batched tables");
     }
   for (size_t b = 0; !rc && b < B->tail_count.size(); ++b)
     if (B->tail_count[b])
-      rc = cuda_check(cudaMalloc(&B->tail_dev[b], (B->precision == BMG_FP64 ? sizeof(TailDesc<double>)
+      rc = cuda_check(dev_malloc((void**)&B->tail_dev[b], (B->precision == BMG_FP64 ? sizeof(TailDesc<double>)
                                                                              : sizeof(TailDesc<float>)) *
                                                       B->tail_count[b]),
                       "batched tails");
-  if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_top, sizeof(TopDesc) * nprob), "batched tables");
-  if (!rc) rc = cuda_check(cudaMalloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
-  if (!rc) rc = cuda_check(cudaMallocHost((void**)&B->h_alldone, sizeof(int)), "pinned");
+  if (!rc) rc = cuda_check(dev_malloc((void**)&B->d_top, sizeof(TopDesc) * nprob), "batched tables");
+  if (!rc) rc = cuda_check(dev_malloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
+  if (!rc) rc = cuda_check(host_malloc((void**)&B->h_alldone, sizeof(int)), "pinned");
   if (!rc) rc = batch_ensure_ctl(B, 64);
   if (!rc && B->smoother >= BMG_SMOOTHER_TILE) rc = force_batch_onepass(B);
   if (!rc && B->use_graph) rc = autotune_batch(B);
@@ -2298,6 +2350,7 @@ int batch_finish(bmg_batch* B, int rc) {
 extern "C" {
 
 int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_opts* o, bmg_batch** out) {
+  Range nvtx("bmg_setup_batched");
   if (!out) return set_error(BMG_EINVAL, "bmg_setup_batched: out is NULL");
   *out = nullptr;
   if (nprob < 1 || !A || !n) return set_error(BMG_EINVAL, "bmg_setup_batched: bad argument");
@@ -2331,6 +2384,7 @@ int bmg_setup_batched(int nprob, const bmg_stencil* A, const int* n, const bmg_o
 }
 
 int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch** out) {
+  Range nvtx("bmg_batch_rhs");
   if (!out) return set_error(BMG_EINVAL, "bmg_batch_rhs: out is NULL");
   *out = nullptr;
   if (!h0 || k < 1) return set_error(BMG_EINVAL, "bmg_batch_rhs: bad argument");
@@ -2371,6 +2425,7 @@ int bmg_batch_rhs(const bmg_hierarchy* h0, int k, const bmg_opts* o, bmg_batch**
 
 int bmg_solve_batched(bmg_batch* B, const double* const* rhs, double* const* x, double tol, int maxit, int* iters,
                       double* relres) {
+  Range nvtx("bmg_solve_batched");
   if (!B || !rhs || !x) return set_error(BMG_EINVAL, "bmg_solve_batched: NULL argument");
   if (maxit < 0 || !(tol >= 0.0)) return set_error(BMG_EINVAL, "bmg_solve_batched: bad tol or maxit");
   for (int p = 0; p < B->nprob; ++p)

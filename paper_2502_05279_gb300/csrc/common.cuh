@@ -139,4 +139,10 @@ namespace bmg {
 void count_launch();
 int set_error(int code, const char* fmt, ...);
 int cuda_check(cudaError_t e, const char* what);
+// cudaMalloc / cudaMallocHost of the setup calls, with the test hook for
+// out-of-memory paths: when the environment variable BMG_FAIL_ALLOC holds
+// k > 0, the k-th such allocation (counted from when the variable last changed)
+// fails with cudaErrorMemoryAllocation without reaching the driver.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t host_malloc(void** p, size_t bytes);
 }  // namespace bmg

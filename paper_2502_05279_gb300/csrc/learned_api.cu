@@ -48,7 +48,7 @@ void free_ws(bmg_mlp* m) {
 
 template <typename T>
 int alloc0(T** p, size_t count) {
-  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  CK(dev_malloc((void**)p, count * sizeof(T)));
   CK(cudaMemset(*p, 0, count * sizeof(T)));
   return BMG_OK;
 }

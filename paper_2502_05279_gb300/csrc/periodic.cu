@@ -521,7 +521,7 @@ int per_levels_for(int nx, int ny, int periodic) {
 
 static int palloc(double** p, size_t count, cudaStream_t s) {
   *p = nullptr;
-  if (cudaMalloc((void**)p, count * sizeof(double)) != cudaSuccess) {
+  if (dev_malloc((void**)p, count * sizeof(double)) != cudaSuccess) {
     *p = nullptr;
     return set_error(BMG_ENOMEM, "periodic setup: device allocation of %zu doubles failed", count);
   }
@@ -578,7 +578,7 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
   const int m = gc.nx * gc.ny;
   if (!rc) rc = palloc(&P->L, (size_t)m * m, s);
   if (!rc) rc = palloc(&P->work, (size_t)m * m, s);
-  if (!rc && cudaMalloc((void**)&P->err, sizeof(int)) != cudaSuccess) rc = set_error(BMG_ENOMEM, "periodic setup");
+  if (!rc && dev_malloc((void**)&P->err, sizeof(int)) != cudaSuccess) rc = set_error(BMG_ENOMEM, "periodic setup");
   if (!rc) rc = cuda_check(cudaMemsetAsync(P->err, 0, sizeof(int), s), "periodic setup: memset");
   if (rc) {
     per_free(P);
