@@ -127,6 +127,7 @@ struct Ctl {
   double scale_applied;  // the scale the current FP32 residual carries
   // flexible CG scalars
   double zq, pq, pr, pq_prev;
+  double beta;           // -zq / pq_prev of the current step, formed once by the zq reduction
   int first;             // 1 until the first direction is formed
   int pad2;
   double hist[1];        // [maxit + 1] residual norms (allocated past the struct)

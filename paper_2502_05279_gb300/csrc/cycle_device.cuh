@@ -1409,6 +1409,10 @@ __device__ __forceinline__ void coarse_solve_body(int n, const double* __restric
 // double, or when s is not such a power of two, does it take the FP64 multiply.
 // Both routes give the same bits; the bit route spares the FP64 pipe two
 // operations.
+// The general route of pow2_times_widened, kept out of line so that the common
+// route compiles to integer operations only (no FP64 work predicated in).
+static __device__ __noinline__ double pow2_times_widened_slow(double s, float e) { return rmul(s, (double)e); }
+
 __device__ __forceinline__ double pow2_times_widened(double s, float e) {
   const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
   const int es = (int)((sb >> 52) & 0x7ff);
@@ -1422,7 +1426,7 @@ __device__ __forceinline__ double pow2_times_widened(double s, float e) {
       return __longlong_as_double(
           (long long)(sign | ((unsigned long long)ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
   }
-  return rmul(s, (double)e);
+  return pow2_times_widened_slow(s, e);
 }
 
 __device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, const float* __restrict__ e32,

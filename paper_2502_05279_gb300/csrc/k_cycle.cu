@@ -724,7 +724,10 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __res
   if (ctl->done) return;
   if (which == 0) {
     double v = reduce_partials(partials, np);
-    if (threadIdx.x == 0) ctl->zq = v;
+    if (threadIdx.x == 0) {
+      ctl->zq = v;
+      if (!ctl->first) ctl->beta = -rdiv(v, ctl->pq_prev);   // one division per step, not per point
+    }
   } else {
     double a = reduce_partials(partials, np);
     __syncthreads();
@@ -746,12 +749,10 @@ __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float
   if (i > n || j > n) return;
   size_t p = (size_t)j * (n + 2) + i;
   double zp = zval(z, z32, ctl->scale_applied, p);
-  if (ctl->first) {
+  if (ctl->first)
     pv[p] = zp;
-  } else {
-    double beta = -rdiv(ctl->zq, ctl->pq_prev);
-    pv[p] = madd<FU>(zp, beta, pv[p]);
-  }
+  else
+    pv[p] = madd<FU>(zp, ctl->beta, pv[p]);
 }
 
 // q = A p (row sum a_O p + a_W p_W + ... in canonical order), partial p.q and p.r
