@@ -70,6 +70,14 @@
  * returns once its results are ready, unless stated otherwise.  No call takes
  * ownership of a caller pointer.
  *
+ * Environment.  BMG_TUNE_CACHE=<file>: the autotuner appends each decision it
+ * times (Gauss-Seidel kernel and shape per level or batched stage, the fused
+ * two-sweep pass) to the file, keyed by the device model, and reuses the
+ * decisions it finds there instead of timing again; every candidate computes
+ * the same bits, and records with out-of-range values are ignored.
+ * BMG_FAIL_ALLOC=k (testing): the k-th device or pinned allocation of the setup
+ * calls, counted from when the value last changed, fails as BMG_ENOMEM.
+ *
  * Errors.  Every int-returning call returns BMG_OK (0) or a negative code;
  * bmg_strerror() names it and bmg_last_error() gives the detail of the most
  * recent failure on the calling thread.  No exception crosses the ABI.  A

@@ -423,6 +423,109 @@ int time_call(cudaStream_t s, F&& fn, float* ms) {
   return BMG_OK;
 }
 
+// ---- the autotuner's record file ----------------------------------------------------
+// With the environment variable BMG_TUNE_CACHE naming a file, every tuner
+// decision is appended to it as one line
+//   <device> <tuner key> <count> <value 1> ... <value count> <best ms>
+// and a decision found there for this kind of device is reused instead of
+// timed again, so a later process skips the timing.  Every candidate of every
+// tuner computes the same bits, so a record changes only the speed; records
+// whose values are out of range for their tuner are ignored.
+struct TuneRecord {
+  std::vector<int> v;
+  float ms = 0.0f;
+};
+
+std::string device_tag() {
+  static std::string tag;
+  if (tag.empty()) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+      tag = prop.name;
+      for (char& c : tag)
+        if (c == ' ') c = '_';
+      tag += "/sm" + std::to_string(prop.multiProcessorCount);
+    } else {
+      tag = "unknown";
+    }
+  }
+  return tag;
+}
+
+struct TuneFile {
+  std::mutex mu;
+  std::string path;
+  std::map<std::string, TuneRecord> recs;
+};
+
+TuneFile& tune_file() {
+  static TuneFile tf;
+  return tf;
+}
+
+// (Re)load the records when BMG_TUNE_CACHE names another file than last time.
+// Caller holds the lock.
+void tune_file_sync(TuneFile& tf) {
+  const char* e = getenv("BMG_TUNE_CACHE");
+  const std::string path = e ? e : "";
+  if (path == tf.path) return;
+  tf.path = path;
+  tf.recs.clear();
+  if (path.empty()) return;
+  FILE* fp = fopen(path.c_str(), "r");
+  if (!fp) return;
+  char line[512];
+  while (fgets(line, sizeof line, fp)) {
+    char dev[128], key[256];
+    int count = 0, used = 0;
+    if (sscanf(line, "%127s %255s %d%n", dev, key, &count, &used) != 3 || count < 1 || count > 8) continue;
+    TuneRecord r;
+    const char* q = line + used;
+    bool ok = true;
+    for (int k = 0; k < count && ok; ++k) {
+      int val = 0, adv = 0;
+      ok = sscanf(q, "%d%n", &val, &adv) == 1;
+      r.v.push_back(val);
+      q += adv;
+    }
+    if (!ok || sscanf(q, "%f", &r.ms) != 1) continue;
+    tf.recs[std::string(dev) + " " + key] = r;
+  }
+  fclose(fp);
+}
+
+bool tune_file_get(const std::string& key, size_t count, TuneRecord* out) {
+  TuneFile& tf = tune_file();
+  std::lock_guard<std::mutex> guard(tf.mu);
+  tune_file_sync(tf);
+  if (tf.path.empty()) return false;
+  auto it = tf.recs.find(device_tag() + " " + key);
+  if (it == tf.recs.end() || it->second.v.size() != count) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_file_put(const std::string& key, const TuneRecord& r) {
+  TuneFile& tf = tune_file();
+  std::lock_guard<std::mutex> guard(tf.mu);
+  tune_file_sync(tf);
+  if (tf.path.empty()) return;
+  tf.recs[device_tag() + " " + key] = r;
+  FILE* fp = fopen(tf.path.c_str(), "a");
+  if (!fp) return;
+  fprintf(fp, "%s %s %zu", device_tag().c_str(), key.c_str(), r.v.size());
+  for (int x : r.v) fprintf(fp, " %d", x);
+  fprintf(fp, " %.6g\n", r.ms);
+  fclose(fp);
+}
+
+std::string tune_key(const char* tuner, std::initializer_list<int> fields) {
+  std::string k = tuner;
+  for (int f : fields) k += ":" + std::to_string(f);
+  return k;
+}
+
 // Autotuner of the solo hierarchy.  For every 9-point level with n >= 127 it
 // times two Gauss-Seidel sweeps on scratch iterates with the level's real
 // stencil: the row kernel for each admissible cluster size (1, 2, 4, 8 CTAs
@@ -442,6 +545,17 @@ int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* 
     return BMG_OK;
   }
   const int base = rows_cluster<T>(v.n);
+  const std::string fkey = tune_key("rows", {v.n, (int)sizeof(T), (int)sizeof(S), v.fused});
+  TuneRecord fr;
+  if (tune_file_get(fkey, 1, &fr)) {
+    const int cl = fr.v[0];
+    if ((cl == base || (cl > base && cl <= 8 && (cl & (cl - 1)) == 0 && ((v.n + 1) / 2 + cl - 1) / cl >= 32))) {
+      cache[key] = {cl, fr.ms};
+      *best_out = cl;
+      if (ms_out) *ms_out = fr.ms;
+      return BMG_OK;
+    }
+  }
   size_t ps = plane_size(v.n);
   T* scratch = nullptr;
   if (int e = dalloc_zero(&scratch, 2 * ps, s)) return e;
@@ -460,6 +574,7 @@ int tune_rows(const StencilView<T, S>& v, cudaStream_t s, int* best_out, float* 
   cudaFree(scratch);
   if (rc) return rc;
   cache[key] = {best_cl, best};
+  tune_file_put(fkey, TuneRecord{{best_cl}, best});
   *best_out = best_cl;
   if (ms_out) *ms_out = best;
   return BMG_OK;
@@ -473,6 +588,14 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
   if (it != cache.end()) {
     *best_out = it->second.first;
     *ms_out = it->second.second;
+    return BMG_OK;
+  }
+  const std::string fkey = tune_key("tile", {v.n, (int)sizeof(S), v.fused});
+  TuneRecord fr;
+  if (tune_file_get(fkey, 1, &fr) && fr.v[0] >= 0 && fr.v[0] < GS_TILE_SHAPES) {
+    cache[key] = {fr.v[0], fr.ms};
+    *best_out = fr.v[0];
+    *ms_out = fr.ms;
     return BMG_OK;
   }
   size_t ps = plane_stride32(v.n);
@@ -498,6 +621,7 @@ int tune_tile(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
   if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "one-pass sweep: bulk copies did not complete");
   if (rc) return rc;
   cache[key] = {best_shape, best};
+  tune_file_put(fkey, TuneRecord{{best_shape}, best});
   *best_out = best_shape;
   *ms_out = best;
   return BMG_OK;
@@ -511,6 +635,14 @@ int tune_pair(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
   if (it != cache.end()) {
     *best_out = it->second.first;
     *ms_out = it->second.second;
+    return BMG_OK;
+  }
+  const std::string fkey = tune_key("pair", {v.n, (int)sizeof(S), v.fused});
+  TuneRecord fr;
+  if (tune_file_get(fkey, 1, &fr) && fr.v[0] >= -1 && fr.v[0] < GS_PAIR_SHAPES) {
+    cache[key] = {fr.v[0], fr.ms};
+    *best_out = fr.v[0];
+    *ms_out = fr.ms;
     return BMG_OK;
   }
   size_t ps = plane_stride32(v.n);
@@ -537,6 +669,7 @@ int tune_pair(const StencilView<float, S>& v, cudaStream_t s, int* best_out, flo
   if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "two-sweep pass: bulk copies did not complete");
   if (rc) return rc;
   cache[key] = {best_shape, best};
+  tune_file_put(fkey, TuneRecord{{best_shape}, best});
   *best_out = best_shape;
   *ms_out = best;
   return BMG_OK;
@@ -572,6 +705,14 @@ int tune_tile64(const StencilView<double, double>& v, cudaStream_t s, int* best_
     *ms_out = it->second.second;
     return BMG_OK;
   }
+  const std::string fkey = tune_key("tile64", {v.n, v.fused});
+  TuneRecord fr;
+  if (tune_file_get(fkey, 1, &fr) && fr.v[0] >= 0 && fr.v[0] < GS_TILE64_SHAPES) {
+    cache[key] = {fr.v[0], fr.ms};
+    *best_out = fr.v[0];
+    *ms_out = fr.ms;
+    return BMG_OK;
+  }
   const size_t ps = plane_size(v.n);
   double* scratch = nullptr;   // x, x', f
   if (int e = dalloc_zero(&scratch, 3 * ps, s)) return e;
@@ -592,6 +733,7 @@ int tune_tile64(const StencilView<double, double>& v, cudaStream_t s, int* best_
   cudaFree(scratch);
   if (rc) return rc;
   cache[key] = {best_shape, best};
+  tune_file_put(fkey, TuneRecord{{best_shape}, best});
   *best_out = best_shape;
   *ms_out = best;
   return BMG_OK;
@@ -713,6 +855,12 @@ int autotune_solo(bmg_hierarchy* h) {
 // side and iterate are written by both (they are rewritten every cycle).
 template <typename S>
 int tune_pair_restrict(Level& L, Level& C, const StencilView<float, S>& v, cudaStream_t s) {
+  const std::string fkey = tune_key("pair_restrict", {v.n, (int)sizeof(S), v.fused, L.pair32});
+  TuneRecord fr;
+  if (tune_file_get(fkey, 1, &fr) && (fr.v[0] == 0 || fr.v[0] == 1)) {
+    L.pair_rr = fr.v[0];
+    return BMG_OK;
+  }
   size_t ps = plane_stride32(v.n);
   float* scratch = nullptr;   // x, x', f laid out like a level's arrays
   int rc = galloc(&scratch, v.n, 3, s);
@@ -741,6 +889,7 @@ int tune_pair_restrict(Level& L, Level& C, const StencilView<float, S>& v, cudaS
   if (!rc && strip_timeouts()) rc = set_error(BMG_ETIMEOUT, "two-sweep pass: bulk copies did not complete");
   if (rc) return rc;
   L.pair_rr = fused_ok && ms_fused < ms_sep ? 1 : 0;
+  tune_file_put(fkey, TuneRecord{{L.pair_rr}, L.pair_rr ? ms_fused : ms_sep});
   return BMG_OK;
 }
 
@@ -2046,6 +2195,16 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
   const bool shared = sizeof(T) == 4 && B->rhs_block != BMG_RHS_BLOCK_OFF && group_shared(B, g, b);
   auto key = std::make_tuple(g.n, g.storage, g.count, g.kind, B->arith, shared ? 1 : 0);
   auto it = g_tuned.find(key);
+  const std::string fkey = tune_key("group", {g.n, g.storage, g.count, g.kind, B->arith, shared ? 1 : 0});
+  TuneRecord fr;
+  if (it == g_tuned.end() && tune_file_get(fkey, 4, &fr)) {
+    const int base = rows_cluster<T>(g.n), cl = fr.v[0], tile = fr.v[1], pair = fr.v[2], multi = fr.v[3];
+    const bool cl_ok = cl == base || (cl > base && cl <= 8 && (cl & (cl - 1)) == 0 && ((g.n + 1) / 2 + cl - 1) / cl >= 32);
+    const bool tile_ok = tile >= -1 && tile <= 3;
+    const bool pair_ok = pair == -1 || (sizeof(T) == 4 && pair >= 0 && pair <= 3);
+    const bool multi_ok = multi == 0 || (shared && (multi == 2 || multi == 4) && g.count >= multi && tile >= 0);
+    if (cl_ok && tile_ok && pair_ok && multi_ok) it = g_tuned.emplace(key, GroupChoice{cl, tile, pair, multi}).first;
+  }
   if (it == g_tuned.end()) {
     const int base = rows_cluster<T>(g.n);
     const size_t ps = plane_stride32(g.n);   // scratch x, x2, f per problem, laid out like level arrays
@@ -2145,6 +2304,7 @@ int tune_group(bmg_batch* B, bmg_batch::Group& g, int b) {
     if (!rc && strip_timeouts_b()) rc = set_error(BMG_ETIMEOUT, "batched one-pass sweep: bulk copies did not complete");
     if (rc) return rc;
     it = g_tuned.emplace(key, best).first;
+    tune_file_put(fkey, TuneRecord{{best.cl, best.tile, best.pair, best.multi}, best_ms});
   }
   g.cl = it->second.cl;
   g.tile = it->second.tile;
