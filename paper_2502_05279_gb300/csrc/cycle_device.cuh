@@ -1429,6 +1429,30 @@ __device__ __forceinline__ double pow2_times_widened(double s, float e) {
   return pow2_times_widened_slow(s, e);
 }
 
+// fl32(r * inv) for inv a power of two (the scaled FP32 residual of the
+// refinement).  Narrowed first and scaled in FP32, it is the same number
+// whenever fl32(r) and the scaled value lie in [2^-125, 2^127]: both r and
+// r * inv are then in normal binades, where rounding to 24 bits commutes with
+// scaling by a power of two, and the FP32 product is exact.  Everything else
+// (tiny, huge, non-finite values, or a scale outside the FP32 range, signalled
+// by inv32 = 0) takes the FP64 product; this spares the FP64 pipe one multiply
+// per point on the FP64-bound outer residual.
+static __device__ __noinline__ float narrow_scaled_slow(double r, double inv) {
+  return __double2float_rn(rmul(r, inv));
+}
+
+__device__ __forceinline__ float narrow_scale32(double inv) {
+  return inv >= 0x1p-125 && inv <= 0x1p125 ? (float)inv : 0.0f;
+}
+
+__device__ __forceinline__ float narrow_scaled(double r, double inv, float inv32) {
+  const float a = __double2float_rn(r);
+  const float b = __fmul_rn(a, inv32);
+  const float ma = fabsf(a), mb = fabsf(b);
+  if (ma >= 0x1p-125f && ma <= 0x1p127f && mb >= 0x1p-125f && mb <= 0x1p127f) return b;
+  return narrow_scaled_slow(r, inv);
+}
+
 __device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, const float* __restrict__ e32,
                                                const Ctl* ctl, int i, int j) {
   if (i < 1 || j < 1 || i > n || j > n) return;
@@ -1445,13 +1469,14 @@ __device__ __forceinline__ void ir_residual_body(const StencilView<double, doubl
   const int n = v.n, ld = v.ld;
   const double s = ctl->scale_next;
   const double inv = 1.0 / s;   // exact: s is a power of two
+  const float inv32 = narrow_scale32(inv);
   double acc = 0.0;
   for (int j = 1 + b; j <= n; j += G)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
       double rr = nine ? row_residual<double, double, true, true, FU>(v, x, p, f[p])
                        : row_residual<double, double, false, true, FU>(v, x, p, f[p]);
-      r32[p] = __double2float_rn(rmul(rr, inv));
+      r32[p] = narrow_scaled(rr, inv, inv32);
       e32[p] = 0.0f;
       acc = madd<FU>(acc, rr, rr);
     }
