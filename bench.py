@@ -579,7 +579,7 @@ def run_ours(args, rank, local_rank, world):
     if args.only:
         # one hierarchy, warm-up and timed cycles only: the small run profiled by ncu
         h = bmg.Hierarchy(kind, coef, precision=args.only, krylov=args.krylov, smoother=args.smoother,
-                          arith=args.arith)
+                          arith=args.arith, fuse_restrict=args.fuse_restrict)
         x = torch.zeros_like(rhs)
         h.time_cycles(rhs, x, args.warmup)
         ms = h.time_cycles(rhs, x, args.steps)
@@ -1008,6 +1008,8 @@ def main():
                     help="time one hierarchy's cycles only (short run for profilers)")
     ap.add_argument("--krylov", choices=("none", "fcg"), default="none", help="solve mode for --only")
     ap.add_argument("--smoother", default="auto", help="FP32 Gauss-Seidel kernel for --only (auto, rows, tile0..4)")
+    ap.add_argument("--fuse-restrict", default="auto", choices=("auto", "off", "on"),
+                    help="two sweeps + residual + restriction in one pass, for --only")
     ap.add_argument("--learned-problems", type=int, default=2000, help="training problems (one crop each)")
     ap.add_argument("--learned-epochs", type=int, default=8, help="training epochs of the learned variant")
     ap.add_argument("--arith", choices=("rounded", "fused"), default="fused",
