@@ -1291,14 +1291,24 @@ __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, con
 // Block b of G = min(n, 1024) handles rows j = 1 + b, 1 + b + G, ...; thread t
 // the columns i = 1 + t, 1 + t + 256, ...; each thread sums in that order,
 // then a fixed halving tree; the G block sums are reduced the same way.
+// The halving tree s[t] += s[t + h], h = 128, 64, ..., 1: the levels h >= 32
+// through shared memory with a block barrier each, the levels h < 32 inside
+// warp 0 by shuffles (lane t adds lane t + h; lanes >= h hold values no lane
+// below h reads), so every sum pairs the same operands as the all-shared tree.
 __device__ __forceinline__ double block_sum(double acc) {
   __shared__ double red[NORM_THREADS];
   red[threadIdx.x] = acc;
   __syncthreads();
-  for (int s = NORM_THREADS / 2; s > 0; s >>= 1) {
+  for (int s = NORM_THREADS / 2; s >= 32; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
     __syncthreads();
   }
+  if (threadIdx.x < 32) {
+    double v = red[threadIdx.x];
+    for (int s = 16; s > 0; s >>= 1) v = v + __shfl_down_sync(0xffffffffu, v, s);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
   double v = red[0];
   __syncthreads();   // the buffer may be reused by a following block_sum
   return v;
