@@ -171,3 +171,47 @@ def test_square_only_calls_refuse(bmg):
     assert bmg.lib.bmg_batch_rhs(h._h, 2, None, ctypes.byref(out)) == bmg.BMG_EINVAL
     assert bmg.lib.bmg_tuned_cluster(h._h, 0) == bmg.BMG_EINVAL
     h.close()
+
+
+@pytest.mark.parametrize("axes", AXES)
+def test_smallest_grid_is_one_direct_solve(bmg, axes):
+    """Periodic 4 points (Dirichlet 3) per axis: the hierarchy is its coarsest
+    level alone, and one iteration solves the system to rounding."""
+    kind, planes, f, px, py = problem(3, axes)
+    levels = pr.setup(kind, planes, px, py)
+    assert len(levels) == 1
+    h = hierarchy(bmg, kind, planes, axes)
+    assert h.num_levels == 1
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-12, maxit=5)
+    assert ok and it == 1 and rr <= 1e-13
+    x_o, _ = pr.solve(levels, f, tol=1e-12, maxit=5)
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
+    h.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (0, 2), (3, 0)])
+def test_other_sweep_counts_bitwise(bmg, nu1, nu2):
+    kind, planes, f, px, py = problem(63, "xy", seed=60)
+    levels = pr.setup(kind, planes, px, py, arith="fused")
+    x_o = np.zeros_like(f)
+    for _ in range(3):
+        pr.vcycle(levels, 0, x_o, f, nu1, nu2)
+    h = hierarchy(bmg, kind, planes, "xy", arith="fused", nu1=nu1, nu2=nu2)
+    x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=3)
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
+    h.close()
+
+
+def test_zero_rhs_maxit_zero_and_nan(bmg):
+    kind, planes, f, px, py = problem(63, "x")
+    h = hierarchy(bmg, kind, planes, "x")
+    x, it, rr, ok = h.solve(torch.zeros_like(torch.from_numpy(f)).cuda())
+    assert ok and it == 0 and not x.any()
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), maxit=0)
+    assert not ok and it == 0 and not x.any()
+    g = f.copy()
+    g[5, 7] = np.nan
+    with pytest.raises(bmg.BmgError) as e:
+        h.solve(torch.from_numpy(g).cuda())
+    assert e.value.code == -5
+    h.close()
