@@ -202,9 +202,11 @@ PERIODIC = {
 
 
 def run_periodic(args, rank, local_rank, world):
-    """Periodic sides: the FP64 V(2,1) of the periodic hierarchy (one launch
-    per colour of each sweep, indices wrapped), its throughput, its time to
-    1e-10 and the level-0 sweep against the copy bandwidth."""
+    """Periodic sides: the FP64 V(2,1) of the periodic hierarchy (each 9-point
+    level swept by the one-pass strip kernel with wrapped indices or the
+    row-parity pair, whichever setup timed as faster), its
+    throughput, its time to 1e-10 and the level-0 sweep against the copy
+    bandwidth and the FP64 instruction rate."""
     import torch
     import paper_2502_05279_gb300 as bmg
     torch.cuda.set_device(local_rank)
@@ -230,6 +232,7 @@ def run_periodic(args, rank, local_rank, world):
         h.close()
         ranks.close()
         return
+    fp64_rate = bmg.measure_fp64_rate() * 1e9        # DP instructions per second, measured here
     h.time_cycles(rhs, x, max(args.warmup, 3))
     ranks.barrier()
     before = h.launch_count
@@ -265,6 +268,8 @@ def run_periodic(args, rank, local_rank, world):
         e2e_cycles += it
     e2e_s = ranks.max(time.perf_counter() - t0)
     levels = h.num_levels
+    sweep_kind = {bmg.TILE_SWEEP: "strip", 1: "rows", 0: "direct"}
+    sweep_by_level = [sweep_kind[h.tuned_cluster(l)] for l in range(levels)]
     h.close()
     if rank != 0:
         ranks.close()
@@ -275,6 +280,7 @@ def run_periodic(args, rank, local_rank, world):
     per_sweep_s = relax0["ms"] / sweeps * 1e-3
     byt = SWEEP_BYTES[("fp64", kind)] * N
     gbs = byt / per_sweep_s / 1e9
+    instr_pt = ALG_FP64_INSTR_PER_POINT[(kind, args.arith)]
     out = {"metric": METRIC, "value": whole_job_rate(N * args.steps, ms * 1e-3, ranks), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -282,18 +288,24 @@ def run_periodic(args, rank, local_rank, world):
            "config": {"workload": args.workload, "description": spec["text"], "unknowns": N, "arith": args.arith,
                       "levels": levels, "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "working set > L2 (FP64 level-0 stencil + vectors = %.0f MB)" % (N * 64 / 1e6)},
-           "roofline": {"bound": "hbm", "kernel": "k_p_gs_rows level 0 (two row-parity launches per sweep)",
+           "roofline": {"bound": "hbm", "kernel": "k_p_gs_strip level 0 (one-pass strip walk, one launch per sweep)",
                         "achieved": round(gbs, 1), "peak": hbm_peak[0], "unit": "GB/s",
                         "frac": round(gbs / hbm_peak[0], 4), "peak_source": hbm_peak[1], "traffic": None,
                         "traffic_source": None, "alg_bytes_per_sweep": byt,
                         "alg_bytes_per_point": SWEEP_BYTES[("fp64", kind)],
+                        "fp64_pipe": {"achieved": round(instr_pt * N / per_sweep_s / 1e12, 4),
+                                      "peak": round(fp64_rate / 1e12, 4), "unit": "T FP64 instr/s",
+                                      "frac": round(instr_pt * N / per_sweep_s / fp64_rate, 4),
+                                      "instr_per_point": instr_pt,
+                                      "peak_source": "FP64 instruction rate measured in this run "
+                                                     "(bmg_measure_fp64_rate)"},
                         "time_share": round(relax0["ms"] / sum(q["ms"] for q in prof), 3),
                         "avg_sweep_us": round(per_sweep_s * 1e6, 2)},
            "e2e": {"value": world * N * e2e_cycles / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
                    "d2h_bytes_per_step": int(f.nbytes),
                    "note": "bmg_solve (FP64 V(2,1)) to 1e-10 from a zero guess per step; rhs H2D from pinned "
                            "memory, x D2H"},
-           "gpu_launches": int(launches), "clocks": clocks,
+           "gpu_launches": int(launches), "clocks": clocks, "sweep_by_level": sweep_by_level,
            "time_to_tol": {"fp64": {"setup_ms": round(setup_ms, 1),
                                     "vcycle": dict(solve_ms=round(t_solve * 1e3, 3), iterations=iters, relres=relres,
                                                    converged=ok)}},

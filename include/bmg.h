@@ -160,9 +160,13 @@ typedef struct {
                            (always that many per warp).  Same bits. */
   int periodic;         /* 0 (default): Dirichlet sides; BMG_PERIODIC_X | BMG_PERIODIC_Y: those axes
                            wrap around (see Periodic sides above).  Periodic hierarchies run FP64
-                           stationary V(nu1, nu2) cycles with point Gauss-Seidel (smoother AUTO or
-                           ROWS), Dendy interpolation and the default coarsest level, in either
-                           arithmetic mode, with or without graphs; other options give EINVAL */
+                           stationary V(nu1, nu2) cycles with point Gauss-Seidel, Dendy
+                           interpolation and the default coarsest level, in either arithmetic mode,
+                           with or without graphs; other options give EINVAL.  Their 9-point levels
+                           are swept (the same bits either way) by two row-parity launches in place
+                           (smoother ROWS), by the one-pass strip kernel into a second iterate
+                           (smoother TILE), or, by default (AUTO), per level by whichever of the
+                           two setup timed as faster */
 } bmg_opts;
 
 #define BMG_PERIODIC_X 1
@@ -261,7 +265,10 @@ int bmg_profile(bmg_hierarchy* h, const double* rhs, double* x, int cycles, bmg_
  * rows into registers, TY = 32, 16; FP64 cycles: rows copied per lane into RING
  * slots, (TY, RING) = (W, 4), (16, 4), (W, 6), (8, 4), W the smallest even
  * height whose strips fit into one wave of resident warps), or 0 (default;
- * not tuned).  Every choice computes the same bits. */
+ * not tuned).  With periodic sides: BMG_TILE_SWEEP for a level swept by the
+ * one-pass strip kernel, 1 for the row-parity pair (or, on a 5-point level 0,
+ * one launch per colour), 0 for the coarsest level.  Every choice computes the
+ * same bits. */
 #define BMG_TILE_SWEEP 16
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level);
 

@@ -1249,8 +1249,8 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
   else if (h->precision != BMG_FP64) why = "periodic sides take FP64 cycles only";
   else if (h->interp != BMG_INTERP_DENDY) why = "periodic sides take Dendy interpolation only";
   else if (h->krylov != BMG_KRYLOV_NONE) why = "periodic sides take stationary cycles only";
-  else if (h->smoother != BMG_SMOOTHER_AUTO && h->smoother != BMG_SMOOTHER_ROWS)
-    why = "periodic sides take point Gauss-Seidel only";
+  else if (h->smoother != BMG_SMOOTHER_AUTO && h->smoother != BMG_SMOOTHER_ROWS && h->smoother != BMG_SMOOTHER_TILE)
+    why = "periodic sides take point Gauss-Seidel (smoother AUTO, ROWS or TILE) only";
   else if (h->coarsest != 3) why = "periodic sides take the default coarsest level";
   else if (!per_levels_for(nx, ny, periodic))
     why = "a periodic axis needs 2^m points, a Dirichlet axis 2^m - 1, both axes the same m >= 2";
@@ -1267,6 +1267,9 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = dalloc(&h->partials, 2 * (size_t)norm_partials_max());
   if (!rc) rc = per_setup(&h->per, A->kind, A->coef, nx, ny, periodic, h->arith == BMG_ARITH_FUSED, h->nu1, h->nu2,
+                          h->smoother == BMG_SMOOTHER_ROWS   ? PER_SWEEP_ROWS
+                          : h->smoother == BMG_SMOOTHER_TILE ? PER_SWEEP_STRIP
+                                                             : PER_SWEEP_AUTO,
                           h->ws);
   if (!rc) rc = ensure_ctl(h, 64);
   if (rc) {
@@ -1381,6 +1384,11 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
 }
 
 int bmg_tuned_cluster(const bmg_hierarchy* h, int level) {
+  if (h && h->per) {
+    if (level < 0 || level >= per_num_levels(h->per)) return set_error(BMG_EINVAL, "bmg_tuned_cluster: bad level");
+    const int k = per_level_sweep(h->per, level);
+    return k == 2 ? BMG_TILE_SWEEP : k;
+  }
   if (!h || level < 0 || level >= h->nlev) return set_error(BMG_EINVAL, "bmg_tuned_cluster: bad level");
   const Level& L = h->lv[level];
   if (h->precision != BMG_FP64 && L.tile32 >= 0) return BMG_TILE_SWEEP + L.tile32;

@@ -376,6 +376,126 @@ __global__ void __launch_bounds__(256) k_p_gs_rows(PGeom g, const double* __rest
   }
 }
 
+// One-pass 9-point sweep xin -> xout: the FP64 strip walk of the Dirichlet
+// levels (56-column warp strips of height ty; lane l holds columns 2l, 2l + 1
+// of a 64-column window; the colour regions shrink by one column per colour,
+// so lanes 2..29 end with the sweep's values; band rows j0 - 1 .. j1 + 1 pass
+// through a per-warp ring of 8-byte cp.async copies) with the window's
+// columns and band rows taken modulo N on a periodic axis.  Strips stay
+// independent across a periodic seam for the reason they are independent
+// inside the grid: a strip's first row is odd and reads only old even rows,
+// and its last row (even) needs the new odd row above, which the strip forms
+// itself as a halo row; on a periodic y axis that halo row is row ny + 1, i.e.
+// row 1, computed from copies of the old values and never stored.  Every point
+// takes the operands of the colour-by-colour sweep in the same order, so the
+// result is bit-identical to it.
+template <int RING, bool FU>
+__device__ __forceinline__ void p_strip64_body(const PGeom& g, const double* __restrict__ st,
+                                               const double* __restrict__ f, const double* __restrict__ xin,
+                                               double* __restrict__ xout, int sx, int sy, int ty,
+                                               unsigned char* ring) {
+  using Row = dev::StripRowT<double, double>;
+  const int nx = g.nx, ny = g.ny, ld = nx + 2;
+  const size_t ps = g.ps();
+  const int lane = threadIdx.x & 31;
+  const int i0 = 1 + 56 * sx, j0 = 1 + ty * sy, j1 = j0 + ty;
+  const int ic = i0 - 4 + 2 * lane;
+  // source column of window column i (modulo nx on a periodic axis, else
+  // inside [0, nx + 1] or zero-filled) and whether it is a point of the level
+  auto col = [&](int i, bool& copy, bool& point) {
+    if (g.px) {
+      copy = point = true;
+      return 1 + ((i - 1) % nx + nx) % nx;
+    }
+    copy = i >= 0 && i <= nx + 1;
+    point = i >= 1 && i <= nx;
+    return copy ? i : 0;
+  };
+  bool cpa, cpb, pta, ptb;
+  const int ca = col(ic, cpa, pta), cb = col(ic + 1, cpb, ptb);
+  const bool c1 = pta && lane >= 1, c2 = ptb && lane >= 1 && lane <= 30;
+  const bool c3 = pta && lane >= 2 && lane <= 30, c4 = ptb && lane >= 2 && lane <= 29;
+  const bool own = lane >= 2 && lane <= 29;
+  const int rlim = g.py ? ny + 1 : ny;            // last row a colour-1/2 update reaches
+  // ring slot arrays x, f, D, W, S, SW, NW: the iterate, the right-hand side, stencil planes 5, 1, 2, 3, 4
+  constexpr int plane[7] = {-1, -1, 5, 1, 2, 3, 4};
+  const int NR = ty + 3;                          // band rows q = 0 .. NR - 1, j = j0 - 1 + q
+  auto issue = [&](int q) {
+    if (q < NR) {
+      const int j = j0 - 1 + q;
+      const bool rin = g.py || (j >= 0 && j <= ny + 1);
+      const int jr = g.py ? 1 + ((j - 1) % ny + ny) % ny : (rin ? j : 0);
+      const size_t pa = (size_t)jr * ld + ca, pb = (size_t)jr * ld + cb;
+      double* d = reinterpret_cast<double*>(ring + (q % RING) * dev::STRIP64_SLOT) + 2 * lane;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const double* a = k == 0 ? xin : k == 1 ? f : st + (size_t)plane[k] * ps;
+        dev::cp_async8(d + 64 * k, a + pa, rin && cpa);
+        dev::cp_async8(d + 64 * k + 1, a + pb, rin && cpb);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+#pragma unroll
+  for (int q = 0; q < RING; ++q) issue(q);
+  auto take = [&](int q, Row& R) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(RING - 1) : "memory");
+    dev::row64_read(ring + (q % RING) * dev::STRIP64_SLOT, lane, R);
+    issue(q + RING);
+  };
+  auto store = [&](int j, const Row& R) {
+    if (!own || j > ny) return;
+    const size_t p = (size_t)j * ld + ic;
+    if (ic <= nx) xout[p] = R.xa;
+    if (ic + 1 <= nx) xout[p + 1] = R.xb;
+  };
+  Row P0, P1, Q0, Q1;
+  take(0, P1);
+  take(1, Q0);
+  take(2, Q1);
+  if (j0 <= rlim) {
+    dev::strip_row<double, double, FU>(P1, Q0, Q1, c1, c2);   // row j0: colours 1, 2
+    store(j0, Q0);
+  }
+  auto step = [&](int m, Row& E0, Row& E1, Row& E2, Row& E3) {
+    const int a = j0 + 2 * m;
+    take(2 * m + 1, E2);
+    take(2 * m + 2, E3);
+    if (a <= rlim) {
+      dev::strip_row<double, double, FU>(E1, E2, E3, c1, c2); // row a: colours 1, 2
+      if (a < j1) store(a, E2);
+    }
+    if (a - 1 <= ny) {
+      dev::strip_row<double, double, FU>(E0, E1, E2, c3, c4); // row a - 1: colours 3, 4
+      store(a - 1, E1);
+    }
+  };
+#pragma unroll 1
+  for (int m = 1; m <= ty / 2; m += 2) {
+    step(m, Q0, Q1, P0, P1);
+    if (m + 1 <= ty / 2) step(m + 1, P0, P1, Q0, Q1);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // no copy outlives the warp
+}
+
+constexpr int P_STRIP_WARPS = 4, P_STRIP_RING = 4;
+constexpr size_t P_STRIP_SMEM = (size_t)P_STRIP_WARPS * P_STRIP_RING * dev::STRIP64_SLOT;
+
+template <bool FU>
+__global__ void __launch_bounds__(32 * P_STRIP_WARPS, 4) k_p_gs_strip(PGeom g, const double* __restrict__ st,
+                                                                   const double* __restrict__ f,
+                                                                   const double* __restrict__ xin,
+                                                                   double* __restrict__ xout, int ty,
+                                                                   const int* done) {
+  extern __shared__ __align__(128) unsigned char p_strip_smem[];
+  if (dev::stopped(done)) return;
+  const int nbx = (g.nx + 55) / 56, nby = (g.ny + ty - 1) / ty;
+  const int w = threadIdx.x >> 5, s = blockIdx.x * P_STRIP_WARPS + w;
+  if (s >= nbx * nby) return;                     // whole warps only
+  p_strip64_body<P_STRIP_RING, FU>(g, st, f, xin, xout, s % nbx, s / nbx, ty,
+                                   p_strip_smem + (size_t)w * P_STRIP_RING * dev::STRIP64_SLOT);
+}
+
 // r = f - A x (when r != NULL) and the partial sums of r^2 in the canonical
 // reduction order (block b of G = min(ny, 1024): rows 1 + b, 1 + b + G, ...;
 // thread t: columns 1 + t, 1 + t + 256, ...; then the halving tree).
@@ -426,13 +546,13 @@ __global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const doubl
   fc[(size_t)jc * (c.ncx + 2) + ic] = t;
 }
 
-// x += P e_c at fine point (i, j): the interpolated value is formed first, then
-// added (coincident e; x-edge LL e_W + LR e_E; y-edge LB e_S + LA e_N; centre
+// x_out = x_in + P e_c at fine point (i, j) (x_in and x_out may be the same
+// array): the interpolated value is formed first, then added (coincident e; x-edge LL e_W + LR e_E; y-edge LB e_S + LA e_N; centre
 // ((LSW e_SW + LSE e_SE) + LNW e_NW) + LNE e_NE), coarse neighbours wrapped on a
 // periodic axis, a Dirichlet ghost reading its zero.
 template <bool FU>
 __global__ void k_p_interp(PGeom g, const double* __restrict__ ci, const double* __restrict__ ec,
-                           double* __restrict__ x, const int* done) {
+                           const double* xin, double* xout, const int* done) {
   if (dev::stopped(done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (i > g.nx || j > g.ny) return;
@@ -459,7 +579,7 @@ __global__ void k_p_interp(PGeom g, const double* __restrict__ ci, const double*
     t = madd<FU>(t, w(CI_LNW, ic, jc), e(ic - 1, jc));
     t = madd<FU>(t, w(CI_LNE, ic, jc), e(ic, jc));
   }
-  x[p] = radd(x[p], t);
+  xout[p] = radd(xin[p], t);
 }
 
 // L L^T x = f on the coarsest level (one thread, m <= 16): forward then backward
@@ -503,6 +623,9 @@ struct PerLevel {
   double* x = nullptr;    // iterate and right-hand side of a coarse level
   double* f = nullptr;
   double* r = nullptr;    // residual of a level above the coarsest
+  double* xb = nullptr;   // second iterate for strip sweeps (9-point levels above the coarsest)
+  int ty = 0;             // strip height
+  bool strip = false;     // swept by the strip kernel (else by the row-parity pair, in place)
 };
 
 struct PerHier {
@@ -512,6 +635,23 @@ struct PerHier {
   double* work = nullptr;
   int* err = nullptr;
 };
+
+// The smallest even strip height whose strips fit into one wave of the strip
+// kernel's resident warps (a warp walks its strip serially; a partial second
+// wave would leave most FP64 pipes idle).
+static int strip_height(const PGeom& g, int fused) {
+  auto k = fused ? k_p_gs_strip<true> : k_p_gs_strip<false>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_STRIP_SMEM);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * P_STRIP_WARPS, P_STRIP_SMEM);
+  const int resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * P_STRIP_WARPS;
+  const int nbx = (g.nx + 55) / 56;
+  const int nby_max = resident / nbx > 1 ? resident / nbx : 1;
+  const int half = (g.ny + 2 * nby_max - 1) / (2 * nby_max);
+  return 2 * (half > 1 ? half : 1);
+}
 
 int per_levels_for(int nx, int ny, int periodic) {
   const int mx = m_of(nx, periodic & 1), my = m_of(ny, periodic & 2);
@@ -536,6 +676,7 @@ void per_free(PerHier* P) {
     cudaFree(L.x);
     cudaFree(L.f);
     cudaFree(L.r);
+    cudaFree(L.xb);
   }
   cudaFree(P->L);
   cudaFree(P->work);
@@ -543,8 +684,43 @@ void per_free(PerHier* P) {
   delete P;
 }
 
+namespace {
+template <bool FU>
+double* per_sweep(const PerLevel& L, const double* f, double* x, double* home, const int* done, cudaStream_t s);
+
+// The sweep of each 9-point level: the strip walk or the row-parity pair,
+// whichever takes less time here over 3 sweeps (after one untimed), run on
+// zero data in the level's scratch arrays (r as iterate and right-hand side,
+// xb; both stay zero).
+int tune_sweeps(PerHier* P, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_check(cudaEventCreate(&e0), "periodic setup: event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "periodic setup: event");
+  for (PerLevel& L : P->lv) {
+    if (rc || !L.xb) continue;
+    float t[2] = {0.f, 0.f};
+    for (int k = 0; k < 2 && !rc; ++k) {
+      L.strip = k == 0;
+      auto sweep = [&](double* x) {
+        return P->fused ? per_sweep<true>(L, L.r, x, L.r, nullptr, s) : per_sweep<false>(L, L.r, x, L.r, nullptr, s);
+      };
+      double* x = sweep(L.r);
+      cudaEventRecord(e0, s);
+      for (int q = 0; q < 3; ++q) x = sweep(x);
+      cudaEventRecord(e1, s);
+      rc = cuda_check(cudaEventSynchronize(e1), "periodic setup: sweep timing");
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&t[k], e0, e1), "periodic setup: sweep timing");
+    }
+    L.strip = t[0] <= t[1];
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
+}  // namespace
+
 int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int periodic, int fused, int nu1,
-              int nu2, cudaStream_t s) {
+              int nu2, int sweep, cudaStream_t s) {
   *out = nullptr;
   const int nlev = per_levels_for(nx, ny, periodic);
   if (nlev < 1)
@@ -571,6 +747,7 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
       rc = palloc(&L.ci, 8 * psc, s);
       if (!rc) rc = palloc(&L.r, ps, s);
     }
+    if (!rc && sweep != PER_SWEEP_ROWS && l + 1 < nlev && L.kind == 9) rc = palloc(&L.xb, ps, s);
     if (!rc && l > 0) rc = palloc(&L.x, ps, s);
     if (!rc && l > 0) rc = palloc(&L.f, ps, s);
   }
@@ -584,6 +761,11 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
     per_free(P);
     return rc;
   }
+  for (PerLevel& L : P->lv)
+    if (L.xb) {
+      L.ty = strip_height(L.g, fused);
+      L.strip = true;
+    }
   const PGeom g0 = P->lv[0].g;
   k_p_prepare<<<pgrid(g0.nx + 2, g0.ny + 2), dim3(PBX, PBY), 0, s>>>(g0, kind, coef, P->lv[0].st);
   count_launch();
@@ -609,6 +791,7 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
     rc = set_error(BMG_ESINGULAR, "periodic setup: non-positive %s (a grid periodic along both axes needs a "
                                   "non-singular operator)",
                    herr == 1 ? "diagonal" : herr == 2 ? "interpolation denominator" : "Cholesky pivot");
+  if (!rc && sweep == PER_SWEEP_AUTO) rc = tune_sweeps(P, s);
   if (rc) {
     per_free(P);
     return rc;
@@ -629,8 +812,19 @@ struct Bracket {
   }
 };
 
+// One sweep starting from x, which is the level's iterate `home` or its
+// second iterate L.xb; returns the array holding the result: the other one of
+// the two for a level swept by strips (one launch), x itself otherwise.
 template <bool FU>
-void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, cudaStream_t s) {
+double* per_sweep(const PerLevel& L, const double* f, double* x, double* home, const int* done, cudaStream_t s) {
+  if (L.strip) {
+    double* out = x == L.xb ? home : L.xb;
+    const int warps = ((L.g.nx + 55) / 56) * ((L.g.ny + L.ty - 1) / L.ty);
+    k_p_gs_strip<FU><<<(warps + P_STRIP_WARPS - 1) / P_STRIP_WARPS, 32 * P_STRIP_WARPS, P_STRIP_SMEM, s>>>(
+        L.g, L.st, f, x, out, L.ty, done);
+    count_launch();
+    return out;
+  }
   // 9-point: the two row-parity halves; 5-point (level 0 only): one launch per
   // colour, red ((odd,odd), (even,even)) then black
   static const int c5[4][2] = {{1, 1}, {0, 0}, {0, 1}, {1, 0}};
@@ -641,7 +835,7 @@ void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, c
       k_p_gs_rows<FU><<<rows, 256, 0, s>>>(L.g, L.st, f, x, pj, done);
       count_launch();
     }
-    return;
+    return x;
   }
   for (int k = 0; k < 4; ++k) {
     const int pi = c5[k][0], pj = c5[k][1];
@@ -649,6 +843,7 @@ void per_sweep(const PerLevel& L, const double* f, double* x, const int* done, c
     k_p_gs<false, FU><<<pgrid(cx, cy), dim3(PBX, PBY), 0, s>>>(L.g, L.st, f, x, pi, pj, done);
     count_launch();
   }
+  return x;
 }
 
 template <bool FU>
@@ -674,26 +869,30 @@ void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, 
     return;
   }
   PerLevel& C = P->lv[l + 1];
+  double* cur = x;                                // where the iterate is
   for (int k = 0; k < P->nu1; ++k) {
     Bracket b(mk, l, BMG_K_RELAX);
-    per_sweep<FU>(L, f, x, done, s);
+    cur = per_sweep<FU>(L, f, cur, x, done, s);
   }
   {
     Bracket b(mk, l, BMG_K_RESID_RESTRICT);
-    per_residual<FU>(L, x, f, L.r, nullptr, done, s);
+    per_residual<FU>(L, cur, f, L.r, nullptr, done, s);
     k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, done);
     count_launch();
     cudaMemsetAsync(C.x, 0, C.g.ps() * sizeof(double), s);
   }
   per_vcycle<FU>(P, l + 1, C.x, C.f, done, s, mk);
   {
+    // corrected iterate into the array from which the nu2 post-sweeps end in x
     Bracket b(mk, l, BMG_K_INTERP);
-    k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, x, done);
+    double* dst = L.strip && (P->nu2 & 1) ? L.xb : x;
+    k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, cur, dst, done);
     count_launch();
+    cur = dst;
   }
   for (int k = 0; k < P->nu2; ++k) {
     Bracket b(mk, l, BMG_K_RELAX);
-    per_sweep<FU>(L, f, x, done, s);
+    cur = per_sweep<FU>(L, f, cur, x, done, s);
   }
 }
 
@@ -723,6 +922,11 @@ void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* par
 }
 
 int per_num_levels(const PerHier* P) { return (int)P->lv.size(); }
+
+int per_level_sweep(const PerHier* P, int l) {
+  if (l < 0 || l + 1 >= (int)P->lv.size()) return 0;
+  return P->lv[l].strip ? 2 : 1;
+}
 
 int per_level_shape(const PerHier* P, int l, int* nx, int* ny) {
   if (l < 0 || l >= (int)P->lv.size()) return set_error(BMG_EINVAL, "bmg_level_shape: bad level %d", l);

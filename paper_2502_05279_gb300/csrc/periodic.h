@@ -8,8 +8,8 @@
 // (N_y + 2) x (N_x + 2) with zero ghost lines: the kernels wrap indices on
 // the periodic axes instead of reading ghost copies.  The cycle is the FP64
 // V(nu1, nu2) of the Dirichlet hierarchy (the same formulas, term orders and
-// arithmetic modes); a 9-point sweep is two row-parity launches, a 5-point one
-// (level 0) one launch per colour.
+// arithmetic modes); a 9-point sweep is one launch of the strip walk (or two
+// row-parity launches), a 5-point one (level 0) one launch per colour.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,9 +25,14 @@ int per_levels_for(int nx, int ny, int periodic);
 
 // Build the hierarchy on stream s from the caller's planes (kind 5: O, W, S;
 // kind 9: O, W, S, SW, NW; each (ny+2) x (nx+2)).  BMG_ESINGULAR for a
-// non-positive diagonal or pivot or a zero interpolation denominator.
+// non-positive diagonal or pivot or a zero interpolation denominator.  sweep
+// says how 9-point levels are swept (the same bits either way): by the two
+// row-parity launches in place (PER_SWEEP_ROWS), by the one-pass strip kernel
+// into a second iterate (PER_SWEEP_STRIP), or per level by whichever of the
+// two is faster, timed during setup (PER_SWEEP_AUTO).
+enum { PER_SWEEP_AUTO = 0, PER_SWEEP_ROWS = 1, PER_SWEEP_STRIP = 2 };
 int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int periodic, int fused, int nu1,
-              int nu2, cudaStream_t s);
+              int nu2, int sweep, cudaStream_t s);
 void per_free(PerHier* P);
 
 // Profiling brackets around each step's launches (begin: level and BMG_K_*
@@ -46,6 +51,9 @@ void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* par
                            const PerMarks* marks = nullptr);
 
 int per_num_levels(const PerHier* P);
+// How level l is swept: 2 one-pass strip kernel, 1 row-parity pair (9-point)
+// or one launch per colour (5-point), 0 not swept (the coarsest level).
+int per_level_sweep(const PerHier* P, int l);
 int per_level_shape(const PerHier* P, int l, int* nx, int* ny);
 // Level l's five planes O, W, S, SW, NW ((ny+2) x (nx+2) each, ghost lines zero)
 // and its eight interpolation planes toward level l + 1 ((ny_c+2) x (nx_c+2)).

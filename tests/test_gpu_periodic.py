@@ -4,6 +4,7 @@ cycles bit for bit, the residual histories bit for bit in the device's
 summation order and at the stated reading against the plain norm, and the
 solve to 1e-10 confirmed by the oracle's own residual."""
 import ctypes
+import functools
 
 import numpy as np
 import pytest
@@ -75,12 +76,15 @@ def oracle_cycles(levels, f, cycles, fused):
 @pytest.mark.parametrize("axes", AXES)
 @pytest.mark.parametrize("arith", ["rounded", "fused"])
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_cycles_bitwise(bmg, axes, arith, use_graph):
+@pytest.mark.parametrize("smoother", ["auto", "rows", "tile"])
+def test_cycles_bitwise(bmg, axes, arith, use_graph, smoother):
+    """9-point levels swept by the two row-parity launches (rows), by the
+    one-pass strip kernel (tile), or per level by the faster one (auto)."""
     n = 127
     kind, planes, f, px, py = problem(n, axes, seed=56)
     levels = pr.setup(kind, planes, px, py, arith=arith)
     x_o, hist_o, plain_o = oracle_cycles(levels, f, 5, arith == "fused")
-    h = hierarchy(bmg, kind, planes, axes, arith=arith, use_graph=use_graph)
+    h = hierarchy(bmg, kind, planes, axes, arith=arith, use_graph=use_graph, smoother=smoother)
     rhs = torch.from_numpy(f).cuda()
     x, it, rr, ok = h.solve(rhs, tol=0.0, maxit=5)
     assert it == 5 and not ok
@@ -96,6 +100,8 @@ def test_cycles_bitwise(bmg, axes, arith, use_graph):
 
 @pytest.mark.parametrize("axes", ["x", "y"])
 def test_five_point_cycles_bitwise(bmg, axes):
+    """5-point level 0 (one launch per colour, in place) over strip-swept
+    9-point coarse levels."""
     kind, planes, f, px, py = problem(63, axes, kind=5)
     levels = pr.setup(kind, planes, px, py)
     x_o, hist_o, _ = oracle_cycles(levels, f, 4, False)
@@ -120,16 +126,23 @@ def test_solve_to_tolerance(bmg, axes):
     h.close()
 
 
-def test_full_size_cycles_bitwise(bmg):
-    """4096 x 4095, periodic in x: two cycles bitwise, the same launch
-    configuration the bench times."""
+@functools.lru_cache(maxsize=1)
+def full_size_oracle():
     kind, planes, f, px, py = w.periodic_problem(4095, "x", seed_k=50, seed_f=51)
     levels = pr.setup(kind, planes, px, py, arith="fused")
-    h = hierarchy(bmg, kind, planes, "x", arith="fused")
-    x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=2)
     x_o = np.zeros_like(f)
     for _ in range(2):
         pr.vcycle(levels, 0, x_o, f)
+    return kind, planes, f, x_o
+
+
+@pytest.mark.parametrize("smoother", ["auto", "tile"])
+def test_full_size_cycles_bitwise(bmg, smoother):
+    """4096 x 4095, periodic in x: two cycles bitwise, in the launch
+    configuration the bench times (auto) and with strips on every level."""
+    kind, planes, f, x_o = full_size_oracle()
+    h = hierarchy(bmg, kind, planes, "x", arith="fused", smoother=smoother)
+    x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=2)
     assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
     h.close()
 
@@ -154,8 +167,8 @@ def test_bad_periodic_sizes(bmg, shape, axes):
     assert e.value.code == bmg.BMG_EINVAL
 
 
-@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(krylov="fcg"), dict(smoother="tile0"),
-                                dict(coarsest=7)])
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(krylov="fcg"), dict(smoother="tile1"),
+                                dict(smoother="pair"), dict(smoother="line"), dict(coarsest=7)])
 def test_unsupported_options(bmg, kw):
     kind, planes, f, px, py = problem(63, "x")
     with pytest.raises(bmg.BmgError) as e:
@@ -169,7 +182,19 @@ def test_square_only_calls_refuse(bmg):
     assert bmg.lib.bmg_level_size(h._h, 0) == bmg.BMG_EINVAL
     out = ctypes.c_void_p()
     assert bmg.lib.bmg_batch_rhs(h._h, 2, None, ctypes.byref(out)) == bmg.BMG_EINVAL
-    assert bmg.lib.bmg_tuned_cluster(h._h, 0) == bmg.BMG_EINVAL
+    h.close()
+
+
+@pytest.mark.parametrize("smoother", ["auto", "rows", "tile"])
+def test_sweep_choice_is_reported(bmg, smoother):
+    kind, planes, f, px, py = problem(255, "xy")
+    h = hierarchy(bmg, kind, planes, "xy", smoother=smoother)
+    got = [h.tuned_cluster(l) for l in range(h.num_levels)]
+    assert got[-1] == 0
+    want = {"rows": 1, "tile": bmg.TILE_SWEEP}.get(smoother)
+    assert all(c == want if want else c in (1, bmg.TILE_SWEEP) for c in got[:-1])
+    with pytest.raises(bmg.BmgError):
+        h.tuned_cluster(h.num_levels)
     h.close()
 
 
@@ -189,14 +214,18 @@ def test_smallest_grid_is_one_direct_solve(bmg, axes):
     h.close()
 
 
-@pytest.mark.parametrize("nu1,nu2", [(1, 1), (0, 2), (3, 0)])
-def test_other_sweep_counts_bitwise(bmg, nu1, nu2):
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (0, 2), (3, 0), (2, 3)])
+@pytest.mark.parametrize("smoother", ["rows", "tile"])
+def test_other_sweep_counts_bitwise(bmg, nu1, nu2, smoother):
+    """Odd and even sweep counts: with strips the cycle alternates between two
+    iterates, and the interpolation writes the one from which the post-sweeps
+    end in x."""
     kind, planes, f, px, py = problem(63, "xy", seed=60)
     levels = pr.setup(kind, planes, px, py, arith="fused")
     x_o = np.zeros_like(f)
     for _ in range(3):
         pr.vcycle(levels, 0, x_o, f, nu1, nu2)
-    h = hierarchy(bmg, kind, planes, "xy", arith="fused", nu1=nu1, nu2=nu2)
+    h = hierarchy(bmg, kind, planes, "xy", arith="fused", nu1=nu1, nu2=nu2, smoother=smoother)
     x, it, _, _ = h.solve(torch.from_numpy(f).cuda(), tol=0.0, maxit=3)
     assert np.array_equal(interior(x.cpu().numpy()), interior(x_o))
     h.close()
