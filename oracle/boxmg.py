@@ -330,12 +330,54 @@ def line_sweep(kind: int, planes, x, f) -> None:
             xr[:, i] = d[:, i] - c[:, i] * xr[:, i + 1]
 
 
+def line_sweep_y(kind: int, planes, x, f) -> None:
+    """One zebra y-line Gauss-Seidel sweep: the odd columns, then the even
+    columns.  Each column i is solved exactly along y with the other columns
+    held fixed: the column's equations form a tridiagonal system with diagonal
+    a_O, sub-diagonal a_S and super-diagonal a_N, whose right-hand side is f
+    minus the couplings to columns i - 1 and i + 1 in the order W, E, SW, NE,
+    SE, NW (the x-line order S, N, SW, NE, NW, SE with the two axes exchanged).
+    The system is solved by the Thomas algorithm from j = 1 upward
+    (m_j = a_O - a_S c_{j-1}, c_j = a_N / m_j, d_j = (g_j - a_S d_{j-1}) / m_j,
+    then x_n = d_n, x_j = d_j - c_j x_{j+1}), one rounding per operation.
+    Columns of one parity share no coupling, so they are solved together."""
+    del kind   # the 5-point planes SW, NW are zero: their terms subtract exact zeros
+    n = size_of(x)
+    for first in (1, 2):                                 # odd columns, then even columns
+        cols = slice(first - 1, n, 2)                    # interior column index i - 1
+        g = at(f, 0, 0)[:, cols].copy()
+        for di, dj in ((-1, 0), (1, 0), (-1, -1), (1, 1), (1, -1), (-1, 1)):   # W, E, SW, NE, SE, NW
+            g = g - coupling(planes, di, dj)[:, cols] * at(x, di, dj)[:, cols]
+        aO = coupling(planes, 0, 0)[:, cols]
+        aS = coupling(planes, 0, -1)[:, cols]
+        aN = coupling(planes, 0, 1)[:, cols]
+        c = np.empty_like(g)
+        d = np.empty_like(g)
+        c[0] = aN[0] / aO[0]
+        d[0] = g[0] / aO[0]
+        for j in range(1, n):
+            m = aO[j] - aS[j] * c[j - 1]
+            c[j] = aN[j] / m
+            d[j] = (g[j] - aS[j] * d[j - 1]) / m
+        xc = at(x, 0, 0)[:, cols]                        # a view: written in place
+        xc[n - 1] = d[n - 1]
+        for j in range(n - 2, -1, -1):
+            xc[j] = d[j] - c[j] * xc[j + 1]
+
+
+LINE_SMOOTHERS = ("line", "yline", "xyline")
+
+
 def relax(lev, x, f, bands=None) -> None:
-    """One sweep of the level's smoother: point Gauss-Seidel (default) or
-    zebra x-line Gauss-Seidel."""
-    if getattr(lev, "smoother", "point") == "line":
+    """One sweep of the level's smoother: point Gauss-Seidel (default), zebra
+    x-line ("line") or y-line ("yline") Gauss-Seidel, or alternating lines
+    ("xyline": an x-line sweep, then a y-line sweep)."""
+    sm = getattr(lev, "smoother", "point")
+    if sm in ("line", "xyline"):
         line_sweep(lev.kind, lev.planes, x, f)
-    else:
+    if sm in ("yline", "xyline"):
+        line_sweep_y(lev.kind, lev.planes, x, f)
+    if sm not in LINE_SMOOTHERS:
         gs_sweep(lev.kind, lev.planes, lev.dinv, x, f, getattr(lev, "fused", False), bands)
 
 
@@ -597,11 +639,12 @@ def setup(kind: int, planes: np.ndarray, coarsest: int = 3, smoother: str = "poi
           arith: str = "rounded") -> list[Level]:
     """Build the hierarchy: Dendy P and Galerkin A_c level by level, then the
     Cholesky factor of the coarsest operator.  smoother: "point" (Gauss-Seidel
-    by colours) or "line" (zebra x-line Gauss-Seidel) on every level.  arith:
+    by colours), "line" (zebra x-line Gauss-Seidel), "yline" (zebra y-lines) or
+    "xyline" (an x-line then a y-line sweep per sweep) on every level.  arith:
     "rounded" (one rounding per operation) or "fused" (the cycle's
     multiply-adds fused, see the module notes); the setup itself is the same."""
-    if smoother not in ("point", "line"):
-        raise ValueError("smoother must be 'point' or 'line'")
+    if smoother not in ("point",) + LINE_SMOOTHERS:
+        raise ValueError("smoother must be 'point', 'line', 'yline' or 'xyline'")
     if arith not in ("rounded", "fused"):
         raise ValueError("arith must be 'rounded' or 'fused'")
     planes = np.array(planes, dtype=np.float64)

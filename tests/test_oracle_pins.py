@@ -672,3 +672,72 @@ def test_line_relaxation_handles_strong_x_coupling():
         k = min(len(hist) - 1, 8)
         factors[sm] = (hist[k] / hist[k - 3]) ** (1 / 3)
     assert factors["point"] > 0.9 and factors["line"] < 0.1, factors
+
+
+def transposed(planes):
+    """The stencil of the problem with x and y exchanged (point (i, j) becomes
+    (j, i)): W and S swap, SW stays, and B's NW coupling at (i, j) is A's SE
+    coupling at (j, i), which A stores as NW at (j + 1, i - 1)."""
+    O, W, S, SW, NW = planes
+    n = O.shape[0] - 2
+    nw = np.zeros_like(NW)
+    nw[0:n + 1, 1:n + 2] = NW[0:n + 1, 1:n + 2].T
+    return np.stack([O.T, S.T, W.T, SW.T, nw])
+
+
+@pytest.mark.parametrize("case", ["lognormal", "binary"])
+def test_yline_sweep_is_the_xline_sweep_of_the_transposed_problem(case):
+    """A y-line sweep on A equals, bit for bit, the x-line sweep (pinned above)
+    of the transposed problem, transposed back: the same operations on the
+    same operands with the axes exchanged."""
+    n = 31
+    kind, planes, f = (w.lognormal_problem(n, 2.0, 8.0, seed_k=4, seed_f=7) if case == "lognormal"
+                       else w.binary_contrast_problem(n, 4, seed_k=2, seed_f=3))
+    planes = bx.drop_ghost_couplings(np.array(planes))
+    x = w.rhs_uniform(n, 44)
+    xt = np.ascontiguousarray(x.T)
+    bx.line_sweep_y(kind, planes, x, f)
+    bx.line_sweep(kind, transposed(planes), xt, np.ascontiguousarray(f.T))
+    assert np.array_equal(x, xt.T)
+    # and the transposition itself: the residual of the transposed problem is the transposed
+    # residual (to rounding: the residual's term order is not symmetric in x and y)
+    r = bx.residual(planes, x, f)
+    rt = bx.residual(transposed(planes), xt, np.ascontiguousarray(f.T))
+    scale = 9 * np.abs(planes).max() * np.abs(x).max() + np.abs(f).max()
+    assert np.abs(bx.at(r, 0, 0) - bx.at(rt, 0, 0).T).max() <= 1e-14 * scale
+    assert np.abs(bx.at(r, 0, 0)).max() > 1e-3 * scale   # not trivially zero
+
+
+def test_yline_sweep_solves_columns_without_cross_coupling_exactly():
+    """With couplings along y only, A is block diagonal by columns and one
+    y-line sweep is a direct solve (dense LU)."""
+    n = 31
+    planes = transposed(_row_coupled_only(n, 41))
+    f = w.rhs_uniform(n, 42)
+    x = w.rhs_uniform(n, 43)
+    bx.line_sweep_y(5, planes, x, f)
+    A = sparse_A(planes).toarray()
+    xs = np.linalg.solve(A, bx.at(f, 0, 0).reshape(-1))
+    assert np.allclose(bx.at(x, 0, 0).reshape(-1), xs, rtol=1e-12, atol=1e-13)
+
+
+def test_line_directions_follow_the_anisotropy():
+    """-(eps u_xx + u_yy), eps = 1e-3 (the transposed x-anisotropy): point
+    Gauss-Seidel and x-lines stall, y-lines and alternating lines converge
+    fast; on -(u_xx + eps u_yy) alternating lines converge fast as well."""
+    n, eps = 63, 1e-3
+    px = w.anisotropic5(n, eps)
+    py = transposed(px)
+    f = w.rhs_uniform(n, 5)
+    factor = {}
+    for name, planes in (("y", py), ("x", px)):
+        for sm in ("point", "line", "yline", "xyline"):
+            if name == "x" and sm in ("point", "line"):
+                continue                                  # pinned by the x-line test above
+            levels = bx.setup(5, planes, smoother=sm)
+            x, hist = bx.solve(levels, f, tol=1e-12, maxit=30)
+            k = min(len(hist) - 1, 8)
+            factor[name, sm] = (hist[k] / hist[k - 3]) ** (1 / 3)
+    assert factor["y", "point"] > 0.9 and factor["y", "line"] > 0.9, factor
+    assert factor["y", "yline"] < 0.1 and factor["y", "xyline"] < 0.1, factor
+    assert factor["x", "yline"] > 0.9 and factor["x", "xyline"] < 0.1, factor
