@@ -189,6 +189,10 @@ typedef struct {
                                  single sweeps with one-pass shape 3 */
 #define BMG_SMOOTHER_LINE 12  /* zebra x-line Gauss-Seidel on every level (FP64 and FP32 cycles, single
                                  problems): odd rows, then even rows, each solved exactly along x */
+#define BMG_SMOOTHER_LINE_Y 13   /* zebra y-lines likewise: odd columns, then even columns, each solved
+                                    exactly along y (for operators coupled strongly along y) */
+#define BMG_SMOOTHER_LINE_XY 14  /* alternating lines: every sweep an x-line sweep, then a y-line sweep
+                                    (anisotropy along x in some regions and along y in others) */
 
 /* ---- whole solver ------------------------------------------------------ */
 
@@ -485,6 +489,15 @@ int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, i
  * BMG_ECUDA. */
 int bmg_relax_line(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
                    void* stream);
+
+/* Zebra y-line Gauss-Seidel (the same relaxation with the axes exchanged),
+ * `sweeps` sweeps in place on x: the odd columns, then the even columns, each
+ * solved exactly along y (Thomas algorithm from j = 1 upward, sub-diagonal
+ * a_S, super-diagonal a_N) with the other columns held fixed; the couplings
+ * to columns i - 1, i + 1 move to the right-hand side in the order W, E, SW,
+ * NE, SE, NW.  Arguments, scratch and errors as bmg_relax_line. */
+int bmg_relax_line_y(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
+                     void* stream);
 
 /* f_c = P^T (f - A x) with the Fig. 2 restriction (Fig. 1 "Residual",
  * "Restrict"); fc: out, (n_c+2)^2, interior written, ghost ring zeroed. */

@@ -51,7 +51,8 @@ _FUSE = {"auto": 0, "off": 1, "on": 2}
 _RHS_BLOCK = {"auto": 0, "off": 1, 2: 2, 4: 4}
 # Gauss-Seidel kernel of the FP32 cycle's 9-point levels (all compute the same bits)
 _SMOOTHER = {"auto": 0, "rows": 1, "tile": 2, **{f"tile{k}": 2 + k for k in range(6)},
-             "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12}
+             "pair": 8, **{f"pair{k}": 8 + k for k in range(4)}, "line": 12, "yline": 13,
+             "xyline": 14}
 TILE_SWEEP = 16   # bmg_tuned_cluster value of tile shape 0 (shape s: 16 + s)
 # cycle arithmetic: one rounding per operation, or fused multiply-adds
 _ARITH = {"rounded": 0, "fused": 1}
@@ -84,6 +85,7 @@ _sig = {
     "bmg_rap": (I, [I, P, P, P, P]),
     "bmg_relax": (I, [I, I, P, P, P, I, P]),
     "bmg_relax_line": (I, [I, I, P, P, P, P, I, P]),
+    "bmg_relax_line_y": (I, [I, I, P, P, P, P, I, P]),
     "bmg_resid_restrict": (I, [I, I, P, P, P, P, P, P]),
     "bmg_interp_correct": (I, [I, P, P, P, P]),
     "bmg_residual": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
@@ -545,11 +547,14 @@ def relax(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweep
     return x
 
 
-def relax_line(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1) -> torch.Tensor:
-    """Zebra x-line Gauss-Seidel sweeps in place on x (bmg_relax_line)."""
+def relax_line(kind: int, coef: torch.Tensor, f: torch.Tensor, x: torch.Tensor, sweeps: int = 1,
+               axis: str = "x") -> torch.Tensor:
+    """Zebra line Gauss-Seidel sweeps in place on x: x-lines (bmg_relax_line)
+    or y-lines (axis="y", bmg_relax_line_y)."""
     _need_level(kind, coef, f, x)
     work = torch.empty_like(x)
-    _check(lib.bmg_relax_line(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), _ptr(work), sweeps, _stream()))
+    fn = {"x": lib.bmg_relax_line, "y": lib.bmg_relax_line_y}[axis]
+    _check(fn(_n_of(coef), kind, _ptr(coef), _ptr(f), _ptr(x), _ptr(work), sweeps, _stream()))
     return x
 
 

@@ -49,6 +49,12 @@ struct Range {
 };
 
 namespace {
+// Line smoothers: BMG_SMOOTHER_LINE (x-lines), _LINE_Y, _LINE_XY (alternating).
+bool is_line(int smoother) { return smoother >= BMG_SMOOTHER_LINE && smoother <= BMG_SMOOTHER_LINE_XY; }
+int line_dir(int smoother) {
+  return smoother == BMG_SMOOTHER_LINE_Y ? LINE_Y : smoother == BMG_SMOOTHER_LINE_XY ? LINE_XY : LINE_X;
+}
+
 bool alloc_fault() {
   static std::mutex mu;
   static std::string seen;
@@ -284,8 +290,9 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
   // the interpolation writes the array from which nu2 sweeps end in x.
   double* cur = x;
   auto relax64 = [&](int sweeps) {
-    if (h->smoother == BMG_SMOOTHER_LINE)
-      step(h, l, BMG_K_RELAX, 0, [&] { launch_line<double, double>(v, L.kind, f, x, L.lcp, sweeps, done, s); });
+    if (is_line(h->smoother))
+      step(h, l, BMG_K_RELAX, 0,
+           [&] { launch_line<double, double>(v, L.kind, f, x, L.lcp, sweeps, line_dir(h->smoother), done, s); });
     else if (L.tile64 >= 0)
       for (int k = 0; k < sweeps; ++k) {
         double* nxt = cur == x ? L.x64b : x;
@@ -309,9 +316,11 @@ void vcycle64(bmg_hierarchy* h, int l, double* x, const double* f, const int* do
 template <typename S>
 void relax32(bmg_hierarchy* h, const StencilView<float, S>& v, int l, int sweeps, float** cur, const int* done) {
   Level& L = h->lv[l];
-  if (h->smoother == BMG_SMOOTHER_LINE) {
-    step(h, l, BMG_K_RELAX, 1,
-         [&] { launch_line<float, S>(v, L.kind, (const float*)L.f32, L.x32, L.lcp32, sweeps, done, h->ws); });
+  if (is_line(h->smoother)) {
+    step(h, l, BMG_K_RELAX, 1, [&] {
+      launch_line<float, S>(v, L.kind, (const float*)L.f32, L.x32, L.lcp32, sweeps, line_dir(h->smoother), done,
+                            h->ws);
+    });
     return;
   }
   if (L.tile32 < 0) {
@@ -810,7 +819,7 @@ int force_tile(bmg_hierarchy* h) {
   return BMG_OK;
 }
 
-// BMG_SMOOTHER_LINE: the multiplier scratch of every relaxed level.
+// BMG_SMOOTHER_LINE / _LINE_Y / _LINE_XY: the multiplier scratch of every relaxed level.
 int alloc_line(bmg_hierarchy* h) {
   for (int l = 0; l + 1 < h->nlev; ++l) {
     Level& L = h->lv[l];
@@ -1320,12 +1329,12 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   }
   if (h->smoother < BMG_SMOOTHER_AUTO ||
       (h->smoother >= BMG_SMOOTHER_TILE + GS_TILE_SHAPES && h->smoother < BMG_SMOOTHER_PAIR) ||
-      (h->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES && h->smoother != BMG_SMOOTHER_LINE)) {
+      (h->smoother >= BMG_SMOOTHER_PAIR + GS_PAIR_SHAPES && !is_line(h->smoother))) {
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: bad smoother %d", h->smoother);
   }
   if (h->precision == BMG_FP64 && h->smoother >= BMG_SMOOTHER_TILE + GS_TILE64_SHAPES &&
-      h->smoother != BMG_SMOOTHER_LINE) {
+      !is_line(h->smoother)) {
     int sm = h->smoother;
     delete h;
     return set_error(BMG_EINVAL, "bmg_setup: smoother %d has no FP64 kernel (tile0 .. tile3 do)", sm);
@@ -1344,7 +1353,7 @@ int bmg_setup(const bmg_stencil* A, int nx, int ny, const bmg_opts* o, bmg_hiera
   if (!rc) rc = cuda_check(host_malloc((void**)&h->ctl_host, sizeof(Ctl)), "pinned");
   if (!rc) rc = order_after_user(h);
   if (!rc) rc = setup_impl(h, A, h->n, o);
-  const bool line = h->smoother == BMG_SMOOTHER_LINE;
+  const bool line = is_line(h->smoother);
   if (!rc && line) rc = alloc_line(h);
   if (!rc && !line && h->smoother >= BMG_SMOOTHER_TILE) rc = force_tile(h);
   if (!rc && !line && h->use_graph) rc = autotune_solo(h);
@@ -1708,8 +1717,17 @@ int bmg_relax_line(int n, int kind, const double* coef, const double* f, double*
   if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !f || !x || !work || sweeps < 0)
     return set_error(BMG_EINVAL, "bmg_relax_line: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
-  launch_line<double, double>(raw_view(n, coef, false), kind, f, x, work, sweeps, (const int*)nullptr, s);
+  launch_line<double, double>(raw_view(n, coef, false), kind, f, x, work, sweeps, LINE_X, (const int*)nullptr, s);
   return step_done(s, "bmg_relax_line");
+}
+
+int bmg_relax_line_y(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
+                     void* stream) {
+  if (!is_level_size(n) || (kind != 5 && kind != 9) || !coef || !f || !x || !work || sweeps < 0)
+    return set_error(BMG_EINVAL, "bmg_relax_line_y: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_line<double, double>(raw_view(n, coef, false), kind, f, x, work, sweeps, LINE_Y, (const int*)nullptr, s);
+  return step_done(s, "bmg_relax_line_y");
 }
 
 int bmg_resid_restrict(int n, int kind, const double* coef, const double* ci, const double* x, const double* f,
@@ -2390,7 +2408,7 @@ int batch_init(bmg_batch* B, const bmg_opts* o, bmg_opts* so) {
   so->use_graph = 0;
   so->smoother = BMG_SMOOTHER_AUTO;
   if (o) B->smoother = o->smoother;
-  if (B->smoother == BMG_SMOOTHER_LINE)
+  if (is_line(B->smoother))
     return set_error(BMG_EINVAL, "batched solves: line relaxation is available for single problems only");
   if (B->smoother < BMG_SMOOTHER_AUTO ||
       (B->smoother >= BMG_SMOOTHER_TILE + 4 && B->smoother < BMG_SMOOTHER_PAIR) ||

@@ -191,6 +191,44 @@ __device__ __forceinline__ void line_row_body(const StencilView<T, S>& v, const 
   }
 }
 
+// Column i of a zebra y-line sweep: the x-line solve with the axes exchanged.
+// Right-hand side f minus the couplings to columns i - 1, i + 1 in the order
+// W, E, SW, NE, SE, NW; Thomas elimination from j = 1 upward with sub-diagonal
+// a_S and super-diagonal a_N, then back substitution; one rounding per operation.
+template <typename T, typename S, bool NINE>
+__device__ __forceinline__ void line_col_body(const StencilView<T, S>& v, const T* __restrict__ f, T* x,
+                                              T* __restrict__ cp, int i) {
+  const int n = v.n, ld = v.ld;
+  T c = T(0), d = T(0);
+  for (int j = 1; j <= n; ++j) {
+    const size_t p = (size_t)j * ld + i;
+    T g = f[p];
+    g = rsub(g, rmul(cvt<T>(v.W[p]), x[p - 1]));
+    g = rsub(g, rmul(cvt<T>(v.W[p + 1]), x[p + 1]));
+    if (NINE) {
+      g = rsub(g, rmul(cvt<T>(v.SW[p]), x[p - ld - 1]));
+      g = rsub(g, rmul(cvt<T>(v.SW[p + ld + 1]), x[p + ld + 1]));
+      g = rsub(g, rmul(cvt<T>(v.NW[p + 1 - ld]), x[p + 1 - ld]));
+      g = rsub(g, rmul(cvt<T>(v.NW[p]), x[p + ld - 1]));
+    }
+    const T aO = v.O[p], aS = cvt<T>(v.S_[p]), aN = cvt<T>(v.S_[p + ld]);
+    if (j == 1) {
+      c = rdiv(aN, aO);
+      d = rdiv(g, aO);
+    } else {
+      const T m = rsub(aO, rmul(aS, c));
+      c = rdiv(aN, m);
+      d = rdiv(rsub(g, rmul(aS, d)), m);
+    }
+    cp[p] = c;
+    x[p] = d;
+  }
+  for (int j = n - 1; j >= 1; --j) {
+    const size_t p = (size_t)j * ld + i;
+    x[p] = rsub(x[p], rmul(cp[p], x[p + ld]));
+  }
+}
+
 // Red-black half sweep for 5-point stencils: the points with (i + j) % 2 == c
 // (c = 0 red, c = 1 black), which share no coupling.  Thread grid: x over the
 // points of a row, y over rows.

@@ -143,6 +143,17 @@ __global__ void k_line_rows(StencilView<T, S> v, const T* __restrict__ f, T* x, 
   line_row_body<T, S, NINE>(v, f, x, cp, j);
 }
 
+// Zebra y-lines: one thread per column of the parity (first column 1 or 2).
+template <typename T, typename S, bool NINE>
+__global__ void k_line_cols(StencilView<T, S> v, const T* __restrict__ f, T* x, T* __restrict__ cp, int first,
+                            const int* done) {
+  pdl_enter();
+  if (stopped(done)) return;
+  const int i = first + 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i > v.n) return;
+  line_col_body<T, S, NINE>(v, f, x, cp, i);
+}
+
 template <typename T, typename S, bool NINE, bool FU>
 __global__ void __launch_bounds__(TXC* TYC) k_resid_restrict(StencilView<T, S> v, const T* __restrict__ ci,
                                                             const T* __restrict__ x, const T* __restrict__ f,
@@ -534,27 +545,34 @@ int strip_timeouts() {
 }
 
 template <typename T, typename S>
-void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, const int* done,
-                 cudaStream_t s) {
+void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, int dir,
+                 const int* done, cudaStream_t s) {
   constexpr int TPB = 64;
   for (int k = 0; k < sweeps; ++k)
-    for (int first = 1; first <= 2; ++first) {           // odd rows, then even rows
-      const int rows = first == 1 ? (v.n + 1) / 2 : (v.n - 1) / 2;
-      if (rows <= 0) continue;
-      const unsigned g = (unsigned)((rows + TPB - 1) / TPB);
-      if (kind == 9)
-        pdl_launch(k_line_rows<T, S, true>, g, TPB, 0, s, v, f, x, cp, first, done);
-      else
-        pdl_launch(k_line_rows<T, S, false>, g, TPB, 0, s, v, f, x, cp, first, done);
-      count_launch();
+    for (int axis = 0; axis <= 1; ++axis) {               // x-lines (rows), then y-lines (columns)
+      if ((axis == 0 && dir == LINE_Y) || (axis == 1 && dir == LINE_X)) continue;
+      for (int first = 1; first <= 2; ++first) {          // odd lines, then even lines
+        const int lines = first == 1 ? (v.n + 1) / 2 : (v.n - 1) / 2;
+        if (lines <= 0) continue;
+        const unsigned g = (unsigned)((lines + TPB - 1) / TPB);
+        if (axis == 0 && kind == 9)
+          pdl_launch(k_line_rows<T, S, true>, g, TPB, 0, s, v, f, x, cp, first, done);
+        else if (axis == 0)
+          pdl_launch(k_line_rows<T, S, false>, g, TPB, 0, s, v, f, x, cp, first, done);
+        else if (kind == 9)
+          pdl_launch(k_line_cols<T, S, true>, g, TPB, 0, s, v, f, x, cp, first, done);
+        else
+          pdl_launch(k_line_cols<T, S, false>, g, TPB, 0, s, v, f, x, cp, first, done);
+        count_launch();
+      }
     }
 }
 template void launch_line<double, double>(const StencilView<double, double>&, int, const double*, double*, double*,
-                                          int, const int*, cudaStream_t);
+                                          int, int, const int*, cudaStream_t);
 template void launch_line<float, float>(const StencilView<float, float>&, int, const float*, float*, float*, int,
-                                        const int*, cudaStream_t);
+                                        int, const int*, cudaStream_t);
 template void launch_line<float, __nv_bfloat16>(const StencilView<float, __nv_bfloat16>&, int, const float*, float*,
-                                                float*, int, const int*, cudaStream_t);
+                                                float*, int, int, const int*, cudaStream_t);
 
 template <typename T>
 void launch_interp_correct(int n, const T* ci, const T* ec, T* x, const int* done, cudaStream_t s, int fused) {

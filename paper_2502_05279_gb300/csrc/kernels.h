@@ -53,12 +53,14 @@ constexpr int PK_WORDS_F32 = 5, PK_WORDS_BF16 = 3;
 template <typename T, typename S>
 void launch_gs(const StencilView<T, S>& v, int kind, const T* f, T* x, int sweeps, const int* done, cudaStream_t s,
                int cl = 0);   // cl: row-kernel cluster size, 0 = the smallest that covers a row
-// Zebra x-line Gauss-Seidel sweeps (odd rows, then even rows, each solved
-// exactly along x); cp: scratch of the level's (n+2)^2 layout for the
-// elimination multipliers.
+// Zebra line Gauss-Seidel sweeps: dir LINE_X (odd rows, then even rows, each
+// solved exactly along x), LINE_Y (odd columns, then even columns, each solved
+// exactly along y) or LINE_XY (an x-line sweep, then a y-line sweep); cp:
+// scratch of the level's (n+2)^2 layout for the elimination multipliers.
+enum { LINE_X = 0, LINE_Y = 1, LINE_XY = 2 };
 template <typename T, typename S>
-void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, const int* done,
-                 cudaStream_t s);
+void launch_line(const StencilView<T, S>& v, int kind, const T* f, T* x, T* cp, int sweeps, int dir,
+                 const int* done, cudaStream_t s);
 // FP32 / BF16 level arrays are allocated with STRIP_GUARD zeroed elements
 // before and after each array (plane), every array starting on a 256-byte
 // boundary; planes of one level are plane_stride32(n) elements apart.  The

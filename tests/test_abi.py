@@ -52,7 +52,7 @@ def test_binding_imports_and_reports_errors_without_gpu(libpath):
         assert bmg.lib.bmg_setup(ctypes.byref(st), nx, ny, None, ctypes.byref(h)) == bmg._lib.BMG_EINVAL
         assert "outside" in bmg.lib.bmg_last_error().decode()
     o = bmg._lib.Opts()
-    for bad in (13, 99, -1):   # valid: 0 auto, 1 rows, 2 .. 7 one-pass, 8 .. 11 two-sweep shapes, 12 lines
+    for bad in (15, 99, -1):   # valid: 0 auto, 1 rows, 2 .. 7 one-pass, 8 .. 11 two-sweep shapes, 12 .. 14 lines
         o.smoother = bad
         assert bmg.lib.bmg_setup(ctypes.byref(st), 127, 127, ctypes.byref(o), ctypes.byref(h)) == bmg._lib.BMG_EINVAL
         assert "smoother" in bmg.lib.bmg_last_error().decode()

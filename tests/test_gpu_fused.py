@@ -93,12 +93,13 @@ def test_fused_one_pass_kernels_bitwise(bmg, precision, nbf, smoother):
 
 
 @pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0)])
-def test_fused_line_relaxation_solve_bitwise(bmg, precision, nbf):
+@pytest.mark.parametrize("smoother", ["line", "xyline"])
+def test_fused_line_relaxation_solve_bitwise(bmg, precision, nbf, smoother):
     """Line relaxation keeps its own (rounded) arithmetic; the residual,
     restriction and interpolation around it are fused."""
     kind, planes, f = 5, w.anisotropic5(127, 0.01), w.rhs_uniform(127, 1)
-    xw, hw = oracle_solve(kind, planes, f, precision, nbf, smoother="line")
-    h = bmg.Hierarchy(kind, dev(planes[:3]), precision=precision, smoother="line", arith="fused")
+    xw, hw = oracle_solve(kind, planes, f, precision, nbf, smoother=smoother)
+    h = bmg.Hierarchy(kind, dev(planes[:3]), precision=precision, smoother=smoother, arith="fused")
     x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=200)
     assert ok and it == len(hw) - 1
     assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))

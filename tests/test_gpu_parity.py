@@ -628,34 +628,41 @@ def test_bounded_wait_gives_up_and_context_stays_usable(bmg):
     h.close()
 
 
-# ---- zebra x-line relaxation ---------------------------------------------------------------
+# ---- zebra line relaxation (x-lines, y-lines, alternating) ---------------------------------
 
 def line_problem(case, n):
-    if case == "aniso":
+    if case == "aniso":                                   # -(u_xx + eps u_yy)
         return 5, w.anisotropic5(n, 1e-3), w.rhs_uniform(n, 5)
+    if case == "anisoy":                                  # -(eps u_xx + u_yy)
+        return 5, w.transposed_stencil(w.anisotropic5(n, 1e-3)), w.rhs_uniform(n, 5)
     return problem(case, n)
 
 
-@pytest.mark.parametrize("case,n", [("poisson", 63), ("lognormal", 255), ("binary", 127), ("aniso", 127)])
+@pytest.mark.parametrize("case,n", [("poisson", 63), ("lognormal", 255), ("binary", 127), ("aniso", 127),
+                                    ("anisoy", 127)])
 @pytest.mark.parametrize("sweeps", [1, 2])
-def test_line_relax_step_bitwise(bmg, case, n, sweeps):
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_line_relax_step_bitwise(bmg, case, n, sweeps, axis):
     kind, planes, f = line_problem(case, n)
     planes = bx.drop_ghost_couplings(np.array(planes))
     x0 = w.rhs_uniform(n, 98)
     want = x0.copy()
     for _ in range(sweeps):
-        bx.line_sweep(kind, planes, want, f)
-    got = host(bmg.relax_line(kind, dev(planes[:3] if kind == 5 else planes), dev(f), dev(x0), sweeps))
+        (bx.line_sweep if axis == "x" else bx.line_sweep_y)(kind, planes, want, f)
+    got = host(bmg.relax_line(kind, dev(planes[:3] if kind == 5 else planes), dev(f), dev(x0), sweeps, axis=axis))
     assert np.array_equal(bx.at(got, 0, 0), bx.at(want, 0, 0))
 
 
-@pytest.mark.parametrize("case,n", [("aniso", 127), ("lognormal", 255), ("binary", 127)])
+@pytest.mark.parametrize("smoother,case,n", [("line", "aniso", 127), ("line", "lognormal", 255),
+                                             ("line", "binary", 127), ("yline", "anisoy", 127),
+                                             ("yline", "lognormal", 255), ("xyline", "aniso", 127),
+                                             ("xyline", "anisoy", 127), ("xyline", "binary", 127)])
 @pytest.mark.parametrize("graph", [True, False])
-def test_line_solve_matches_oracle(bmg, case, n, graph):
+def test_line_solve_matches_oracle(bmg, smoother, case, n, graph):
     kind, planes, f = line_problem(case, n)
-    levels = bx.setup(kind, planes, smoother="line")
+    levels = bx.setup(kind, planes, smoother=smoother)
     xw, hw = bx.solve(levels, f, tol=1e-10, maxit=100)
-    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), smoother="line", use_graph=graph)
+    h = bmg.Hierarchy(kind, dev(planes[:3] if kind == 5 else planes), smoother=smoother, use_graph=graph)
     x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
     assert ok and it == len(hw) - 1
     assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
@@ -664,19 +671,20 @@ def test_line_solve_matches_oracle(bmg, case, n, graph):
 
 
 @pytest.mark.parametrize("precision,nbf", [("fp32", 0), ("bf16", 2)])
-def test_line_refinement_and_fcg_match_oracle(bmg, precision, nbf):
-    kind, planes, f = line_problem("aniso", 127)
-    levels = bx.setup(kind, planes, smoother="line")
+@pytest.mark.parametrize("smoother,case", [("line", "aniso"), ("yline", "anisoy"), ("xyline", "anisoy")])
+def test_line_refinement_and_fcg_match_oracle(bmg, precision, nbf, smoother, case):
+    kind, planes, f = line_problem(case, 127)
+    levels = bx.setup(kind, planes, smoother=smoother)
     xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), f, tol=1e-10, maxit=100)
-    h = bmg.Hierarchy(kind, dev(planes[:3]), precision=precision, smoother="line")
+    h = bmg.Hierarchy(kind, dev(planes[:3]), precision=precision, smoother=smoother)
     x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
     assert ok and it == len(hw) - 1
     assert np.array_equal(bx.at(host(x), 0, 0), bx.at(xw, 0, 0))
     check_history(h.history(), hw)
     h.close()
     kind, planes, f = line_problem("lognormal", 127)
-    levels = bx.setup(kind, planes, smoother="line")
-    h = bmg.Hierarchy(kind, dev(planes), smoother="line", krylov="fcg")
+    levels = bx.setup(kind, planes, smoother=smoother)
+    h = bmg.Hierarchy(kind, dev(planes), smoother=smoother, krylov="fcg")
     x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
     assert ok
     check_fcg(x, h.history(), bx.solve_fcg(levels, f, tol=1e-10, maxit=100),
@@ -684,17 +692,25 @@ def test_line_refinement_and_fcg_match_oracle(bmg, precision, nbf):
     h.close()
 
 
-def test_line_relaxation_solves_anisotropy_point_gs_does_not(bmg):
-    kind, planes, f = line_problem("aniso", 255)
+@pytest.mark.parametrize("case", ["aniso", "anisoy"])
+def test_line_relaxation_solves_anisotropy_point_gs_does_not(bmg, case):
+    """Lines along the strong coupling (x-lines for aniso, y-lines for anisoy)
+    and alternating lines converge in a few cycles; point Gauss-Seidel and
+    lines across the strong coupling do not."""
+    kind, planes, f = line_problem(case, 255)
     its = {}
-    for sm in ("auto", "line"):
+    for sm in ("auto", "line", "yline", "xyline"):
         h = bmg.Hierarchy(kind, dev(planes[:3]), smoother=sm)
         x, it, rr, ok = h.solve(dev(f), tol=1e-8, maxit=60)
         its[sm] = (it, ok)
         h.close()
-    assert its["line"][1] and its["line"][0] <= 10 and not its["auto"][1], its
-    with pytest.raises(bmg.BmgError):
-        bmg.Batch(5, [dev(planes[:3])], smoother="line")
+    along, across = ("line", "yline") if case == "aniso" else ("yline", "line")
+    for sm in (along, "xyline"):
+        assert its[sm][1] and its[sm][0] <= 10, its
+    assert not its["auto"][1] and not its[across][1], its
+    for sm in ("line", "yline", "xyline"):
+        with pytest.raises(bmg.BmgError):
+            bmg.Batch(5, [dev(planes[:3])], smoother=sm)
 
 
 @pytest.mark.parametrize("coarsest", [7, 15])

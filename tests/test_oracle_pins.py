@@ -674,15 +674,7 @@ def test_line_relaxation_handles_strong_x_coupling():
     assert factors["point"] > 0.9 and factors["line"] < 0.1, factors
 
 
-def transposed(planes):
-    """The stencil of the problem with x and y exchanged (point (i, j) becomes
-    (j, i)): W and S swap, SW stays, and B's NW coupling at (i, j) is A's SE
-    coupling at (j, i), which A stores as NW at (j + 1, i - 1)."""
-    O, W, S, SW, NW = planes
-    n = O.shape[0] - 2
-    nw = np.zeros_like(NW)
-    nw[0:n + 1, 1:n + 2] = NW[0:n + 1, 1:n + 2].T
-    return np.stack([O.T, S.T, W.T, SW.T, nw])
+transposed = w.transposed_stencil
 
 
 @pytest.mark.parametrize("case", ["lognormal", "binary"])

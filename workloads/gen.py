@@ -126,6 +126,18 @@ def anisotropic5(n: int, eps: float) -> np.ndarray:
     return zero_ghost_couplings(planes)
 
 
+def transposed_stencil(planes: np.ndarray) -> np.ndarray:
+    """The planes of the same operator with x and y exchanged (point (i, j)
+    becomes (j, i)), for square planes: W and S swap and SW stays (each
+    transposed); the new NW coupling at (i, j) is the old SE coupling at
+    (j, i), which the old planes store as NW at (j + 1, i - 1)."""
+    O, W, S, SW, NW = planes
+    n = O.shape[0] - 2
+    nw = np.zeros_like(NW)
+    nw[0:n + 1, 1:n + 2] = NW[0:n + 1, 1:n + 2].T
+    return np.stack([O.T, S.T, W.T, SW.T, nw])
+
+
 def fe9_from_cells(k: np.ndarray) -> np.ndarray:
     """9-point bilinear (Q1) finite-element stiffness stencil of -div(k grad u)
     on a uniform grid, with k constant on each cell.
