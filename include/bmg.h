@@ -101,7 +101,8 @@ enum {
                            diagonal, or a zero / non-finite interpolation denominator */
   BMG_ENAN = -5,        /* the residual norm became NaN or Inf */
   BMG_ENOTCONV = -6,    /* maxit cycles ran without reaching tol; x holds the last iterate */
-  BMG_ETIMEOUT = -7     /* a bounded device-side wait gave up */
+  BMG_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
+  BMG_EBOUNDS = -8      /* debug builds only: a device bounds check failed (bmg_debug_take) */
 };
 
 enum { BMG_FP64 = 0, BMG_FP32_IR = 1, BMG_BF16_IR = 2 };
@@ -489,6 +490,31 @@ int bmg_relax(int n, int kind, const double* coef, const double* f, double* x, i
  * BMG_ECUDA. */
 int bmg_relax_line(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
                    void* stream);
+
+/* ---- debug build ------------------------------------------------------- */
+/* libbmg_debug.so (the same sources compiled with -DBMG_DEBUG) checks, in its
+ * kernels, the index of each global store and the source range of each
+ * asynchronous row copy against the logical extent of the level array it
+ * addresses (the (n+2)^2 points of a level, the guard bands of FP32 arrays
+ * included for copies).  A failed check does not trap: the store is skipped
+ * (a copy is zero-filled, or reads the array's first element so that its
+ * transaction completes) and the first failure of each source file is
+ * recorded.  bmg_solve, bmg_solve_batched, bmg_time_cycles, bmg_profile,
+ * bmg_inner_cycle and the single-kernel entry points then return BMG_EBOUNDS
+ * until the record is taken.  compute-sanitizer is not needed for it; the
+ * release library compiles every check to the constant true. */
+int bmg_debug_build(void);   /* 1 for libbmg_debug.so, 0 for libbmg.so */
+/* The first failure recorded since the last call (the device is synchronized
+ * first): returns 1 and fills site (a kernel family, bmg_debug_site_name),
+ * index and extent, or returns 0 when there is none; then clears the records.
+ * Release builds return 0. */
+int bmg_debug_take(int* site, long long* index, long long* extent);
+const char* bmg_debug_site_name(int site);
+/* Test hook (debug builds; BMG_EINVAL in release builds): every later check
+ * uses extent - k, so that accesses to the last k elements of each array
+ * count as outside and are skipped; none of them leaves its array.  k = 0
+ * restores the exact extents. */
+int bmg_debug_shrink(long long k);
 
 /* Zebra y-line Gauss-Seidel (the same relaxation with the axes exchanged),
  * `sweeps` sweeps in place on x: the odd columns, then the even columns, each

@@ -1,5 +1,7 @@
 """ctypes binding of libbmg.so.  Argument marshalling only: every step of the
-solver runs in the library's CUDA kernels.
+solver runs in the library's CUDA kernels.  With the environment variable
+BMG_LIB=debug at import the binding loads libbmg_debug.so instead (the same
+library with device bounds checks, built by build.build(debug=True)).
 
 Tensors passed in must be contiguous CUDA tensors of the documented dtype and
 shape; work is enqueued on torch's current CUDA stream, with which the library
@@ -13,9 +15,10 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-library_path = os.path.join(_HERE, "libbmg.so")
+library_path = os.path.join(_HERE, "libbmg_debug.so" if os.environ.get("BMG_LIB") == "debug" else "libbmg.so")
 
 BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ESINGULAR, BMG_ENAN, BMG_ENOTCONV, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+BMG_EBOUNDS = -8
 BMG_FP64, BMG_FP32_IR, BMG_BF16_IR = 0, 1, 2
 BMG_PERIODIC_X, BMG_PERIODIC_Y = 1, 2
 _PREC = {"fp64": BMG_FP64, "fp32": BMG_FP32_IR, "bf16": BMG_BF16_IR}
@@ -29,7 +32,7 @@ class BmgError(RuntimeError):
 
 if not os.path.exists(library_path):
     raise ImportError(f"{library_path} is missing: build it with paper_2502_05279_gb300.build.build() "
-                      "(there is no CPU fallback)")
+                      "(debug=True for libbmg_debug.so; there is no CPU fallback)")
 lib = ctypes.CDLL(library_path)
 
 
@@ -86,6 +89,10 @@ _sig = {
     "bmg_relax": (I, [I, I, P, P, P, I, P]),
     "bmg_relax_line": (I, [I, I, P, P, P, P, I, P]),
     "bmg_relax_line_y": (I, [I, I, P, P, P, P, I, P]),
+    "bmg_debug_build": (I, []),
+    "bmg_debug_take": (I, [ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "bmg_debug_site_name": (ctypes.c_char_p, [I]),
+    "bmg_debug_shrink": (I, [ctypes.c_longlong]),
     "bmg_resid_restrict": (I, [I, I, P, P, P, P, P, P]),
     "bmg_interp_correct": (I, [I, P, P, P, P]),
     "bmg_residual": (I, [I, I, P, P, P, P, ctypes.POINTER(D), P]),
@@ -609,3 +616,23 @@ def measure_fp64_rate() -> float:
     v = ctypes.c_double(0.0)
     _check(lib.bmg_measure_fp64_rate(ctypes.byref(v), _stream()))
     return v.value
+
+
+def debug_build() -> bool:
+    """True when the loaded library is libbmg_debug.so (bmg_debug_build)."""
+    return bool(lib.bmg_debug_build())
+
+
+def debug_take():
+    """The first device bounds-check failure recorded since the last call, as
+    (site name, index, extent), or None; clears the records (bmg_debug_take)."""
+    site, index, extent = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    rc = _check_size(lib.bmg_debug_take(ctypes.byref(site), ctypes.byref(index), ctypes.byref(extent)))
+    if rc == 0:
+        return None
+    return lib.bmg_debug_site_name(site.value).decode(), index.value, extent.value
+
+
+def debug_shrink(k: int) -> None:
+    """Test hook of debug builds: checks use extent - k (bmg_debug_shrink)."""
+    _check(lib.bmg_debug_shrink(k))

@@ -87,10 +87,64 @@ cudaError_t host_malloc(void** p, size_t bytes) {
   return cudaMallocHost(p, bytes);
 }
 
+// ---- debug builds: the bounds-check records of every translation unit ----
+#ifdef BMG_DEBUG
+std::vector<DbgHooks>& dbg_hooks() {
+  static std::vector<DbgHooks> v;
+  return v;
+}
+void dbg_register(DbgHooks h) { dbg_hooks().push_back(h); }
+
+// The first failed check recorded by any translation unit (hit = 0: none);
+// clear: reset every record.
+static cudaError_t dbg_collect(DbgRecord* first, bool clear) {
+  *first = DbgRecord{0, 0, 0, 0};
+  for (const DbgHooks& h : dbg_hooks()) {
+    DbgRecord r;
+    const cudaError_t e = h.take(&r, clear);
+    if (e != cudaSuccess) return e;
+    if (r.hit && !first->hit) *first = r;
+  }
+  return cudaSuccess;
+}
+#endif
+
+const char* dbg_site_name(int site) {
+  static const char* names[DBG_SITES] = {"none",
+                                         "point Gauss-Seidel store",
+                                         "strip sweep store",
+                                         "FP64 strip row copy",
+                                         "FP32 strip row copy",
+                                         "restriction store",
+                                         "interpolation store",
+                                         "residual store",
+                                         "line relaxation store",
+                                         "refinement / FCG store",
+                                         "periodic-sides kernel"};
+  return site >= 0 && site < DBG_SITES ? names[site] : "unknown";
+}
+
+// BMG_EBOUNDS when a debug build's bounds check failed since the last
+// bmg_debug_take (the record stays until it is taken); BMG_OK otherwise and
+// always in release builds.
+int debug_check(const char* where) {
+#ifdef BMG_DEBUG
+  DbgRecord r;
+  if (cudaDeviceSynchronize() != cudaSuccess || dbg_collect(&r, false) != cudaSuccess)
+    return set_error(BMG_ECUDA, "%s: reading the debug bounds records failed", where);
+  if (r.hit)
+    return set_error(BMG_EBOUNDS, "%s: debug bounds check failed: %s, index %lld outside [0, %lld)", where,
+                     dbg_site_name(r.site), r.index, r.extent);
+#else
+  (void)where;
+#endif
+  return BMG_OK;
+}
+
 // BMG_ETIMEOUT when a one-pass sweep gave up on its bulk copies since the last check.
 int timeout_check(const char* where) {
   if (strip_timeouts()) return set_error(BMG_ETIMEOUT, "%s: a one-pass sweep timed out waiting for its copies", where);
-  return BMG_OK;
+  return debug_check(where);
 }
 
 int cuda_check(cudaError_t e, const char* what) {
@@ -1242,6 +1296,7 @@ const char* bmg_strerror(int code) {
     case BMG_ENAN: return "residual is NaN or Inf";
     case BMG_ENOTCONV: return "not converged within maxit";
     case BMG_ETIMEOUT: return "device wait timed out";
+    case BMG_EBOUNDS: return "debug bounds check failed";
     default: return "unknown error";
   }
 }
@@ -1673,7 +1728,7 @@ static StencilView<double, double> raw_view(int n, const double* coef, bool with
 static int step_done(cudaStream_t s, const char* what) {
   CK(cudaGetLastError());
   int rc = cuda_check(cudaStreamSynchronize(s), what);
-  return rc;
+  return rc ? rc : debug_check(what);
 }
 
 int bmg_dendy_interp(int n, const double* coef, double* ci, void* stream) {
@@ -1719,6 +1774,45 @@ int bmg_relax_line(int n, int kind, const double* coef, const double* f, double*
   cudaStream_t s = (cudaStream_t)stream;
   launch_line<double, double>(raw_view(n, coef, false), kind, f, x, work, sweeps, LINE_X, (const int*)nullptr, s);
   return step_done(s, "bmg_relax_line");
+}
+
+int bmg_debug_build(void) {
+#ifdef BMG_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int bmg_debug_take(int* site, long long* index, long long* extent) {
+#ifdef BMG_DEBUG
+  DbgRecord r;
+  if (cudaDeviceSynchronize() != cudaSuccess || dbg_collect(&r, true) != cudaSuccess)
+    return set_error(BMG_ECUDA, "bmg_debug_take: reading the records failed");
+  if (site) *site = r.site;
+  if (index) *index = r.index;
+  if (extent) *extent = r.extent;
+  return r.hit ? 1 : 0;
+#else
+  if (site) *site = 0;
+  if (index) *index = 0;
+  if (extent) *extent = 0;
+  return 0;
+#endif
+}
+
+const char* bmg_debug_site_name(int site) { return dbg_site_name(site); }
+
+int bmg_debug_shrink(long long k) {
+#ifdef BMG_DEBUG
+  if (k < 0) return set_error(BMG_EINVAL, "bmg_debug_shrink: negative count");
+  for (const DbgHooks& h : dbg_hooks())
+    if (h.shrink(k) != cudaSuccess) return set_error(BMG_ECUDA, "bmg_debug_shrink: setting the extent failed");
+  return BMG_OK;
+#else
+  (void)k;
+  return set_error(BMG_EINVAL, "bmg_debug_shrink: not a debug build (BMG_DEBUG)");
+#endif
 }
 
 int bmg_relax_line_y(int n, int kind, const double* coef, const double* f, double* x, double* work, int sweeps,
@@ -2647,6 +2741,7 @@ int bmg_solve_batched(bmg_batch* B, const double* const* rhs, double* const* x, 
     else if (c->done != 1 && worst == BMG_OK) worst = BMG_ENOTCONV;
   }
   if (strip_timeouts_b()) return set_error(BMG_ETIMEOUT, "bmg_solve_batched: a one-pass sweep timed out");
+  if ((rc = debug_check("bmg_solve_batched"))) return rc;
   if (worst == BMG_ENAN) return set_error(BMG_ENAN, "bmg_solve_batched: a residual norm is not finite");
   if (worst == BMG_ENOTCONV) return set_error(BMG_ENOTCONV, "bmg_solve_batched: not every problem converged");
   return BMG_OK;

@@ -135,6 +135,83 @@ struct Ctl {
 
 }  // namespace bmg
 
+// ---- debug build: device bounds checks ------------------------------------------
+// Compiled with -DBMG_DEBUG (libbmg_debug.so), the kernels check the index of
+// each global store, and the source range of each asynchronous row copy,
+// against the logical extent of the level array it addresses.  A failed check
+// skips the store (a copy reads the array's first element instead, or is
+// zero-filled, so that its transaction still completes) and records the first
+// failure of the translation unit: site, index, extent.  Nothing traps.  The
+// host collects the records (bmg_debug_take; bmg_solve returns BMG_EBOUNDS).
+// Test hook (bmg_debug_shrink(k)): every check uses extent - k, so the last k
+// elements of each array count as outside; the accesses there are skipped and
+// none leaves its array.  Without BMG_DEBUG every check is the constant true.
+namespace bmg {
+enum DbgSite {
+  DBG_GS_STORE = 1,      // point Gauss-Seidel (row, checkerboard and tail kernels)
+  DBG_STRIP_STORE,       // one-pass / two-pass strip kernels
+  DBG_STRIP64_COPY,      // FP64 strip row copies (cp.async sources)
+  DBG_RING_COPY,         // FP32 strip row copies (bulk-copy sources)
+  DBG_RESTRICT_STORE,    // coarse right-hand side and iterate written by the restriction
+  DBG_INTERP_STORE,      // interpolation + correction
+  DBG_RESIDUAL_STORE,    // residual and the norm's partial sums
+  DBG_LINE_STORE,        // line relaxation
+  DBG_REFINE_STORE,      // refinement residual and update, FCG vectors
+  DBG_PERIODIC,          // kernels of periodic hierarchies (stores and row copies)
+  DBG_SITES
+};
+struct DbgRecord {
+  int hit, site;
+  long long index, extent;
+};
+}  // namespace bmg
+
+#ifdef BMG_DEBUG
+namespace bmg {
+namespace {
+__device__ DbgRecord g_dbg;          // one record per translation unit (no relocatable device code)
+__device__ long long g_dbg_shrink;
+}  // namespace
+__device__ __forceinline__ bool dbg_in(int site, long long idx, long long lo, long long hi) {
+  hi -= g_dbg_shrink;
+  if (idx >= lo && idx < hi) return true;
+  if (atomicCAS(&g_dbg.hit, 0, 1) == 0) {
+    g_dbg.site = site;
+    g_dbg.index = idx;
+    g_dbg.extent = hi;
+  }
+  return false;
+}
+// Host side: each translation unit registers the accessors of its record
+// (bmg_api.cu keeps the list).
+struct DbgHooks {
+  cudaError_t (*take)(DbgRecord* out, bool clear);
+  cudaError_t (*shrink)(long long k);
+};
+void dbg_register(DbgHooks h);
+namespace {
+cudaError_t dbg_take_here(DbgRecord* out, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_dbg, sizeof(DbgRecord));
+  if (e == cudaSuccess && clear && out->hit) {
+    const DbgRecord zero = {0, 0, 0, 0};
+    e = cudaMemcpyToSymbol(g_dbg, &zero, sizeof(DbgRecord));
+  }
+  return e;
+}
+cudaError_t dbg_shrink_here(long long k) { return cudaMemcpyToSymbol(g_dbg_shrink, &k, sizeof(long long)); }
+struct DbgRegistrar {
+  DbgRegistrar() { dbg_register(DbgHooks{dbg_take_here, dbg_shrink_here}); }
+};
+DbgRegistrar g_dbg_registrar;
+}  // namespace
+}  // namespace bmg
+#define BMG_IN(site, idx, extent) ::bmg::dbg_in((site), (long long)(idx), 0LL, (long long)(extent))
+#define BMG_IN_RANGE(site, idx, lo, hi) ::bmg::dbg_in((site), (long long)(idx), (long long)(lo), (long long)(hi))
+#else
+#define BMG_IN(site, idx, extent) true
+#define BMG_IN_RANGE(site, idx, lo, hi) true
+#endif
+
 // Host-side launch helpers (implemented in bmg_api.cu).
 namespace bmg {
 void count_launch();

@@ -50,7 +50,7 @@ template <typename T, typename S, bool NINE, bool FU = false>
 __device__ __forceinline__ void gs_point(const StencilView<T, S>& v, const T* __restrict__ f, T* x, size_t p) {
   T s = row_residual<T, S, NINE, false, FU>(v, x, p, f[p]);
   T d = v.D ? v.D[p] : rdiv(T(1), v.O[p]);
-  x[p] = rmul(s, d);
+  if (BMG_IN(DBG_GS_STORE, p, (size_t)(v.n + 2) * v.ld)) x[p] = rmul(s, d);
 }
 
 template <typename T>
@@ -125,7 +125,7 @@ __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T
   if (has1) load_point(v, f, x, p1, B, false);
   if (has0) {
     T xn = update_from<T, FU>(A);
-    x[p0] = xn;
+    if (BMG_IN(DBG_GS_STORE, p0, (size_t)(n + 2) * ld)) x[p0] = xn;
     xo[threadIdx.x] = xn;
     B.xs[0] = xn;
   }
@@ -146,7 +146,8 @@ __device__ __forceinline__ void gs_rows_body(const StencilView<T, S>& v, const T
   }
   if (has1) {
     B.xs[1] = right;
-    x[p1] = update_from<T, FU>(B);
+    const T xn = update_from<T, FU>(B);
+    if (BMG_IN(DBG_GS_STORE, p1, (size_t)(n + 2) * ld)) x[p1] = xn;
   }
 }
 
@@ -182,12 +183,14 @@ __device__ __forceinline__ void line_row_body(const StencilView<T, S>& v, const 
       c = rdiv(aE, m);
       d = rdiv(rsub(g, rmul(aW, d)), m);
     }
-    cp[p] = c;
-    x[p] = d;
+    if (BMG_IN(DBG_LINE_STORE, p, (size_t)(n + 2) * ld)) {
+      cp[p] = c;
+      x[p] = d;
+    }
   }
   for (int i = n - 1; i >= 1; --i) {
     const size_t p = r0 + i;
-    x[p] = rsub(x[p], rmul(cp[p], x[p + 1]));
+    if (BMG_IN(DBG_LINE_STORE, p, (size_t)(n + 2) * ld)) x[p] = rsub(x[p], rmul(cp[p], x[p + 1]));
   }
 }
 
@@ -220,12 +223,14 @@ __device__ __forceinline__ void line_col_body(const StencilView<T, S>& v, const 
       c = rdiv(aN, m);
       d = rdiv(rsub(g, rmul(aS, d)), m);
     }
-    cp[p] = c;
-    x[p] = d;
+    if (BMG_IN(DBG_LINE_STORE, p, (size_t)(n + 2) * ld)) {
+      cp[p] = c;
+      x[p] = d;
+    }
   }
   for (int j = n - 1; j >= 1; --j) {
     const size_t p = (size_t)j * ld + i;
-    x[p] = rsub(x[p], rmul(cp[p], x[p + ld]));
+    if (BMG_IN(DBG_LINE_STORE, p, (size_t)(n + 2) * ld)) x[p] = rsub(x[p], rmul(cp[p], x[p + ld]));
   }
 }
 
@@ -343,8 +348,8 @@ __device__ __forceinline__ void strip_store(T* __restrict__ xout, int n, int ld,
                                             const StripRowT<T, S>& R) {
   if (!own || j > n) return;
   const size_t p = (size_t)j * ld + ic;
-  if (ic <= n) xout[p] = R.xa;
-  if (ic + 1 <= n) xout[p + 1] = R.xb;
+  if (ic <= n && BMG_IN(DBG_STRIP_STORE, p, (size_t)(n + 2) * ld)) xout[p] = R.xa;
+  if (ic + 1 <= n && BMG_IN(DBG_STRIP_STORE, p + 1, (size_t)(n + 2) * ld)) xout[p + 1] = R.xb;
 }
 
 template <typename S, int TY, bool FU = false>
@@ -483,11 +488,14 @@ __device__ __forceinline__ void ring_issue_warp(const StripSrc& A, int ld, int i
   if (lane < 3) {
     const long long e = (long long)j * ld + icol;   // first point of the row segment
     const long long e4 = e - (e & 3);
+    // (debug builds: a segment outside the array's guarded extent is read from its start instead)
+    const long long s4 =
+        BMG_IN_RANGE(DBG_RING_COPY, e4, -STRIP_GUARD, (long long)ld * ld + STRIP_GUARD - RG::CP + 1) ? e4 : 0;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (lane < 2)
-      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + e4, RG::BF, bar);
+      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + s4, RG::BF, bar);
     else
-      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * e4, RG::BP, bar);
+      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * s4, RG::BP, bar);
   }
 }
 
@@ -787,13 +795,16 @@ __device__ __forceinline__ void ring_issue_warp_k(const float* pk, const float* 
   if (lane <= 2 * K) {
     const long long e = (long long)j * ld + icol;
     const long long e4 = e - (e & 3);
+    // (debug builds: a segment outside the array's guarded extent is read from its start instead)
+    const long long s4 =
+        BMG_IN_RANGE(DBG_RING_COPY, e4, -STRIP_GUARD, (long long)ld * ld + STRIP_GUARD - RG::CP + 1) ? e4 : 0;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (lane == 0) {
-      bulk_copy(slot, pk + RG::PK * e4, RG::BP, bar);
+      bulk_copy(slot, pk + RG::PK * s4, RG::BP, bar);
     } else {
       const int q = (lane - 1) >> 1;
       const float* src = (lane & 1) ? xs[q] : fs[q];
-      bulk_copy(slot + RG::BP + (lane - 1) * RG::BF, src + e4, RG::BF, bar);
+      bulk_copy(slot + RG::BP + (lane - 1) * RG::BF, src + s4, RG::BF, bar);
     }
   }
 }
@@ -866,8 +877,8 @@ __device__ __forceinline__ bool gs_strip_ring_k_body(const StencilView<float, S>
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       if (!((active >> q) & 1u)) continue;
-      if (ic <= n) xout[q][p] = R.xa[q];
-      if (ic + 1 <= n) xout[q][p + 1] = R.xb[q];
+      if (ic <= n && BMG_IN(DBG_STRIP_STORE, p, (size_t)(n + 2) * ld)) xout[q][p] = R.xa[q];
+      if (ic + 1 <= n && BMG_IN(DBG_STRIP_STORE, p + 1, (size_t)(n + 2) * ld)) xout[q][p + 1] = R.xb[q];
     }
   };
   StripRowK<K> P0, P1, Q0, Q1;
@@ -980,13 +991,16 @@ __device__ __forceinline__ void ring_issue_warp_r(const StripSrc& A, const float
   if (lane < 4) {
     const long long e = (long long)j * ld + icol;
     const long long e4 = e - (e & 3);
+    // (debug builds: a segment outside the array's guarded extent is read from its start instead)
+    const long long s4 =
+        BMG_IN_RANGE(DBG_RING_COPY, e4, -STRIP_GUARD, (long long)ld * ld + STRIP_GUARD - RG::CP + 1) ? e4 : 0;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (lane < 2)
-      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + e4, RG::BF, bar);
+      bulk_copy(slot + lane * RG::BF, (lane == 0 ? A.x : A.f) + s4, RG::BF, bar);
     else if (lane == 2)
-      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * e4, RG::BP, bar);
+      bulk_copy(slot + 2 * RG::BF, A.pk + RG::PK * s4, RG::BP, bar);
     else
-      bulk_copy(slot + RG::SLOT, O + e4, RG::BF, bar);
+      bulk_copy(slot + RG::SLOT, O + s4, RG::BF, bar);
   }
 }
 
@@ -1097,8 +1111,10 @@ __device__ __forceinline__ bool gs_strip2r_ring_body(const StencilView<float, S>
           t = madd<FU>(t, w(CI_LB, 0, 1), ob);
           t = madd<FU>(t, w(CI_LSW, 1, 1), oa_n);
           const size_t pc = (size_t)jc * ldc + icc;
-          fc[pc] = t;
-          xc[pc] = 0.f;
+          if (BMG_IN(DBG_RESTRICT_STORE, pc, (size_t)ldc * ldc)) {
+            fc[pc] = t;
+            xc[pc] = 0.f;
+          }
         }
       }
       rpa = oa;
@@ -1158,12 +1174,15 @@ __device__ __forceinline__ void row64_issue(const StripSrc64& A, int n, int ld, 
   const bool rowin = j >= 0 && j <= n + 1;
   const bool ina = rowin && ic >= 0 && ic <= n + 1, inb = rowin && ic + 1 >= 0 && ic + 1 <= n + 1;
   const size_t pa = ina ? (size_t)j * ld + ic : 0, pb = inb ? (size_t)j * ld + ic + 1 : 0;
+  // (debug builds: a copy from outside the array is zero-filled instead)
+  const bool oka = ina && BMG_IN(DBG_STRIP64_COPY, pa, (size_t)(n + 2) * ld);
+  const bool okb = inb && BMG_IN(DBG_STRIP64_COPY, pb, (size_t)(n + 2) * ld);
   double* d = reinterpret_cast<double*>(slot) + 2 * lane;
   const double* src[7] = {A.x, A.f, A.d, A.w, A.s, A.sw, A.nw};
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    cp_async8(d + 64 * k, src[k] + pa, ina);
-    cp_async8(d + 64 * k + 1, src[k] + pb, inb);
+    cp_async8(d + 64 * k, src[k] + (oka ? pa : 0), oka);
+    cp_async8(d + 64 * k + 1, src[k] + (okb ? pb : 0), okb);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -1288,6 +1307,7 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
   t = madd<FU>(t, w(CI_LB, 0, 1), r[lj + 1][li]);
   t = madd<FU>(t, w(CI_LSW, 1, 1), r[lj + 1][li + 1]);
   size_t pc = (size_t)jc * ldc + ic;
+  if (!BMG_IN(DBG_RESTRICT_STORE, pc, (size_t)ldc * ldc)) return;
   fc[pc] = t;
   if (xc) xc[pc] = T(0);
 }
@@ -1305,23 +1325,24 @@ __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, con
   size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
   T e_sw = ec[pc - ldc - 1], e_se = ec[pc - ldc], e_nw = ec[pc - 1], e_ne = ec[pc];
   size_t pf = (size_t)(2 * jc) * ld + 2 * ic;   // coincident fine point
-  if (ic <= nc && jc <= nc) xout[pf] = radd(xin[pf], e_ne);
+  const size_t ext = (size_t)ld * ld;
+  if (ic <= nc && jc <= nc && BMG_IN(DBG_INTERP_STORE, pf, ext)) xout[pf] = radd(xin[pf], e_ne);
   if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
     T t = rmul(ci[CI_LL * psc + pc], e_nw);
     t = madd<FU>(t, ci[CI_LR * psc + pc], e_ne);
-    xout[pf - 1] = radd(xin[pf - 1], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - 1, ext)) xout[pf - 1] = radd(xin[pf - 1], t);
   }
   if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
     T t = rmul(ci[CI_LB * psc + pc], e_se);
     t = madd<FU>(t, ci[CI_LA * psc + pc], e_ne);
-    xout[pf - ld] = radd(xin[pf - ld], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - ld, ext)) xout[pf - ld] = radd(xin[pf - ld], t);
   }
   {                                               // centre (2ic-1, 2jc-1)
     T t = rmul(ci[CI_LSW * psc + pc], e_sw);
     t = madd<FU>(t, ci[CI_LSE * psc + pc], e_se);
     t = madd<FU>(t, ci[CI_LNW * psc + pc], e_nw);
     t = madd<FU>(t, ci[CI_LNE * psc + pc], e_ne);
-    xout[pf - ld - 1] = radd(xin[pf - ld - 1], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - ld - 1, ext)) xout[pf - ld - 1] = radd(xin[pf - ld - 1], t);
   }
 }
 
@@ -1364,7 +1385,7 @@ __device__ __forceinline__ void residual_body(const StencilView<T, S>& v, const 
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
       T s = row_residual<T, S, NINE, true, FU>(v, x, p, f[p]);
-      if (r) r[p] = s;
+      if (r && BMG_IN(DBG_RESIDUAL_STORE, p, (size_t)(n + 2) * ld)) r[p] = s;
       double d = (double)s;
       acc = madd<FU>(acc, d, d);
     }
@@ -1505,7 +1526,8 @@ __device__ __forceinline__ void ir_update_body(int n, double* __restrict__ x, co
                                                const Ctl* ctl, int i, int j) {
   if (i < 1 || j < 1 || i > n || j > n) return;
   size_t p = (size_t)j * (n + 2) + i;
-  x[p] = radd(x[p], pow2_times_widened(ctl->scale_applied, e32[p]));
+  if (BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2)))
+    x[p] = radd(x[p], pow2_times_widened(ctl->scale_applied, e32[p]));
 }
 
 // r = f - A x (FP64), r32 = fl32(r / scale_next), e32 = 0, partial sums of r^2.
@@ -1524,8 +1546,10 @@ __device__ __forceinline__ void ir_residual_body(const StencilView<double, doubl
       size_t p = (size_t)j * ld + i;
       double rr = nine ? row_residual<double, double, true, true, FU>(v, x, p, f[p])
                        : row_residual<double, double, false, true, FU>(v, x, p, f[p]);
-      r32[p] = narrow_scaled(rr, inv, inv32);
-      e32[p] = 0.0f;
+      if (BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) {
+        r32[p] = narrow_scaled(rr, inv, inv32);
+        e32[p] = 0.0f;
+      }
       acc = madd<FU>(acc, rr, rr);
     }
   double tot = block_sum(acc);
@@ -1626,8 +1650,10 @@ __device__ __forceinline__ void resid_restrict_block(const LevelDesc<T, T>& q) {
     t = madd<FU>(t, w(CI_LB, 0, 1), r(0, 1));
     t = madd<FU>(t, w(CI_LSW, 1, 1), r(1, 1));
     size_t pc = (size_t)jc * ldc + ic;
-    q.fc[pc] = t;
-    q.xc[pc] = T(0);
+    if (BMG_IN(DBG_RESTRICT_STORE, pc, (size_t)ldc * ldc)) {
+      q.fc[pc] = t;
+      q.xc[pc] = T(0);
+    }
   }
   __syncthreads();
 }

@@ -766,6 +766,7 @@ __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float
   int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (i > n || j > n) return;
   size_t p = (size_t)j * (n + 2) + i;
+  if (!BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2))) return;
   double zp = zval(z, z32, ctl->scale_applied, p);
   if (ctl->first)
     pv[p] = zp;
@@ -797,7 +798,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_matvec(StencilView<double,
         acc = madd<FU>(acc, v.NW[p], pv[p + ld - 1]);
         acc = madd<FU>(acc, v.NW[p + 1 - ld], pv[p + 1 - ld]);
       }
-      q[p] = acc;
+      if (BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) q[p] = acc;
       apq = madd<FU>(apq, pv[p], acc);
       apr = madd<FU>(apr, pv[p], r[p]);
     }
@@ -828,6 +829,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
     for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
       size_t p = (size_t)j * ld + i;
+      if (!BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) continue;
       x[p] = madd<FU>(x[p], alpha, pv[p]);
       double rr = msub<FU>(r[p], alpha, q[p]);
       r[p] = rr;
@@ -867,6 +869,7 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_init(StencilView<double, d
       size_t p = (size_t)j * ld + i;
       double rr = nine ? row_residual<double, double, true, true, FU>(v, x, p, f[p])
                        : row_residual<double, double, false, true, FU>(v, x, p, f[p]);
+      if (!BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) continue;
       r[p] = rr;
       if (r32) {
         r32[p] = __double2float_rn(rmul(rr, inv));

@@ -341,7 +341,7 @@ __global__ void k_p_gs(PGeom g, const double* __restrict__ st, const double* __r
   if (i > g.nx || j > g.ny) return;
   const size_t p = (size_t)j * (g.nx + 2) + i;
   const double s = prow<NINE, false, FU>(st, x, g, i, j, f[p]);
-  x[p] = rmul(s, st[5 * g.ps() + p]);
+  if (BMG_IN(DBG_PERIODIC, p, g.ps())) x[p] = rmul(s, st[5 * g.ps() + p]);
 }
 
 // Half of a 9-point sweep: one CTA per row j of parity pj, its odd-i points
@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(256) k_p_gs_rows(PGeom g, const double* __rest
   auto point = [&](int i) {
     if (i > g.nx) return;
     const size_t p = row + i;
-    x[p] = rmul(prow<true, false, FU>(st, x, g, i, j, f[p]), st[dp + p]);
+    const double xn = rmul(prow<true, false, FU>(st, x, g, i, j, f[p]), st[dp + p]);
+    if (BMG_IN(DBG_PERIODIC, p, g.ps())) x[p] = xn;
   };
   point(1 + 2 * (int)threadIdx.x);                          // odd points of chunk 0
   for (int c = 0; c < chunks; ++c) {
@@ -426,12 +427,14 @@ __device__ __forceinline__ void p_strip64_body(const PGeom& g, const double* __r
       const bool rin = g.py || (j >= 0 && j <= ny + 1);
       const int jr = g.py ? 1 + ((j - 1) % ny + ny) % ny : (rin ? j : 0);
       const size_t pa = (size_t)jr * ld + ca, pb = (size_t)jr * ld + cb;
+      // (debug builds: a copy from outside the array is zero-filled instead)
+      const bool oka = rin && cpa && BMG_IN(DBG_PERIODIC, pa, ps), okb = rin && cpb && BMG_IN(DBG_PERIODIC, pb, ps);
       double* d = reinterpret_cast<double*>(ring + (q % RING) * dev::STRIP64_SLOT) + 2 * lane;
 #pragma unroll
       for (int k = 0; k < 7; ++k) {
         const double* a = k == 0 ? xin : k == 1 ? f : st + (size_t)plane[k] * ps;
-        dev::cp_async8(d + 64 * k, a + pa, rin && cpa);
-        dev::cp_async8(d + 64 * k + 1, a + pb, rin && cpb);
+        dev::cp_async8(d + 64 * k, a + (oka ? pa : 0), oka);
+        dev::cp_async8(d + 64 * k + 1, a + (okb ? pb : 0), okb);
       }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -446,8 +449,8 @@ __device__ __forceinline__ void p_strip64_body(const PGeom& g, const double* __r
   auto store = [&](int j, const Row& R) {
     if (!own || j > ny) return;
     const size_t p = (size_t)j * ld + ic;
-    if (ic <= nx) xout[p] = R.xa;
-    if (ic + 1 <= nx) xout[p + 1] = R.xb;
+    if (ic <= nx && BMG_IN(DBG_PERIODIC, p, ps)) xout[p] = R.xa;
+    if (ic + 1 <= nx && BMG_IN(DBG_PERIODIC, p + 1, ps)) xout[p + 1] = R.xb;
   };
   Row P0, P1, Q0, Q1;
   take(0, P1);
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(dev::NORM_THREADS) k_p_residual(PGeom g, const
     for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
       const size_t p = (size_t)j * (g.nx + 2) + i;
       const double s = prow<NINE, true, FU>(st, x, g, i, j, f[p]);
-      if (r) r[p] = s;
+      if (r && BMG_IN(DBG_PERIODIC, p, g.ps())) r[p] = s;
       acc = madd<FU>(acc, s, s);
     }
   if (partials) {
@@ -543,7 +546,7 @@ __global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const doubl
   t = madd<FU>(t, w(CI_LSE, 0, 1), q(-1, 1));
   t = madd<FU>(t, w(CI_LB, 0, 1), q(0, 1));
   t = madd<FU>(t, w(CI_LSW, 1, 1), q(1, 1));
-  fc[(size_t)jc * (c.ncx + 2) + ic] = t;
+  if (BMG_IN(DBG_PERIODIC, (size_t)jc * (c.ncx + 2) + ic, psc)) fc[(size_t)jc * (c.ncx + 2) + ic] = t;
 }
 
 // x_out = x_in + P e_c at fine point (i, j) (x_in and x_out may be the same
@@ -579,7 +582,7 @@ __global__ void k_p_interp(PGeom g, const double* __restrict__ ci, const double*
     t = madd<FU>(t, w(CI_LNW, ic, jc), e(ic - 1, jc));
     t = madd<FU>(t, w(CI_LNE, ic, jc), e(ic, jc));
   }
-  xout[p] = radd(xin[p], t);
+  if (BMG_IN(DBG_PERIODIC, p, g.ps())) xout[p] = radd(xin[p], t);
 }
 
 // L L^T x = f on the coarsest level (one thread, m <= 16): forward then backward

@@ -127,3 +127,17 @@ def test_binding_checks_sizes_before_the_library(libpath):
         bmg.interp_correct(z(8, 5, 5), z(4, 5), z(9, 9))
     with pytest.raises(ValueError, match="L holds"):
         bmg.coarse_solve(z(8, 10), z(5, 5), z(5, 5))   # n = 3: L is 9 x 9
+
+
+def test_release_library_has_no_debug_checks(libpath):
+    """libbmg.so compiles every device bounds check to the constant true: it
+    reports itself as a release build, never holds a record, and refuses the
+    debug builds' test hook (no device call is made for any of this)."""
+    import paper_2502_05279_gb300 as bmg
+    assert not bmg.debug_build()
+    assert bmg.debug_take() is None
+    with pytest.raises(bmg.BmgError) as e:
+        bmg.debug_shrink(1)
+    assert e.value.code == bmg._lib.BMG_EINVAL
+    assert bmg.lib.bmg_strerror(-8).decode() == "debug bounds check failed"
+    assert bmg.lib.bmg_debug_site_name(1).decode() == "point Gauss-Seidel store"
