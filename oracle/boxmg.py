@@ -744,12 +744,17 @@ def _precondition64(levels, r, nu1, nu2):
     return z
 
 
-def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False, inner=None):
+def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False, inner=None, ops=None):
+    """The FCG(1) recurrence of solve_fcg.  ops: the operator's (residual(x, f),
+    apply(p)) pair, by default those of the Dirichlet planes (the periodic
+    oracle passes its wrap-around ones)."""
     fu = fused
     ip = dot if inner is None else inner
     nrm = _norm_of(inner)
+    res, app = ops if ops is not None else (lambda x_, f_: residual(planes, x_, f_, fu),
+                                            lambda p_: apply(planes, p_, fu))
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
-    r = residual(planes, x, f, fu)
+    r = res(x, f)
     hist = [nrm(r)]
     if hist[0] == 0.0:
         return x, hist
@@ -763,7 +768,7 @@ def _fcg(planes, precond, f, x0, tol, maxit, fused: bool = False, inner=None):
         else:
             beta = -(ip(z, q) / pq)
             p = madd(z, beta, p, fu)
-        q = apply(planes, p, fu)
+        q = app(p)
         pq = ip(p, q)
         alpha = ip(p, r) / pq
         x = madd(x, alpha, p, fu)

@@ -412,6 +412,24 @@ def vcycle(levels, l, x, f, nu1=2, nu2=1) -> None:
         gs_sweep(lev.kind, lev.planes, lev.dinv, x, f, px, py, fu)
 
 
+def solve_fcg(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1, inner=None):
+    """Flexible CG, FCG(1), preconditioned by one periodic V(nu1, nu2) cycle
+    from a zero guess: the recurrence of boxmg.solve_fcg (the same steps,
+    inner products and updates) with this module's wrap-around residual and
+    operator product.  inner(a, b): the interior inner product (default the
+    plain dot).  Returns (x, history)."""
+    lev = levels[0]
+    px, py, fu = lev.px, lev.py, lev.fused
+
+    def precond(r):
+        z = np.zeros_like(r)
+        vcycle(levels, 0, z, r, nu1, nu2)
+        return z
+
+    ops = (lambda x, g: residual(lev.planes, x, g, px, py, fu), lambda p: apply(lev.planes, p, px, py, fu))
+    return bx._fcg(lev.planes, precond, f, x0, tol, maxit, fu, inner, ops)
+
+
 def solve(levels, f, x0=None, tol=1e-10, maxit=100, nu1=2, nu2=1):
     """V(nu1, nu2) iterations until ||r_k|| / ||r_0|| <= tol or maxit cycles
     (boxmg.solve's loop); returns (x, history)."""
