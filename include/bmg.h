@@ -161,9 +161,10 @@ typedef struct {
                            (always that many per warp).  Same bits. */
   int periodic;         /* 0 (default): Dirichlet sides; BMG_PERIODIC_X | BMG_PERIODIC_Y: those axes
                            wrap around (see Periodic sides above).  Periodic hierarchies run FP64
-                           stationary V(nu1, nu2) cycles with point Gauss-Seidel, Dendy
-                           interpolation and the default coarsest level, in either arithmetic mode,
-                           with or without graphs; other options give EINVAL.  Their 9-point levels
+                           V(nu1, nu2) cycles, stationary or as the preconditioner of flexible CG
+                           (krylov), with point Gauss-Seidel, Dendy interpolation and the default
+                           coarsest level, in either arithmetic mode, with or without graphs; other
+                           options give EINVAL.  Their 9-point levels
                            are swept (the same bits either way) by two row-parity launches in place
                            (smoother ROWS), by the one-pass strip kernel into a second iterate
                            (smoother TILE), or, by default (AUTO), per level by whichever of the

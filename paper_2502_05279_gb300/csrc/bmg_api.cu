@@ -1312,7 +1312,7 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
   if (periodic & ~(BMG_PERIODIC_X | BMG_PERIODIC_Y)) why = "bad periodic flags";
   else if (h->precision != BMG_FP64) why = "periodic sides take FP64 cycles only";
   else if (h->interp != BMG_INTERP_DENDY) why = "periodic sides take Dendy interpolation only";
-  else if (h->krylov != BMG_KRYLOV_NONE) why = "periodic sides take stationary cycles only";
+  else if (h->krylov != BMG_KRYLOV_NONE && h->krylov != BMG_KRYLOV_FCG) why = "bad krylov mode";
   else if (h->smoother != BMG_SMOOTHER_AUTO && h->smoother != BMG_SMOOTHER_ROWS && h->smoother != BMG_SMOOTHER_TILE)
     why = "periodic sides take point Gauss-Seidel (smoother AUTO, ROWS or TILE) only";
   else if (h->coarsest != 3) why = "periodic sides take the default coarsest level";
@@ -1334,7 +1334,7 @@ int setup_periodic(bmg_hierarchy* h, const bmg_stencil* A, int nx, int ny, int p
                           h->smoother == BMG_SMOOTHER_ROWS   ? PER_SWEEP_ROWS
                           : h->smoother == BMG_SMOOTHER_TILE ? PER_SWEEP_STRIP
                                                              : PER_SWEEP_AUTO,
-                          h->ws);
+                          h->krylov == BMG_KRYLOV_FCG, h->ws);
   if (!rc) rc = ensure_ctl(h, 64);
   if (rc) {
     bmg_free(h);

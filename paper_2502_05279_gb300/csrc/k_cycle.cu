@@ -931,6 +931,11 @@ static void fcg_step(const StencilView<double, double>& v, int kind, double* x, 
   if (mark) mark(mark_arg, 3);
 }
 
+void launch_fcg_reduce(const double* partials, int np, void* ctl, int which, cudaStream_t s) {
+  pdl_launch(k_fcg_reduce, 1, NORM_THREADS, 0, s, partials, np, (Ctl*)ctl, which);
+  count_launch();
+}
+
 void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
                      const float* z32, double* pv, double* q, float* r32, float* z32_zero, double* z_zero,
                      double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg) {

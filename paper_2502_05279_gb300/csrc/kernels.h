@@ -145,6 +145,11 @@ int launch_fcg_init(const StencilView<double, double>& v, int kind, const double
 void launch_fcg_step(const StencilView<double, double>& v, int kind, double* x, double* r, const double* z,
                      const float* z32, double* p, double* q, float* r32, float* z32_zero, double* z_zero,
                      double* partials, void* ctl, cudaStream_t s, void (*mark)(void*, int), void* mark_arg);
+// The step's scalar reductions over np partial sums in the canonical order:
+// which = 0: z.q into ctl (and beta = -(z.q) / (p.q)_prev after the first
+// step); which = 1: p.q and p.r (the second partial array NORM_BLOCKS_MAX
+// entries after the first).
+void launch_fcg_reduce(const double* partials, int np, void* ctl, int which, cudaStream_t s);
 
 // FP64 throughput probe.
 double measure_fp64_rate(cudaStream_t s);

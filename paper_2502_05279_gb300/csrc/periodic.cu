@@ -606,6 +606,133 @@ __global__ void k_p_coarse_solve(PGeom g, const double* __restrict__ L, const do
   for (int i = 0; i < m; ++i) x[(size_t)(i / g.nx + 1) * (g.nx + 2) + (i % g.nx + 1)] = z[i];
 }
 
+// ---- flexible CG (FCG(1)) on level 0, preconditioned by the periodic V-cycle ----
+// The recurrence of the Dirichlet FCG kernels (k_cycle.cu) over a grid whose
+// products wrap: every inner product in the canonical order of k_p_residual
+// (block b of G = min(ny, 1024): rows 1 + b, 1 + b + G, ...; thread t: columns
+// 1 + t, 1 + t + 256, ...; then the halving tree), the scalars formed once per
+// step by the shared reduction kernel.
+
+// r = f - A x (stored), z = 0, partial r.r; the control block's first step.
+template <bool NINE, bool FU>
+__global__ void __launch_bounds__(dev::NORM_THREADS) k_p_fcg_init(PGeom g, const double* __restrict__ st,
+                                                                  const double* __restrict__ x,
+                                                                  const double* __restrict__ f,
+                                                                  double* __restrict__ r, double* __restrict__ z,
+                                                                  double* __restrict__ partials, Ctl* ctl) {
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= g.ny; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
+      const size_t p = (size_t)j * (g.nx + 2) + i;
+      const double rr = prow<NINE, true, FU>(st, x, g, i, j, f[p]);
+      if (BMG_IN(DBG_PERIODIC, p, g.ps())) {
+        r[p] = rr;
+        z[p] = 0.0;
+      }
+      acc = madd<FU>(acc, rr, rr);
+    }
+  const double tot = dev::block_sum(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = tot;
+    if (blockIdx.x == 0) ctl->first = 1;
+  }
+}
+
+// partial z.q
+template <bool FU>
+__global__ void __launch_bounds__(dev::NORM_THREADS) k_p_fcg_zq(PGeom g, const double* __restrict__ z,
+                                                                const double* __restrict__ q,
+                                                                double* __restrict__ partials, const Ctl* ctl) {
+  if (ctl->done) return;
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= g.ny; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
+      const size_t p = (size_t)j * (g.nx + 2) + i;
+      acc = madd<FU>(acc, z[p], q[p]);
+    }
+  const double tot = dev::block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// p = z (first step) or z + beta p
+template <bool FU>
+__global__ void k_p_fcg_direction(PGeom g, const double* __restrict__ z, double* __restrict__ pv, const Ctl* ctl) {
+  if (ctl->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > g.nx || j > g.ny) return;
+  const size_t p = (size_t)j * (g.nx + 2) + i;
+  if (!BMG_IN(DBG_PERIODIC, p, g.ps())) return;
+  pv[p] = ctl->first ? z[p] : madd<FU>(z[p], ctl->beta, pv[p]);
+}
+
+// q = A p (a_O p first, then the neighbours in the canonical order, wrapped),
+// partial p.q and p.r
+template <bool NINE, bool FU>
+__global__ void __launch_bounds__(dev::NORM_THREADS) k_p_fcg_matvec(PGeom g, const double* __restrict__ st,
+                                                                    const double* __restrict__ pv,
+                                                                    const double* __restrict__ r,
+                                                                    double* __restrict__ q,
+                                                                    double* __restrict__ partials, const Ctl* ctl) {
+  if (ctl->done) return;
+  double apq = 0.0, apr = 0.0;
+  for (int j = 1 + blockIdx.x; j <= g.ny; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
+      const size_t p = (size_t)j * (g.nx + 2) + i;
+      double acc = rmul(coup<0>(st, g, i, j), pv[p]);
+      acc = madd<FU>(acc, coup<1>(st, g, i, j), pv[g.at(i - 1, j)]);
+      acc = madd<FU>(acc, coup<2>(st, g, i, j), pv[g.at(i + 1, j)]);
+      acc = madd<FU>(acc, coup<3>(st, g, i, j), pv[g.at(i, j - 1)]);
+      acc = madd<FU>(acc, coup<4>(st, g, i, j), pv[g.at(i, j + 1)]);
+      if (NINE) {
+        acc = madd<FU>(acc, coup<5>(st, g, i, j), pv[g.at(i - 1, j - 1)]);
+        acc = madd<FU>(acc, coup<6>(st, g, i, j), pv[g.at(i + 1, j + 1)]);
+        acc = madd<FU>(acc, coup<7>(st, g, i, j), pv[g.at(i - 1, j + 1)]);
+        acc = madd<FU>(acc, coup<8>(st, g, i, j), pv[g.at(i + 1, j - 1)]);
+      }
+      if (BMG_IN(DBG_PERIODIC, p, g.ps())) q[p] = acc;
+      apq = madd<FU>(apq, pv[p], acc);
+      apr = madd<FU>(apr, pv[p], r[p]);
+    }
+  const double t1 = dev::block_sum(apq);
+  __syncthreads();
+  const double t2 = dev::block_sum(apr);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = t1;
+    partials[dev::NORM_BLOCKS_MAX + blockIdx.x] = t2;
+  }
+}
+
+// x += alpha p, r -= alpha q (alpha = (p.r) / (p.q)), z = 0, partial r.r
+template <bool FU>
+__global__ void __launch_bounds__(dev::NORM_THREADS) k_p_fcg_update(PGeom g, double* __restrict__ x,
+                                                                    double* __restrict__ r,
+                                                                    const double* __restrict__ pv,
+                                                                    const double* __restrict__ q,
+                                                                    double* __restrict__ z,
+                                                                    double* __restrict__ partials, Ctl* ctl) {
+  if (ctl->done) return;
+  const double alpha = rdiv(ctl->pr, ctl->pq);
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= g.ny; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= g.nx; i += dev::NORM_THREADS) {
+      const size_t p = (size_t)j * (g.nx + 2) + i;
+      if (!BMG_IN(DBG_PERIODIC, p, g.ps())) continue;
+      x[p] = madd<FU>(x[p], alpha, pv[p]);
+      const double rr = msub<FU>(r[p], alpha, q[p]);
+      r[p] = rr;
+      z[p] = 0.0;
+      acc = madd<FU>(acc, rr, rr);
+    }
+  const double tot = dev::block_sum(acc);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = tot;
+    if (blockIdx.x == 0) {
+      ctl->pq_prev = ctl->pq;
+      ctl->first = 0;
+    }
+  }
+}
+
 dim3 pgrid(int nx, int ny) { return dim3((unsigned)((nx + PBX - 1) / PBX), (unsigned)((ny + PBY - 1) / PBY)); }
 
 int m_of(int n, int periodic) {
@@ -632,8 +759,9 @@ struct PerLevel {
 };
 
 struct PerHier {
-  int periodic = 0, fused = 0, nu1 = 2, nu2 = 1;
+  int periodic = 0, fused = 0, nu1 = 2, nu2 = 1, krylov = 0;
   std::vector<PerLevel> lv;
+  double* kr = nullptr;   // FCG: r, z, p, q on level 0's layout (krylov)
   double* L = nullptr;
   double* work = nullptr;
   int* err = nullptr;
@@ -684,6 +812,7 @@ void per_free(PerHier* P) {
   cudaFree(P->L);
   cudaFree(P->work);
   cudaFree(P->err);
+  cudaFree(P->kr);
   delete P;
 }
 
@@ -723,7 +852,7 @@ int tune_sweeps(PerHier* P, cudaStream_t s) {
 }  // namespace
 
 int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int periodic, int fused, int nu1,
-              int nu2, int sweep, cudaStream_t s) {
+              int nu2, int sweep, int krylov, cudaStream_t s) {
   *out = nullptr;
   const int nlev = per_levels_for(nx, ny, periodic);
   if (nlev < 1)
@@ -736,6 +865,7 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
   P->fused = fused;
   P->nu1 = nu1;
   P->nu2 = nu2;
+  P->krylov = krylov;
   P->lv.resize(nlev);
   const int px = periodic & 1 ? 1 : 0, py = periodic & 2 ? 1 : 0;
   int rc = BMG_OK;
@@ -758,6 +888,7 @@ int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int p
   const int m = gc.nx * gc.ny;
   if (!rc) rc = palloc(&P->L, (size_t)m * m, s);
   if (!rc) rc = palloc(&P->work, (size_t)m * m, s);
+  if (!rc && krylov) rc = palloc(&P->kr, 4 * P->lv[0].g.ps(), s);
   if (!rc && dev_malloc((void**)&P->err, sizeof(int)) != cudaSuccess) rc = set_error(BMG_ENOMEM, "periodic setup");
   if (!rc) rc = cuda_check(cudaMemsetAsync(P->err, 0, sizeof(int), s), "periodic setup: memset");
   if (rc) {
@@ -902,20 +1033,67 @@ void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, 
 }  // namespace
 
 void per_enqueue_initial(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s) {
+  if (P->krylov) {
+    const PerLevel& L = P->lv[0];
+    const size_t ps = L.g.ps();
+    const int G = L.g.ny < dev::NORM_BLOCKS_MAX ? L.g.ny : dev::NORM_BLOCKS_MAX;
+    auto k = P->fused ? (L.kind == 9 ? k_p_fcg_init<true, true> : k_p_fcg_init<false, true>)
+                      : (L.kind == 9 ? k_p_fcg_init<true, false> : k_p_fcg_init<false, false>);
+    k<<<G, dev::NORM_THREADS, 0, s>>>(L.g, L.st, x, rhs, P->kr, P->kr + ps, partials, ctl);
+    count_launch();
+    launch_norm_finalize(partials, G, ctl, 0, nullptr, s);
+    return;
+  }
   const int G = P->fused ? per_residual<true>(P->lv[0], x, rhs, nullptr, partials, nullptr, s)
                          : per_residual<false>(P->lv[0], x, rhs, nullptr, partials, nullptr, s);
   launch_norm_finalize(partials, G, ctl, 0, nullptr, s);
 }
 
+namespace {
+// One FCG step after the preconditioner z = V(r): z.q and beta, p, q = A p with
+// p.q and p.r, then the x / r update with the r.r partial sums; returns G.
+template <bool FU>
+int per_fcg_step(PerHier* P, double* x, double* partials, Ctl* ctl, cudaStream_t s) {
+  const PerLevel& L = P->lv[0];
+  const size_t ps = L.g.ps();
+  double *r = P->kr, *z = P->kr + ps, *pv = P->kr + 2 * ps, *q = P->kr + 3 * ps;
+  const int G = L.g.ny < dev::NORM_BLOCKS_MAX ? L.g.ny : dev::NORM_BLOCKS_MAX;
+  k_p_fcg_zq<FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, z, q, partials, ctl);
+  count_launch();
+  launch_fcg_reduce(partials, G, ctl, 0, s);
+  k_p_fcg_direction<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, z, pv, ctl);
+  count_launch();
+  if (L.kind == 9)
+    k_p_fcg_matvec<true, FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, L.st, pv, r, q, partials, ctl);
+  else
+    k_p_fcg_matvec<false, FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, L.st, pv, r, q, partials, ctl);
+  count_launch();
+  launch_fcg_reduce(partials, G, ctl, 1, s);
+  k_p_fcg_update<FU><<<G, dev::NORM_THREADS, 0, s>>>(L.g, x, r, pv, q, z, partials, ctl);
+  count_launch();
+  return G;
+}
+}  // namespace
+
 void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s,
                            const PerMarks* mk) {
   const int* done = &ctl->done;
   int G;
-  if (P->fused)
-    per_vcycle<true>(P, 0, x, rhs, done, s, mk);
-  else
-    per_vcycle<false>(P, 0, x, rhs, done, s, mk);
-  {
+  if (P->krylov) {
+    // z = V(r) from z = 0 (zeroed by the previous update or the initial step), then the FCG step
+    const size_t ps = P->lv[0].g.ps();
+    double *r = P->kr, *z = P->kr + ps;
+    if (P->fused)
+      per_vcycle<true>(P, 0, z, r, done, s, mk);
+    else
+      per_vcycle<false>(P, 0, z, r, done, s, mk);
+    Bracket b(mk, 0, BMG_K_FCG);
+    G = P->fused ? per_fcg_step<true>(P, x, partials, ctl, s) : per_fcg_step<false>(P, x, partials, ctl, s);
+  } else {
+    if (P->fused)
+      per_vcycle<true>(P, 0, x, rhs, done, s, mk);
+    else
+      per_vcycle<false>(P, 0, x, rhs, done, s, mk);
     Bracket b(mk, 0, BMG_K_NORM);
     G = P->fused ? per_residual<true>(P->lv[0], x, rhs, nullptr, partials, done, s)
                  : per_residual<false>(P->lv[0], x, rhs, nullptr, partials, done, s);

@@ -30,9 +30,11 @@ int per_levels_for(int nx, int ny, int periodic);
 // row-parity launches in place (PER_SWEEP_ROWS), by the one-pass strip kernel
 // into a second iterate (PER_SWEEP_STRIP), or per level by whichever of the
 // two is faster, timed during setup (PER_SWEEP_AUTO).
+// krylov: the solve runs flexible CG (FCG(1)) preconditioned by one V(nu1, nu2)
+// cycle per step instead of stationary cycles.
 enum { PER_SWEEP_AUTO = 0, PER_SWEEP_ROWS = 1, PER_SWEEP_STRIP = 2 };
 int per_setup(PerHier** out, int kind, const double* coef, int nx, int ny, int periodic, int fused, int nu1,
-              int nu2, int sweep, cudaStream_t s);
+              int nu2, int sweep, int krylov, cudaStream_t s);
 void per_free(PerHier* P);
 
 // Profiling brackets around each step's launches (begin: level and BMG_K_*
@@ -45,7 +47,9 @@ struct PerMarks {
 
 // The solve loop's device work: the initial residual norm (phase 0 of the
 // control block), and one iteration = V-cycle + residual norm + convergence
-// test (phase 1).  partials holds at least min(ny, 1024) doubles.
+// test (phase 1); with krylov, the initial step r = f - A x, z = 0 and one
+// iteration = z = V(r) + FCG step (updated residual's norm, convergence
+// test).  partials holds at least 2 x 1024 doubles.
 void per_enqueue_initial(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s);
 void per_enqueue_iteration(PerHier* P, const double* rhs, double* x, double* partials, Ctl* ctl, cudaStream_t s,
                            const PerMarks* marks = nullptr);

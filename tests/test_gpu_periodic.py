@@ -167,7 +167,7 @@ def test_bad_periodic_sizes(bmg, shape, axes):
     assert e.value.code == bmg.BMG_EINVAL
 
 
-@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(krylov="fcg"), dict(smoother="tile1"),
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(precision="bf16"), dict(smoother="tile1"),
                                 dict(smoother="pair"), dict(smoother="line"), dict(coarsest=7)])
 def test_unsupported_options(bmg, kw):
     kind, planes, f, px, py = problem(63, "x")
@@ -244,3 +244,41 @@ def test_zero_rhs_maxit_zero_and_nan(bmg):
         h.solve(torch.from_numpy(g).cuda())
     assert e.value.code == -5
     h.close()
+
+
+@pytest.mark.parametrize("axes", AXES)
+@pytest.mark.parametrize("arith", ["rounded", "fused"])
+@pytest.mark.parametrize("smoother", ["auto", "rows"])
+def test_fcg_matches_oracle(bmg, axes, arith, smoother):
+    """FCG(1) with the periodic V(2,1) preconditioner: iterates and history
+    bit for bit against the oracle's FCG run in the device's inner-product
+    order, iteration counts equal to the plain-sum oracle's."""
+    from reduction_order import device_inner
+    kind, planes, f, px, py = problem(127, axes, seed=62)
+    levels = pr.setup(kind, planes, px, py, arith=arith)
+    x_d, h_d = pr.solve_fcg(levels, f, tol=1e-10, maxit=60, inner=device_inner(arith == "fused"))
+    x_p, h_p = pr.solve_fcg(levels, f, tol=1e-10, maxit=60)
+    h = hierarchy(bmg, kind, planes, axes, arith=arith, krylov="fcg", smoother=smoother)
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=60)
+    assert ok and it == len(h_d) - 1
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_d))
+    hist = h.history()
+    assert hist == h_d
+    assert abs(len(h_p) - len(h_d)) <= 1
+    h.close()
+
+
+def test_fcg_needs_fewer_steps_and_solves(bmg):
+    """At 511 x 512 (periodic in y) FCG reaches 1e-10 in fewer steps than the
+    stationary cycle, and the oracle's own residual of the returned x confirms it."""
+    kind, planes, f, px, py = w.periodic_problem(511, "y", std=2.0, corr_len=8.0, seed_k=64, seed_f=65)
+    h = hierarchy(bmg, kind, planes, "y", arith="fused", krylov="fcg")
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=100)
+    h.close()
+    s = hierarchy(bmg, kind, planes, "y", arith="fused")
+    _, its, _, oks = s.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=100)
+    s.close()
+    assert ok and oks and it < its
+    P = pr.prepare(kind, planes, px, py)
+    r = pr.residual(P, x.cpu().numpy(), f, px, py)
+    assert bx.norm(r) <= 2e-10 * bx.norm(pr.residual(P, np.zeros_like(f), f, px, py))
