@@ -525,10 +525,11 @@ __global__ void __launch_bounds__(dev::NORM_THREADS) k_p_residual(PGeom g, const
 
 // f_c = P^T r at coarse point (ic, jc), term by term in the order of the Fig. 2
 // loop (a primed weight read at the neighbouring cell, wrapped on a periodic
-// axis); the coincident term has weight 1.
+// axis); the coincident term has weight 1.  Also zeroes the coarse iterate
+// there.
 template <bool FU>
 __global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const double* __restrict__ r,
-                             double* __restrict__ fc, const int* done) {
+                             double* __restrict__ fc, double* __restrict__ xc, const int* done) {
   if (dev::stopped(done)) return;
   const CellMap c = cells_of(g);
   const int ic = blockIdx.x * blockDim.x + threadIdx.x + 1, jc = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -546,7 +547,11 @@ __global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const doubl
   t = madd<FU>(t, w(CI_LSE, 0, 1), q(-1, 1));
   t = madd<FU>(t, w(CI_LB, 0, 1), q(0, 1));
   t = madd<FU>(t, w(CI_LSW, 1, 1), q(1, 1));
-  if (BMG_IN(DBG_PERIODIC, (size_t)jc * (c.ncx + 2) + ic, psc)) fc[(size_t)jc * (c.ncx + 2) + ic] = t;
+  const size_t pc = (size_t)jc * (c.ncx + 2) + ic;
+  if (BMG_IN(DBG_PERIODIC, pc, psc)) {
+    fc[pc] = t;
+    xc[pc] = 0.0;   // the coarse iterate starts from zero (its ghost lines stay zero)
+  }
 }
 
 // x_out = x_in + P e_c at fine point (i, j) (x_in and x_out may be the same
@@ -1011,9 +1016,8 @@ void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, 
   {
     Bracket b(mk, l, BMG_K_RESID_RESTRICT);
     per_residual<FU>(L, cur, f, L.r, nullptr, done, s);
-    k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, done);
+    k_p_restrict<FU><<<pgrid(C.g.nx, C.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, L.r, C.f, C.x, done);
     count_launch();
-    cudaMemsetAsync(C.x, 0, C.g.ps() * sizeof(double), s);
   }
   per_vcycle<FU>(P, l + 1, C.x, C.f, done, s, mk);
   {
