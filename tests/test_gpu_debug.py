@@ -152,3 +152,39 @@ def test_shrunk_extents_are_caught_and_skipped(debug_lib):
         assert again is None                      # taken records are cleared
     exact, record = got["after"]
     assert exact and record is None
+
+
+FULL = r"""
+import hashlib, json, sys, numpy as np, torch
+import workloads as w
+import paper_2502_05279_gb300 as bmg
+kind, planes, f = w.lognormal_problem(8191, 2.0, 32.0, seed_k=4, seed_f=7)
+coef, rhs = torch.from_numpy(planes).cuda(), torch.from_numpy(f).cuda()
+del planes
+out = {"debug": bmg.debug_build()}
+for prec in ("fp64", "fp32", "bf16"):
+    h = bmg.Hierarchy(kind, coef, precision=prec, arith="fused")
+    x, it, _, _ = h.solve(rhs, tol=0.0, maxit=2)
+    out[prec] = [hashlib.sha256(x.cpu().numpy().tobytes()).hexdigest(), bmg.debug_take()]
+    h.close()
+    del x
+    torch.cuda.empty_cache()
+print(json.dumps(out))
+"""
+
+
+def test_full_size_workload_records_nothing_and_matches_release(debug_lib):
+    """The 8191^2 log-normal workload (two cycles or refinement steps in each
+    precision, the launch configuration of the bench): the debug library
+    records no bounds failure and returns the release library's bits (the
+    release library is compared with the oracle at this size elsewhere)."""
+    dbg = run_child(FULL)
+    env = {k: v for k, v in os.environ.items() if k != "BMG_LIB"}
+    out = subprocess.run([sys.executable, "-c", FULL], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=900)
+    assert out.returncode == 0, out.stderr[-3000:]
+    rel = json.loads(out.stdout.strip().splitlines()[-1])
+    assert dbg["debug"] and not rel["debug"]
+    for prec in ("fp64", "fp32", "bf16"):
+        assert dbg[prec][1] is None, (prec, dbg[prec][1])
+        assert dbg[prec][0] == rel[prec][0], prec
