@@ -132,3 +132,26 @@ def test_neumann_sides_bitwise(bmg, sides, nx, ny, precision):
     assert np.array_equal(host(x)[1:ny + 1, 1:nx + 1], xw[1:ny + 1, 1:nx + 1])
     check_history(h.history(), hw)
     h.close()
+
+
+@pytest.mark.parametrize("smoother", ["line", "yline", "xyline"])
+@pytest.mark.parametrize("nx,ny,kind", [(100, 37, 9), (37, 100, 5), (200, 129, 9)])
+@pytest.mark.parametrize("precision,nbf", [("fp64", None), ("fp32", 0)])
+def test_general_size_line_relaxation_bitwise(bmg, smoother, nx, ny, kind, precision, nbf):
+    """Line relaxation in either direction (and alternating) on an embedded
+    nx x ny problem: the identity rows outside the caller's grid decouple, so
+    the embedded lines are solved as the oracle's embedding solves them."""
+    _, planes, f = w.general_size_problem(nx, ny, kind)
+    pn, fn = bx.embed(planes, f)
+    levels = bx.setup(kind, pn, smoother=smoother)
+    if precision == "fp64":
+        xw, hw = bx.solve(levels, fn, tol=1e-10, maxit=100)
+    else:
+        xw, hw = mx.solve_ir(levels, mx.lower(levels, nbf), fn, tol=1e-10, maxit=100)
+    xw = bx.extract(xw, nx, ny)
+    h = bmg.Hierarchy(kind, caller_planes(kind, planes), precision=precision, smoother=smoother)
+    x, it, rr, ok = h.solve(dev(f), tol=1e-10, maxit=100)
+    assert ok and it == len(hw) - 1
+    assert np.array_equal(host(x)[1:ny + 1, 1:nx + 1], xw[1:ny + 1, 1:nx + 1])
+    check_history(h.history(), hw)
+    h.close()
