@@ -1281,7 +1281,7 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
   const int ic0 = bx * TXC + 1, jc0 = by * TYC + 1;
   const int i0 = 2 * ic0 - 1, j0 = 2 * jc0 - 1;
   const int tid = threadIdx.y * TXC + threadIdx.x;
-  for (int k = tid; k < RFX * RFY; k += TXC * TYC) {
+  auto fine = [&](int k) {
     int li = k % RFX, lj = k / RFX;
     int i = i0 + li, j = j0 + lj;
     T val = T(0);
@@ -1290,6 +1290,16 @@ __device__ __forceinline__ void resid_restrict_body(const StencilView<T, S>& v, 
       val = row_residual<T, S, NINE, true, FU>(v, x, p, f[p]);
     }
     r[lj][li] = val;
+  };
+  if constexpr (sizeof(T) == 4) {
+    // FP32 levels wait on loads: unrolled, the residuals' loads of all of a
+    // thread's points can be in flight together
+    constexpr int NQ = (RFX * RFY + TXC * TYC - 1) / (TXC * TYC);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (tid + q * TXC * TYC < RFX * RFY) fine(tid + q * TXC * TYC);
+  } else {
+    for (int k = tid; k < RFX * RFY; k += TXC * TYC) fine(k);
   }
   __syncthreads();
   int ic = ic0 + threadIdx.x, jc = jc0 + threadIdx.y;
