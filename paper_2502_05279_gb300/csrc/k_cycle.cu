@@ -207,10 +207,32 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ L, const T* __r
   coarse_solve_body<T>(n, L, f, x, y);
 }
 
+// x += scale_applied * e32 (the per-point operation of ir_update_body), IRU_COLS
+// points of a row per thread, BX apart: every load is issued before the first
+// store, so that a thread keeps several in flight.
+constexpr int IRU_COLS = 4;
 __global__ void k_ir_update(int n, double* __restrict__ x, const float* __restrict__ e32, const Ctl* ctl) {
   pdl_enter();
   if (ctl->done) return;
-  ir_update_body(n, x, e32, ctl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+  const int i0 = blockIdx.x * (BX * IRU_COLS) + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (j > n) return;
+  const double s = ctl->scale_applied;
+  double xv[IRU_COLS];
+  float ev[IRU_COLS];
+#pragma unroll
+  for (int q = 0; q < IRU_COLS; ++q) {
+    const size_t p = (size_t)j * (n + 2) + i0 + q * BX;
+    if (i0 + q * BX <= n) {
+      xv[q] = x[p];
+      ev[q] = e32[p];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < IRU_COLS; ++q) {
+    const size_t p = (size_t)j * (n + 2) + i0 + q * BX;
+    if (i0 + q * BX <= n && BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2)))
+      x[p] = radd(xv[q], pow2_times_widened(s, ev[q]));
+  }
 }
 
 template <bool FU>
@@ -618,7 +640,7 @@ void launch_norm_finalize(const double* partials, int np, void* ctl, int phase, 
 }
 
 void launch_ir_update(int n, double* x, const float* e32, void* ctl, cudaStream_t s) {
-  pdl_launch(k_ir_update, grid2(n, n), dim3(BX, BY), 0, s, n, x, e32, (const Ctl*)ctl);
+  pdl_launch(k_ir_update, grid2((n + IRU_COLS - 1) / IRU_COLS, n), dim3(BX, BY), 0, s, n, x, e32, (const Ctl*)ctl);
   count_launch();
 }
 
