@@ -730,16 +730,10 @@ __device__ __forceinline__ double zval(const double* z, const float* z32, double
   return z32 ? pow2_times_widened(s, z32[p]) : z[p];   // s * fl64(z32) is exact: s is a power of two
 }
 
-// An inner product over the grid in the canonical order; step(acc, p) adds
-// point p's product to the running sum.
-template <class F>
-__device__ __forceinline__ void ordered_partial(int n, int ld, double* partials, F step) {
-  double acc = 0.0;
-  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
-    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) acc = step(acc, (size_t)j * ld + i);
-  double tot = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
+// FCG_COLS columns of a row per thread iteration (NORM_THREADS apart): their
+// loads are issued together, and the running sum still takes the columns in
+// the canonical order.
+constexpr int FCG_COLS = 4;
 
 template <bool FU>
 __global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __restrict__ z,
@@ -748,7 +742,25 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_zq(int n, const double* __
   pdl_enter();
   if (ctl->done) return;
   const double s = ctl->scale_applied;
-  ordered_partial(n, n + 2, partials, [&](double acc, size_t p) { return madd<FU>(acc, zval(z, z32, s, p), q[p]); });
+  const int ld = n + 2;
+  double acc = 0.0;
+  for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS * FCG_COLS) {
+      double zv[FCG_COLS], qv[FCG_COLS];
+#pragma unroll
+      for (int c = 0; c < FCG_COLS; ++c) {
+        const size_t p = (size_t)j * ld + i + c * NORM_THREADS;
+        if (i + c * NORM_THREADS <= n) {
+          zv[c] = zval(z, z32, s, p);
+          qv[c] = q[p];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < FCG_COLS; ++c)
+        if (i + c * NORM_THREADS <= n) acc = madd<FU>(acc, zv[c], qv[c]);
+    }
+  double tot = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 __device__ __forceinline__ double reduce_partials(const double* partials, int np) {
@@ -779,21 +791,31 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_reduce(const double* __res
   }
 }
 
+// FCG_COLS points of a row per thread, FBX apart, every load before the first store
 template <bool FU>
 __global__ void k_fcg_direction(int n, const double* __restrict__ z, const float* __restrict__ z32,
                                 double* __restrict__ pv, const Ctl* ctl) {
   pdl_enter();
   if (ctl->done) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > n || j > n) return;
-  size_t p = (size_t)j * (n + 2) + i;
-  if (!BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2))) return;
-  double zp = zval(z, z32, ctl->scale_applied, p);
-  if (ctl->first)
-    pv[p] = zp;
-  else
-    pv[p] = madd<FU>(zp, ctl->beta, pv[p]);
+  const int i0 = blockIdx.x * (FBX * FCG_COLS) + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (j > n) return;
+  const double s = ctl->scale_applied, beta = ctl->beta;
+  const bool first = ctl->first;
+  double zp[FCG_COLS], pp[FCG_COLS];
+#pragma unroll
+  for (int c = 0; c < FCG_COLS; ++c) {
+    const size_t p = (size_t)j * (n + 2) + i0 + c * FBX;
+    if (i0 + c * FBX <= n) {
+      zp[c] = zval(z, z32, s, p);
+      pp[c] = first ? 0.0 : pv[p];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < FCG_COLS; ++c) {
+    const size_t p = (size_t)j * (n + 2) + i0 + c * FBX;
+    if (i0 + c * FBX <= n && BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2)))
+      pv[p] = first ? zp[c] : madd<FU>(zp[c], beta, pp[c]);
+  }
 }
 
 // q = A p (row sum a_O p + a_W p_W + ... in canonical order), partial p.q and p.r
@@ -849,19 +871,33 @@ __global__ void __launch_bounds__(NORM_THREADS) k_fcg_update(int n, double* __re
   const double inv = 1.0 / s;
   double acc = 0.0;
   for (int j = 1 + blockIdx.x; j <= n; j += gridDim.x)
-    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS) {
-      size_t p = (size_t)j * ld + i;
-      if (!BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) continue;
-      x[p] = madd<FU>(x[p], alpha, pv[p]);
-      double rr = msub<FU>(r[p], alpha, q[p]);
-      r[p] = rr;
-      if (r32) {
-        r32[p] = __double2float_rn(rmul(rr, inv));
-        z32[p] = 0.0f;
-      } else {
-        z[p] = 0.0;
+    for (int i = 1 + threadIdx.x; i <= n; i += NORM_THREADS * FCG_COLS) {
+      double xv[FCG_COLS], rv[FCG_COLS], pw[FCG_COLS], qv[FCG_COLS];
+#pragma unroll
+      for (int c = 0; c < FCG_COLS; ++c) {
+        const size_t p = (size_t)j * ld + i + c * NORM_THREADS;
+        if (i + c * NORM_THREADS <= n) {
+          xv[c] = x[p];
+          rv[c] = r[p];
+          pw[c] = pv[p];
+          qv[c] = q[p];
+        }
       }
-      acc = madd<FU>(acc, rr, rr);
+#pragma unroll
+      for (int c = 0; c < FCG_COLS; ++c) {
+        const size_t p = (size_t)j * ld + i + c * NORM_THREADS;
+        if (i + c * NORM_THREADS > n || !BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * ld)) continue;
+        x[p] = madd<FU>(xv[c], alpha, pw[c]);
+        const double rr = msub<FU>(rv[c], alpha, qv[c]);
+        r[p] = rr;
+        if (r32) {
+          r32[p] = __double2float_rn(rmul(rr, inv));
+          z32[p] = 0.0f;
+        } else {
+          z[p] = 0.0;
+        }
+        acc = madd<FU>(acc, rr, rr);
+      }
     }
   double tot = block_sum(acc);
   if (threadIdx.x == 0) {
@@ -939,8 +975,8 @@ static void fcg_step(const StencilView<double, double>& v, int kind, double* x, 
   count_launch();
   pdl_launch(k_fcg_reduce, 1, NORM_THREADS, 0, s, partials, g, c, 0);
   count_launch();
-  pdl_launch(k_fcg_direction<FU>, dim3((n + FBX - 1) / FBX, (n + FBY - 1) / FBY), dim3(FBX, FBY), 0, s, n, z, z32,
-             pv, c);
+  pdl_launch(k_fcg_direction<FU>, dim3((n + FBX * FCG_COLS - 1) / (FBX * FCG_COLS), (n + FBY - 1) / FBY),
+             dim3(FBX, FBY), 0, s, n, z, z32, pv, c);
   count_launch();
   if (mark) mark(mark_arg, 1);
   pdl_launch(k_fcg_matvec<FU>, g, NORM_THREADS, 0, s, v, kind == 9, pv, r, q, partials, c);
