@@ -185,8 +185,8 @@ __global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
   pdl_enter();
   const TopDesc q = d[blockIdx.z];
   if (q.ctl->done) return;
-  ir_update_body(q.v.n, q.x, q.e32, q.ctl, blockIdx.x * blockDim.x + threadIdx.x + 1,
-                 blockIdx.y * blockDim.y + threadIdx.y + 1);
+  ir_update_cols(q.v.n, q.x, q.e32, q.ctl->scale_applied, blockIdx.x * (BX * IRU_COLS) + threadIdx.x + 1,
+                 blockIdx.y * blockDim.y + threadIdx.y + 1, BX);
 }
 
 template <bool FU>
@@ -530,7 +530,8 @@ void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s) {
 }
 
 void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
-  pdl_launch(k_ir_update_b, dim3((maxn + BX - 1) / BX, (maxn + BY - 1) / BY, count), dim3(BX, BY), 0, s, d);
+  pdl_launch(k_ir_update_b, dim3((maxn + BX * IRU_COLS - 1) / (BX * IRU_COLS), (maxn + BY - 1) / BY, count),
+             dim3(BX, BY), 0, s, d);
   count_launch();
 }
 

@@ -207,32 +207,12 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ L, const T* __r
   coarse_solve_body<T>(n, L, f, x, y);
 }
 
-// x += scale_applied * e32 (the per-point operation of ir_update_body), IRU_COLS
-// points of a row per thread, BX apart: every load is issued before the first
-// store, so that a thread keeps several in flight.
-constexpr int IRU_COLS = 4;
+// x += scale_applied * e32, IRU_COLS points of a row per thread, BX apart.
 __global__ void k_ir_update(int n, double* __restrict__ x, const float* __restrict__ e32, const Ctl* ctl) {
   pdl_enter();
   if (ctl->done) return;
-  const int i0 = blockIdx.x * (BX * IRU_COLS) + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (j > n) return;
-  const double s = ctl->scale_applied;
-  double xv[IRU_COLS];
-  float ev[IRU_COLS];
-#pragma unroll
-  for (int q = 0; q < IRU_COLS; ++q) {
-    const size_t p = (size_t)j * (n + 2) + i0 + q * BX;
-    if (i0 + q * BX <= n) {
-      xv[q] = x[p];
-      ev[q] = e32[p];
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < IRU_COLS; ++q) {
-    const size_t p = (size_t)j * (n + 2) + i0 + q * BX;
-    if (i0 + q * BX <= n && BMG_IN(DBG_REFINE_STORE, p, (size_t)(n + 2) * (n + 2)))
-      x[p] = radd(xv[q], pow2_times_widened(s, ev[q]));
-  }
+  ir_update_cols(n, x, e32, ctl->scale_applied, blockIdx.x * (BX * IRU_COLS) + threadIdx.x + 1,
+                 blockIdx.y * blockDim.y + threadIdx.y + 1, BX);
 }
 
 template <bool FU>
