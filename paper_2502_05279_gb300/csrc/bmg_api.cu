@@ -1935,6 +1935,8 @@ struct bmg_batch {
   std::vector<void*> tail_dev;
   std::vector<TopDesc> top;
   TopDesc* d_top = nullptr;
+  std::vector<int2> bmap;       // (problem, block) of the top-level residual launches
+  int2* d_bmap = nullptr;
   char* ctls = nullptr;
   size_t ctl_stride = 0;
   int maxit_cap = 0;
@@ -2173,20 +2175,20 @@ void batch_vcycle(bmg_batch* B) {
 void batch_iteration(bmg_batch* B) {
   if (B->precision == BMG_FP64) {
     batch_vcycle(B);
-    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
+    launch_residual_b(B->d_top, B->d_bmap, (int)B->bmap.size(), B->ws, B->arith);
   } else {
     for (int c = 0; c < B->inner; ++c) batch_vcycle(B);
     launch_ir_update_b(B->d_top, B->nprob, B->maxn, B->ws);
-    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
+    launch_ir_residual_b(B->d_top, B->d_bmap, (int)B->bmap.size(), B->ws, B->arith);
   }
   launch_finalize_b(B->d_top, B->nprob, 1, B->ws);
 }
 
 void batch_initial(bmg_batch* B) {
   if (B->precision == BMG_FP64)
-    launch_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
+    launch_residual_b(B->d_top, B->d_bmap, (int)B->bmap.size(), B->ws, B->arith);
   else
-    launch_ir_residual_b(B->d_top, B->nprob, B->maxn, B->ws, B->arith);
+    launch_ir_residual_b(B->d_top, B->d_bmap, (int)B->bmap.size(), B->ws, B->arith);
   launch_finalize_b(B->d_top, B->nprob, 0, B->ws);
 }
 
@@ -2615,6 +2617,17 @@ int batch_finish(bmg_batch* B, int rc) {
                                                       B->tail_count[b]),
                       "batched tails");
   if (!rc) rc = cuda_check(dev_malloc((void**)&B->d_top, sizeof(TopDesc) * nprob), "batched tables");
+  if (!rc) {
+    for (int p = 0; p < nprob; ++p) {
+      const int G = B->hs[p]->n < norm_partials_max() ? B->hs[p]->n : norm_partials_max();
+      for (int b = 0; b < G; ++b) B->bmap.push_back(make_int2(p, b));
+    }
+    rc = cuda_check(dev_malloc((void**)&B->d_bmap, sizeof(int2) * B->bmap.size()), "batched tables");
+    if (!rc)
+      rc = cuda_check(cudaMemcpyAsync(B->d_bmap, B->bmap.data(), sizeof(int2) * B->bmap.size(), cudaMemcpyHostToDevice,
+                                      B->ws),
+                      "batched tables");
+  }
   if (!rc) rc = cuda_check(dev_malloc((void**)&B->d_alldone, sizeof(int)), "batched flag");
   if (!rc) rc = cuda_check(host_malloc((void**)&B->h_alldone, sizeof(int)), "pinned");
   if (!rc) rc = batch_ensure_ctl(B, 64);
@@ -2796,6 +2809,7 @@ void bmg_free_batched(bmg_batch* B) {
     for (auto& g : st) cudaFree(g.d);
   for (void* t : B->tail_dev) cudaFree(t);
   cudaFree(B->d_top);
+  cudaFree(B->d_bmap);
   cudaFree(B->ctls);
   cudaFree(B->d_alldone);
   if (B->h_alldone) cudaFreeHost(B->h_alldone);

@@ -164,15 +164,20 @@ __global__ void k_coarse_b(const LevelDesc<T, S>* __restrict__ d) {
 // problem runs only when b < G = min(n, 1024) of that problem, so every
 // problem keeps the reduction order of its solo solve.
 template <bool FU>
-__global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __restrict__ d) {
+// The residual-type kernels of the top levels run the blocks of every problem's
+// canonical reduction (block b of G = min(n, 1024)) and no others: bmap[k] =
+// (problem, b) for the k-th block of the launch.
+__global__ void __launch_bounds__(NORM_THREADS) k_residual_b(const TopDesc* __restrict__ d,
+                                                             const int2* __restrict__ bmap) {
   pdl_enter();
-  const TopDesc q = d[blockIdx.y];
+  const int2 m = bmap[blockIdx.x];
+  const TopDesc& q = d[m.x];
   const int G = norm_blocks(q.v.n);
-  if (q.ctl->done || (int)blockIdx.x >= G) return;
+  if (q.ctl->done) return;
   if (q.kind == 9)
-    residual_body<double, double, true, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+    residual_body<double, double, true, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, m.y, G);
   else
-    residual_body<double, double, false, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, blockIdx.x, G);
+    residual_body<double, double, false, FU>(q.v, q.x, q.f, (double*)nullptr, q.partials, m.y, G);
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) k_finalize_b(const TopDesc* __restrict__ d, int phase) {
@@ -190,12 +195,14 @@ __global__ void k_ir_update_b(const TopDesc* __restrict__ d) {
 }
 
 template <bool FU>
-__global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* __restrict__ d) {
+__global__ void __launch_bounds__(NORM_THREADS) k_ir_residual_b(const TopDesc* __restrict__ d,
+                                                                const int2* __restrict__ bmap) {
   pdl_enter();
-  const TopDesc q = d[blockIdx.y];
+  const int2 m = bmap[blockIdx.x];
+  const TopDesc& q = d[m.x];
   const int G = norm_blocks(q.v.n);
-  if (q.ctl->done || (int)blockIdx.x >= G) return;
-  ir_residual_body<FU>(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, blockIdx.x, G);
+  if (q.ctl->done) return;
+  ir_residual_body<FU>(q.v, q.kind == 9, q.x, q.f, q.r32, q.e32, q.partials, q.ctl, m.y, G);
 }
 
 // One problem's level-fused tail per CTA.  The iterates and right-hand sides
@@ -516,11 +523,11 @@ void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s) {
   count_launch();
 }
 
-void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
+void launch_residual_b(const TopDesc* d, const int2* bmap, int nblocks, cudaStream_t s, int fused) {
   if (fused)
-    pdl_launch(k_residual_b<true>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
+    pdl_launch(k_residual_b<true>, nblocks, NORM_THREADS, 0, s, d, bmap);
   else
-    pdl_launch(k_residual_b<false>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
+    pdl_launch(k_residual_b<false>, nblocks, NORM_THREADS, 0, s, d, bmap);
   count_launch();
 }
 
@@ -535,11 +542,11 @@ void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s) {
   count_launch();
 }
 
-void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused) {
+void launch_ir_residual_b(const TopDesc* d, const int2* bmap, int nblocks, cudaStream_t s, int fused) {
   if (fused)
-    pdl_launch(k_ir_residual_b<true>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
+    pdl_launch(k_ir_residual_b<true>, nblocks, NORM_THREADS, 0, s, d, bmap);
   else
-    pdl_launch(k_ir_residual_b<false>, dim3(norm_blocks(maxn), count), NORM_THREADS, 0, s, d);
+    pdl_launch(k_ir_residual_b<false>, nblocks, NORM_THREADS, 0, s, d, bmap);
   count_launch();
 }
 

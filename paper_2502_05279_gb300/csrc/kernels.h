@@ -222,10 +222,12 @@ void launch_gs_tile64_b(const LevelDesc<double, double>* d, int count, int n, in
 int strip_timeouts_b();
 template <typename T, typename S>
 void launch_coarse_b(const LevelDesc<T, S>* d, int count, cudaStream_t s);
-void launch_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused = 0);
+// bmap: (problem, block) of each of the nblocks blocks, every problem's
+// min(n, 1024) canonical reduction blocks in turn.
+void launch_residual_b(const TopDesc* d, const int2* bmap, int nblocks, cudaStream_t s, int fused = 0);
 void launch_finalize_b(const TopDesc* d, int count, int phase, cudaStream_t s);
 void launch_ir_update_b(const TopDesc* d, int count, int maxn, cudaStream_t s);
-void launch_ir_residual_b(const TopDesc* d, int count, int maxn, cudaStream_t s, int fused = 0);
+void launch_ir_residual_b(const TopDesc* d, const int2* bmap, int nblocks, cudaStream_t s, int fused = 0);
 void launch_all_done(const char* ctls, size_t stride, int count, int* out, cudaStream_t s);
 template <typename T>
 int rows_cluster(int n);
