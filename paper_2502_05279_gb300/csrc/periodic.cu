@@ -554,40 +554,64 @@ __global__ void k_p_restrict(PGeom g, const double* __restrict__ ci, const doubl
   }
 }
 
-// x_out = x_in + P e_c at fine point (i, j) (x_in and x_out may be the same
-// array): the interpolated value is formed first, then added (coincident e; x-edge LL e_W + LR e_E; y-edge LB e_S + LA e_N; centre
-// ((LSW e_SW + LSE e_SE) + LNW e_NW) + LNE e_NE), coarse neighbours wrapped on a
-// periodic axis, a Dirichlet ghost reading its zero.
+// x_out = x_in + P e_c (x_in and x_out may be the same array), one thread per
+// coarse cell (ic, jc): its coincident point (2ic, 2jc), x-edge point (2ic-1,
+// 2jc), y-edge point (2ic, 2jc-1) and centre point (2ic-1, 2jc-1); a point
+// beyond a Dirichlet side is skipped.  The interpolated value is formed first,
+// then added (coincident e_NE; x-edge LL e_NW + LR e_NE; y-edge LB e_SE + LA
+// e_NE; centre ((LSW e_SW + LSE e_SE) + LNW e_NW) + LNE e_NE, e_SW .. e_NE the
+// cell's coarse corners, wrapped on a periodic axis, a Dirichlet ghost reading
+// its zero).  Every load of the cell is issued before its first store.
 template <bool FU>
 __global__ void k_p_interp(PGeom g, const double* __restrict__ ci, const double* __restrict__ ec,
                            const double* xin, double* xout, const int* done) {
   if (dev::stopped(done)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > g.nx || j > g.ny) return;
-  const PGeom gc = coarse_geom(g);
   const CellMap c = cells_of(g);
-  const size_t psc = c.ps(), p = (size_t)j * (g.nx + 2) + i;
-  auto e = [&](int a, int b) { return ec[gc.at(a, b)]; };
-  auto w = [&](int k, int ic, int jc) { return ci[k * psc + (size_t)jc * (c.ncx + 2) + ic]; };
-  double t;
-  if (!(i & 1) && !(j & 1)) {
-    t = e(i / 2, j / 2);
-  } else if ((i & 1) && !(j & 1)) {
-    const int ic = (i + 1) / 2, jc = j / 2;
-    t = rmul(w(CI_LL, ic, jc), e(ic - 1, jc));
-    t = madd<FU>(t, w(CI_LR, ic, jc), e(ic, jc));
-  } else if (!(i & 1) && (j & 1)) {
-    const int ic = i / 2, jc = (j + 1) / 2;
-    t = rmul(w(CI_LB, ic, jc), e(ic, jc - 1));
-    t = madd<FU>(t, w(CI_LA, ic, jc), e(ic, jc));
-  } else {
-    const int ic = (i + 1) / 2, jc = (j + 1) / 2;
-    t = rmul(w(CI_LSW, ic, jc), e(ic - 1, jc - 1));
-    t = madd<FU>(t, w(CI_LSE, ic, jc), e(ic, jc - 1));
-    t = madd<FU>(t, w(CI_LNW, ic, jc), e(ic - 1, jc));
-    t = madd<FU>(t, w(CI_LNE, ic, jc), e(ic, jc));
+  const int ic = blockIdx.x * blockDim.x + threadIdx.x + 1, jc = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (ic > c.kx() || jc > c.ky()) return;
+  const PGeom gc = coarse_geom(g);
+  const size_t psc = c.ps(), pc = (size_t)jc * (c.ncx + 2) + ic, ld = g.nx + 2;
+  const double e_sw = ec[gc.at(ic - 1, jc - 1)], e_se = ec[gc.at(ic, jc - 1)];
+  const double e_nw = ec[gc.at(ic - 1, jc)], e_ne = ec[gc.at(ic, jc)];
+  auto w = [&](int k) { return ci[k * psc + pc]; };
+  const bool ie = 2 * ic <= g.nx, je = 2 * jc <= g.ny;   // the even column / row exists
+  const size_t pf = (size_t)(2 * jc) * ld + 2 * ic;       // coincident point
+  double x_co = 0, x_xe = 0, x_ye = 0, x_ce, lsw, lse, lnw, lne, ll = 0, lr = 0, lb = 0, la = 0;
+  if (ie && je) x_co = xin[pf];
+  if (je) {
+    x_xe = xin[pf - 1];
+    ll = w(CI_LL);
+    lr = w(CI_LR);
   }
-  if (BMG_IN(DBG_PERIODIC, p, g.ps())) xout[p] = radd(xin[p], t);
+  if (ie) {
+    x_ye = xin[pf - ld];
+    lb = w(CI_LB);
+    la = w(CI_LA);
+  }
+  x_ce = xin[pf - ld - 1];
+  lsw = w(CI_LSW);
+  lse = w(CI_LSE);
+  lnw = w(CI_LNW);
+  lne = w(CI_LNE);
+  const size_t ps = g.ps();
+  if (ie && je && BMG_IN(DBG_PERIODIC, pf, ps)) xout[pf] = radd(x_co, e_ne);
+  if (je) {
+    double t = rmul(ll, e_nw);
+    t = madd<FU>(t, lr, e_ne);
+    if (BMG_IN(DBG_PERIODIC, pf - 1, ps)) xout[pf - 1] = radd(x_xe, t);
+  }
+  if (ie) {
+    double t = rmul(lb, e_se);
+    t = madd<FU>(t, la, e_ne);
+    if (BMG_IN(DBG_PERIODIC, pf - ld, ps)) xout[pf - ld] = radd(x_ye, t);
+  }
+  {
+    double t = rmul(lsw, e_sw);
+    t = madd<FU>(t, lse, e_se);
+    t = madd<FU>(t, lnw, e_nw);
+    t = madd<FU>(t, lne, e_ne);
+    if (BMG_IN(DBG_PERIODIC, pf - ld - 1, ps)) xout[pf - ld - 1] = radd(x_ce, t);
+  }
 }
 
 // L L^T x = f on the coarsest level (one thread, m <= 16): forward then backward
@@ -1024,7 +1048,8 @@ void per_vcycle(PerHier* P, int l, double* x, const double* f, const int* done, 
     // corrected iterate into the array from which the nu2 post-sweeps end in x
     Bracket b(mk, l, BMG_K_INTERP);
     double* dst = L.strip && (P->nu2 & 1) ? L.xb : x;
-    k_p_interp<FU><<<pgrid(L.g.nx, L.g.ny), dim3(PBX, PBY), 0, s>>>(L.g, L.ci, C.x, cur, dst, done);
+    k_p_interp<FU><<<pgrid(L.g.px ? C.g.nx : C.g.nx + 1, L.g.py ? C.g.ny : C.g.ny + 1), dim3(PBX, PBY), 0, s>>>(
+        L.g, L.ci, C.x, cur, dst, done);
     count_launch();
     cur = dst;
   }
