@@ -1336,23 +1336,28 @@ __device__ __forceinline__ void interp_body(int n, const T* __restrict__ ci, con
   T e_sw = ec[pc - ldc - 1], e_se = ec[pc - ldc], e_nw = ec[pc - 1], e_ne = ec[pc];
   size_t pf = (size_t)(2 * jc) * ld + 2 * ic;   // coincident fine point
   const size_t ext = (size_t)ld * ld;
-  if (ic <= nc && jc <= nc && BMG_IN(DBG_INTERP_STORE, pf, ext)) xout[pf] = radd(xin[pf], e_ne);
-  if (jc <= nc) {                                 // x-edge (2ic-1, 2jc)
+  // the cell's iterate values first (xin may be xout, so a load after a store
+  // would wait for it)
+  const bool in_i = ic <= nc, in_j = jc <= nc;
+  const T x_co = in_i && in_j ? xin[pf] : T(0), x_xe = in_j ? xin[pf - 1] : T(0);
+  const T x_ye = in_i ? xin[pf - ld] : T(0), x_ce = xin[pf - ld - 1];
+  if (in_i && in_j && BMG_IN(DBG_INTERP_STORE, pf, ext)) xout[pf] = radd(x_co, e_ne);
+  if (in_j) {                                     // x-edge (2ic-1, 2jc)
     T t = rmul(ci[CI_LL * psc + pc], e_nw);
     t = madd<FU>(t, ci[CI_LR * psc + pc], e_ne);
-    if (BMG_IN(DBG_INTERP_STORE, pf - 1, ext)) xout[pf - 1] = radd(xin[pf - 1], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - 1, ext)) xout[pf - 1] = radd(x_xe, t);
   }
-  if (ic <= nc) {                                 // y-edge (2ic, 2jc-1)
+  if (in_i) {                                     // y-edge (2ic, 2jc-1)
     T t = rmul(ci[CI_LB * psc + pc], e_se);
     t = madd<FU>(t, ci[CI_LA * psc + pc], e_ne);
-    if (BMG_IN(DBG_INTERP_STORE, pf - ld, ext)) xout[pf - ld] = radd(xin[pf - ld], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - ld, ext)) xout[pf - ld] = radd(x_ye, t);
   }
   {                                               // centre (2ic-1, 2jc-1)
     T t = rmul(ci[CI_LSW * psc + pc], e_sw);
     t = madd<FU>(t, ci[CI_LSE * psc + pc], e_se);
     t = madd<FU>(t, ci[CI_LNW * psc + pc], e_nw);
     t = madd<FU>(t, ci[CI_LNE * psc + pc], e_ne);
-    if (BMG_IN(DBG_INTERP_STORE, pf - ld - 1, ext)) xout[pf - ld - 1] = radd(xin[pf - ld - 1], t);
+    if (BMG_IN(DBG_INTERP_STORE, pf - ld - 1, ext)) xout[pf - ld - 1] = radd(x_ce, t);
   }
 }
 
