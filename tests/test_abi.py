@@ -141,3 +141,22 @@ def test_release_library_has_no_debug_checks(libpath):
     assert e.value.code == bmg._lib.BMG_EINVAL
     assert bmg.lib.bmg_strerror(-8).decode() == "debug bounds check failed"
     assert bmg.lib.bmg_debug_site_name(1).decode() == "point Gauss-Seidel store"
+
+
+def test_header_is_a_c_abi(libpath, tmp_path):
+    """include/bmg.h compiles as strict C99 (-pedantic -Werror) and a C program
+    links against the library and makes the calls that need no GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(libpath)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_check.c"), "-L", libdir, "-lbmg", f"-Wl,-rpath,{libdir}",
+                        "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("ok ") == 7
