@@ -494,8 +494,8 @@ int bmg_relax_line(int n, int kind, const double* coef, const double* f, double*
 
 /* ---- debug build ------------------------------------------------------- */
 /* libbmg_debug.so (the same sources compiled with -DBMG_DEBUG) checks, in its
- * kernels, the index of each global store and the source range of each
- * asynchronous row copy against the logical extent of the level array it
+ * cycle and setup kernels, the index of each global store and the source range
+ * of each asynchronous row copy against the logical extent of the level array it
  * addresses (the (n+2)^2 points of a level, the guard bands of FP32 arrays
  * included for copies).  A failed check does not trap: the store is skipped
  * (a copy is zero-filled, or reads the array's first element so that its

@@ -120,7 +120,8 @@ const char* dbg_site_name(int site) {
                                          "residual store",
                                          "line relaxation store",
                                          "refinement / FCG store",
-                                         "periodic-sides kernel"};
+                                         "periodic-sides kernel",
+                                         "setup store"};
   return site >= 0 && site < DBG_SITES ? names[site] : "unknown";
 }
 

@@ -158,6 +158,7 @@ enum DbgSite {
   DBG_LINE_STORE,        // line relaxation
   DBG_REFINE_STORE,      // refinement residual and update, FCG vectors
   DBG_PERIODIC,          // kernels of periodic hierarchies (stores and row copies)
+  DBG_SETUP_STORE,       // setup: stencil preparation, 1/a_O, Dendy weights, Galerkin operator
   DBG_SITES
 };
 struct DbgRecord {

@@ -39,6 +39,7 @@ __global__ void k_prepare(int n, int nx, int ny, int kind, const double* __restr
       if (i > 1 && j < ny) nw = in[4 * psi + q];
     }
   }
+  if (!BMG_IN(DBG_SETUP_STORE, p, ps)) return;
   st[p] = o;
   st[ps + p] = w;
   st[2 * ps + p] = s;
@@ -54,7 +55,7 @@ __global__ void k_dinv(int n, double* __restrict__ st, int* err) {
   size_t ps = plane_size(n), p = (size_t)j * (n + 2) + i;
   double o = st[p];
   if (!(o > 0.0)) atomicExch(err, 1);
-  st[5 * ps + p] = rdiv(1.0, o);
+  if (BMG_IN(DBG_SETUP_STORE, p, ps)) st[5 * ps + p] = rdiv(1.0, o);
 }
 
 // ---- Dendy interpolation -------------------------------------------------
@@ -102,6 +103,7 @@ __global__ void k_dendy(int n, const double* __restrict__ st, double* __restrict
   int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
   if (ic > nc + 1 || jc > nc + 1) return;
   size_t pc = (size_t)jc * ldc + ic, psc = plane_size(nc);
+  if (!BMG_IN(DBG_SETUP_STORE, pc, psc)) return;
   if (ic == 0 || jc == 0) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) ci[k * psc + pc] = 0.0;
@@ -137,6 +139,7 @@ __global__ void k_rap(int n, const double* __restrict__ st, const double* __rest
   int nc = (n - 1) / 2, ldc = nc + 2, ld = n + 2;
   if (ic > nc + 1 || jc > nc + 1) return;
   size_t psc = plane_size(nc), pc = (size_t)jc * ldc + ic;
+  if (!BMG_IN(DBG_SETUP_STORE, pc, psc)) return;
   if (ic == 0 || jc == 0 || ic == nc + 1 || jc == nc + 1) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) stc[k * psc + pc] = 0.0;
