@@ -638,8 +638,8 @@ def line_problem(case, n):
     return problem(case, n)
 
 
-@pytest.mark.parametrize("case,n", [("poisson", 63), ("lognormal", 255), ("binary", 127), ("aniso", 127),
-                                    ("anisoy", 127)])
+@pytest.mark.parametrize("case,n", [("poisson", 3), ("lognormal", 7), ("poisson", 63), ("lognormal", 255),
+                                    ("binary", 127), ("aniso", 127), ("anisoy", 127)])
 @pytest.mark.parametrize("sweeps", [1, 2])
 @pytest.mark.parametrize("axis", ["x", "y"])
 def test_line_relax_step_bitwise(bmg, case, n, sweeps, axis):

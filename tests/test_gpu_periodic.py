@@ -282,3 +282,21 @@ def test_fcg_needs_fewer_steps_and_solves(bmg):
     P = pr.prepare(kind, planes, px, py)
     r = pr.residual(P, x.cpu().numpy(), f, px, py)
     assert bx.norm(r) <= 2e-10 * bx.norm(pr.residual(P, np.zeros_like(f), f, px, py))
+
+
+@pytest.mark.parametrize("axes", AXES)
+def test_fcg_on_the_smallest_grid_is_one_direct_solve(bmg, axes):
+    """A one-level periodic hierarchy: the preconditioner is the coarsest
+    solve itself, so one FCG step reaches the solution to rounding, bit for
+    bit the oracle's step in the device's inner-product order."""
+    from reduction_order import device_inner
+    kind, planes, f, px, py = problem(3, axes)
+    levels = pr.setup(kind, planes, px, py)
+    assert len(levels) == 1
+    x_d, h_d = pr.solve_fcg(levels, f, tol=1e-12, maxit=5, inner=device_inner(False))
+    h = hierarchy(bmg, kind, planes, axes, krylov="fcg")
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-12, maxit=5)
+    assert ok and it == 1 == len(h_d) - 1 and rr <= 1e-13
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_d))
+    assert h.history() == h_d
+    h.close()
