@@ -300,3 +300,36 @@ def test_fcg_on_the_smallest_grid_is_one_direct_solve(bmg, axes):
     assert np.array_equal(interior(x.cpu().numpy()), interior(x_d))
     assert h.history() == h_d
     h.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 2)])
+def test_fcg_other_sweep_counts_bitwise(bmg, nu1, nu2):
+    """FCG around periodic cycles of other sweep counts (odd and even numbers of
+    post-sweeps move the strip levels' iterate differently)."""
+    from reduction_order import device_inner
+    kind, planes, f, px, py = problem(63, "xy", seed=66)
+    levels = pr.setup(kind, planes, px, py, arith="fused")
+    x_d, h_d = pr.solve_fcg(levels, f, tol=1e-10, maxit=40, nu1=nu1, nu2=nu2, inner=device_inner(True))
+    h = hierarchy(bmg, kind, planes, "xy", arith="fused", krylov="fcg", nu1=nu1, nu2=nu2, smoother="tile")
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=40)
+    assert ok and it == len(h_d) - 1
+    assert np.array_equal(interior(x.cpu().numpy()), interior(x_d))
+    assert h.history() == h_d
+    h.close()
+
+
+def test_fcg_zero_rhs_maxit_zero_and_nan(bmg):
+    kind, planes, f, px, py = problem(63, "x")
+    h = hierarchy(bmg, kind, planes, "x", krylov="fcg")
+    x, it, rr, ok = h.solve(torch.zeros_like(torch.from_numpy(f)).cuda())
+    assert ok and it == 0 and not x.any()
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), maxit=0)
+    assert not ok and it == 0 and not x.any()
+    g = f.copy()
+    g[5, 7] = np.nan
+    with pytest.raises(bmg.BmgError) as e:
+        h.solve(torch.from_numpy(g).cuda())
+    assert e.value.code == -5
+    x, it, rr, ok = h.solve(torch.from_numpy(f).cuda(), tol=1e-10, maxit=60)   # still usable
+    assert ok
+    h.close()
