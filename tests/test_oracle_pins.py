@@ -733,3 +733,23 @@ def test_line_directions_follow_the_anisotropy():
     assert factor["y", "point"] > 0.9 and factor["y", "line"] > 0.9, factor
     assert factor["y", "yline"] < 0.1 and factor["y", "xyline"] < 0.1, factor
     assert factor["x", "yline"] > 0.9 and factor["x", "xyline"] < 0.1, factor
+
+
+@pytest.mark.parametrize("case", ["lognormal", "binary", "aniso"])
+def test_transposed_stencil_is_the_permuted_operator(case):
+    """workloads.transposed_stencil: the assembled matrix of the transposed
+    planes is P A P^T, P the permutation (i, j) -> (j, i) of the unknowns, and
+    transposing twice gives the planes back."""
+    n = 15
+    if case == "aniso":
+        planes = w.anisotropic5(n, 1e-2)
+    else:
+        _, planes, _ = (w.lognormal_problem(n, 2.0, 8.0, seed_k=4, seed_f=7) if case == "lognormal"
+                        else w.binary_contrast_problem(n, 4, seed_k=2, seed_f=3))
+    planes = bx.drop_ghost_couplings(np.array(planes))
+    A = sparse_A(planes).toarray()
+    B = sparse_A(transposed(planes)).toarray()
+    idx = np.arange(n * n).reshape(n, n)        # unknown (i, j) at row j, column i
+    perm = idx.T.reshape(-1)                    # (i, j) of the transposed grid is (j, i) of the original
+    assert np.array_equal(B, A[np.ix_(perm, perm)])
+    assert np.array_equal(transposed(transposed(planes))[:, 1:-1, 1:-1], planes[:, 1:-1, 1:-1])
