@@ -271,6 +271,10 @@ def run_periodic(args, rank, local_rank, world):
     x_host = torch.empty_like(rhs_host).pin_memory()
     rhs_dev, x_dev = torch.empty_like(rhs), torch.empty_like(rhs)
     e2e_cycles = 0
+    rhs_dev.copy_(rhs_host, non_blocking=True)          # one untimed step: the graph for these buffers
+    x_dev.zero_()
+    hf.solve(rhs_dev, x_dev, tol=1e-10, maxit=args.maxit_vcycle)
+    torch.cuda.synchronize()
     ranks.barrier()
     t0 = time.perf_counter()
     for _ in range(2):
@@ -693,6 +697,12 @@ def run_ours(args, rank, local_rank, world):
     x_dev = torch.empty_like(rhs)
     e2e_steps = 2
     e2e_cycles = 0
+    # one untimed step: the solve's graph is captured for these buffers (a warm-up, as for the
+    # device-timed steps); every timed step still copies its inputs in and its result out
+    rhs_dev.copy_(rhs_host, non_blocking=True)
+    x_dev.zero_()
+    h.solve(rhs_dev, x_dev, tol=1e-10, maxit=500)
+    torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
